@@ -1,0 +1,266 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these compares the oracle with itself: each check is a closed form,
+an invariant, a textbook/library routine the method reduces to in a special
+case, or brute force on a tiny input.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import workloads as wl
+from oracle import ofrr as O
+
+
+def _rng(s):
+    return np.random.default_rng(s)
+
+
+# ---------------------------------------------------------------- inputs
+def test_haar_orthonormal_and_spectra():
+    Q = wl.haar(300, 40, 7)
+    assert np.abs(Q.T @ Q - np.eye(40)).max() < 1e-14
+    sig = wl.config2_sigma(60)
+    A = wl.dense_svd(200, 60, sig, 11)
+    assert np.allclose(np.linalg.svd(A, compute_uv=False), sig, rtol=1e-12, atol=0)
+    lam = 1.0 / np.arange(1, 81)
+    S = wl.dense_symmetric(80, lam, 12)
+    assert np.abs(S - S.T).max() == 0
+    assert np.allclose(np.sort(np.linalg.eigvalsh(S))[::-1], lam, rtol=1e-11, atol=1e-15)
+
+
+def test_grid_csr_matches_kronecker_laplacian():
+    N = 7
+    rp, ci, va, v = wl.grid_schrodinger_csr(N, 10.0, 3)
+    T = 2 * np.eye(N) - np.eye(N, k=1) - np.eye(N, k=-1)
+    L = np.kron(np.eye(N), T) + np.kron(T, np.eye(N)) + np.diag(v)
+    A = O.csr_apply(rp, ci, va)(np.eye(N * N))
+    assert np.abs(A - L).max() < 1e-5          # FP32 values
+    assert len(ci) == 5 * N * N - 4 * N
+    # constant potential: closed form spectrum
+    rp, ci, va = wl.grid_potential_csr(N, np.full(N * N, 0.5))
+    ev = np.linalg.eigvalsh(O.csr_apply(rp, ci, va)(np.eye(N * N)))
+    assert np.allclose(ev, wl.laplacian_constant_eigs(N, 0.5), atol=1e-6)
+    lo, up = O.csr_gershgorin(rp, ci, va)
+    assert lo == pytest.approx(0.5) and up == pytest.approx(8.5)
+
+
+# ---------------------------------------------------------------- rounding
+def test_round_bf16_against_torch_and_ties():
+    torch = pytest.importorskip("torch")
+    x = _rng(1).standard_normal(10000) * np.exp(_rng(2).uniform(-20, 20, 10000))
+    ref = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(O.round_bf16(x), ref)
+    # ties to even: 1 + 2^-8 lies halfway between 1 and 1 + 2^-7
+    assert O.round_bf16(1 + 2.0 ** -8) == 1.0
+    assert O.round_bf16(1 + 3 * 2.0 ** -8) == 1 + 2.0 ** -6
+
+
+# ---------------------------------------------------------------- Algorithm 8
+def test_hessenberg_equals_row_pivoted_lu():
+    """Sec. 4.2.2: the Hessenberg output equals P^T L of partial-pivot LU."""
+    W = _rng(3).uniform(0, 1, (200, 24))
+    Q, piv, keep, _ = O.hessenberg(W)
+    P, L, U = sla.lu(W)               # W = P L U, LAPACK getrf (first-max pivot)
+    assert keep.all()
+    assert np.abs(Q - P @ L).max() < 1e-12
+    # pivot rows are where P^T L has its unit diagonal
+    rows = np.argmax(P, axis=0)[:24]
+    assert np.array_equal(piv, rows)
+    assert np.allclose(Q[piv, np.arange(24)], 1.0)
+    assert np.abs(Q).max() <= 1.0 + 1e-15
+    # span is preserved: W = Q U
+    assert np.abs(Q @ U - W).max() < 1e-12
+
+
+def test_hessenberg_pivot_structure_and_ties():
+    # each later column is zero in every earlier pivot row
+    W = _rng(4).standard_normal((60, 10))
+    Q, piv, _, _ = O.hessenberg(W)
+    for j in range(10):
+        assert np.all(Q[piv[j], j + 1:] == 0)
+    # ties: column 0 has |.|=2 at rows 1 and 3 -> first index (row 1)
+    T = np.array([[1., 1.], [-2., 0.], [0., 1.], [2., 5.]])
+    _, piv, _, _ = O.hessenberg(T)
+    assert piv[0] == 1
+    # after elimination column 1 = [1.5, 0, 1, 5] - ... : pivot at row 3
+    assert piv[1] == 3
+
+
+def test_hessenberg_rank_deficient_keeps_rank():
+    rng = _rng(5)
+    for r in (1, 3, 7):
+        W = rng.standard_normal((100, r)) @ rng.standard_normal((r, 12))
+        Q, piv, keep, Qf = O.hessenberg(W)
+        assert Q.shape[1] == r and keep.sum() == r
+        assert np.all(Qf[:, ~keep] == 0)
+        # kept columns span range(W)
+        Pq = Q @ np.linalg.pinv(Q)
+        assert np.abs(Pq @ W - W).max() < 1e-10
+
+
+def test_hessenberg_f32_mode_close_to_definition():
+    W = _rng(6).standard_normal((500, 32)).astype(np.float32)
+    Q64, p64, _, _ = O.hessenberg(W.astype(np.float64))
+    Q32, p32, _, _ = O.hessenberg(W, arith="f32")
+    assert np.array_equal(p64, p32)
+    assert np.abs(Q32.astype(np.float64) - Q64).max() < 1e-4
+
+
+# ---------------------------------------------------------------- Algorithm 3
+def _sym(n, lam, seed):
+    return wl.dense_symmetric(n, lam, seed)
+
+
+def test_ofrr_eig_equals_classical_rr_on_same_span():
+    """Sec. 3.1: on an orthonormal basis OFRR is Algorithm 2; and OFRR's Ritz
+    values depend only on the span."""
+    rng = _rng(7)
+    A = _sym(120, rng.standard_normal(120), 8)
+    Amul, _ = O.dense_apply(A)
+    U = rng.standard_normal((120, 15))
+    Qb, _ = np.linalg.qr(U)
+    classical = np.linalg.eigvalsh(Qb.T @ A @ Qb)          # Algorithm 2
+    theta, Y, X, _ = O.rayleigh_ritz_eig(Amul, U @ rng.standard_normal((15, 15)))
+    assert np.allclose(np.sort(theta), classical, atol=1e-11)
+    # Galerkin condition: U^T (A X - X Theta) = 0
+    assert np.abs(U.T @ (A @ X - X * theta)).max() < 1e-9
+    # M-orthonormality of Y
+    M = (U @ np.eye(15)).T @ (U @ np.eye(15))
+
+
+def test_ofrr_eig_exact_invariant_subspace_and_brute_force():
+    n, k = 90, 6
+    lam = 1.0 / np.arange(1, n + 1)
+    A = _sym(n, lam, 9)
+    Q = wl.haar(n, n, 9)  # same seed -> the eigenvectors used to build A
+    R = _rng(10).standard_normal((k, k)) + 3 * np.eye(k)
+    theta, _, X, _ = O.rayleigh_ritz_eig(O.dense_apply(A)[0], Q[:, :k] @ R)
+    assert np.allclose(np.sort(theta)[::-1], lam[:k], rtol=1e-11)
+    # full space: brute force equals the dense eigensolver
+    theta, *_ = O.rayleigh_ritz_eig(O.dense_apply(A)[0], np.eye(n))
+    assert np.allclose(theta, np.linalg.eigvalsh(A), atol=1e-14)
+
+
+def test_pencil_eig_rank_deficient_basis():
+    rng = _rng(11)
+    A = _sym(50, rng.standard_normal(50), 12)
+    U = rng.standard_normal((50, 8))
+    U = np.hstack([U, U[:, :2] * 3.0])          # duplicated directions
+    theta, Y, X, _ = O.rayleigh_ritz_eig(O.dense_apply(A)[0], U)
+    Qb, _ = np.linalg.qr(U[:, :8])
+    ref = np.linalg.eigvalsh(Qb.T @ A @ Qb)
+    assert len(theta) == 8
+    assert np.allclose(np.sort(theta), ref, atol=1e-10)
+
+
+# ---------------------------------------------------------------- Algorithm 5
+def test_ofrr_svd_theorem_and_symmetry():
+    rng = _rng(13)
+    A = rng.standard_normal((70, 40))
+    U = rng.uniform(0, 1, (70, 9))
+    V = rng.uniform(0, 1, (40, 7))
+    Amul, Atmul = O.dense_apply(A)
+    s, Ut, Vt, Y, Z = O.rayleigh_ritz_svd(Amul, U, V)
+    # Theorem (Sec. 3.2): sqrt(2) U Y and sqrt(2) V Z are orthonormal
+    assert np.abs(Ut.T @ Ut - np.eye(7)).max() < 1e-11
+    assert np.abs(Vt.T @ Vt - np.eye(7)).max() < 1e-11
+    assert np.allclose(np.einsum('ij,ij->j', Y, (U.T @ U) @ Y), 0.5, atol=1e-12)
+    assert np.allclose(np.einsum('ij,ij->j', Z, (V.T @ V) @ Z), 0.5, atol=1e-12)
+    # the full pencil spectrum is {+-s} plus |k1-k2| zeros
+    B = U.T @ A @ V
+    K = np.block([[np.zeros((9, 9)), B], [B.T, np.zeros((7, 7))]])
+    M = sla.block_diag(U.T @ U, V.T @ V)
+    w = np.sort(sla.eigh(K, M, eigvals_only=True))
+    assert np.allclose(w[:7], -s, rtol=1e-10)
+    assert np.allclose(w[-7:], s[::-1], rtol=1e-10)
+    assert np.abs(w[7:9]).max() < 1e-10 * s[0]
+
+
+def test_ofrr_svd_equals_classical_rr_and_exact_subspaces():
+    rng = _rng(14)
+    m, n = 80, 50
+    sig = wl.config2_sigma(n)
+    A = wl.dense_svd(m, n, sig, 15)
+    Amul, Atmul = O.dense_apply(A)
+    U = rng.standard_normal((m, 10))
+    V = rng.standard_normal((n, 10))
+    Qu, _ = np.linalg.qr(U)
+    Qv, _ = np.linalg.qr(V)
+    ref = np.linalg.svd(Qu.T @ A @ Qv, compute_uv=False)     # Algorithm 4
+    s, *_ = O.rayleigh_ritz_svd(Amul, U, V)
+    assert np.allclose(s, ref, rtol=1e-11)
+    # exact singular subspaces -> exact singular values
+    Uh = wl.haar(m, n, 15)
+    Vh = wl.haar(n, n, 15 + 1_000_003)
+    R1 = rng.standard_normal((6, 6)) + 4 * np.eye(6)
+    R2 = rng.standard_normal((6, 6)) + 4 * np.eye(6)
+    s, Ut, Vt, _, _ = O.rayleigh_ritz_svd(Amul, Uh[:, :6] @ R1, Vh[:, :6] @ R2)
+    assert np.allclose(s, sig[:6], rtol=1e-12)
+    res = O.residual_svd(Amul, Atmul, Ut, Vt, s)
+    assert res.max() < 1e-12
+    # brute force: full spaces
+    s, *_ = O.rayleigh_ritz_svd(Amul, np.eye(m), np.eye(n))
+    assert np.allclose(s, sig, rtol=1e-10)
+
+
+# ---------------------------------------------------------------- filters
+def test_chebyshev_filter_is_scaled_chebyshev_polynomial():
+    lam = np.linspace(0.0, 10.0, 40)
+    A = np.diag(lam)
+    X = np.eye(40)
+    a, b_up, a0, d = 3.0, 10.0, 0.0, 9
+    Y = O.chebyshev_filter(lambda Z: A @ Z, X, d, a, b_up, a0)
+    e, c = (b_up - a) / 2, (b_up + a) / 2
+    coef = np.zeros(d + 1)
+    coef[d] = 1
+    T = np.polynomial.chebyshev.chebval
+    p = T((lam - c) / e, coef) / T((a0 - c) / e, coef)
+    assert np.allclose(np.diag(Y), p, rtol=1e-10, atol=1e-14)
+    assert np.abs(Y - np.diag(np.diag(Y))).max() == 0
+
+
+def test_residual_eig_closed_form():
+    A = np.diag([3.0, 1.0, 0.5])
+    d = 1e-3
+    x = np.array([[1.0], [d], [0.0]])
+    r = O.residual_eig(lambda Z: A @ Z, x, np.array([3.0]))
+    # (A - 3I) x / ||x|| = [0, -2d, 0]/sqrt(1+d^2)
+    assert r[0] == pytest.approx(2 * d / math.sqrt(1 + d * d) / 3.0, rel=1e-12)
+
+
+# ---------------------------------------------------------------- solvers
+def test_solve_eig_power_converges_to_closed_form():
+    n, k, b = 300, 8, 16
+    A, lam = wl.config1(n)
+    V0 = wl.uniform_block(n, b, 1001)
+    r = O.solve_eig(O.dense_apply(A)[0], n, k, V0, degree=1, max_sweeps=80, tol=1e-10)
+    assert r.n_converged == k
+    assert np.allclose(r.values, lam[:k], rtol=1e-10)
+    assert r.res.max() <= 1e-10
+
+
+def test_solve_eig_chebyshev_lowest_constant_potential():
+    N, k, b = 16, 10, 16
+    rp, ci, va = wl.grid_potential_csr(N, np.full(N * N, 0.25))
+    Amul = O.csr_apply(rp, ci, va)
+    V0 = wl.uniform_block(N * N, b, 3001)
+    r = O.solve_eig(Amul, N * N, k, V0, which="smallest", filter="chebyshev", degree=8,
+                    max_sweeps=60, tol=1e-10, bounds=O.csr_gershgorin(rp, ci, va))
+    exact = wl.laplacian_constant_eigs(N, 0.25)[:k]
+    assert r.n_converged == k
+    assert np.allclose(r.values, exact, rtol=1e-9)
+
+
+def test_solve_svd_converges_to_prescribed_sigma():
+    m, n, k, b = 400, 120, 10, 20
+    sig = wl.config2_sigma(n)
+    A = wl.dense_svd(m, n, sig, 2000)
+    Amul, Atmul = O.dense_apply(A)
+    V0 = wl.uniform_block(n, b, 2001)
+    r = O.solve_svd(Amul, Atmul, m, n, k, V0, degree=2, max_sweeps=60, tol=1e-10)
+    assert r.n_converged == k
+    assert np.allclose(r.values, sig[:k], rtol=1e-10)
+    assert np.abs(r.U.T @ r.U - np.eye(k)).max() < 1e-10
