@@ -1,0 +1,251 @@
+/*
+ * rr.h -- C ABI of the GB300 orthogonalization-free Rayleigh-Ritz library.
+ *
+ * Method: arXiv 2505.00281, "Mixed Precision Orthogonalization-Free
+ * Projection Methods for Eigenvalue and Singular Value Problems".
+ *   - Algorithm 1 (multi-step subspace iteration) coupled with the RR output
+ *     as the next start block (Sec. 2),
+ *   - Algorithm 3 (OFRR for eigenvalue problems: B = U^T A U, M = U^T U,
+ *     B Y = M Y Lambda, U~ = U Y),
+ *   - Algorithm 5 (OFRR for the SVD: the 2x2 block pencil, positive
+ *     eigenvalues, lift sqrt(2) U Y, sqrt(2) V Z; theorem of Sec. 3.2),
+ *   - Algorithm 8 (Hessenberg process for a block, the inner-product-free
+ *     basis step; equal to row-pivoted LU, Sec. 4.2.2),
+ *   - the mixed-precision map of Sec. 4.2 (Fig. 4): low-precision basis and
+ *     products, higher-precision projection, FP64 small solve.
+ *
+ * Conventions for every entry point:
+ *   - All matrices are column-major ("Fortran", Sec. 5.1) with an explicit
+ *     leading dimension; all matrix pointers are DEVICE pointers unless the
+ *     comment says "host".
+ *   - The caller owns every buffer.  The library allocates no device memory:
+ *     scratch space is the caller's workspace (see rr_workspace_size).
+ *   - Calls are asynchronous on `stream` (a cudaStream_t passed as void*;
+ *     NULL = the legacy default stream) except where a comment says the call
+ *     synchronises.  The solvers (rr_eig, rr_svd, rr_batch_svd) synchronise
+ *     the stream to read convergence counts and return only when done.
+ *   - Errors are returned as rr_status; nothing aborts or throws across the
+ *     ABI.  RR_ERR_ARG: invalid sizes/pointers (nothing launched).
+ *     RR_ERR_CUDA: a CUDA launch or runtime call failed (rr_last_error()
+ *     returns its text).  RR_ERR_TIMEOUT: a device-side bounded wait gave up
+ *     (the kernel returned early; outputs are undefined).
+ */
+#ifndef RR_H_
+#define RR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { RR_F64 = 0, RR_F32 = 1, RR_BF16 = 2, RR_E4M3 = 3 } rr_dtype;
+
+typedef enum {
+  RR_OK = 0,
+  RR_ERR_ARG = 1,
+  RR_ERR_CUDA = 2,
+  RR_ERR_NOT_SPD = 3,
+  RR_ERR_NO_CONV = 4,
+  RR_ERR_TIMEOUT = 5,
+  RR_ERR_WORKSPACE = 6,
+  RR_ERR_NAN = 7
+} rr_status;
+
+enum { RR_DENSE = 0, RR_CSR = 1 };
+enum { RR_LARGEST = 0, RR_SMALLEST = 1 };
+enum { RR_POWER = 0, RR_CHEBYSHEV = 1 };
+
+/* The operator A.
+ *   RR_DENSE: m x n FP64, column-major, leading dimension ld >= m.
+ *   RR_CSR:   square n x n (m == n), FP32 values, int32 row_ptr[n+1] and
+ *             col_idx[nnz] (sorted within rows), symmetric (used by rr_eig).
+ * All pointers are device pointers.  The library never writes to them. */
+typedef struct {
+  int32_t kind;
+  int32_t dtype;
+  int64_t m, n, ld, nnz;
+  const void* values;
+  const int32_t* row_ptr;
+  const int32_t* col_idx;
+} rr_operator;
+
+/* Solver parameters (Algorithm 1 inputs A, k, m, iter; Sec. 4.2 precisions). */
+typedef struct {
+  int32_t k;             /* wanted pairs (k <= block)                                */
+  int32_t block;         /* block size b of the subspace                             */
+  int32_t filter;        /* RR_POWER (products per sweep) or RR_CHEBYSHEV            */
+  int32_t degree;        /* power: products per sweep (Alg. 1 "iter"); Chebyshev: d  */
+  int32_t max_sweeps;    /* projections (Alg. 1 "m"), counting both phases           */
+  int32_t which;         /* RR_LARGEST or RR_SMALLEST (RR_SMALLEST needs Chebyshev)  */
+  int32_t basis;         /* RR_F64, RR_F32 or RR_BF16: storage of the basis and of
+                            the operator copy the filter products use                */
+  int32_t hessenberg;    /* 1: Algorithm 8 after each product; 0: inf-norm scaling   */
+  int32_t refine;        /* 1: after `phase1_sweeps` projections, refine with FP64-
+                            accurate residuals and low-precision corrections         */
+  int32_t phase1_sweeps; /* projections of the plain (paper) phase before refining   */
+  double tol;            /* relative residual target (Sec. 5.2.2)                    */
+  double bounds[2];      /* Chebyshev: spectral bounds (lo, up); lo >= up -> computed */
+  const double* v0;      /* n x block FP64 start block (device), e.g. U(0,1)         */
+} rr_params;
+
+typedef struct {
+  int32_t n_converged;   /* wanted pairs with residual <= tol                        */
+  int32_t sweeps;        /* projections performed                                    */
+  int32_t refine_sweeps; /* of which in the refinement phase                         */
+  int32_t cols_dropped;  /* basis columns dropped by Alg. 8 / the whitening (last)   */
+  double max_res;        /* largest residual among the k wanted pairs                */
+  double res_history[64];/* max residual of the wanted pairs after each projection   */
+} rr_info;
+
+/* Text of the last RR_ERR_CUDA (thread-local, static storage). */
+const char* rr_last_error(void);
+
+/* ---------------------------------------------------------------------------
+ * Solvers
+ * ------------------------------------------------------------------------- */
+
+/* Bytes of device workspace rr_eig (svd = 0) or rr_svd (svd = 1) needs. */
+size_t rr_workspace_size(const rr_operator* A, const rr_params* p, int svd);
+
+/* Wanted eigenpairs of a symmetric operator (dense n x n or CSR).
+ * theta: k FP64 (device), ordered by `which`; X: n x k FP64 (device, ld n),
+ * unit 2-norm columns, sign fixed so the largest-|.| entry is positive.
+ * Returns RR_ERR_NO_CONV (outputs filled with the best pairs) when fewer than
+ * k pairs reached tol within max_sweeps.  Synchronises `stream`. */
+rr_status rr_eig(const rr_operator* A, const rr_params* p, double* theta, double* X,
+                 void* ws, size_t ws_bytes, rr_info* info, void* stream);
+
+/* Largest k singular triplets of a dense m x n operator (m >= n) (Alg. 5).
+ * sigma: k FP64 descending; U: m x k; V: n x k (device, FP64, unit columns,
+ * sign fixed so the largest-|.| entry of v is positive).  Synchronises. */
+rr_status rr_svd(const rr_operator* A, const rr_params* p, double* sigma, double* U,
+                 double* V, void* ws, size_t ws_bytes, rr_info* info, void* stream);
+
+/* Bytes of device workspace rr_batch_svd needs for `count` operators. */
+size_t rr_batch_workspace_size(int32_t count, const rr_operator* A, const rr_params* p);
+
+/* `count` independent rr_svd problems (host arrays of operators and of device
+ * output pointers).  One parameter set for all (p->v0 is ignored; each problem
+ * draws its start block from U(0,1) with a counter-based generator seeded by
+ * `seed` + problem index).  per_problem (host, count entries) and info (host,
+ * count entries) receive each problem's status and counts.  The whole batch
+ * runs as one captured CUDA graph launch on `stream`.  Synchronises. */
+rr_status rr_batch_svd(int32_t count, const rr_operator* A, const rr_params* p, uint64_t seed,
+                       double* const* sigma, double* const* U, double* const* V,
+                       void* ws, size_t ws_bytes, rr_status* per_problem, rr_info* info,
+                       void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Stage entry points (the hot-path steps, callable on their own)
+ * ------------------------------------------------------------------------- */
+
+/* Start block and casts (Sec. 5.2: U(0,1) in FP64 cast to the working
+ * precision; Sec. 2: column scaling).  Y(:,j) = X(:,j) / ||X(:,j)||_inf cast to
+ * `dtype` (RR_F64, RR_F32 or RR_BF16); zero columns stay zero.  scale (device,
+ * cols FP64, required) receives the inf-norms. */
+rr_status rr_colscale_cast(int64_t rows, int64_t cols, const double* X, int64_t ldx,
+                           int32_t dtype, void* Y, int64_t ldy, double* scale, void* stream);
+
+/* Cast a dense FP64 m x n operator to `dtype` (RR_F32 or RR_BF16), writing the
+ * column-major copy (ld m) to out_col and, if out_row != NULL, the row-major
+ * copy (element (i,j) at out_row[i*n + j]) used as the K-major operand of
+ * A * V.  `workspace` unused; one pass over A. */
+rr_status rr_cast_operator(int64_t m, int64_t n, const double* A, int64_t lda, int32_t dtype,
+                           void* out_col, void* out_row, void* stream);
+
+/* Low-precision block product (Eq. of Sec. 2, X_iter = A X; Fig. 4 "W = AV"):
+ * C (M x N, FP32, ld ldc) = A_k^T * B + coef[j] * R(:,j)
+ * where A_k is the K x M operand stored K-contiguous (element (kk,i) at
+ * A_k[kk + i*lda]) and B is K x N column-major, both of `dtype` (RR_BF16 or
+ * RR_F32), FP32 accumulation.  R (M x N FP64, ld ldr) and coef (N FP64) may
+ * be NULL (no added term).  This one shape serves both W = A V (A_k = the
+ * row-major copy of A) and Z = A^T W (A_k = the column-major copy). */
+rr_status rr_gemm_lowp(int32_t dtype, int64_t M, int64_t N, int64_t K, const void* A_k,
+                       int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc,
+                       const double* R, int64_t ldr, const double* coef, void* stream);
+
+/* FP64 product C = op(A) * B (+ C if accumulate), op(A) = A (trans = 0, A is
+ * M x K, ld lda) or A^T (trans = 1, A is K x M).  B is K x N FP64 (ld ldb).
+ * Used for the FP64-accurate residual products and by the all-FP64 mode. */
+rr_status rr_gemm_f64(int32_t trans, int64_t M, int64_t N, int64_t K, const double* A,
+                      int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc,
+                      int32_t accumulate, void* stream);
+
+/* Algorithm 8, right-looking Hessenberg process on an n x k block (Sec. 4.2.2).
+ * W (FP32 if arith == RR_F32, FP64 if RR_F64; ld ldw) is overwritten by the
+ * process; the result is also written to Q (dtype qtype: RR_BF16, RR_F32 or
+ * RR_F64; ld ldq; may alias W when the types match).  Skipped columns (pivot
+ * magnitude below tol * the column's entry inf-norm) are set to zero instead
+ * of being compacted.  piv (k int32, device): pivot row per column, -1 if
+ * skipped.  tol <= 0 selects 4*k*eps(arith).  Argmax ties resolve to the
+ * smallest row index.  Arithmetic is IEEE with separately rounded multiply
+ * and subtract (no FMA contraction), so results are reproducible bit for bit.
+ * Needs rr_hessenberg_workspace_size(n, k, arith) bytes of workspace.
+ * Runs as one cooperative launch with one grid barrier per column. */
+size_t rr_hessenberg_workspace_size(int64_t n, int64_t k, int32_t arith);
+rr_status rr_hessenberg(int32_t arith, int64_t n, int64_t k, void* W, int64_t ldw,
+                        int32_t qtype, void* Q, int64_t ldq, int32_t* piv, double tol,
+                        void* ws, size_t ws_bytes, void* stream);
+
+/* Projection products (Alg. 3 lines B = U^T A U, M = U^T U; Alg. 5 U^T A V,
+ * U^T U, V^T V): G (p x q FP64, ld ldg) = X^T Y (+ G if accumulate) for tall
+ * X (n x p) and Y (n x q) of types xtype/ytype (RR_F64, RR_F32, RR_BF16).
+ * Accumulation is FP64 (accurate to FP64 rounding of the exact sum).  Needs
+ * rr_gram_workspace_size(n, p, q) bytes (deterministic split-K partials). */
+size_t rr_gram_workspace_size(int64_t n, int64_t p, int64_t q);
+rr_status rr_gram(int64_t n, int64_t p, int64_t q, int32_t xtype, const void* X, int64_t ldx,
+                  int32_t ytype, const void* Y, int64_t ldy, double* G, int64_t ldg,
+                  int32_t accumulate, void* ws, size_t ws_bytes, void* stream);
+
+/* Small projected problems, FP64 (Alg. 3 line "B Y = M Y Lambda"; Alg. 5).
+ * rr_pencil_eig: H, G (b x b, ld b) symmetric, G positive semidefinite.
+ *   theta (b) ascending; Y (b x b) with Y^T G Y = I on the kept part.
+ *   Whitening by Cholesky with column dropping (a pivot with L_jj^2 <=
+ *   64 u64 max_i G_ii drops column j); dropped directions get theta = NaN and
+ *   a zero column of Y, sorted last.  dropped (host int*, may be NULL).
+ * rr_pencil_svd: B (b1 x b2, ld b1), Gu (b1 x b1), Gv (b2 x b2).
+ *   s (min(b1,b2)) descending, Y (b1 x r), Z (b2 x r) with sqrt(2)-scaled
+ *   normalisation already applied: U~ = U Y, V~ = V Z are orthonormal
+ *   (theorem of Sec. 3.2).  Solved as the whitened SVD of
+ *   Lu^-1 B Lv^-T by one-sided Jacobi (equivalent to the positive half of
+ *   the 2x2 block pencil).
+ * Both need rr_pencil_workspace_size(b1, b2) bytes of workspace and
+ * synchronise nothing (dropped counts are read only when dropped != NULL,
+ * which synchronises). */
+size_t rr_pencil_workspace_size(int64_t b1, int64_t b2);
+rr_status rr_pencil_eig(int64_t b, const double* H, const double* G, double* theta, double* Y,
+                        void* ws, size_t ws_bytes, int32_t* dropped, void* stream);
+rr_status rr_pencil_svd(int64_t b1, int64_t b2, const double* B, const double* Gu,
+                        const double* Gv, double* s, double* Y, double* Z, void* ws,
+                        size_t ws_bytes, int32_t* dropped, void* stream);
+
+/* Sparse block product (a CSR operator applied to a block; Sec. 5.1 CSR):
+ * Y (n x b, FP32 out, ld ldy) = A X with A CSR FP32, X (n x b, dtype xtype
+ * RR_BF16/RR_F32/RR_F64, ld ldx).  FP32 accumulation (FP64 when xtype is F64,
+ * then Y must be FP64: pass ytype RR_F64). */
+rr_status rr_csr_spmm(int64_t n, int64_t b, const int32_t* row_ptr, const int32_t* col_idx,
+                      const float* values, int32_t xtype, const void* X, int64_t ldx,
+                      int32_t ytype, void* Y, int64_t ldy, void* stream);
+
+/* One step of the scaled Chebyshev three-term recurrence (the chebfsi filter
+ * the paper cites in Sec. 2), fused with the CSR product:
+ *   Y_next(:,j) = alpha (A - c I) Y_cur(:,j) - beta * bc_j * Y_prev(:,j)
+ *                 + gamma_j * R(:,j)
+ * with A CSR FP32, Y_cur/Y_prev of dtype ytype (RR_BF16/RR_F32/RR_F64,
+ * ld ld), FP32 accumulation (FP64 when ytype is RR_F64).  Y_next is written
+ * as out_type (ytype or RR_F32; ld ld_next).  Y_prev may be NULL (first step).
+ * bc (beta_col) may be NULL (bc_j = 1); R (FP64, ld ldr) and gamma may be
+ * NULL (no added term). */
+rr_status rr_chebyshev_step(int64_t n, int64_t b, const int32_t* row_ptr,
+                            const int32_t* col_idx, const float* values, int32_t ytype,
+                            const void* Y_cur, const void* Y_prev, int64_t ld, double alpha,
+                            double c, double beta, const double* beta_col, const double* R,
+                            int64_t ldr, const double* gamma, int32_t out_type, void* Y_next,
+                            int64_t ld_next, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RR_H_ */

@@ -1,0 +1,13 @@
+"""GB300 (sm_103a) orthogonalization-free Rayleigh-Ritz library.
+
+The compute path is the CUDA library ``librr.so`` (C ABI declared in
+``include/rr.h``); this package only marshals arguments to it.  Importing
+the package does not load the library; the first call does, and raises if the
+library is missing.  There is no CPU fallback.
+"""
+from ._lib import RR, RrError, lib  # noqa: F401
+from .api import (  # noqa: F401
+    rr_eig, rr_svd, rr_batch_svd, rr_colscale_cast, rr_cast_operator, rr_gemm_lowp,
+    rr_gemm_f64, rr_hessenberg, rr_gram, rr_pencil_eig, rr_pencil_svd, rr_csr_spmm,
+    rr_chebyshev_step, fortran, RrParams, RrOperator, RrInfo,
+)

@@ -1,0 +1,268 @@
+"""Python binding of the C ABI (include/rr.h): argument marshalling only.
+
+Tensors are PyTorch CUDA tensors used as device memory; every computation
+runs in librr.so.  Matrices are column-major: a (rows x cols) tensor with
+stride (1, ld).  ``fortran(t)`` returns such a copy.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from ._lib import RR, RrError, RrInfo, RrOperator, RrParams, check, lib
+
+__all__ = [
+    "fortran", "ld_of", "dense_operator", "csr_operator", "make_params", "rr_eig", "rr_svd",
+    "rr_batch_svd", "rr_colscale_cast", "rr_cast_operator", "rr_gemm_lowp", "rr_gemm_f64",
+    "rr_hessenberg", "rr_gram", "rr_pencil_eig", "rr_pencil_svd", "rr_csr_spmm",
+    "rr_chebyshev_step", "RrParams", "RrOperator", "RrInfo", "DTYPES",
+]
+
+DTYPES = {torch.float64: RR.F64, torch.float32: RR.F32, torch.bfloat16: RR.BF16}
+_BASIS = {"f64": RR.F64, "f32": RR.F32, "bf16": RR.BF16}
+
+
+def fortran(t: torch.Tensor) -> torch.Tensor:
+    """Column-major copy (stride (1, rows)) of a 2-D tensor."""
+    if t.dim() == 1:
+        t = t[:, None]
+    return t.t().contiguous().t()
+
+
+def ld_of(t: torch.Tensor) -> int:
+    if t.dim() == 1:
+        return max(1, t.shape[0])
+    if t.shape[1] == 1 or t.shape[0] == 0:
+        return max(1, t.shape[0])
+    if t.shape[0] == 1:
+        return max(1, t.stride(1))
+    if t.stride(0) != 1:
+        raise ValueError("matrix must be column-major (stride (1, ld))")
+    return t.stride(1)
+
+
+def _p(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ws(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def dense_operator(A: torch.Tensor) -> RrOperator:
+    if A.dtype != torch.float64:
+        raise ValueError("dense operator must be FP64")
+    op = RrOperator(RR.DENSE, RR.F64, A.shape[0], A.shape[1], ld_of(A), 0, A.data_ptr(), None, None)
+    op._keep = (A,)   # the struct holds raw pointers: keep the tensor alive with it
+    return op
+
+
+def csr_operator(row_ptr: torch.Tensor, col_idx: torch.Tensor, values: torch.Tensor) -> RrOperator:
+    n = row_ptr.shape[0] - 1
+    op = RrOperator(RR.CSR, RR.F32, n, n, n, values.shape[0], values.data_ptr(), row_ptr.data_ptr(),
+                    col_idx.data_ptr())
+    op._keep = (row_ptr, col_idx, values)
+    return op
+
+
+def make_params(k, block, degree, max_sweeps, tol, basis="bf16", v0=None, filter=RR.POWER,
+                which=RR.LARGEST, hessenberg=True, refine=True, phase1_sweeps=1, bounds=(0.0, 0.0)):
+    p = RrParams()
+    p.k, p.block, p.filter, p.degree = k, block, filter, degree
+    p.max_sweeps, p.which = max_sweeps, which
+    p.basis = _BASIS[basis] if isinstance(basis, str) else basis
+    p.hessenberg, p.refine, p.phase1_sweeps = int(hessenberg), int(refine), phase1_sweeps
+    p.tol = tol
+    p.bounds[0], p.bounds[1] = bounds
+    p.v0 = None if v0 is None else v0.data_ptr()
+    p._keep = (v0,)
+    return p
+
+
+def _info_dict(info: RrInfo, status: int):
+    sweeps = info.sweeps
+    return {"status": RR.NAMES.get(status, status), "n_converged": info.n_converged,
+            "sweeps": sweeps, "refine_sweeps": info.refine_sweeps, "max_res": info.max_res,
+            "res_history": [info.res_history[i] for i in range(min(sweeps, 64))]}
+
+
+def rr_eig(op: RrOperator, params: RrParams, n: int, device="cuda", stream=None, keep=()):
+    """Wanted eigenpairs.  Returns (theta[k], X[n, k], info dict)."""
+    L = lib()
+    k = params.k
+    theta = torch.empty(k, dtype=torch.float64, device=device)
+    X = fortran(torch.empty(n, k, dtype=torch.float64, device=device))
+    wsb = L.rr_workspace_size(ctypes.byref(op), ctypes.byref(params), 0)
+    if wsb == 0:
+        raise RrError("rr_workspace_size", RR.ERR_ARG)
+    ws = _ws(wsb, device)
+    info = RrInfo()
+    st = L.rr_eig(ctypes.byref(op), ctypes.byref(params), _p(theta), _p(X), _p(ws), ws.numel(),
+                  ctypes.byref(info), _stream(stream))
+    if st not in (RR.OK, RR.ERR_NO_CONV):
+        check("rr_eig", st)
+    return theta, X, _info_dict(info, st)
+
+
+def rr_svd(op: RrOperator, params: RrParams, device="cuda", stream=None, ws=None):
+    """Largest singular triplets.  Returns (sigma[k], U[m, k], V[n, k], info dict)."""
+    L = lib()
+    k, m, n = params.k, op.m, op.n
+    sigma = torch.empty(k, dtype=torch.float64, device=device)
+    U = fortran(torch.empty(m, k, dtype=torch.float64, device=device))
+    V = fortran(torch.empty(n, k, dtype=torch.float64, device=device))
+    wsb = L.rr_workspace_size(ctypes.byref(op), ctypes.byref(params), 1)
+    if wsb == 0:
+        raise RrError("rr_workspace_size", RR.ERR_ARG)
+    if ws is None or ws.numel() < wsb:
+        ws = _ws(wsb, device)
+    info = RrInfo()
+    st = L.rr_svd(ctypes.byref(op), ctypes.byref(params), _p(sigma), _p(U), _p(V), _p(ws), ws.numel(),
+                  ctypes.byref(info), _stream(stream))
+    if st not in (RR.OK, RR.ERR_NO_CONV):
+        check("rr_svd", st)
+    return sigma, U, V, _info_dict(info, st)
+
+
+def rr_batch_svd(ops, params: RrParams, seed: int, device="cuda", stream=None):
+    """Batched SVDs in one graph launch.  Returns (list of (sigma, U, V), statuses, infos)."""
+    L = lib()
+    cnt = len(ops)
+    arr = (RrOperator * cnt)(*ops)
+    k = params.k
+    outs = [(torch.empty(k, dtype=torch.float64, device=device),
+             fortran(torch.empty(o.m, k, dtype=torch.float64, device=device)),
+             fortran(torch.empty(o.n, k, dtype=torch.float64, device=device))) for o in ops]
+    S = (ctypes.c_void_p * cnt)(*[o[0].data_ptr() for o in outs])
+    U = (ctypes.c_void_p * cnt)(*[o[1].data_ptr() for o in outs])
+    V = (ctypes.c_void_p * cnt)(*[o[2].data_ptr() for o in outs])
+    wsb = L.rr_batch_workspace_size(cnt, arr, ctypes.byref(params))
+    if wsb == 0:
+        raise RrError("rr_batch_workspace_size", RR.ERR_ARG)
+    ws = _ws(wsb, device)
+    per = (ctypes.c_int32 * cnt)()
+    infos = (RrInfo * cnt)()
+    st = L.rr_batch_svd(cnt, arr, ctypes.byref(params), seed, S, U, V, _p(ws), ws.numel(), per, infos,
+                        _stream(stream))
+    if st not in (RR.OK, RR.ERR_NO_CONV):
+        check("rr_batch_svd", st)
+    return outs, [int(x) for x in per], [_info_dict(infos[i], per[i]) for i in range(cnt)]
+
+
+# ---------------------------------------------------------------- stages
+def rr_colscale_cast(X, dtype, stream=None):
+    rows, cols = X.shape
+    Y = fortran(torch.empty(rows, cols, dtype=dtype, device=X.device))
+    scale = torch.empty(cols, dtype=torch.float64, device=X.device)
+    check("rr_colscale_cast", lib().rr_colscale_cast(rows, cols, _p(X), ld_of(X), DTYPES[dtype], _p(Y),
+                                                      ld_of(Y), _p(scale), _stream(stream)))
+    return Y, scale
+
+
+def rr_cast_operator(A, dtype, row_copy=True, stream=None):
+    m, n = A.shape
+    col = fortran(torch.empty(m, n, dtype=dtype, device=A.device))
+    row = torch.empty(m * n, dtype=dtype, device=A.device) if row_copy else None
+    check("rr_cast_operator", lib().rr_cast_operator(m, n, _p(A), ld_of(A), DTYPES[dtype], _p(col),
+                                                      _p(row), _stream(stream)))
+    return col, row
+
+
+def rr_gemm_lowp(dtype, M, N, K, A_k, lda, B, ldb, C=None, R=None, coef=None, stream=None):
+    if C is None:
+        C = fortran(torch.empty(M, N, dtype=torch.float32, device=B.device))
+    check("rr_gemm_lowp", lib().rr_gemm_lowp(dtype, M, N, K, _p(A_k), lda, _p(B), ldb, _p(C), ld_of(C),
+                                              _p(R), ld_of(R) if R is not None else 0, _p(coef),
+                                              _stream(stream)))
+    return C
+
+
+def rr_gemm_f64(trans, A, B, C=None, accumulate=False, stream=None):
+    M = A.shape[1] if trans else A.shape[0]
+    K = A.shape[0] if trans else A.shape[1]
+    N = B.shape[1]
+    if C is None:
+        C = fortran(torch.zeros(M, N, dtype=torch.float64, device=B.device))
+    check("rr_gemm_f64", lib().rr_gemm_f64(int(trans), M, N, K, _p(A), ld_of(A), _p(B), ld_of(B), _p(C),
+                                            ld_of(C), int(accumulate), _stream(stream)))
+    return C
+
+
+def rr_hessenberg(W, qtype=torch.bfloat16, tol=0.0, stream=None):
+    """Algorithm 8 on W (FP32 or FP64, modified in place).  Returns (Q, piv, err)."""
+    n, k = W.shape
+    arith = DTYPES[W.dtype]
+    Q = fortran(torch.empty(n, k, dtype=qtype, device=W.device))
+    piv = torch.empty(k, dtype=torch.int32, device=W.device)
+    L = lib()
+    wsb = L.rr_hessenberg_workspace_size(n, k, arith)
+    ws = _ws(wsb, W.device)
+    check("rr_hessenberg", L.rr_hessenberg(arith, n, k, _p(W), ld_of(W), DTYPES[qtype], _p(Q), ld_of(Q),
+                                           _p(piv), tol, _p(ws), ws.numel(), _stream(stream)))
+    err = ws[:4].view(torch.int32)
+    return Q, piv, err
+
+
+def rr_gram(X, Y, G=None, accumulate=False, stream=None):
+    n, p = X.shape
+    q = Y.shape[1]
+    if G is None:
+        G = fortran(torch.zeros(p, q, dtype=torch.float64, device=X.device))
+    L = lib()
+    ws = _ws(L.rr_gram_workspace_size(n, p, q), X.device)
+    check("rr_gram", L.rr_gram(n, p, q, DTYPES[X.dtype], _p(X), ld_of(X), DTYPES[Y.dtype], _p(Y), ld_of(Y),
+                               _p(G), ld_of(G), int(accumulate), _p(ws), ws.numel(), _stream(stream)))
+    return G
+
+
+def rr_pencil_eig(H, G, stream=None):
+    b = H.shape[0]
+    theta = torch.empty(b, dtype=torch.float64, device=H.device)
+    Y = fortran(torch.empty(b, b, dtype=torch.float64, device=H.device))
+    L = lib()
+    ws = _ws(L.rr_pencil_workspace_size(b, b), H.device)
+    dropped = ctypes.c_int32(0)
+    check("rr_pencil_eig", L.rr_pencil_eig(b, _p(H), _p(G), _p(theta), _p(Y), _p(ws), ws.numel(),
+                                           ctypes.byref(dropped), _stream(stream)))
+    return theta, Y, dropped.value
+
+
+def rr_pencil_svd(B, Gu, Gv, stream=None):
+    b1, b2 = B.shape
+    r = min(b1, b2)
+    s = torch.empty(r, dtype=torch.float64, device=B.device)
+    Y = fortran(torch.empty(b1, r, dtype=torch.float64, device=B.device))
+    Z = fortran(torch.empty(b2, r, dtype=torch.float64, device=B.device))
+    L = lib()
+    ws = _ws(L.rr_pencil_workspace_size(b1, b2), B.device)
+    dropped = ctypes.c_int32(0)
+    check("rr_pencil_svd", L.rr_pencil_svd(b1, b2, _p(B), _p(Gu), _p(Gv), _p(s), _p(Y), _p(Z), _p(ws),
+                                           ws.numel(), ctypes.byref(dropped), _stream(stream)))
+    return s, Y, Z, dropped.value
+
+
+def rr_csr_spmm(row_ptr, col_idx, values, X, out_dtype=torch.float32, stream=None):
+    n, b = X.shape
+    Y = fortran(torch.empty(n, b, dtype=out_dtype, device=X.device))
+    check("rr_csr_spmm", lib().rr_csr_spmm(n, b, _p(row_ptr), _p(col_idx), _p(values), DTYPES[X.dtype],
+                                           _p(X), ld_of(X), DTYPES[out_dtype], _p(Y), ld_of(Y),
+                                           _stream(stream)))
+    return Y
+
+
+def rr_chebyshev_step(row_ptr, col_idx, values, Y_cur, Y_prev, alpha, c, beta, beta_col=None, R=None,
+                      gamma=None, out_dtype=None, stream=None):
+    n, b = Y_cur.shape
+    out_dtype = out_dtype or Y_cur.dtype
+    Yn = fortran(torch.empty(n, b, dtype=out_dtype, device=Y_cur.device))
+    check("rr_chebyshev_step", lib().rr_chebyshev_step(
+        n, b, _p(row_ptr), _p(col_idx), _p(values), DTYPES[Y_cur.dtype], _p(Y_cur), _p(Y_prev),
+        ld_of(Y_cur), alpha, c, beta, _p(beta_col), _p(R), ld_of(R) if R is not None else 0, _p(gamma),
+        DTYPES[out_dtype], _p(Yn), ld_of(Yn), _stream(stream)))
+    return Yn

@@ -1,0 +1,429 @@
+// Dense stages: start-block scaling and casts (Sec. 2 column scaling; Sec. 5.2
+// U(0,1) start cast to the working precision), the low-precision block
+// product (Sec. 2, X_iter = A X; Fig. 4 "W = AV"), FP64 products and the
+// projection Gram products (Alg. 3 / Alg. 5).
+#include <cstdio>
+#include <cstring>
+
+#include "rr_common.cuh"
+
+namespace rr {
+
+static thread_local char g_last_error[512] = "";
+
+void set_last_error(const char* what, cudaError_t e) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s: %s", what, cudaGetErrorString(e));
+}
+
+rr_status check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_last_error(what, e);
+    return RR_ERR_CUDA;
+  }
+  return RR_OK;
+}
+
+int num_sms() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+// ---------------------------------------------------------------------------
+// a1: column inf-norm scaling + cast
+// ---------------------------------------------------------------------------
+__global__ void k_colmax_f64(int64_t rows, const double* __restrict__ X, int64_t ldx,
+                             double* __restrict__ out) {
+  int64_t j = blockIdx.x;
+  const double* x = X + j * ldx;
+  double m = 0.0;
+  for (int64_t i = threadIdx.x; i < rows; i += blockDim.x) m = fmax(m, fabs(x[i]));
+  __shared__ double sm[32];
+  m = warp_max(m);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = (threadIdx.x < (blockDim.x >> 5)) ? sm[threadIdx.x] : 0.0;
+    m = warp_max(m);
+    if (threadIdx.x == 0) out[j] = m;
+  }
+}
+
+template <typename TO>
+__global__ void k_scale_cast(int64_t rows, int64_t cols, const double* __restrict__ X, int64_t ldx,
+                             const double* __restrict__ mx, TO* __restrict__ Y, int64_t ldy) {
+  int64_t j = blockIdx.y;
+  double m = mx[j];
+  if (!(m > 0.0)) m = 1.0;  // zero column stays zero
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows;
+       i += (int64_t)gridDim.x * blockDim.x)
+    Y[i + j * ldy] = from_f64<TO>(X[i + j * ldx] / m);
+}
+
+}  // namespace rr
+
+using namespace rr;
+
+extern "C" const char* rr_last_error(void) { return g_last_error; }
+
+extern "C" rr_status rr_colscale_cast(int64_t rows, int64_t cols, const double* X, int64_t ldx,
+                                      int32_t dtype, void* Y, int64_t ldy, double* scale,
+                                      void* stream) {
+  if (rows < 0 || cols < 0 || ldx < rows || ldy < rows || !X || !Y) return RR_ERR_ARG;
+  if (!scale) return RR_ERR_ARG;  // caller provides the cols-long scale buffer
+  if (rows == 0 || cols == 0) return RR_OK;
+  cudaStream_t s = as_stream(stream);
+  k_colmax_f64<<<(unsigned)cols, 256, 0, s>>>(rows, X, ldx, scale);
+  dim3 g((unsigned)std::min<int64_t>((rows + 255) / 256, 1024), (unsigned)cols);
+  switch (dtype) {
+    case RR_F64: k_scale_cast<double><<<g, 256, 0, s>>>(rows, cols, X, ldx, scale, (double*)Y, ldy); break;
+    case RR_F32: k_scale_cast<float><<<g, 256, 0, s>>>(rows, cols, X, ldx, scale, (float*)Y, ldy); break;
+    case RR_BF16: k_scale_cast<__nv_bfloat16><<<g, 256, 0, s>>>(rows, cols, X, ldx, scale, (__nv_bfloat16*)Y, ldy); break;
+    default: return RR_ERR_ARG;
+  }
+  return check_launch("rr_colscale_cast");
+}
+
+// ---------------------------------------------------------------------------
+// operator cast: FP64 column-major -> dtype column-major (+ row-major copy)
+// 32x32 tiles through shared memory so both the read and the transposed
+// write are coalesced.
+// ---------------------------------------------------------------------------
+namespace rr {
+template <typename TO>
+__global__ void k_cast_operator(int64_t m, int64_t n, const double* __restrict__ A, int64_t lda,
+                                TO* __restrict__ out_col, TO* __restrict__ out_row) {
+  __shared__ TO tile[32][33];
+  int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
+  int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int r = ty; r < 32; r += 8) {
+    int64_t i = i0 + tx, j = j0 + r;
+    if (i < m && j < n) {
+      TO v = from_f64<TO>(A[i + j * lda]);
+      out_col[i + j * m] = v;
+      tile[r][tx] = v;
+    }
+  }
+  if (!out_row) return;
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    int64_t i = i0 + r, j = j0 + tx;
+    if (i < m && j < n) out_row[i * n + j] = tile[tx][r];
+  }
+}
+}  // namespace rr
+
+extern "C" rr_status rr_cast_operator(int64_t m, int64_t n, const double* A, int64_t lda,
+                                      int32_t dtype, void* out_col, void* out_row, void* stream) {
+  if (m < 0 || n < 0 || lda < m || !A || !out_col) return RR_ERR_ARG;
+  if (m == 0 || n == 0) return RR_OK;
+  dim3 g((unsigned)((m + 31) / 32), (unsigned)((n + 31) / 32)), b(32, 8);
+  cudaStream_t s = as_stream(stream);
+  switch (dtype) {
+    case RR_F32: k_cast_operator<float><<<g, b, 0, s>>>(m, n, A, lda, (float*)out_col, (float*)out_row); break;
+    case RR_BF16: k_cast_operator<__nv_bfloat16><<<g, b, 0, s>>>(m, n, A, lda, (__nv_bfloat16*)out_col, (__nv_bfloat16*)out_row); break;
+    case RR_F64: k_cast_operator<double><<<g, b, 0, s>>>(m, n, A, lda, (double*)out_col, (double*)out_row); break;
+    default: return RR_ERR_ARG;
+  }
+  return check_launch("rr_cast_operator");
+}
+
+// ---------------------------------------------------------------------------
+// SIMT block product with FP32 accumulation (portable baseline kernel; the
+// tcgen05 path in k_gemm_tc.cu takes BF16 shapes it supports)
+// C(M x N) = A_k^T B (+ coef_j R(:,j)),  A_k: K x M K-contiguous, B: K x N.
+// ---------------------------------------------------------------------------
+namespace rr {
+constexpr int GBM = 64, GBN = 64, GBK = 32;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm_lowp_simt(
+    int64_t M, int64_t N, int64_t K, const T* __restrict__ A, int64_t lda,
+    const T* __restrict__ B, int64_t ldb, float* __restrict__ C, int64_t ldc,
+    const double* __restrict__ R, int64_t ldr, const double* __restrict__ coef) {
+  __shared__ float As[GBK][GBM + 1];
+  __shared__ float Bs[GBK][GBN + 1];
+  int64_t m0 = (int64_t)blockIdx.x * GBM, n0 = (int64_t)blockIdx.y * GBN;
+  int tid = threadIdx.x;
+  int tm = tid % 16, tn = tid / 16;  // 16 x 16 threads, 4 x 4 outputs each
+  float acc[4][4] = {};
+  for (int64_t k0 = 0; k0 < K; k0 += GBK) {
+    for (int e = tid; e < GBK * GBM; e += 256) {
+      int kk = e % GBK, i = e / GBK;
+      int64_t gk = k0 + kk, gi = m0 + i;
+      As[kk][i] = (gk < K && gi < M) ? Ld<T>::f32(A + gk + gi * lda) : 0.f;
+    }
+    for (int e = tid; e < GBK * GBN; e += 256) {
+      int kk = e % GBK, j = e / GBK;
+      int64_t gk = k0 + kk, gj = n0 + j;
+      Bs[kk][j] = (gk < K && gj < N) ? Ld<T>::f32(B + gk + gj * ldb) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < GBK; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = As[kk][tm + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tn + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    int64_t j = n0 + tn + 16 * c;
+    if (j >= N) continue;
+    float cf = (R && coef) ? (float)coef[j] : 0.f;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int64_t i = m0 + tm + 16 * r;
+      if (i >= M) continue;
+      float v = acc[r][c];
+      if (R && coef) v += (float)((double)cf * R[i + j * ldr]);
+      C[i + j * ldc] = v;
+    }
+  }
+}
+}  // namespace rr
+
+// tcgen05 path (k_gemm_tc.cu); returns RR_ERR_ARG when the shape is unsupported
+namespace rr {
+rr_status gemm_bf16_tc(int64_t M, int64_t N, int64_t K, const __nv_bfloat16* A, int64_t lda,
+                       const __nv_bfloat16* B, int64_t ldb, float* C, int64_t ldc,
+                       const double* R, int64_t ldr, const double* coef, cudaStream_t s);
+bool gemm_bf16_tc_supported(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb,
+                            const void* A, const void* B);
+int& gemm_force_simt();
+}  // namespace rr
+
+extern "C" rr_status rr_gemm_lowp(int32_t dtype, int64_t M, int64_t N, int64_t K, const void* A_k,
+                                  int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc,
+                                  const double* R, int64_t ldr, const double* coef, void* stream) {
+  if (M < 0 || N < 0 || K < 0 || lda < K || ldb < K || ldc < M || !C) return RR_ERR_ARG;
+  if (M == 0 || N == 0) return RR_OK;
+  if ((R != nullptr) != (coef != nullptr)) return RR_ERR_ARG;
+  if (R && ldr < M) return RR_ERR_ARG;
+  cudaStream_t s = as_stream(stream);
+  if (dtype == RR_BF16 && !gemm_force_simt() &&
+      gemm_bf16_tc_supported(M, N, K, lda, ldb, A_k, B))
+    return gemm_bf16_tc(M, N, K, (const __nv_bfloat16*)A_k, lda, (const __nv_bfloat16*)B, ldb,
+                        C, ldc, R, ldr, coef, s);
+  dim3 g((unsigned)((M + GBM - 1) / GBM), (unsigned)((N + GBN - 1) / GBN));
+  switch (dtype) {
+    case RR_BF16:
+      k_gemm_lowp_simt<__nv_bfloat16><<<g, 256, 0, s>>>(M, N, K, (const __nv_bfloat16*)A_k, lda,
+                                                         (const __nv_bfloat16*)B, ldb, C, ldc, R, ldr, coef);
+      break;
+    case RR_F32:
+      k_gemm_lowp_simt<float><<<g, 256, 0, s>>>(M, N, K, (const float*)A_k, lda, (const float*)B,
+                                                ldb, C, ldc, R, ldr, coef);
+      break;
+    default: return RR_ERR_ARG;
+  }
+  return check_launch("rr_gemm_lowp");
+}
+
+// ---------------------------------------------------------------------------
+// FP64 products C = op(A) B (+C): SIMT, 64 x 64 tiles, 4 x 4 per thread.
+// FP64 issue rate, not memory, bounds this on GB300.
+// ---------------------------------------------------------------------------
+namespace rr {
+constexpr int DBM = 64, DBN = 64, DBK = 16;
+__global__ void __launch_bounds__(256) k_gemm_f64(
+    int trans, int64_t M, int64_t N, int64_t K, const double* __restrict__ A, int64_t lda,
+    const double* __restrict__ B, int64_t ldb, double* __restrict__ C, int64_t ldc, int accum) {
+  __shared__ double As[DBK][DBM + 1];
+  __shared__ double Bs[DBK][DBN + 1];
+  int64_t m0 = (int64_t)blockIdx.x * DBM, n0 = (int64_t)blockIdx.y * DBN;
+  int tid = threadIdx.x;
+  int tm = tid % 16, tn = tid / 16;
+  double acc[4][4] = {};
+  for (int64_t k0 = 0; k0 < K; k0 += DBK) {
+    if (trans) {
+      for (int e = tid; e < DBK * DBM; e += 256) {
+        int kk = e % DBK, i = e / DBK;
+        int64_t gk = k0 + kk, gi = m0 + i;
+        As[kk][i] = (gk < K && gi < M) ? A[gk + gi * lda] : 0.0;
+      }
+    } else {
+      for (int e = tid; e < DBK * DBM; e += 256) {
+        int i = e % DBM, kk = e / DBM;
+        int64_t gk = k0 + kk, gi = m0 + i;
+        As[kk][i] = (gk < K && gi < M) ? A[gi + gk * lda] : 0.0;
+      }
+    }
+    for (int e = tid; e < DBK * DBN; e += 256) {
+      int kk = e % DBK, j = e / DBK;
+      int64_t gk = k0 + kk, gj = n0 + j;
+      Bs[kk][j] = (gk < K && gj < N) ? B[gk + gj * ldb] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < DBK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = As[kk][tm + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tn + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    int64_t j = n0 + tn + 16 * c;
+    if (j >= N) continue;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int64_t i = m0 + tm + 16 * r;
+      if (i >= M) continue;
+      double v = acc[r][c];
+      if (accum) v += C[i + j * ldc];
+      C[i + j * ldc] = v;
+    }
+  }
+}
+}  // namespace rr
+
+extern "C" rr_status rr_gemm_f64(int32_t trans, int64_t M, int64_t N, int64_t K, const double* A,
+                                 int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc,
+                                 int32_t accumulate, void* stream) {
+  if (M < 0 || N < 0 || K < 0 || ldb < K || ldc < M || !C) return RR_ERR_ARG;
+  if (trans ? lda < K : lda < M) return RR_ERR_ARG;
+  if (M == 0 || N == 0) return RR_OK;
+  dim3 g((unsigned)((M + DBM - 1) / DBM), (unsigned)((N + DBN - 1) / DBN));
+  k_gemm_f64<<<g, 256, 0, as_stream(stream)>>>(trans, M, N, K, A, lda, B, ldb, C, ldc, accumulate);
+  return check_launch("rr_gemm_f64");
+}
+
+// ---------------------------------------------------------------------------
+// Gram products G = X^T Y for tall X (n x p), Y (n x q), FP64 accumulation,
+// split over rows into chunks with deterministic second-pass reduction.
+// ---------------------------------------------------------------------------
+namespace rr {
+constexpr int GT = 32;      // output tile GT x GT
+constexpr int GROWS = 32;   // rows per smem stage
+
+template <typename TX, typename TY>
+__global__ void __launch_bounds__(256) k_gram_partial(
+    int64_t n, int64_t p, int64_t q, const TX* __restrict__ X, int64_t ldx,
+    const TY* __restrict__ Y, int64_t ldy, int64_t rows_per_chunk, double* __restrict__ part) {
+  __shared__ double Xs[GROWS][GT + 1];
+  __shared__ double Ys[GROWS][GT + 1];
+  int64_t p0 = (int64_t)blockIdx.x * GT, q0 = (int64_t)blockIdx.y * GT;
+  int64_t r0 = (int64_t)blockIdx.z * rows_per_chunk;
+  int64_t r1 = r0 + rows_per_chunk < n ? r0 + rows_per_chunk : n;
+  int tid = threadIdx.x;
+  int ti = tid % 16, tj = tid / 16;  // 2 x 2 outputs per thread
+  double acc[2][2] = {};
+  for (int64_t rs = r0; rs < r1; rs += GROWS) {
+    for (int e = tid; e < GROWS * GT; e += 256) {
+      int rr_ = e % GROWS, c = e / GROWS;
+      int64_t row = rs + rr_;
+      Xs[rr_][c] = (row < r1 && p0 + c < p) ? Ld<TX>::f64(X + row + (p0 + c) * ldx) : 0.0;
+      Ys[rr_][c] = (row < r1 && q0 + c < q) ? Ld<TY>::f64(Y + row + (q0 + c) * ldy) : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int rr_ = 0; rr_ < GROWS; ++rr_) {
+      double x0 = Xs[rr_][ti], x1 = Xs[rr_][ti + 16];
+      double y0 = Ys[rr_][tj], y1 = Ys[rr_][tj + 16];
+      acc[0][0] = fma(x0, y0, acc[0][0]);
+      acc[0][1] = fma(x0, y1, acc[0][1]);
+      acc[1][0] = fma(x1, y0, acc[1][0]);
+      acc[1][1] = fma(x1, y1, acc[1][1]);
+    }
+    __syncthreads();
+  }
+  double* out = part + (size_t)blockIdx.z * p * q;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      int64_t i = p0 + ti + 16 * a, j = q0 + tj + 16 * b;
+      if (i < p && j < q) out[i + j * p] = acc[a][b];
+    }
+}
+
+__global__ void k_gram_reduce(int64_t p, int64_t q, int64_t chunks, const double* __restrict__ part,
+                              double* __restrict__ G, int64_t ldg, int accum) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= p * q) return;
+  double s = 0.0;
+  for (int64_t c = 0; c < chunks; ++c) s += part[c * p * q + e];
+  int64_t i = e % p, j = e / p;
+  if (accum) s += G[i + j * ldg];
+  G[i + j * ldg] = s;
+}
+
+static int64_t gram_chunks(int64_t n, int64_t p, int64_t q) {
+  int64_t tiles = ((p + GT - 1) / GT) * ((q + GT - 1) / GT);
+  int64_t want = (4 * (int64_t)num_sms() + tiles - 1) / tiles;
+  int64_t maxc = (n + 255) / 256;
+  int64_t c = want < maxc ? want : maxc;
+  return c < 1 ? 1 : c;
+}
+}  // namespace rr
+
+extern "C" size_t rr_gram_workspace_size(int64_t n, int64_t p, int64_t q) {
+  return align_up((size_t)gram_chunks(n, p, q) * p * q * sizeof(double)) + 256;
+}
+
+namespace rr {
+template <typename TX>
+static rr_status gram_dispatch_y(int32_t ytype, dim3 g, cudaStream_t s, int64_t n, int64_t p,
+                                 int64_t q, const TX* X, int64_t ldx, const void* Y, int64_t ldy,
+                                 int64_t rpc, double* part) {
+  switch (ytype) {
+    case RR_F64: k_gram_partial<TX, double><<<g, 256, 0, s>>>(n, p, q, X, ldx, (const double*)Y, ldy, rpc, part); break;
+    case RR_F32: k_gram_partial<TX, float><<<g, 256, 0, s>>>(n, p, q, X, ldx, (const float*)Y, ldy, rpc, part); break;
+    case RR_BF16: k_gram_partial<TX, __nv_bfloat16><<<g, 256, 0, s>>>(n, p, q, X, ldx, (const __nv_bfloat16*)Y, ldy, rpc, part); break;
+    default: return RR_ERR_ARG;
+  }
+  return RR_OK;
+}
+}  // namespace rr
+
+extern "C" rr_status rr_gram(int64_t n, int64_t p, int64_t q, int32_t xtype, const void* X,
+                             int64_t ldx, int32_t ytype, const void* Y, int64_t ldy, double* G,
+                             int64_t ldg, int32_t accumulate, void* ws, size_t ws_bytes,
+                             void* stream) {
+  if (n < 0 || p < 0 || q < 0 || ldx < n || ldy < n || ldg < p || !G) return RR_ERR_ARG;
+  if (p == 0 || q == 0) return RR_OK;
+  cudaStream_t s = as_stream(stream);
+  if (n == 0) {
+    if (!accumulate)
+      for (int64_t j = 0; j < q; ++j) RR_CUDA(cudaMemsetAsync(G + j * ldg, 0, p * sizeof(double), s));
+    return RR_OK;
+  }
+  int64_t chunks = gram_chunks(n, p, q);
+  if (ws_bytes < (size_t)chunks * p * q * sizeof(double) || !ws) return RR_ERR_WORKSPACE;
+  int64_t rpc = (n + chunks - 1) / chunks;
+  chunks = (n + rpc - 1) / rpc;
+  double* part = (double*)ws;
+  dim3 g((unsigned)((p + GT - 1) / GT), (unsigned)((q + GT - 1) / GT), (unsigned)chunks);
+  rr_status st;
+  switch (xtype) {
+    case RR_F64: st = gram_dispatch_y<double>(ytype, g, s, n, p, q, (const double*)X, ldx, Y, ldy, rpc, part); break;
+    case RR_F32: st = gram_dispatch_y<float>(ytype, g, s, n, p, q, (const float*)X, ldx, Y, ldy, rpc, part); break;
+    case RR_BF16: st = gram_dispatch_y<__nv_bfloat16>(ytype, g, s, n, p, q, (const __nv_bfloat16*)X, ldx, Y, ldy, rpc, part); break;
+    default: return RR_ERR_ARG;
+  }
+  if (st != RR_OK) return st;
+  RR_TRY(check_launch("rr_gram partial"));
+  k_gram_reduce<<<(unsigned)((p * q + 255) / 256), 256, 0, s>>>(p, q, chunks, part, G, ldg, accumulate);
+  return check_launch("rr_gram reduce");
+}

@@ -1,0 +1,302 @@
+// Algorithm 8: the right-looking Hessenberg process for a block (Sec. 4.2.2),
+// the paper's inner-product-free basis step.  Its output equals P^T L of
+// row-pivoted LU.
+//
+// GB300 design: one cooperative launch over all SMs.  Each CTA owns a
+// contiguous slab of rows.  Per column j:
+//   (a) every CTA finds the largest |W(r, j)| in its slab (first index on
+//       ties) and publishes (value, row) plus that row's trailing entries;
+//   (b) one grid barrier (bounded wait);
+//   (c) every CTA reduces the published candidates itself (no second
+//       barrier) and gets the pivot r, W(r, j) and the weights W(r, j+1:k);
+//   (d) every CTA scales its part of column j by 1/W(r, j) and applies the
+//       rank-1 update to its rows of the trailing columns.
+// The candidate buffers are double-buffered by column parity so no CTA can
+// overwrite a buffer another CTA still reads.  Arithmetic: IEEE divide,
+// multiply and subtract, each rounded separately (no FMA contraction), so the
+// result is bit-reproducible and equals a plain FP32/FP64 loop.
+#include <climits>
+
+#include "rr_common.cuh"
+
+namespace rr {
+
+template <typename T>
+struct HessWs {
+  int* err;
+  GridBarrier* bar;
+  T* pval;      // [2][G] signed candidate pivot value
+  int* pidx;    // [2][G] candidate row
+  T* prow;      // [2][G][k] candidate row's entries
+  T* pcolmax;   // [G][k] per-slab column inf-norms
+};
+
+template <typename T> __device__ __forceinline__ T ld_cg(const T* p);
+template <> __device__ __forceinline__ float ld_cg<float>(const float* p) { return __ldcg(p); }
+template <> __device__ __forceinline__ double ld_cg<double>(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ int ld_cg_i(const int* p) { return __ldcg(p); }
+
+template <typename T> __device__ __forceinline__ T rn_div(T a, T b);
+template <> __device__ __forceinline__ float rn_div<float>(float a, float b) { return __fdiv_rn(a, b); }
+template <> __device__ __forceinline__ double rn_div<double>(double a, double b) { return __ddiv_rn(a, b); }
+template <typename T> __device__ __forceinline__ T rn_mul(T a, T b);
+template <> __device__ __forceinline__ float rn_mul<float>(float a, float b) { return __fmul_rn(a, b); }
+template <> __device__ __forceinline__ double rn_mul<double>(double a, double b) { return __dmul_rn(a, b); }
+template <typename T> __device__ __forceinline__ T rn_sub(T a, T b);
+template <> __device__ __forceinline__ float rn_sub<float>(float a, float b) { return __fsub_rn(a, b); }
+template <> __device__ __forceinline__ double rn_sub<double>(double a, double b) { return __dsub_rn(a, b); }
+
+// (|v|, idx) with "larger |v| wins, then smaller idx"
+template <typename T>
+__device__ __forceinline__ void argmax_merge(T& av, int& ai, T bv, int bi) {
+  if (bv > av || (bv == av && bi < ai)) {
+    av = bv;
+    ai = bi;
+  }
+}
+
+constexpr int kHessThreads = 512;
+
+template <typename T, typename TO>
+__global__ void __launch_bounds__(kHessThreads) k_hessenberg(
+    int64_t n, int k, T* __restrict__ W, int64_t ldw, TO* __restrict__ Q, int64_t ldq,
+    int* __restrict__ piv, T tol, HessWs<T> ws) {
+  const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = kHessThreads / 32;
+  const int64_t rpc = (n + G - 1) / G;
+  const int64_t r0 = (int64_t)g * rpc;
+  const int64_t r1 = r0 + rpc < n ? r0 + rpc : n;
+  const int64_t nr = r1 > r0 ? r1 - r0 : 0;
+
+  extern __shared__ unsigned char smem_raw[];
+  T* thr = reinterpret_cast<T*>(smem_raw);   // [k]
+  T* wgt = thr + k;                          // [k]
+  __shared__ T red_v[32];
+  __shared__ int red_i[32];
+  __shared__ T s_qr;
+  __shared__ int s_r, s_win, s_keep;
+
+  // ---- column inf-norms on entry (relative skip threshold) ----
+  for (int c = warp; c < k; c += nwarps) {
+    T m = T(0);
+    for (int64_t r = r0 + lane; r < r1; r += 32) m = fmax(m, fabs(W[r + c * ldw]));
+    m = warp_max(m);
+    if (lane == 0) ws.pcolmax[(size_t)g * k + c] = m;
+  }
+  if (!grid_barrier(ws.bar, G, ws.err)) return;
+  for (int c = tid; c < k; c += kHessThreads) {
+    T m = T(0);
+    for (int h = 0; h < G; ++h) m = fmax(m, ld_cg(ws.pcolmax + (size_t)h * k + c));
+    thr[c] = rn_mul(tol, m);
+  }
+  __syncthreads();
+
+  for (int j = 0; j < k; ++j) {
+    const int par = j & 1;
+    // (a) local argmax of |W(r, j)|
+    T bv = T(-1);
+    int bi = INT_MAX;
+    for (int64_t r = r0 + tid; r < r1; r += kHessThreads) {
+      T v = fabs(W[r + j * ldw]);
+      if (v > bv) {  // strictly greater: first index wins within a thread
+        bv = v;
+        bi = (int)r;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      argmax_merge(bv, bi, ov, oi);
+    }
+    if (lane == 0) {
+      red_v[warp] = bv;
+      red_i[warp] = bi;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      bv = lane < nwarps ? red_v[lane] : T(-1);
+      bi = lane < nwarps ? red_i[lane] : INT_MAX;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        argmax_merge(bv, bi, ov, oi);
+      }
+      if (lane == 0) {
+        s_r = bi;
+        ws.pidx[par * G + g] = bi;
+        ws.pval[par * G + g] = (bi != INT_MAX) ? W[bi + j * ldw] : T(0);
+      }
+    }
+    __syncthreads();
+    {
+      const int rloc = s_r;
+      T* prow = ws.prow + ((size_t)par * G + g) * k;
+      for (int c = j + 1 + tid; c < k; c += kHessThreads)
+        prow[c] = (rloc != INT_MAX) ? W[rloc + c * ldw] : T(0);
+    }
+    // (b)
+    if (!grid_barrier(ws.bar, G, ws.err)) return;
+    // (c) global winner, computed redundantly by every CTA
+    if (warp == 0) {
+      T av = T(-1);
+      int ai = INT_MAX, ag = -1;
+      for (int h = lane; h < G; h += 32) {
+        int hi = ld_cg_i(ws.pidx + par * G + h);
+        T hv = fabs(ld_cg(ws.pval + par * G + h));
+        if (hi == INT_MAX) continue;
+        if (hv > av || (hv == av && hi < ai)) {
+          av = hv;
+          ai = hi;
+          ag = h;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        T ov = __shfl_xor_sync(0xffffffffu, av, o);
+        int oi = __shfl_xor_sync(0xffffffffu, ai, o);
+        int og = __shfl_xor_sync(0xffffffffu, ag, o);
+        if (ov > av || (ov == av && oi < ai)) {
+          av = ov;
+          ai = oi;
+          ag = og;
+        }
+      }
+      if (lane == 0) {
+        T qr = (ag >= 0) ? ld_cg(ws.pval + par * G + ag) : T(0);
+        s_qr = qr;
+        s_r = ai;
+        s_win = ag;
+        s_keep = (ag >= 0 && qr != T(0) && fabs(qr) >= thr[j]) ? 1 : 0;
+        if (g == 0) piv[j] = s_keep ? ai : -1;
+      }
+    }
+    __syncthreads();
+    // (d) scale and rank-1 update of this slab
+    if (s_keep) {
+      const T qr = s_qr;
+      const T* prow = ws.prow + ((size_t)par * G + s_win) * k;
+      for (int c = j + 1 + tid; c < k; c += kHessThreads) wgt[c] = ld_cg(prow + c);
+      for (int64_t r = r0 + tid; r < r1; r += kHessThreads)
+        W[r + j * ldw] = rn_div(W[r + j * ldw], qr);
+      __syncthreads();
+      const int64_t ncols = k - j - 1;
+      const int64_t total = ncols * nr;
+      for (int64_t e = tid; e < total; e += kHessThreads) {
+        const int64_t c = j + 1 + e / nr;
+        const int64_t r = r0 + e % nr;
+        W[r + c * ldw] = rn_sub(W[r + c * ldw], rn_mul(wgt[c], W[r + j * ldw]));
+      }
+    } else {
+      for (int64_t r = r0 + tid; r < r1; r += kHessThreads) W[r + j * ldw] = T(0);
+    }
+    __syncthreads();
+  }
+  // write the result in the requested storage type
+  if ((void*)Q != (void*)W) {
+    const int64_t total = (int64_t)k * nr;
+    for (int64_t e = tid; e < total; e += kHessThreads) {
+      const int64_t c = e / nr, r = r0 + e % nr;
+      Q[r + c * ldq] = from_f64<TO>((double)W[r + c * ldw]);
+    }
+  }
+}
+
+static int hess_grid(int64_t n, size_t smem, const void* fn) {
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kHessThreads, smem);
+  if (occ < 1) occ = 1;
+  int64_t maxg = (int64_t)num_sms() * (occ > 1 ? 1 : occ);  // one CTA per SM
+  int64_t want = (n + 63) / 64;  // at least 64 rows per CTA
+  int64_t g = want < maxg ? want : maxg;
+  return (int)(g < 1 ? 1 : g);
+}
+
+template <typename T>
+static size_t hess_ws_bytes(int64_t k, int G) {
+  size_t b = 0;
+  b += align_up(sizeof(int));
+  b += align_up(sizeof(GridBarrier));
+  b += align_up(2 * (size_t)G * sizeof(T));
+  b += align_up(2 * (size_t)G * sizeof(int));
+  b += align_up(2 * (size_t)G * k * sizeof(T));
+  b += align_up((size_t)G * k * sizeof(T));
+  return b;
+}
+
+template <typename T, typename TO>
+static rr_status hess_launch(int64_t n, int64_t k, T* W, int64_t ldw, TO* Q, int64_t ldq, int* piv,
+                             double tol, void* ws, size_t ws_bytes, cudaStream_t s, int max_grid) {
+  size_t smem = 2 * (size_t)k * sizeof(T);
+  const void* fn = (const void*)k_hessenberg<T, TO>;
+  if (smem > 48 * 1024)
+    RR_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int G = max_grid == 1 ? 1 : hess_grid(n, smem, fn);
+  if (ws_bytes < hess_ws_bytes<T>(k, G) || !ws) return RR_ERR_WORKSPACE;
+  Arena ar(ws, ws_bytes);
+  HessWs<T> h;
+  h.err = ar.take<int>(1);
+  h.bar = ar.take<GridBarrier>(1);
+  h.pval = ar.take<T>(2 * (size_t)G);
+  h.pidx = ar.take<int>(2 * (size_t)G);
+  h.prow = ar.take<T>(2 * (size_t)G * k);
+  h.pcolmax = ar.take<T>((size_t)G * k);
+  RR_CUDA(cudaMemsetAsync(ws, 0, 512, s));  // err + barrier
+  T t = tol > 0 ? (T)tol : (T)(4.0 * (double)k * (sizeof(T) == 4 ? 0x1p-23 : 0x1p-52));
+  int kk = (int)k;
+  void* args[] = {&n, &kk, &W, &ldw, &Q, &ldq, &piv, &t, &h};
+  if (G == 1) {
+    // a single CTA never waits on another one: plain launch (graph-capturable,
+    // safe to run concurrently with other work)
+    k_hessenberg<T, TO><<<1, kHessThreads, smem, s>>>(n, kk, W, ldw, Q, ldq, piv, t, h);
+    return check_launch("rr_hessenberg");
+  }
+  RR_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kHessThreads), args, smem, s));
+  return RR_OK;
+}
+
+}  // namespace rr
+
+using namespace rr;
+
+extern "C" size_t rr_hessenberg_workspace_size(int64_t n, int64_t k, int32_t arith) {
+  int G = num_sms();
+  return arith == RR_F64 ? hess_ws_bytes<double>(k, G) : hess_ws_bytes<float>(k, G);
+}
+
+namespace rr {
+rr_status hessenberg_ex(int32_t arith, int64_t n, int64_t k, void* W, int64_t ldw, int32_t qtype,
+                        void* Q, int64_t ldq, int32_t* piv, double tol, void* ws, size_t ws_bytes,
+                        cudaStream_t s, int max_grid);
+}
+extern "C" rr_status rr_hessenberg(int32_t arith, int64_t n, int64_t k, void* W, int64_t ldw,
+                                   int32_t qtype, void* Q, int64_t ldq, int32_t* piv, double tol,
+                                   void* ws, size_t ws_bytes, void* stream) {
+  return hessenberg_ex(arith, n, k, W, ldw, qtype, Q, ldq, piv, tol, ws, ws_bytes,
+                       as_stream(stream), 0);
+}
+
+rr_status rr::hessenberg_ex(int32_t arith, int64_t n, int64_t k, void* W, int64_t ldw,
+                            int32_t qtype, void* Q, int64_t ldq, int32_t* piv, double tol,
+                            void* ws, size_t ws_bytes, cudaStream_t s, int max_grid) {
+  if (n < 0 || k < 0 || k > 4096 || ldw < n || ldq < n || !W || !Q || !piv) return RR_ERR_ARG;
+  if (n > INT_MAX) return RR_ERR_ARG;
+  if (k == 0) return RR_OK;
+  if (arith == RR_F32) {
+    float* w = (float*)W;
+    switch (qtype) {
+      case RR_F32: return hess_launch<float, float>(n, k, w, ldw, (float*)Q, ldq, piv, tol, ws, ws_bytes, s, max_grid);
+      case RR_BF16: return hess_launch<float, __nv_bfloat16>(n, k, w, ldw, (__nv_bfloat16*)Q, ldq, piv, tol, ws, ws_bytes, s, max_grid);
+      case RR_F64: return hess_launch<float, double>(n, k, w, ldw, (double*)Q, ldq, piv, tol, ws, ws_bytes, s, max_grid);
+    }
+  } else if (arith == RR_F64) {
+    double* w = (double*)W;
+    switch (qtype) {
+      case RR_F64: return hess_launch<double, double>(n, k, w, ldw, (double*)Q, ldq, piv, tol, ws, ws_bytes, s, max_grid);
+      case RR_F32: return hess_launch<double, float>(n, k, w, ldw, (float*)Q, ldq, piv, tol, ws, ws_bytes, s, max_grid);
+      case RR_BF16: return hess_launch<double, __nv_bfloat16>(n, k, w, ldw, (__nv_bfloat16*)Q, ldq, piv, tol, ws, ws_bytes, s, max_grid);
+    }
+  }
+  return RR_ERR_ARG;
+}

@@ -1,0 +1,390 @@
+// Solver-side block kernels: Ritz lift (Alg. 3 "U~ = U Y", Alg. 5 lift),
+// residual blocks and norms (Sec. 5.2.2), per-column scaling of correction
+// blocks, selection and output normalisation.
+#include <cfloat>
+
+#include "rr_common.cuh"
+#include "solver_kernels.cuh"
+
+namespace rr {
+
+// X (n x b, TO, ld ldx) = [X +] alpha * S (n x p, TS, ld lds) * Y (p x b FP64, ld ldy)
+constexpr int LBM = 64, LBN = 64, LBK = 16;
+template <typename TS, typename TO = double>
+__global__ void __launch_bounds__(256) k_lift(int64_t n, int64_t b, int64_t p, const TS* __restrict__ S,
+                                             int64_t lds, const double* __restrict__ Y, int64_t ldy,
+                                             TO* __restrict__ X, int64_t ldx, int accum, double alpha = 1.0) {
+  __shared__ double Ss[LBK][LBM + 1];
+  __shared__ double Ys[LBK][LBN + 1];
+  const int64_t m0 = (int64_t)blockIdx.x * LBM, n0 = (int64_t)blockIdx.y * LBN;
+  const int tid = threadIdx.x, tm = tid % 16, tn = tid / 16;
+  double acc[4][4] = {};
+  for (int64_t k0 = 0; k0 < p; k0 += LBK) {
+    for (int e = tid; e < LBK * LBM; e += 256) {
+      int i = e % LBM, kk = e / LBM;
+      int64_t gi = m0 + i, gk = k0 + kk;
+      Ss[kk][i] = (gi < n && gk < p) ? Ld<TS>::f64(S + gi + gk * lds) : 0.0;
+    }
+    for (int e = tid; e < LBK * LBN; e += 256) {
+      int kk = e % LBK, j = e / LBK;
+      int64_t gk = k0 + kk, gj = n0 + j;
+      Ys[kk][j] = (gk < p && gj < b) ? Y[gk + gj * ldy] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < LBK; ++kk) {
+      double a[4], c[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = Ss[kk][tm + 16 * r];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) c[q] = Ys[kk][tn + 16 * q];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[r][q] = fma(a[r], c[q], acc[r][q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    int64_t j = n0 + tn + 16 * q;
+    if (j >= b) continue;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int64_t i = m0 + tm + 16 * r;
+      if (i >= n) continue;
+      double v = alpha * acc[r][q];
+      if (accum) v += (double)X[i + j * ldx];
+      X[i + j * ldx] = (TO)v;
+    }
+  }
+}
+
+// T (n x b, FP32) -= X (n x p, FP64) * K (p x b)
+rr_status sub_lowrank_f32(cudaStream_t s, int64_t n, int64_t b, int64_t p, const double* X, int64_t ldx,
+                          const double* K, int64_t ldk, float* T, int64_t ldt) {
+  if (n == 0 || b == 0 || p == 0) return RR_OK;
+  dim3 g((unsigned)((n + LBM - 1) / LBM), (unsigned)((b + LBN - 1) / LBN));
+  k_lift<double, float><<<g, 256, 0, s>>>(n, b, p, X, ldx, K, ldk, T, ldt, 1, -1.0);
+  return check_launch("sub_lowrank_f32");
+}
+
+rr_status lift(cudaStream_t s, int32_t stype, int64_t n, int64_t b, int64_t p, const void* S,
+               int64_t lds, const double* Y, int64_t ldy, double* X, int64_t ldx, int accum) {
+  if (n == 0 || b == 0) return RR_OK;
+  if (p == 0) {
+    if (!accum)
+      for (int64_t j = 0; j < b; ++j) RR_CUDA(cudaMemsetAsync(X + j * ldx, 0, n * sizeof(double), s));
+    return RR_OK;
+  }
+  dim3 g((unsigned)((n + LBM - 1) / LBM), (unsigned)((b + LBN - 1) / LBN));
+  switch (stype) {
+    case RR_F64: k_lift<double><<<g, 256, 0, s>>>(n, b, p, (const double*)S, lds, Y, ldy, X, ldx, accum); break;
+    case RR_F32: k_lift<float><<<g, 256, 0, s>>>(n, b, p, (const float*)S, lds, Y, ldy, X, ldx, accum); break;
+    case RR_BF16: k_lift<__nv_bfloat16><<<g, 256, 0, s>>>(n, b, p, (const __nv_bfloat16*)S, lds, Y, ldy, X, ldx, accum); break;
+    default: return RR_ERR_ARG;
+  }
+  return check_launch("lift");
+}
+
+// R = P - X diag(theta); ss[j] += sum_i R(i,j)^2 (one block per column)
+__global__ void k_residual_block(int64_t n, const double* __restrict__ P, int64_t ldp,
+                                 const double* __restrict__ X, int64_t ldx,
+                                 const double* __restrict__ theta, double* __restrict__ R,
+                                 int64_t ldr, double* __restrict__ ss, int accum_ss) {
+  const int64_t j = blockIdx.x;
+  const double t = theta[j];
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    double r = P[i + j * ldp] - t * X[i + j * ldx];
+    R[i + j * ldr] = r;
+    acc = fma(r, r, acc);
+  }
+  __shared__ double sm[32];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    acc = (threadIdx.x < (blockDim.x >> 5)) ? sm[threadIdx.x] : 0.0;
+    acc = warp_sum(acc);
+    if (threadIdx.x == 0) ss[j] = (accum_ss ? ss[j] : 0.0) + acc;
+  }
+}
+
+rr_status residual_block(cudaStream_t s, int64_t n, int64_t b, const double* P, int64_t ldp,
+                         const double* X, int64_t ldx, const double* theta, double* R, int64_t ldr,
+                         double* ss, int accum_ss) {
+  if (b == 0) return RR_OK;
+  k_residual_block<<<(unsigned)b, 512, 0, s>>>(n, P, ldp, X, ldx, theta, R, ldr, ss, accum_ss);
+  return check_launch("residual_block");
+}
+
+// res[j] = sqrt(ss[j]) / |theta[j]|
+__global__ void k_res_finish(int64_t b, const double* __restrict__ ss, const double* __restrict__ theta,
+                             double* __restrict__ res) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j < b) {
+    double t = fabs(theta[j]);
+    res[j] = t > 0 ? sqrt(ss[j]) / t : INFINITY;
+  }
+}
+
+rr_status res_finish(cudaStream_t s, int64_t b, const double* ss, const double* theta, double* res) {
+  k_res_finish<<<(unsigned)((b + 127) / 128), 128, 0, s>>>(b, ss, theta, res);
+  return check_launch("res_finish");
+}
+
+// Column inf-norm of a block T (FP32 or FP64), then D = T / mu cast to TO.
+// If coef/sig given: coef[j] *= sig[j] / mu[j] (the correction recurrence's
+// injection coefficient, see solver.cu).  Zero columns: mu = 1.
+template <typename TI>
+__global__ void k_colmax_any(int64_t n, const TI* __restrict__ T, int64_t ldt, double* __restrict__ mu) {
+  const int64_t j = blockIdx.x;
+  double m = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, fabs((double)T[i + j * ldt]));
+  __shared__ double sm[32];
+  m = warp_max(m);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = (threadIdx.x < (blockDim.x >> 5)) ? sm[threadIdx.x] : 0.0;
+    m = warp_max(m);
+    if (threadIdx.x == 0) mu[j] = m > 0.0 ? m : 1.0;
+  }
+}
+
+template <typename TI, typename TO>
+__global__ void k_scale_cast2(int64_t n, int64_t b, const TI* __restrict__ T, int64_t ldt,
+                              const double* __restrict__ mu, TO* __restrict__ D, int64_t ldd) {
+  const int64_t j = blockIdx.y;
+  const double s = 1.0 / mu[j];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    D[i + j * ldd] = from_f64<TO>((double)T[i + j * ldt] * s);
+}
+
+__global__ void k_coef_update(int64_t b, const double* __restrict__ mu, const double* __restrict__ sig,
+                              double* __restrict__ coef) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j < b) coef[j] = coef[j] * sig[j] / mu[j];
+}
+
+template <typename TI>
+static rr_status scale_cast_t(cudaStream_t s, int64_t n, int64_t b, const TI* T, int64_t ldt,
+                              double* mu, int32_t dtype, void* D, int64_t ldd) {
+  k_colmax_any<TI><<<(unsigned)b, 512, 0, s>>>(n, T, ldt, mu);
+  dim3 g((unsigned)std::min<int64_t>((n + 255) / 256, 512), (unsigned)b);
+  switch (dtype) {
+    case RR_F64: k_scale_cast2<TI, double><<<g, 256, 0, s>>>(n, b, T, ldt, mu, (double*)D, ldd); break;
+    case RR_F32: k_scale_cast2<TI, float><<<g, 256, 0, s>>>(n, b, T, ldt, mu, (float*)D, ldd); break;
+    case RR_BF16: k_scale_cast2<TI, __nv_bfloat16><<<g, 256, 0, s>>>(n, b, T, ldt, mu, (__nv_bfloat16*)D, ldd); break;
+    default: return RR_ERR_ARG;
+  }
+  return check_launch("scale_cast");
+}
+
+rr_status scale_cast(cudaStream_t s, int32_t ttype, int64_t n, int64_t b, const void* T, int64_t ldt,
+                     double* mu, int32_t dtype, void* D, int64_t ldd, double* coef,
+                     const double* sig) {
+  if (b == 0) return RR_OK;
+  rr_status st = ttype == RR_F64
+                     ? scale_cast_t<double>(s, n, b, (const double*)T, ldt, mu, dtype, D, ldd)
+                     : scale_cast_t<float>(s, n, b, (const float*)T, ldt, mu, dtype, D, ldd);
+  if (st != RR_OK) return st;
+  if (coef) {
+    k_coef_update<<<(unsigned)((b + 127) / 128), 128, 0, s>>>(b, mu, sig, coef);
+    return check_launch("coef_update");
+  }
+  return RR_OK;
+}
+
+// dst (q x p, ld ldd) = src^T (src p x q, ld lds)
+__global__ void k_transpose(int64_t p, int64_t q, const double* __restrict__ src, int64_t lds,
+                            double* __restrict__ dst, int64_t ldd) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= p * q) return;
+  int64_t i = e % p, j = e / p;
+  dst[j + i * ldd] = src[i + j * lds];
+}
+
+rr_status transpose(cudaStream_t s, int64_t p, int64_t q, const double* src, int64_t lds, double* dst,
+                    int64_t ldd) {
+  if (p * q == 0) return RR_OK;
+  k_transpose<<<(unsigned)((p * q + 255) / 256), 256, 0, s>>>(p, q, src, lds, dst, ldd);
+  return check_launch("transpose");
+}
+
+// Select b eigenpairs from an ascending theta (NaN = dropped, last) in the
+// wanted order: largest -> descending from the top valid; smallest ->
+// ascending from the bottom.  Ysel(:, out) = Y(:, src).
+__global__ void k_select_eig(int64_t nb, int64_t b, int which, const double* __restrict__ theta,
+                             const double* __restrict__ Y, int64_t ldy, double* __restrict__ tsel,
+                             double* __restrict__ Ysel, int64_t ldys, int* __restrict__ nsel) {
+  __shared__ int s_nv;
+  if (threadIdx.x == 0) {
+    int nv = 0;
+    for (int64_t i = 0; i < nb; ++i) nv += !isnan(theta[i]);
+    s_nv = nv;
+    if (nsel) *nsel = nv < b ? nv : (int)b;
+  }
+  __syncthreads();
+  const int64_t nv = s_nv;
+  for (int64_t e = threadIdx.x + blockIdx.x * (int64_t)blockDim.x; e < nb * b;
+       e += (int64_t)blockDim.x * gridDim.x) {
+    int64_t i = e % nb, out = e / nb;
+    double v = 0.0;
+    if (out < nv) {
+      int64_t src = which == RR_LARGEST ? nv - 1 - out : out;
+      v = Y[i + src * ldy];
+    }
+    Ysel[i + out * ldys] = v;
+  }
+  if (blockIdx.x == 0)
+    for (int64_t out = threadIdx.x; out < b; out += blockDim.x) {
+      int64_t src = which == RR_LARGEST ? nv - 1 - out : out;
+      tsel[out] = out < nv ? theta[src] : nan("");
+    }
+}
+
+rr_status select_eig(cudaStream_t s, int64_t nb, int64_t b, int which, const double* theta,
+                     const double* Y, int64_t ldy, double* tsel, double* Ysel, int64_t ldys) {
+  k_select_eig<<<1, 1024, 0, s>>>(nb, b, which, theta, Y, ldy, tsel, Ysel, ldys, nullptr);
+  return check_launch("select_eig");
+}
+
+// Normalise columns to unit 2-norm and fix the sign so the largest-|.| entry
+// (first on ties) of X's column is positive; the same sign flips U's column.
+// One block per column.
+__global__ void k_normalize_sign(int64_t n, double* __restrict__ X, int64_t ldx, int64_t m,
+                                 double* __restrict__ U, int64_t ldu) {
+  const int64_t j = blockIdx.x;
+  double* x = X + j * ldx;
+  double ss = 0.0, bv = -1.0;
+  int64_t bi = INT64_MAX;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    double v = x[i];
+    ss = fma(v, v, ss);
+    if (fabs(v) > bv) {
+      bv = fabs(v);
+      bi = i;
+    }
+  }
+  __shared__ double s_ss[32], s_bv[32];
+  __shared__ int64_t s_bi[32];
+  __shared__ double s_scale;
+  for (int o = 16; o > 0; o >>= 1) {
+    ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+    int64_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ov > bv || (ov == bv && oi < bi)) {
+      bv = ov;
+      bi = oi;
+    }
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s_ss[threadIdx.x >> 5] = ss;
+    s_bv[threadIdx.x >> 5] = bv;
+    s_bi[threadIdx.x >> 5] = bi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0, v = -1.0;
+    int64_t id = INT64_MAX;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      t += s_ss[w];
+      if (s_bv[w] > v || (s_bv[w] == v && s_bi[w] < id)) {
+        v = s_bv[w];
+        id = s_bi[w];
+      }
+    }
+    double nr = sqrt(t);
+    double sg = (id != INT64_MAX && x[id] < 0) ? -1.0 : 1.0;
+    s_scale = nr > 0 ? sg / nr : 1.0;
+  }
+  __syncthreads();
+  const double sc = s_scale;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) x[i] *= sc;
+  if (U) {
+    // U's column: same sign, its own norm
+    double* u = U + j * ldu;
+    double us = 0.0;
+    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) us = fma(u[i], u[i], us);
+    __shared__ double s_us[32];
+    us = warp_sum(us);
+    if ((threadIdx.x & 31) == 0) s_us[threadIdx.x >> 5] = us;
+    __syncthreads();
+    __shared__ double s_uscale;
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_us[w];
+      double nr = sqrt(t);
+      s_uscale = nr > 0 ? (sc > 0 ? 1.0 : -1.0) / nr : 1.0;
+    }
+    __syncthreads();
+    const double us2 = s_uscale;
+    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) u[i] *= us2;
+  }
+}
+
+rr_status normalize_sign(cudaStream_t s, int64_t n, int64_t k, double* X, int64_t ldx, int64_t m,
+                         double* U, int64_t ldu) {
+  if (k == 0) return RR_OK;
+  k_normalize_sign<<<(unsigned)k, 512, 0, s>>>(n, X, ldx, m, U, ldu);
+  return check_launch("normalize_sign");
+}
+
+// d[j] = a[j] * b[j] (or copy if b == NULL)
+__global__ void k_vec_mul(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+                          double* __restrict__ d) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j < n) d[j] = b ? a[j] * b[j] : a[j];
+}
+
+rr_status vec_mul(cudaStream_t s, int64_t n, const double* a, const double* b, double* d) {
+  if (n == 0) return RR_OK;
+  k_vec_mul<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(n, a, b, d);
+  return check_launch("vec_mul");
+}
+
+__global__ void k_fill(int64_t n, double v, double* __restrict__ d) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j < n) d[j] = v;
+}
+
+rr_status fill(cudaStream_t s, int64_t n, double v, double* d) {
+  if (n == 0) return RR_OK;
+  k_fill<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, v, d);
+  return check_launch("fill");
+}
+
+// Counter-based U(0,1) start block: splitmix64 of (seed, index), top 53 bits.
+__global__ void k_uniform(int64_t n, int64_t b, uint64_t seed, double* __restrict__ V, int64_t ldv) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * b;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t z = seed * 0x9E3779B97F4A7C15ull + (uint64_t)e + 1;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    int64_t i = e % n, j = e / n;
+    V[i + j * ldv] = (double)(z >> 11) * 0x1.0p-53;
+  }
+}
+
+rr_status uniform_block(cudaStream_t s, int64_t n, int64_t b, uint64_t seed, double* V, int64_t ldv) {
+  k_uniform<<<256, 256, 0, s>>>(n, b, seed, V, ldv);
+  return check_launch("uniform_block");
+}
+
+}  // namespace rr
+
+namespace rr {
+__global__ void k_vec_scale(int64_t n, double alpha, const double* __restrict__ a, double* __restrict__ d) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j < n) d[j] = alpha * a[j];
+}
+rr_status vec_scale(cudaStream_t s, int64_t n, double alpha, const double* a, double* d) {
+  if (n == 0) return RR_OK;
+  k_vec_scale<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(n, alpha, a, d);
+  return check_launch("vec_scale");
+}
+}  // namespace rr

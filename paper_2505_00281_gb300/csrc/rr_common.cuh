@@ -1,0 +1,178 @@
+// Shared device helpers: status, bounded grid barrier, reductions, casts.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <math.h>
+
+#include "../../include/rr.h"
+
+namespace rr {
+
+// ---------------------------------------------------------------------------
+// host-side status plumbing
+// ---------------------------------------------------------------------------
+void set_last_error(const char* what, cudaError_t e);
+rr_status check_launch(const char* what);
+
+#define RR_TRY(expr)                                   \
+  do {                                                 \
+    rr_status _s = (expr);                             \
+    if (_s != RR_OK) return _s;                        \
+  } while (0)
+
+#define RR_CUDA(expr)                                  \
+  do {                                                 \
+    cudaError_t _e = (expr);                           \
+    if (_e != cudaSuccess) {                           \
+      ::rr::set_last_error(#expr, _e);                 \
+      return RR_ERR_CUDA;                              \
+    }                                                  \
+  } while (0)
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+int num_sms();
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t global_timer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Upper bound on any single device-side wait (2 s): after it the waiting
+// thread records RR_ERR_TIMEOUT in *err and the kernel returns early.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+
+struct GridBarrier {
+  unsigned int count;
+  unsigned int gen;
+};
+
+// Grid-wide barrier for cooperative launches, with a bounded wait.
+// Returns false (and all later calls return false at once) when *err is set.
+__device__ __forceinline__ bool grid_barrier(GridBarrier* gb, unsigned nblocks, int* err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vgen = &gb->gen;
+    volatile int* verr = err;
+    if (*verr == 0) {
+      unsigned int g = *vgen;
+      __threadfence();
+      unsigned int prev = atomicAdd(&gb->count, 1u);
+      if (prev == nblocks - 1) {
+        atomicExch(&gb->count, 0u);
+        __threadfence();
+        atomicAdd(&gb->gen, 1u);
+      } else {
+        uint64_t t0 = global_timer_ns();
+        while (*vgen == g) {
+          if (*verr != 0) break;
+          if (global_timer_ns() - t0 > kWaitLimitNs) {
+            atomicCAS(err, 0, (int)RR_ERR_TIMEOUT);
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+      __threadfence();
+    }
+  }
+  __syncthreads();
+  return *(volatile int*)err == 0;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// load/store with conversion for the basis storage types
+template <typename T> struct Ld;
+template <> struct Ld<double> {
+  static __device__ __forceinline__ double f64(const double* p) { return *p; }
+  static __device__ __forceinline__ float f32(const double* p) { return (float)*p; }
+};
+template <> struct Ld<float> {
+  static __device__ __forceinline__ double f64(const float* p) { return (double)*p; }
+  static __device__ __forceinline__ float f32(const float* p) { return *p; }
+};
+template <> struct Ld<__nv_bfloat16> {
+  static __device__ __forceinline__ double f64(const __nv_bfloat16* p) {
+    return (double)__bfloat162float(*p);
+  }
+  static __device__ __forceinline__ float f32(const __nv_bfloat16* p) {
+    return __bfloat162float(*p);
+  }
+};
+
+template <typename T> __device__ __forceinline__ T from_f64(double v);
+template <> __device__ __forceinline__ double from_f64<double>(double v) { return v; }
+template <> __device__ __forceinline__ float from_f64<float>(double v) { return (float)v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f64<__nv_bfloat16>(double v) {
+  return __float2bfloat16_rn((float)v);
+}
+template <typename T> __device__ __forceinline__ T from_f32(float v);
+template <> __device__ __forceinline__ double from_f32<double>(float v) { return v; }
+template <> __device__ __forceinline__ float from_f32<float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f32<__nv_bfloat16>(float v) {
+  return __float2bfloat16_rn(v);
+}
+
+inline size_t dtype_size(int32_t dt) {
+  switch (dt) {
+    case RR_F64: return 8;
+    case RR_F32: return 4;
+    case RR_BF16: return 2;
+    case RR_E4M3: return 1;
+  }
+  return 0;
+}
+
+inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+// Simple bump allocator over the caller's workspace.
+struct Arena {
+  char* base;
+  size_t cap;
+  size_t off;
+  bool overflow;
+  explicit Arena(void* b, size_t c) : base((char*)b), cap(c), off(0), overflow(false) {}
+  template <typename T>
+  T* take(size_t count) {
+    size_t bytes = align_up(count * sizeof(T));
+    if (off + bytes > cap) {
+      overflow = true;
+      off += bytes;
+      return nullptr;
+    }
+    T* p = (T*)(base + off);
+    off += bytes;
+    return p;
+  }
+  void* take_bytes(size_t bytes) {
+    bytes = align_up(bytes);
+    if (off + bytes > cap) {
+      overflow = true;
+      off += bytes;
+      return nullptr;
+    }
+    void* p = base + off;
+    off += bytes;
+    return p;
+  }
+};
+
+}  // namespace rr

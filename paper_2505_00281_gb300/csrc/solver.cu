@@ -1,0 +1,883 @@
+// Host orchestration of the solvers (rr_eig, rr_svd, rr_batch_svd).
+//
+// Phase 1 is the paper's method: Algorithm 1 (subspace iteration, the RR
+// output restarting the next sweep, Sec. 2) with Algorithm 8 after every
+// product and OFRR (Algorithm 3 / 5) in the precision map of Sec. 4.2:
+// basis and products in the low precision, projection accumulated in FP64,
+// small problem in FP64.
+//
+// Phase 2 (refinement; the paper reaches only the basis precision, so this
+// is an added step) keeps the Ritz vectors X in FP64 and, per sweep:
+//   P = A X   (FP64-accurate), R = P - X Theta, residual check (Sec. 5.2.2);
+//   the correction block D = p(A) X - X p(Theta) built in the low precision
+//   from R by the filter's own recurrence (every low-precision quantity is
+//   O(|R|), so its rounding error is relative to the residual, not to X);
+//   OFRR over S = [X, D] with FP64-accurate blocks where X is involved.
+// The span of [X, D] equals span(X, p(A) X), so a sweep contracts the error
+// by the filter rate, limited below by the low precision's unit roundoff.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "rr_common.cuh"
+#include "solver_kernels.cuh"
+
+namespace rr {
+
+struct Op {
+  int kind;
+  int64_t m, n;
+  const double* A;
+  int64_t lda;
+  const int32_t* rp;
+  const int32_t* ci;
+  const float* va;
+  void* lo_col;  // K-major operand of A^T X (column-major copy), dtype dt
+  void* lo_row;  // K-major operand of A X (row-major copy), dtype dt
+  int32_t dt;    // basis dtype
+  int32_t wt;    // product output type (F32, or F64 when dt is F64)
+};
+
+static size_t dsz(int32_t t) { return dtype_size(t); }
+
+// ---------------------------------------------------------------------------
+// products
+// ---------------------------------------------------------------------------
+// out (m x b, wt) = A X (+ coef_j R(:,j)),  X (n x b, dt)
+static rr_status apply_lowp(const Op& op, int64_t b, const void* X, int64_t ldx, void* out,
+                            int64_t ldo, const double* R, int64_t ldr, const double* coef,
+                            cudaStream_t s) {
+  if (op.kind == RR_DENSE) {
+    if (op.dt == RR_F64) {
+      RR_TRY(rr_gemm_f64(0, op.m, b, op.n, op.A, op.lda, (const double*)X, ldx, (double*)out, ldo, 0, s));
+      if (R) {
+        // out += coef * R  (FP64 path: lift-style axpy via residual kernel is not needed; use lift)
+        return RR_ERR_ARG;
+      }
+      return RR_OK;
+    }
+    return rr_gemm_lowp(op.dt, op.m, b, op.n, op.lo_row, op.n, X, ldx, (float*)out, ldo, R, ldr,
+                        coef, s);
+  }
+  // CSR: Y = A X via the Chebyshev step with alpha = 1, c = 0, beta = 0
+  return rr_chebyshev_step(op.n, b, op.rp, op.ci, op.va, op.dt, X, nullptr, ldx, 1.0, 0.0, 0.0,
+                           nullptr, R, ldr, coef, op.wt, out, ldo, s);
+}
+
+// out (n x b, wt) = A^T X (+ coef_j R(:,j)),  X (m x b, dt)
+static rr_status apply_lowp_T(const Op& op, int64_t b, const void* X, int64_t ldx, void* out,
+                              int64_t ldo, const double* R, int64_t ldr, const double* coef,
+                              cudaStream_t s) {
+  if (op.kind != RR_DENSE) return RR_ERR_ARG;
+  if (op.dt == RR_F64) {
+    if (R) return RR_ERR_ARG;
+    return rr_gemm_f64(1, op.n, b, op.m, op.A, op.lda, (const double*)X, ldx, (double*)out, ldo, 0, s);
+  }
+  return rr_gemm_lowp(op.dt, op.n, b, op.m, op.lo_col, op.m, X, ldx, (float*)out, ldo, R, ldr, coef, s);
+}
+
+// FP64-accurate products with the given operator
+static rr_status apply_f64(const Op& op, int64_t b, const double* X, int64_t ldx, double* out,
+                           int64_t ldo, cudaStream_t s) {
+  if (op.kind == RR_DENSE) return rr_gemm_f64(0, op.m, b, op.n, op.A, op.lda, X, ldx, out, ldo, 0, s);
+  return rr_csr_spmm(op.n, b, op.rp, op.ci, op.va, RR_F64, X, ldx, RR_F64, out, ldo, s);
+}
+static rr_status apply_f64_T(const Op& op, int64_t b, const double* X, int64_t ldx, double* out,
+                             int64_t ldo, cudaStream_t s) {
+  if (op.kind != RR_DENSE) return RR_ERR_ARG;
+  return rr_gemm_f64(1, op.n, b, op.m, op.A, op.lda, X, ldx, out, ldo, 0, s);
+}
+
+// ---------------------------------------------------------------------------
+// workspace
+// ---------------------------------------------------------------------------
+struct Common {
+  void* hess_ws;
+  size_t hess_bytes;
+  void* gram_ws;
+  size_t gram_bytes;
+  void* pen_ws;
+  size_t pen_bytes;
+  int32_t* piv;
+  double* scale;  // b
+  double* hres;   // unused host mirror placeholder
+  int hess_grid;  // 0 = full GPU, 1 = one CTA
+};
+
+static void carve_common(Arena& ar, int64_t rows, int64_t b2, int32_t wt, Common& c) {
+  c.hess_bytes = rr_hessenberg_workspace_size(rows, b2, wt);
+  c.hess_ws = ar.take_bytes(c.hess_bytes);
+  c.gram_bytes = rr_gram_workspace_size(rows, b2, b2);
+  c.gram_ws = ar.take_bytes(c.gram_bytes);
+  c.pen_bytes = rr_pencil_workspace_size(b2, b2);
+  c.pen_ws = ar.take_bytes(c.pen_bytes);
+  c.piv = ar.take<int32_t>(b2);
+  c.scale = ar.take<double>(b2);
+  c.hess_grid = 0;
+}
+
+static rr_status basis_step(const Common& c, bool hess, int32_t wt, int32_t dt, int64_t rows,
+                            int64_t b, void* W, int64_t ldw, void* Q, int64_t ldq, cudaStream_t s) {
+  if (hess)
+    return hessenberg_ex(wt, rows, b, W, ldw, dt, Q, ldq, c.piv, 0.0, c.hess_ws, c.hess_bytes, s,
+                         c.hess_grid);
+  return scale_cast(s, wt, rows, b, W, ldw, c.scale, dt, Q, ldq, nullptr, nullptr);
+}
+
+static rr_status gram(const Common& c, int64_t n, int64_t p, int64_t q, int32_t xt, const void* X,
+                      int64_t ldx, int32_t yt, const void* Y, int64_t ldy, double* G, int64_t ldg,
+                      cudaStream_t s) {
+  return rr_gram(n, p, q, xt, X, ldx, yt, Y, ldy, G, ldg, 0, c.gram_ws, c.gram_bytes, s);
+}
+
+// Remove the span of the orthonormal FP64 Ritz vectors X (n x b) from the FP32
+// block T (n x b): T <- T - X (X^T T).  Keeps the correction blocks of the
+// refinement phase away from the converged directions, which the power /
+// Chebyshev steps would otherwise amplify until [X, D] is numerically
+// dependent.  K is b x b FP64 scratch.
+static rr_status project_out(const Common& c, cudaStream_t s, int64_t n, int64_t b, const double* X,
+                             int64_t ldx, float* T, int64_t ldt, double* K) {
+  RR_TRY(rr_gram(n, b, b, RR_F64, X, ldx, RR_F32, T, ldt, K, b, 0, c.gram_ws, c.gram_bytes, s));
+  return sub_lowrank_f32(s, n, b, b, X, ldx, K, b, T, ldt);
+}
+
+static int count_converged(const double* res, int k, double tol, double* maxres) {
+  int n = 0;
+  double mx = 0.0;
+  for (int i = 0; i < k; ++i) {
+    if (res[i] <= tol) ++n;
+    mx = std::isnan(res[i]) ? INFINITY : fmax(mx, res[i]);
+  }
+  *maxres = mx;
+  return n;
+}
+
+static rr_status read_err(const Common& c, cudaStream_t s) {
+  int e = 0;
+  RR_CUDA(cudaMemcpyAsync(&e, c.hess_ws, sizeof(int), cudaMemcpyDeviceToHost, s));
+  RR_CUDA(cudaStreamSynchronize(s));
+  return e ? (rr_status)e : RR_OK;
+}
+
+static rr_status check_params(const rr_params* p, int64_t rows_min) {
+  if (!p) return RR_ERR_ARG;
+  if (p->k <= 0 || p->block < p->k || p->block > rows_min || p->block > 1024) return RR_ERR_ARG;
+  if (p->degree <= 0 || p->max_sweeps <= 0 || p->max_sweeps > 10000) return RR_ERR_ARG;
+  if (p->basis != RR_F64 && p->basis != RR_F32 && p->basis != RR_BF16) return RR_ERR_ARG;
+  return RR_OK;
+}
+
+// ===========================================================================
+// SVD (Algorithm 5 with Algorithm 1/8 and the refinement phase)
+// ===========================================================================
+struct SvdBufs {
+  Common c;
+  void *Ulo, *Vlo, *W, *Pw, *Elo, *Flo, *AF;
+  double *Gu, *Gv, *Bm, *Ys, *Zs, *sig2;
+  double *Ut, *Vt, *Ut2, *Vt2, *sig, *P, *Qm, *Rv, *Ru, *ss, *res, *mu, *coef;
+};
+
+static void carve_svd(Arena& ar, const Op& op, int64_t b, bool refine, SvdBufs& w) {
+  const int64_t m = op.m, n = op.n, mx = m > n ? m : n, b2 = refine ? 2 * b : b;
+  const size_t ds = dsz(op.dt), ws_ = dsz(op.wt);
+  carve_common(ar, mx, b2, op.wt, w.c);
+  w.Ulo = ar.take_bytes(m * b * ds);
+  w.Vlo = ar.take_bytes(n * b * ds);
+  w.W = ar.take_bytes(mx * b * ws_);
+  w.Pw = ar.take_bytes(m * b * ws_);
+  w.Gu = ar.take<double>(b2 * b2);
+  w.Gv = ar.take<double>(b2 * b2);
+  w.Bm = ar.take<double>(b2 * b2);
+  w.Ys = ar.take<double>(b2 * b2);
+  w.Zs = ar.take<double>(b2 * b2);
+  w.sig2 = ar.take<double>(b2);
+  w.Ut = ar.take<double>(m * b);
+  w.Vt = ar.take<double>(n * b);
+  w.sig = ar.take<double>(b);
+  w.P = ar.take<double>(m * b);
+  w.Qm = ar.take<double>(n * b);
+  w.ss = ar.take<double>(b);
+  w.res = ar.take<double>(b);
+  if (refine) {
+    w.Ut2 = ar.take<double>(m * b);
+    w.Vt2 = ar.take<double>(n * b);
+    w.Rv = ar.take<double>(m * b);
+    w.Ru = ar.take<double>(n * b);
+    w.Elo = ar.take_bytes(m * b * ds);
+    w.Flo = ar.take_bytes(n * b * ds);
+    w.AF = ar.take_bytes(m * b * ws_);
+    w.mu = ar.take<double>(b);
+    w.coef = ar.take<double>(b);
+  } else {
+    w.Ut2 = w.Vt2 = w.Rv = w.Ru = w.mu = w.coef = nullptr;
+    w.Elo = w.Flo = w.AF = nullptr;
+  }
+}
+
+static void make_op(const rr_operator* A, int32_t dt, Op& op) {
+  op.kind = A->kind;
+  op.m = A->kind == RR_DENSE ? A->m : A->n;
+  op.n = A->n;
+  op.A = (const double*)A->values;
+  op.lda = A->ld;
+  op.rp = A->row_ptr;
+  op.ci = A->col_idx;
+  op.va = (const float*)A->values;
+  op.lo_col = op.lo_row = nullptr;
+  op.dt = dt;
+  op.wt = dt == RR_F64 ? RR_F64 : RR_F32;
+}
+
+// The operator copies live at the front of the workspace.
+static void carve_op(Arena& ar, Op& op, bool symmetric) {
+  if (op.kind != RR_DENSE || op.dt == RR_F64) return;
+  op.lo_col = ar.take_bytes(op.m * op.n * dsz(op.dt));
+  op.lo_row = symmetric ? op.lo_col : ar.take_bytes(op.m * op.n * dsz(op.dt));
+}
+
+// FP64 residual of the first kk triplets: res = sqrt(|A v - s u|^2 + |A^T u - s v|^2) / s
+static rr_status svd_residual(const Op& op, SvdBufs& w, int64_t kk, double* R1, double* R2,
+                              cudaStream_t s) {
+  const int64_t m = op.m, n = op.n;
+  RR_TRY(apply_f64(op, kk, w.Vt, n, w.P, m, s));
+  RR_TRY(apply_f64_T(op, kk, w.Ut, m, w.Qm, n, s));
+  RR_TRY(residual_block(s, m, kk, w.P, m, w.Ut, m, w.sig, R1, m, w.ss, 0));
+  RR_TRY(residual_block(s, n, kk, w.Qm, n, w.Vt, n, w.sig, R2, n, w.ss, 1));
+  return res_finish(s, kk, w.ss, w.sig, w.res);
+}
+
+static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sigma_out,
+                         double* U_out, double* V_out, void* ws, size_t ws_bytes, rr_info* info,
+                         cudaStream_t s, bool batch_mode, int hess_grid, uint64_t seed) {
+  const int32_t dt = p->basis;
+  Op op;
+  make_op(Aop, dt, op);
+  const int64_t m = op.m, n = op.n, b = p->block, k = p->k;
+  const int q = p->degree;
+  const bool hess = p->hessenberg != 0;
+  const bool refine = p->refine != 0 && dt != RR_F64;
+  const int ph1 = refine ? (p->phase1_sweeps > 0 ? p->phase1_sweeps : 1) : p->max_sweeps;
+  Arena ar(ws, ws_bytes);
+  carve_op(ar, op, false);
+  SvdBufs w;
+  carve_svd(ar, op, b, refine, w);
+  double* v0buf = batch_mode ? ar.take<double>(n * b) : nullptr;
+  if (ar.overflow) return RR_ERR_WORKSPACE;
+  w.c.hess_grid = hess_grid;
+  RR_CUDA(cudaMemsetAsync(w.c.hess_ws, 0, 512, s));
+  const size_t ds = dsz(dt);
+  (void)ds;
+
+  // one-time operator casts (counted in the solve time)
+  if (op.lo_col) RR_TRY(rr_cast_operator(m, n, op.A, op.lda, dt, op.lo_col, op.lo_row, s));
+
+  // a1: start block
+  const double* v0 = p->v0;
+  if (batch_mode) {
+    RR_TRY(uniform_block(s, n, b, seed, v0buf, n));
+    v0 = v0buf;
+  }
+  RR_TRY(rr_colscale_cast(n, b, v0, n, dt, w.Vlo, n, w.c.scale, s));
+
+  rr_info inf;
+  memset(&inf, 0, sizeof(inf));
+  std::vector<double> hres(b);
+  int sweep = 0;
+  bool converged = false;
+
+  // ---------------- phase 1: the paper's method ----------------
+  for (int ps = 0; ps < ph1 && sweep < p->max_sweeps; ++ps) {
+    if (ps > 0) RR_TRY(rr_colscale_cast(n, b, w.Vt, n, dt, w.Vlo, n, w.c.scale, s));
+    for (int it = 0; it < q; ++it) {
+      RR_TRY(apply_lowp(op, b, w.Vlo, n, w.W, m, nullptr, 0, nullptr, s));        // W = A V
+      RR_TRY(basis_step(w.c, hess, op.wt, dt, m, b, w.W, m, w.Ulo, m, s));          // U = basis(W)
+      RR_TRY(apply_lowp_T(op, b, w.Ulo, m, w.W, n, nullptr, 0, nullptr, s));       // Z = A^T U
+      RR_TRY(basis_step(w.c, hess, op.wt, dt, n, b, w.W, n, w.Vlo, n, s));          // V = basis(Z)
+    }
+    // Algorithm 5: B = U^T (A V), Gu = U^T U, Gv = V^T V (FP64 accumulation)
+    RR_TRY(apply_lowp(op, b, w.Vlo, n, w.Pw, m, nullptr, 0, nullptr, s));
+    RR_TRY(gram(w.c, m, b, b, dt, w.Ulo, m, dt, w.Ulo, m, w.Gu, b, s));
+    RR_TRY(gram(w.c, n, b, b, dt, w.Vlo, n, dt, w.Vlo, n, w.Gv, b, s));
+    RR_TRY(gram(w.c, m, b, b, dt, w.Ulo, m, op.wt, w.Pw, m, w.Bm, b, s));
+    RR_TRY(rr_pencil_svd(b, b, w.Bm, w.Gu, w.Gv, w.sig2, w.Ys, w.Zs, w.c.pen_ws, w.c.pen_bytes,
+                         nullptr, s));
+    RR_TRY(lift(s, dt, m, b, b, w.Ulo, m, w.Ys, b, w.Ut, m, 0));
+    RR_TRY(lift(s, dt, n, b, b, w.Vlo, n, w.Zs, b, w.Vt, n, 0));
+    RR_CUDA(cudaMemcpyAsync(w.sig, w.sig2, b * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    ++sweep;
+    if (!refine && !batch_mode) {
+      // plain method: FP64 residual check of the wanted triplets every sweep
+      RR_TRY(svd_residual(op, w, k, w.Rv ? w.Rv : w.P, w.Ru ? w.Ru : w.Qm, s));
+      RR_CUDA(cudaMemcpyAsync(hres.data(), w.res, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+      RR_CUDA(cudaStreamSynchronize(s));
+      RR_TRY(read_err(w.c, s));
+      double mx;
+      inf.n_converged = count_converged(hres.data(), (int)k, p->tol, &mx);
+      inf.max_res = mx;
+      if (sweep <= 64) inf.res_history[sweep - 1] = mx;
+      if (inf.n_converged == k) {
+        converged = true;
+        break;
+      }
+    }
+  }
+
+  // ---------------- phase 2: refinement ----------------
+  if (refine) {
+    const int64_t b2 = 2 * b;
+    for (;;) {
+      // residual of all b Ritz triplets, FP64-accurate
+      RR_TRY(apply_f64(op, b, w.Vt, n, w.P, m, s));      // P = A V~
+      RR_TRY(apply_f64_T(op, b, w.Ut, m, w.Qm, n, s));   // Q = A^T U~
+      RR_TRY(residual_block(s, m, b, w.P, m, w.Ut, m, w.sig, w.Rv, m, w.ss, 0));
+      RR_TRY(residual_block(s, n, b, w.Qm, n, w.Vt, n, w.sig, w.Ru, n, w.ss, 1));
+      RR_TRY(res_finish(s, b, w.ss, w.sig, w.res));
+      if (!batch_mode) {
+        RR_CUDA(cudaMemcpyAsync(hres.data(), w.res, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+        RR_CUDA(cudaStreamSynchronize(s));
+        RR_TRY(read_err(w.c, s));
+        double mx;
+        inf.n_converged = count_converged(hres.data(), (int)k, p->tol, &mx);
+        inf.max_res = mx;
+        if (sweep >= 1 && sweep <= 64) inf.res_history[sweep - 1] = mx;
+        if (inf.n_converged == k) {
+          converged = true;
+          break;
+        }
+      }
+      if (sweep >= p->max_sweeps) break;
+      // correction recurrence (low precision):
+      //   E_1 = R_v;  F_j = A^T E_j + R_u S^(2j-1);  E_{j+1} = A F_j + R_v S^(2j)
+      // each block kept at unit column inf-norm, the injection coefficient
+      // tracked per column (coef <- coef * sigma / mu after each scaling).
+      RR_TRY(fill(s, b, 1.0, w.coef));
+      RR_TRY(scale_cast(s, RR_F64, m, b, w.Rv, m, w.mu, dt, w.Elo, m, w.coef, w.sig));
+      for (int j = 0; j < q; ++j) {
+        RR_TRY(apply_lowp_T(op, b, w.Elo, m, w.W, n, w.Ru, n, w.coef, s));
+        RR_TRY(project_out(w.c, s, n, b, w.Vt, n, (float*)w.W, n, w.Ys));
+        RR_TRY(scale_cast(s, op.wt, n, b, w.W, n, w.mu, dt, w.Flo, n, w.coef, w.sig));
+        RR_TRY(apply_lowp(op, b, w.Flo, n, w.AF, m, w.Rv, m, w.coef, s));
+        RR_TRY(project_out(w.c, s, m, b, w.Ut, m, (float*)w.AF, m, w.Ys));
+        if (j + 1 < q) RR_TRY(scale_cast(s, op.wt, m, b, w.AF, m, w.mu, dt, w.Elo, m, w.coef, w.sig));
+      }
+      // conditioning of the correction blocks (Algorithm 8), then A F for the
+      // low-precision block of the projected matrix
+      RR_TRY(basis_step(w.c, hess, op.wt, dt, m, b, w.AF, m, w.Elo, m, s));
+      RR_TRY(basis_step(w.c, hess, op.wt, dt, n, b, w.W, n, w.Flo, n, s));
+      RR_TRY(apply_lowp(op, b, w.Flo, n, w.AF, m, nullptr, 0, nullptr, s));
+      // projected blocks over S_u = [U~, E], S_v = [V~, F]  (ld 2b)
+      double* B = w.Bm;
+      RR_TRY(gram(w.c, m, b, b, RR_F64, w.Ut, m, RR_F64, w.P, m, B, b2, s));                   // U~^T A V~
+      RR_TRY(gram(w.c, n, b, b, RR_F64, w.Qm, n, dt, w.Flo, n, B + b * b2, b2, s));          // U~^T A F
+      RR_TRY(gram(w.c, m, b, b, dt, w.Elo, m, RR_F64, w.P, m, B + b, b2, s));                // E^T A V~
+      RR_TRY(gram(w.c, m, b, b, dt, w.Elo, m, op.wt, w.AF, m, B + b + b * b2, b2, s));       // E^T A F
+      RR_TRY(gram(w.c, m, b, b, RR_F64, w.Ut, m, RR_F64, w.Ut, m, w.Gu, b2, s));
+      RR_TRY(gram(w.c, m, b, b, RR_F64, w.Ut, m, dt, w.Elo, m, w.Gu + b * b2, b2, s));
+      RR_TRY(transpose(s, b, b, w.Gu + b * b2, b2, w.Gu + b, b2));
+      RR_TRY(gram(w.c, m, b, b, dt, w.Elo, m, dt, w.Elo, m, w.Gu + b + b * b2, b2, s));
+      RR_TRY(gram(w.c, n, b, b, RR_F64, w.Vt, n, RR_F64, w.Vt, n, w.Gv, b2, s));
+      RR_TRY(gram(w.c, n, b, b, RR_F64, w.Vt, n, dt, w.Flo, n, w.Gv + b * b2, b2, s));
+      RR_TRY(transpose(s, b, b, w.Gv + b * b2, b2, w.Gv + b, b2));
+      RR_TRY(gram(w.c, n, b, b, dt, w.Flo, n, dt, w.Flo, n, w.Gv + b + b * b2, b2, s));
+      RR_TRY(rr_pencil_svd(b2, b2, B, w.Gu, w.Gv, w.sig2, w.Ys, w.Zs, w.c.pen_ws, w.c.pen_bytes,
+                           nullptr, s));
+      // lift the leading b triplets
+      RR_TRY(lift(s, RR_F64, m, b, b, w.Ut, m, w.Ys, b2, w.Ut2, m, 0));
+      RR_TRY(lift(s, dt, m, b, b, w.Elo, m, w.Ys + b, b2, w.Ut2, m, 1));
+      RR_TRY(lift(s, RR_F64, n, b, b, w.Vt, n, w.Zs, b2, w.Vt2, n, 0));
+      RR_TRY(lift(s, dt, n, b, b, w.Flo, n, w.Zs + b, b2, w.Vt2, n, 1));
+      std::swap(w.Ut, w.Ut2);
+      std::swap(w.Vt, w.Vt2);
+      RR_CUDA(cudaMemcpyAsync(w.sig, w.sig2, b * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      ++sweep;
+      ++inf.refine_sweeps;
+    }
+  }
+  if (batch_mode && !refine) {
+    // final residual for the caller's convergence count (read after the graph)
+    RR_TRY(svd_residual(op, w, k, w.P, w.Qm, s));
+  }
+
+  // outputs: sigma, U, V (first k), unit columns, sign fixed on V
+  RR_CUDA(cudaMemcpyAsync(sigma_out, w.sig, k * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  RR_CUDA(cudaMemcpy2DAsync(U_out, m * sizeof(double), w.Ut, m * sizeof(double), m * sizeof(double), k,
+                            cudaMemcpyDeviceToDevice, s));
+  RR_CUDA(cudaMemcpy2DAsync(V_out, n * sizeof(double), w.Vt, n * sizeof(double), n * sizeof(double), k,
+                            cudaMemcpyDeviceToDevice, s));
+  RR_TRY(normalize_sign(s, n, k, V_out, n, m, U_out, m));
+  inf.sweeps = sweep;
+  if (info) *info = inf;
+  if (batch_mode) return RR_OK;
+  RR_CUDA(cudaStreamSynchronize(s));
+  RR_TRY(read_err(w.c, s));
+  return converged ? RR_OK : RR_ERR_NO_CONV;
+}
+
+static size_t svd_ws(const rr_operator* A, const rr_params* p, bool batch) {
+  Op op;
+  make_op(A, p->basis, op);
+  Arena ar(nullptr, 0);
+  carve_op(ar, op, false);
+  SvdBufs w;
+  const bool refine = p->refine != 0 && p->basis != RR_F64;
+  carve_svd(ar, op, p->block, refine, w);
+  if (batch) ar.take<double>(op.n * p->block);
+  return ar.off + 4096;
+}
+
+// ===========================================================================
+// symmetric eigenproblem (Algorithm 3 with Algorithm 1/8, power or Chebyshev
+// filter, and the refinement phase)
+// ===========================================================================
+struct EigBufs {
+  Common c;
+  void *Vlo, *W, *Pw, *Dlo, *Dprev, *AD;
+  double *G, *H, *Y, *Ysel, *th2;
+  double *X, *X2, *theta, *P, *R, *ss, *res, *mu, *coef, *kap, *kap_prev, *rho, *gam, *gersh;
+};
+
+static void carve_eig(Arena& ar, const Op& op, int64_t b, bool refine, EigBufs& w) {
+  const int64_t n = op.n, b2 = refine ? 2 * b : b;
+  const size_t ds = dsz(op.dt), ws_ = dsz(op.wt);
+  carve_common(ar, n, b2, op.wt, w.c);
+  w.Vlo = ar.take_bytes(n * b * ds);
+  w.W = ar.take_bytes(n * b * ws_);
+  w.Pw = ar.take_bytes(n * b * ws_);
+  w.Dprev = ar.take_bytes(n * b * ds);
+  w.G = ar.take<double>(b2 * b2);
+  w.H = ar.take<double>(b2 * b2);
+  w.Y = ar.take<double>(b2 * b2);
+  w.Ysel = ar.take<double>(b2 * b);
+  w.th2 = ar.take<double>(b2);
+  w.X = ar.take<double>(n * b);
+  w.theta = ar.take<double>(b);
+  w.P = ar.take<double>(n * b);
+  w.R = ar.take<double>(n * b);
+  w.ss = ar.take<double>(b);
+  w.res = ar.take<double>(b);
+  w.gersh = ar.take<double>(520);
+  w.mu = ar.take<double>(b);
+  w.coef = ar.take<double>(b);
+  w.kap = ar.take<double>(b);
+  w.kap_prev = ar.take<double>(b);
+  w.rho = ar.take<double>(b);
+  w.gam = ar.take<double>(b);
+  if (refine) {
+    w.X2 = ar.take<double>(n * b);
+    w.Dlo = ar.take_bytes(n * b * ds);
+    w.AD = ar.take_bytes(n * b * ws_);
+  } else {
+    w.X2 = nullptr;
+    w.Dlo = w.AD = nullptr;
+  }
+}
+
+// Plain scaled Chebyshev filter of the block V (dt) into the wt buffer `out`
+// (Y_d, unscaled); Y_j in dt ping-pong buffers.  Bounds: damp [a, up],
+// normalised at a0.
+static rr_status cheb_filter(const Op& op, EigBufs& w, int64_t b, int d, double a, double up,
+                             double a0, cudaStream_t s) {
+  const int64_t n = op.n;
+  const double e = (up - a) / 2, c = (up + a) / 2, s1 = e / (a0 - c);
+  void* y0 = w.Vlo;   // Y_0 (kept: Vlo is overwritten later by the basis step)
+  void* y1 = w.Dprev;
+  void* y2 = w.Pw;    // scratch in wt; reuse only when wt == dt
+  // Y_1 = (s1/e)(A - cI) Y_0
+  if (d == 1) return rr_chebyshev_step(n, b, op.rp, op.ci, op.va, op.dt, y0, nullptr, n, s1 / e, c,
+                                       0.0, nullptr, nullptr, 0, nullptr, op.wt, w.W, n, s);
+  RR_TRY(rr_chebyshev_step(n, b, op.rp, op.ci, op.va, op.dt, y0, nullptr, n, s1 / e, c, 0.0, nullptr,
+                           nullptr, 0, nullptr, op.dt, y1, n, s));
+  // ping-pong among three dt buffers: y0 (Vlo), y1 (Dprev), y2 (needs dt storage)
+  // use W's storage as the third dt buffer when dt is narrower than wt
+  y2 = w.W;
+  double sg = s1;
+  void *pm1 = y0, *p0 = y1, *p1 = y2;
+  for (int j = 2; j <= d; ++j) {
+    const double sn = 1.0 / (2.0 / s1 - sg);
+    const bool last = (j == d);
+    void* outp = last ? w.Pw : p1;  // final step written in wt to Pw
+    RR_TRY(rr_chebyshev_step(n, b, op.rp, op.ci, op.va, op.dt, p0, pm1, n, 2.0 * sn / e, c, sg * sn,
+                             nullptr, nullptr, 0, nullptr, last ? op.wt : op.dt, outp, n, s));
+    void* t = pm1;
+    pm1 = p0;
+    p0 = p1;
+    p1 = t;
+    sg = sn;
+  }
+  // result Y_d is in Pw (wt); move to W for the basis step
+  RR_CUDA(cudaMemcpyAsync(w.W, w.Pw, n * b * dsz(op.wt), cudaMemcpyDeviceToDevice, s));
+  return RR_OK;
+}
+
+static rr_status eig_run(const rr_operator* Aop, const rr_params* p, double* theta_out,
+                         double* X_out, void* ws, size_t ws_bytes, rr_info* info, cudaStream_t s) {
+  const int32_t dt = p->basis;
+  Op op;
+  make_op(Aop, dt, op);
+  const int64_t n = op.n, b = p->block, k = p->k;
+  const int q = p->degree;
+  const bool hess = p->hessenberg != 0;
+  const bool cheb = p->filter == RR_CHEBYSHEV;
+  const bool refine = p->refine != 0 && dt != RR_F64;
+  const int ph1 = refine ? (p->phase1_sweeps > 0 ? p->phase1_sweeps : 1) : p->max_sweeps;
+  if (cheb && op.kind != RR_CSR) return RR_ERR_ARG;
+  if (!cheb && p->which != RR_LARGEST) return RR_ERR_ARG;
+  Arena ar(ws, ws_bytes);
+  carve_op(ar, op, true);
+  EigBufs w;
+  carve_eig(ar, op, b, refine, w);
+  if (ar.overflow) return RR_ERR_WORKSPACE;
+  RR_CUDA(cudaMemsetAsync(w.c.hess_ws, 0, 512, s));
+  if (op.lo_col) RR_TRY(rr_cast_operator(n, n, op.A, op.lda, dt, op.lo_col, nullptr, s));
+
+  double lo = p->bounds[0], up = p->bounds[1];
+  if (cheb && !(lo < up)) {
+    RR_TRY(csr_gershgorin(s, n, op.rp, op.ci, op.va, w.gersh));
+    double h2[2];
+    RR_CUDA(cudaMemcpyAsync(h2, w.gersh + 512, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    RR_CUDA(cudaStreamSynchronize(s));
+    lo = h2[0];
+    up = h2[1];
+  }
+  double ca = lo + 0.1 * (up - lo), ca0 = lo;  // Chebyshev cut and scaling point
+
+  RR_TRY(rr_colscale_cast(n, b, p->v0, n, dt, w.Vlo, n, w.c.scale, s));
+  rr_info inf;
+  memset(&inf, 0, sizeof(inf));
+  std::vector<double> hres(b), hth(b);
+  int sweep = 0;
+  bool converged = false;
+
+  auto update_bounds = [&]() -> rr_status {
+    if (!cheb) return RR_OK;
+    RR_CUDA(cudaMemcpyAsync(hth.data(), w.theta, b * sizeof(double), cudaMemcpyDeviceToHost, s));
+    RR_CUDA(cudaStreamSynchronize(s));
+    double mn = INFINITY, mxv = -INFINITY;
+    for (int i = 0; i < b; ++i)
+      if (!std::isnan(hth[i])) {
+        mn = fmin(mn, hth[i]);
+        mxv = fmax(mxv, hth[i]);
+      }
+    if (mn < mxv && mxv < up) {
+      ca = mxv;
+      ca0 = mn;
+    }
+    return RR_OK;
+  };
+
+  // ---------------- phase 1 ----------------
+  for (int ps = 0; ps < ph1 && sweep < p->max_sweeps; ++ps) {
+    if (ps > 0) RR_TRY(rr_colscale_cast(n, b, w.X, n, dt, w.Vlo, n, w.c.scale, s));
+    if (cheb) {
+      RR_TRY(cheb_filter(op, w, b, q, ca, up, ca0, s));
+      RR_TRY(basis_step(w.c, hess, op.wt, dt, n, b, w.W, n, w.Vlo, n, s));
+    } else {
+      for (int it = 0; it < q; ++it) {
+        RR_TRY(apply_lowp(op, b, w.Vlo, n, w.W, n, nullptr, 0, nullptr, s));
+        RR_TRY(basis_step(w.c, hess, op.wt, dt, n, b, w.W, n, w.Vlo, n, s));
+      }
+    }
+    // Algorithm 3: H = V^T (A V), G = V^T V, H Y = G Y Theta, X = V Y
+    RR_TRY(apply_lowp(op, b, w.Vlo, n, w.Pw, n, nullptr, 0, nullptr, s));
+    RR_TRY(gram(w.c, n, b, b, dt, w.Vlo, n, dt, w.Vlo, n, w.G, b, s));
+    RR_TRY(gram(w.c, n, b, b, dt, w.Vlo, n, op.wt, w.Pw, n, w.H, b, s));
+    RR_TRY(rr_pencil_eig(b, w.H, w.G, w.th2, w.Y, w.c.pen_ws, w.c.pen_bytes, nullptr, s));
+    RR_TRY(select_eig(s, b, b, p->which, w.th2, w.Y, b, w.theta, w.Ysel, b));
+    RR_TRY(lift(s, dt, n, b, b, w.Vlo, n, w.Ysel, b, w.X, n, 0));
+    ++sweep;
+    RR_TRY(update_bounds());
+    if (!refine) {
+      // FP64 residual of the wanted pairs.  With an FP64 basis A X = (A V) Y exactly.
+      if (dt == RR_F64) RR_TRY(lift(s, RR_F64, n, k, b, w.Pw, n, w.Ysel, b, w.P, n, 0));
+      else RR_TRY(apply_f64(op, k, w.X, n, w.P, n, s));
+      RR_TRY(residual_block(s, n, k, w.P, n, w.X, n, w.theta, w.R, n, w.ss, 0));
+      RR_TRY(res_finish(s, k, w.ss, w.theta, w.res));
+      RR_CUDA(cudaMemcpyAsync(hres.data(), w.res, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+      RR_CUDA(cudaStreamSynchronize(s));
+      RR_TRY(read_err(w.c, s));
+      double mx;
+      inf.n_converged = count_converged(hres.data(), (int)k, p->tol, &mx);
+      inf.max_res = mx;
+      if (sweep <= 64) inf.res_history[sweep - 1] = mx;
+      if (inf.n_converged == k) {
+        converged = true;
+        break;
+      }
+    }
+  }
+
+  // ---------------- phase 2 ----------------
+  if (refine) {
+    const int64_t b2 = 2 * b;
+    for (;;) {
+      RR_TRY(apply_f64(op, b, w.X, n, w.P, n, s));  // P = A X, FP64-accurate
+      RR_TRY(residual_block(s, n, b, w.P, n, w.X, n, w.theta, w.R, n, w.ss, 0));
+      RR_TRY(res_finish(s, b, w.ss, w.theta, w.res));
+      RR_CUDA(cudaMemcpyAsync(hres.data(), w.res, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+      RR_CUDA(cudaStreamSynchronize(s));
+      RR_TRY(read_err(w.c, s));
+      double mx;
+      inf.n_converged = count_converged(hres.data(), (int)k, p->tol, &mx);
+      inf.max_res = mx;
+      if (sweep >= 1 && sweep <= 64) inf.res_history[sweep - 1] = mx;
+      if (inf.n_converged == k) {
+        converged = true;
+        break;
+      }
+      if (sweep >= p->max_sweeps) break;
+      if (cheb) {
+        // D_1 = (s1/e) R;  D_{j+1} = (2 s_{j+1}/e)(A - cI) D_j - s_j s_{j+1} D_{j-1}
+        //                           + (2 s_{j+1}/e) phi_j(theta) R
+        // with D_j = s_j * Dhat_j, kappa_j = phi_j / s_j, rho_j = s_{j-1} / s_j.
+        const double e = (up - ca) / 2, c = (up + ca) / 2, s1 = e / (ca0 - c);
+        RR_TRY(scale_cast(s, RR_F64, n, b, w.R, n, w.mu, dt, w.Vlo, n, nullptr, nullptr));
+        // kappa_1 = (theta - c)/mu_1 ; kappa_0 rho_1 = e/(s1 mu_1)  (phi_0 / s_1)
+        // computed by the coefficient kernel from kappa=1/(mu s1/e) seeds:
+        RR_TRY(fill(s, b, 0.0, w.kap));
+        RR_TRY(fill(s, b, 0.0, w.kap_prev));
+        RR_TRY(fill(s, b, 1.0, w.rho));
+        // kap <- ((s1/e)(theta - c)*1 - 0)/((s1/e) mu) : an = 1, bn = 0 with kap = 1, then divide
+        RR_TRY(fill(s, b, e / s1, w.kap));
+        RR_TRY(cheb_coef_update(s, b, w.theta, w.mu, s1 / e, c, 0.0, w.kap, w.kap_prev, w.rho));
+        // now kap = (theta - c)/mu_1, kap_prev = e/s1, rho = 1/mu_1 -> kap_prev*rho = e/(s1 mu_1)
+        void* dm1 = nullptr;  // Dhat_0 = 0
+        void* d0 = w.Vlo;
+        void* d1 = w.Dprev;
+        double sg = s1;
+        for (int j = 1; j < q; ++j) {
+          const double sn = 1.0 / (2.0 / s1 - sg);
+          const double an = 2.0 * sn / e, bn = sg * sn;
+          RR_TRY(vec_scale(s, b, an, w.kap, w.gam));
+          RR_TRY(rr_chebyshev_step(n, b, op.rp, op.ci, op.va, dt, d0, dm1, n, an, c, bn, w.rho, w.R, n,
+                                   w.gam, op.wt, w.W, n, s));
+          RR_TRY(project_out(w.c, s, n, b, w.X, n, (float*)w.W, n, w.Y));
+          if (j + 1 < q) {
+            // Dhat_{j+1} = T / mu into the buffer of Dhat_{j-1}
+            void* dst = dm1 ? dm1 : d1;
+            RR_TRY(scale_cast(s, op.wt, n, b, w.W, n, w.mu, dt, dst, n, nullptr, nullptr));
+            RR_TRY(cheb_coef_update(s, b, w.theta, w.mu, an, c, bn, w.kap, w.kap_prev, w.rho));
+            dm1 = d0;
+            d0 = dst;
+          }
+          sg = sn;
+        }
+        if (q == 1) RR_TRY(scale_cast(s, RR_F64, n, b, w.R, n, w.mu, op.wt, w.W, n, nullptr, nullptr));
+      } else {
+        // D_1 = R;  D_{j+1} = A D_j + R Theta^j  (coef <- coef theta / mu)
+        RR_TRY(fill(s, b, 1.0, w.coef));
+        if (q == 1) {
+          RR_TRY(scale_cast(s, RR_F64, n, b, w.R, n, w.mu, op.wt, w.W, n, nullptr, nullptr));
+        } else {
+          RR_TRY(scale_cast(s, RR_F64, n, b, w.R, n, w.mu, dt, w.Vlo, n, w.coef, w.theta));
+          for (int j = 1; j < q; ++j) {
+            RR_TRY(apply_lowp(op, b, w.Vlo, n, w.W, n, w.R, n, w.coef, s));
+            RR_TRY(project_out(w.c, s, n, b, w.X, n, (float*)w.W, n, w.Y));
+            if (j + 1 < q) RR_TRY(scale_cast(s, op.wt, n, b, w.W, n, w.mu, dt, w.Vlo, n, w.coef, w.theta));
+          }
+        }
+      }
+      RR_TRY(basis_step(w.c, hess, op.wt, dt, n, b, w.W, n, w.Dlo, n, s));
+      RR_TRY(apply_lowp(op, b, w.Dlo, n, w.AD, n, nullptr, 0, nullptr, s));
+      // projected pencil over S = [X, D] (ld 2b)
+      RR_TRY(gram(w.c, n, b, b, RR_F64, w.X, n, RR_F64, w.X, n, w.G, b2, s));
+      RR_TRY(gram(w.c, n, b, b, RR_F64, w.X, n, dt, w.Dlo, n, w.G + b * b2, b2, s));
+      RR_TRY(transpose(s, b, b, w.G + b * b2, b2, w.G + b, b2));
+      RR_TRY(gram(w.c, n, b, b, dt, w.Dlo, n, dt, w.Dlo, n, w.G + b + b * b2, b2, s));
+      RR_TRY(gram(w.c, n, b, b, RR_F64, w.X, n, RR_F64, w.P, n, w.H, b2, s));
+      RR_TRY(gram(w.c, n, b, b, RR_F64, w.P, n, dt, w.Dlo, n, w.H + b * b2, b2, s));
+      RR_TRY(transpose(s, b, b, w.H + b * b2, b2, w.H + b, b2));
+      RR_TRY(gram(w.c, n, b, b, dt, w.Dlo, n, op.wt, w.AD, n, w.H + b + b * b2, b2, s));
+      RR_TRY(rr_pencil_eig(b2, w.H, w.G, w.th2, w.Y, w.c.pen_ws, w.c.pen_bytes, nullptr, s));
+      RR_TRY(select_eig(s, b2, b, p->which, w.th2, w.Y, b2, w.theta, w.Ysel, b2));
+      RR_TRY(lift(s, RR_F64, n, b, b, w.X, n, w.Ysel, b2, w.X2, n, 0));
+      RR_TRY(lift(s, dt, n, b, b, w.Dlo, n, w.Ysel + b, b2, w.X2, n, 1));
+      std::swap(w.X, w.X2);
+      ++sweep;
+      ++inf.refine_sweeps;
+      RR_TRY(update_bounds());
+    }
+  }
+
+  RR_CUDA(cudaMemcpyAsync(theta_out, w.theta, k * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  RR_CUDA(cudaMemcpy2DAsync(X_out, n * sizeof(double), w.X, n * sizeof(double), n * sizeof(double), k,
+                            cudaMemcpyDeviceToDevice, s));
+  RR_TRY(normalize_sign(s, n, k, X_out, n, 0, nullptr, 0));
+  RR_CUDA(cudaStreamSynchronize(s));
+  RR_TRY(read_err(w.c, s));
+  inf.sweeps = sweep;
+  if (info) *info = inf;
+  return converged ? RR_OK : RR_ERR_NO_CONV;
+}
+
+static size_t eig_ws(const rr_operator* A, const rr_params* p) {
+  Op op;
+  make_op(A, p->basis, op);
+  Arena ar(nullptr, 0);
+  carve_op(ar, op, true);
+  EigBufs w;
+  const bool refine = p->refine != 0 && p->basis != RR_F64;
+  carve_eig(ar, op, p->block, refine, w);
+  return ar.off + 4096;
+}
+
+static rr_status check_op(const rr_operator* A, bool svd) {
+  if (!A || !A->values) return RR_ERR_ARG;
+  if (A->kind == RR_DENSE) {
+    if (A->dtype != RR_F64 || A->m <= 0 || A->n <= 0 || A->ld < A->m) return RR_ERR_ARG;
+    if (svd && A->m < A->n) return RR_ERR_ARG;
+    if (!svd && A->m != A->n) return RR_ERR_ARG;
+    return RR_OK;
+  }
+  if (A->kind == RR_CSR) {
+    if (svd || A->dtype != RR_F32 || A->n <= 0 || !A->row_ptr || !A->col_idx) return RR_ERR_ARG;
+    if (A->n > 0x7fffffff || A->nnz > 0x7fffffff) return RR_ERR_ARG;
+    return RR_OK;
+  }
+  return RR_ERR_ARG;
+}
+
+}  // namespace rr
+
+using namespace rr;
+
+extern "C" size_t rr_workspace_size(const rr_operator* A, const rr_params* p, int svd) {
+  if (check_op(A, svd != 0) != RR_OK || !p) return 0;
+  return svd ? svd_ws(A, p, false) : eig_ws(A, p);
+}
+
+extern "C" rr_status rr_eig(const rr_operator* A, const rr_params* p, double* theta, double* X,
+                            void* ws, size_t ws_bytes, rr_info* info, void* stream) {
+  RR_TRY(check_op(A, false));
+  RR_TRY(check_params(p, A->n));
+  if (!theta || !X || !p->v0) return RR_ERR_ARG;
+  if (!ws || ws_bytes < eig_ws(A, p)) return RR_ERR_WORKSPACE;
+  return eig_run(A, p, theta, X, ws, ws_bytes, info, as_stream(stream));
+}
+
+extern "C" rr_status rr_svd(const rr_operator* A, const rr_params* p, double* sigma, double* U,
+                            double* V, void* ws, size_t ws_bytes, rr_info* info, void* stream) {
+  RR_TRY(check_op(A, true));
+  RR_TRY(check_params(p, A->n));
+  if (!sigma || !U || !V || !p->v0) return RR_ERR_ARG;
+  if (!ws || ws_bytes < svd_ws(A, p, false)) return RR_ERR_WORKSPACE;
+  return svd_run(A, p, sigma, U, V, ws, ws_bytes, info, as_stream(stream), false, 0, 0);
+}
+
+extern "C" size_t rr_batch_workspace_size(int32_t count, const rr_operator* A, const rr_params* p) {
+  if (count <= 0 || !A || !p) return 0;
+  size_t tot = 0;
+  for (int i = 0; i < count; ++i) {
+    if (check_op(&A[i], true) != RR_OK) return 0;
+    tot += align_up(svd_ws(&A[i], p, true), 4096);
+  }
+  return tot + 4096;
+}
+
+// All problems are captured into one CUDA graph: NS streams fork from the
+// caller's stream, problems are dealt round-robin to them, every problem runs
+// a fixed number of sweeps (phase 1 + refinement) with no host
+// synchronisation, its Hessenberg steps on one CTA (plain launches), and the
+// branches join back before the single graph launch completes.
+extern "C" rr_status rr_batch_svd(int32_t count, const rr_operator* A, const rr_params* p,
+                                  uint64_t seed, double* const* sigma, double* const* U,
+                                  double* const* V, void* ws, size_t ws_bytes,
+                                  rr_status* per_problem, rr_info* info, void* stream) {
+  if (count <= 0 || !A || !p || !sigma || !U || !V || !ws) return RR_ERR_ARG;
+  for (int i = 0; i < count; ++i) {
+    RR_TRY(check_op(&A[i], true));
+    RR_TRY(check_params(p, A[i].n));
+  }
+  if (ws_bytes < rr_batch_workspace_size(count, A, p)) return RR_ERR_WORKSPACE;
+  cudaStream_t s = as_stream(stream);
+  const int NS = 16;
+  // Capture on a private stream (the legacy default stream cannot be
+  // captured); the instantiated graph is launched on the caller's stream.
+  cudaStream_t cap = nullptr;
+  cudaStream_t br[NS] = {};
+  cudaEvent_t fork = nullptr, join[NS] = {};
+  rr_params pp = *p;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  rr_status st = RR_OK;
+  std::vector<size_t> offs(count);
+  size_t off = 0;
+  for (int i = 0; i < count; ++i) {
+    offs[i] = off;
+    off += align_up(svd_ws(&A[i], p, true), 4096);
+  }
+  std::vector<rr_info> infos(count);
+  auto cu = [&](cudaError_t e, const char* what) {
+    if (e != cudaSuccess && st == RR_OK) {
+      set_last_error(what, e);
+      st = RR_ERR_CUDA;
+    }
+  };
+  cu(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "rr_batch_svd stream");
+  for (int i = 0; i < NS && st == RR_OK; ++i) {
+    cu(cudaStreamCreateWithFlags(&br[i], cudaStreamNonBlocking), "rr_batch_svd stream");
+    cu(cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming), "rr_batch_svd event");
+  }
+  cu(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming), "rr_batch_svd event");
+  // the graph must see the caller's prior work on `s`: order cap after s
+  cudaEvent_t pre = nullptr;
+  cu(cudaEventCreateWithFlags(&pre, cudaEventDisableTiming), "rr_batch_svd event");
+  if (st == RR_OK) {
+    cu(cudaEventRecord(pre, s), "rr_batch_svd record");
+    cu(cudaStreamWaitEvent(cap, pre, 0), "rr_batch_svd wait");
+  }
+  bool capturing = false;
+  if (st == RR_OK) {
+    cu(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "rr_batch_svd capture");
+    capturing = st == RR_OK;
+  }
+  if (capturing) {
+    cu(cudaEventRecord(fork, cap), "rr_batch_svd fork");
+    for (int i = 0; i < NS; ++i) cu(cudaStreamWaitEvent(br[i], fork, 0), "rr_batch_svd fork wait");
+    for (int i = 0; i < count && st == RR_OK; ++i) {
+      size_t need = align_up(svd_ws(&A[i], p, true), 4096);
+      st = svd_run(&A[i], &pp, sigma[i], U[i], V[i], (char*)ws + offs[i], need, &infos[i], br[i % NS],
+                   true, 1, seed + (uint64_t)i);
+    }
+    for (int i = 0; i < NS; ++i) {
+      cudaEventRecord(join[i], br[i]);
+      cudaStreamWaitEvent(cap, join[i], 0);
+    }
+    cudaError_t ce = cudaStreamEndCapture(cap, &graph);
+    cu(ce, "rr_batch_svd end capture");
+  }
+  if (st == RR_OK) cu(cudaGraphInstantiate(&exec, graph, 0), "rr_batch_svd instantiate");
+  if (st == RR_OK) cu(cudaGraphLaunch(exec, s), "rr_batch_svd launch");
+  if (st == RR_OK) cu(cudaStreamSynchronize(s), "rr_batch_svd sync");
+  if (pre) cudaEventDestroy(pre);
+  if (cap) cudaStreamDestroy(cap);
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  for (int i = 0; i < NS; ++i) {
+    if (br[i]) cudaStreamDestroy(br[i]);
+    if (join[i]) cudaEventDestroy(join[i]);
+  }
+  if (fork) cudaEventDestroy(fork);
+  if (st != RR_OK) return st;
+  // per-problem residuals (device) -> convergence counts
+  int nbad = 0;
+  for (int i = 0; i < count; ++i) {
+    Op op;
+    make_op(&A[i], p->basis, op);
+    Arena ar((char*)ws + offs[i], align_up(svd_ws(&A[i], p, true), 4096));
+    carve_op(ar, op, false);
+    SvdBufs w;
+    carve_svd(ar, op, p->block, p->refine != 0 && p->basis != RR_F64, w);
+    std::vector<double> hres(p->k);
+    RR_CUDA(cudaMemcpy(hres.data(), w.res, p->k * sizeof(double), cudaMemcpyDeviceToHost));
+    int e = 0;
+    RR_CUDA(cudaMemcpy(&e, w.c.hess_ws, sizeof(int), cudaMemcpyDeviceToHost));
+    double mx;
+    infos[i].n_converged = count_converged(hres.data(), p->k, p->tol, &mx);
+    infos[i].max_res = mx;
+    rr_status ps = e ? (rr_status)e : (infos[i].n_converged == p->k ? RR_OK : RR_ERR_NO_CONV);
+    if (ps != RR_OK) ++nbad;
+    if (per_problem) per_problem[i] = ps;
+    if (info) info[i] = infos[i];
+  }
+  return nbad ? RR_ERR_NO_CONV : RR_OK;
+}

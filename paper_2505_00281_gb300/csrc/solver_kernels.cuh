@@ -1,0 +1,40 @@
+// Internal launchers shared between the kernel files and the host solver.
+#pragma once
+#include "rr_common.cuh"
+
+namespace rr {
+rr_status lift(cudaStream_t s, int32_t stype, int64_t n, int64_t b, int64_t p, const void* S,
+               int64_t lds, const double* Y, int64_t ldy, double* X, int64_t ldx, int accum);
+rr_status residual_block(cudaStream_t s, int64_t n, int64_t b, const double* P, int64_t ldp,
+                         const double* X, int64_t ldx, const double* theta, double* R, int64_t ldr,
+                         double* ss, int accum_ss);
+rr_status res_finish(cudaStream_t s, int64_t b, const double* ss, const double* theta, double* res);
+rr_status scale_cast(cudaStream_t s, int32_t ttype, int64_t n, int64_t b, const void* T, int64_t ldt,
+                     double* mu, int32_t dtype, void* D, int64_t ldd, double* coef,
+                     const double* sig);
+rr_status transpose(cudaStream_t s, int64_t p, int64_t q, const double* src, int64_t lds, double* dst,
+                    int64_t ldd);
+rr_status select_eig(cudaStream_t s, int64_t nb, int64_t b, int which, const double* theta,
+                     const double* Y, int64_t ldy, double* tsel, double* Ysel, int64_t ldys);
+rr_status normalize_sign(cudaStream_t s, int64_t n, int64_t k, double* X, int64_t ldx, int64_t m,
+                         double* U, int64_t ldu);
+rr_status vec_mul(cudaStream_t s, int64_t n, const double* a, const double* b, double* d);
+rr_status fill(cudaStream_t s, int64_t n, double v, double* d);
+rr_status uniform_block(cudaStream_t s, int64_t n, int64_t b, uint64_t seed, double* V, int64_t ldv);
+rr_status cheb_coef_update(cudaStream_t s, int64_t b, const double* theta, const double* mu,
+                           double alpha_next, double cshift, double beta_next, double* kappa,
+                           double* kappa_prev, double* rho);
+void small_gemm(cudaStream_t s, int ta, int tb, int M, int N, int K, double alpha, const double* A,
+                int lda, const double* B, int ldb, double beta, double* C, int ldc);
+rr_status csr_gershgorin(cudaStream_t s, int64_t n, const int32_t* rp, const int32_t* ci,
+                         const float* va, double* out2);
+}  // namespace rr
+
+namespace rr {
+rr_status hessenberg_ex(int32_t arith, int64_t n, int64_t k, void* W, int64_t ldw, int32_t qtype,
+                        void* Q, int64_t ldq, int32_t* piv, double tol, void* ws, size_t ws_bytes,
+                        cudaStream_t s, int max_grid);
+rr_status sub_lowrank_f32(cudaStream_t s, int64_t n, int64_t b, int64_t p, const double* X, int64_t ldx,
+                          const double* K, int64_t ldk, float* T, int64_t ldt);
+rr_status vec_scale(cudaStream_t s, int64_t n, double alpha, const double* a, double* d);
+}  // namespace rr

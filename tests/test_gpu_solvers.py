@@ -1,0 +1,155 @@
+"""End-to-end parity of the solvers (rr_eig, rr_svd, rr_batch_svd) with the
+FP64 oracle: converged values against the closed-form spectra and the
+oracle's own solve, residuals recomputed by the oracle in FP64 from the GPU's
+vectors, and the theorem's orthonormality."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import ofrr as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module")
+def rr():
+    import paper_2505_00281_gb300 as pkg
+    from paper_2505_00281_gb300 import build
+
+    build.build()
+    pkg.lib()
+    return pkg
+
+
+def dev(a):
+    import paper_2505_00281_gb300 as pkg
+    return pkg.fortran(torch.from_numpy(np.asfortranarray(a)).to(DEV))
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+@pytest.mark.parametrize("basis", ["f32", "bf16", "f64"])
+def test_eig_dense_config1_shape(rr, basis):
+    """Dense symmetric lambda_i = 1/i (config 1 recipe, n reduced), top 8, block 16."""
+    n, k, b = 600, 8, 16
+    A, lam = wl.config1(n)
+    V0 = wl.uniform_block(n, b, 1001)
+    refine = basis != "f64"
+    p = rr.api.make_params(k, b, 2, 60, 1e-10, basis=basis, v0=dev(V0), refine=refine, phase1_sweeps=2)
+    th, X, info = rr.rr_eig(rr.api.dense_operator(dev(A)), p, n)
+    th, X = host(th), host(X)
+    assert info["n_converged"] == k, info
+    assert np.max(np.abs(th - lam[:k]) / lam[:k]) <= 1e-10
+    res = O.residual_eig(O.dense_apply(A)[0], X, th)
+    assert res.max() <= 1.5e-10, res
+    assert np.abs(X.T @ X - np.eye(k)).max() < 1e-10
+
+
+def test_eig_fixed_sweeps_trajectory_config1(rr):
+    """Fixed work (6 sweeps, no refinement, FP32 basis) against the oracle's
+    FP64 trajectory.  The GPU's plain phase projects with the FP32 copy of A
+    (Sec. 4.2: working precision = input precision of the products), so its
+    Ritz values carry the operator rounding u32 |A|_2 on top of the
+    first-order basis term: |dtheta| <= 1e-10 |theta| + 2 u32 |A| + 10 u32 |A| r_oracle."""
+    n, k, b = 2000, 8, 16
+    A, lam = wl.config1(n)
+    V0 = wl.uniform_block(n, b, 1001)
+    p = rr.api.make_params(k, b, 1, 6, 1e-30, basis="f32", v0=dev(V0), refine=False)
+    th, X, info = rr.rr_eig(rr.api.dense_operator(dev(A)), p, n)
+    ora = O.solve_eig(O.dense_apply(A)[0], n, k, V0, degree=1, max_sweeps=6, tol=1e-30)
+    assert info["sweeps"] == 6 and ora.sweeps == 6
+    th = host(th)
+    u32, normA = 2.0 ** -24, 1.0
+    bound = 1e-10 * np.abs(ora.values) + 2 * u32 * normA + 10 * u32 * normA * ora.res
+    assert np.all(np.abs(th - ora.values) <= bound), (th - ora.values, bound)
+
+
+def test_svd_dense_bf16_refined(rr):
+    """Dense SVD sigma_i = exp(-i/60) (config 2 recipe, reduced), BF16 basis + refinement."""
+    m, n, b, k = 2048, 512, 32, 16
+    sig = wl.config2_sigma(n)
+    A = wl.dense_svd(m, n, sig, 2000)
+    V0 = wl.uniform_block(n, b, 2001)
+    p = rr.api.make_params(k, b, 4, 30, 1e-10, basis="bf16", v0=dev(V0), refine=True, phase1_sweeps=1)
+    s, U, V, info = rr.rr_svd(rr.api.dense_operator(dev(A)), p)
+    s, U, V = host(s), host(U), host(V)
+    assert info["n_converged"] == k, info
+    assert np.max(np.abs(s - sig[:k]) / sig[:k]) <= 1e-10
+    Amul, Atmul = O.dense_apply(A)
+    assert O.residual_svd(Amul, Atmul, U, V, s).max() <= 1.5e-10
+    assert np.abs(U.T @ U - np.eye(k)).max() < 1e-10
+    assert np.abs(V.T @ V - np.eye(k)).max() < 1e-10
+    ref = O.solve_svd(Amul, Atmul, m, n, k, V0, degree=4, max_sweeps=30, tol=1e-10)
+    assert np.max(np.abs(s - ref.values) / ref.values) <= 1e-10
+    # singular vectors agree with the oracle's up to the sign convention
+    for j in range(k):
+        assert min(np.abs(V[:, j] - ref.X[:, j]).max(), np.abs(V[:, j] + ref.X[:, j]).max()) < 1e-8
+
+
+def test_svd_dense_fp64_plain_method(rr):
+    m, n, b, k = 800, 200, 24, 8
+    sig = wl.config2_sigma(n)
+    A = wl.dense_svd(m, n, sig, 2100)
+    V0 = wl.uniform_block(n, b, 2101)
+    p = rr.api.make_params(k, b, 2, 40, 1e-10, basis="f64", v0=dev(V0), refine=False)
+    s, U, V, info = rr.rr_svd(rr.api.dense_operator(dev(A)), p)
+    assert info["n_converged"] == k, info
+    assert np.max(np.abs(host(s) - sig[:k]) / sig[:k]) <= 1e-10
+
+
+def test_eig_csr_chebyshev_lowest_constant_potential(rr):
+    """Chebyshev-filtered, lowest pairs of -Lap + c on a grid: closed form."""
+    N, k, b = 32, 12, 20
+    rp, ci, va = wl.grid_potential_csr(N, np.full(N * N, 0.5))
+    n = N * N
+    V0 = wl.uniform_block(n, b, 3001)
+    d = [torch.from_numpy(a).to(DEV) for a in (rp, ci, va)]
+    op = rr.api.csr_operator(*d)
+    p = rr.api.make_params(k, b, 10, 60, 1e-10, basis="bf16", v0=dev(V0), filter=rr.RR.CHEBYSHEV,
+                           which=rr.RR.SMALLEST, refine=True, phase1_sweeps=4)
+    th, X, info = rr.rr_eig(op, p, n)
+    exact = wl.laplacian_constant_eigs(N, 0.5)[:k]
+    th = host(th)
+    assert info["n_converged"] == k, info
+    assert np.max(np.abs(th - exact) / exact) <= 1e-9
+    res = O.residual_eig(O.csr_apply(rp, ci, va), host(X), th)
+    assert res.max() <= 1.5e-10
+
+
+def test_eig_csr_random_potential_vs_oracle(rr):
+    N, k, b = 24, 10, 16
+    rp, ci, va, v = wl.grid_schrodinger_csr(N, 10.0, 3000)
+    n = N * N
+    V0 = wl.uniform_block(n, b, 3002)
+    d = [torch.from_numpy(a).to(DEV) for a in (rp, ci, va)]
+    p = rr.api.make_params(k, b, 8, 80, 1e-10, basis="bf16", v0=dev(V0), filter=rr.RR.CHEBYSHEV,
+                           which=rr.RR.SMALLEST, refine=True, phase1_sweeps=4)
+    th, X, info = rr.rr_eig(rr.api.csr_operator(*d), p, n)
+    Amul = O.csr_apply(rp, ci, va)
+    dense = Amul(np.eye(n))
+    exact = np.linalg.eigvalsh(dense)[:k]          # brute force
+    assert info["n_converged"] == k, info
+    assert np.max(np.abs(host(th) - exact) / np.abs(exact)) <= 1e-9
+
+
+def test_batch_svd_small(rr):
+    shapes = [(256, 64), (400, 100), (300, 75), (512, 128), (260, 65)]
+    ops, As, sigs = [], [], []
+    for i, (m, n) in enumerate(shapes):
+        sg = wl.config4_sigma(n)
+        A = wl.dense_svd(m, n, sg, 4000 + i)
+        t = dev(A)
+        As.append((A, t))
+        sigs.append(sg)
+        ops.append(rr.api.dense_operator(t))
+    p = rr.api.make_params(8, 16, 2, 12, 1e-10, basis="bf16", refine=True, phase1_sweeps=2)
+    outs, st, infos = rr.rr_batch_svd(ops, p, seed=4000)
+    for i, ((s, U, V), (A, _)) in enumerate(zip(outs, As)):
+        s = host(s)
+        assert np.max(np.abs(s - sigs[i][:8]) / sigs[i][:8]) <= 1e-10, (i, s, sigs[i][:8], infos[i])
+        Amul, Atmul = O.dense_apply(A)
+        assert O.residual_svd(Amul, Atmul, host(U), host(V), s).max() <= 1.5e-10

@@ -1,0 +1,219 @@
+"""Parity of each hot-path stage (CUDA, through the C ABI) with the FP64 oracle.
+
+Integer/byte work (casts to BF16, Hessenberg pivots and FP32 arithmetic) is
+compared bit for bit; floating-point accumulations within the error bound of
+the arithmetic they use (stated per test).
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import ofrr as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rr():
+    import paper_2505_00281_gb300 as pkg
+    from paper_2505_00281_gb300 import build
+
+    build.build()
+    pkg.lib()
+    return pkg
+
+
+DEV = "cuda"
+U24 = 2.0 ** -24
+U53 = 2.0 ** -53
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.asfortranarray(a)).to(DEV)
+    if dtype is not None:
+        t = t.to(dtype)
+    import paper_2505_00281_gb300 as pkg
+    return pkg.fortran(t)
+
+
+def host(t):
+    return t.detach().to(torch.float64).cpu().numpy()
+
+
+# ---------------------------------------------------------------- a1
+@pytest.mark.parametrize("rows,cols", [(1000, 16), (257, 3), (1, 5)])
+def test_colscale_cast_bitexact(rr, rows, cols):
+    X = wl.uniform_block(rows, cols, 1001) - 0.3
+    X[:, 0] = 0.0  # zero column stays zero
+    for dt, rnd in ((torch.bfloat16, O.round_bf16), (torch.float32, lambda a: a.astype(np.float32).astype(np.float64)),
+                    (torch.float64, lambda a: a)):
+        Y, sc = rr.rr_colscale_cast(dev(X), dt)
+        ref = rnd(O.colscale_inf(X))
+        assert np.array_equal(host(Y), ref)
+        assert np.array_equal(host(sc), np.abs(X).max(axis=0))
+
+
+def test_cast_operator_bitexact(rr):
+    A = wl.gaussian(333, 130, 5)
+    col, row = rr.rr_cast_operator(dev(A), torch.bfloat16)
+    ref = O.round_bf16(A)
+    assert np.array_equal(host(col), ref)
+    assert np.array_equal(host(row).reshape(333, 130), ref)   # row-major copy
+
+
+# ---------------------------------------------------------------- a2
+@pytest.mark.parametrize("M,N,K", [(300, 40, 700), (128, 128, 4096), (1000, 7, 33)])
+def test_gemm_lowp_bf16_within_fp32_bound(rr, M, N, K):
+    rng = np.random.default_rng(M + N + K)
+    Ak = O.round_bf16(rng.standard_normal((K, M)))       # K x M, K-contiguous
+    B = O.round_bf16(rng.standard_normal((K, N)))
+    R = rng.standard_normal((M, N))
+    coef = rng.standard_normal(N)
+    C = rr.rr_gemm_lowp(2, M, N, K, dev(Ak, torch.bfloat16), K, dev(B, torch.bfloat16), K,
+                        R=dev(R), coef=dev(coef))
+    ref = Ak.T @ B + R * coef
+    bound = K * U24 * (np.abs(Ak).T @ np.abs(B)) + 2 * U24 * np.abs(R * coef) + 1e-30
+    err = np.abs(host(C) - ref)
+    assert np.all(err <= 2 * bound), (err / bound).max()
+
+
+def test_gemm_f64_both_layouts(rr):
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((250, 90))
+    B = rng.standard_normal((90, 17))
+    C = rr.rr_gemm_f64(0, dev(A), dev(B))
+    bound = 90 * U53 * (np.abs(A) @ np.abs(B))
+    assert np.all(np.abs(host(C) - A @ B) <= 2 * bound)
+    B2 = rng.standard_normal((250, 9))
+    C2 = rr.rr_gemm_f64(1, dev(A), dev(B2))
+    bound = 250 * U53 * (np.abs(A).T @ np.abs(B2))
+    assert np.all(np.abs(host(C2) - A.T @ B2) <= 2 * bound)
+
+
+# ---------------------------------------------------------------- a4 (Algorithm 8)
+@pytest.mark.parametrize("n,k", [(1000, 48), (20000, 32), (77, 77), (5, 3)])
+def test_hessenberg_bitexact_fp32(rr, n, k):
+    W = np.random.default_rng(n + k).standard_normal((n, k)).astype(np.float32)
+    Qo, pivo, keepo, Qfo = O.hessenberg(W, arith="f32")
+    Wd = dev(W.astype(np.float64), torch.float32)
+    Q, piv, err = rr.rr_hessenberg(Wd, qtype=torch.float32)
+    assert int(err.cpu()[0]) == 0
+    assert np.array_equal(piv.cpu().numpy().astype(np.int64), pivo)
+    assert np.array_equal(Q.cpu().numpy(), Qfo)
+
+
+def test_hessenberg_ties_rank_deficiency_and_bf16_output(rr):
+    # integer-valued block with repeated maxima and an exactly dependent column
+    rng = np.random.default_rng(9)
+    W = rng.integers(-3, 4, size=(600, 12)).astype(np.float32)
+    W[:, 5] = W[:, 1] + W[:, 2]
+    Qo, pivo, keepo, Qfo = O.hessenberg(W, arith="f32")
+    assert not keepo[5]
+    Q, piv, err = rr.rr_hessenberg(dev(W.astype(np.float64), torch.float32), qtype=torch.bfloat16)
+    assert np.array_equal(piv.cpu().numpy().astype(np.int64), pivo)
+    assert np.array_equal(host(Q), O.round_bf16(Qfo))
+
+
+def test_hessenberg_fp64_matches_lu(rr):
+    import scipy.linalg as sla
+    W = np.random.default_rng(11).uniform(0, 1, (3000, 40))
+    Q, piv, err = rr.rr_hessenberg(dev(W), qtype=torch.float64)
+    P, L, U = sla.lu(W)
+    assert np.abs(host(Q) - P @ L).max() < 1e-12
+    Qo, pivo, _, Qfo = O.hessenberg(W)
+    assert np.array_equal(piv.cpu().numpy().astype(np.int64), pivo)
+    assert np.array_equal(host(Q), Qfo)
+
+
+# ---------------------------------------------------------------- a5
+def test_gram_fp64_accurate_mixed_types(rr):
+    rng = np.random.default_rng(12)
+    n = 5000
+    X = O.round_bf16(rng.standard_normal((n, 37)))
+    Y = rng.standard_normal((n, 50))
+    G = rr.rr_gram(dev(X, torch.bfloat16), dev(Y))
+    ref = X.T @ Y
+    bound = n * U53 * (np.abs(X).T @ np.abs(Y))
+    assert np.all(np.abs(host(G) - ref) <= 2 * bound)
+    G2 = rr.rr_gram(dev(Y), dev(Y))
+    assert np.all(np.abs(host(G2) - Y.T @ Y) <= 2 * n * U53 * (np.abs(Y).T @ np.abs(Y)))
+
+
+# ---------------------------------------------------------------- a6
+@pytest.mark.parametrize("b", [16, 64, 129])
+def test_pencil_eig_matches_generalized_eigensolver(rr, b):
+    import scipy.linalg as sla
+    rng = np.random.default_rng(b)
+    U = rng.uniform(0, 1, (4 * b, b))
+    S = rng.standard_normal((4 * b, 4 * b))
+    A = S + S.T
+    H = U.T @ A @ U
+    G = U.T @ U
+    th, Y, dropped = rr.rr_pencil_eig(dev(H), dev(G))
+    ref = sla.eigh(H, G, eigvals_only=True)
+    th = host(th)
+    assert dropped == 0
+    scale = np.abs(ref).max()
+    assert np.abs(th - ref).max() <= 1e-10 * scale
+    Yh = host(Y)
+    assert np.abs(Yh.T @ G @ Yh - np.eye(b)).max() < 1e-8
+    assert np.abs(H @ Yh - G @ Yh * th).max() < 1e-8 * scale
+
+
+def test_pencil_eig_rank_deficient_drops(rr):
+    rng = np.random.default_rng(5)
+    U = rng.standard_normal((80, 10))
+    U = np.hstack([U, U[:, :3]])
+    S = rng.standard_normal((80, 80))
+    A = S + S.T
+    th, Y, dropped = rr.rr_pencil_eig(dev(U.T @ A @ U), dev(U.T @ U))
+    th = host(th)
+    assert dropped == 3
+    ref, *_ = O.rayleigh_ritz_eig(lambda Z: A @ Z, U)
+    assert np.all(np.isnan(th[10:]))
+    assert np.allclose(th[:10], ref, atol=1e-9)
+
+
+@pytest.mark.parametrize("b1,b2", [(32, 32), (64, 48), (130, 130)])
+def test_pencil_svd_matches_block_pencil(rr, b1, b2):
+    rng = np.random.default_rng(b1 * b2)
+    A = rng.standard_normal((300, 200))
+    U = rng.uniform(0, 1, (300, b1))
+    V = rng.uniform(0, 1, (200, b2))
+    B, Gu, Gv = U.T @ A @ V, U.T @ U, V.T @ V
+    s, Y, Z, dropped = rr.rr_pencil_svd(dev(B), dev(Gu), dev(Gv))
+    so, Yo, Zo = O.pencil_svd(B, Gu, Gv)          # literal 2x2 block pencil (Algorithm 5)
+    s = host(s)
+    assert np.allclose(s, so, rtol=1e-9, atol=1e-12 * so[0])
+    Ut = U @ host(Y)
+    Vt = V @ host(Z)
+    r = min(b1, b2)
+    assert np.abs(Ut.T @ Ut - np.eye(r)).max() < 1e-8
+    assert np.abs(Vt.T @ Vt - np.eye(r)).max() < 1e-8
+
+
+# ---------------------------------------------------------------- a3
+def test_csr_spmm_and_chebyshev_step(rr):
+    N, b = 40, 24
+    rp, ci, va, v = wl.grid_schrodinger_csr(N, 10.0, 3000)
+    n = N * N
+    Amul = O.csr_apply(rp, ci, va)
+    X = O.round_bf16(np.random.default_rng(1).standard_normal((n, b)))
+    Xp = O.round_bf16(np.random.default_rng(2).standard_normal((n, b)))
+    R = np.random.default_rng(3).standard_normal((n, b))
+    gam = np.random.default_rng(4).standard_normal(b)
+    bc = np.random.default_rng(5).uniform(0.5, 2, b)
+    d_rp, d_ci, d_va = (torch.from_numpy(a).to(DEV) for a in (rp, ci, va))
+    Y = rr.rr_csr_spmm(d_rp, d_ci, d_va, dev(X, torch.bfloat16))
+    ref = Amul(X)
+    assert np.abs(host(Y) - ref).max() <= 8 * U24 * (np.abs(ref).max() + 20)
+    alpha, c, beta = 0.7, 3.0, 0.4
+    Yn = rr.rr_chebyshev_step(d_rp, d_ci, d_va, dev(X, torch.bfloat16), dev(Xp, torch.bfloat16), alpha, c,
+                              beta, beta_col=dev(bc), R=dev(R), gamma=dev(gam), out_dtype=torch.float32)
+    ref = alpha * (Amul(X) - c * X) - beta * bc * Xp + gam * R
+    assert np.abs(host(Yn) - ref).max() <= 16 * U24 * (np.abs(ref).max() + 40)
+    # FP64 path (used for the FP64-accurate residual)
+    Xd = np.random.default_rng(6).standard_normal((n, b))
+    Y64 = rr.rr_csr_spmm(d_rp, d_ci, d_va, dev(Xd), out_dtype=torch.float64)
+    assert np.abs(host(Y64) - Amul(Xd)).max() < 1e-13 * (np.abs(Xd).max() * 20)
