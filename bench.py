@@ -1,0 +1,394 @@
+#!/usr/bin/env python
+"""Benchmark: converged Ritz triplets per second at 1e-10 relative residual.
+
+Workload (one "step" = one full solve): the dense SVD of
+A = U diag(sigma) V^T, 16384 x 4096 FP64, U and V Haar (QR of seeded
+Gaussians), sigma_i = exp(-i/60); top k = 64 triplets, block 128, 4 power
+sweeps per projection, BF16 basis with FP32 accumulation, FP64 projection,
+refinement to relative residual <= 1e-10 (synthetic data, seeded).
+
+Reported: the mixed-precision solve's converged triplets/s (``value``), the
+same algorithm all-FP64 on the same GPU (``fp64``), per-stage device times
+from CUDA events inside the timed solves (``stages``) and the roofline of the
+dominant stage, an end-to-end number through host buffers (``e2e``), and the
+FP64 oracle timed on the host cores (``cpu_baseline``).
+
+``--impl reference`` times the oracle (plain FP64 numpy/LAPACK on the host
+cores) on the same workload.  N > 1 (torchrun): every rank solves its own
+instance (seed + rank), no collective on the data path ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+M, N, B, K, Q = 16384, 4096, 128, 64, 4
+TOL = 1e-10
+SEED = wl.seed_for(2)
+METRIC = "Ritz pairs/s at 1e-10 rel. residual, mixed vs all-FP64 on GB300; % of roofline"
+WORKLOAD = ("dense SVD A=U diag(exp(-i/60)) V^T 16384x4096 FP64 (Haar U, V), top 64 triplets, "
+            "block 128, 4 power sweeps per projection, BF16 basis + FP32 accumulation, FP64 "
+            "projection, refined to rel. residual <= 1e-10")
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# nominal FP64 rate of a GB300 (no measured FP64 figure exists): 1.25 TFLOP/s
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, mx, reasons = [], [], set()
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                  "sw_power_cap"), parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------- oracle legs
+def oracle_sweep_seconds(A: np.ndarray, V0: np.ndarray, reps: int = 1) -> float:
+    """Time one sweep of the oracle's solve (FP64: q products with A and A^T,
+    each followed by Algorithm 8, then Algorithm 5 and the residual check)."""
+    from oracle import ofrr as O
+
+    Amul, Atmul = O.dense_apply(A)
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        O.solve_svd(Amul, Atmul, A.shape[0], A.shape[1], K, V0, degree=Q, max_sweeps=1, tol=TOL)
+        ts.append(time.perf_counter() - t0)
+    return statistics.median(ts)
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle on the host cores, same workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import ofrr as O
+
+    A = wl.dense_svd(M, N, wl.config2_sigma(N), SEED)
+    V0 = wl.uniform_block(N, B, SEED + 1)
+    Amul, Atmul = O.dense_apply(A)
+    # one full oracle solve fixes the number of sweeps S the method needs here
+    t0 = time.perf_counter()
+    full = O.solve_svd(Amul, Atmul, M, N, K, V0, degree=Q, max_sweeps=40, tol=TOL)
+    t_full = time.perf_counter() - t0
+    S = full.sweeps
+    for _ in range(args.warmup):
+        oracle_sweep_seconds(A, V0)
+    ts = [oracle_sweep_seconds(A, V0) for _ in range(args.steps)]
+    t_sweep = statistics.median(ts)
+    value = full.n_converged / (S * t_sweep)
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_sweep * S * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+        "config": {"workload": WORKLOAD, "m": M, "n": N, "block": B, "k": K, "power_sweeps": Q},
+        "cpu_baseline": {"kind": "oracle", "value": value, "unit": "pairs/s", "cores": cores,
+                         "sample": f"each step = 1 of the {S} sweeps the oracle needs "
+                                   f"(full solve measured once: {t_full:.1f} s, "
+                                   f"{full.n_converged}/{K} converged); value = converged / "
+                                   f"(S x median sweep time)"},
+        "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------------- GPU arm
+def stage_roofline(info, peaks, src):
+    """Achieved rate of each stage from its CUDA-event time and its
+    algorithmic work per launch; the dominant stage becomes ``roofline``."""
+    ms, calls = info["stage_ms"], info["stage_calls"]
+    names = ["lowp_product", "f64_product", "hessenberg", "gram", "pencil", "lift", "other"]
+    stages = {}
+    for i, nm in enumerate(names):
+        if calls[i] == 0:
+            continue
+        stages[nm] = {"ms": ms[i], "calls": calls[i], "ms_per_call": ms[i] / calls[i]}
+    dom = max(stages, key=lambda s: stages[s]["ms"])
+    d = stages[dom]
+    avg_s = d["ms_per_call"] * 1e-3
+    hbm = peaks["hbm_gbs"]
+    if dom == "f64_product":
+        # FP64 residual products A V~ / A^T U~ with b = 128 columns: 2 m n b flops per launch
+        flops = 2.0 * M * N * B
+        ach = flops / avg_s / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_NOMINAL_TFLOPS, "traffic": None, "kernel": "k_gemm_f64",
+                "peak_source": "nominal FP64 rate (no measured FP64 peak)"}
+    elif dom == "lowp_product":
+        # A (BF16, m n 2 bytes) streamed once per launch; V/W blocks are small
+        byts = 2.0 * M * N + 2.0 * (M + N) * B * 3
+        ach = byts / avg_s / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": None, "kernel": "rr_gemm_lowp", "peak_source": src}
+    elif dom == "hessenberg":
+        # floor: read the FP32 block once, write the BF16 basis once
+        byts = (M + N) / 2 * B * (4 + 2)
+        ach = byts / avg_s / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": None, "kernel": "k_hessenberg", "peak_source": src}
+    elif dom == "gram":
+        flops = 2.0 * (M + N) / 2 * B * B
+        ach = flops / avg_s / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_NOMINAL_TFLOPS, "traffic": None, "kernel": "k_gram_partial",
+                "peak_source": "nominal FP64 rate"}
+    else:
+        roof = {"bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
+                "traffic": None, "kernel": dom}
+    roof["stage"] = dom
+    return roof, stages
+
+
+def run_ours(args):
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2505_00281_gb300 import build
+
+    build.build()
+    import paper_2505_00281_gb300 as rr
+
+    L = rr.lib()
+    dev = torch.device("cuda", local)
+    seed = SEED + 7919 * rank
+    sigma = wl.config2_sigma(N)
+    At = wl.dense_svd_torch(M, N, sigma, seed, device=str(dev))   # n x m row-major = A col-major
+    A = At.t()                                                     # (m, n), stride (1, m)
+    V0 = rr.fortran(torch.from_numpy(wl.uniform_block(N, B, seed + 1)).to(dev))
+    op = rr.api.dense_operator(A)
+    peaks, src = load_peaks()
+
+    def params(basis="bf16", profile=False):
+        if basis == "f64":
+            return rr.api.make_params(K, B, Q, 40, TOL, basis="f64", v0=V0, refine=False,
+                                      profile=profile)
+        return rr.api.make_params(K, B, Q, 30, TOL, basis=basis, v0=V0, refine=True,
+                                  phase1_sweeps=1, profile=profile)
+
+    p_mixed = params()
+    wsb = L.rr_workspace_size(rr.api.ctypes.byref(op), rr.api.ctypes.byref(p_mixed), 1)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up
+    for _ in range(args.warmup):
+        rr.rr_svd(op, p_mixed, device=dev, ws=ws)
+    # timed steps
+    clocks = ClockSampler(local)
+    launches0 = L.rr_kernel_launches()
+    barrier()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    conv = 0
+    infos = []
+    for _ in range(args.steps):
+        s, U, V, info = rr.rr_svd(op, p_mixed, device=dev, ws=ws)
+        conv += info["n_converged"]
+        infos.append(info)
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    launches = L.rr_kernel_launches() - launches0
+    t = ev0.elapsed_time(ev1) / 1e3
+    if dist:
+        tt = torch.tensor([t, conv], dtype=torch.float64, device=dev)
+        tmax = tt[:1].clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        csum = tt[1:].clone()
+        dist.all_reduce(csum, op=dist.ReduceOp.SUM)
+        t, conv = float(tmax.item()), int(csum.item())
+    value = conv / t
+
+    # correctness of the timed result against the closed form (sampled outputs)
+    s_h = s.cpu().numpy()
+    sig_err = float(np.max(np.abs(s_h - sigma[:K]) / sigma[:K]))
+
+    # stage profile (one more solve, CUDA events around every stage)
+    _, _, _, pinfo = rr.rr_svd(op, params(profile=True), device=dev, ws=ws)
+    roof, stages = stage_roofline(pinfo, peaks, src)
+
+    # all-FP64 run of the same algorithm
+    fp64 = None
+    if not args.no_fp64:
+        p64 = params("f64")
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s64, _, _, info64 = rr.rr_svd(op, p64, device=dev)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1) / 1e3
+        fp64 = {"value": info64["n_converged"] / t64, "unit": "pairs/s", "seconds": t64,
+                "n_converged": info64["n_converged"], "sweeps": info64["sweeps"],
+                "mixed_over_fp64": value / (info64["n_converged"] / t64) if info64["n_converged"] else None}
+
+    # end to end through host buffers: H2D of A and V0 from pinned memory,
+    # the solve, D2H of sigma, U, V every step
+    A_host = torch.empty((N, M), dtype=torch.float64, pin_memory=True)
+    A_host.copy_(At)
+    V0_host = torch.empty((B, N), dtype=torch.float64, pin_memory=True)
+    V0_host.copy_(V0.t())
+    A_dev2 = torch.empty_like(At)
+    V0_dev2 = torch.empty((B, N), dtype=torch.float64, device=dev)
+    op2 = rr.api.dense_operator(A_dev2.t())
+    p2 = rr.api.make_params(K, B, Q, 30, TOL, basis="bf16", v0=V0_dev2.t(), refine=True, phase1_sweeps=1)
+    s_host = torch.empty(K, dtype=torch.float64, pin_memory=True)
+    U_host = torch.empty((K, M), dtype=torch.float64, pin_memory=True)
+    V_host = torch.empty((K, N), dtype=torch.float64, pin_memory=True)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    conv2 = 0
+    for _ in range(args.steps):
+        A_dev2.copy_(A_host, non_blocking=True)
+        V0_dev2.copy_(V0_host, non_blocking=True)
+        s2, U2, V2, info2 = rr.rr_svd(op2, p2, device=dev, ws=ws)
+        s_host.copy_(s2, non_blocking=True)
+        U_host.copy_(U2.t(), non_blocking=True)
+        V_host.copy_(V2.t(), non_blocking=True)
+        conv2 += info2["n_converged"]
+    e1.record(stream)
+    barrier()
+    t2 = e0.elapsed_time(e1) / 1e3
+    if dist:
+        tt = torch.tensor([t2], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t2 = float(tt.item())
+        cc = torch.tensor([conv2], dtype=torch.float64, device=dev)
+        dist.all_reduce(cc, op=dist.ReduceOp.SUM)
+        conv2 = int(cc.item())
+    e2e = {"value": conv2 / t2, "unit": "pairs/s", "h2d_bytes_per_step": (M * N + N * B) * 8,
+           "d2h_bytes_per_step": (K + M * K + N * K) * 8}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        A_np = At.t().cpu().numpy()  # column-major view of the same matrix
+        V0_np = V0.cpu().numpy()
+        t_sweep = oracle_sweep_seconds(np.asfortranarray(A_np), V0_np)
+        S = fp64["sweeps"] if fp64 else 4
+        cpu = {"value": K / (S * t_sweep), "unit": "pairs/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"one oracle sweep (q={Q} power sweeps with Algorithm 8, Algorithm 5, FP64 "
+                         f"residuals) on the full 16384x4096 input took {t_sweep:.2f} s; value = "
+                         f"{K} / ({S} sweeps, the count the same algorithm needs in FP64 on the GPU, "
+                         f"x sweep time)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic (seeded Haar factors, prescribed spectrum)",
+            "config": {"workload": WORKLOAD, "m": M, "n": N, "block": B, "k": K, "power_sweeps": Q,
+                       "tol": TOL, "l2": "inputs larger than L2 (A: 512 MiB FP64 + 256 MiB BF16 copies)",
+                       "parallelism": f"replicas x{world}"},
+            "converged": conv, "sigma_max_rel_err": sig_err,
+            "sweeps": infos[-1]["sweeps"], "refine_sweeps": infos[-1]["refine_sweeps"],
+            "res_history": infos[-1]["res_history"],
+            "fp64": fp64, "stages": stages, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "clocks": clk, "gpu_launches": int(launches),
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -88,6 +88,7 @@ typedef struct {
   double tol;            /* relative residual target (Sec. 5.2.2)                    */
   double bounds[2];      /* Chebyshev: spectral bounds (lo, up); lo >= up -> computed */
   const double* v0;      /* n x block FP64 start block (device), e.g. U(0,1)         */
+  int32_t profile;       /* 1: time every stage with CUDA events (rr_info.stage_ms)  */
 } rr_params;
 
 typedef struct {
@@ -97,7 +98,23 @@ typedef struct {
   int32_t cols_dropped;  /* basis columns dropped by Alg. 8 / the whitening (last)   */
   double max_res;        /* largest residual among the k wanted pairs                */
   double res_history[64];/* max residual of the wanted pairs after each projection   */
+  double stage_ms[8];    /* with params.profile: device time per stage (see below)   */
+  int32_t stage_calls[8];/* number of timed calls per stage                          */
 } rr_info;
+
+/* Stages of rr_info.stage_ms: */
+enum {
+  RR_STAGE_LOWP_PRODUCT = 0, /* low-precision block products (filter, corrections)   */
+  RR_STAGE_F64_PRODUCT = 1,  /* FP64-accurate products with A (residuals)            */
+  RR_STAGE_HESSENBERG = 2,   /* Algorithm 8                                          */
+  RR_STAGE_GRAM = 3,         /* projection products G, H / B                         */
+  RR_STAGE_PENCIL = 4,       /* small FP64 pencil solve                              */
+  RR_STAGE_LIFT = 5,         /* Ritz lift                                            */
+  RR_STAGE_OTHER = 6         /* casts, scaling, residual norms, projections          */
+};
+
+/* Number of kernels this library has launched in this process so far. */
+uint64_t rr_kernel_launches(void);
 
 /* Text of the last RR_ERR_CUDA (thread-local, static storage). */
 const char* rr_last_error(void);

@@ -37,16 +37,18 @@ class RrParams(ctypes.Structure):
     _fields_ = [("k", c_i32), ("block", c_i32), ("filter", c_i32), ("degree", c_i32),
                 ("max_sweeps", c_i32), ("which", c_i32), ("basis", c_i32), ("hessenberg", c_i32),
                 ("refine", c_i32), ("phase1_sweeps", c_i32), ("tol", c_dbl),
-                ("bounds", c_dbl * 2), ("v0", c_vp)]
+                ("bounds", c_dbl * 2), ("v0", c_vp), ("profile", c_i32)]
 
 
 class RrInfo(ctypes.Structure):
     _fields_ = [("n_converged", c_i32), ("sweeps", c_i32), ("refine_sweeps", c_i32),
-                ("cols_dropped", c_i32), ("max_res", c_dbl), ("res_history", c_dbl * 64)]
+                ("cols_dropped", c_i32), ("max_res", c_dbl), ("res_history", c_dbl * 64),
+                ("stage_ms", c_dbl * 8), ("stage_calls", c_i32 * 8)]
 
 
 _SIGS = {
     "rr_last_error": (ctypes.c_char_p, []),
+    "rr_kernel_launches": (c_u64, []),
     "rr_workspace_size": (c_sz, [ctypes.POINTER(RrOperator), ctypes.POINTER(RrParams), ctypes.c_int]),
     "rr_eig": (c_i32, [ctypes.POINTER(RrOperator), ctypes.POINTER(RrParams), c_vp, c_vp, c_vp, c_sz,
                        ctypes.POINTER(RrInfo), c_vp]),

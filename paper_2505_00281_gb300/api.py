@@ -72,7 +72,8 @@ def csr_operator(row_ptr: torch.Tensor, col_idx: torch.Tensor, values: torch.Ten
 
 
 def make_params(k, block, degree, max_sweeps, tol, basis="bf16", v0=None, filter=RR.POWER,
-                which=RR.LARGEST, hessenberg=True, refine=True, phase1_sweeps=1, bounds=(0.0, 0.0)):
+                which=RR.LARGEST, hessenberg=True, refine=True, phase1_sweeps=1, bounds=(0.0, 0.0),
+                profile=False):
     p = RrParams()
     p.k, p.block, p.filter, p.degree = k, block, filter, degree
     p.max_sweeps, p.which = max_sweeps, which
@@ -81,6 +82,7 @@ def make_params(k, block, degree, max_sweeps, tol, basis="bf16", v0=None, filter
     p.tol = tol
     p.bounds[0], p.bounds[1] = bounds
     p.v0 = None if v0 is None else v0.data_ptr()
+    p.profile = int(profile)
     p._keep = (v0,)
     return p
 
@@ -89,7 +91,9 @@ def _info_dict(info: RrInfo, status: int):
     sweeps = info.sweeps
     return {"status": RR.NAMES.get(status, status), "n_converged": info.n_converged,
             "sweeps": sweeps, "refine_sweeps": info.refine_sweeps, "max_res": info.max_res,
-            "res_history": [info.res_history[i] for i in range(min(sweeps, 64))]}
+            "res_history": [info.res_history[i] for i in range(min(sweeps, 64))],
+            "stage_ms": [info.stage_ms[i] for i in range(8)],
+            "stage_calls": [info.stage_calls[i] for i in range(8)]}
 
 
 def rr_eig(op: RrOperator, params: RrParams, n: int, device="cuda", stream=None, keep=()):

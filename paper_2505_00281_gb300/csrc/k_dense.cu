@@ -2,6 +2,7 @@
 // U(0,1) start cast to the working precision), the low-precision block
 // product (Sec. 2, X_iter = A X; Fig. 4 "W = AV"), FP64 products and the
 // projection Gram products (Alg. 3 / Alg. 5).
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 
@@ -15,7 +16,11 @@ void set_last_error(const char* what, cudaError_t e) {
   snprintf(g_last_error, sizeof(g_last_error), "%s: %s", what, cudaGetErrorString(e));
 }
 
+static std::atomic<uint64_t> g_launches{0};
+void note_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
 rr_status check_launch(const char* what) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_last_error(what, e);
@@ -71,6 +76,7 @@ __global__ void k_scale_cast(int64_t rows, int64_t cols, const double* __restric
 using namespace rr;
 
 extern "C" const char* rr_last_error(void) { return g_last_error; }
+extern "C" uint64_t rr_kernel_launches(void) { return g_launches.load(); }
 
 extern "C" rr_status rr_colscale_cast(int64_t rows, int64_t cols, const double* X, int64_t ldx,
                                       int32_t dtype, void* Y, int64_t ldy, double* scale,
@@ -87,6 +93,7 @@ extern "C" rr_status rr_colscale_cast(int64_t rows, int64_t cols, const double* 
     case RR_BF16: k_scale_cast<__nv_bfloat16><<<g, 256, 0, s>>>(rows, cols, X, ldx, scale, (__nv_bfloat16*)Y, ldy); break;
     default: return RR_ERR_ARG;
   }
+  note_launches(1);
   return check_launch("rr_colscale_cast");
 }
 

@@ -253,6 +253,7 @@ static rr_status hess_launch(int64_t n, int64_t k, T* W, int64_t ldw, TO* Q, int
     return check_launch("rr_hessenberg");
   }
   RR_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kHessThreads), args, smem, s));
+  note_launches(1);
   return RR_OK;
 }
 

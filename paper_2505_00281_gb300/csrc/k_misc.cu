@@ -180,6 +180,7 @@ static rr_status scale_cast_t(cudaStream_t s, int64_t n, int64_t b, const TI* T,
     case RR_BF16: k_scale_cast2<TI, __nv_bfloat16><<<g, 256, 0, s>>>(n, b, T, ldt, mu, (__nv_bfloat16*)D, ldd); break;
     default: return RR_ERR_ARG;
   }
+  note_launches(1);
   return check_launch("scale_cast");
 }
 

@@ -339,27 +339,370 @@ __global__ void k_svd_finish(int b1, int b2, const double* __restrict__ sig_desc
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 Cholesky with column dropping (single CTA).  A column j is dropped
+// when its Schur-complement pivot is below 64 u32 times its original
+// diagonal (its new content is below ~1e-3 of its length: rounding noise for
+// a basis stored in BF16/FP32) or not positive.  Dropped indices get a unit
+// diagonal and zero row/column.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSmallThreads) k_chol_f32(int b, const double* __restrict__ G, int ldg,
+                                                            float* __restrict__ L, int* __restrict__ dropped) {
+  const int tid = threadIdx.x;
+  __shared__ int s_keep;
+  for (int e = tid; e < b * b; e += kSmallThreads) {
+    int i = e % b, j = e / b;
+    L[i + j * b] = (i >= j) ? (float)(0.5 * (G[i + j * ldg] + G[j + i * ldg])) : 0.f;
+  }
+  __syncthreads();
+  for (int j = 0; j < b; ++j) {
+    if (tid == 0) {
+      float d = L[j + j * b];
+      float g0 = (float)G[j + j * ldg];
+      s_keep = (g0 > 0.f && d > 64.f * 0x1p-24f * g0) ? 1 : 0;
+      dropped[j] = s_keep ? 0 : 1;
+      L[j + j * b] = s_keep ? sqrtf(d) : 1.f;
+    }
+    __syncthreads();
+    const float ljj = L[j + j * b];
+    if (s_keep) {
+      for (int i = j + 1 + tid; i < b; i += kSmallThreads) L[i + j * b] /= ljj;
+    } else {
+      for (int i = j + 1 + tid; i < b; i += kSmallThreads) L[i + j * b] = 0.f;
+      for (int l = tid; l < j; l += kSmallThreads) L[j + l * b] = 0.f;
+    }
+    __syncthreads();
+    if (s_keep) {
+      const int m = b - j - 1;
+      for (int e = tid; e < m * m; e += kSmallThreads) {
+        int ii = e % m, ll = e / m;
+        if (ii < ll) continue;
+        int i = j + 1 + ii, l = j + 1 + ll;
+        L[i + l * b] = fmaf(-L[i + j * b], L[l + j * b], L[i + l * b]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// W0 = (L^-1)^T in FP64 with dropped columns zeroed; L lower triangular FP32.
+// One thread per column of L^-1 (forward substitution in FP32).
+__global__ void __launch_bounds__(kSmallThreads) k_whitener0(int b, const float* __restrict__ L,
+                                                             float* __restrict__ Li,
+                                                             const int* __restrict__ dropped,
+                                                             double* __restrict__ W) {
+  for (int c = threadIdx.x; c < b; c += kSmallThreads) {
+    for (int i = 0; i < c; ++i) Li[i + c * b] = 0.f;
+    Li[c + c * b] = 1.f / L[c + c * b];
+    for (int i = c + 1; i < b; ++i) {
+      float s = 0.f;
+      for (int l = c; l < i; ++l) s = fmaf(L[i + l * b], Li[l + c * b], s);
+      Li[i + c * b] = -s / L[i + i * b];
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < b * b; e += kSmallThreads) {
+    int i = e % b, j = e / b;
+    W[i + j * b] = dropped[j] ? 0.0 : (double)Li[j + i * b];
+  }
+}
+
+// E <- E - diag(kept)  (E = W^T G W, so E becomes W^T G W - I on the kept part)
+// then F = I - E/2 (+ 3/8 E2 if given)
+__global__ void k_whiten_corr(int b, double* __restrict__ E, const double* __restrict__ E2,
+                              const int* __restrict__ dropped, double* __restrict__ F, int stage) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= b * b) return;
+  int i = e % b, j = e / b;
+  double v = E[e];
+  if (stage == 0) {
+    if (i == j && !dropped[i]) v -= 1.0;
+    E[e] = v;
+    return;
+  }
+  double f = (i == j ? 1.0 : 0.0) - 0.5 * v;
+  if (E2) f += 0.375 * E2[e];
+  F[e] = f;
+}
+
+// One-sided block Jacobi (Hestenes) on the columns of M (r x cpad):
+// M <- M V, V orthogonal (cpad x cpad, initialised to I by the launcher).
+// The cpad columns form 2P blocks of w; CTA g takes one block pair per round
+// (circle method over the blocks, 2P-1 rounds per sweep), loads its 2w
+// columns of M and V into shared memory, orthogonalises every column pair
+// among them (circle method over the 2w columns, one warp per pair), and
+// writes them back; a bounded grid barrier separates rounds.  A pair whose
+// inner product is exactly zero is never rotated, so zero columns (dropped
+// directions, padding) stay decoupled.  Converged when a sweep rotates
+// nothing (rotation counts per sweep in rot[]).
+constexpr int kBJThreads = 256;
+template <typename T>
+__global__ void __launch_bounds__(kBJThreads) k_block_jacobi(int r, int cpad, int w, T* __restrict__ M,
+                                                             int ldm, T* __restrict__ V, int ldv, T tol,
+                                                             int max_sweeps, int* __restrict__ rot,
+                                                             GridBarrier* bar, int* err,
+                                                             int* __restrict__ sweeps_out) {
+  extern __shared__ unsigned char smem_raw[];
+  T* Ms = reinterpret_cast<T*>(smem_raw);   // [2w][r]
+  T* Vs = Ms + (size_t)2 * w * r;           // [2w][cpad]
+  const int P = gridDim.x, g = blockIdx.x, nblk = 2 * P;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kBJThreads / 32;
+  const int w2 = 2 * w;
+  __shared__ int s_rot;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) s_rot = 0;
+    for (int round = 0; round < nblk - 1; ++round) {
+      const int ba = (g == 0) ? 0 : 1 + (g - 1 + round) % (nblk - 1);
+      const int bb = 1 + (nblk - 2 - g + round) % (nblk - 1);
+      // load the 2w columns
+      for (int e = tid; e < w2 * r; e += kBJThreads) {
+        int l = e / r, i = e % r;
+        int gc = (l < w ? ba * w + l : bb * w + (l - w));
+        Ms[(size_t)l * r + i] = M[i + (size_t)gc * ldm];
+      }
+      for (int e = tid; e < w2 * cpad; e += kBJThreads) {
+        int l = e / cpad, i = e % cpad;
+        int gc = (l < w ? ba * w + l : bb * w + (l - w));
+        Vs[(size_t)l * cpad + i] = V[i + (size_t)gc * ldv];
+      }
+      __syncthreads();
+      // all pairs among the 2w local columns: circle method, w pairs per sub-round
+      for (int sr = 0; sr < w2 - 1; ++sr) {
+        for (int pi = warp; pi < w; pi += nw) {
+          int a = (pi == 0) ? 0 : 1 + (pi - 1 + sr) % (w2 - 1);
+          int bq = 1 + (w2 - 2 - pi + sr) % (w2 - 1);
+          int p = a < bq ? a : bq, q = a < bq ? bq : a;
+          T* mp = Ms + (size_t)p * r;
+          T* mq = Ms + (size_t)q * r;
+          T al = T(0), be = T(0), ga = T(0);
+          for (int i = lane; i < r; i += 32) {
+            T x = mp[i], y = mq[i];
+            al = fma(x, x, al);
+            be = fma(y, y, be);
+            ga = fma(x, y, ga);
+          }
+          al = warp_sum(al);
+          be = warp_sum(be);
+          ga = warp_sum(ga);
+          if (ga == T(0) || fabs(ga) <= tol * sqrt(al * be)) continue;
+          T zeta = (be - al) / (T(2) * ga);
+          T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+          T cs = T(1) / sqrt(T(1) + t * t), sn = cs * t;
+          for (int i = lane; i < r; i += 32) {
+            T x = mp[i], y = mq[i];
+            mp[i] = cs * x - sn * y;
+            mq[i] = sn * x + cs * y;
+          }
+          T* vp = Vs + (size_t)p * cpad;
+          T* vq = Vs + (size_t)q * cpad;
+          for (int i = lane; i < cpad; i += 32) {
+            T x = vp[i], y = vq[i];
+            vp[i] = cs * x - sn * y;
+            vq[i] = sn * x + cs * y;
+          }
+          if (lane == 0) s_rot = 1;
+        }
+        __syncthreads();
+      }
+      // store back
+      for (int e = tid; e < w2 * r; e += kBJThreads) {
+        int l = e / r, i = e % r;
+        int gc = (l < w ? ba * w + l : bb * w + (l - w));
+        M[i + (size_t)gc * ldm] = Ms[(size_t)l * r + i];
+      }
+      for (int e = tid; e < w2 * cpad; e += kBJThreads) {
+        int l = e / cpad, i = e % cpad;
+        int gc = (l < w ? ba * w + l : bb * w + (l - w));
+        V[i + (size_t)gc * ldv] = Vs[(size_t)l * cpad + i];
+      }
+      if (P > 1) {
+        if (!grid_barrier(bar, P, err)) return;
+      } else {
+        __syncthreads();
+      }
+    }
+    // convergence test over the whole grid
+    if (P > 1) {
+      if (tid == 0 && s_rot) atomicAdd(&rot[sweep], 1);
+      if (!grid_barrier(bar, P, err)) return;
+      if (__ldcg(&rot[sweep]) == 0) break;
+    } else {
+      __syncthreads();
+      if (!s_rot) break;
+    }
+    __syncthreads();
+  }
+  if (g == 0 && tid == 0 && sweeps_out) *sweeps_out = sweep;
+}
+
+// identity (cpad x cpad) and copy/convert of an r x c matrix into an r x cpad
+// padded one (zero padding columns)
+template <typename TI, typename TO>
+__global__ void k_pad_copy(int r, int c, int cpad, const TI* __restrict__ A, int lda,
+                           TO* __restrict__ M, TO* __restrict__ V) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < r * cpad; e += gridDim.x * blockDim.x) {
+    int i = e % r, j = e / r;
+    M[e] = j < c ? (TO)A[i + j * lda] : TO(0);
+  }
+  if (V)
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cpad * cpad; e += gridDim.x * blockDim.x) {
+      int i = e % cpad, j = e / cpad;
+      V[e] = i == j ? TO(1) : TO(0);
+    }
+}
+
+// V64 (c x c, ld c) = V32 (top-left of cpad x cpad)
+__global__ void k_v32_to_64(int c, int cpad, const float* __restrict__ V32, double* __restrict__ V) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < c * c; e += gridDim.x * blockDim.x) {
+    int i = e % c, j = e / c;
+    V[e] = (double)V32[i + j * cpad];
+  }
+}
+
+// F = 1.5 I - 0.5 T
+__global__ void k_ns_coef(int c, const double* __restrict__ T, double* __restrict__ F) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= c * c) return;
+  int i = e % c, j = e / c;
+  F[e] = (i == j ? 1.5 : 0.0) - 0.5 * T[e];
+}
+
 struct PencilWs {
-  double *L1, *Li1, *L2, *Li2, *T, *C, *V, *sig, *mu;
-  int *drop1, *drop2, *order, *nvalid;
+  double *W1, *W2, *T, *E, *E2, *F, *C, *V, *Vp, *M, *Mp, *sig, *mu;
+  float *L32, *Li32, *M32, *V32;
+  int *drop1, *drop2, *order, *nvalid, *rot, *err, *sweeps;
+  GridBarrier* bar;
 };
+
+static int bj_cpad(int c, int* w_out, int* P_out, size_t elt, int r) {
+  int w, P;
+  if (c <= 64) {
+    w = (c + 1) / 2;
+    if (w < 1) w = 1;
+    P = 1;
+  } else {
+    w = 4;
+    size_t per_w = 2 * (size_t)(r + c + 64) * elt;
+    while (w > 1 && per_w * w > 200 * 1024) --w;
+    P = (c + 2 * w - 1) / (2 * w);
+  }
+  *w_out = w;
+  *P_out = P;
+  return 2 * P * w;
+}
 
 static bool carve_pencil(Arena& ar, int b1, int b2, PencilWs& w) {
   int bm = b1 > b2 ? b1 : b2;
-  w.L1 = ar.take<double>((size_t)b1 * b1);
-  w.Li1 = ar.take<double>((size_t)b1 * b1);
-  w.L2 = ar.take<double>((size_t)b2 * b2);
-  w.Li2 = ar.take<double>((size_t)b2 * b2);
-  w.T = ar.take<double>((size_t)bm * bm);
-  w.C = ar.take<double>((size_t)bm * bm);
-  w.V = ar.take<double>((size_t)bm * bm);
-  w.sig = ar.take<double>(bm);
+  int ww, P;
+  int cp = bj_cpad(b2 > b1 ? b2 : b1, &ww, &P, 8, bm);
+  size_t bb = (size_t)bm * bm, cc = (size_t)cp * cp, rc = (size_t)bm * cp;
+  w.W1 = ar.take<double>(bb);
+  w.W2 = ar.take<double>(bb);
+  w.T = ar.take<double>(bb);
+  w.E = ar.take<double>(bb);
+  w.E2 = ar.take<double>(bb);
+  w.F = ar.take<double>(bb);
+  w.C = ar.take<double>(bb);
+  w.V = ar.take<double>(bb);
+  w.Vp = ar.take<double>(cc);
+  w.M = ar.take<double>(rc);
+  w.Mp = ar.take<double>(rc);
+  w.sig = ar.take<double>(cp);
   w.mu = ar.take<double>(1);
-  w.drop1 = ar.take<int>(b1);
-  w.drop2 = ar.take<int>(b2);
-  w.order = ar.take<int>(bm);
+  w.L32 = ar.take<float>(bb);
+  w.Li32 = ar.take<float>(bb);
+  w.M32 = ar.take<float>(rc);
+  w.V32 = ar.take<float>(cc);
+  w.drop1 = ar.take<int>(bm);
+  w.drop2 = ar.take<int>(bm);
+  w.order = ar.take<int>(cp);
   w.nvalid = ar.take<int>(1);
+  w.rot = ar.take<int>(64);
+  w.err = ar.take<int>(1);
+  w.sweeps = ar.take<int>(2);
+  w.bar = ar.take<GridBarrier>(1);
   return !ar.overflow;
+}
+
+// Whitening matrix W (b x b) with W^T G W = I on the kept part: FP32
+// Cholesky for W0 = L^-T, then two steps of FP64 iterative refinement,
+// W <- W (I - E/2 + 3/8 E^2), E = W^T G W - I, whose error squares per step.
+static void whiten(cudaStream_t s, int b, const double* G, PencilWs& w, int* dropped, double* Wout) {
+  const int g1 = (b * b + 255) / 256;
+  k_chol_f32<<<1, kSmallThreads, 0, s>>>(b, G, b, w.L32, dropped);
+  k_whitener0<<<1, kSmallThreads, 0, s>>>(b, w.L32, w.Li32, dropped, w.W1);
+  // step 1: E = W0^T G W0 - I, F = I - E/2 + 3/8 E^2, W1 = W0 F
+  gemm_small(s, 0, 0, b, b, b, 1.0, G, b, w.W1, b, 0.0, w.T, b);
+  gemm_small(s, 1, 0, b, b, b, 1.0, w.W1, b, w.T, b, 0.0, w.E, b);
+  k_whiten_corr<<<g1, 256, 0, s>>>(b, w.E, nullptr, dropped, nullptr, 0);
+  gemm_small(s, 0, 0, b, b, b, 1.0, w.E, b, w.E, b, 0.0, w.E2, b);
+  k_whiten_corr<<<g1, 256, 0, s>>>(b, w.E, w.E2, dropped, w.F, 1);
+  gemm_small(s, 0, 0, b, b, b, 1.0, w.W1, b, w.F, b, 0.0, w.W2, b);
+  // step 2: E = W1^T G W1 - I, W = W1 (I - E/2)
+  gemm_small(s, 0, 0, b, b, b, 1.0, G, b, w.W2, b, 0.0, w.T, b);
+  gemm_small(s, 1, 0, b, b, b, 1.0, w.W2, b, w.T, b, 0.0, w.E, b);
+  k_whiten_corr<<<g1, 256, 0, s>>>(b, w.E, nullptr, dropped, nullptr, 0);
+  k_whiten_corr<<<g1, 256, 0, s>>>(b, w.E, nullptr, dropped, w.F, 1);
+  gemm_small(s, 0, 0, b, b, b, 1.0, w.W2, b, w.F, b, 0.0, Wout, b);
+  note_launches(14);
+}
+
+template <typename T>
+static rr_status launch_bj(cudaStream_t s, int r, int cpad, int w, int P, T* M, T* V, T tol,
+                           int max_sweeps, PencilWs& ws) {
+  size_t smem = (size_t)2 * w * (r + cpad) * sizeof(T);
+  const void* fn = (const void*)k_block_jacobi<T>;
+  if (smem > 48 * 1024)
+    RR_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  RR_CUDA(cudaMemsetAsync(ws.rot, 0, 64 * sizeof(int), s));
+  RR_CUDA(cudaMemsetAsync(ws.bar, 0, sizeof(GridBarrier), s));
+  int ld = r, ldv = cpad;
+  if (P == 1) {
+    k_block_jacobi<T><<<1, kBJThreads, smem, s>>>(r, cpad, w, M, ld, V, ldv, tol, max_sweeps, ws.rot,
+                                                  ws.bar, ws.err, ws.sweeps);
+    return check_launch("block_jacobi");
+  }
+  int* rot = ws.rot;
+  GridBarrier* bar = ws.bar;
+  int* err = ws.err;
+  int* sw = ws.sweeps;
+  void* args[] = {&r, &cpad, &w, &M, &ld, &V, &ldv, &tol, &max_sweeps, &rot, &bar, &err, &sw};
+  RR_CUDA(cudaLaunchCooperativeKernel(fn, dim3(P), dim3(kBJThreads), args, smem, s));
+  note_launches(1);
+  return RR_OK;
+}
+
+// SVD of the r x c matrix C (FP64, ld r): on exit Mout (r x c) = C V with
+// orthogonal columns, Vout (c x c) orthogonal.  FP32 block Jacobi to
+// convergence, FP64 orthonormalisation of its V by two Newton-Schulz steps,
+// then FP64 block Jacobi sweeps (quadratic convergence from the FP32 point).
+static rr_status jacobi_svd(cudaStream_t s, int r, int c, const double* C, PencilWs& w, double* Mout,
+                            double* Vout) {
+  int ww, P;
+  const int cpad = bj_cpad(c, &ww, &P, 8, r);
+  const int g = 256;
+  k_pad_copy<double, float><<<g, 256, 0, s>>>(r, c, cpad, C, r, w.M32, w.V32);
+  RR_TRY(launch_bj<float>(s, r, cpad, ww, P, w.M32, w.V32, 4.0f * sqrtf((float)r) * 0x1p-24f, 40, w));
+  // V = NS(V32) in FP64
+  k_v32_to_64<<<g, 256, 0, s>>>(c, cpad, w.V32, w.V);
+  for (int it = 0; it < 2; ++it) {
+    gemm_small(s, 1, 0, c, c, c, 1.0, w.V, c, w.V, c, 0.0, w.T, c);
+    k_ns_coef<<<(c * c + 255) / 256, 256, 0, s>>>(c, w.T, w.F);
+    gemm_small(s, 0, 0, c, c, c, 1.0, w.V, c, w.F, c, 0.0, w.E, c);
+    RR_CUDA(cudaMemcpyAsync(w.V, w.E, (size_t)c * c * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  // M = C V, then FP64 sweeps on it
+  gemm_small(s, 0, 0, r, c, c, 1.0, C, r, w.V, c, 0.0, w.Mp, r);
+  k_pad_copy<double, double><<<g, 256, 0, s>>>(r, c, cpad, w.Mp, r, w.M, w.Vp);
+  RR_TRY(launch_bj<double>(s, r, cpad, ww, P, w.M, w.Vp, 4.0 * sqrt((double)r) * 0x1p-53, 6, w));
+  // outputs: Mout = M (first c columns), Vout = V * Vp(1:c, 1:c)  (via E: Vout may be V)
+  gemm_small(s, 0, 0, c, c, c, 1.0, w.V, c, w.Vp, cpad, 0.0, w.E, c);
+  RR_CUDA(cudaMemcpyAsync(Vout, w.E, (size_t)c * c * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (Mout != w.M)
+    RR_CUDA(cudaMemcpyAsync(Mout, w.M, (size_t)r * c * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  note_launches(8);
+  return check_launch("jacobi_svd");
 }
 
 }  // namespace rr
@@ -393,17 +736,18 @@ extern "C" rr_status rr_pencil_eig(int64_t b, const double* H, const double* G, 
   if (!ws || !carve_pencil(ar, (int)b, (int)b, w)) return RR_ERR_WORKSPACE;
   cudaStream_t s = as_stream(stream);
   const int n = (int)b;
-  k_chol_drop<<<1, kSmallThreads, 0, s>>>(n, G, n, w.L1, w.drop1);
-  k_tri_inv_lower<<<1, kSmallThreads, 0, s>>>(n, w.L1, w.Li1);
-  // C = Li H Li^T
-  gemm_small(s, 0, 0, n, n, n, 1.0, w.Li1, n, H, n, 0.0, w.T, n);
-  gemm_small(s, 0, 1, n, n, n, 1.0, w.T, n, w.Li1, n, 0.0, w.C, n);
+  RR_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), s));
+  whiten(s, n, G, w, w.drop1, w.W1);
+  // C = W^T H W, symmetrised and shifted positive definite (C - mu I)
+  gemm_small(s, 0, 0, n, n, n, 1.0, H, n, w.W1, n, 0.0, w.T, n);
+  gemm_small(s, 1, 0, n, n, n, 1.0, w.W1, n, w.T, n, 0.0, w.C, n);
   k_eig_prep<<<1, kSmallThreads, 0, s>>>(n, w.C, w.drop1, w.mu);
-  k_jacobi1s<double><<<1, kSmallThreads, 0, s>>>(n, n, w.C, n, w.V, n, 40, 4.0 * DBL_EPSILON, nullptr);
-  k_colnorm_sort<<<1, kSmallThreads, n * sizeof(double), s>>>(n, n, w.C, n, w.sig, w.order);
+  RR_TRY(jacobi_svd(s, n, n, w.C, w, w.M, w.V));
+  k_colnorm_sort<<<1, kSmallThreads, n * sizeof(double), s>>>(n, n, w.M, n, w.sig, w.order);
   k_eig_finish<<<1, 256, 0, s>>>(n, w.sig, w.order, w.mu, w.V, theta, w.T, w.nvalid);
-  // Y = Li^T Z
-  gemm_small(s, 1, 0, n, n, n, 1.0, w.Li1, n, w.T, n, 0.0, Y, n);
+  // Y = W Z
+  gemm_small(s, 0, 0, n, n, n, 1.0, w.W1, n, w.T, n, 0.0, Y, n);
+  note_launches(5);
   RR_TRY(check_launch("rr_pencil_eig"));
   if (dropped) {
     *dropped = 0;
@@ -422,23 +766,26 @@ extern "C" rr_status rr_pencil_svd(int64_t b1, int64_t b2, const double* B, cons
   if (!ws || !carve_pencil(ar, (int)b1, (int)b2, w)) return RR_ERR_WORKSPACE;
   cudaStream_t s = as_stream(stream);
   const int n1 = (int)b1, n2 = (int)b2, r = n1 < n2 ? n1 : n2;
-  k_chol_drop<<<1, kSmallThreads, 0, s>>>(n1, Gu, n1, w.L1, w.drop1);
-  k_tri_inv_lower<<<1, kSmallThreads, 0, s>>>(n1, w.L1, w.Li1);
-  k_chol_drop<<<1, kSmallThreads, 0, s>>>(n2, Gv, n2, w.L2, w.drop2);
-  k_tri_inv_lower<<<1, kSmallThreads, 0, s>>>(n2, w.L2, w.Li2);
-  // C = Lu^-1 B Lv^-T  (b1 x b2)
-  gemm_small(s, 0, 0, n1, n2, n1, 1.0, w.Li1, n1, B, n1, 0.0, w.T, n1);
-  gemm_small(s, 0, 1, n1, n2, n2, 1.0, w.T, n1, w.Li2, n2, 0.0, w.C, n1);
-  k_zero_dropped<<<(n1 * n2 + 255) / 256, 256, 0, s>>>(n1, n2, w.C, w.drop1, w.drop2);
-  k_jacobi1s<double><<<1, kSmallThreads, 0, s>>>(n1, n2, w.C, n1, w.V, n2, 40, 4.0 * DBL_EPSILON, nullptr);
-  k_colnorm_sort<<<1, kSmallThreads, n2 * sizeof(double), s>>>(n1, n2, w.C, n1, w.sig, w.order);
-  // whitened singular vectors (Uw in T, Vw in L1-sized scratch reuse: use Li? no: dedicated)
+  RR_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), s));
+  // whitening of both sides: Wu -> C, Wv -> V (whiten() uses W1/W2/T/E/E2/F as scratch)
+  whiten(s, n1, Gu, w, w.drop1, w.C);
+  whiten(s, n2, Gv, w, w.drop2, w.V);
+  // Cw = Wu^T B Wv  (b1 x b2)  -> Mp
+  gemm_small(s, 0, 0, n1, n2, n2, 1.0, B, n1, w.V, n2, 0.0, w.T, n1);
+  gemm_small(s, 1, 0, n1, n2, n1, 1.0, w.C, n1, w.T, n1, 0.0, w.E2, n1);
+  k_zero_dropped<<<(n1 * n2 + 255) / 256, 256, 0, s>>>(n1, n2, w.E2, w.drop1, w.drop2);
+  // keep Wu, Wv: copy them out of C / V (jacobi_svd uses C/V... it uses V, M, Mp, Vp, T, E, F)
+  RR_CUDA(cudaMemcpyAsync(w.W1, w.C, (size_t)n1 * n1 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  RR_CUDA(cudaMemcpyAsync(w.W2, w.V, (size_t)n2 * n2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  RR_TRY(jacobi_svd(s, n1, n2, w.E2, w, w.M, w.V));   // M = Cw V (b1 x b2), V (b2 x b2)
+  k_colnorm_sort<<<1, kSmallThreads, n2 * sizeof(double), s>>>(n1, n2, w.M, n1, w.sig, w.order);
   double* Uw = w.T;   // b1 x r
-  double* Vw = w.L2;  // b2 x r (L2 no longer needed)
-  k_svd_finish<<<64, 256, 0, s>>>(n1, n2, w.sig, w.order, w.C, w.V, sv, Uw, Vw, r);
-  // Y = Lu^-T Uw, Z = Lv^-T Vw
-  gemm_small(s, 1, 0, n1, r, n1, 1.0, w.Li1, n1, Uw, n1, 0.0, Y, n1);
-  gemm_small(s, 1, 0, n2, r, n2, 1.0, w.Li2, n2, Vw, n2, 0.0, Z, n2);
+  double* Vw = w.E;   // b2 x r
+  k_svd_finish<<<64, 256, 0, s>>>(n1, n2, w.sig, w.order, w.M, w.V, sv, Uw, Vw, r);
+  // Y = Wu Uw, Z = Wv Vw
+  gemm_small(s, 0, 0, n1, r, n1, 1.0, w.W1, n1, Uw, n1, 0.0, Y, n1);
+  gemm_small(s, 0, 0, n2, r, n2, 1.0, w.W2, n2, Vw, n2, 0.0, Z, n2);
+  note_launches(7);
   RR_TRY(check_launch("rr_pencil_svd"));
   if (dropped) {
     *dropped = 0;

@@ -134,6 +134,7 @@ rr_status csr_gershgorin(cudaStream_t s, int64_t n, const int32_t* rp, const int
   // scratch: 2*256 partials followed by the 2 outputs
   k_gersh_partial<<<256, 256, 0, s>>>(n, rp, ci, va, scratch);
   k_gersh_final<<<1, 32, 0, s>>>(256, scratch, scratch + 512);
+  note_launches(1);
   return check_launch("csr_gershgorin");
 }
 

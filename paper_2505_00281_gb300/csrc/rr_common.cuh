@@ -13,7 +13,8 @@ namespace rr {
 // host-side status plumbing
 // ---------------------------------------------------------------------------
 void set_last_error(const char* what, cudaError_t e);
-rr_status check_launch(const char* what);
+rr_status check_launch(const char* what);  // counts one launch
+void note_launches(int n);                  // counts n further launches
 
 #define RR_TRY(expr)                                   \
   do {                                                 \

@@ -40,6 +40,65 @@ struct Op {
 
 static size_t dsz(int32_t t) { return dtype_size(t); }
 
+// Per-stage device timing with CUDA events on the solver's stream (enabled by
+// rr_params.profile; read once, after the solve's final synchronisation).
+struct Prof {
+  bool on = false;
+  cudaStream_t s = nullptr;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  std::vector<std::pair<int, size_t>> recs;  // (stage, index of the start event)
+  cudaEvent_t get() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+  void finish(rr_info* inf) {
+    if (on && inf) {
+      cudaStreamSynchronize(s);
+      for (auto& r : recs) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, pool[r.second], pool[r.second + 1]) == cudaSuccess) {
+          inf->stage_ms[r.first] += ms;
+          inf->stage_calls[r.first] += 1;
+        }
+      }
+    }
+    for (auto e : pool) cudaEventDestroy(e);
+    pool.clear();
+    recs.clear();
+    used = 0;
+  }
+  ~Prof() { finish(nullptr); }
+};
+
+struct StageScope {
+  Prof* p;
+  int st;
+  size_t i0;
+  StageScope(Prof* p_, int st_) : p(p_), st(st_), i0(0) {
+    if (p->on) {
+      i0 = p->used;
+      cudaEventRecord(p->get(), p->s);
+    }
+  }
+  ~StageScope() {
+    if (p->on) {
+      cudaEventRecord(p->get(), p->s);
+      p->recs.push_back({st, i0});
+    }
+  }
+};
+
+#define STAGE(st, expr)              \
+  do {                               \
+    StageScope _sc(&prof, (st));     \
+    RR_TRY(expr);                    \
+  } while (0)
+
 // ---------------------------------------------------------------------------
 // products
 // ---------------------------------------------------------------------------
@@ -263,21 +322,24 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
   carve_svd(ar, op, b, refine, w);
   double* v0buf = batch_mode ? ar.take<double>(n * b) : nullptr;
   if (ar.overflow) return RR_ERR_WORKSPACE;
+  Prof prof;
+  prof.on = p->profile != 0 && !batch_mode;
+  prof.s = s;
   w.c.hess_grid = hess_grid;
   RR_CUDA(cudaMemsetAsync(w.c.hess_ws, 0, 512, s));
   const size_t ds = dsz(dt);
   (void)ds;
 
   // one-time operator casts (counted in the solve time)
-  if (op.lo_col) RR_TRY(rr_cast_operator(m, n, op.A, op.lda, dt, op.lo_col, op.lo_row, s));
+  if (op.lo_col) STAGE(RR_STAGE_OTHER, rr_cast_operator(m, n, op.A, op.lda, dt, op.lo_col, op.lo_row, s));
 
   // a1: start block
   const double* v0 = p->v0;
   if (batch_mode) {
-    RR_TRY(uniform_block(s, n, b, seed, v0buf, n));
+    STAGE(RR_STAGE_OTHER, uniform_block(s, n, b, seed, v0buf, n));
     v0 = v0buf;
   }
-  RR_TRY(rr_colscale_cast(n, b, v0, n, dt, w.Vlo, n, w.c.scale, s));
+  STAGE(RR_STAGE_OTHER, rr_colscale_cast(n, b, v0, n, dt, w.Vlo, n, w.c.scale, s));
 
   rr_info inf;
   memset(&inf, 0, sizeof(inf));
@@ -287,27 +349,27 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
 
   // ---------------- phase 1: the paper's method ----------------
   for (int ps = 0; ps < ph1 && sweep < p->max_sweeps; ++ps) {
-    if (ps > 0) RR_TRY(rr_colscale_cast(n, b, w.Vt, n, dt, w.Vlo, n, w.c.scale, s));
+    if (ps > 0) STAGE(RR_STAGE_OTHER, rr_colscale_cast(n, b, w.Vt, n, dt, w.Vlo, n, w.c.scale, s));
     for (int it = 0; it < q; ++it) {
-      RR_TRY(apply_lowp(op, b, w.Vlo, n, w.W, m, nullptr, 0, nullptr, s));        // W = A V
-      RR_TRY(basis_step(w.c, hess, op.wt, dt, m, b, w.W, m, w.Ulo, m, s));          // U = basis(W)
-      RR_TRY(apply_lowp_T(op, b, w.Ulo, m, w.W, n, nullptr, 0, nullptr, s));       // Z = A^T U
-      RR_TRY(basis_step(w.c, hess, op.wt, dt, n, b, w.W, n, w.Vlo, n, s));          // V = basis(Z)
+      STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp(op, b, w.Vlo, n, w.W, m, nullptr, 0, nullptr, s));        // W = A V
+      STAGE(RR_STAGE_HESSENBERG, basis_step(w.c, hess, op.wt, dt, m, b, w.W, m, w.Ulo, m, s));          // U = basis(W)
+      STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp_T(op, b, w.Ulo, m, w.W, n, nullptr, 0, nullptr, s));       // Z = A^T U
+      STAGE(RR_STAGE_HESSENBERG, basis_step(w.c, hess, op.wt, dt, n, b, w.W, n, w.Vlo, n, s));          // V = basis(Z)
     }
     // Algorithm 5: B = U^T (A V), Gu = U^T U, Gv = V^T V (FP64 accumulation)
-    RR_TRY(apply_lowp(op, b, w.Vlo, n, w.Pw, m, nullptr, 0, nullptr, s));
-    RR_TRY(gram(w.c, m, b, b, dt, w.Ulo, m, dt, w.Ulo, m, w.Gu, b, s));
-    RR_TRY(gram(w.c, n, b, b, dt, w.Vlo, n, dt, w.Vlo, n, w.Gv, b, s));
-    RR_TRY(gram(w.c, m, b, b, dt, w.Ulo, m, op.wt, w.Pw, m, w.Bm, b, s));
-    RR_TRY(rr_pencil_svd(b, b, w.Bm, w.Gu, w.Gv, w.sig2, w.Ys, w.Zs, w.c.pen_ws, w.c.pen_bytes,
+    STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp(op, b, w.Vlo, n, w.Pw, m, nullptr, 0, nullptr, s));
+    STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, dt, w.Ulo, m, dt, w.Ulo, m, w.Gu, b, s));
+    STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, dt, w.Vlo, n, dt, w.Vlo, n, w.Gv, b, s));
+    STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, dt, w.Ulo, m, op.wt, w.Pw, m, w.Bm, b, s));
+    STAGE(RR_STAGE_PENCIL, rr_pencil_svd(b, b, w.Bm, w.Gu, w.Gv, w.sig2, w.Ys, w.Zs, w.c.pen_ws, w.c.pen_bytes,
                          nullptr, s));
-    RR_TRY(lift(s, dt, m, b, b, w.Ulo, m, w.Ys, b, w.Ut, m, 0));
-    RR_TRY(lift(s, dt, n, b, b, w.Vlo, n, w.Zs, b, w.Vt, n, 0));
+    STAGE(RR_STAGE_LIFT, lift(s, dt, m, b, b, w.Ulo, m, w.Ys, b, w.Ut, m, 0));
+    STAGE(RR_STAGE_LIFT, lift(s, dt, n, b, b, w.Vlo, n, w.Zs, b, w.Vt, n, 0));
     RR_CUDA(cudaMemcpyAsync(w.sig, w.sig2, b * sizeof(double), cudaMemcpyDeviceToDevice, s));
     ++sweep;
     if (!refine && !batch_mode) {
       // plain method: FP64 residual check of the wanted triplets every sweep
-      RR_TRY(svd_residual(op, w, k, w.Rv ? w.Rv : w.P, w.Ru ? w.Ru : w.Qm, s));
+      STAGE(RR_STAGE_F64_PRODUCT, svd_residual(op, w, k, w.Rv ? w.Rv : w.P, w.Ru ? w.Ru : w.Qm, s));
       RR_CUDA(cudaMemcpyAsync(hres.data(), w.res, k * sizeof(double), cudaMemcpyDeviceToHost, s));
       RR_CUDA(cudaStreamSynchronize(s));
       RR_TRY(read_err(w.c, s));
@@ -327,11 +389,11 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
     const int64_t b2 = 2 * b;
     for (;;) {
       // residual of all b Ritz triplets, FP64-accurate
-      RR_TRY(apply_f64(op, b, w.Vt, n, w.P, m, s));      // P = A V~
-      RR_TRY(apply_f64_T(op, b, w.Ut, m, w.Qm, n, s));   // Q = A^T U~
-      RR_TRY(residual_block(s, m, b, w.P, m, w.Ut, m, w.sig, w.Rv, m, w.ss, 0));
-      RR_TRY(residual_block(s, n, b, w.Qm, n, w.Vt, n, w.sig, w.Ru, n, w.ss, 1));
-      RR_TRY(res_finish(s, b, w.ss, w.sig, w.res));
+      STAGE(RR_STAGE_F64_PRODUCT, apply_f64(op, b, w.Vt, n, w.P, m, s));      // P = A V~
+      STAGE(RR_STAGE_F64_PRODUCT, apply_f64_T(op, b, w.Ut, m, w.Qm, n, s));   // Q = A^T U~
+      STAGE(RR_STAGE_OTHER, residual_block(s, m, b, w.P, m, w.Ut, m, w.sig, w.Rv, m, w.ss, 0));
+      STAGE(RR_STAGE_OTHER, residual_block(s, n, b, w.Qm, n, w.Vt, n, w.sig, w.Ru, n, w.ss, 1));
+      STAGE(RR_STAGE_OTHER, res_finish(s, b, w.ss, w.sig, w.res));
       if (!batch_mode) {
         RR_CUDA(cudaMemcpyAsync(hres.data(), w.res, k * sizeof(double), cudaMemcpyDeviceToHost, s));
         RR_CUDA(cudaStreamSynchronize(s));
@@ -350,42 +412,42 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
       //   E_1 = R_v;  F_j = A^T E_j + R_u S^(2j-1);  E_{j+1} = A F_j + R_v S^(2j)
       // each block kept at unit column inf-norm, the injection coefficient
       // tracked per column (coef <- coef * sigma / mu after each scaling).
-      RR_TRY(fill(s, b, 1.0, w.coef));
-      RR_TRY(scale_cast(s, RR_F64, m, b, w.Rv, m, w.mu, dt, w.Elo, m, w.coef, w.sig));
+      STAGE(RR_STAGE_OTHER, fill(s, b, 1.0, w.coef));
+      STAGE(RR_STAGE_OTHER, scale_cast(s, RR_F64, m, b, w.Rv, m, w.mu, dt, w.Elo, m, w.coef, w.sig));
       for (int j = 0; j < q; ++j) {
-        RR_TRY(apply_lowp_T(op, b, w.Elo, m, w.W, n, w.Ru, n, w.coef, s));
-        RR_TRY(project_out(w.c, s, n, b, w.Vt, n, (float*)w.W, n, w.Ys));
-        RR_TRY(scale_cast(s, op.wt, n, b, w.W, n, w.mu, dt, w.Flo, n, w.coef, w.sig));
-        RR_TRY(apply_lowp(op, b, w.Flo, n, w.AF, m, w.Rv, m, w.coef, s));
-        RR_TRY(project_out(w.c, s, m, b, w.Ut, m, (float*)w.AF, m, w.Ys));
-        if (j + 1 < q) RR_TRY(scale_cast(s, op.wt, m, b, w.AF, m, w.mu, dt, w.Elo, m, w.coef, w.sig));
+        STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp_T(op, b, w.Elo, m, w.W, n, w.Ru, n, w.coef, s));
+        STAGE(RR_STAGE_GRAM, project_out(w.c, s, n, b, w.Vt, n, (float*)w.W, n, w.Ys));
+        STAGE(RR_STAGE_OTHER, scale_cast(s, op.wt, n, b, w.W, n, w.mu, dt, w.Flo, n, w.coef, w.sig));
+        STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp(op, b, w.Flo, n, w.AF, m, w.Rv, m, w.coef, s));
+        STAGE(RR_STAGE_GRAM, project_out(w.c, s, m, b, w.Ut, m, (float*)w.AF, m, w.Ys));
+        if (j + 1 < q) STAGE(RR_STAGE_OTHER, scale_cast(s, op.wt, m, b, w.AF, m, w.mu, dt, w.Elo, m, w.coef, w.sig));
       }
       // conditioning of the correction blocks (Algorithm 8), then A F for the
       // low-precision block of the projected matrix
-      RR_TRY(basis_step(w.c, hess, op.wt, dt, m, b, w.AF, m, w.Elo, m, s));
-      RR_TRY(basis_step(w.c, hess, op.wt, dt, n, b, w.W, n, w.Flo, n, s));
-      RR_TRY(apply_lowp(op, b, w.Flo, n, w.AF, m, nullptr, 0, nullptr, s));
+      STAGE(RR_STAGE_HESSENBERG, basis_step(w.c, hess, op.wt, dt, m, b, w.AF, m, w.Elo, m, s));
+      STAGE(RR_STAGE_HESSENBERG, basis_step(w.c, hess, op.wt, dt, n, b, w.W, n, w.Flo, n, s));
+      STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp(op, b, w.Flo, n, w.AF, m, nullptr, 0, nullptr, s));
       // projected blocks over S_u = [U~, E], S_v = [V~, F]  (ld 2b)
       double* B = w.Bm;
-      RR_TRY(gram(w.c, m, b, b, RR_F64, w.Ut, m, RR_F64, w.P, m, B, b2, s));                   // U~^T A V~
-      RR_TRY(gram(w.c, n, b, b, RR_F64, w.Qm, n, dt, w.Flo, n, B + b * b2, b2, s));          // U~^T A F
-      RR_TRY(gram(w.c, m, b, b, dt, w.Elo, m, RR_F64, w.P, m, B + b, b2, s));                // E^T A V~
-      RR_TRY(gram(w.c, m, b, b, dt, w.Elo, m, op.wt, w.AF, m, B + b + b * b2, b2, s));       // E^T A F
-      RR_TRY(gram(w.c, m, b, b, RR_F64, w.Ut, m, RR_F64, w.Ut, m, w.Gu, b2, s));
-      RR_TRY(gram(w.c, m, b, b, RR_F64, w.Ut, m, dt, w.Elo, m, w.Gu + b * b2, b2, s));
-      RR_TRY(transpose(s, b, b, w.Gu + b * b2, b2, w.Gu + b, b2));
-      RR_TRY(gram(w.c, m, b, b, dt, w.Elo, m, dt, w.Elo, m, w.Gu + b + b * b2, b2, s));
-      RR_TRY(gram(w.c, n, b, b, RR_F64, w.Vt, n, RR_F64, w.Vt, n, w.Gv, b2, s));
-      RR_TRY(gram(w.c, n, b, b, RR_F64, w.Vt, n, dt, w.Flo, n, w.Gv + b * b2, b2, s));
-      RR_TRY(transpose(s, b, b, w.Gv + b * b2, b2, w.Gv + b, b2));
-      RR_TRY(gram(w.c, n, b, b, dt, w.Flo, n, dt, w.Flo, n, w.Gv + b + b * b2, b2, s));
-      RR_TRY(rr_pencil_svd(b2, b2, B, w.Gu, w.Gv, w.sig2, w.Ys, w.Zs, w.c.pen_ws, w.c.pen_bytes,
+      STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, RR_F64, w.Ut, m, RR_F64, w.P, m, B, b2, s));                   // U~^T A V~
+      STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, RR_F64, w.Qm, n, dt, w.Flo, n, B + b * b2, b2, s));          // U~^T A F
+      STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, dt, w.Elo, m, RR_F64, w.P, m, B + b, b2, s));                // E^T A V~
+      STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, dt, w.Elo, m, op.wt, w.AF, m, B + b + b * b2, b2, s));       // E^T A F
+      STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, RR_F64, w.Ut, m, RR_F64, w.Ut, m, w.Gu, b2, s));
+      STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, RR_F64, w.Ut, m, dt, w.Elo, m, w.Gu + b * b2, b2, s));
+      STAGE(RR_STAGE_OTHER, transpose(s, b, b, w.Gu + b * b2, b2, w.Gu + b, b2));
+      STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, dt, w.Elo, m, dt, w.Elo, m, w.Gu + b + b * b2, b2, s));
+      STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, RR_F64, w.Vt, n, RR_F64, w.Vt, n, w.Gv, b2, s));
+      STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, RR_F64, w.Vt, n, dt, w.Flo, n, w.Gv + b * b2, b2, s));
+      STAGE(RR_STAGE_OTHER, transpose(s, b, b, w.Gv + b * b2, b2, w.Gv + b, b2));
+      STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, dt, w.Flo, n, dt, w.Flo, n, w.Gv + b + b * b2, b2, s));
+      STAGE(RR_STAGE_PENCIL, rr_pencil_svd(b2, b2, B, w.Gu, w.Gv, w.sig2, w.Ys, w.Zs, w.c.pen_ws, w.c.pen_bytes,
                            nullptr, s));
       // lift the leading b triplets
-      RR_TRY(lift(s, RR_F64, m, b, b, w.Ut, m, w.Ys, b2, w.Ut2, m, 0));
-      RR_TRY(lift(s, dt, m, b, b, w.Elo, m, w.Ys + b, b2, w.Ut2, m, 1));
-      RR_TRY(lift(s, RR_F64, n, b, b, w.Vt, n, w.Zs, b2, w.Vt2, n, 0));
-      RR_TRY(lift(s, dt, n, b, b, w.Flo, n, w.Zs + b, b2, w.Vt2, n, 1));
+      STAGE(RR_STAGE_LIFT, lift(s, RR_F64, m, b, b, w.Ut, m, w.Ys, b2, w.Ut2, m, 0));
+      STAGE(RR_STAGE_LIFT, lift(s, dt, m, b, b, w.Elo, m, w.Ys + b, b2, w.Ut2, m, 1));
+      STAGE(RR_STAGE_LIFT, lift(s, RR_F64, n, b, b, w.Vt, n, w.Zs, b2, w.Vt2, n, 0));
+      STAGE(RR_STAGE_LIFT, lift(s, dt, n, b, b, w.Flo, n, w.Zs + b, b2, w.Vt2, n, 1));
       std::swap(w.Ut, w.Ut2);
       std::swap(w.Vt, w.Vt2);
       RR_CUDA(cudaMemcpyAsync(w.sig, w.sig2, b * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -395,7 +457,7 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
   }
   if (batch_mode && !refine) {
     // final residual for the caller's convergence count (read after the graph)
-    RR_TRY(svd_residual(op, w, k, w.P, w.Qm, s));
+    STAGE(RR_STAGE_F64_PRODUCT, svd_residual(op, w, k, w.P, w.Qm, s));
   }
 
   // outputs: sigma, U, V (first k), unit columns, sign fixed on V
@@ -404,10 +466,14 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
                             cudaMemcpyDeviceToDevice, s));
   RR_CUDA(cudaMemcpy2DAsync(V_out, n * sizeof(double), w.Vt, n * sizeof(double), n * sizeof(double), k,
                             cudaMemcpyDeviceToDevice, s));
-  RR_TRY(normalize_sign(s, n, k, V_out, n, m, U_out, m));
+  STAGE(RR_STAGE_OTHER, normalize_sign(s, n, k, V_out, n, m, U_out, m));
   inf.sweeps = sweep;
+  if (batch_mode) {
+    if (info) *info = inf;
+    return RR_OK;
+  }
+  prof.finish(&inf);
   if (info) *info = inf;
-  if (batch_mode) return RR_OK;
   RR_CUDA(cudaStreamSynchronize(s));
   RR_TRY(read_err(w.c, s));
   return converged ? RR_OK : RR_ERR_NO_CONV;
@@ -527,12 +593,15 @@ static rr_status eig_run(const rr_operator* Aop, const rr_params* p, double* the
   EigBufs w;
   carve_eig(ar, op, b, refine, w);
   if (ar.overflow) return RR_ERR_WORKSPACE;
+  Prof prof;
+  prof.on = p->profile != 0;
+  prof.s = s;
   RR_CUDA(cudaMemsetAsync(w.c.hess_ws, 0, 512, s));
-  if (op.lo_col) RR_TRY(rr_cast_operator(n, n, op.A, op.lda, dt, op.lo_col, nullptr, s));
+  if (op.lo_col) STAGE(RR_STAGE_OTHER, rr_cast_operator(n, n, op.A, op.lda, dt, op.lo_col, nullptr, s));
 
   double lo = p->bounds[0], up = p->bounds[1];
   if (cheb && !(lo < up)) {
-    RR_TRY(csr_gershgorin(s, n, op.rp, op.ci, op.va, w.gersh));
+    STAGE(RR_STAGE_OTHER, csr_gershgorin(s, n, op.rp, op.ci, op.va, w.gersh));
     double h2[2];
     RR_CUDA(cudaMemcpyAsync(h2, w.gersh + 512, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     RR_CUDA(cudaStreamSynchronize(s));
@@ -541,7 +610,7 @@ static rr_status eig_run(const rr_operator* Aop, const rr_params* p, double* the
   }
   double ca = lo + 0.1 * (up - lo), ca0 = lo;  // Chebyshev cut and scaling point
 
-  RR_TRY(rr_colscale_cast(n, b, p->v0, n, dt, w.Vlo, n, w.c.scale, s));
+  STAGE(RR_STAGE_OTHER, rr_colscale_cast(n, b, p->v0, n, dt, w.Vlo, n, w.c.scale, s));
   rr_info inf;
   memset(&inf, 0, sizeof(inf));
   std::vector<double> hres(b), hth(b);
@@ -567,31 +636,31 @@ static rr_status eig_run(const rr_operator* Aop, const rr_params* p, double* the
 
   // ---------------- phase 1 ----------------
   for (int ps = 0; ps < ph1 && sweep < p->max_sweeps; ++ps) {
-    if (ps > 0) RR_TRY(rr_colscale_cast(n, b, w.X, n, dt, w.Vlo, n, w.c.scale, s));
+    if (ps > 0) STAGE(RR_STAGE_OTHER, rr_colscale_cast(n, b, w.X, n, dt, w.Vlo, n, w.c.scale, s));
     if (cheb) {
-      RR_TRY(cheb_filter(op, w, b, q, ca, up, ca0, s));
-      RR_TRY(basis_step(w.c, hess, op.wt, dt, n, b, w.W, n, w.Vlo, n, s));
+      STAGE(RR_STAGE_LOWP_PRODUCT, cheb_filter(op, w, b, q, ca, up, ca0, s));
+      STAGE(RR_STAGE_HESSENBERG, basis_step(w.c, hess, op.wt, dt, n, b, w.W, n, w.Vlo, n, s));
     } else {
       for (int it = 0; it < q; ++it) {
-        RR_TRY(apply_lowp(op, b, w.Vlo, n, w.W, n, nullptr, 0, nullptr, s));
-        RR_TRY(basis_step(w.c, hess, op.wt, dt, n, b, w.W, n, w.Vlo, n, s));
+        STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp(op, b, w.Vlo, n, w.W, n, nullptr, 0, nullptr, s));
+        STAGE(RR_STAGE_HESSENBERG, basis_step(w.c, hess, op.wt, dt, n, b, w.W, n, w.Vlo, n, s));
       }
     }
     // Algorithm 3: H = V^T (A V), G = V^T V, H Y = G Y Theta, X = V Y
-    RR_TRY(apply_lowp(op, b, w.Vlo, n, w.Pw, n, nullptr, 0, nullptr, s));
-    RR_TRY(gram(w.c, n, b, b, dt, w.Vlo, n, dt, w.Vlo, n, w.G, b, s));
-    RR_TRY(gram(w.c, n, b, b, dt, w.Vlo, n, op.wt, w.Pw, n, w.H, b, s));
-    RR_TRY(rr_pencil_eig(b, w.H, w.G, w.th2, w.Y, w.c.pen_ws, w.c.pen_bytes, nullptr, s));
-    RR_TRY(select_eig(s, b, b, p->which, w.th2, w.Y, b, w.theta, w.Ysel, b));
-    RR_TRY(lift(s, dt, n, b, b, w.Vlo, n, w.Ysel, b, w.X, n, 0));
+    STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp(op, b, w.Vlo, n, w.Pw, n, nullptr, 0, nullptr, s));
+    STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, dt, w.Vlo, n, dt, w.Vlo, n, w.G, b, s));
+    STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, dt, w.Vlo, n, op.wt, w.Pw, n, w.H, b, s));
+    STAGE(RR_STAGE_PENCIL, rr_pencil_eig(b, w.H, w.G, w.th2, w.Y, w.c.pen_ws, w.c.pen_bytes, nullptr, s));
+    STAGE(RR_STAGE_PENCIL, select_eig(s, b, b, p->which, w.th2, w.Y, b, w.theta, w.Ysel, b));
+    STAGE(RR_STAGE_LIFT, lift(s, dt, n, b, b, w.Vlo, n, w.Ysel, b, w.X, n, 0));
     ++sweep;
-    RR_TRY(update_bounds());
+    STAGE(RR_STAGE_OTHER, update_bounds());
     if (!refine) {
       // FP64 residual of the wanted pairs.  With an FP64 basis A X = (A V) Y exactly.
-      if (dt == RR_F64) RR_TRY(lift(s, RR_F64, n, k, b, w.Pw, n, w.Ysel, b, w.P, n, 0));
+      if (dt == RR_F64) STAGE(RR_STAGE_LIFT, lift(s, RR_F64, n, k, b, w.Pw, n, w.Ysel, b, w.P, n, 0));
       else RR_TRY(apply_f64(op, k, w.X, n, w.P, n, s));
-      RR_TRY(residual_block(s, n, k, w.P, n, w.X, n, w.theta, w.R, n, w.ss, 0));
-      RR_TRY(res_finish(s, k, w.ss, w.theta, w.res));
+      STAGE(RR_STAGE_OTHER, residual_block(s, n, k, w.P, n, w.X, n, w.theta, w.R, n, w.ss, 0));
+      STAGE(RR_STAGE_OTHER, res_finish(s, k, w.ss, w.theta, w.res));
       RR_CUDA(cudaMemcpyAsync(hres.data(), w.res, k * sizeof(double), cudaMemcpyDeviceToHost, s));
       RR_CUDA(cudaStreamSynchronize(s));
       RR_TRY(read_err(w.c, s));
@@ -610,9 +679,9 @@ static rr_status eig_run(const rr_operator* Aop, const rr_params* p, double* the
   if (refine) {
     const int64_t b2 = 2 * b;
     for (;;) {
-      RR_TRY(apply_f64(op, b, w.X, n, w.P, n, s));  // P = A X, FP64-accurate
-      RR_TRY(residual_block(s, n, b, w.P, n, w.X, n, w.theta, w.R, n, w.ss, 0));
-      RR_TRY(res_finish(s, b, w.ss, w.theta, w.res));
+      STAGE(RR_STAGE_F64_PRODUCT, apply_f64(op, b, w.X, n, w.P, n, s));  // P = A X, FP64-accurate
+      STAGE(RR_STAGE_OTHER, residual_block(s, n, b, w.P, n, w.X, n, w.theta, w.R, n, w.ss, 0));
+      STAGE(RR_STAGE_OTHER, res_finish(s, b, w.ss, w.theta, w.res));
       RR_CUDA(cudaMemcpyAsync(hres.data(), w.res, k * sizeof(double), cudaMemcpyDeviceToHost, s));
       RR_CUDA(cudaStreamSynchronize(s));
       RR_TRY(read_err(w.c, s));
@@ -630,15 +699,15 @@ static rr_status eig_run(const rr_operator* Aop, const rr_params* p, double* the
         //                           + (2 s_{j+1}/e) phi_j(theta) R
         // with D_j = s_j * Dhat_j, kappa_j = phi_j / s_j, rho_j = s_{j-1} / s_j.
         const double e = (up - ca) / 2, c = (up + ca) / 2, s1 = e / (ca0 - c);
-        RR_TRY(scale_cast(s, RR_F64, n, b, w.R, n, w.mu, dt, w.Vlo, n, nullptr, nullptr));
+        STAGE(RR_STAGE_OTHER, scale_cast(s, RR_F64, n, b, w.R, n, w.mu, dt, w.Vlo, n, nullptr, nullptr));
         // kappa_1 = (theta - c)/mu_1 ; kappa_0 rho_1 = e/(s1 mu_1)  (phi_0 / s_1)
         // computed by the coefficient kernel from kappa=1/(mu s1/e) seeds:
-        RR_TRY(fill(s, b, 0.0, w.kap));
-        RR_TRY(fill(s, b, 0.0, w.kap_prev));
-        RR_TRY(fill(s, b, 1.0, w.rho));
+        STAGE(RR_STAGE_OTHER, fill(s, b, 0.0, w.kap));
+        STAGE(RR_STAGE_OTHER, fill(s, b, 0.0, w.kap_prev));
+        STAGE(RR_STAGE_OTHER, fill(s, b, 1.0, w.rho));
         // kap <- ((s1/e)(theta - c)*1 - 0)/((s1/e) mu) : an = 1, bn = 0 with kap = 1, then divide
-        RR_TRY(fill(s, b, e / s1, w.kap));
-        RR_TRY(cheb_coef_update(s, b, w.theta, w.mu, s1 / e, c, 0.0, w.kap, w.kap_prev, w.rho));
+        STAGE(RR_STAGE_OTHER, fill(s, b, e / s1, w.kap));
+        STAGE(RR_STAGE_OTHER, cheb_coef_update(s, b, w.theta, w.mu, s1 / e, c, 0.0, w.kap, w.kap_prev, w.rho));
         // now kap = (theta - c)/mu_1, kap_prev = e/s1, rho = 1/mu_1 -> kap_prev*rho = e/(s1 mu_1)
         void* dm1 = nullptr;  // Dhat_0 = 0
         void* d0 = w.Vlo;
@@ -647,64 +716,65 @@ static rr_status eig_run(const rr_operator* Aop, const rr_params* p, double* the
         for (int j = 1; j < q; ++j) {
           const double sn = 1.0 / (2.0 / s1 - sg);
           const double an = 2.0 * sn / e, bn = sg * sn;
-          RR_TRY(vec_scale(s, b, an, w.kap, w.gam));
-          RR_TRY(rr_chebyshev_step(n, b, op.rp, op.ci, op.va, dt, d0, dm1, n, an, c, bn, w.rho, w.R, n,
+          STAGE(RR_STAGE_OTHER, vec_scale(s, b, an, w.kap, w.gam));
+          STAGE(RR_STAGE_LOWP_PRODUCT, rr_chebyshev_step(n, b, op.rp, op.ci, op.va, dt, d0, dm1, n, an, c, bn, w.rho, w.R, n,
                                    w.gam, op.wt, w.W, n, s));
-          RR_TRY(project_out(w.c, s, n, b, w.X, n, (float*)w.W, n, w.Y));
+          STAGE(RR_STAGE_GRAM, project_out(w.c, s, n, b, w.X, n, (float*)w.W, n, w.Y));
           if (j + 1 < q) {
             // Dhat_{j+1} = T / mu into the buffer of Dhat_{j-1}
             void* dst = dm1 ? dm1 : d1;
-            RR_TRY(scale_cast(s, op.wt, n, b, w.W, n, w.mu, dt, dst, n, nullptr, nullptr));
-            RR_TRY(cheb_coef_update(s, b, w.theta, w.mu, an, c, bn, w.kap, w.kap_prev, w.rho));
+            STAGE(RR_STAGE_OTHER, scale_cast(s, op.wt, n, b, w.W, n, w.mu, dt, dst, n, nullptr, nullptr));
+            STAGE(RR_STAGE_OTHER, cheb_coef_update(s, b, w.theta, w.mu, an, c, bn, w.kap, w.kap_prev, w.rho));
             dm1 = d0;
             d0 = dst;
           }
           sg = sn;
         }
-        if (q == 1) RR_TRY(scale_cast(s, RR_F64, n, b, w.R, n, w.mu, op.wt, w.W, n, nullptr, nullptr));
+        if (q == 1) STAGE(RR_STAGE_OTHER, scale_cast(s, RR_F64, n, b, w.R, n, w.mu, op.wt, w.W, n, nullptr, nullptr));
       } else {
         // D_1 = R;  D_{j+1} = A D_j + R Theta^j  (coef <- coef theta / mu)
-        RR_TRY(fill(s, b, 1.0, w.coef));
+        STAGE(RR_STAGE_OTHER, fill(s, b, 1.0, w.coef));
         if (q == 1) {
-          RR_TRY(scale_cast(s, RR_F64, n, b, w.R, n, w.mu, op.wt, w.W, n, nullptr, nullptr));
+          STAGE(RR_STAGE_OTHER, scale_cast(s, RR_F64, n, b, w.R, n, w.mu, op.wt, w.W, n, nullptr, nullptr));
         } else {
-          RR_TRY(scale_cast(s, RR_F64, n, b, w.R, n, w.mu, dt, w.Vlo, n, w.coef, w.theta));
+          STAGE(RR_STAGE_OTHER, scale_cast(s, RR_F64, n, b, w.R, n, w.mu, dt, w.Vlo, n, w.coef, w.theta));
           for (int j = 1; j < q; ++j) {
-            RR_TRY(apply_lowp(op, b, w.Vlo, n, w.W, n, w.R, n, w.coef, s));
-            RR_TRY(project_out(w.c, s, n, b, w.X, n, (float*)w.W, n, w.Y));
-            if (j + 1 < q) RR_TRY(scale_cast(s, op.wt, n, b, w.W, n, w.mu, dt, w.Vlo, n, w.coef, w.theta));
+            STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp(op, b, w.Vlo, n, w.W, n, w.R, n, w.coef, s));
+            STAGE(RR_STAGE_GRAM, project_out(w.c, s, n, b, w.X, n, (float*)w.W, n, w.Y));
+            if (j + 1 < q) STAGE(RR_STAGE_OTHER, scale_cast(s, op.wt, n, b, w.W, n, w.mu, dt, w.Vlo, n, w.coef, w.theta));
           }
         }
       }
-      RR_TRY(basis_step(w.c, hess, op.wt, dt, n, b, w.W, n, w.Dlo, n, s));
-      RR_TRY(apply_lowp(op, b, w.Dlo, n, w.AD, n, nullptr, 0, nullptr, s));
+      STAGE(RR_STAGE_HESSENBERG, basis_step(w.c, hess, op.wt, dt, n, b, w.W, n, w.Dlo, n, s));
+      STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp(op, b, w.Dlo, n, w.AD, n, nullptr, 0, nullptr, s));
       // projected pencil over S = [X, D] (ld 2b)
-      RR_TRY(gram(w.c, n, b, b, RR_F64, w.X, n, RR_F64, w.X, n, w.G, b2, s));
-      RR_TRY(gram(w.c, n, b, b, RR_F64, w.X, n, dt, w.Dlo, n, w.G + b * b2, b2, s));
-      RR_TRY(transpose(s, b, b, w.G + b * b2, b2, w.G + b, b2));
-      RR_TRY(gram(w.c, n, b, b, dt, w.Dlo, n, dt, w.Dlo, n, w.G + b + b * b2, b2, s));
-      RR_TRY(gram(w.c, n, b, b, RR_F64, w.X, n, RR_F64, w.P, n, w.H, b2, s));
-      RR_TRY(gram(w.c, n, b, b, RR_F64, w.P, n, dt, w.Dlo, n, w.H + b * b2, b2, s));
-      RR_TRY(transpose(s, b, b, w.H + b * b2, b2, w.H + b, b2));
-      RR_TRY(gram(w.c, n, b, b, dt, w.Dlo, n, op.wt, w.AD, n, w.H + b + b * b2, b2, s));
-      RR_TRY(rr_pencil_eig(b2, w.H, w.G, w.th2, w.Y, w.c.pen_ws, w.c.pen_bytes, nullptr, s));
-      RR_TRY(select_eig(s, b2, b, p->which, w.th2, w.Y, b2, w.theta, w.Ysel, b2));
-      RR_TRY(lift(s, RR_F64, n, b, b, w.X, n, w.Ysel, b2, w.X2, n, 0));
-      RR_TRY(lift(s, dt, n, b, b, w.Dlo, n, w.Ysel + b, b2, w.X2, n, 1));
+      STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, RR_F64, w.X, n, RR_F64, w.X, n, w.G, b2, s));
+      STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, RR_F64, w.X, n, dt, w.Dlo, n, w.G + b * b2, b2, s));
+      STAGE(RR_STAGE_OTHER, transpose(s, b, b, w.G + b * b2, b2, w.G + b, b2));
+      STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, dt, w.Dlo, n, dt, w.Dlo, n, w.G + b + b * b2, b2, s));
+      STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, RR_F64, w.X, n, RR_F64, w.P, n, w.H, b2, s));
+      STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, RR_F64, w.P, n, dt, w.Dlo, n, w.H + b * b2, b2, s));
+      STAGE(RR_STAGE_OTHER, transpose(s, b, b, w.H + b * b2, b2, w.H + b, b2));
+      STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, dt, w.Dlo, n, op.wt, w.AD, n, w.H + b + b * b2, b2, s));
+      STAGE(RR_STAGE_PENCIL, rr_pencil_eig(b2, w.H, w.G, w.th2, w.Y, w.c.pen_ws, w.c.pen_bytes, nullptr, s));
+      STAGE(RR_STAGE_PENCIL, select_eig(s, b2, b, p->which, w.th2, w.Y, b2, w.theta, w.Ysel, b2));
+      STAGE(RR_STAGE_LIFT, lift(s, RR_F64, n, b, b, w.X, n, w.Ysel, b2, w.X2, n, 0));
+      STAGE(RR_STAGE_LIFT, lift(s, dt, n, b, b, w.Dlo, n, w.Ysel + b, b2, w.X2, n, 1));
       std::swap(w.X, w.X2);
       ++sweep;
       ++inf.refine_sweeps;
-      RR_TRY(update_bounds());
+      STAGE(RR_STAGE_OTHER, update_bounds());
     }
   }
 
   RR_CUDA(cudaMemcpyAsync(theta_out, w.theta, k * sizeof(double), cudaMemcpyDeviceToDevice, s));
   RR_CUDA(cudaMemcpy2DAsync(X_out, n * sizeof(double), w.X, n * sizeof(double), n * sizeof(double), k,
                             cudaMemcpyDeviceToDevice, s));
-  RR_TRY(normalize_sign(s, n, k, X_out, n, 0, nullptr, 0));
+  STAGE(RR_STAGE_OTHER, normalize_sign(s, n, k, X_out, n, 0, nullptr, 0));
   RR_CUDA(cudaStreamSynchronize(s));
   RR_TRY(read_err(w.c, s));
   inf.sweeps = sweep;
+  prof.finish(&inf);
   if (info) *info = inf;
   return converged ? RR_OK : RR_ERR_NO_CONV;
 }
