@@ -1,17 +1,393 @@
-// tcgen05 BF16 block product (placeholder until the tensor-core kernel lands):
-// reports every shape as unsupported so rr_gemm_lowp uses the SIMT kernel.
+// tcgen05 tensor-core block product for the low-precision filter (Sec. 2's
+// X_iter = A X with the BF16 basis of the precision map in Sec. 4.2):
+//   C (M x N, FP32, column-major) = A_k^T B  [+ coef_j R(:, j)]
+// A_k: K x M BF16, K contiguous (the K-major "A" operand: rows of A for
+// A V, columns of A for A^T W); B: K x N BF16, K contiguous.
+//
+// One CTA per 128-row tile of C and K-split, 4 warps:
+//   warp 0 (one lane): TMA producer, 128B-swizzled 64-wide K slabs of A and
+//                      B into an S-stage shared-memory ring (mbarrier
+//                      complete_tx per stage);
+//   warp 1 (one lane): issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32,
+//                      M = 128, N = padded N, K = 16 per instruction) into a
+//                      TMEM accumulator, tcgen05.commit frees each stage;
+//   warps 0-3:        epilogue, tcgen05.ld 32x32b from TMEM (warp w owns
+//                      lanes 32w..32w+31 = rows), coalesced column stores.
+// K splits (small M) add their partial tiles with FP32 atomics into a C
+// pre-initialised to the added term.
+// Every mbarrier wait is bounded (2 s); on expiry the kernel records an error
+// (read by the host), stops issuing, waits (bounded) for its in-flight copies,
+// frees its TMEM and returns.
+#include <cuda.h>
+
 #include "rr_common.cuh"
 
 namespace rr {
+
+__device__ int g_tc_error = 0;
+
+namespace {
+
+constexpr int kBM = 128;
+constexpr int kBK = 64;  // bf16 elements per 128-byte swizzle row
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait; returns false (and flags the error) on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_timer_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*(volatile int*)&g_tc_error) return false;
+    if (global_timer_ns() - t0 > kWaitLimitNs) {
+      atomicCAS(&g_tc_error, 0, (int)RR_ERR_TIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                            int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], "
+      "[%2];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// shared-memory matrix descriptor, K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SM100 descriptor format, version 1)
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
+  d |= (uint64_t)1 << 46;             // descriptor version
+  d |= (uint64_t)2 << 61;             // SWIZZLE_128B
+  return d;
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+}  // namespace
+
+struct TcArgs {
+  int64_t M, N, K;
+  int npad;        // N rounded up to 16 (UMMA N)
+  int tmem_cols;   // power of two >= max(32, npad)
+  int stages;
+  int ksteps_per_split;
+  int nk;          // total K steps
+  float* C;
+  int64_t ldc;
+  const double* R;
+  int64_t ldr;
+  const double* coef;
+  int atomic;      // 1: K-split, add into C
+};
+
+__global__ void __launch_bounds__(128, 1) k_gemm_bf16_tc(const __grid_constant__ CUtensorMap tmA,
+                                                          const __grid_constant__ CUtensorMap tmB,
+                                                          TcArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  // 1024-byte alignment for the swizzled tiles
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const uint32_t a_bytes = kBM * kBK * 2;            // 16 KB
+  const uint32_t b_bytes = (uint32_t)a.npad * kBK * 2;
+  const uint32_t stage_bytes = a_bytes + b_bytes;     // multiple of 1024 (npad % 16 == 0 -> b_bytes % 2048)
+  uint64_t* full = (uint64_t*)(base + (size_t)a.stages * stage_bytes);
+  uint64_t* empty = full + a.stages;
+  uint64_t* accum = empty + a.stages;
+  __shared__ uint32_t s_tmem;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * kBM;
+  const int split = blockIdx.y;
+  const int ks0 = split * a.ksteps_per_split;
+  int ks1 = ks0 + a.ksteps_per_split;
+  if (ks1 > a.nk) ks1 = a.nk;
+  const int nks = ks1 > ks0 ? ks1 - ks0 : 0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < a.stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accum, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"(a.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+
+  if (nks > 0) {
+    if (warp == 0 && lane == 0) {
+      // ---------------- TMA producer ----------------
+      int issued = 0;
+      for (int i = 0; i < nks; ++i) {
+        const int s = i % a.stages;
+        if (i >= a.stages && !mbar_wait(&empty[s], ((i / a.stages) - 1) & 1)) break;
+        unsigned char* sa = base + (size_t)s * stage_bytes;
+        unsigned char* sb = sa + a_bytes;
+        mbar_expect_tx(&full[s], stage_bytes);
+        const int kx = (ks0 + i) * kBK;
+        tma_load_2d(sa, &tmA, &full[s], kx, (int)m0);
+        tma_load_2d(sb, &tmB, &full[s], kx, 0);
+        ++issued;
+      }
+      if (issued < nks) {
+        // error: drain the copies still in flight (bounded) before leaving
+        for (int i = (issued > a.stages ? issued - a.stages : 0); i < issued; ++i) {
+          const int s = i % a.stages;
+          const uint64_t t0 = global_timer_ns();
+          while (!mbar_try_wait(&full[s], (i / a.stages) & 1) && global_timer_ns() - t0 < kWaitLimitNs) {
+          }
+        }
+      }
+    } else if (warp == 1 && lane == 0) {
+      // ---------------- MMA issuer ----------------
+      const uint32_t idesc = (1u << 4)                          // D: FP32
+                             | (1u << 7) | (1u << 10)            // A, B: BF16
+                             | ((uint32_t)(a.npad >> 3) << 17)  // N / 8
+                             | ((uint32_t)(kBM >> 4) << 24);    // M / 16
+      bool ok = true;
+      for (int i = 0; i < nks; ++i) {
+        const int s = i % a.stages;
+        if (!mbar_wait(&full[s], (i / a.stages) & 1)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t sa = smem_u32(base + (size_t)s * stage_bytes);
+        const uint32_t sb = sa + a_bytes;
+        const uint64_t ad = sdesc_sw128(sa), bd = sdesc_sw128(sb);
+#pragma unroll
+        for (int kk = 0; kk < kBK / 16; ++kk)  // K = 16 per instruction: +32 bytes
+          umma_bf16(tmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc,
+                    (i > 0 || kk > 0) ? 1u : 0u);
+        umma_commit(&empty[s]);
+      }
+      // the final commit arrives once every MMA issued above has completed,
+      // also after an error, so TMEM is never freed under a running MMA
+      umma_commit(accum);
+      (void)ok;
+    }
+    // ---------------- epilogue (all 4 warps) ----------------
+    __syncwarp();
+    bool ready = mbar_wait(accum, 0);
+    __syncwarp();
+    ready = __all_sync(0xffffffffu, ready) && *(volatile int*)&g_tc_error == 0;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ready) {
+      const int64_t row = m0 + warp * 32 + lane;
+      for (int c0 = 0; c0 < a.npad; c0 += 32) {
+        uint32_t r[32];
+        tmem_ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+        if (row < a.M) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int64_t col = c0 + j;
+            if (col < a.N) {
+              float v = __uint_as_float(r[j]);
+              float* dst = a.C + row + col * a.ldc;
+              if (a.atomic) {
+                atomicAdd(dst, v);
+              } else {
+                if (a.R) v += (float)(a.coef[col] * a.R[row + col * a.ldr]);
+                *dst = v;
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols)
+                 : "memory");
+  }
+}
+
+// C = coef_j R(:, j) (or 0): the starting value for K-split accumulation
+__global__ void k_tc_init_c(int64_t M, int64_t N, float* __restrict__ C, int64_t ldc,
+                            const double* __restrict__ R, int64_t ldr, const double* __restrict__ coef) {
+  const int64_t j = blockIdx.y;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x)
+    C[i + j * ldc] = R ? (float)(coef[j] * R[i + j * ldr]) : 0.f;
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
 int& gemm_force_simt() {
   static int v = 0;
   return v;
 }
-bool gemm_bf16_tc_supported(int64_t, int64_t, int64_t, int64_t, int64_t, const void*, const void*) {
-  return false;
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
 }
-rr_status gemm_bf16_tc(int64_t, int64_t, int64_t, const __nv_bfloat16*, int64_t, const __nv_bfloat16*,
-                       int64_t, float*, int64_t, const double*, int64_t, const double*, cudaStream_t) {
-  return RR_ERR_ARG;
+
+bool gemm_bf16_tc_supported(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb, const void* A,
+                            const void* B) {
+  if (M <= 0 || N <= 0 || N > 256 || K <= 0) return false;
+  if (lda % 8 || ldb % 8) return false;                          // 16-byte strides
+  if (((uintptr_t)A & 15) || ((uintptr_t)B & 15)) return false;  // 16-byte aligned bases
+  if (M > 0x7fffffff || K > 0x7fffffff) return false;
+  return encode_fn() != nullptr;
 }
+
+static bool make_map(CUtensorMap* m, const void* base, int64_t inner, int64_t outer, int64_t ld_elems,
+                     uint32_t box_inner, uint32_t box_outer) {
+  cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+  cuuint64_t strides[1] = {(cuuint64_t)ld_elems * 2};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides,
+                           box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+rr_status gemm_bf16_tc(int64_t M, int64_t N, int64_t K, const __nv_bfloat16* A, int64_t lda,
+                       const __nv_bfloat16* B, int64_t ldb, float* C, int64_t ldc, const double* R,
+                       int64_t ldr, const double* coef, cudaStream_t s) {
+  const int npad = (int)((N + 15) / 16 * 16);
+  int tcols = 32;
+  while (tcols < npad) tcols <<= 1;
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, A, K, M, lda, kBK, kBM)) return RR_ERR_ARG;
+  if (!make_map(&tb, B, K, N, ldb, kBK, (uint32_t)npad)) return RR_ERR_ARG;
+  const int64_t tiles = (M + kBM - 1) / kBM;
+  const int nk = (int)((K + kBK - 1) / kBK);
+  const int sms = num_sms();
+  int splits = 1;
+  if (tiles < sms) {
+    splits = (int)(sms / tiles);
+    if (splits > nk) splits = nk;
+    if (splits < 1) splits = 1;
+  }
+  const int per = (nk + splits - 1) / splits;
+  splits = (nk + per - 1) / per;
+  const uint32_t stage_bytes = kBM * kBK * 2 + (uint32_t)npad * kBK * 2;
+  int stages = (int)((200 * 1024) / stage_bytes);
+  if (stages > 8) stages = 8;
+  if (stages < 2) return RR_ERR_ARG;
+  const size_t smem = 1024 + (size_t)stages * stage_bytes + (2 * stages + 1) * sizeof(uint64_t);
+  RR_CUDA(cudaFuncSetAttribute(k_gemm_bf16_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  TcArgs a;
+  a.M = M;
+  a.N = N;
+  a.K = K;
+  a.npad = npad;
+  a.tmem_cols = tcols;
+  a.stages = stages;
+  a.ksteps_per_split = per;
+  a.nk = nk;
+  a.C = C;
+  a.ldc = ldc;
+  a.R = R;
+  a.ldr = ldr;
+  a.coef = coef;
+  a.atomic = splits > 1;
+  if (splits > 1) {
+    dim3 gi((unsigned)std::min<int64_t>((M + 255) / 256, 256), (unsigned)N);
+    k_tc_init_c<<<gi, 256, 0, s>>>(M, N, C, ldc, R, ldr, coef);
+    note_launches(1);
+  }
+  dim3 grid((unsigned)tiles, (unsigned)splits);
+  k_gemm_bf16_tc<<<grid, 128, smem, s>>>(ta, tb, a);
+  return check_launch("gemm_bf16_tc");
+}
+
+// error word of the tensor-core kernels (0 = ok); cleared on read
+rr_status tc_take_error(cudaStream_t s) {
+  int e = 0;
+  RR_CUDA(cudaMemcpyFromSymbolAsync(&e, g_tc_error, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
+  RR_CUDA(cudaStreamSynchronize(s));
+  if (e) {
+    int z = 0;
+    RR_CUDA(cudaMemcpyToSymbolAsync(g_tc_error, &z, sizeof(int), 0, cudaMemcpyHostToDevice, s));
+    return (rr_status)e;
+  }
+  return RR_OK;
+}
+
 }  // namespace rr

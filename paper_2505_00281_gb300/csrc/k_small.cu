@@ -82,52 +82,43 @@ __global__ void __launch_bounds__(kSmallThreads) k_tri_inv_lower(int b, const do
   }
 }
 
-// Small FP64 GEMM: C = alpha op(A) op(B) + beta C (32 x 32 tiles).
+// Small FP64 GEMM: C = alpha op(A) op(B) + beta C.  16 x 16 output tiles,
+// one output per thread, so a 256 x 256 product spreads over 256 CTAs (FP64
+// issue rate per SM is the limit on GB300, so the work must cover the GPU).
 __global__ void __launch_bounds__(256) k_gemm_f64_small(int ta, int tb, int M, int N, int K,
                                                         double alpha, const double* __restrict__ A,
                                                         int lda, const double* __restrict__ B,
                                                         int ldb, double beta, double* __restrict__ C,
                                                         int ldc) {
-  __shared__ double As[16][33];
-  __shared__ double Bs[16][33];
-  const int m0 = blockIdx.x * 32, n0 = blockIdx.y * 32;
+  __shared__ double As[32][17];
+  __shared__ double Bs[32][17];
+  const int m0 = blockIdx.x * 16, n0 = blockIdx.y * 16;
   const int tid = threadIdx.x, ti = tid % 16, tj = tid / 16;
-  double acc[2][2] = {};
-  for (int k0 = 0; k0 < K; k0 += 16) {
-    for (int e = tid; e < 16 * 32; e += 256) {
-      int kk = e % 16, i = e / 16;
+  double acc = 0.0;
+  for (int k0 = 0; k0 < K; k0 += 32) {
+    for (int e = tid; e < 32 * 16; e += 256) {
+      int kk = e % 32, i = e / 32;
       int gk = k0 + kk, gi = m0 + i, gj = n0 + i;
       As[kk][i] = (gk < K && gi < M) ? (ta ? A[gk + gi * lda] : A[gi + gk * lda]) : 0.0;
       Bs[kk][i] = (gk < K && gj < N) ? (tb ? B[gj + gk * ldb] : B[gk + gj * ldb]) : 0.0;
     }
     __syncthreads();
 #pragma unroll
-    for (int kk = 0; kk < 16; ++kk) {
-      double a0 = As[kk][ti], a1 = As[kk][ti + 16], b0 = Bs[kk][tj], b1 = Bs[kk][tj + 16];
-      acc[0][0] = fma(a0, b0, acc[0][0]);
-      acc[0][1] = fma(a0, b1, acc[0][1]);
-      acc[1][0] = fma(a1, b0, acc[1][0]);
-      acc[1][1] = fma(a1, b1, acc[1][1]);
-    }
+    for (int kk = 0; kk < 32; ++kk) acc = fma(As[kk][ti], Bs[kk][tj], acc);
     __syncthreads();
   }
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      int i = m0 + ti + 16 * a, j = n0 + tj + 16 * c;
-      if (i < M && j < N) {
-        double v = alpha * acc[a][c];
-        if (beta != 0.0) v += beta * C[i + j * ldc];
-        C[i + j * ldc] = v;
-      }
-    }
+  int i = m0 + ti, j = n0 + tj;
+  if (i < M && j < N) {
+    double v = alpha * acc;
+    if (beta != 0.0) v += beta * C[i + j * ldc];
+    C[i + j * ldc] = v;
+  }
 }
 
 static void gemm_small(cudaStream_t s, int ta, int tb, int M, int N, int K, double alpha,
                        const double* A, int lda, const double* B, int ldb, double beta, double* C,
                        int ldc) {
-  dim3 g((M + 31) / 32, (N + 31) / 32);
+  dim3 g((M + 15) / 16, (N + 15) / 16);
   k_gemm_f64_small<<<g, 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
 }
 
@@ -582,7 +573,7 @@ static int bj_cpad(int c, int* w_out, int* P_out, size_t elt, int r) {
     if (w < 1) w = 1;
     P = 1;
   } else {
-    w = 4;
+    w = 16;
     size_t per_w = 2 * (size_t)(r + c + 64) * elt;
     while (w > 1 && per_w * w > 200 * 1024) --w;
     P = (c + 2 * w - 1) / (2 * w);

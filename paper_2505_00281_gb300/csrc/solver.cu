@@ -215,7 +215,8 @@ static rr_status read_err(const Common& c, cudaStream_t s) {
   int e = 0;
   RR_CUDA(cudaMemcpyAsync(&e, c.hess_ws, sizeof(int), cudaMemcpyDeviceToHost, s));
   RR_CUDA(cudaStreamSynchronize(s));
-  return e ? (rr_status)e : RR_OK;
+  if (e) return (rr_status)e;
+  return tc_take_error(s);
 }
 
 static rr_status check_params(const rr_params* p, int64_t rows_min) {

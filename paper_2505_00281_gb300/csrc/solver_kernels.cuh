@@ -36,5 +36,6 @@ rr_status hessenberg_ex(int32_t arith, int64_t n, int64_t k, void* W, int64_t ld
                         cudaStream_t s, int max_grid);
 rr_status sub_lowrank_f32(cudaStream_t s, int64_t n, int64_t b, int64_t p, const double* X, int64_t ldx,
                           const double* K, int64_t ldk, float* T, int64_t ldt);
+rr_status tc_take_error(cudaStream_t s);
 rr_status vec_scale(cudaStream_t s, int64_t n, double alpha, const double* a, double* d);
 }  // namespace rr

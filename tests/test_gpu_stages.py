@@ -63,8 +63,13 @@ def test_cast_operator_bitexact(rr):
 
 
 # ---------------------------------------------------------------- a2
-@pytest.mark.parametrize("M,N,K", [(300, 40, 700), (128, 128, 4096), (1000, 7, 33)])
+@pytest.mark.parametrize("M,N,K", [(300, 40, 700), (128, 128, 4096), (1000, 7, 33),
+                                   # tcgen05 path: ragged M, K tail, N padded to 16, K-split
+                                   (1000, 128, 2048), (300, 40, 520), (4096, 128, 16384),
+                                   (16384, 128, 4096), (2048, 256, 1024)])
 def test_gemm_lowp_bf16_within_fp32_bound(rr, M, N, K):
+    """C = A_k^T B (+ coef R) within the FP32 recursive-summation bound
+    K u32 |A|^T |B| (tensor-core and SIMT paths; lda % 8 == 0 takes tcgen05)."""
     rng = np.random.default_rng(M + N + K)
     Ak = O.round_bf16(rng.standard_normal((K, M)))       # K x M, K-contiguous
     B = O.round_bf16(rng.standard_normal((K, N)))
