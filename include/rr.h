@@ -74,7 +74,7 @@ typedef struct {
 /* Solver parameters (Algorithm 1 inputs A, k, m, iter; Sec. 4.2 precisions). */
 typedef struct {
   int32_t k;             /* wanted pairs (k <= block)                                */
-  int32_t block;         /* block size b of the subspace                             */
+  int32_t block;         /* block size b (b <= 336, and b <= 168 with refinement)    */
   int32_t filter;        /* RR_POWER (products per sweep) or RR_CHEBYSHEV            */
   int32_t degree;        /* power: products per sweep (Alg. 1 "iter"); Chebyshev: d  */
   int32_t max_sweeps;    /* projections (Alg. 1 "m"), counting both phases           */
@@ -228,6 +228,7 @@ rr_status rr_gram(int64_t n, int64_t p, int64_t q, int32_t xtype, const void* X,
  *   (theorem of Sec. 3.2).  Solved as the whitened SVD of
  *   Lu^-1 B Lv^-T by one-sided Jacobi (equivalent to the positive half of
  *   the 2x2 block pencil).
+ * Sizes up to 336 x 336 (RR_ERR_ARG above).
  * Both need rr_pencil_workspace_size(b1, b2) bytes of workspace and
  * synchronise nothing (dropped counts are read only when dropped != NULL,
  * which synchronises). */

@@ -16,6 +16,9 @@
 namespace rr {
 
 constexpr int kSmallThreads = 1024;
+// largest pencil side: the packed FP32 Cholesky factor must fit in shared
+// memory (b (b + 1) / 2 floats <= 227 KB)
+constexpr int kMaxPencil = 336;
 
 // Cholesky G = L L^T (lower), dropping column j when its pivot
 // L_jj^2 <= 64 u64 max_i G_ii (or is not positive).  A dropped index gets a
@@ -331,36 +334,41 @@ __global__ void k_svd_finish(int b1, int b2, const double* __restrict__ sig_desc
 }
 
 // ---------------------------------------------------------------------------
-// FP32 Cholesky with column dropping (single CTA).  A column j is dropped
-// when its Schur-complement pivot is below 64 u32 times its original
-// diagonal (its new content is below ~1e-3 of its length: rounding noise for
-// a basis stored in BF16/FP32) or not positive.  Dropped indices get a unit
-// diagonal and zero row/column.
+// FP32 Cholesky with column dropping, then the inverse of the factor, in one
+// CTA with the lower triangle packed in shared memory (b(b+1)/2 floats).
+// A column j is dropped when its Schur-complement pivot is below 64 u32 times
+// its original diagonal (its new content is below ~1e-3 of its length:
+// rounding noise for a basis stored in BF16/FP32) or not positive; dropped
+// indices get a unit diagonal and zero row/column.  Output W0 = L^-T (FP64)
+// with dropped columns zeroed.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSmallThreads) k_chol_f32(int b, const double* __restrict__ G, int ldg,
-                                                            float* __restrict__ L, int* __restrict__ dropped) {
+__device__ __forceinline__ int pk(int i, int j, int b) { return j * b - (j * (j - 1)) / 2 + (i - j); }
+
+__global__ void __launch_bounds__(kSmallThreads) k_chol_inv_f32(int b, const double* __restrict__ G, int ldg,
+                                                                int* __restrict__ dropped,
+                                                                double* __restrict__ W) {
+  extern __shared__ float Ls[];  // packed lower triangle, column-major
   const int tid = threadIdx.x;
   __shared__ int s_keep;
-  for (int e = tid; e < b * b; e += kSmallThreads) {
-    int i = e % b, j = e / b;
-    L[i + j * b] = (i >= j) ? (float)(0.5 * (G[i + j * ldg] + G[j + i * ldg])) : 0.f;
-  }
+  for (int j = 0; j < b; ++j)
+    for (int i = j + tid; i < b; i += kSmallThreads)
+      Ls[pk(i, j, b)] = (float)(0.5 * (G[i + j * ldg] + G[j + i * ldg]));
   __syncthreads();
   for (int j = 0; j < b; ++j) {
     if (tid == 0) {
-      float d = L[j + j * b];
+      float d = Ls[pk(j, j, b)];
       float g0 = (float)G[j + j * ldg];
       s_keep = (g0 > 0.f && d > 64.f * 0x1p-24f * g0) ? 1 : 0;
       dropped[j] = s_keep ? 0 : 1;
-      L[j + j * b] = s_keep ? sqrtf(d) : 1.f;
+      Ls[pk(j, j, b)] = s_keep ? sqrtf(d) : 1.f;
     }
     __syncthreads();
-    const float ljj = L[j + j * b];
+    const float ljj = Ls[pk(j, j, b)];
     if (s_keep) {
-      for (int i = j + 1 + tid; i < b; i += kSmallThreads) L[i + j * b] /= ljj;
+      for (int i = j + 1 + tid; i < b; i += kSmallThreads) Ls[pk(i, j, b)] /= ljj;
     } else {
-      for (int i = j + 1 + tid; i < b; i += kSmallThreads) L[i + j * b] = 0.f;
-      for (int l = tid; l < j; l += kSmallThreads) L[j + l * b] = 0.f;
+      for (int i = j + 1 + tid; i < b; i += kSmallThreads) Ls[pk(i, j, b)] = 0.f;
+      for (int l = tid; l < j; l += kSmallThreads) Ls[pk(j, l, b)] = 0.f;
     }
     __syncthreads();
     if (s_keep) {
@@ -369,32 +377,33 @@ __global__ void __launch_bounds__(kSmallThreads) k_chol_f32(int b, const double*
         int ii = e % m, ll = e / m;
         if (ii < ll) continue;
         int i = j + 1 + ii, l = j + 1 + ll;
-        L[i + l * b] = fmaf(-L[i + j * b], L[l + j * b], L[i + l * b]);
+        Ls[pk(i, l, b)] = fmaf(-Ls[pk(i, j, b)], Ls[pk(l, j, b)], Ls[pk(i, l, b)]);
       }
     }
     __syncthreads();
   }
-}
-
-// W0 = (L^-1)^T in FP64 with dropped columns zeroed; L lower triangular FP32.
-// One thread per column of L^-1 (forward substitution in FP32).
-__global__ void __launch_bounds__(kSmallThreads) k_whitener0(int b, const float* __restrict__ L,
-                                                             float* __restrict__ Li,
-                                                             const int* __restrict__ dropped,
-                                                             double* __restrict__ W) {
-  for (int c = threadIdx.x; c < b; c += kSmallThreads) {
-    for (int i = 0; i < c; ++i) Li[i + c * b] = 0.f;
-    Li[c + c * b] = 1.f / L[c + c * b];
-    for (int i = c + 1; i < b; ++i) {
-      float s = 0.f;
-      for (int l = c; l < i; ++l) s = fmaf(L[i + l * b], Li[l + c * b], s);
-      Li[i + c * b] = -s / L[i + i * b];
+  // in-place inverse, last column first: column j of L^-1 from the already
+  // inverted trailing block: x = -(Linv[j+1:, j+1:] L[j+1:, j]) / L_jj
+  for (int j = b - 1; j >= 0; --j) {
+    const float ajj = 1.f / Ls[pk(j, j, b)];
+    // each thread computes one row i > j of the new column (reads old column j)
+    float acc[8];
+    int cnt = 0;
+    for (int i = j + 1 + tid; i < b && cnt < 8; i += kSmallThreads, ++cnt) {
+      float sum = 0.f;
+      for (int l = j + 1; l <= i; ++l) sum = fmaf(Ls[pk(i, l, b)], Ls[pk(l, j, b)], sum);
+      acc[cnt] = -sum * ajj;
     }
+    __syncthreads();
+    cnt = 0;
+    for (int i = j + 1 + tid; i < b && cnt < 8; i += kSmallThreads, ++cnt) Ls[pk(i, j, b)] = acc[cnt];
+    if (tid == 0) Ls[pk(j, j, b)] = ajj;
+    __syncthreads();
   }
-  __syncthreads();
-  for (int e = threadIdx.x; e < b * b; e += kSmallThreads) {
+  // W0 = (L^-1)^T, dropped columns zero
+  for (int e = tid; e < b * b; e += kSmallThreads) {
     int i = e % b, j = e / b;
-    W[i + j * b] = dropped[j] ? 0.0 : (double)Li[j + i * b];
+    W[i + j * b] = (dropped[j] || j < i) ? 0.0 : (double)Ls[pk(j, i, b)];
   }
 }
 
@@ -586,7 +595,9 @@ static int bj_cpad(int c, int* w_out, int* P_out, size_t elt, int r) {
 static bool carve_pencil(Arena& ar, int b1, int b2, PencilWs& w) {
   int bm = b1 > b2 ? b1 : b2;
   int ww, P;
-  int cp = bj_cpad(b2 > b1 ? b2 : b1, &ww, &P, 8, bm);
+  int cp8 = bj_cpad(b2 > b1 ? b2 : b1, &ww, &P, 8, bm);
+  int cp4 = bj_cpad(b2 > b1 ? b2 : b1, &ww, &P, 4, bm);
+  int cp = cp8 > cp4 ? cp8 : cp4;
   size_t bb = (size_t)bm * bm, cc = (size_t)cp * cp, rc = (size_t)bm * cp;
   w.W1 = ar.take<double>(bb);
   w.W2 = ar.take<double>(bb);
@@ -621,8 +632,10 @@ static bool carve_pencil(Arena& ar, int b1, int b2, PencilWs& w) {
 // W <- W (I - E/2 + 3/8 E^2), E = W^T G W - I, whose error squares per step.
 static void whiten(cudaStream_t s, int b, const double* G, PencilWs& w, int* dropped, double* Wout) {
   const int g1 = (b * b + 255) / 256;
-  k_chol_f32<<<1, kSmallThreads, 0, s>>>(b, G, b, w.L32, dropped);
-  k_whitener0<<<1, kSmallThreads, 0, s>>>(b, w.L32, w.Li32, dropped, w.W1);
+  const size_t sm = (size_t)b * (b + 1) / 2 * sizeof(float);
+  if (sm > 48 * 1024)
+    cudaFuncSetAttribute(k_chol_inv_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_chol_inv_f32<<<1, kSmallThreads, sm, s>>>(b, G, b, dropped, w.W1);
   // step 1: E = W0^T G W0 - I, F = I - E/2 + 3/8 E^2, W1 = W0 F
   gemm_small(s, 0, 0, b, b, b, 1.0, G, b, w.W1, b, 0.0, w.T, b);
   gemm_small(s, 1, 0, b, b, b, 1.0, w.W1, b, w.T, b, 0.0, w.E, b);
@@ -636,7 +649,7 @@ static void whiten(cudaStream_t s, int b, const double* G, PencilWs& w, int* dro
   k_whiten_corr<<<g1, 256, 0, s>>>(b, w.E, nullptr, dropped, nullptr, 0);
   k_whiten_corr<<<g1, 256, 0, s>>>(b, w.E, nullptr, dropped, w.F, 1);
   gemm_small(s, 0, 0, b, b, b, 1.0, w.W2, b, w.F, b, 0.0, Wout, b);
-  note_launches(14);
+  note_launches(13);
 }
 
 template <typename T>
@@ -664,35 +677,78 @@ static rr_status launch_bj(cudaStream_t s, int r, int cpad, int w, int P, T* M, 
   return RR_OK;
 }
 
+// Omega (c x c) from K = N^T N: for i < j the exact one-sided Jacobi angle
+// that makes columns i and j of N orthogonal, Omega_ij = phi, Omega_ji = -phi
+// (V <- V (I + Omega) to first order).  Zero columns are never rotated.
+__global__ void k_polish_angles(int c, const double* __restrict__ K, double* __restrict__ Om) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= c * c) return;
+  int i = e % c, j = e / c;
+  if (i == j) {
+    Om[e] = 0.0;
+    return;
+  }
+  int p = i < j ? i : j, q = i < j ? j : i;
+  double al = K[p + p * c], be = K[q + q * c], ga = K[p + q * c];
+  double phi = 0.0;
+  if (ga != 0.0 && al > 0.0 && be > 0.0) {
+    double zeta = (be - al) / (2.0 * ga);
+    double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+    phi = atan(t);
+  }
+  Om[e] = (i < j) ? phi : -phi;
+}
+
+// F = I + Om + Om2/2
+__global__ void k_expm2(int c, const double* __restrict__ Om, const double* __restrict__ Om2,
+                        double* __restrict__ F) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= c * c) return;
+  int i = e % c, j = e / c;
+  F[e] = (i == j ? 1.0 : 0.0) + Om[e] + 0.5 * Om2[e];
+}
+
+// V <- V (3I - V^T V)/2, twice (Newton-Schulz polar step; orthogonality error
+// d -> ~3d^2/4 per step).  Uses T, F, E as scratch.
+static void ns_orthonormalize(cudaStream_t s, int c, double* V, PencilWs& w) {
+  for (int it = 0; it < 2; ++it) {
+    gemm_small(s, 1, 0, c, c, c, 1.0, V, c, V, c, 0.0, w.T, c);
+    k_ns_coef<<<(c * c + 255) / 256, 256, 0, s>>>(c, w.T, w.F);
+    gemm_small(s, 0, 0, c, c, c, 1.0, V, c, w.F, c, 0.0, w.E, c);
+    cudaMemcpyAsync(V, w.E, (size_t)c * c * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  }
+  note_launches(6);
+}
+
 // SVD of the r x c matrix C (FP64, ld r): on exit Mout (r x c) = C V with
-// orthogonal columns, Vout (c x c) orthogonal.  FP32 block Jacobi to
-// convergence, FP64 orthonormalisation of its V by two Newton-Schulz steps,
-// then FP64 block Jacobi sweeps (quadratic convergence from the FP32 point).
+// orthogonal columns, Vout (c x c) orthogonal.  FP32 block one-sided Jacobi
+// to 1e-5 relative orthogonality, then FP64 polish made only of small
+// parallel GEMMs: V <- NS(V); N = C V; K = N^T N; rotate every pair by its
+// exact Jacobi angle at once (V <- V (I + Om + Om^2/2)); repeat.  Each polish
+// step squares the off-diagonal of K; two steps reach FP64 level.
 static rr_status jacobi_svd(cudaStream_t s, int r, int c, const double* C, PencilWs& w, double* Mout,
                             double* Vout) {
   int ww, P;
-  const int cpad = bj_cpad(c, &ww, &P, 8, r);
-  const int g = 256;
+  const int cpad = bj_cpad(c, &ww, &P, 4, r);
+  const int g = 256, gc = (c * c + 255) / 256;
   k_pad_copy<double, float><<<g, 256, 0, s>>>(r, c, cpad, C, r, w.M32, w.V32);
-  RR_TRY(launch_bj<float>(s, r, cpad, ww, P, w.M32, w.V32, 4.0f * sqrtf((float)r) * 0x1p-24f, 40, w));
-  // V = NS(V32) in FP64
+  RR_TRY(launch_bj<float>(s, r, cpad, ww, P, w.M32, w.V32, 1e-5f, 20, w));
   k_v32_to_64<<<g, 256, 0, s>>>(c, cpad, w.V32, w.V);
   for (int it = 0; it < 2; ++it) {
-    gemm_small(s, 1, 0, c, c, c, 1.0, w.V, c, w.V, c, 0.0, w.T, c);
-    k_ns_coef<<<(c * c + 255) / 256, 256, 0, s>>>(c, w.T, w.F);
-    gemm_small(s, 0, 0, c, c, c, 1.0, w.V, c, w.F, c, 0.0, w.E, c);
+    ns_orthonormalize(s, c, w.V, w);
+    gemm_small(s, 0, 0, r, c, c, 1.0, C, r, w.V, c, 0.0, w.Mp, r);          // N = C V
+    gemm_small(s, 1, 0, c, c, r, 1.0, w.Mp, r, w.Mp, r, 0.0, w.Vp, c);      // K = N^T N
+    k_polish_angles<<<gc, 256, 0, s>>>(c, w.Vp, w.E2);
+    gemm_small(s, 0, 0, c, c, c, 1.0, w.E2, c, w.E2, c, 0.0, w.T, c);       // Om^2
+    k_expm2<<<gc, 256, 0, s>>>(c, w.E2, w.T, w.F);
+    gemm_small(s, 0, 0, c, c, c, 1.0, w.V, c, w.F, c, 0.0, w.E, c);         // V (I + Om + Om^2/2)
     RR_CUDA(cudaMemcpyAsync(w.V, w.E, (size_t)c * c * sizeof(double), cudaMemcpyDeviceToDevice, s));
   }
-  // M = C V, then FP64 sweeps on it
-  gemm_small(s, 0, 0, r, c, c, 1.0, C, r, w.V, c, 0.0, w.Mp, r);
-  k_pad_copy<double, double><<<g, 256, 0, s>>>(r, c, cpad, w.Mp, r, w.M, w.Vp);
-  RR_TRY(launch_bj<double>(s, r, cpad, ww, P, w.M, w.Vp, 4.0 * sqrt((double)r) * 0x1p-53, 6, w));
-  // outputs: Mout = M (first c columns), Vout = V * Vp(1:c, 1:c)  (via E: Vout may be V)
-  gemm_small(s, 0, 0, c, c, c, 1.0, w.V, c, w.Vp, cpad, 0.0, w.E, c);
-  RR_CUDA(cudaMemcpyAsync(Vout, w.E, (size_t)c * c * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  if (Mout != w.M)
-    RR_CUDA(cudaMemcpyAsync(Mout, w.M, (size_t)r * c * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  note_launches(8);
+  ns_orthonormalize(s, c, w.V, w);
+  gemm_small(s, 0, 0, r, c, c, 1.0, C, r, w.V, c, 0.0, Mout, r);            // M = C V
+  if (Vout != w.V)
+    RR_CUDA(cudaMemcpyAsync(Vout, w.V, (size_t)c * c * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  note_launches(18);
   return check_launch("jacobi_svd");
 }
 
@@ -721,7 +777,7 @@ static rr_status count_dropped(const int* d, int b, int32_t* out, cudaStream_t s
 extern "C" rr_status rr_pencil_eig(int64_t b, const double* H, const double* G, double* theta,
                                    double* Y, void* ws, size_t ws_bytes, int32_t* dropped,
                                    void* stream) {
-  if (b <= 0 || b > 4096 || !H || !G || !theta || !Y) return RR_ERR_ARG;
+  if (b <= 0 || b > kMaxPencil || !H || !G || !theta || !Y) return RR_ERR_ARG;
   Arena ar(ws, ws_bytes);
   PencilWs w;
   if (!ws || !carve_pencil(ar, (int)b, (int)b, w)) return RR_ERR_WORKSPACE;
@@ -750,7 +806,7 @@ extern "C" rr_status rr_pencil_eig(int64_t b, const double* H, const double* G, 
 extern "C" rr_status rr_pencil_svd(int64_t b1, int64_t b2, const double* B, const double* Gu,
                                    const double* Gv, double* sv, double* Y, double* Z, void* ws,
                                    size_t ws_bytes, int32_t* dropped, void* stream) {
-  if (b1 <= 0 || b2 <= 0 || b1 > 4096 || b2 > 4096 || !B || !Gu || !Gv || !sv || !Y || !Z)
+  if (b1 <= 0 || b2 <= 0 || b1 > kMaxPencil || b2 > kMaxPencil || !B || !Gu || !Gv || !sv || !Y || !Z)
     return RR_ERR_ARG;
   Arena ar(ws, ws_bytes);
   PencilWs w;
@@ -761,14 +817,13 @@ extern "C" rr_status rr_pencil_svd(int64_t b1, int64_t b2, const double* B, cons
   // whitening of both sides: Wu -> C, Wv -> V (whiten() uses W1/W2/T/E/E2/F as scratch)
   whiten(s, n1, Gu, w, w.drop1, w.C);
   whiten(s, n2, Gv, w, w.drop2, w.V);
-  // Cw = Wu^T B Wv  (b1 x b2)  -> Mp
-  gemm_small(s, 0, 0, n1, n2, n2, 1.0, B, n1, w.V, n2, 0.0, w.T, n1);
-  gemm_small(s, 1, 0, n1, n2, n1, 1.0, w.C, n1, w.T, n1, 0.0, w.E2, n1);
-  k_zero_dropped<<<(n1 * n2 + 255) / 256, 256, 0, s>>>(n1, n2, w.E2, w.drop1, w.drop2);
-  // keep Wu, Wv: copy them out of C / V (jacobi_svd uses C/V... it uses V, M, Mp, Vp, T, E, F)
   RR_CUDA(cudaMemcpyAsync(w.W1, w.C, (size_t)n1 * n1 * sizeof(double), cudaMemcpyDeviceToDevice, s));
   RR_CUDA(cudaMemcpyAsync(w.W2, w.V, (size_t)n2 * n2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  RR_TRY(jacobi_svd(s, n1, n2, w.E2, w, w.M, w.V));   // M = Cw V (b1 x b2), V (b2 x b2)
+  // Cw = Wu^T B Wv (b1 x b2) -> C
+  gemm_small(s, 0, 0, n1, n2, n2, 1.0, B, n1, w.W2, n2, 0.0, w.T, n1);
+  gemm_small(s, 1, 0, n1, n2, n1, 1.0, w.W1, n1, w.T, n1, 0.0, w.C, n1);
+  k_zero_dropped<<<(n1 * n2 + 255) / 256, 256, 0, s>>>(n1, n2, w.C, w.drop1, w.drop2);
+  RR_TRY(jacobi_svd(s, n1, n2, w.C, w, w.M, w.V));   // M = Cw V (b1 x b2), V (b2 x b2)
   k_colnorm_sort<<<1, kSmallThreads, n2 * sizeof(double), s>>>(n1, n2, w.M, n1, w.sig, w.order);
   double* Uw = w.T;   // b1 x r
   double* Vw = w.E;   // b2 x r

@@ -224,6 +224,9 @@ static rr_status check_params(const rr_params* p, int64_t rows_min) {
   if (p->k <= 0 || p->block < p->k || p->block > rows_min || p->block > 1024) return RR_ERR_ARG;
   if (p->degree <= 0 || p->max_sweeps <= 0 || p->max_sweeps > 10000) return RR_ERR_ARG;
   if (p->basis != RR_F64 && p->basis != RR_F32 && p->basis != RR_BF16) return RR_ERR_ARG;
+  // the projected pencil (2 block with refinement) must fit the small solver
+  const bool refine = p->refine != 0 && p->basis != RR_F64;
+  if ((refine ? 2 * p->block : p->block) > 336) return RR_ERR_ARG;
   return RR_OK;
 }
 
