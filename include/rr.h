@@ -74,7 +74,7 @@ typedef struct {
 /* Solver parameters (Algorithm 1 inputs A, k, m, iter; Sec. 4.2 precisions). */
 typedef struct {
   int32_t k;             /* wanted pairs (k <= block)                                */
-  int32_t block;         /* block size b (b <= 336, and b <= 168 with refinement)    */
+  int32_t block;         /* block size b (b <= 335, and b <= 167 with refinement)    */
   int32_t filter;        /* RR_POWER (products per sweep) or RR_CHEBYSHEV            */
   int32_t degree;        /* power: products per sweep (Alg. 1 "iter"); Chebyshev: d  */
   int32_t max_sweeps;    /* projections (Alg. 1 "m"), counting both phases           */
@@ -190,6 +190,22 @@ rr_status rr_gemm_f64(int32_t trans, int64_t M, int64_t N, int64_t K, const doub
                       int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc,
                       int32_t accumulate, void* stream);
 
+/* FP64-accurate product C = op(A) B on the BF16 tensor cores (error-free
+ * fixed-point slicing): op(A) as in rr_gemm_f64, A and B FP64, C FP64.
+ * Rows of A (trans = 0) or columns of A (trans = 1) and columns of B are
+ * scaled by powers of two and split into `slices` (1..10) integer BF16
+ * slices of 6 bits; every slice product is exact in the FP32 tensor-core
+ * accumulator (K-chunks of at most 4096), and is scaled and summed in FP64.
+ * With 8 slices the result agrees with FP64 arithmetic to about 2^-54 of
+ * |op(A)| |B|.  N <= 256; the row strides of op(A)'s K-major copy (m and n)
+ * must be multiples of 8.  Needs rr_gemm_f64_emulated_workspace_size bytes
+ * (it holds the slices of A and B). */
+size_t rr_gemm_f64_emulated_workspace_size(int32_t trans, int64_t M, int64_t N, int64_t K,
+                                           int32_t slices);
+rr_status rr_gemm_f64_emulated(int32_t trans, int64_t M, int64_t N, int64_t K, const double* A,
+                               int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc,
+                               int32_t slices, void* ws, size_t ws_bytes, void* stream);
+
 /* Algorithm 8, right-looking Hessenberg process on an n x k block (Sec. 4.2.2).
  * W (FP32 if arith == RR_F32, FP64 if RR_F64; ld ldw) is overwritten by the
  * process; the result is also written to Q (dtype qtype: RR_BF16, RR_F32 or
@@ -228,7 +244,7 @@ rr_status rr_gram(int64_t n, int64_t p, int64_t q, int32_t xtype, const void* X,
  *   (theorem of Sec. 3.2).  Solved as the whitened SVD of
  *   Lu^-1 B Lv^-T by one-sided Jacobi (equivalent to the positive half of
  *   the 2x2 block pencil).
- * Sizes up to 336 x 336 (RR_ERR_ARG above).
+ * Sizes up to 335 x 335 (RR_ERR_ARG above).
  * Both need rr_pencil_workspace_size(b1, b2) bytes of workspace and
  * synchronise nothing (dropped counts are read only when dropped != NULL,
  * which synchronises). */

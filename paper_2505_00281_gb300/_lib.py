@@ -64,6 +64,9 @@ _SIGS = {
                              c_i64, c_vp, c_vp]),
     "rr_gemm_f64": (c_i32, [c_i32, c_i64, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_i32,
                             c_vp]),
+    "rr_gemm_f64_emulated_workspace_size": (c_sz, [c_i32, c_i64, c_i64, c_i64, c_i32]),
+    "rr_gemm_f64_emulated": (c_i32, [c_i32, c_i64, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_i64,
+                                     c_i32, c_vp, c_sz, c_vp]),
     "rr_hessenberg_workspace_size": (c_sz, [c_i64, c_i64, c_i32]),
     "rr_hessenberg": (c_i32, [c_i32, c_i64, c_i64, c_vp, c_i64, c_i32, c_vp, c_i64, c_vp, c_dbl, c_vp,
                               c_sz, c_vp]),

@@ -198,6 +198,20 @@ def rr_gemm_f64(trans, A, B, C=None, accumulate=False, stream=None):
     return C
 
 
+def rr_gemm_f64_emulated(trans, A, B, slices=8, C=None, stream=None):
+    M = A.shape[1] if trans else A.shape[0]
+    K = A.shape[0] if trans else A.shape[1]
+    N = B.shape[1]
+    if C is None:
+        C = fortran(torch.empty(M, N, dtype=torch.float64, device=B.device))
+    L = lib()
+    ws = _ws(L.rr_gemm_f64_emulated_workspace_size(int(trans), M, N, K, slices), B.device)
+    check("rr_gemm_f64_emulated", L.rr_gemm_f64_emulated(int(trans), M, N, K, _p(A), ld_of(A), _p(B),
+                                                          ld_of(B), _p(C), ld_of(C), slices, _p(ws),
+                                                          ws.numel(), _stream(stream)))
+    return C
+
+
 def rr_hessenberg(W, qtype=torch.bfloat16, tol=0.0, stream=None):
     """Algorithm 8 on W (FP32 or FP64, modified in place).  Returns (Q, piv, err)."""
     n, k = W.shape

@@ -1,0 +1,235 @@
+// FP64-accurate block products on the BF16 tensor cores (error-free fixed-
+// point slicing, the Ozaki scheme), for the refinement phase's residual
+// products A X and A^T Y (FP64 operator, FP64 Ritz vectors).  GB300 has few
+// FP64 units; its BF16 tensor cores are ~1500x faster.
+//
+// Slicing: every row of A (for A X) or column of A (for A^T Y) and every
+// column of X is scaled by a power of two 2^e so its entries lie in (-1, 1),
+// then split into S integer slices of beta = 6 bits:
+//   x = 2^e (sum_{p=1..S} s_p 2^(-beta p) + r),  |s_1| <= 64, |s_p| <= 32,
+//   |r| <= 2^(-beta S - 1);
+// each s_p is an integer exactly representable in BF16.  The product of two
+// slices, summed over a K-chunk of at most 4096, is an integer of magnitude
+// at most 4096 * 64 * 64 = 2^24, which the tensor core's FP32 accumulator
+// holds exactly.  The epilogue multiplies each exact partial product by the
+// power of two 2^(e_row + e_col - beta (p + q)) and adds it into the FP64
+// result.  Slice pairs with p + q <= S + 1 are kept; the dropped ones and the
+// remainders contribute below 2^(-beta (S + 1)) relative to the row and
+// column scales (S = 8: ~2^-54).
+#include "rr_common.cuh"
+#include "solver_kernels.cuh"
+
+namespace rr {
+
+rr_status gemm_bf16_tc_emu(int64_t M, int64_t N, int64_t K, const __nv_bfloat16* A, int64_t lda,
+                           const __nv_bfloat16* B, int64_t ldb, double* C64, int64_t ldc64,
+                           const int* rexp, int rshift, const double* cscale, int nb, int max_kchunk,
+                           cudaStream_t s);
+bool gemm_bf16_tc_supported(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb, const void* A,
+                            const void* B);
+
+constexpr int kBeta = 6;
+constexpr int kMaxSlices = 10;
+
+__device__ __forceinline__ int exp_above(double mx) {
+  if (!(mx > 0.0)) return 0;
+  int e;
+  frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1)  ->  mx < 2^e
+  return e;
+}
+
+// exponent of the largest |entry| of every row of a column-major matrix
+__global__ void k_row_exp(int64_t m, int64_t n, const double* __restrict__ A, int64_t lda,
+                          int* __restrict__ e) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  double mx = 0.0;
+  for (int64_t j = 0; j < n; ++j) mx = fmax(mx, fabs(A[i + j * lda]));
+  e[i] = exp_above(mx);
+}
+
+// exponent of the largest |entry| of every column (one block per column)
+__global__ void k_col_exp(int64_t m, const double* __restrict__ A, int64_t lda, int* __restrict__ e) {
+  const int64_t j = blockIdx.x;
+  double mx = 0.0;
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) mx = fmax(mx, fabs(A[i + j * lda]));
+  __shared__ double sm[32];
+  mx = warp_max(mx);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    mx = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0.0;
+    mx = warp_max(mx);
+    if (threadIdx.x == 0) e[j] = exp_above(mx);
+  }
+}
+
+__device__ __forceinline__ void slice_value(double x, int e, int S, float* out) {
+  double r = ldexp(x, -e);
+  for (int p = 0; p < S; ++p) {
+    r = ldexp(r, kBeta);
+    const double t = rint(r);
+    out[p] = (float)t;
+    r -= t;
+  }
+}
+
+// column-scaled slices, same layout as the input: out[p] (m x n, ld m)
+__global__ void k_slice_cols(int64_t m, int64_t n, const double* __restrict__ A, int64_t lda,
+                             const int* __restrict__ cexp, int S, __nv_bfloat16* __restrict__ out) {
+  const int64_t j = blockIdx.y;
+  const int e = cexp[j];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    float sl[kMaxSlices];
+    slice_value(A[i + j * lda], e, S, sl);
+    for (int p = 0; p < S; ++p) out[(size_t)p * m * n + i + j * m] = __float2bfloat16_rn(sl[p]);
+  }
+}
+
+// row-scaled slices written row-major (element (i, j) at i*n + j): the
+// K-major operand of A X.  32 x 32 tiles through shared memory.
+__global__ void k_slice_rows(int64_t m, int64_t n, const double* __restrict__ A, int64_t lda,
+                             const int* __restrict__ rexp, int S, __nv_bfloat16* __restrict__ out) {
+  __shared__ float tile[kMaxSlices][32][33];
+  const int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t i = i0 + tx, j = j0 + r;
+    float sl[kMaxSlices];
+    if (i < m && j < n) {
+      slice_value(A[i + j * lda], rexp[i], S, sl);
+    } else {
+      for (int p = 0; p < S; ++p) sl[p] = 0.f;
+    }
+    for (int p = 0; p < S; ++p) tile[p][r][tx] = sl[p];
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t i = i0 + r, j = j0 + tx;
+    if (i < m && j < n)
+      for (int p = 0; p < S; ++p) out[(size_t)p * m * n + i * n + j] = __float2bfloat16_rn(tile[p][tx][r]);
+  }
+}
+
+// cs[(q-1) N + c] = 2^(e_c - beta q), q = 1..S
+__global__ void k_col_scales(int64_t N, int S, const int* __restrict__ e, double* __restrict__ cs) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= N * S) return;
+  const int64_t c = t % N, q = t / N + 1;
+  cs[t] = ldexp(1.0, e[c] - kBeta * (int)q);
+}
+
+__global__ void k_zero_f64(int64_t M, int64_t N, double* __restrict__ C, int64_t ldc) {
+  const int64_t j = blockIdx.y;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x)
+    C[i + j * ldc] = 0.0;
+}
+
+// ---------------------------------------------------------------------------
+size_t emu_operator_bytes(int64_t m, int64_t n, int S, bool rows, bool cols) {
+  size_t b = 0;
+  if (rows) b += align_up((size_t)S * m * n * 2) + align_up((size_t)m * 4);
+  if (cols) b += align_up((size_t)S * m * n * 2) + align_up((size_t)n * 4);
+  return b;
+}
+
+size_t emu_block_bytes(int64_t K, int64_t N, int S) {
+  return align_up((size_t)S * K * N * 2) + align_up((size_t)N * 4) + align_up((size_t)S * N * 8);
+}
+
+// Slice the FP64 operator A (m x n, column-major) once: row-scaled slices
+// (row-major) for A X and/or column-scaled slices (column-major) for A^T Y.
+rr_status emu_prepare(cudaStream_t s, const double* A, int64_t m, int64_t n, int64_t lda, int S,
+                      EmuOperator& op, void* mem, bool rows, bool cols) {
+  if (S < 1 || S > kMaxSlices) return RR_ERR_ARG;
+  Arena ar(mem, emu_operator_bytes(m, n, S, rows, cols));
+  op.m = m;
+  op.n = n;
+  op.S = S;
+  op.rows = nullptr;
+  op.rexp = nullptr;
+  op.cols = nullptr;
+  op.cexp = nullptr;
+  if (rows) {
+    op.rows = (__nv_bfloat16*)ar.take_bytes((size_t)S * m * n * 2);
+    op.rexp = ar.take<int>(m);
+    k_row_exp<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(m, n, A, lda, op.rexp);
+    dim3 g((unsigned)((m + 31) / 32), (unsigned)((n + 31) / 32)), b(32, 8);
+    k_slice_rows<<<g, b, 0, s>>>(m, n, A, lda, op.rexp, S, op.rows);
+    note_launches(1);
+    RR_TRY(check_launch("emu_prepare rows"));
+  }
+  if (cols) {
+    op.cols = (__nv_bfloat16*)ar.take_bytes((size_t)S * m * n * 2);
+    op.cexp = ar.take<int>(n);
+    k_col_exp<<<(unsigned)n, 512, 0, s>>>(m, A, lda, op.cexp);
+    dim3 g((unsigned)std::min<int64_t>((m + 255) / 256, 1024), (unsigned)n);
+    k_slice_cols<<<g, 256, 0, s>>>(m, n, A, lda, op.cexp, S, op.cols);
+    note_launches(1);
+    RR_TRY(check_launch("emu_prepare cols"));
+  }
+  return RR_OK;
+}
+
+// C (FP64, M x N) = A X (trans = 0, M = m, K = n) or A^T X (trans = 1, M = n,
+// K = m), X FP64 K x N column-major; mem: emu_block_bytes(K, N, S).
+rr_status emu_gemm(cudaStream_t s, const EmuOperator& op, int trans, int64_t N, const double* X,
+                   int64_t ldx, double* C, int64_t ldc, void* mem) {
+  const int S = op.S;
+  const int64_t M = trans ? op.n : op.m, K = trans ? op.m : op.n;
+  const __nv_bfloat16* As = trans ? op.cols : op.rows;
+  const int* rexp = trans ? op.cexp : op.rexp;
+  if (!As || N <= 0 || N > 256) return RR_ERR_ARG;
+  Arena ar(mem, emu_block_bytes(K, N, S));
+  __nv_bfloat16* T = (__nv_bfloat16*)ar.take_bytes((size_t)S * K * N * 2);
+  int* xe = ar.take<int>(N);
+  double* cs = ar.take<double>((size_t)S * N);
+  k_col_exp<<<(unsigned)N, 512, 0, s>>>(K, X, ldx, xe);
+  dim3 g((unsigned)std::min<int64_t>((K + 255) / 256, 1024), (unsigned)N);
+  k_slice_cols<<<g, 256, 0, s>>>(K, N, X, ldx, xe, S, T);
+  k_col_scales<<<(unsigned)((N * S + 255) / 256), 256, 0, s>>>(N, S, xe, cs);
+  dim3 gz((unsigned)std::min<int64_t>((M + 255) / 256, 1024), (unsigned)N);
+  k_zero_f64<<<gz, 256, 0, s>>>(M, N, C, ldc);
+  note_launches(3);
+  RR_TRY(check_launch("emu_gemm slices"));
+  const int64_t lda = trans ? op.m : op.n;  // K-contiguous leading dimension of the A slices
+  const int per_call = (2 * N <= 256) ? 2 : 1;
+  for (int p = 1; p <= S; ++p) {
+    const int qmax = S + 1 - p;
+    for (int q0 = 1; q0 <= qmax; q0 += per_call) {
+      const int nq = (q0 + per_call - 1 <= qmax) ? per_call : 1;
+      const __nv_bfloat16* Ap = As + (size_t)(p - 1) * op.m * op.n;
+      const __nv_bfloat16* Tq = T + (size_t)(q0 - 1) * K * N;  // slices q0.. are contiguous (ld K)
+      RR_TRY(gemm_bf16_tc_emu(M, N * nq, K, Ap, lda, Tq, K, C, ldc, rexp, kBeta * p,
+                              cs + (size_t)(q0 - 1) * N, (int)N, 4096, s));
+    }
+  }
+  return RR_OK;
+}
+
+}  // namespace rr
+
+using namespace rr;
+
+extern "C" size_t rr_gemm_f64_emulated_workspace_size(int32_t trans, int64_t M, int64_t N, int64_t K,
+                                                      int32_t slices) {
+  const int64_t m = trans ? K : M, n = trans ? M : K;
+  return emu_operator_bytes(m, n, slices, !trans, trans != 0) + emu_block_bytes(K, N, slices) + 512;
+}
+
+extern "C" rr_status rr_gemm_f64_emulated(int32_t trans, int64_t M, int64_t N, int64_t K, const double* A,
+                                          int64_t lda, const double* B, int64_t ldb, double* C,
+                                          int64_t ldc, int32_t slices, void* ws, size_t ws_bytes,
+                                          void* stream) {
+  if (M <= 0 || N <= 0 || N > 256 || K <= 0 || !A || !B || !C || ldb < K || ldc < M) return RR_ERR_ARG;
+  if (slices < 1 || slices > kMaxSlices) return RR_ERR_ARG;
+  if (trans ? lda < K : lda < M) return RR_ERR_ARG;
+  const int64_t m = trans ? K : M, n = trans ? M : K;
+  if (!ws || ws_bytes < rr_gemm_f64_emulated_workspace_size(trans, M, N, K, slices)) return RR_ERR_WORKSPACE;
+  if (n % 8 || m % 8) return RR_ERR_ARG;  // 16-byte row strides of the BF16 slices (TMA)
+  cudaStream_t s = as_stream(stream);
+  EmuOperator op;
+  const size_t ob = emu_operator_bytes(m, n, slices, !trans, trans != 0);
+  RR_TRY(emu_prepare(s, A, m, n, lda, slices, op, ws, !trans, trans != 0));
+  return emu_gemm(s, op, trans, N, B, ldb, C, ldc, (char*)ws + align_up(ob));
+}

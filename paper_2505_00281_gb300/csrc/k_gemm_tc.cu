@@ -136,6 +136,14 @@ struct TcArgs {
   int64_t ldr;
   const double* coef;
   int atomic;      // 1: K-split, add into C
+  // FP64-emulation epilogue (C64 != nullptr): C64[row, col % nb] +=
+  //   v * 2^(rexp[row] - rshift) * cscale[col]   (v: exact integer-valued FP32)
+  double* C64;
+  int64_t ldc64;
+  const int* rexp;
+  int rshift;
+  const double* cscale;
+  int nb;
 };
 
 __global__ void __launch_bounds__(128, 1) k_gemm_bf16_tc(const __grid_constant__ CUtensorMap tmA,
@@ -237,7 +245,26 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16_tc(const __grid_constant__
     __syncwarp();
     ready = __all_sync(0xffffffffu, ready) && *(volatile int*)&g_tc_error == 0;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ready) {
+    if (ready && a.C64) {
+      const int64_t row = m0 + warp * 32 + lane;
+      const double rs = row < a.M ? ldexp(1.0, a.rexp[row] - a.rshift) : 0.0;
+      for (int c0 = 0; c0 < a.npad; c0 += 32) {
+        uint32_t r[32];
+        tmem_ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+        if (row < a.M) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int64_t col = c0 + j;
+            if (col < a.N) {
+              const double v = (double)__uint_as_float(r[j]) * rs * a.cscale[col];
+              double* dst = a.C64 + row + (col % a.nb) * a.ldc64;
+              if (a.atomic) atomicAdd(dst, v);
+              else *dst += v;
+            }
+          }
+        }
+      }
+    } else if (ready) {
       const int64_t row = m0 + warp * 32 + lane;
       for (int c0 = 0; c0 < a.npad; c0 += 32) {
         uint32_t r[32];
@@ -286,6 +313,17 @@ int& gemm_force_simt() {
   return v;
 }
 
+// Raise the kernel's dynamic shared-memory limit once (outside any stream
+// capture: rr_batch_svd calls this before it starts capturing).
+rr_status tc_prepare_attributes() {
+  static bool done = false;
+  if (!done) {
+    RR_CUDA(cudaFuncSetAttribute(k_gemm_bf16_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    done = true;
+  }
+  return RR_OK;
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -326,9 +364,39 @@ static bool make_map(CUtensorMap* m, const void* base, int64_t inner, int64_t ou
   return r == CUDA_SUCCESS;
 }
 
+struct TcEmu {
+  double* C64;
+  int64_t ldc64;
+  const int* rexp;
+  int rshift;
+  const double* cscale;
+  int nb;
+  int max_kchunk;  // K elements one CTA may accumulate before its FP64 update
+};
+
+static rr_status gemm_bf16_tc_impl(int64_t M, int64_t N, int64_t K, const __nv_bfloat16* A, int64_t lda,
+                                   const __nv_bfloat16* B, int64_t ldb, float* C, int64_t ldc,
+                                   const double* R, int64_t ldr, const double* coef, const TcEmu* emu,
+                                   cudaStream_t s);
+
 rr_status gemm_bf16_tc(int64_t M, int64_t N, int64_t K, const __nv_bfloat16* A, int64_t lda,
                        const __nv_bfloat16* B, int64_t ldb, float* C, int64_t ldc, const double* R,
                        int64_t ldr, const double* coef, cudaStream_t s) {
+  return gemm_bf16_tc_impl(M, N, K, A, lda, B, ldb, C, ldc, R, ldr, coef, nullptr, s);
+}
+
+rr_status gemm_bf16_tc_emu(int64_t M, int64_t N, int64_t K, const __nv_bfloat16* A, int64_t lda,
+                           const __nv_bfloat16* B, int64_t ldb, double* C64, int64_t ldc64,
+                           const int* rexp, int rshift, const double* cscale, int nb, int max_kchunk,
+                           cudaStream_t s) {
+  TcEmu e{C64, ldc64, rexp, rshift, cscale, nb, max_kchunk};
+  return gemm_bf16_tc_impl(M, N, K, A, lda, B, ldb, nullptr, 0, nullptr, 0, nullptr, &e, s);
+}
+
+static rr_status gemm_bf16_tc_impl(int64_t M, int64_t N, int64_t K, const __nv_bfloat16* A, int64_t lda,
+                                   const __nv_bfloat16* B, int64_t ldb, float* C, int64_t ldc,
+                                   const double* R, int64_t ldr, const double* coef, const TcEmu* emu,
+                                   cudaStream_t s) {
   const int npad = (int)((N + 15) / 16 * 16);
   int tcols = 32;
   while (tcols < npad) tcols <<= 1;
@@ -344,14 +412,16 @@ rr_status gemm_bf16_tc(int64_t M, int64_t N, int64_t K, const __nv_bfloat16* A, 
     if (splits > nk) splits = nk;
     if (splits < 1) splits = 1;
   }
-  const int per = (nk + splits - 1) / splits;
+  int per = (nk + splits - 1) / splits;
+  if (emu && per * kBK > emu->max_kchunk) per = emu->max_kchunk / kBK;  // exactness of the FP32 sums
+  if (per < 1) return RR_ERR_ARG;
   splits = (nk + per - 1) / per;
   const uint32_t stage_bytes = kBM * kBK * 2 + (uint32_t)npad * kBK * 2;
   int stages = (int)((200 * 1024) / stage_bytes);
   if (stages > 8) stages = 8;
   if (stages < 2) return RR_ERR_ARG;
   const size_t smem = 1024 + (size_t)stages * stage_bytes + (2 * stages + 1) * sizeof(uint64_t);
-  RR_CUDA(cudaFuncSetAttribute(k_gemm_bf16_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  RR_TRY(tc_prepare_attributes());
   TcArgs a;
   a.M = M;
   a.N = N;
@@ -367,7 +437,13 @@ rr_status gemm_bf16_tc(int64_t M, int64_t N, int64_t K, const __nv_bfloat16* A, 
   a.ldr = ldr;
   a.coef = coef;
   a.atomic = splits > 1;
-  if (splits > 1) {
+  a.C64 = emu ? emu->C64 : nullptr;
+  a.ldc64 = emu ? emu->ldc64 : 0;
+  a.rexp = emu ? emu->rexp : nullptr;
+  a.rshift = emu ? emu->rshift : 0;
+  a.cscale = emu ? emu->cscale : nullptr;
+  a.nb = emu ? emu->nb : 1;
+  if (splits > 1 && !emu) {
     dim3 gi((unsigned)std::min<int64_t>((M + 255) / 256, 256), (unsigned)N);
     k_tc_init_c<<<gi, 256, 0, s>>>(M, N, C, ldc, R, ldr, coef);
     note_launches(1);

@@ -18,7 +18,7 @@ namespace rr {
 constexpr int kSmallThreads = 1024;
 // largest pencil side: the packed FP32 Cholesky factor must fit in shared
 // memory (b (b + 1) / 2 floats <= 227 KB)
-constexpr int kMaxPencil = 336;
+constexpr int kMaxPencil = 335;
 
 // Cholesky G = L L^T (lower), dropping column j when its pivot
 // L_jj^2 <= 64 u64 max_i G_ii (or is not positive).  A dropped index gets a
@@ -383,22 +383,25 @@ __global__ void __launch_bounds__(kSmallThreads) k_chol_inv_f32(int b, const dou
     __syncthreads();
   }
   // in-place inverse, last column first: column j of L^-1 from the already
-  // inverted trailing block: x = -(Linv[j+1:, j+1:] L[j+1:, j]) / L_jj
-  for (int j = b - 1; j >= 0; --j) {
-    const float ajj = 1.f / Ls[pk(j, j, b)];
-    // each thread computes one row i > j of the new column (reads old column j)
-    float acc[8];
-    int cnt = 0;
-    for (int i = j + 1 + tid; i < b && cnt < 8; i += kSmallThreads, ++cnt) {
-      float sum = 0.f;
-      for (int l = j + 1; l <= i; ++l) sum = fmaf(Ls[pk(i, l, b)], Ls[pk(l, j, b)], sum);
-      acc[cnt] = -sum * ajj;
+  // inverted trailing block, x = -(Linv[j+1:, j+1:] L[j+1:, j]) / L_jj; one
+  // warp per row, lanes split the dot product.  New values are staged in
+  // xbuf (the old column j is read by every row).
+  {
+    float* xbuf = Ls + (size_t)b * (b + 1) / 2;  // [b]
+    const int lane = tid & 31, warp = tid >> 5, nw = kSmallThreads / 32;
+    for (int j = b - 1; j >= 0; --j) {
+      const float ajj = 1.f / Ls[pk(j, j, b)];
+      for (int i = j + 1 + warp; i < b; i += nw) {
+        float sum = 0.f;
+        for (int l = j + 1 + lane; l <= i; l += 32) sum = fmaf(Ls[pk(i, l, b)], Ls[pk(l, j, b)], sum);
+        sum = warp_sum(sum);
+        if (lane == 0) xbuf[i] = -sum * ajj;
+      }
+      __syncthreads();
+      for (int i = j + 1 + tid; i < b; i += kSmallThreads) Ls[pk(i, j, b)] = xbuf[i];
+      if (tid == 0) Ls[pk(j, j, b)] = ajj;
+      __syncthreads();
     }
-    __syncthreads();
-    cnt = 0;
-    for (int i = j + 1 + tid; i < b && cnt < 8; i += kSmallThreads, ++cnt) Ls[pk(i, j, b)] = acc[cnt];
-    if (tid == 0) Ls[pk(j, j, b)] = ajj;
-    __syncthreads();
   }
   // W0 = (L^-1)^T, dropped columns zero
   for (int e = tid; e < b * b; e += kSmallThreads) {
@@ -441,13 +444,17 @@ __global__ void __launch_bounds__(kBJThreads) k_block_jacobi(int r, int cpad, in
                                                              int ldm, T* __restrict__ V, int ldv, T tol,
                                                              int max_sweeps, int* __restrict__ rot,
                                                              GridBarrier* bar, int* err,
-                                                             int* __restrict__ sweeps_out) {
+                                                             int* __restrict__ sweeps_out,
+                                                             const T* __restrict__ floor_ptr) {
   extern __shared__ unsigned char smem_raw[];
   T* Ms = reinterpret_cast<T*>(smem_raw);   // [2w][r]
   T* Vs = Ms + (size_t)2 * w * r;           // [2w][cpad]
   const int P = gridDim.x, g = blockIdx.x, nblk = 2 * P;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kBJThreads / 32;
   const int w2 = 2 * w;
+  // columns whose squared norm is below the floor (rounding-level directions)
+  // count as converged against everything
+  const T nfloor = floor_ptr ? *floor_ptr : T(0);
   __shared__ int s_rot;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
@@ -485,7 +492,7 @@ __global__ void __launch_bounds__(kBJThreads) k_block_jacobi(int r, int cpad, in
           al = warp_sum(al);
           be = warp_sum(be);
           ga = warp_sum(ga);
-          if (ga == T(0) || fabs(ga) <= tol * sqrt(al * be)) continue;
+          if (ga == T(0) || fabs(ga) <= tol * sqrt(fmax(al, nfloor) * fmax(be, nfloor))) continue;
           T zeta = (be - al) / (T(2) * ga);
           T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
           T cs = T(1) / sqrt(T(1) + t * t), sn = cs * t;
@@ -611,7 +618,7 @@ static bool carve_pencil(Arena& ar, int b1, int b2, PencilWs& w) {
   w.M = ar.take<double>(rc);
   w.Mp = ar.take<double>(rc);
   w.sig = ar.take<double>(cp);
-  w.mu = ar.take<double>(1);
+  w.mu = ar.take<double>(2);
   w.L32 = ar.take<float>(bb);
   w.Li32 = ar.take<float>(bb);
   w.M32 = ar.take<float>(rc);
@@ -632,29 +639,51 @@ static bool carve_pencil(Arena& ar, int b1, int b2, PencilWs& w) {
 // W <- W (I - E/2 + 3/8 E^2), E = W^T G W - I, whose error squares per step.
 static void whiten(cudaStream_t s, int b, const double* G, PencilWs& w, int* dropped, double* Wout) {
   const int g1 = (b * b + 255) / 256;
-  const size_t sm = (size_t)b * (b + 1) / 2 * sizeof(float);
+  const size_t sm = ((size_t)b * (b + 1) / 2 + b) * sizeof(float);
   if (sm > 48 * 1024)
     cudaFuncSetAttribute(k_chol_inv_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_chol_inv_f32<<<1, kSmallThreads, sm, s>>>(b, G, b, dropped, w.W1);
-  // step 1: E = W0^T G W0 - I, F = I - E/2 + 3/8 E^2, W1 = W0 F
-  gemm_small(s, 0, 0, b, b, b, 1.0, G, b, w.W1, b, 0.0, w.T, b);
-  gemm_small(s, 1, 0, b, b, b, 1.0, w.W1, b, w.T, b, 0.0, w.E, b);
-  k_whiten_corr<<<g1, 256, 0, s>>>(b, w.E, nullptr, dropped, nullptr, 0);
-  gemm_small(s, 0, 0, b, b, b, 1.0, w.E, b, w.E, b, 0.0, w.E2, b);
-  k_whiten_corr<<<g1, 256, 0, s>>>(b, w.E, w.E2, dropped, w.F, 1);
-  gemm_small(s, 0, 0, b, b, b, 1.0, w.W1, b, w.F, b, 0.0, w.W2, b);
-  // step 2: E = W1^T G W1 - I, W = W1 (I - E/2)
-  gemm_small(s, 0, 0, b, b, b, 1.0, G, b, w.W2, b, 0.0, w.T, b);
-  gemm_small(s, 1, 0, b, b, b, 1.0, w.W2, b, w.T, b, 0.0, w.E, b);
-  k_whiten_corr<<<g1, 256, 0, s>>>(b, w.E, nullptr, dropped, nullptr, 0);
-  k_whiten_corr<<<g1, 256, 0, s>>>(b, w.E, nullptr, dropped, w.F, 1);
-  gemm_small(s, 0, 0, b, b, b, 1.0, w.W2, b, w.F, b, 0.0, Wout, b);
-  note_launches(13);
+  // three refinement steps W <- W (I - E/2 + 3/8 E^2), E = W^T G W - I;
+  // each cubes the error (|E| ~ u32 cond(G) after the FP32 factorisation)
+  double* Wc = w.W1;
+  double* Wn = w.W2;
+  for (int it = 0; it < 3; ++it) {
+    gemm_small(s, 0, 0, b, b, b, 1.0, G, b, Wc, b, 0.0, w.T, b);
+    gemm_small(s, 1, 0, b, b, b, 1.0, Wc, b, w.T, b, 0.0, w.E, b);
+    k_whiten_corr<<<g1, 256, 0, s>>>(b, w.E, nullptr, dropped, nullptr, 0);
+    gemm_small(s, 0, 0, b, b, b, 1.0, w.E, b, w.E, b, 0.0, w.E2, b);
+    k_whiten_corr<<<g1, 256, 0, s>>>(b, w.E, w.E2, dropped, w.F, 1);
+    gemm_small(s, 0, 0, b, b, b, 1.0, Wc, b, w.F, b, 0.0, it == 2 ? Wout : Wn, b);
+    double* t = Wc;
+    Wc = Wn;
+    Wn = t;
+  }
+  note_launches(17);
+}
+
+// floor[0] = scale * max_j |M(:, j)|^2 (one block)
+template <typename T>
+__global__ void k_colnorm_floor(int r, int c, const T* __restrict__ M, int ldm, T scale, T* __restrict__ floor_out) {
+  __shared__ T red[32];
+  T mx = T(0);
+  for (int j = threadIdx.x >> 5; j < c; j += blockDim.x >> 5) {
+    T sacc = T(0);
+    for (int i = threadIdx.x & 31; i < r; i += 32) sacc = fma(M[i + (size_t)j * ldm], M[i + (size_t)j * ldm], sacc);
+    sacc = warp_sum(sacc);
+    mx = fmax(mx, sacc);
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    T m = T(0);
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m = fmax(m, red[k]);
+    *floor_out = scale * m;
+  }
 }
 
 template <typename T>
 static rr_status launch_bj(cudaStream_t s, int r, int cpad, int w, int P, T* M, T* V, T tol,
-                           int max_sweeps, PencilWs& ws) {
+                           int max_sweeps, PencilWs& ws, const T* floor_ptr = nullptr) {
   size_t smem = (size_t)2 * w * (r + cpad) * sizeof(T);
   const void* fn = (const void*)k_block_jacobi<T>;
   if (smem > 48 * 1024)
@@ -664,14 +693,15 @@ static rr_status launch_bj(cudaStream_t s, int r, int cpad, int w, int P, T* M, 
   int ld = r, ldv = cpad;
   if (P == 1) {
     k_block_jacobi<T><<<1, kBJThreads, smem, s>>>(r, cpad, w, M, ld, V, ldv, tol, max_sweeps, ws.rot,
-                                                  ws.bar, ws.err, ws.sweeps);
+                                                  ws.bar, ws.err, ws.sweeps, floor_ptr);
     return check_launch("block_jacobi");
   }
   int* rot = ws.rot;
   GridBarrier* bar = ws.bar;
   int* err = ws.err;
   int* sw = ws.sweeps;
-  void* args[] = {&r, &cpad, &w, &M, &ld, &V, &ldv, &tol, &max_sweeps, &rot, &bar, &err, &sw};
+  const T* fl = floor_ptr;
+  void* args[] = {&r, &cpad, &w, &M, &ld, &V, &ldv, &tol, &max_sweeps, &rot, &bar, &err, &sw, &fl};
   RR_CUDA(cudaLaunchCooperativeKernel(fn, dim3(P), dim3(kBJThreads), args, smem, s));
   note_launches(1);
   return RR_OK;
@@ -722,19 +752,22 @@ static void ns_orthonormalize(cudaStream_t s, int c, double* V, PencilWs& w) {
 
 // SVD of the r x c matrix C (FP64, ld r): on exit Mout (r x c) = C V with
 // orthogonal columns, Vout (c x c) orthogonal.  FP32 block one-sided Jacobi
-// to 1e-5 relative orthogonality, then FP64 polish made only of small
-// parallel GEMMs: V <- NS(V); N = C V; K = N^T N; rotate every pair by its
-// exact Jacobi angle at once (V <- V (I + Om + Om^2/2)); repeat.  Each polish
-// step squares the off-diagonal of K; two steps reach FP64 level.
+// (relative orthogonality 1e-6, column norms floored at 1e-10 of the largest
+// so rounding-level directions do not stall it), then an FP64 polish made
+// only of small parallel GEMMs: V <- NS(V); N = C V; K = N^T N; rotate every
+// pair by its exact Jacobi angle at once (V <- V (I + Om + Om^2/2)); three
+// times.  Each polish step roughly squares the relative off-diagonal of K.
 static rr_status jacobi_svd(cudaStream_t s, int r, int c, const double* C, PencilWs& w, double* Mout,
                             double* Vout) {
   int ww, P;
   const int cpad = bj_cpad(c, &ww, &P, 4, r);
   const int g = 256, gc = (c * c + 255) / 256;
   k_pad_copy<double, float><<<g, 256, 0, s>>>(r, c, cpad, C, r, w.M32, w.V32);
-  RR_TRY(launch_bj<float>(s, r, cpad, ww, P, w.M32, w.V32, 1e-5f, 20, w));
+  float* fl = (float*)(w.mu + 1);  // scratch slot after mu
+  k_colnorm_floor<float><<<1, 1024, 0, s>>>(r, cpad, w.M32, r, 1e-10f, fl);
+  RR_TRY(launch_bj<float>(s, r, cpad, ww, P, w.M32, w.V32, 1e-6f, 15, w, fl));
   k_v32_to_64<<<g, 256, 0, s>>>(c, cpad, w.V32, w.V);
-  for (int it = 0; it < 2; ++it) {
+  for (int it = 0; it < 3; ++it) {
     ns_orthonormalize(s, c, w.V, w);
     gemm_small(s, 0, 0, r, c, c, 1.0, C, r, w.V, c, 0.0, w.Mp, r);          // N = C V
     gemm_small(s, 1, 0, c, c, r, 1.0, w.Mp, r, w.Mp, r, 0.0, w.Vp, c);      // K = N^T N

@@ -36,7 +36,14 @@ struct Op {
   void* lo_row;  // K-major operand of A X (row-major copy), dtype dt
   int32_t dt;    // basis dtype
   int32_t wt;    // product output type (F32, or F64 when dt is F64)
+  // FP64-accurate products on the tensor cores (dense operator, refinement)
+  bool has_emu;
+  EmuOperator emu;
+  void* emu_mem;
+  void* emu_blk;
 };
+
+constexpr int kEmuSlices = 8;
 
 static size_t dsz(int32_t t) { return dtype_size(t); }
 
@@ -135,15 +142,21 @@ static rr_status apply_lowp_T(const Op& op, int64_t b, const void* X, int64_t ld
   return rr_gemm_lowp(op.dt, op.n, b, op.m, op.lo_col, op.m, X, ldx, (float*)out, ldo, R, ldr, coef, s);
 }
 
-// FP64-accurate products with the given operator
+// FP64-accurate products with the given operator: on the tensor cores by
+// error-free slicing when the operator was sliced (mixed precision with
+// refinement), otherwise FP64 arithmetic (the all-FP64 mode, CSR operators).
 static rr_status apply_f64(const Op& op, int64_t b, const double* X, int64_t ldx, double* out,
                            int64_t ldo, cudaStream_t s) {
-  if (op.kind == RR_DENSE) return rr_gemm_f64(0, op.m, b, op.n, op.A, op.lda, X, ldx, out, ldo, 0, s);
+  if (op.kind == RR_DENSE) {
+    if (op.has_emu && b <= 256) return emu_gemm(s, op.emu, 0, b, X, ldx, out, ldo, op.emu_blk);
+    return rr_gemm_f64(0, op.m, b, op.n, op.A, op.lda, X, ldx, out, ldo, 0, s);
+  }
   return rr_csr_spmm(op.n, b, op.rp, op.ci, op.va, RR_F64, X, ldx, RR_F64, out, ldo, s);
 }
 static rr_status apply_f64_T(const Op& op, int64_t b, const double* X, int64_t ldx, double* out,
                              int64_t ldo, cudaStream_t s) {
   if (op.kind != RR_DENSE) return RR_ERR_ARG;
+  if (op.has_emu && op.emu.cols && b <= 256) return emu_gemm(s, op.emu, 1, b, X, ldx, out, ldo, op.emu_blk);
   return rr_gemm_f64(1, op.n, b, op.m, op.A, op.lda, X, ldx, out, ldo, 0, s);
 }
 
@@ -226,7 +239,7 @@ static rr_status check_params(const rr_params* p, int64_t rows_min) {
   if (p->basis != RR_F64 && p->basis != RR_F32 && p->basis != RR_BF16) return RR_ERR_ARG;
   // the projected pencil (2 block with refinement) must fit the small solver
   const bool refine = p->refine != 0 && p->basis != RR_F64;
-  if ((refine ? 2 * p->block : p->block) > 336) return RR_ERR_ARG;
+  if ((refine ? 2 * p->block : p->block) > 335) return RR_ERR_ARG;
   return RR_OK;
 }
 
@@ -289,13 +302,32 @@ static void make_op(const rr_operator* A, int32_t dt, Op& op) {
   op.lo_col = op.lo_row = nullptr;
   op.dt = dt;
   op.wt = dt == RR_F64 ? RR_F64 : RR_F32;
+  op.has_emu = false;
+  op.emu_mem = op.emu_blk = nullptr;
 }
 
-// The operator copies live at the front of the workspace.
-static void carve_op(Arena& ar, Op& op, bool symmetric) {
+// The operator copies live at the front of the workspace: the low-precision
+// copies for the filter and, with refinement, the BF16 slices of the FP64
+// operator for the FP64-accurate products (row-scaled for A X, and
+// column-scaled for A^T Y when the operator is not symmetric).
+static void carve_op(Arena& ar, Op& op, bool symmetric, bool refine, int64_t b) {
   if (op.kind != RR_DENSE || op.dt == RR_F64) return;
   op.lo_col = ar.take_bytes(op.m * op.n * dsz(op.dt));
   op.lo_row = symmetric ? op.lo_col : ar.take_bytes(op.m * op.n * dsz(op.dt));
+  if (refine && op.m % 8 == 0 && op.n % 8 == 0 && b <= 256) {
+    op.has_emu = true;
+    op.emu_mem = ar.take_bytes(emu_operator_bytes(op.m, op.n, kEmuSlices, true, !symmetric));
+    op.emu_blk = ar.take_bytes(emu_block_bytes(op.m > op.n ? op.m : op.n, b, kEmuSlices));
+  }
+}
+
+static rr_status prepare_op(const Op& op_in, Op& op, bool symmetric, cudaStream_t s) {
+  (void)op_in;
+  if (op.lo_col)
+    RR_TRY(rr_cast_operator(op.m, op.n, op.A, op.lda, op.dt, op.lo_col, symmetric ? nullptr : op.lo_row, s));
+  if (op.has_emu)
+    RR_TRY(emu_prepare(s, op.A, op.m, op.n, op.lda, kEmuSlices, op.emu, op.emu_mem, true, !symmetric));
+  return RR_OK;
 }
 
 // FP64 residual of the first kk triplets: res = sqrt(|A v - s u|^2 + |A^T u - s v|^2) / s
@@ -321,7 +353,7 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
   const bool refine = p->refine != 0 && dt != RR_F64;
   const int ph1 = refine ? (p->phase1_sweeps > 0 ? p->phase1_sweeps : 1) : p->max_sweeps;
   Arena ar(ws, ws_bytes);
-  carve_op(ar, op, false);
+  carve_op(ar, op, false, refine, b);
   SvdBufs w;
   carve_svd(ar, op, b, refine, w);
   double* v0buf = batch_mode ? ar.take<double>(n * b) : nullptr;
@@ -334,8 +366,8 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
   const size_t ds = dsz(dt);
   (void)ds;
 
-  // one-time operator casts (counted in the solve time)
-  if (op.lo_col) STAGE(RR_STAGE_OTHER, rr_cast_operator(m, n, op.A, op.lda, dt, op.lo_col, op.lo_row, s));
+  // one-time operator casts and slicing (counted in the solve time)
+  STAGE(RR_STAGE_OTHER, prepare_op(op, op, false, s));
 
   // a1: start block
   const double* v0 = p->v0;
@@ -487,9 +519,9 @@ static size_t svd_ws(const rr_operator* A, const rr_params* p, bool batch) {
   Op op;
   make_op(A, p->basis, op);
   Arena ar(nullptr, 0);
-  carve_op(ar, op, false);
-  SvdBufs w;
   const bool refine = p->refine != 0 && p->basis != RR_F64;
+  carve_op(ar, op, false, refine, p->block);
+  SvdBufs w;
   carve_svd(ar, op, p->block, refine, w);
   if (batch) ar.take<double>(op.n * p->block);
   return ar.off + 4096;
@@ -593,7 +625,7 @@ static rr_status eig_run(const rr_operator* Aop, const rr_params* p, double* the
   if (cheb && op.kind != RR_CSR) return RR_ERR_ARG;
   if (!cheb && p->which != RR_LARGEST) return RR_ERR_ARG;
   Arena ar(ws, ws_bytes);
-  carve_op(ar, op, true);
+  carve_op(ar, op, true, refine, b);
   EigBufs w;
   carve_eig(ar, op, b, refine, w);
   if (ar.overflow) return RR_ERR_WORKSPACE;
@@ -601,7 +633,7 @@ static rr_status eig_run(const rr_operator* Aop, const rr_params* p, double* the
   prof.on = p->profile != 0;
   prof.s = s;
   RR_CUDA(cudaMemsetAsync(w.c.hess_ws, 0, 512, s));
-  if (op.lo_col) STAGE(RR_STAGE_OTHER, rr_cast_operator(n, n, op.A, op.lda, dt, op.lo_col, nullptr, s));
+  STAGE(RR_STAGE_OTHER, prepare_op(op, op, true, s));
 
   double lo = p->bounds[0], up = p->bounds[1];
   if (cheb && !(lo < up)) {
@@ -787,9 +819,9 @@ static size_t eig_ws(const rr_operator* A, const rr_params* p) {
   Op op;
   make_op(A, p->basis, op);
   Arena ar(nullptr, 0);
-  carve_op(ar, op, true);
-  EigBufs w;
   const bool refine = p->refine != 0 && p->basis != RR_F64;
+  carve_op(ar, op, true, refine, p->block);
+  EigBufs w;
   carve_eig(ar, op, p->block, refine, w);
   return ar.off + 4096;
 }
@@ -862,6 +894,7 @@ extern "C" rr_status rr_batch_svd(int32_t count, const rr_operator* A, const rr_
     RR_TRY(check_params(p, A[i].n));
   }
   if (ws_bytes < rr_batch_workspace_size(count, A, p)) return RR_ERR_WORKSPACE;
+  RR_TRY(tc_prepare_attributes());
   cudaStream_t s = as_stream(stream);
   const int NS = 16;
   // Capture on a private stream (the legacy default stream cannot be
@@ -938,7 +971,7 @@ extern "C" rr_status rr_batch_svd(int32_t count, const rr_operator* A, const rr_
     Op op;
     make_op(&A[i], p->basis, op);
     Arena ar((char*)ws + offs[i], align_up(svd_ws(&A[i], p, true), 4096));
-    carve_op(ar, op, false);
+    carve_op(ar, op, false, p->refine != 0 && p->basis != RR_F64, p->block);
     SvdBufs w;
     carve_svd(ar, op, p->block, p->refine != 0 && p->basis != RR_F64, w);
     std::vector<double> hres(p->k);

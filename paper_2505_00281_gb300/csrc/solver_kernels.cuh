@@ -37,5 +37,22 @@ rr_status hessenberg_ex(int32_t arith, int64_t n, int64_t k, void* W, int64_t ld
 rr_status sub_lowrank_f32(cudaStream_t s, int64_t n, int64_t b, int64_t p, const double* X, int64_t ldx,
                           const double* K, int64_t ldk, float* T, int64_t ldt);
 rr_status tc_take_error(cudaStream_t s);
+rr_status tc_prepare_attributes();
+
+// FP64-accurate products on the tensor cores (k_f64emu.cu)
+struct EmuOperator {
+  int64_t m, n;
+  int S;
+  __nv_bfloat16* rows;  // S row-scaled slices, row-major (for A X)
+  int* rexp;
+  __nv_bfloat16* cols;  // S column-scaled slices, column-major (for A^T Y)
+  int* cexp;
+};
+size_t emu_operator_bytes(int64_t m, int64_t n, int S, bool rows, bool cols);
+size_t emu_block_bytes(int64_t K, int64_t N, int S);
+rr_status emu_prepare(cudaStream_t s, const double* A, int64_t m, int64_t n, int64_t lda, int S,
+                      EmuOperator& op, void* mem, bool rows, bool cols);
+rr_status emu_gemm(cudaStream_t s, const EmuOperator& op, int trans, int64_t N, const double* X,
+                   int64_t ldx, double* C, int64_t ldc, void* mem);
 rr_status vec_scale(cudaStream_t s, int64_t n, double alpha, const double* a, double* d);
 }  // namespace rr

@@ -96,6 +96,30 @@ def test_gemm_f64_both_layouts(rr):
     assert np.all(np.abs(host(C2) - A.T @ B2) <= 2 * bound)
 
 
+@pytest.mark.parametrize("trans,M,N,K", [(0, 1000, 64, 512), (1, 512, 128, 16384), (0, 16384, 128, 4096),
+                                         (1, 4096, 128, 16384), (0, 256, 40, 1024)])
+def test_gemm_f64_emulated_matches_fp64(rr, trans, M, N, K):
+    """Error-free BF16 slicing on the tensor cores.  8 slices of 6 bits carry
+    every entry to 2^-49 of its row's (op(A)) or column's (B) largest |entry|;
+    the slice products are exact, so the error is that representation error
+    plus FP64 rounding of the summation:
+      |err| <= 2^-48 (rowmax_i sum_j |b_jc| + colmax_c sum_j |a_ij|) + 64 u64 (|A||B|)_ic."""
+    rng = np.random.default_rng(M + N + K + trans)
+    A = rng.standard_normal((K, M) if trans else (M, K)) * np.exp(rng.uniform(-3, 3, (1, M) if trans else (M, 1)))
+    B = rng.standard_normal((K, N)) * np.exp(rng.uniform(-2, 2, (1, N)))
+    C = rr.rr_gemm_f64_emulated(trans, dev(A), dev(B))
+    Aop = A.T if trans else A
+    ref = Aop @ B
+    rowmax = np.abs(Aop).max(axis=1)[:, None]
+    colmax = np.abs(B).max(axis=0)[None, :]
+    bound = 2.0 ** -48 * (rowmax * np.abs(B).sum(axis=0)[None, :] + colmax * np.abs(Aop).sum(axis=1)[:, None]) \
+        + 64 * U53 * (np.abs(Aop) @ np.abs(B))
+    err = np.abs(host(C) - ref)
+    assert np.all(err <= bound), (err / bound).max()
+    # and it is far more accurate than the FP32-accumulated product
+    assert np.max(err / (np.abs(Aop) @ np.abs(B))) < 1e-12
+
+
 # ---------------------------------------------------------------- a4 (Algorithm 8)
 @pytest.mark.parametrize("n,k", [(1000, 48), (20000, 32), (77, 77), (5, 3)])
 def test_hessenberg_bitexact_fp32(rr, n, k):
