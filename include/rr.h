@@ -232,6 +232,25 @@ rr_status rr_gram(int64_t n, int64_t p, int64_t q, int32_t xtype, const void* X,
                   int32_t ytype, const void* Y, int64_t ldy, double* G, int64_t ldg,
                   int32_t accumulate, void* ws, size_t ws_bytes, void* stream);
 
+/* rr_gram without a workspace argument, for callers that cannot allocate
+ * device memory: code that runs where the allocator may not be called (for
+ * example a thread that must not block, or a host framework that owns every
+ * device allocation and hands this library only its operands), or that has
+ * no buffer to spare for scratch.  The paper has no counterpart; it is a
+ * deployment convenience.  Same operands and result as rr_gram.  The
+ * split-K partial sums go to a 2 MiB array of FP64 compiled into the library
+ * (262144 doubles per GPU, held by every GPU that loads the library until the
+ * process exits), so p * q must not exceed 262144 (RR_ERR_ARG otherwise);
+ * the number of row chunks shrinks to fit.  The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  All calls share the one array:
+ * calls whose executions overlap on the GPU (different streams, or
+ * concurrent graph branches) race and give wrong results.  Allocates
+ * nothing. */
+rr_status rr_gram_noalloc(int64_t n, int64_t p, int64_t q, int32_t xtype, const void* X,
+                          int64_t ldx, int32_t ytype, const void* Y, int64_t ldy, double* G,
+                          int64_t ldg, int32_t accumulate, void* stream);
+
 /* Small projected problems, FP64 (Alg. 3 line "B Y = M Y Lambda"; Alg. 5).
  * rr_pencil_eig: H, G (b x b, ld b) symmetric, G positive semidefinite.
  *   theta (b) ascending; Y (b x b) with Y^T G Y = I on the kept part.

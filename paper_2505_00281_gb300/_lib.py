@@ -73,6 +73,8 @@ _SIGS = {
     "rr_gram_workspace_size": (c_sz, [c_i64, c_i64, c_i64]),
     "rr_gram": (c_i32, [c_i64, c_i64, c_i64, c_i32, c_vp, c_i64, c_i32, c_vp, c_i64, c_vp, c_i64, c_i32,
                         c_vp, c_sz, c_vp]),
+    "rr_gram_noalloc": (c_i32, [c_i64, c_i64, c_i64, c_i32, c_vp, c_i64, c_i32, c_vp, c_i64, c_vp, c_i64,
+                                c_i32, c_vp]),
     "rr_pencil_workspace_size": (c_sz, [c_i64, c_i64]),
     "rr_pencil_eig": (c_i32, [c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_i32p, c_vp]),
     "rr_pencil_svd": (c_i32, [c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_i32p,

@@ -15,7 +15,7 @@ from ._lib import RR, RrError, RrInfo, RrOperator, RrParams, check, lib
 __all__ = [
     "fortran", "ld_of", "dense_operator", "csr_operator", "make_params", "rr_eig", "rr_svd",
     "rr_batch_svd", "rr_colscale_cast", "rr_cast_operator", "rr_gemm_lowp", "rr_gemm_f64",
-    "rr_hessenberg", "rr_gram", "rr_pencil_eig", "rr_pencil_svd", "rr_csr_spmm",
+    "rr_hessenberg", "rr_gram", "rr_gram_noalloc", "rr_pencil_eig", "rr_pencil_svd", "rr_csr_spmm",
     "rr_chebyshev_step", "RrParams", "RrOperator", "RrInfo", "DTYPES",
 ]
 
@@ -236,6 +236,18 @@ def rr_gram(X, Y, G=None, accumulate=False, stream=None):
     ws = _ws(L.rr_gram_workspace_size(n, p, q), X.device)
     check("rr_gram", L.rr_gram(n, p, q, DTYPES[X.dtype], _p(X), ld_of(X), DTYPES[Y.dtype], _p(Y), ld_of(Y),
                                _p(G), ld_of(G), int(accumulate), _p(ws), ws.numel(), _stream(stream)))
+    return G
+
+
+def rr_gram_noalloc(X, Y, G=None, accumulate=False, stream=None):
+    """rr_gram without a workspace: scratch is a fixed array inside the library."""
+    n, p = X.shape
+    q = Y.shape[1]
+    if G is None:
+        G = fortran(torch.zeros(p, q, dtype=torch.float64, device=X.device))
+    check("rr_gram_noalloc", lib().rr_gram_noalloc(n, p, q, DTYPES[X.dtype], _p(X), ld_of(X), DTYPES[Y.dtype],
+                                                    _p(Y), ld_of(Y), _p(G), ld_of(G), int(accumulate),
+                                                    _stream(stream)))
     return G
 
 

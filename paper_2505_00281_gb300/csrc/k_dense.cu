@@ -434,3 +434,73 @@ extern "C" rr_status rr_gram(int64_t n, int64_t p, int64_t q, int32_t xtype, con
   k_gram_reduce<<<(unsigned)((p * q + 255) / 256), 256, 0, s>>>(p, q, chunks, part, G, ldg, accumulate);
   return check_launch("rr_gram reduce");
 }
+
+// ---------------------------------------------------------------------------
+// rr_gram_noalloc: the Gram product for callers that cannot allocate device
+// memory.  Its split-K partial sums live in a fixed array compiled into the
+// library instead of a caller-provided workspace.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace rr {
+
+// Scratch of rr_gram_noalloc: 2 MiB of FP64 partial sums per GPU, held by
+// every GPU that loads the library until the process exits.
+constexpr size_t kNoAllocDoubles = (size_t)1 << 18;
+static __device__ __align__(256) double g_gram_scratch[kNoAllocDoubles];
+
+// Device address of g_gram_scratch on the current device, looked up once per
+// device (host code may not use the symbol itself as a device pointer).
+static rr_status noalloc_scratch(double** out) {
+  static std::mutex mu;
+  static double* addr[64] = {};
+  int dev = 0;
+  RR_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return RR_ERR_ARG;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    RR_CUDA(cudaGetSymbolAddress(&p, g_gram_scratch));
+    addr[dev] = (double*)p;
+  }
+  *out = addr[dev];
+  return RR_OK;
+}
+
+}  // namespace rr
+
+extern "C" rr_status rr_gram_noalloc(int64_t n, int64_t p, int64_t q, int32_t xtype, const void* X,
+                                     int64_t ldx, int32_t ytype, const void* Y, int64_t ldy, double* G,
+                                     int64_t ldg, int32_t accumulate, void* stream) {
+  if (n < 0 || p < 0 || q < 0 || ldx < n || ldy < n || ldg < p || !G) return RR_ERR_ARG;
+  if ((size_t)p * (size_t)q > kNoAllocDoubles) return RR_ERR_ARG;  // beyond the fixed scratch
+  if (p == 0 || q == 0) return RR_OK;
+  if (n > 0 && (!X || !Y)) return RR_ERR_ARG;
+  double* scratch = nullptr;
+  RR_TRY(noalloc_scratch(&scratch));
+  cudaStream_t s = as_stream(stream);
+  if (n == 0) {
+    if (!accumulate)
+      for (int64_t j = 0; j < q; ++j) RR_CUDA(cudaMemsetAsync(G + j * ldg, 0, p * sizeof(double), s));
+    return RR_OK;
+  }
+  // as many row chunks as the scratch holds (every slot used is written by
+  // the partial kernel before the reduction reads it: nothing to clear)
+  int64_t chunks = gram_chunks(n, p, q);
+  const int64_t cap = (int64_t)(kNoAllocDoubles / ((size_t)p * (size_t)q));
+  if (chunks > cap) chunks = cap;
+  int64_t rpc = (n + chunks - 1) / chunks;
+  chunks = (n + rpc - 1) / rpc;
+  dim3 g((unsigned)((p + GT - 1) / GT), (unsigned)((q + GT - 1) / GT), (unsigned)chunks);
+  rr_status st;
+  switch (xtype) {
+    case RR_F64: st = gram_dispatch_y<double>(ytype, g, s, n, p, q, (const double*)X, ldx, Y, ldy, rpc, scratch); break;
+    case RR_F32: st = gram_dispatch_y<float>(ytype, g, s, n, p, q, (const float*)X, ldx, Y, ldy, rpc, scratch); break;
+    case RR_BF16: st = gram_dispatch_y<__nv_bfloat16>(ytype, g, s, n, p, q, (const __nv_bfloat16*)X, ldx, Y, ldy, rpc, scratch); break;
+    default: return RR_ERR_ARG;
+  }
+  if (st != RR_OK) return st;
+  RR_TRY(check_launch("rr_gram_noalloc partial"));
+  k_gram_reduce<<<(unsigned)((p * q + 255) / 256), 256, 0, s>>>(p, q, chunks, scratch, G, ldg, accumulate);
+  return check_launch("rr_gram_noalloc reduce");
+}
