@@ -158,6 +158,21 @@ def run_reference(args):
     return 0
 
 
+# --------------------------------------------------------------------------- ranks
+def aggregate(seconds: float, converged: int, dist=None, device=None):
+    """Whole-job numbers across ranks: the slowest rank's time and the total
+    converged pairs (every rank solves its own instance; no data exchange)."""
+    if dist is None:
+        return seconds, converged
+    import torch
+
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    c = torch.tensor([float(converged)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(c.item())
+
+
 # --------------------------------------------------------------------------- GPU arm
 def stage_roofline(info, peaks, src):
     """Achieved rate of each stage from its CUDA-event time and its
@@ -271,13 +286,7 @@ def run_ours(args):
     clk = clocks.stop()
     launches = L.rr_kernel_launches() - launches0
     t = ev0.elapsed_time(ev1) / 1e3
-    if dist:
-        tt = torch.tensor([t, conv], dtype=torch.float64, device=dev)
-        tmax = tt[:1].clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        csum = tt[1:].clone()
-        dist.all_reduce(csum, op=dist.ReduceOp.SUM)
-        t, conv = float(tmax.item()), int(csum.item())
+    t, conv = aggregate(t, conv, dist, dev)
     value = conv / t
 
     # correctness of the timed result against the closed form (sampled outputs)
@@ -333,13 +342,7 @@ def run_ours(args):
     e1.record(stream)
     barrier()
     t2 = e0.elapsed_time(e1) / 1e3
-    if dist:
-        tt = torch.tensor([t2], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t2 = float(tt.item())
-        cc = torch.tensor([conv2], dtype=torch.float64, device=dev)
-        dist.all_reduce(cc, op=dist.ReduceOp.SUM)
-        conv2 = int(cc.item())
+    t2, conv2 = aggregate(t2, conv2, dist, dev)
     e2e = {"value": conv2 / t2, "unit": "pairs/s", "h2d_bytes_per_step": (M * N + N * B) * 8,
            "d2h_bytes_per_step": (K + M * K + N * K) * 8}
 
