@@ -379,6 +379,48 @@ def run_ours(args):
     return 0
 
 
+def run_stage(args):
+    """Single-stage driver for profiling (ncu -k on one kernel): runs one
+    stage of the bench workload twice (warm-up, then the profiled call)."""
+    import torch
+
+    from paper_2505_00281_gb300 import build
+
+    build.build()
+    import paper_2505_00281_gb300 as rr
+
+    rng = np.random.default_rng(7)
+    b = args.b
+
+    def dev(a, dt=None):
+        t = torch.from_numpy(np.asfortranarray(a)).cuda()
+        return rr.fortran(t.to(dt) if dt is not None else t)
+
+    if args.stage == "pencil":
+        A = rng.standard_normal((3 * b, 2 * b))
+        U = rng.uniform(0, 1, (3 * b, b))
+        V = rng.uniform(0, 1, (2 * b, b))
+        B, Gu, Gv = dev(U.T @ A @ V), dev(U.T @ U), dev(V.T @ V)
+        for _ in range(2):
+            rr.rr_pencil_svd(B, Gu, Gv)
+    elif args.stage == "hessenberg":
+        W0 = torch.randn(b, M, device="cuda", dtype=torch.float32).t()  # M x b column-major
+        for _ in range(2):
+            rr.rr_hessenberg(W0.clone(), qtype=torch.bfloat16)
+    elif args.stage in ("gemm", "f64emu"):
+        A = torch.randn(N, M, device="cuda", dtype=torch.float64).t()   # M x N column-major
+        X = rr.fortran(torch.randn(N, B, device="cuda", dtype=torch.float64))
+        for _ in range(2):
+            if args.stage == "f64emu":
+                rr.rr_gemm_f64_emulated(0, A, X)
+            else:
+                Ab = A.to(torch.bfloat16)
+                rr.rr_gemm_lowp(2, M, B, N, Ab.t().contiguous(), N, X.to(torch.bfloat16), N)
+    torch.cuda.synchronize()
+    print("stage", args.stage, "done")
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -387,7 +429,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--stage", choices=["pencil", "hessenberg", "gemm", "f64emu"],
+                    help="run one stage of the workload (profiling driver)")
+    ap.add_argument("--b", type=int, default=256, help="pencil size for --stage pencil")
     args = ap.parse_args()
+    if args.stage:
+        return run_stage(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

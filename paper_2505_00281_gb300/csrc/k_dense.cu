@@ -324,30 +324,30 @@ namespace rr {
 constexpr int GT = 32;      // output tile GT x GT
 constexpr int GROWS = 32;   // rows per smem stage
 
-template <typename TX, typename TY>
+template <typename TX, typename TY, typename TA = double>
 __global__ void __launch_bounds__(256) k_gram_partial(
     int64_t n, int64_t p, int64_t q, const TX* __restrict__ X, int64_t ldx,
     const TY* __restrict__ Y, int64_t ldy, int64_t rows_per_chunk, double* __restrict__ part) {
-  __shared__ double Xs[GROWS][GT + 1];
-  __shared__ double Ys[GROWS][GT + 1];
+  __shared__ TA Xs[GROWS][GT + 1];
+  __shared__ TA Ys[GROWS][GT + 1];
   int64_t p0 = (int64_t)blockIdx.x * GT, q0 = (int64_t)blockIdx.y * GT;
   int64_t r0 = (int64_t)blockIdx.z * rows_per_chunk;
   int64_t r1 = r0 + rows_per_chunk < n ? r0 + rows_per_chunk : n;
   int tid = threadIdx.x;
   int ti = tid % 16, tj = tid / 16;  // 2 x 2 outputs per thread
-  double acc[2][2] = {};
+  TA acc[2][2] = {};
   for (int64_t rs = r0; rs < r1; rs += GROWS) {
     for (int e = tid; e < GROWS * GT; e += 256) {
       int rr_ = e % GROWS, c = e / GROWS;
       int64_t row = rs + rr_;
-      Xs[rr_][c] = (row < r1 && p0 + c < p) ? Ld<TX>::f64(X + row + (p0 + c) * ldx) : 0.0;
-      Ys[rr_][c] = (row < r1 && q0 + c < q) ? Ld<TY>::f64(Y + row + (q0 + c) * ldy) : 0.0;
+      Xs[rr_][c] = (row < r1 && p0 + c < p) ? (TA)Ld<TX>::f64(X + row + (p0 + c) * ldx) : TA(0);
+      Ys[rr_][c] = (row < r1 && q0 + c < q) ? (TA)Ld<TY>::f64(Y + row + (q0 + c) * ldy) : TA(0);
     }
     __syncthreads();
 #pragma unroll 8
     for (int rr_ = 0; rr_ < GROWS; ++rr_) {
-      double x0 = Xs[rr_][ti], x1 = Xs[rr_][ti + 16];
-      double y0 = Ys[rr_][tj], y1 = Ys[rr_][tj + 16];
+      TA x0 = Xs[rr_][ti], x1 = Xs[rr_][ti + 16];
+      TA y0 = Ys[rr_][tj], y1 = Ys[rr_][tj + 16];
       acc[0][0] = fma(x0, y0, acc[0][0]);
       acc[0][1] = fma(x0, y1, acc[0][1]);
       acc[1][0] = fma(x1, y0, acc[1][0]);
@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(256) k_gram_partial(
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
       int64_t i = p0 + ti + 16 * a, j = q0 + tj + 16 * b;
-      if (i < p && j < q) out[i + j * p] = acc[a][b];
+      if (i < p && j < q) out[i + j * p] = (double)acc[a][b];
     }
 }
 
@@ -401,6 +401,25 @@ static rr_status gram_dispatch_y(int32_t ytype, dim3 g, cudaStream_t s, int64_t 
     default: return RR_ERR_ARG;
   }
   return RR_OK;
+}
+}  // namespace rr
+
+namespace rr {
+// G = X^T Y with FP32 products and FP32 accumulation per row chunk (chunk
+// sums added in FP64): for X FP64 (read as FP32) and Y FP32, where FP32
+// accuracy is all the caller needs.
+rr_status gram_f32acc(cudaStream_t s, int64_t n, int64_t p, int64_t q, const double* X, int64_t ldx,
+                      const float* Y, int64_t ldy, double* G, int64_t ldg, void* ws, size_t ws_bytes) {
+  if (p == 0 || q == 0) return RR_OK;
+  int64_t chunks = gram_chunks(n, p, q);
+  if (ws_bytes < (size_t)chunks * p * q * sizeof(double) || !ws) return RR_ERR_WORKSPACE;
+  int64_t rpc = (n + chunks - 1) / chunks;
+  chunks = (n + rpc - 1) / rpc;
+  dim3 g((unsigned)((p + GT - 1) / GT), (unsigned)((q + GT - 1) / GT), (unsigned)chunks);
+  k_gram_partial<double, float, float><<<g, 256, 0, s>>>(n, p, q, X, ldx, Y, ldy, rpc, (double*)ws);
+  RR_TRY(check_launch("gram_f32acc partial"));
+  k_gram_reduce<<<(unsigned)((p * q + 255) / 256), 256, 0, s>>>(p, q, chunks, (const double*)ws, G, ldg, 0);
+  return check_launch("gram_f32acc reduce");
 }
 }  // namespace rr
 

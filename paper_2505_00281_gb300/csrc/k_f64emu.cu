@@ -5,7 +5,8 @@
 //
 // Slicing: every row of A (for A X) or column of A (for A^T Y) and every
 // column of X is scaled by a power of two 2^e so its entries lie in (-1, 1),
-// then split into S integer slices of beta = 6 bits:
+// then split into S integer slices of beta = 6 bits (balanced digits of the
+// rounded fixed-point value, computed with integer operations only):
 //   x = 2^e (sum_{p=1..S} s_p 2^(-beta p) + r),  |s_1| <= 64, |s_p| <= 32,
 //   |r| <= 2^(-beta S - 1);
 // each s_p is an integer exactly representable in BF16.  The product of two
@@ -31,47 +32,69 @@ bool gemm_bf16_tc_supported(int64_t M, int64_t N, int64_t K, int64_t lda, int64_
 constexpr int kBeta = 6;
 constexpr int kMaxSlices = 10;
 
-__device__ __forceinline__ int exp_above(double mx) {
-  if (!(mx > 0.0)) return 0;
-  int e;
-  frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1)  ->  mx < 2^e
-  return e;
+// Exponent e with |x| < 2^e from the IEEE bit pattern (integer work only):
+// for a normal x = 1.f 2^(E-1023), e = E - 1022; zero and subnormals -> -1100.
+__device__ __forceinline__ int exp_bits(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((u >> 52) & 0x7FF);
+  return E == 0 ? -1100 : E - 1022;
 }
 
 // exponent of the largest |entry| of every row of a column-major matrix
+// (max over the entries' exponents = exponent of the largest entry)
 __global__ void k_row_exp(int64_t m, int64_t n, const double* __restrict__ A, int64_t lda,
                           int* __restrict__ e) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= m) return;
-  double mx = 0.0;
-  for (int64_t j = 0; j < n; ++j) mx = fmax(mx, fabs(A[i + j * lda]));
-  e[i] = exp_above(mx);
+  int mx = -1100;
+  for (int64_t j = 0; j < n; ++j) mx = max(mx, exp_bits(A[i + j * lda]));
+  e[i] = mx;
 }
 
 // exponent of the largest |entry| of every column (one block per column)
 __global__ void k_col_exp(int64_t m, const double* __restrict__ A, int64_t lda, int* __restrict__ e) {
   const int64_t j = blockIdx.x;
-  double mx = 0.0;
-  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) mx = fmax(mx, fabs(A[i + j * lda]));
-  __shared__ double sm[32];
-  mx = warp_max(mx);
+  int mx = -1100;
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) mx = max(mx, exp_bits(A[i + j * lda]));
+  __shared__ int sm[32];
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = mx;
   __syncthreads();
   if (threadIdx.x < 32) {
-    mx = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0.0;
-    mx = warp_max(mx);
-    if (threadIdx.x == 0) e[j] = exp_above(mx);
+    mx = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : -1100;
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (threadIdx.x == 0) e[j] = mx;
   }
 }
 
+// Error-free slicing of x relative to 2^e (|x| < 2^e) in integer arithmetic:
+// F = round(|x| 2^(6S - e)) (a fixed-point integer below 2^(6S) + 1), then
+// balanced base-64 digits from the least significant end (each in
+// [-32, 31]; the leading one in [-32, 64]), signed like x:
+//   x = 2^e sum_{p=1..S} out[p-1] 2^(-6p) + r,  |r| <= 2^(e - 6S - 1).
 __device__ __forceinline__ void slice_value(double x, int e, int S, float* out) {
-  double r = ldexp(x, -e);
-  for (int p = 0; p < S; ++p) {
-    r = ldexp(r, kBeta);
-    const double t = rint(r);
-    out[p] = (float)t;
-    r -= t;
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((u >> 52) & 0x7FF);
+  long long F = 0;
+  if (E != 0) {
+    const unsigned long long M = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    // |x| 2^(6S - e) = M 2^(E - 1075 + 6S - e)
+    const int sh = E - 1075 + kBeta * S - e;  // <= 6S - 53 - 1 (|x| < 2^e)
+    if (sh >= 0) F = (long long)(M << sh);
+    else if (sh > -63) F = (long long)((M + (1ull << (-sh - 1))) >> (-sh));
   }
+  for (int p = S - 1; p >= 1; --p) {
+    long long d = F & 63;
+    F >>= 6;
+    if (d >= 32) {
+      d -= 64;
+      F += 1;
+    }
+    out[p] = (float)d;
+  }
+  out[0] = (float)F;
+  if (u >> 63)
+    for (int p = 0; p < S; ++p) out[p] = -out[p];
 }
 
 // column-scaled slices, same layout as the input: out[p] (m x n, ld m)
@@ -90,7 +113,7 @@ __global__ void k_slice_cols(int64_t m, int64_t n, const double* __restrict__ A,
 // K-major operand of A X.  32 x 32 tiles through shared memory.
 __global__ void k_slice_rows(int64_t m, int64_t n, const double* __restrict__ A, int64_t lda,
                              const int* __restrict__ rexp, int S, __nv_bfloat16* __restrict__ out) {
-  __shared__ float tile[kMaxSlices][32][33];
+  __shared__ __nv_bfloat16 tile[kMaxSlices][32][34];
   const int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
   for (int r = ty; r < 32; r += 8) {
@@ -101,13 +124,13 @@ __global__ void k_slice_rows(int64_t m, int64_t n, const double* __restrict__ A,
     } else {
       for (int p = 0; p < S; ++p) sl[p] = 0.f;
     }
-    for (int p = 0; p < S; ++p) tile[p][r][tx] = sl[p];
+    for (int p = 0; p < S; ++p) tile[p][r][tx] = __float2bfloat16_rn(sl[p]);
   }
   __syncthreads();
   for (int r = ty; r < 32; r += 8) {
     const int64_t i = i0 + r, j = j0 + tx;
     if (i < m && j < n)
-      for (int p = 0; p < S; ++p) out[(size_t)p * m * n + i * n + j] = __float2bfloat16_rn(tile[p][tx][r]);
+      for (int p = 0; p < S; ++p) out[(size_t)p * m * n + i * n + j] = tile[p][tx][r];
   }
 }
 

@@ -2,13 +2,15 @@
 // the paper's inner-product-free basis step.  Its output equals P^T L of
 // row-pivoted LU.
 //
-// GB300 design: one cooperative launch over all SMs.  Each CTA owns a
-// contiguous slab of rows.  Per column j:
+// GB300 design: one cooperative launch; each CTA owns a contiguous slab of
+// rows (kept in shared memory when it fits).  Per column j:
 //   (a) every CTA finds the largest |W(r, j)| in its slab (first index on
-//       ties) and publishes (value, row) plus that row's trailing entries;
-//   (b) one grid barrier (bounded wait);
-//   (c) every CTA reduces the published candidates itself (no second
-//       barrier) and gets the pivot r, W(r, j) and the weights W(r, j+1:k);
+//       ties) and publishes (value, row) plus that row's trailing entries,
+//       then releases its flag (step j + 1);
+//   (b) every CTA acquires all flags (bounded wait) — an all-gather, not a
+//       barrier followed by reads;
+//   (c) every CTA reduces the published candidates itself and gets the
+//       pivot r, W(r, j) and the weights W(r, j+1:k);
 //   (d) every CTA scales its part of column j by 1/W(r, j) and applies the
 //       rank-1 update to its rows of the trailing columns.
 // The candidate buffers are double-buffered by column parity so no CTA can
@@ -29,7 +31,19 @@ struct HessWs {
   int* pidx;    // [2][G] candidate row
   T* prow;      // [2][G][k] candidate row's entries
   T* pcolmax;   // [G][k] per-slab column inf-norms
+  int* flags;   // [G] column steps published by each CTA (j + 1 after column j)
 };
+
+// Publish/await the per-column candidates: CTA g releases flags[g] = step once
+// its candidate is written; readers acquire every flag before reading.
+__device__ __forceinline__ void flag_release(int* f, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(f), "r"(v) : "memory");
+}
+__device__ __forceinline__ int flag_acquire(const int* f) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+  return v;
+}
 
 template <typename T> __device__ __forceinline__ T ld_cg(const T* p);
 template <> __device__ __forceinline__ float ld_cg<float>(const float* p) { return __ldcg(p); }
@@ -57,10 +71,13 @@ __device__ __forceinline__ void argmax_merge(T& av, int& ai, T bv, int bi) {
 
 constexpr int kHessThreads = 512;
 
+// The kernel works on "Wv": the CTA's slab of W, either in shared memory
+// (slab mode: rows r0..r1 of all k columns, column-major with ld = rows per
+// CTA; loaded once, written back at the end) or W itself in global memory.
 template <typename T, typename TO>
 __global__ void __launch_bounds__(kHessThreads) k_hessenberg(
     int64_t n, int k, T* __restrict__ W, int64_t ldw, TO* __restrict__ Q, int64_t ldq,
-    int* __restrict__ piv, T tol, HessWs<T> ws) {
+    int* __restrict__ piv, T tol, HessWs<T> ws, int slab) {
   const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = kHessThreads / 32;
   const int64_t rpc = (n + G - 1) / G;
@@ -71,6 +88,18 @@ __global__ void __launch_bounds__(kHessThreads) k_hessenberg(
   extern __shared__ unsigned char smem_raw[];
   T* thr = reinterpret_cast<T*>(smem_raw);   // [k]
   T* wgt = thr + k;                          // [k]
+  T* slabp = wgt + k;                        // [k][rpc] in slab mode
+  // element (r, c) of the working block (r a global row of this CTA)
+  T* const Wv = slab ? slabp - r0 : W;
+  const int64_t ldv = slab ? rpc : ldw;
+  if (slab) {
+    const int64_t total = (int64_t)k * nr;
+    for (int64_t e = tid; e < total; e += kHessThreads) {
+      const int64_t c = e / nr, r = r0 + e % nr;
+      Wv[r + c * ldv] = W[r + c * ldw];
+    }
+    __syncthreads();
+  }
   __shared__ T red_v[32];
   __shared__ int red_i[32];
   __shared__ T s_qr;
@@ -79,7 +108,7 @@ __global__ void __launch_bounds__(kHessThreads) k_hessenberg(
   // ---- column inf-norms on entry (relative skip threshold) ----
   for (int c = warp; c < k; c += nwarps) {
     T m = T(0);
-    for (int64_t r = r0 + lane; r < r1; r += 32) m = fmax(m, fabs(W[r + c * ldw]));
+    for (int64_t r = r0 + lane; r < r1; r += 32) m = fmax(m, fabs(Wv[r + c * ldv]));
     m = warp_max(m);
     if (lane == 0) ws.pcolmax[(size_t)g * k + c] = m;
   }
@@ -97,7 +126,7 @@ __global__ void __launch_bounds__(kHessThreads) k_hessenberg(
     T bv = T(-1);
     int bi = INT_MAX;
     for (int64_t r = r0 + tid; r < r1; r += kHessThreads) {
-      T v = fabs(W[r + j * ldw]);
+      T v = fabs(Wv[r + j * ldv]);
       if (v > bv) {  // strictly greater: first index wins within a thread
         bv = v;
         bi = (int)r;
@@ -126,7 +155,7 @@ __global__ void __launch_bounds__(kHessThreads) k_hessenberg(
       if (lane == 0) {
         s_r = bi;
         ws.pidx[par * G + g] = bi;
-        ws.pval[par * G + g] = (bi != INT_MAX) ? W[bi + j * ldw] : T(0);
+        ws.pval[par * G + g] = (bi != INT_MAX) ? Wv[bi + j * ldv] : T(0);
       }
     }
     __syncthreads();
@@ -134,10 +163,30 @@ __global__ void __launch_bounds__(kHessThreads) k_hessenberg(
       const int rloc = s_r;
       T* prow = ws.prow + ((size_t)par * G + g) * k;
       for (int c = j + 1 + tid; c < k; c += kHessThreads)
-        prow[c] = (rloc != INT_MAX) ? W[rloc + c * ldw] : T(0);
+        prow[c] = (rloc != INT_MAX) ? Wv[rloc + c * ldv] : T(0);
     }
-    // (b)
-    if (!grid_barrier(ws.bar, G, ws.err)) return;
+    // (b) publish this CTA's candidate, then wait for every CTA's (bounded)
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      flag_release(ws.flags + g, j + 1);
+    }
+    if (warp == 0) {
+      const uint64_t t0 = global_timer_ns();
+      bool ok = true;
+      for (int h = lane; h < G && ok; h += 32) {
+        while (flag_acquire(ws.flags + h) < j + 1) {
+          if (*(volatile int*)ws.err != 0 || global_timer_ns() - t0 > kWaitLimitNs) {
+            atomicCAS(ws.err, 0, (int)RR_ERR_TIMEOUT);
+            ok = false;
+            break;
+          }
+        }
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    if (*(volatile int*)ws.err != 0) return;
     // (c) global winner, computed redundantly by every CTA
     if (warp == 0) {
       T av = T(-1);
@@ -179,26 +228,28 @@ __global__ void __launch_bounds__(kHessThreads) k_hessenberg(
       const T* prow = ws.prow + ((size_t)par * G + s_win) * k;
       for (int c = j + 1 + tid; c < k; c += kHessThreads) wgt[c] = ld_cg(prow + c);
       for (int64_t r = r0 + tid; r < r1; r += kHessThreads)
-        W[r + j * ldw] = rn_div(W[r + j * ldw], qr);
+        Wv[r + j * ldv] = rn_div(Wv[r + j * ldv], qr);
       __syncthreads();
       const int64_t ncols = k - j - 1;
       const int64_t total = ncols * nr;
       for (int64_t e = tid; e < total; e += kHessThreads) {
         const int64_t c = j + 1 + e / nr;
         const int64_t r = r0 + e % nr;
-        W[r + c * ldw] = rn_sub(W[r + c * ldw], rn_mul(wgt[c], W[r + j * ldw]));
+        Wv[r + c * ldv] = rn_sub(Wv[r + c * ldv], rn_mul(wgt[c], Wv[r + j * ldv]));
       }
     } else {
-      for (int64_t r = r0 + tid; r < r1; r += kHessThreads) W[r + j * ldw] = T(0);
+      for (int64_t r = r0 + tid; r < r1; r += kHessThreads) Wv[r + j * ldv] = T(0);
     }
     __syncthreads();
   }
-  // write the result in the requested storage type
-  if ((void*)Q != (void*)W) {
+  // write the result in the requested storage type (and W itself in slab mode)
+  {
     const int64_t total = (int64_t)k * nr;
     for (int64_t e = tid; e < total; e += kHessThreads) {
       const int64_t c = e / nr, r = r0 + e % nr;
-      Q[r + c * ldq] = from_f64<TO>((double)W[r + c * ldw]);
+      const T v = Wv[r + c * ldv];
+      if (slab) W[r + c * ldw] = v;
+      if ((void*)Q != (void*)W) Q[r + c * ldq] = from_f64<TO>((double)v);
     }
   }
 }
@@ -222,17 +273,35 @@ static size_t hess_ws_bytes(int64_t k, int G) {
   b += align_up(2 * (size_t)G * sizeof(int));
   b += align_up(2 * (size_t)G * k * sizeof(T));
   b += align_up((size_t)G * k * sizeof(T));
+  b += align_up((size_t)G * sizeof(int));
   return b;
 }
 
 template <typename T, typename TO>
 static rr_status hess_launch(int64_t n, int64_t k, T* W, int64_t ldw, TO* Q, int64_t ldq, int* piv,
                              double tol, void* ws, size_t ws_bytes, cudaStream_t s, int max_grid) {
-  size_t smem = 2 * (size_t)k * sizeof(T);
   const void* fn = (const void*)k_hessenberg<T, TO>;
+  // Grid: about 256 rows per CTA (fewer CTAs make the per-column barrier and
+  // candidate reduction cheaper), more CTAs if a slab would not fit in shared
+  // memory; slab mode when the CTA's rows of all k columns fit in 200 KB.
+  const size_t kSlabLimit = 200 * 1024;
+  int G;
+  int slab = 0;
+  if (max_grid == 1) {
+    G = 1;
+  } else {
+    int64_t g = (n + 255) / 256;
+    const int64_t fit = (int64_t)(kSlabLimit / ((size_t)k * sizeof(T)));  // rows per CTA that fit
+    if (fit > 0 && (n + g - 1) / g > fit) g = (n + fit - 1) / fit;
+    if (g > num_sms()) g = num_sms();
+    if (g < 1) g = 1;
+    G = (int)g;
+  }
+  const int64_t rpc = (n + G - 1) / G;
+  if ((size_t)rpc * k * sizeof(T) <= kSlabLimit) slab = 1;
+  size_t smem = 2 * (size_t)k * sizeof(T) + (slab ? (size_t)rpc * k * sizeof(T) : 0);
   if (smem > 48 * 1024)
     RR_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int G = max_grid == 1 ? 1 : hess_grid(n, smem, fn);
   if (ws_bytes < hess_ws_bytes<T>(k, G) || !ws) return RR_ERR_WORKSPACE;
   Arena ar(ws, ws_bytes);
   HessWs<T> h;
@@ -242,14 +311,16 @@ static rr_status hess_launch(int64_t n, int64_t k, T* W, int64_t ldw, TO* Q, int
   h.pidx = ar.take<int>(2 * (size_t)G);
   h.prow = ar.take<T>(2 * (size_t)G * k);
   h.pcolmax = ar.take<T>((size_t)G * k);
+  h.flags = ar.take<int>(G);
   RR_CUDA(cudaMemsetAsync(ws, 0, 512, s));  // err + barrier
+  RR_CUDA(cudaMemsetAsync(h.flags, 0, (size_t)G * sizeof(int), s));
   T t = tol > 0 ? (T)tol : (T)(4.0 * (double)k * (sizeof(T) == 4 ? 0x1p-23 : 0x1p-52));
   int kk = (int)k;
-  void* args[] = {&n, &kk, &W, &ldw, &Q, &ldq, &piv, &t, &h};
+  void* args[] = {&n, &kk, &W, &ldw, &Q, &ldq, &piv, &t, &h, &slab};
   if (G == 1) {
     // a single CTA never waits on another one: plain launch (graph-capturable,
     // safe to run concurrently with other work)
-    k_hessenberg<T, TO><<<1, kHessThreads, smem, s>>>(n, kk, W, ldw, Q, ldq, piv, t, h);
+    k_hessenberg<T, TO><<<1, kHessThreads, smem, s>>>(n, kk, W, ldw, Q, ldq, piv, t, h, slab);
     return check_launch("rr_hessenberg");
   }
   RR_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kHessThreads), args, smem, s));

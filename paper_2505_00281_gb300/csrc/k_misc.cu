@@ -10,30 +10,30 @@ namespace rr {
 
 // X (n x b, TO, ld ldx) = [X +] alpha * S (n x p, TS, ld lds) * Y (p x b FP64, ld ldy)
 constexpr int LBM = 64, LBN = 64, LBK = 16;
-template <typename TS, typename TO = double>
+template <typename TS, typename TO = double, typename TA = double>
 __global__ void __launch_bounds__(256) k_lift(int64_t n, int64_t b, int64_t p, const TS* __restrict__ S,
                                              int64_t lds, const double* __restrict__ Y, int64_t ldy,
                                              TO* __restrict__ X, int64_t ldx, int accum, double alpha = 1.0) {
-  __shared__ double Ss[LBK][LBM + 1];
-  __shared__ double Ys[LBK][LBN + 1];
+  __shared__ TA Ss[LBK][LBM + 1];
+  __shared__ TA Ys[LBK][LBN + 1];
   const int64_t m0 = (int64_t)blockIdx.x * LBM, n0 = (int64_t)blockIdx.y * LBN;
   const int tid = threadIdx.x, tm = tid % 16, tn = tid / 16;
-  double acc[4][4] = {};
+  TA acc[4][4] = {};
   for (int64_t k0 = 0; k0 < p; k0 += LBK) {
     for (int e = tid; e < LBK * LBM; e += 256) {
       int i = e % LBM, kk = e / LBM;
       int64_t gi = m0 + i, gk = k0 + kk;
-      Ss[kk][i] = (gi < n && gk < p) ? Ld<TS>::f64(S + gi + gk * lds) : 0.0;
+      Ss[kk][i] = (gi < n && gk < p) ? (TA)Ld<TS>::f64(S + gi + gk * lds) : TA(0);
     }
     for (int e = tid; e < LBK * LBN; e += 256) {
       int kk = e % LBK, j = e / LBK;
       int64_t gk = k0 + kk, gj = n0 + j;
-      Ys[kk][j] = (gk < p && gj < b) ? Y[gk + gj * ldy] : 0.0;
+      Ys[kk][j] = (gk < p && gj < b) ? (TA)Y[gk + gj * ldy] : TA(0);
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < LBK; ++kk) {
-      double a[4], c[4];
+      TA a[4], c[4];
 #pragma unroll
       for (int r = 0; r < 4; ++r) a[r] = Ss[kk][tm + 16 * r];
 #pragma unroll
@@ -53,19 +53,19 @@ __global__ void __launch_bounds__(256) k_lift(int64_t n, int64_t b, int64_t p, c
     for (int r = 0; r < 4; ++r) {
       int64_t i = m0 + tm + 16 * r;
       if (i >= n) continue;
-      double v = alpha * acc[r][q];
+      double v = alpha * (double)acc[r][q];
       if (accum) v += (double)X[i + j * ldx];
       X[i + j * ldx] = (TO)v;
     }
   }
 }
 
-// T (n x b, FP32) -= X (n x p, FP64) * K (p x b)
+// T (n x b, FP32) -= X (n x p, FP64) * K (p x b), in FP32 arithmetic
 rr_status sub_lowrank_f32(cudaStream_t s, int64_t n, int64_t b, int64_t p, const double* X, int64_t ldx,
                           const double* K, int64_t ldk, float* T, int64_t ldt) {
   if (n == 0 || b == 0 || p == 0) return RR_OK;
   dim3 g((unsigned)((n + LBM - 1) / LBM), (unsigned)((b + LBN - 1) / LBN));
-  k_lift<double, float><<<g, 256, 0, s>>>(n, b, p, X, ldx, K, ldk, T, ldt, 1, -1.0);
+  k_lift<double, float, float><<<g, 256, 0, s>>>(n, b, p, X, ldx, K, ldk, T, ldt, 1, -1.0);
   return check_launch("sub_lowrank_f32");
 }
 

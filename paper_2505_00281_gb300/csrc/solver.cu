@@ -203,13 +203,14 @@ static rr_status gram(const Common& c, int64_t n, int64_t p, int64_t q, int32_t 
 }
 
 // Remove the span of the orthonormal FP64 Ritz vectors X (n x b) from the FP32
-// block T (n x b): T <- T - X (X^T T).  Keeps the correction blocks of the
-// refinement phase away from the converged directions, which the power /
-// Chebyshev steps would otherwise amplify until [X, D] is numerically
-// dependent.  K is b x b FP64 scratch.
+// block T (n x b): T <- T - X (X^T T), in FP32 arithmetic (the block is
+// stored in BF16 next; FP32 leaves components along X of ~1e-7 relative).
+// Keeps the correction blocks of the refinement phase away from the
+// converged directions, which the power / Chebyshev steps would otherwise
+// amplify until [X, D] is numerically dependent.  K is b x b FP64 scratch.
 static rr_status project_out(const Common& c, cudaStream_t s, int64_t n, int64_t b, const double* X,
                              int64_t ldx, float* T, int64_t ldt, double* K) {
-  RR_TRY(rr_gram(n, b, b, RR_F64, X, ldx, RR_F32, T, ldt, K, b, 0, c.gram_ws, c.gram_bytes, s));
+  RR_TRY(gram_f32acc(s, n, b, b, X, ldx, T, ldt, K, b, c.gram_ws, c.gram_bytes));
   return sub_lowrank_f32(s, n, b, b, X, ldx, K, b, T, ldt);
 }
 

@@ -78,7 +78,13 @@ def dense_svd_torch(m: int, n: int, sigma, seed: int, device: str = "cuda"):
 
     def _haar(r, c):
         x = torch.randn(r, c, generator=g, device=device, dtype=torch.float64)
-        q, rr = torch.linalg.qr(x)
+        try:
+            q, rr = torch.linalg.qr(x)
+        except RuntimeError:
+            # some environments (e.g. under a profiler) cannot load torch's
+            # device linear-algebra library: factor on the host instead
+            q, rr = torch.linalg.qr(x.cpu())
+            q, rr = q.to(device), rr.to(device)
         d = torch.sign(torch.diagonal(rr))
         d[d == 0] = 1
         return q * d
