@@ -400,9 +400,9 @@ def run_stage(args):
         A = rng.standard_normal((3 * b, 2 * b))
         U = rng.uniform(0, 1, (3 * b, b))
         V = rng.uniform(0, 1, (2 * b, b))
-        B, Gu, Gv = dev(U.T @ A @ V), dev(U.T @ U), dev(V.T @ V)
+        Bp, Gu, Gv = dev(U.T @ A @ V), dev(U.T @ U), dev(V.T @ V)
         for _ in range(2):
-            rr.rr_pencil_svd(B, Gu, Gv)
+            rr.rr_pencil_svd(Bp, Gu, Gv)
     elif args.stage == "hessenberg":
         W0 = torch.randn(b, M, device="cuda", dtype=torch.float32).t()  # M x b column-major
         for _ in range(2):
@@ -410,12 +410,13 @@ def run_stage(args):
     elif args.stage in ("gemm", "f64emu"):
         A = torch.randn(N, M, device="cuda", dtype=torch.float64).t()   # M x N column-major
         X = rr.fortran(torch.randn(N, B, device="cuda", dtype=torch.float64))
+        A_row = A.to(torch.bfloat16).contiguous()   # element (i, k) at i*N + k: K-major
+        Xb = rr.fortran(X.to(torch.bfloat16))
         for _ in range(2):
             if args.stage == "f64emu":
                 rr.rr_gemm_f64_emulated(0, A, X)
             else:
-                Ab = A.to(torch.bfloat16)
-                rr.rr_gemm_lowp(2, M, B, N, Ab.t().contiguous(), N, X.to(torch.bfloat16), N)
+                rr.rr_gemm_lowp(2, M, B, N, A_row, N, Xb, N)
     torch.cuda.synchronize()
     print("stage", args.stage, "done")
     return 0

@@ -74,6 +74,14 @@ constexpr int kHessThreads = 512;
 // The kernel works on "Wv": the CTA's slab of W, either in shared memory
 // (slab mode: rows r0..r1 of all k columns, column-major with ld = rows per
 // CTA; loaded once, written back at the end) or W itself in global memory.
+//
+// Look-ahead: after the pivot of column j is known, a CTA scales column j,
+// updates column j+1 only, picks and publishes its candidate for column j+1
+// (the candidate row's trailing entries get the same rank-1 update, computed
+// with the same operations), and only then applies the rank-1 update to
+// columns j+2.. — so that update overlaps the other CTAs' progress instead of
+// sitting on the per-column critical path.  Loop indices are 32-bit: lanes run
+// over rows (consecutive addresses), warps over columns.
 template <typename T, typename TO>
 __global__ void __launch_bounds__(kHessThreads) k_hessenberg(
     int64_t n, int k, T* __restrict__ W, int64_t ldw, TO* __restrict__ Q, int64_t ldq,
@@ -83,20 +91,21 @@ __global__ void __launch_bounds__(kHessThreads) k_hessenberg(
   const int64_t rpc = (n + G - 1) / G;
   const int64_t r0 = (int64_t)g * rpc;
   const int64_t r1 = r0 + rpc < n ? r0 + rpc : n;
-  const int64_t nr = r1 > r0 ? r1 - r0 : 0;
+  const int nr = r1 > r0 ? (int)(r1 - r0) : 0;
 
   extern __shared__ unsigned char smem_raw[];
   T* thr = reinterpret_cast<T*>(smem_raw);   // [k]
   T* wgt = thr + k;                          // [k]
   T* slabp = wgt + k;                        // [k][rpc] in slab mode
-  // element (r, c) of the working block (r a global row of this CTA)
-  T* const Wv = slab ? slabp - r0 : W;
+  // column c of this CTA's rows: col(c)[i], i = 0..nr-1 (row r0 + i)
+  T* const base = slab ? slabp : W + r0;
   const int64_t ldv = slab ? rpc : ldw;
+  auto col = [&](int c) -> T* { return base + (int64_t)c * ldv; };
   if (slab) {
-    const int64_t total = (int64_t)k * nr;
-    for (int64_t e = tid; e < total; e += kHessThreads) {
-      const int64_t c = e / nr, r = r0 + e % nr;
-      Wv[r + c * ldv] = W[r + c * ldw];
+    for (int c = warp; c < k; c += nwarps) {
+      const T* src = W + r0 + (int64_t)c * ldw;
+      T* dst = col(c);
+      for (int i = lane; i < nr; i += 32) dst[i] = src[i];
     }
     __syncthreads();
   }
@@ -108,7 +117,8 @@ __global__ void __launch_bounds__(kHessThreads) k_hessenberg(
   // ---- column inf-norms on entry (relative skip threshold) ----
   for (int c = warp; c < k; c += nwarps) {
     T m = T(0);
-    for (int64_t r = r0 + lane; r < r1; r += 32) m = fmax(m, fabs(Wv[r + c * ldv]));
+    const T* cc = col(c);
+    for (int i = lane; i < nr; i += 32) m = fmax(m, fabs(cc[i]));
     m = warp_max(m);
     if (lane == 0) ws.pcolmax[(size_t)g * k + c] = m;
   }
@@ -120,16 +130,20 @@ __global__ void __launch_bounds__(kHessThreads) k_hessenberg(
   }
   __syncthreads();
 
-  for (int j = 0; j < k; ++j) {
-    const int par = j & 1;
-    // (a) local argmax of |W(r, j)|
+  // local argmax of |column jc| over this CTA's rows, then publish the
+  // candidate (value, global row, row entries jc+1..k-1).  When upd is set,
+  // the row entries are published as they will be after the pending rank-1
+  // update by column jc-1 (weights wgt, multiplier column jc-1).
+  auto publish = [&](int jc, bool upd) {
+    const int par = jc & 1;
+    const T* cj = col(jc);
     T bv = T(-1);
     int bi = INT_MAX;
-    for (int64_t r = r0 + tid; r < r1; r += kHessThreads) {
-      T v = fabs(Wv[r + j * ldv]);
+    for (int i = tid; i < nr; i += kHessThreads) {
+      T v = fabs(cj[i]);
       if (v > bv) {  // strictly greater: first index wins within a thread
         bv = v;
-        bi = (int)r;
+        bi = i;
       }
     }
 #pragma unroll
@@ -154,23 +168,34 @@ __global__ void __launch_bounds__(kHessThreads) k_hessenberg(
       }
       if (lane == 0) {
         s_r = bi;
-        ws.pidx[par * G + g] = bi;
-        ws.pval[par * G + g] = (bi != INT_MAX) ? Wv[bi + j * ldv] : T(0);
+        ws.pidx[par * G + g] = (bi != INT_MAX) ? (int)(r0 + bi) : INT_MAX;
+        ws.pval[par * G + g] = (bi != INT_MAX) ? cj[bi] : T(0);
       }
     }
     __syncthreads();
-    {
-      const int rloc = s_r;
-      T* prow = ws.prow + ((size_t)par * G + g) * k;
-      for (int c = j + 1 + tid; c < k; c += kHessThreads)
-        prow[c] = (rloc != INT_MAX) ? Wv[rloc + c * ldv] : T(0);
+    const int rl = s_r;
+    T* prow = ws.prow + ((size_t)par * G + g) * k;
+    if (rl != INT_MAX) {
+      const T m = upd ? col(jc - 1)[rl] : T(0);
+      for (int c = jc + 1 + tid; c < k; c += kHessThreads) {
+        T v = col(c)[rl];
+        if (upd) v = rn_sub(v, rn_mul(wgt[c], m));
+        prow[c] = v;
+      }
+    } else {
+      for (int c = jc + 1 + tid; c < k; c += kHessThreads) prow[c] = T(0);
     }
-    // (b) publish this CTA's candidate, then wait for every CTA's (bounded)
     __syncthreads();
     if (tid == 0) {
       __threadfence();
-      flag_release(ws.flags + g, j + 1);
+      flag_release(ws.flags + g, jc + 1);
     }
+  };
+
+  publish(0, false);
+  for (int j = 0; j < k; ++j) {
+    const int par = j & 1;
+    // (b) wait for every CTA's candidate for column j (bounded)
     if (warp == 0) {
       const uint64_t t0 = global_timer_ns();
       bool ok = true;
@@ -222,34 +247,44 @@ __global__ void __launch_bounds__(kHessThreads) k_hessenberg(
       }
     }
     __syncthreads();
-    // (d) scale and rank-1 update of this slab
-    if (s_keep) {
+    const bool keep = s_keep != 0;
+    T* cj = col(j);
+    // (d) scale column j, update column j+1, publish column j+1's candidate,
+    // then update columns j+2..k-1
+    if (keep) {
       const T qr = s_qr;
       const T* prow = ws.prow + ((size_t)par * G + s_win) * k;
       for (int c = j + 1 + tid; c < k; c += kHessThreads) wgt[c] = ld_cg(prow + c);
-      for (int64_t r = r0 + tid; r < r1; r += kHessThreads)
-        Wv[r + j * ldv] = rn_div(Wv[r + j * ldv], qr);
+      for (int i = tid; i < nr; i += kHessThreads) cj[i] = rn_div(cj[i], qr);
       __syncthreads();
-      const int64_t ncols = k - j - 1;
-      const int64_t total = ncols * nr;
-      for (int64_t e = tid; e < total; e += kHessThreads) {
-        const int64_t c = j + 1 + e / nr;
-        const int64_t r = r0 + e % nr;
-        Wv[r + c * ldv] = rn_sub(Wv[r + c * ldv], rn_mul(wgt[c], Wv[r + j * ldv]));
+      if (j + 1 < k) {
+        T* cn = col(j + 1);
+        const T wn = wgt[j + 1];
+        for (int i = tid; i < nr; i += kHessThreads) cn[i] = rn_sub(cn[i], rn_mul(wn, cj[i]));
       }
     } else {
-      for (int64_t r = r0 + tid; r < r1; r += kHessThreads) Wv[r + j * ldv] = T(0);
+      for (int i = tid; i < nr; i += kHessThreads) cj[i] = T(0);
+    }
+    __syncthreads();
+    if (j + 1 < k) publish(j + 1, keep);
+    if (keep) {
+      for (int c = j + 2 + warp; c < k; c += nwarps) {
+        T* cc = col(c);
+        const T wc = wgt[c];
+        for (int i = lane; i < nr; i += 32) cc[i] = rn_sub(cc[i], rn_mul(wc, cj[i]));
+      }
     }
     __syncthreads();
   }
   // write the result in the requested storage type (and W itself in slab mode)
-  {
-    const int64_t total = (int64_t)k * nr;
-    for (int64_t e = tid; e < total; e += kHessThreads) {
-      const int64_t c = e / nr, r = r0 + e % nr;
-      const T v = Wv[r + c * ldv];
-      if (slab) W[r + c * ldw] = v;
-      if ((void*)Q != (void*)W) Q[r + c * ldq] = from_f64<TO>((double)v);
+  for (int c = warp; c < k; c += nwarps) {
+    const T* src = col(c);
+    T* dw = W + r0 + (int64_t)c * ldw;
+    TO* dq = Q + r0 + (int64_t)c * ldq;
+    for (int i = lane; i < nr; i += 32) {
+      const T v = src[i];
+      if (slab) dw[i] = v;
+      if ((void*)Q != (void*)W) dq[i] = from_f64<TO>((double)v);
     }
   }
 }

@@ -190,73 +190,6 @@ __global__ void k_zero_dropped(int b1, int b2, double* __restrict__ C, const int
   if (dr[i] || dc[j]) C[i + j * b1] = 0.0;
 }
 
-// One-sided Jacobi (Hestenes) on the columns of M (r x c): M <- M V with V
-// orthogonal, until every column pair is orthogonal to relative tol.
-// Parallel round-robin ordering: c'/2 disjoint pairs per round, one warp per
-// pair, rounds separated by __syncthreads.  A pair whose inner product is
-// exactly zero is never rotated, so exactly-zero (dropped) columns stay
-// decoupled.
-template <typename T>
-__global__ void __launch_bounds__(kSmallThreads) k_jacobi1s(int r, int c, T* __restrict__ M, int ldm,
-                                                            T* __restrict__ V, int ldv, int max_sweeps,
-                                                            T tol, int* __restrict__ sweeps_out) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kSmallThreads / 32;
-  for (int e = tid; e < c * c; e += kSmallThreads) {
-    int i = e % c, j = e / c;
-    V[i + j * ldv] = (i == j) ? T(1) : T(0);
-  }
-  const int cp = c + (c & 1);  // padded to even; index c (if odd) is a dummy
-  __shared__ int s_rot;
-  __syncthreads();
-  int sweep = 0;
-  for (; sweep < max_sweeps; ++sweep) {
-    if (tid == 0) s_rot = 0;
-    __syncthreads();
-    for (int round = 0; round < cp - 1; ++round) {
-      for (int pi = warp; pi < cp / 2; pi += nw) {
-        // round-robin (circle method): position 0 fixed, others rotate
-        int a = (pi == 0) ? 0 : 1 + (pi - 1 + round) % (cp - 1);
-        int bq = 1 + (cp - 2 - pi + round) % (cp - 1);
-        int p = a < bq ? a : bq, q = a < bq ? bq : a;
-        if (q >= c) continue;
-        T* mp = M + (size_t)p * ldm;
-        T* mq = M + (size_t)q * ldm;
-        T al = T(0), be = T(0), ga = T(0);
-        for (int i = lane; i < r; i += 32) {
-          T x = mp[i], y = mq[i];
-          al = fma(x, x, al);
-          be = fma(y, y, be);
-          ga = fma(x, y, ga);
-        }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga = warp_sum(ga);
-        if (ga == T(0) || fabs(ga) <= tol * sqrt(al * be)) continue;
-        T zeta = (be - al) / (T(2) * ga);
-        T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-        T cs = T(1) / sqrt(T(1) + t * t), sn = cs * t;
-        for (int i = lane; i < r; i += 32) {
-          T x = mp[i], y = mq[i];
-          mp[i] = cs * x - sn * y;
-          mq[i] = sn * x + cs * y;
-        }
-        T* vp = V + (size_t)p * ldv;
-        T* vq = V + (size_t)q * ldv;
-        for (int i = lane; i < c; i += 32) {
-          T x = vp[i], y = vq[i];
-          vp[i] = cs * x - sn * y;
-          vq[i] = sn * x + cs * y;
-        }
-        if (lane == 0) s_rot = 1;
-      }
-      __syncthreads();
-    }
-    if (!s_rot) break;
-    __syncthreads();
-  }
-  if (tid == 0 && sweeps_out) *sweeps_out = sweep;
-}
-
 // Column norms sigma_j of M (r x c), descending order with ties by index;
 // zero columns (dropped directions) sort last and are flagged invalid.
 __global__ void __launch_bounds__(kSmallThreads) k_colnorm_sort(int r, int c, const double* __restrict__ M,
@@ -348,34 +281,34 @@ __global__ void __launch_bounds__(kSmallThreads) k_chol_inv_f32(int b, const dou
                                                                 int* __restrict__ dropped,
                                                                 double* __restrict__ W) {
   extern __shared__ float Ls[];  // packed lower triangle, column-major
-  const int tid = threadIdx.x;
-  __shared__ int s_keep;
-  for (int j = 0; j < b; ++j)
-    for (int i = j + tid; i < b; i += kSmallThreads)
-      Ls[pk(i, j, b)] = (float)(0.5 * (G[i + j * ldg] + G[j + i * ldg]));
+  float* gd = Ls + (size_t)b * (b + 1) / 2;  // [b] original diagonal
+  float* cb = gd + b;                        // [b] column buffer
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kSmallThreads / 32;
+  // symmetrised copy, one warp per column
+  for (int j = warp; j < b; j += nw) {
+    for (int i = j + lane; i < b; i += 32)
+      Ls[pk(i, j, b)] = (float)(0.5 * (G[i + (size_t)j * ldg] + G[j + (size_t)i * ldg]));
+    if (lane == 0) gd[j] = (float)G[j + (size_t)j * ldg];
+  }
   __syncthreads();
+  // right-looking factorisation; every thread takes the pivot decision itself
   for (int j = 0; j < b; ++j) {
-    if (tid == 0) {
-      float d = Ls[pk(j, j, b)];
-      float g0 = (float)G[j + j * ldg];
-      s_keep = (g0 > 0.f && d > 64.f * 0x1p-24f * g0) ? 1 : 0;
-      dropped[j] = s_keep ? 0 : 1;
-      Ls[pk(j, j, b)] = s_keep ? sqrtf(d) : 1.f;
-    }
-    __syncthreads();
-    const float ljj = Ls[pk(j, j, b)];
-    if (s_keep) {
-      for (int i = j + 1 + tid; i < b; i += kSmallThreads) Ls[pk(i, j, b)] /= ljj;
-    } else {
-      for (int i = j + 1 + tid; i < b; i += kSmallThreads) Ls[pk(i, j, b)] = 0.f;
+    const float d = Ls[pk(j, j, b)];
+    const float g0 = gd[j];
+    const bool keep = g0 > 0.f && d > 64.f * 0x1p-24f * g0;
+    const float ljj = keep ? sqrtf(d) : 1.f;
+    const int bj = pk(j, j, b) - j;  // column j starts at bj + j
+    for (int i = j + 1 + tid; i < b; i += kSmallThreads) Ls[bj + i] = keep ? Ls[bj + i] / ljj : 0.f;
+    if (!keep)
       for (int l = tid; l < j; l += kSmallThreads) Ls[pk(j, l, b)] = 0.f;
-    }
     __syncthreads();
-    if (s_keep) {
+    if (tid == 0) {
+      Ls[bj + j] = ljj;
+      dropped[j] = keep ? 0 : 1;
+    }
+    if (keep) {
       // trailing update, one warp per column l, lanes over rows i >= l
-      const int lane = tid & 31, warp = tid >> 5;
-      const int bj = pk(j, j, b) - j;  // column j starts at bj + j
-      for (int l = j + 1 + warp; l < b; l += kSmallThreads / 32) {
+      for (int l = j + 1 + warp; l < b; l += nw) {
         const float llj = Ls[bj + l];
         const int bl = pk(l, l, b) - l;
         for (int i = l + lane; i < b; i += 32) Ls[bl + i] = fmaf(-Ls[bj + i], llj, Ls[bl + i]);
@@ -383,26 +316,27 @@ __global__ void __launch_bounds__(kSmallThreads) k_chol_inv_f32(int b, const dou
     }
     __syncthreads();
   }
-  // in-place inverse, last column first: column j of L^-1 from the already
-  // inverted trailing block, x = -(Linv[j+1:, j+1:] L[j+1:, j]) / L_jj; one
-  // warp per row, lanes split the dot product.  New values are staged in
-  // xbuf (the old column j is read by every row).
-  {
-    float* xbuf = Ls + (size_t)b * (b + 1) / 2;  // [b]
-    const int lane = tid & 31, warp = tid >> 5, nw = kSmallThreads / 32;
-    for (int j = b - 1; j >= 0; --j) {
-      const float ajj = 1.f / Ls[pk(j, j, b)];
-      for (int i = j + 1 + warp; i < b; i += nw) {
-        float sum = 0.f;
-        for (int l = j + 1 + lane; l <= i; l += 32) sum = fmaf(Ls[pk(i, l, b)], Ls[pk(l, j, b)], sum);
-        sum = warp_sum(sum);
-        if (lane == 0) xbuf[i] = -sum * ajj;
+  // in-place inverse X = L^-1 by right-looking forward substitution: at step
+  // l row l of X is final up to the factor 1 / L_ll; then every row i > l
+  // takes -L(i, l) X(l, :).  Slot (i, k), k < i, holds L(i, k) until step k
+  // and the accumulating X(i, k) afterwards; column l of L is staged in cb.
+  for (int l = 0; l < b; ++l) {
+    const float ill = 1.f / Ls[pk(l, l, b)];
+    const int bl = pk(l, l, b) - l;
+    for (int i = l + 1 + tid; i < b; i += kSmallThreads) cb[i] = Ls[bl + i];
+    for (int k = tid; k < l; k += kSmallThreads) Ls[pk(l, k, b)] *= ill;
+    __syncthreads();
+    if (tid == 0) Ls[bl + l] = ill;
+    for (int k = warp; k <= l; k += nw) {
+      const int bk = pk(k, k, b) - k;
+      if (k == l) {
+        for (int i = l + 1 + lane; i < b; i += 32) Ls[bk + i] = -cb[i] * ill;
+      } else {
+        const float xlk = Ls[bk + l];
+        for (int i = l + 1 + lane; i < b; i += 32) Ls[bk + i] = fmaf(-cb[i], xlk, Ls[bk + i]);
       }
-      __syncthreads();
-      for (int i = j + 1 + tid; i < b; i += kSmallThreads) Ls[pk(i, j, b)] = xbuf[i];
-      if (tid == 0) Ls[pk(j, j, b)] = ajj;
-      __syncthreads();
     }
+    __syncthreads();
   }
   // W0 = (L^-1)^T, dropped columns zero
   for (int e = tid; e < b * b; e += kSmallThreads) {
@@ -429,112 +363,258 @@ __global__ void k_whiten_corr(int b, double* __restrict__ E, const double* __res
   F[e] = f;
 }
 
-// One-sided block Jacobi (Hestenes) on the columns of M (r x cpad):
+// One-sided block Jacobi (Hestenes) on the columns of M (r x cpad, FP32):
 // M <- M V, V orthogonal (cpad x cpad, initialised to I by the launcher).
 // The cpad columns form 2P blocks of w; CTA g takes one block pair per round
 // (circle method over the blocks, 2P-1 rounds per sweep), loads its 2w
-// columns of M and V into shared memory, orthogonalises every column pair
-// among them (circle method over the 2w columns, one warp per pair), and
-// writes them back; a bounded grid barrier separates rounds.  A pair whose
-// inner product is exactly zero is never rotated, so zero columns (dropped
-// directions, padding) stay decoupled.  Converged when a sweep rotates
-// nothing (rotation counts per sweep in rot[]).
+// columns of M and V into shared memory and orthogonalises column pairs
+// among them, and writes them back; a bounded grid barrier separates rounds.
+// Round 0 of a sweep takes every pair among the 2w local columns (circle
+// method, w pairs per sub-round), which also covers every block's internal
+// pairs once per sweep; later rounds only the w x w pairs across the two
+// blocks (sub-round t pairs column i of block a with column (i + t) mod w of
+// block b), c - 1 sub-rounds per sweep in all.
+//
+// A sub-round has three phases separated by __syncthreads: (1) warp i forms
+// the inner product of its pair (in the cross rounds column i of block a
+// stays in warp i's registers for the whole round); (2) one warp computes the
+// w rotations, lane j for pair j, and carries the squared column norms
+// through them (|x'|^2 = |x|^2 - t g, |y'|^2 = |y|^2 + t g; the norms are
+// computed when the block is loaded); (3) warp i applies its rotation to the
+// pair and to the round's 2w x 2w accumulated rotation Q, which is applied to
+// the V block once at the end of the round (V_blk <- V_blk Q).  A pair whose
+// inner product is exactly zero, or below tol relative to the column norms
+// (floored, so rounding-level columns count as converged against
+// everything), is not rotated; zero columns (dropped directions, padding)
+// stay decoupled.  Converged when a sweep rotates nothing.
 constexpr int kBJThreads = 512;
-template <typename T>
-__global__ void __launch_bounds__(kBJThreads) k_block_jacobi(int r, int cpad, int w, T* __restrict__ M,
-                                                             int ldm, T* __restrict__ V, int ldv, T tol,
-                                                             int max_sweeps, int* __restrict__ rot,
+constexpr int kBJMaxChunks = 3;  // float4 row chunks per lane: r, cpad <= 384
+
+// (x + y) mod m for 0 <= x, y < m
+__device__ __forceinline__ int add_mod(int x, int y, int m) {
+  const int s = x + y;
+  return s >= m ? s - m : s;
+}
+
+// pair pi of sub-round sr: round 0 circle method over the 2w local columns
+// (p < q), later rounds column pi of block a with column (pi + sr) mod w of b
+__device__ __forceinline__ void bj_pair(int round, int pi, int sr, int w, int& p, int& q) {
+  const int w2 = 2 * w;
+  if (round == 0) {
+    const int a = (pi == 0) ? 0 : 1 + add_mod(pi - 1, sr, w2 - 1);
+    const int bq = 1 + add_mod(w2 - 2 - pi, sr, w2 - 1);
+    p = a < bq ? a : bq;
+    q = a < bq ? bq : a;
+  } else {
+    p = pi;
+    q = w + add_mod(pi, sr, w);
+  }
+}
+
+// Shared-memory layout: Ms [2w][rp] and Vs [2w][cp4] with rp, cp4 the row
+// counts rounded up to 4 (zero rows; float4 access), Qs [2w][ldq], nrm [2w],
+// gam / rc / rs [w] (inner products and rotations of the sub-round).
+// NCH = row chunks of 4 per lane (rp <= 128 NCH).
+template <int NCH>
+__global__ void __launch_bounds__(kBJThreads) k_block_jacobi(int r, int cpad, int w, float* __restrict__ M,
+                                                             int ldm, float* __restrict__ V, int ldv,
+                                                             float tol, int max_sweeps, int* __restrict__ rot,
                                                              GridBarrier* bar, int* err,
                                                              int* __restrict__ sweeps_out,
-                                                             const T* __restrict__ floor_ptr) {
-  extern __shared__ unsigned char smem_raw[];
-  T* Ms = reinterpret_cast<T*>(smem_raw);   // [2w][r]
-  T* Vs = Ms + (size_t)2 * w * r;           // [2w][cpad]
+                                                             const float* __restrict__ floor_ptr) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int w2 = 2 * w;
+  const int rp = (r + 3) & ~3, cp4 = (cpad + 3) & ~3;
+  const int ldq = (w2 + 7) & ~3;  // multiple of 4, >= 2w + 4
+  float* Ms = reinterpret_cast<float*>(smem_raw);
+  float* Vs = Ms + (size_t)w2 * rp;
+  float* Qs = Vs + (size_t)w2 * cp4;
+  float* nrm = Qs + w2 * ldq;
+  float* gam = nrm + w2;
+  float* rc = gam + w;
+  float* rs = rc + w;
   const int P = gridDim.x, g = blockIdx.x, nblk = 2 * P;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kBJThreads / 32;
-  const int w2 = 2 * w;
-  // columns whose squared norm is below the floor (rounding-level directions)
-  // count as converged against everything
-  const T nfloor = floor_ptr ? *floor_ptr : T(0);
+  const int rch = rp >> 2;  // float4 chunks per M column
+  const float nfloor = floor_ptr ? *floor_ptr : 0.f;
+  const float tol2 = tol * tol;
   __shared__ int s_rot;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     if (tid == 0) s_rot = 0;
     for (int round = 0; round < nblk - 1; ++round) {
-      const int ba = (g == 0) ? 0 : 1 + (g - 1 + round) % (nblk - 1);
-      const int bb = 1 + (nblk - 2 - g + round) % (nblk - 1);
-      // load the 2w columns
-      for (int e = tid; e < w2 * r; e += kBJThreads) {
-        int l = e / r, i = e % r;
-        int gc = (l < w ? ba * w + l : bb * w + (l - w));
-        Ms[(size_t)l * r + i] = M[i + (size_t)gc * ldm];
+      const int ba = (g == 0) ? 0 : 1 + add_mod(g - 1, round, nblk - 1);
+      const int bb = 1 + add_mod(nblk - 2 - g, round, nblk - 1);
+      // load the 2w columns of M (with their squared norms) and of V; Q = I
+      for (int l = warp; l < w2; l += nw) {
+        const int gc = (l < w ? ba * w + l : bb * w + (l - w));
+        const float* src = M + (size_t)gc * ldm;
+        float* dst = Ms + (size_t)l * rp;
+        float s2 = 0.f;
+        for (int i = lane; i < rp; i += 32) {
+          const float v = i < r ? src[i] : 0.f;
+          dst[i] = v;
+          s2 = fmaf(v, v, s2);
+        }
+        s2 = warp_sum(s2);
+        if (lane == 0) nrm[l] = s2;
+        const float* vsrc = V + (size_t)gc * ldv;
+        float* vdst = Vs + (size_t)l * cp4;
+        for (int i = lane; i < cp4; i += 32) vdst[i] = i < cpad ? vsrc[i] : 0.f;
       }
-      for (int e = tid; e < w2 * cpad; e += kBJThreads) {
-        int l = e / cpad, i = e % cpad;
-        int gc = (l < w ? ba * w + l : bb * w + (l - w));
-        Vs[(size_t)l * cpad + i] = V[i + (size_t)gc * ldv];
+      for (int e = tid; e < w2 * ldq; e += kBJThreads) {
+        const int i = e / ldq, j = e - i * ldq;
+        Qs[e] = (i == j) ? 1.f : 0.f;
       }
       __syncthreads();
-      // Round 0 of a sweep: all pairs among the 2w local columns (circle
-      // method, w pairs per sub-round), which also covers every block's
-      // internal pairs once per sweep.  Later rounds: only the w x w pairs
-      // across the two blocks (sub-round t pairs column i of block a with
-      // column (i + t) mod w of block b).  Per sweep that is c - 1 sub-rounds.
+      const bool resident = round > 0;  // column `warp` of block a lives in registers
+      float4 xr[NCH];
+      if (resident && warp < w) {
+        const float4* mp = reinterpret_cast<const float4*>(Ms + (size_t)warp * rp);
+#pragma unroll
+        for (int t = 0; t < NCH; ++t) {
+          const int c = lane + 32 * t;
+          xr[t] = c < rch ? mp[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
       const int nsub = (round == 0) ? w2 - 1 : w;
       for (int sr = 0; sr < nsub; ++sr) {
-        for (int pi = warp; pi < w; pi += nw) {
-          int p, q;
-          if (round == 0) {
-            int a = (pi == 0) ? 0 : 1 + (pi - 1 + sr) % (w2 - 1);
-            int bq = 1 + (w2 - 2 - pi + sr) % (w2 - 1);
-            p = a < bq ? a : bq;
-            q = a < bq ? bq : a;
-          } else {
-            p = pi;
-            q = w + (pi + sr) % w;
+        // (1) inner products
+        int p = 0, q = 0;
+        float4 x[NCH], y[NCH];
+        if (warp < w) {
+          bj_pair(round, warp, sr, w, p, q);
+          const float4* mp = reinterpret_cast<const float4*>(Ms + (size_t)p * rp);
+          const float4* mq = reinterpret_cast<const float4*>(Ms + (size_t)q * rp);
+          float ga = 0.f;
+#pragma unroll
+          for (int t = 0; t < NCH; ++t) {
+            const int c = lane + 32 * t;
+            x[t] = resident ? xr[t] : (c < rch ? mp[c] : make_float4(0.f, 0.f, 0.f, 0.f));
+            y[t] = c < rch ? mq[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+            ga = fmaf(x[t].x, y[t].x, ga);
+            ga = fmaf(x[t].y, y[t].y, ga);
+            ga = fmaf(x[t].z, y[t].z, ga);
+            ga = fmaf(x[t].w, y[t].w, ga);
           }
-          T* mp = Ms + (size_t)p * r;
-          T* mq = Ms + (size_t)q * r;
-          T al = T(0), be = T(0), ga = T(0);
-          for (int i = lane; i < r; i += 32) {
-            T x = mp[i], y = mq[i];
-            al = fma(x, x, al);
-            be = fma(y, y, be);
-            ga = fma(x, y, ga);
-          }
-          al = warp_sum(al);
-          be = warp_sum(be);
           ga = warp_sum(ga);
-          if (ga == T(0) || fabs(ga) <= tol * sqrt(fmax(al, nfloor) * fmax(be, nfloor))) continue;
-          T zeta = (be - al) / (T(2) * ga);
-          T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-          T cs = T(1) / sqrt(T(1) + t * t), sn = cs * t;
-          for (int i = lane; i < r; i += 32) {
-            T x = mp[i], y = mq[i];
-            mp[i] = cs * x - sn * y;
-            mq[i] = sn * x + cs * y;
+          if (lane == 0) gam[warp] = ga;
+        }
+        __syncthreads();
+        // (2) the rotations, lane j for pair j
+        if (warp == 0 && lane < w) {
+          int pj, qj;
+          bj_pair(round, lane, sr, w, pj, qj);
+          const float ga = gam[lane];
+          const float al = nrm[pj], be = nrm[qj];
+          const float fa = fmaxf(al, nfloor), fb = fmaxf(be, nfloor);
+          float cs = 1.f, sn = 0.f;
+          // rotate unless |g| <= tol |x| |y| (squared form; the block is scaled
+          // so that squared norms stay far from the FP32 range limits)
+          if (ga != 0.f && ga * ga > tol2 * fa * fb) {
+            // t the smaller root of t^2 + 2 zeta t - 1 = 0, zeta = (|y|^2 - |x|^2) / (2 g)
+            const float zeta = __fdividef(be - al, 2.f * ga);
+            const float az = fabsf(zeta);
+            float tt;
+            if (az > 1e18f) {
+              tt = __fdividef(0.5f, az);
+            } else {
+              const float s2 = fmaf(az, az, 1.f);
+              tt = __fdividef(1.f, az + s2 * rsqrtf(s2));
+            }
+            tt = copysignf(tt, zeta);
+            const float u = fmaf(tt, tt, 1.f);
+            cs = rsqrtf(u);
+            cs = cs * fmaf(-0.5f * u, cs * cs, 1.5f);  // one Newton step: cs^2 (1 + t^2) = 1
+            sn = cs * tt;
+            nrm[pj] = al - tt * ga;
+            nrm[qj] = be + tt * ga;
+            s_rot = 1;
           }
-          T* vp = Vs + (size_t)p * cpad;
-          T* vq = Vs + (size_t)q * cpad;
-          for (int i = lane; i < cpad; i += 32) {
-            T x = vp[i], y = vq[i];
-            vp[i] = cs * x - sn * y;
-            vq[i] = sn * x + cs * y;
+          rc[lane] = cs;
+          rs[lane] = sn;
+        }
+        __syncthreads();
+        // (3) apply
+        if (warp < w) {
+          const float cs = rc[warp], sn = rs[warp];
+          if (sn != 0.f) {
+            float4* mp = reinterpret_cast<float4*>(Ms + (size_t)p * rp);
+            float4* mq = reinterpret_cast<float4*>(Ms + (size_t)q * rp);
+#pragma unroll
+            for (int t = 0; t < NCH; ++t) {
+              const int c = lane + 32 * t;
+              float4 a4, b4;
+              a4.x = cs * x[t].x - sn * y[t].x;
+              a4.y = cs * x[t].y - sn * y[t].y;
+              a4.z = cs * x[t].z - sn * y[t].z;
+              a4.w = cs * x[t].w - sn * y[t].w;
+              b4.x = sn * x[t].x + cs * y[t].x;
+              b4.y = sn * x[t].y + cs * y[t].y;
+              b4.z = sn * x[t].z + cs * y[t].z;
+              b4.w = sn * x[t].w + cs * y[t].w;
+              if (resident) xr[t] = a4;
+              else if (c < rch) mp[c] = a4;
+              if (c < rch) mq[c] = b4;
+            }
+            if (lane < w2) {
+              const float qp = Qs[lane * ldq + p], qq = Qs[lane * ldq + q];
+              Qs[lane * ldq + p] = cs * qp - sn * qq;
+              Qs[lane * ldq + q] = sn * qp + cs * qq;
+            }
           }
-          if (lane == 0) s_rot = 1;
         }
         __syncthreads();
       }
-      // store back
-      for (int e = tid; e < w2 * r; e += kBJThreads) {
-        int l = e / r, i = e % r;
-        int gc = (l < w ? ba * w + l : bb * w + (l - w));
-        M[i + (size_t)gc * ldm] = Ms[(size_t)l * r + i];
+      if (resident && warp < w) {
+        float4* mp = reinterpret_cast<float4*>(Ms + (size_t)warp * rp);
+#pragma unroll
+        for (int t = 0; t < NCH; ++t) {
+          const int c = lane + 32 * t;
+          if (c < rch) mp[c] = xr[t];
+        }
       }
-      for (int e = tid; e < w2 * cpad; e += kBJThreads) {
-        int l = e / cpad, i = e % cpad;
-        int gc = (l < w ? ba * w + l : bb * w + (l - w));
-        V[i + (size_t)gc * ldv] = Vs[(size_t)l * cpad + i];
+      __syncthreads();
+      // store back M
+      for (int l = warp; l < w2; l += nw) {
+        const int gc = (l < w ? ba * w + l : bb * w + (l - w));
+        const float* src = Ms + (size_t)l * rp;
+        float* dst = M + (size_t)gc * ldm;
+        for (int i = lane; i < r; i += 32) dst[i] = src[i];
+      }
+      // V_blk <- V_blk Q: thread = (float4 row chunk, 4 output columns)
+      {
+        const int vch = cp4 >> 2, ngrp = (w2 + 3) >> 2;
+        for (int e = tid; e < vch * ngrp; e += kBJThreads) {
+          const int ch = e % vch, c0 = (e / vch) * 4;
+          float4 acc[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+          for (int k2 = 0; k2 < w2; ++k2) {
+            const float4 v = reinterpret_cast<const float4*>(Vs + (size_t)k2 * cp4)[ch];
+            const float4 qv = *reinterpret_cast<const float4*>(Qs + k2 * ldq + c0);
+            const float qq[4] = {qv.x, qv.y, qv.z, qv.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              acc[j].x = fmaf(v.x, qq[j], acc[j].x);
+              acc[j].y = fmaf(v.y, qq[j], acc[j].y);
+              acc[j].z = fmaf(v.z, qq[j], acc[j].z);
+              acc[j].w = fmaf(v.w, qq[j], acc[j].w);
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int l = c0 + j;
+            if (l < w2) {
+              const int gc = (l < w ? ba * w + l : bb * w + (l - w));
+              float* dst = V + (size_t)gc * ldv + 4 * ch;
+              const float a4[4] = {acc[j].x, acc[j].y, acc[j].z, acc[j].w};
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                if (4 * ch + u < cpad) dst[u] = a4[u];
+            }
+          }
+        }
       }
       if (P > 1) {
         if (!grid_barrier(bar, P, err)) return;
@@ -558,12 +638,32 @@ __global__ void __launch_bounds__(kBJThreads) k_block_jacobi(int r, int cpad, in
 
 // identity (cpad x cpad) and copy/convert of an r x c matrix into an r x cpad
 // padded one (zero padding columns)
+// Power of two 2^-e with 2^(e-1) <= max |A| < 2^e (1 for a zero matrix), one block.
+__global__ void k_pow2_scale(int r, int c, const double* __restrict__ A, int lda, float* __restrict__ out) {
+  __shared__ double red[32];
+  double m = 0.0;
+  for (int j = threadIdx.x >> 5; j < c; j += blockDim.x >> 5)
+    for (int i = threadIdx.x & 31; i < r; i += 32) m = fmax(m, fabs(A[i + (size_t)j * lda]));
+  m = warp_max(m);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) v = fmax(v, red[k]);
+    int e = 0;
+    if (v > 0.0) frexp(v, &e);
+    *out = (float)ldexp(1.0, -e);
+  }
+}
+
+// M (r x cpad, ld r) = scale * A padded with zero columns; V = I (cpad x cpad)
 template <typename TI, typename TO>
 __global__ void k_pad_copy(int r, int c, int cpad, const TI* __restrict__ A, int lda,
-                           TO* __restrict__ M, TO* __restrict__ V) {
+                           TO* __restrict__ M, TO* __restrict__ V, const float* __restrict__ scale) {
+  const TI sc = scale ? (TI)*scale : TI(1);
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < r * cpad; e += gridDim.x * blockDim.x) {
     int i = e % r, j = e / r;
-    M[e] = j < c ? (TO)A[i + j * lda] : TO(0);
+    M[e] = j < c ? (TO)(sc * A[i + j * lda]) : TO(0);
   }
   if (V)
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cpad * cpad; e += gridDim.x * blockDim.x) {
@@ -590,14 +690,16 @@ __global__ void k_ns_coef(int c, const double* __restrict__ T, double* __restric
 
 struct PencilWs {
   double *W1, *W2, *T, *E, *E2, *F, *C, *V, *Vp, *M, *Mp, *sig, *mu;
-  float *L32, *Li32, *M32, *V32;
+  float *L32, *Li32, *M32, *V32, *fs;  // fs: [0] Jacobi norm floor, [1] scale
   int *drop1, *drop2, *order, *nvalid, *rot, *err, *sweeps;
   GridBarrier* bar;
 };
 
+// Block layout of the Jacobi columns: 2P blocks of w <= 16 columns (a block
+// pair's 2w columns index the lanes of the round's Q), P CTAs.
 static int bj_cpad(int c, int* w_out, int* P_out, size_t elt, int r) {
   int w, P;
-  if (c <= 64) {
+  if (c <= 32) {
     w = (c + 1) / 2;
     if (w < 1) w = 1;
     P = 1;
@@ -632,6 +734,7 @@ static bool carve_pencil(Arena& ar, int b1, int b2, PencilWs& w) {
   w.Mp = ar.take<double>(rc);
   w.sig = ar.take<double>(cp);
   w.mu = ar.take<double>(2);
+  w.fs = ar.take<float>(4);
   w.L32 = ar.take<float>(bb);
   w.Li32 = ar.take<float>(bb);
   w.M32 = ar.take<float>(rc);
@@ -652,7 +755,7 @@ static bool carve_pencil(Arena& ar, int b1, int b2, PencilWs& w) {
 // W <- W (I - E/2 + 3/8 E^2), E = W^T G W - I, whose error squares per step.
 static void whiten(cudaStream_t s, int b, const double* G, PencilWs& w, int* dropped, double* Wout) {
   const int g1 = (b * b + 255) / 256;
-  const size_t sm = ((size_t)b * (b + 1) / 2 + b) * sizeof(float);
+  const size_t sm = ((size_t)b * (b + 1) / 2 + 2 * (size_t)b) * sizeof(float);
   if (sm > 48 * 1024)
     cudaFuncSetAttribute(k_chol_inv_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_chol_inv_f32<<<1, kSmallThreads, sm, s>>>(b, G, b, dropped, w.W1);
@@ -694,27 +797,36 @@ __global__ void k_colnorm_floor(int r, int c, const T* __restrict__ M, int ldm, 
   }
 }
 
-template <typename T>
-static rr_status launch_bj(cudaStream_t s, int r, int cpad, int w, int P, T* M, T* V, T tol,
-                           int max_sweeps, PencilWs& ws, const T* floor_ptr = nullptr) {
-  size_t smem = (size_t)2 * w * (r + cpad) * sizeof(T);
-  const void* fn = (const void*)k_block_jacobi<T>;
+static size_t bj_smem(int r, int cpad, int w) {
+  const size_t rp = (r + 3) & ~3, cp4 = (cpad + 3) & ~3;
+  const size_t ldq = (2 * w + 7) & ~3;
+  return ((size_t)2 * w * (rp + cp4) + (size_t)2 * w * ldq + 2 * w + 3 * (size_t)w) * sizeof(float);
+}
+
+static rr_status launch_bj(cudaStream_t s, int r, int cpad, int w, int P, float* M, float* V, float tol,
+                           int max_sweeps, PencilWs& ws, const float* floor_ptr = nullptr) {
+  const int rp = (r + 3) & ~3;
+  if (rp > 128 * kBJMaxChunks || cpad > 128 * kBJMaxChunks || 2 * w > 32 || w < 1) return RR_ERR_ARG;
+  const size_t smem = bj_smem(r, cpad, w);
+  const void* fn = rp <= 128 ? (const void*)k_block_jacobi<1>
+                   : rp <= 256 ? (const void*)k_block_jacobi<2>
+                               : (const void*)k_block_jacobi<3>;
   if (smem > 48 * 1024)
     RR_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   RR_CUDA(cudaMemsetAsync(ws.rot, 0, 64 * sizeof(int), s));
   RR_CUDA(cudaMemsetAsync(ws.bar, 0, sizeof(GridBarrier), s));
   int ld = r, ldv = cpad;
-  if (P == 1) {
-    k_block_jacobi<T><<<1, kBJThreads, smem, s>>>(r, cpad, w, M, ld, V, ldv, tol, max_sweeps, ws.rot,
-                                                  ws.bar, ws.err, ws.sweeps, floor_ptr);
-    return check_launch("block_jacobi");
-  }
   int* rot = ws.rot;
   GridBarrier* bar = ws.bar;
   int* err = ws.err;
   int* sw = ws.sweeps;
-  const T* fl = floor_ptr;
+  const float* fl = floor_ptr;
   void* args[] = {&r, &cpad, &w, &M, &ld, &V, &ldv, &tol, &max_sweeps, &rot, &bar, &err, &sw, &fl};
+  if (P == 1) {
+    // a single CTA never waits on another one: plain launch
+    RR_CUDA(cudaLaunchKernel(fn, dim3(1), dim3(kBJThreads), args, smem, s));
+    return check_launch("block_jacobi");
+  }
   RR_CUDA(cudaLaunchCooperativeKernel(fn, dim3(P), dim3(kBJThreads), args, smem, s));
   note_launches(1);
   return RR_OK;
@@ -775,10 +887,13 @@ static rr_status jacobi_svd(cudaStream_t s, int r, int c, const double* C, Penci
   int ww, P;
   const int cpad = bj_cpad(c, &ww, &P, 4, r);
   const int g = 256, gc = (c * c + 255) / 256;
-  k_pad_copy<double, float><<<g, 256, 0, s>>>(r, c, cpad, C, r, w.M32, w.V32);
-  float* fl = (float*)(w.mu + 1);  // scratch slot after mu
+  // FP32 copy scaled by a power of two to max entry in [1/2, 1): squared
+  // column norms stay well inside the FP32 range
+  k_pow2_scale<<<1, 1024, 0, s>>>(r, c, C, r, w.fs + 1);
+  k_pad_copy<double, float><<<g, 256, 0, s>>>(r, c, cpad, C, r, w.M32, w.V32, w.fs + 1);
+  float* fl = w.fs;
   k_colnorm_floor<float><<<1, 1024, 0, s>>>(r, cpad, w.M32, r, 1e-10f, fl);
-  RR_TRY(launch_bj<float>(s, r, cpad, ww, P, w.M32, w.V32, 1e-4f, 15, w, fl));
+  RR_TRY(launch_bj(s, r, cpad, ww, P, w.M32, w.V32, 1e-4f, 15, w, fl));
   k_v32_to_64<<<g, 256, 0, s>>>(c, cpad, w.V32, w.V);
   for (int it = 0; it < 3; ++it) {
     ns_orthonormalize(s, c, w.V, w);
@@ -794,7 +909,7 @@ static rr_status jacobi_svd(cudaStream_t s, int r, int c, const double* C, Penci
   gemm_small(s, 0, 0, r, c, c, 1.0, C, r, w.V, c, 0.0, Mout, r);            // M = C V
   if (Vout != w.V)
     RR_CUDA(cudaMemcpyAsync(Vout, w.V, (size_t)c * c * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  note_launches(18);
+  note_launches(22);  // 4 setup kernels, 3 x 6 polish kernels (+ the final product in check_launch)
   return check_launch("jacobi_svd");
 }
 
