@@ -309,9 +309,15 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize()
         t64 = e0.elapsed_time(e1) / 1e3
+        s64_h = s64.cpu().numpy()
         fp64 = {"value": info64["n_converged"] / t64, "unit": "pairs/s", "seconds": t64,
                 "n_converged": info64["n_converged"], "sweeps": info64["sweeps"],
-                "mixed_over_fp64": value / (info64["n_converged"] / t64) if info64["n_converged"] else None}
+                "mixed_over_fp64": value / (info64["n_converged"] / t64) if info64["n_converged"] else None,
+                # the FP64 path's own distance to the prescribed spectrum (the
+                # rounding of A to FP64 sets a floor near 1e-14), and the
+                # mixed-precision result's distance to it
+                "sigma_max_rel_err": float(np.max(np.abs(s64_h - sigma[:K]) / sigma[:K])),
+                "sigma_max_rel_diff_mixed": float(np.max(np.abs(s_h - s64_h) / s64_h))}
 
     # end to end through host buffers: H2D of A and V0 from pinned memory,
     # the solve, D2H of sigma, U, V every step

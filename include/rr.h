@@ -222,11 +222,15 @@ rr_status rr_hessenberg(int32_t arith, int64_t n, int64_t k, void* W, int64_t ld
                         int32_t qtype, void* Q, int64_t ldq, int32_t* piv, double tol,
                         void* ws, size_t ws_bytes, void* stream);
 
-/* Projection products (Alg. 3 lines B = U^T A U, M = U^T U; Alg. 5 U^T A V,
+/* Projection products (Alg. 3: B = U^T A U, M = U^T U; Alg. 5: U^T A V,
  * U^T U, V^T V): G (p x q FP64, ld ldg) = X^T Y (+ G if accumulate) for tall
  * X (n x p) and Y (n x q) of types xtype/ytype (RR_F64, RR_F32, RR_BF16).
- * Accumulation is FP64 (accurate to FP64 rounding of the exact sum).  Needs
- * rr_gram_workspace_size(n, p, q) bytes (deterministic split-K partials). */
+ * FP64-accurate: when n >= 64, n % 8 == 0 and q <= 128 the products run on
+ * the tensor cores from 8 column-scaled 6-bit slices of each operand with
+ * exact FP32 sums over 4096-long K chunks (error per entry below
+ * 2^-47 n max|X(:,i)| max|Y(:,j)|); otherwise FP64 accumulation on the CUDA
+ * cores.  Needs rr_gram_workspace_size(n, p, q) bytes (slices and
+ * deterministic split-K partials, reduced in a fixed order). */
 size_t rr_gram_workspace_size(int64_t n, int64_t p, int64_t q);
 rr_status rr_gram(int64_t n, int64_t p, int64_t q, int32_t xtype, const void* X, int64_t ldx,
                   int32_t ytype, const void* Y, int64_t ldy, double* G, int64_t ldg,
@@ -251,7 +255,7 @@ rr_status rr_gram_noalloc(int64_t n, int64_t p, int64_t q, int32_t xtype, const 
                           int64_t ldx, int32_t ytype, const void* Y, int64_t ldy, double* G,
                           int64_t ldg, int32_t accumulate, void* stream);
 
-/* Small projected problems, FP64 (Alg. 3 line "B Y = M Y Lambda"; Alg. 5).
+/* Small projected problems, FP64 (Alg. 3: B Y = M Y Lambda; Alg. 5).
  * rr_pencil_eig: H, G (b x b, ld b) symmetric, G positive semidefinite.
  *   theta (b) ascending; Y (b x b) with Y^T G Y = I on the kept part.
  *   Whitening by Cholesky with column dropping (a pivot with L_jj^2 <=

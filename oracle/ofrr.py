@@ -186,7 +186,7 @@ def _whitener(G: np.ndarray):
 
 
 def pencil_eig(H: np.ndarray, G: np.ndarray):
-    """Solve H Y = G Y Theta (Algorithm 3, line "B Y = M Y Lambda"), FP64.
+    """Solve H Y = G Y Theta (the generalized eigenproblem B Y = M Y Lambda of Algorithm 3), FP64.
 
     H symmetric, G symmetric positive (semi)definite.  Returns theta ascending
     and Y with Y^T G Y = I.  When G is numerically definite this is LAPACK's

@@ -7,6 +7,7 @@
 #include <cstring>
 
 #include "rr_common.cuh"
+#include "solver_kernels.cuh"
 
 namespace rr {
 
@@ -385,8 +386,17 @@ static int64_t gram_chunks(int64_t n, int64_t p, int64_t q) {
 }
 }  // namespace rr
 
+// Workspace: the SIMT path's split-K partials, or the tensor-core path's
+// slices and partials when the shape qualifies (for q > 128 the calls with
+// q' <= 128 columns qualify)
 extern "C" size_t rr_gram_workspace_size(int64_t n, int64_t p, int64_t q) {
-  return align_up((size_t)gram_chunks(n, p, q) * p * q * sizeof(double)) + 256;
+  size_t b = align_up((size_t)gram_chunks(n, p, q) * p * q * sizeof(double)) + 256;
+  const int64_t qe = q < 128 ? q : 128;
+  if (emu_gram_supported(n, p, qe)) {
+    const size_t e = emu_gram_bytes(n, p, qe);
+    if (e > b) b = e;
+  }
+  return b;
 }
 
 namespace rr {
@@ -428,6 +438,8 @@ extern "C" rr_status rr_gram(int64_t n, int64_t p, int64_t q, int32_t xtype, con
                              int64_t ldg, int32_t accumulate, void* ws, size_t ws_bytes,
                              void* stream) {
   if (n < 0 || p < 0 || q < 0 || ldx < n || ldy < n || ldg < p || !G) return RR_ERR_ARG;
+  auto valid = [](int32_t t) { return t == RR_F64 || t == RR_F32 || t == RR_BF16; };
+  if (!valid(xtype) || !valid(ytype)) return RR_ERR_ARG;
   if (p == 0 || q == 0) return RR_OK;
   cudaStream_t s = as_stream(stream);
   if (n == 0) {
@@ -435,6 +447,10 @@ extern "C" rr_status rr_gram(int64_t n, int64_t p, int64_t q, int32_t xtype, con
       for (int64_t j = 0; j < q; ++j) RR_CUDA(cudaMemsetAsync(G + j * ldg, 0, p * sizeof(double), s));
     return RR_OK;
   }
+  // FP64-accurate products on the tensor cores when the shape qualifies and
+  // the workspace holds the slices
+  if (emu_gram_supported(n, p, q) && ws && ws_bytes >= emu_gram_bytes(n, p, q))
+    return emu_gram(s, n, p, q, xtype, X, ldx, ytype, Y, ldy, G, ldg, accumulate, ws, ws_bytes);
   int64_t chunks = gram_chunks(n, p, q);
   if (ws_bytes < (size_t)chunks * p * q * sizeof(double) || !ws) return RR_ERR_WORKSPACE;
   int64_t rpc = (n + chunks - 1) / chunks;

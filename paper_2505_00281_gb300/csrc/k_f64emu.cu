@@ -22,10 +22,6 @@
 
 namespace rr {
 
-rr_status gemm_bf16_tc_emu(int64_t M, int64_t N, int64_t K, const __nv_bfloat16* A, int64_t lda,
-                           const __nv_bfloat16* B, int64_t ldb, double* C64, int64_t ldc64,
-                           const int* rexp, int rshift, const double* cscale, int nb, int max_kchunk,
-                           cudaStream_t s);
 bool gemm_bf16_tc_supported(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb, const void* A,
                             const void* B);
 
@@ -134,14 +130,6 @@ __global__ void k_slice_rows(int64_t m, int64_t n, const double* __restrict__ A,
   }
 }
 
-// cs[(q-1) N + c] = 2^(e_c - beta q), q = 1..S
-__global__ void k_col_scales(int64_t N, int S, const int* __restrict__ e, double* __restrict__ cs) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= N * S) return;
-  const int64_t c = t % N, q = t / N + 1;
-  cs[t] = ldexp(1.0, e[c] - kBeta * (int)q);
-}
-
 __global__ void k_zero_f64(int64_t M, int64_t N, double* __restrict__ C, int64_t ldc) {
   const int64_t j = blockIdx.y;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x)
@@ -157,7 +145,7 @@ size_t emu_operator_bytes(int64_t m, int64_t n, int S, bool rows, bool cols) {
 }
 
 size_t emu_block_bytes(int64_t K, int64_t N, int S) {
-  return align_up((size_t)S * K * N * 2) + align_up((size_t)N * 4) + align_up((size_t)S * N * 8);
+  return align_up((size_t)S * K * N * 2) + align_up((size_t)N * 4);
 }
 
 // Slice the FP64 operator A (m x n, column-major) once: row-scaled slices
@@ -194,6 +182,19 @@ rr_status emu_prepare(cudaStream_t s, const double* A, int64_t m, int64_t n, int
   return RR_OK;
 }
 
+// The slice pairs (p, q), p + q <= S + 1 (1-based), grouped by p into runs
+// of one or two consecutive q: pair codes p0 | q0 << 8 | nq << 16 (0-based).
+static int emu_pairs(int S, bool two, uint32_t* out) {
+  int n = 0;
+  for (int p = 1; p <= S; ++p)
+    for (int q = 1; q <= S + 1 - p;) {
+      const int nq = (two && q + 1 <= S + 1 - p) ? 2 : 1;
+      out[n++] = (uint32_t)(p - 1) | ((uint32_t)(q - 1) << 8) | ((uint32_t)nq << 16);
+      q += nq;
+    }
+  return n;
+}
+
 // C (FP64, M x N) = A X (trans = 0, M = m, K = n) or A^T X (trans = 1, M = n,
 // K = m), X FP64 K x N column-major; mem: emu_block_bytes(K, N, S).
 rr_status emu_gemm(cudaStream_t s, const EmuOperator& op, int trans, int64_t N, const double* X,
@@ -206,28 +207,138 @@ rr_status emu_gemm(cudaStream_t s, const EmuOperator& op, int trans, int64_t N, 
   Arena ar(mem, emu_block_bytes(K, N, S));
   __nv_bfloat16* T = (__nv_bfloat16*)ar.take_bytes((size_t)S * K * N * 2);
   int* xe = ar.take<int>(N);
-  double* cs = ar.take<double>((size_t)S * N);
   k_col_exp<<<(unsigned)N, 512, 0, s>>>(K, X, ldx, xe);
   dim3 g((unsigned)std::min<int64_t>((K + 255) / 256, 1024), (unsigned)N);
   k_slice_cols<<<g, 256, 0, s>>>(K, N, X, ldx, xe, S, T);
-  k_col_scales<<<(unsigned)((N * S + 255) / 256), 256, 0, s>>>(N, S, xe, cs);
   dim3 gz((unsigned)std::min<int64_t>((M + 255) / 256, 1024), (unsigned)N);
   k_zero_f64<<<gz, 256, 0, s>>>(M, N, C, ldc);
-  note_launches(3);
+  note_launches(2);
   RR_TRY(check_launch("emu_gemm slices"));
   const int64_t lda = trans ? op.m : op.n;  // K-contiguous leading dimension of the A slices
-  const int per_call = (2 * N <= 256) ? 2 : 1;
-  for (int p = 1; p <= S; ++p) {
-    const int qmax = S + 1 - p;
-    for (int q0 = 1; q0 <= qmax; q0 += per_call) {
-      const int nq = (q0 + per_call - 1 <= qmax) ? per_call : 1;
-      const __nv_bfloat16* Ap = As + (size_t)(p - 1) * op.m * op.n;
-      const __nv_bfloat16* Tq = T + (size_t)(q0 - 1) * K * N;  // slices q0.. are contiguous (ld K)
-      RR_TRY(gemm_bf16_tc_emu(M, N * nq, K, Ap, lda, Tq, K, C, ldc, rexp, kBeta * p,
-                              cs + (size_t)(q0 - 1) * N, (int)N, 4096, s));
-    }
+  uint32_t pairs[64];
+  const int np = emu_pairs(S, 2 * N <= 256, pairs);
+  // one launch per pair: consecutive launches add into C in stream order
+  for (int z = 0; z < np; ++z) {
+    const int nq = (int)(pairs[z] >> 16);
+    TcEmu e{C, ldc, nullptr, rexp, xe, (int)N, S, S, (int)M, (int)N, 1, pairs + z, 4096};
+    RR_TRY(gemm_bf16_tc_emu(M, N * nq, K, As, lda, T, K, e, s));
   }
   return RR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// FP64-accurate Gram products G = X^T Y (X n x p, Y n x q, any storage type)
+// on the tensor cores: both operands sliced by columns, every slice pair in
+// one launch with exact FP32 sums over K chunks, FP64 partials per (pair, K
+// chunk), then a fixed-order FP64 reduction.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_col_exp_t(int64_t m, const T* __restrict__ A, int64_t lda, int* __restrict__ e) {
+  const int64_t j = blockIdx.x;
+  int mx = -1100;
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) mx = max(mx, exp_bits(Ld<T>::f64(A + i + j * lda)));
+  __shared__ int sm[32];
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    mx = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : -1100;
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (threadIdx.x == 0) e[j] = mx;
+  }
+}
+
+template <typename T>
+__global__ void k_slice_cols_t(int64_t m, int64_t n, const T* __restrict__ A, int64_t lda,
+                               const int* __restrict__ cexp, int S, __nv_bfloat16* __restrict__ out) {
+  const int64_t j = blockIdx.y;
+  const int e = cexp[j];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    float sl[kMaxSlices];
+    slice_value(Ld<T>::f64(A + i + j * lda), e, S, sl);
+    for (int p = 0; p < S; ++p) out[(size_t)p * m * n + i + j * m] = __float2bfloat16_rn(sl[p]);
+  }
+}
+
+__global__ void k_emu_reduce(int64_t p, int64_t q, int64_t nparts, const double* __restrict__ part,
+                             double* __restrict__ G, int64_t ldg, int accum) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= p * q) return;
+  double s = 0.0;
+  for (int64_t c = 0; c < nparts; ++c) s += part[c * p * q + e];
+  const int64_t i = e % p, j = e / p;
+  if (accum) s += G[i + j * ldg];
+  G[i + j * ldg] = s;
+}
+
+constexpr int kGramSlices = 8;
+constexpr int kGramKChunk = 4096;
+
+static int emu_gram_npairs() {
+  uint32_t pr[64];
+  return emu_pairs(kGramSlices, true, pr);
+}
+
+bool emu_gram_supported(int64_t n, int64_t p, int64_t q) {
+  return n >= 64 && n % 8 == 0 && p >= 1 && q >= 1 && p <= 4096 && q <= 128 && n <= ((int64_t)1 << 30);
+}
+
+// Workspace of emu_gram, monotone in n, p and q (so one size serves every
+// smaller call): slices of both operands, exponents, and the partials for the
+// largest K-split count a launch of this size can take.
+size_t emu_gram_bytes(int64_t n, int64_t p, int64_t q) {
+  const int S = kGramSlices;
+  const int64_t np = emu_gram_npairs();
+  const int64_t nk = (n + 63) / 64;
+  const int64_t kmin = (n + kGramKChunk - 1) / kGramKChunk;
+  int64_t smax = (num_sms() + np - 1) / np;
+  if (smax < kmin) smax = kmin;
+  if (smax > nk) smax = nk;
+  return align_up((size_t)S * n * p * 2) + align_up((size_t)S * n * q * 2) + align_up((size_t)p * 4) +
+         align_up((size_t)q * 4) + align_up((size_t)(np * smax) * p * q * 8) + 256;
+}
+
+template <typename T>
+static void emu_slice_block(cudaStream_t s, int64_t n, int64_t c, const T* X, int64_t ldx, int* e,
+                            __nv_bfloat16* out) {
+  k_col_exp_t<T><<<(unsigned)c, 512, 0, s>>>(n, X, ldx, e);
+  dim3 g((unsigned)std::min<int64_t>((n + 255) / 256, 1024), (unsigned)c);
+  k_slice_cols_t<T><<<g, 256, 0, s>>>(n, c, X, ldx, e, kGramSlices, out);
+}
+
+static void emu_slice_any(cudaStream_t s, int32_t t, int64_t n, int64_t c, const void* X, int64_t ldx,
+                          int* e, __nv_bfloat16* out) {
+  switch (t) {
+    case RR_F64: emu_slice_block<double>(s, n, c, (const double*)X, ldx, e, out); break;
+    case RR_F32: emu_slice_block<float>(s, n, c, (const float*)X, ldx, e, out); break;
+    default: emu_slice_block<__nv_bfloat16>(s, n, c, (const __nv_bfloat16*)X, ldx, e, out); break;
+  }
+}
+
+rr_status emu_gram(cudaStream_t s, int64_t n, int64_t p, int64_t q, int32_t xt, const void* X, int64_t ldx,
+                   int32_t yt, const void* Y, int64_t ldy, double* G, int64_t ldg, int accum, void* mem,
+                   size_t bytes) {
+  if (!emu_gram_supported(n, p, q)) return RR_ERR_ARG;
+  if (bytes < emu_gram_bytes(n, p, q) || !mem) return RR_ERR_WORKSPACE;
+  const int S = kGramSlices;
+  Arena ar(mem, bytes);
+  __nv_bfloat16* Xs = (__nv_bfloat16*)ar.take_bytes((size_t)S * n * p * 2);
+  __nv_bfloat16* Ys = (__nv_bfloat16*)ar.take_bytes((size_t)S * n * q * 2);
+  int* ex = ar.take<int>(p);
+  int* ey = ar.take<int>(q);
+  uint32_t pairs[64];
+  const int np = emu_pairs(S, true, pairs);
+  const int splits = tc_emu_partial_splits(p, n, np, kGramKChunk);
+  double* part = ar.take<double>((size_t)np * splits * p * q);
+  if (ar.overflow) return RR_ERR_WORKSPACE;
+  emu_slice_any(s, xt, n, p, X, ldx, ex, Xs);
+  emu_slice_any(s, yt, n, q, Y, ldy, ey, Ys);
+  note_launches(3);
+  RR_TRY(check_launch("emu_gram slices"));
+  TcEmu e{nullptr, 0, part, ex, ey, (int)q, S, S, (int)p, (int)q, np, pairs, kGramKChunk};
+  RR_TRY(gemm_bf16_tc_emu(p, 2 * q, n, Xs, n, Ys, n, e, s));
+  k_emu_reduce<<<(unsigned)((p * q + 255) / 256), 256, 0, s>>>(p, q, (int64_t)np * splits, part, G, ldg, accum);
+  return check_launch("emu_gram reduce");
 }
 
 }  // namespace rr

@@ -21,6 +21,7 @@
 #include <cuda.h>
 
 #include "rr_common.cuh"
+#include "solver_kernels.cuh"
 
 namespace rr {
 
@@ -136,15 +137,34 @@ struct TcArgs {
   int64_t ldr;
   const double* coef;
   int atomic;      // 1: K-split, add into C
-  // FP64-emulation epilogue (C64 != nullptr): C64[row, col % nb] +=
-  //   v * 2^(rexp[row] - rshift) * cscale[col]   (v: exact integer-valued FP32)
+  // FP64-emulation epilogue (Ozaki-style slices, see k_f64emu.cu).  Launch z
+  // multiplies A slice p0 by nq = 1 or 2 consecutive B slices q0, q0 + 1
+  // (pair[z] = p0 | q0 << 8 | nq << 16, 0-based); A rows / B rows of slice s
+  // start at s * a_slice_rows / s * b_slice_rows in the operands' tensor maps.
+  // The exact FP32 sums v0, v1 combine into 64 v0 + v1 at the second slice's
+  // scale, and element (row, col) is scaled by
+  //   2^(rexp[row] + cexp[col] - 6 (p0 + 1) - 6 (q0 + nq)).
+  // Output: C64 (!= nullptr) takes += (atomically under a K-split), else part
+  // receives one M x nb block (ld M) per (z, split).
   double* C64;
   int64_t ldc64;
+  double* part;
   const int* rexp;
-  int rshift;
-  const double* cscale;
+  const int* cexp;
   int nb;
+  int a_slice_rows, b_slice_rows;
+  int npairs;
+  uint32_t pair[48];
 };
+
+// d * 2^e, exact: an exponent-field add when the result stays normal
+// (ldexp otherwise: zero, subnormal or overflowing results)
+__device__ __forceinline__ double mul_pow2(double d, int e) {
+  const long long b = __double_as_longlong(d);
+  const int be = (int)((b >> 52) & 0x7FF);
+  if (be != 0 && be + e > 0 && be + e < 2047) return __longlong_as_double(b + ((long long)e << 52));
+  return d == 0.0 ? d : ldexp(d, e);
+}
 
 __global__ void __launch_bounds__(128, 1) k_gemm_bf16_tc(const __grid_constant__ CUtensorMap tmA,
                                                           const __grid_constant__ CUtensorMap tmB,
@@ -167,6 +187,10 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16_tc(const __grid_constant__
   int ks1 = ks0 + a.ksteps_per_split;
   if (ks1 > a.nk) ks1 = a.nk;
   const int nks = ks1 > ks0 ? ks1 - ks0 : 0;
+  // slice pair of this launch row (FP64 emulation; 0 otherwise)
+  const uint32_t pz = a.npairs > 0 ? a.pair[blockIdx.z] : 0u;
+  const int p0 = (int)(pz & 0xFF), q0 = (int)((pz >> 8) & 0xFF), nq = (int)((pz >> 16) & 0xFF);
+  const int a_off = p0 * a.a_slice_rows, b_off = q0 * a.b_slice_rows;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < a.stages; ++s) {
@@ -198,8 +222,8 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16_tc(const __grid_constant__
         unsigned char* sb = sa + a_bytes;
         mbar_expect_tx(&full[s], stage_bytes);
         const int kx = (ks0 + i) * kBK;
-        tma_load_2d(sa, &tmA, &full[s], kx, (int)m0);
-        tma_load_2d(sb, &tmB, &full[s], kx, 0);
+        tma_load_2d(sa, &tmA, &full[s], kx, (int)m0 + a_off);
+        tma_load_2d(sb, &tmB, &full[s], kx, b_off);
         ++issued;
       }
       if (issued < nks) {
@@ -245,22 +269,43 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16_tc(const __grid_constant__
     __syncwarp();
     ready = __all_sync(0xffffffffu, ready) && *(volatile int*)&g_tc_error == 0;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ready && a.C64) {
+    if (ready && a.cexp) {
+      // FP64-emulation epilogue; the 32 C loads of a chunk are issued before
+      // any store (read-modify-write mode)
       const int64_t row = m0 + warp * 32 + lane;
-      const double rs = row < a.M ? ldexp(1.0, a.rexp[row] - a.rshift) : 0.0;
-      for (int c0 = 0; c0 < a.npad; c0 += 32) {
-        uint32_t r[32];
-        tmem_ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-        if (row < a.M) {
+      const bool rv = row < a.M;
+      const int er = rv ? __ldg(a.rexp + row) - 6 * (p0 + 1) - 6 * (q0 + nq) : 0;
+      double* __restrict__ Cr = a.C64 ? a.C64 + row
+                                      : a.part + ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * a.M * a.nb + row;
+      const int64_t ldo = a.C64 ? a.ldc64 : a.M;
+      const bool rmw = a.C64 && !a.atomic;
+      for (int c0 = 0; c0 < a.nb; c0 += 32) {
+        uint32_t r0[32], r1[32];
+        tmem_ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r0);
+        if (nq > 1) tmem_ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a.nb + c0), r1);
+        if (rv) {
+          const int cnt = a.nb - c0 < 32 ? a.nb - c0 : 32;
+          double cv[32];
+          if (rmw) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (j < cnt) cv[j] = Cr[(int64_t)(c0 + j) * ldo];
+          }
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
-            const int64_t col = c0 + j;
-            if (col < a.N) {
-              const double v = (double)__uint_as_float(r[j]) * rs * a.cscale[col];
-              double* dst = a.C64 + row + (col % a.nb) * a.ldc64;
-              if (a.atomic) atomicAdd(dst, v);
-              else *dst += v;
+            if (j < cnt) {
+              int iv = __float2int_rn(__uint_as_float(r0[j]));
+              if (nq > 1) iv = iv * 64 + __float2int_rn(__uint_as_float(r1[j]));
+              const double t = mul_pow2(__int2double_rn(iv), er + __ldg(a.cexp + c0 + j));
+              if (rmw) cv[j] += t;
+              else if (a.C64) atomicAdd(Cr + (int64_t)(c0 + j) * ldo, t);
+              else Cr[(int64_t)(c0 + j) * ldo] = t;
             }
+          }
+          if (rmw) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (j < cnt) Cr[(int64_t)(c0 + j) * ldo] = cv[j];
           }
         }
       }
@@ -364,15 +409,20 @@ static bool make_map(CUtensorMap* m, const void* base, int64_t inner, int64_t ou
   return r == CUDA_SUCCESS;
 }
 
-struct TcEmu {
-  double* C64;
-  int64_t ldc64;
-  const int* rexp;
-  int rshift;
-  const double* cscale;
-  int nb;
-  int max_kchunk;  // K elements one CTA may accumulate before its FP64 update
-};
+static int64_t tc_nk(int64_t K) { return (K + kBK - 1) / kBK; }
+
+// K splits of a partial-output emulation launch: enough for exact FP32
+// sums, and about one CTA per SM over tiles x pairs x splits
+int tc_emu_partial_splits(int64_t M, int64_t K, int npairs, int max_kchunk) {
+  const int64_t tiles = (M + kBM - 1) / kBM, nk = tc_nk(K);
+  const int64_t per_max = max_kchunk / kBK;
+  if (per_max < 1 || npairs < 1) return 0;
+  int64_t splits = (nk + per_max - 1) / per_max;
+  const int64_t want = (num_sms() + tiles * npairs - 1) / (tiles * npairs);
+  if (want > splits) splits = want < nk ? want : nk;
+  const int64_t per = (nk + splits - 1) / splits;
+  return (int)((nk + per - 1) / per);
+}
 
 static rr_status gemm_bf16_tc_impl(int64_t M, int64_t N, int64_t K, const __nv_bfloat16* A, int64_t lda,
                                    const __nv_bfloat16* B, int64_t ldb, float* C, int64_t ldc,
@@ -385,11 +435,12 @@ rr_status gemm_bf16_tc(int64_t M, int64_t N, int64_t K, const __nv_bfloat16* A, 
   return gemm_bf16_tc_impl(M, N, K, A, lda, B, ldb, C, ldc, R, ldr, coef, nullptr, s);
 }
 
+// FP64 emulation launch (TcEmu in solver_kernels.cuh); N = nb or 2 nb
 rr_status gemm_bf16_tc_emu(int64_t M, int64_t N, int64_t K, const __nv_bfloat16* A, int64_t lda,
-                           const __nv_bfloat16* B, int64_t ldb, double* C64, int64_t ldc64,
-                           const int* rexp, int rshift, const double* cscale, int nb, int max_kchunk,
-                           cudaStream_t s) {
-  TcEmu e{C64, ldc64, rexp, rshift, cscale, nb, max_kchunk};
+                           const __nv_bfloat16* B, int64_t ldb, const TcEmu& e, cudaStream_t s) {
+  if (e.npairs < 1 || e.npairs > 48 || (!e.C64) == (!e.part) || !e.rexp || !e.cexp || !e.pair)
+    return RR_ERR_ARG;
+  if (N != e.nb && N != 2 * (int64_t)e.nb) return RR_ERR_ARG;
   return gemm_bf16_tc_impl(M, N, K, A, lda, B, ldb, nullptr, 0, nullptr, 0, nullptr, &e, s);
 }
 
@@ -398,17 +449,32 @@ static rr_status gemm_bf16_tc_impl(int64_t M, int64_t N, int64_t K, const __nv_b
                                    const double* R, int64_t ldr, const double* coef, const TcEmu* emu,
                                    cudaStream_t s) {
   const int npad = (int)((N + 15) / 16 * 16);
+  // TMEM columns: the accumulator, and for a two-slice emulation launch the
+  // epilogue's 32-column reads of the second slice up to nb + 32 ceil(nb / 32)
+  int need = npad;
+  if (emu && N > emu->nb) {
+    const int nb2 = emu->nb + 32 * ((emu->nb + 31) / 32);
+    if (nb2 > need) need = nb2;
+  }
+  if (need > 512) return RR_ERR_ARG;
   int tcols = 32;
-  while (tcols < npad) tcols <<= 1;
+  while (tcols < need) tcols <<= 1;
+  // tensor maps over the whole slice stacks (emulation) or the operands
+  const int64_t a_outer = emu && emu->a_slices > 1 ? (int64_t)emu->a_slices * emu->a_slice_rows : M;
+  const int64_t b_outer = emu && emu->b_slices > 1 ? (int64_t)emu->b_slices * emu->b_slice_rows : N;
   CUtensorMap ta, tb;
-  if (!make_map(&ta, A, K, M, lda, kBK, kBM)) return RR_ERR_ARG;
-  if (!make_map(&tb, B, K, N, ldb, kBK, (uint32_t)npad)) return RR_ERR_ARG;
+  if (!make_map(&ta, A, K, a_outer, lda, kBK, kBM)) return RR_ERR_ARG;
+  if (!make_map(&tb, B, K, b_outer, ldb, kBK, (uint32_t)npad)) return RR_ERR_ARG;
   const int64_t tiles = (M + kBM - 1) / kBM;
-  const int nk = (int)((K + kBK - 1) / kBK);
+  const int nk = (int)tc_nk(K);
   const int sms = num_sms();
+  const int npairs = emu ? emu->npairs : 1;
   int splits = 1;
-  if (tiles < sms) {
-    splits = (int)(sms / tiles);
+  if (emu && emu->part) {
+    splits = tc_emu_partial_splits(M, K, npairs, emu->max_kchunk);
+    if (splits < 1) return RR_ERR_ARG;
+  } else if (tiles * npairs < sms) {
+    splits = (int)(sms / (tiles * npairs));
     if (splits > nk) splits = nk;
     if (splits < 1) splits = 1;
   }
@@ -416,6 +482,7 @@ static rr_status gemm_bf16_tc_impl(int64_t M, int64_t N, int64_t K, const __nv_b
   if (emu && per * kBK > emu->max_kchunk) per = emu->max_kchunk / kBK;  // exactness of the FP32 sums
   if (per < 1) return RR_ERR_ARG;
   splits = (nk + per - 1) / per;
+  if (emu && emu->part && splits != tc_emu_partial_splits(M, K, npairs, emu->max_kchunk)) return RR_ERR_ARG;
   const uint32_t stage_bytes = kBM * kBK * 2 + (uint32_t)npad * kBK * 2;
   int stages = (int)((200 * 1024) / stage_bytes);
   if (stages > 8) stages = 8;
@@ -436,19 +503,23 @@ static rr_status gemm_bf16_tc_impl(int64_t M, int64_t N, int64_t K, const __nv_b
   a.R = R;
   a.ldr = ldr;
   a.coef = coef;
-  a.atomic = splits > 1;
+  a.atomic = splits > 1 || npairs > 1;
   a.C64 = emu ? emu->C64 : nullptr;
   a.ldc64 = emu ? emu->ldc64 : 0;
+  a.part = emu ? emu->part : nullptr;
   a.rexp = emu ? emu->rexp : nullptr;
-  a.rshift = emu ? emu->rshift : 0;
-  a.cscale = emu ? emu->cscale : nullptr;
+  a.cexp = emu ? emu->cexp : nullptr;
   a.nb = emu ? emu->nb : 1;
+  a.a_slice_rows = emu ? emu->a_slice_rows : 0;
+  a.b_slice_rows = emu ? emu->b_slice_rows : 0;
+  a.npairs = emu ? npairs : 0;
+  for (int z = 0; z < 48; ++z) a.pair[z] = (emu && z < npairs) ? emu->pair[z] : 0u;
   if (splits > 1 && !emu) {
     dim3 gi((unsigned)std::min<int64_t>((M + 255) / 256, 256), (unsigned)N);
     k_tc_init_c<<<gi, 256, 0, s>>>(M, N, C, ldc, R, ldr, coef);
     note_launches(1);
   }
-  dim3 grid((unsigned)tiles, (unsigned)splits);
+  dim3 grid((unsigned)tiles, (unsigned)splits, (unsigned)npairs);
   k_gemm_bf16_tc<<<grid, 128, smem, s>>>(ta, tb, a);
   return check_launch("gemm_bf16_tc");
 }

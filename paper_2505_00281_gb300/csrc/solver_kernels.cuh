@@ -41,6 +41,28 @@ rr_status sub_lowrank_f32(cudaStream_t s, int64_t n, int64_t b, int64_t p, const
 rr_status tc_take_error(cudaStream_t s);
 rr_status tc_prepare_attributes();
 
+// Tensor-core launch of an FP64-emulation product (k_gemm_tc.cu): the sum
+// over slice pairs (pair[z] = p0 | q0 << 8 | nq << 16, 0-based) of the A
+// slice p0 times B slices q0 (and q0 + 1 when nq = 2), element (row, col)
+// scaled by 2^(rexp[row] + cexp[col] - 6 (p0 + 1) - 6 (q0 + nq)); added into
+// C64 (ld ldc64) or written as one M x nb partial (ld M) per (pair, K split).
+struct TcEmu {
+  double* C64;
+  int64_t ldc64;
+  double* part;
+  const int* rexp;
+  const int* cexp;
+  int nb;
+  int a_slices, b_slices;          // slices stacked in the A / B operands
+  int a_slice_rows, b_slice_rows;  // rows of one slice in the tensor-map outer dimension
+  int npairs;                      // <= 48
+  const uint32_t* pair;            // host array
+  int max_kchunk;                  // K elements per exact FP32 accumulation
+};
+rr_status gemm_bf16_tc_emu(int64_t M, int64_t N, int64_t K, const __nv_bfloat16* A, int64_t lda,
+                           const __nv_bfloat16* B, int64_t ldb, const TcEmu& e, cudaStream_t s);
+int tc_emu_partial_splits(int64_t M, int64_t K, int npairs, int max_kchunk);
+
 // FP64-accurate products on the tensor cores (k_f64emu.cu)
 struct EmuOperator {
   int64_t m, n;
@@ -57,4 +79,9 @@ rr_status emu_prepare(cudaStream_t s, const double* A, int64_t m, int64_t n, int
 rr_status emu_gemm(cudaStream_t s, const EmuOperator& op, int trans, int64_t N, const double* X,
                    int64_t ldx, double* C, int64_t ldc, void* mem);
 rr_status vec_scale(cudaStream_t s, int64_t n, double alpha, const double* a, double* d);
+bool emu_gram_supported(int64_t n, int64_t p, int64_t q);
+size_t emu_gram_bytes(int64_t n, int64_t p, int64_t q);
+rr_status emu_gram(cudaStream_t s, int64_t n, int64_t p, int64_t q, int32_t xt, const void* X, int64_t ldx,
+                   int32_t yt, const void* Y, int64_t ldy, double* G, int64_t ldg, int accum, void* mem,
+                   size_t bytes);
 }  // namespace rr

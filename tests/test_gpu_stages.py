@@ -120,6 +120,28 @@ def test_gemm_f64_emulated_matches_fp64(rr, trans, M, N, K):
     assert np.max(err / (np.abs(Aop) @ np.abs(B))) < 1e-12
 
 
+@pytest.mark.parametrize("trans", [0, 1])
+def test_f64_emulation_exact_on_integers(rr, trans):
+    """Integer operands that the slices carry exactly (|entries| < 2^15, so
+    every entry is a multiple of its row's or column's 2^-48 slice unit) and
+    whose exact products stay below 2^53: the tensor-core sums, the FP32
+    accumulation over K chunks, the epilogue's integer combination and the
+    FP64 additions are then all exact, so the emulated product must equal the
+    integer product bit for bit.  Also pins the Gram path (both operands
+    sliced) the same way.  K spans several 4096-long chunks and a ragged
+    tail."""
+    rng = np.random.default_rng(77 + trans)
+    M, N, K = 304, 96, 9000
+    A = rng.integers(-2 ** 15 + 1, 2 ** 15, (K, M) if trans else (M, K)).astype(np.int64)
+    B = rng.integers(-2 ** 15 + 1, 2 ** 15, (K, N)).astype(np.int64)
+    ref = (A.T if trans else A) @ B  # |ref| < 9000 * 2^30 < 2^44: exact in FP64
+    C = rr.rr_gemm_f64_emulated(trans, dev(A.astype(np.float64)), dev(B.astype(np.float64)))
+    assert np.array_equal(host(C), ref.astype(np.float64))
+    X = rng.integers(-2 ** 15 + 1, 2 ** 15, (K, 130)).astype(np.int64)
+    G = rr.rr_gram(dev(X.astype(np.float64)), dev(B.astype(np.float64)))
+    assert np.array_equal(host(G), (X.T @ B).astype(np.float64))
+
+
 # ---------------------------------------------------------------- a4 (Algorithm 8)
 @pytest.mark.parametrize("n,k", [(1000, 48), (20000, 32), (77, 77), (5, 3)])
 def test_hessenberg_bitexact_fp32(rr, n, k):
@@ -167,6 +189,34 @@ def test_gram_fp64_accurate_mixed_types(rr):
     assert np.all(np.abs(host(G) - ref) <= 2 * bound)
     G2 = rr.rr_gram(dev(Y), dev(Y))
     assert np.all(np.abs(host(G2) - Y.T @ Y) <= 2 * n * U53 * (np.abs(Y).T @ np.abs(Y)))
+
+
+def test_gram_tensor_core_path_wide_range(rr):
+    """The tensor-core Gram path (n % 8 == 0, q <= 128): ragged tiles, a K
+    range that is not a multiple of the 4096-long exact chunks, columns
+    spanning many binades and rows far below the column maxima, mixed storage
+    types and accumulation.  Bound: the slice truncation (2^-47 n times the
+    column maxima) plus the FP64 reference's own rounding."""
+    rng = np.random.default_rng(31)
+    n, p, q = 8200, 130, 100
+    X = rng.standard_normal((n, p)) * np.exp2(rng.integers(-30, 30, p))[None, :]
+    X[rng.random((n, p)) < 0.3] *= 1e-9
+    Y = rng.standard_normal((n, q)) * np.exp2(rng.integers(-20, 20, q))[None, :]
+    ref = X.T @ Y
+    tail = 2 * n * U53 * (np.abs(X).T @ np.abs(Y))
+    trunc = 2.0 ** -47 * n * np.outer(np.abs(X).max(0), np.abs(Y).max(0))
+    G = host(rr.rr_gram(dev(X), dev(Y)))
+    assert np.all(np.abs(G - ref) <= trunc + tail)
+    # mixed types: BF16 X, FP32 Y, accumulated onto an existing G
+    Xb = O.round_bf16(X)
+    Yf = Y.astype(np.float32).astype(np.float64)
+    G0 = rng.standard_normal((p, q))
+    Gd = dev(G0)
+    rr.rr_gram(dev(Xb, torch.bfloat16), dev(Yf, torch.float32), G=Gd, accumulate=True)
+    ref2 = G0 + Xb.T @ Yf
+    bound2 = 2.0 ** -47 * n * np.outer(np.abs(Xb).max(0), np.abs(Yf).max(0)) + 2 * n * U53 * (
+        np.abs(G0) + np.abs(Xb).T @ np.abs(Yf))
+    assert np.all(np.abs(host(Gd) - ref2) <= bound2)
 
 
 # ---------------------------------------------------------------- a6
