@@ -85,36 +85,46 @@ __global__ void __launch_bounds__(kSmallThreads) k_tri_inv_lower(int b, const do
   }
 }
 
-// Small FP64 GEMM: C = alpha op(A) op(B) + beta C.  16 x 16 output tiles,
+// C = alpha op(A) op(B) + beta C for the small projected matrices (FP64
+// operands and result).  TA is the arithmetic: double, or float for
+// correction terms whose own size is small, so that FP32 relative accuracy
+// of the product is FP64 accuracy of the result (operands rounded to FP32,
+// FP32 accumulation, FP64 combination with beta C).  16 x 16 output tiles,
 // one output per thread, so a 256 x 256 product spreads over 256 CTAs (FP64
-// issue rate per SM is the limit on GB300, so the work must cover the GPU).
-__global__ void __launch_bounds__(256) k_gemm_f64_small(int ta, int tb, int M, int N, int K,
-                                                        double alpha, const double* __restrict__ A,
-                                                        int lda, const double* __restrict__ B,
-                                                        int ldb, double beta, double* __restrict__ C,
-                                                        int ldc) {
-  __shared__ double As[32][17];
-  __shared__ double Bs[32][17];
+// issue rate per SM is the limit on GB300, so the work must cover the GPU);
+// K in panels of KP staged in shared memory with all of a panel's loads in
+// flight at once.
+template <typename TA, int KP>
+__global__ void __launch_bounds__(256) k_gemm_small(int ta, int tb, int M, int N, int K, double alpha,
+                                                    const double* __restrict__ A, int lda,
+                                                    const double* __restrict__ B, int ldb, double beta,
+                                                    double* __restrict__ C, int ldc) {
+  __shared__ TA As[KP][17];
+  __shared__ TA Bs[KP][17];
   const int m0 = blockIdx.x * 16, n0 = blockIdx.y * 16;
   const int tid = threadIdx.x, ti = tid % 16, tj = tid / 16;
-  double acc = 0.0;
-  for (int k0 = 0; k0 < K; k0 += 32) {
-    for (int e = tid; e < 32 * 16; e += 256) {
-      int kk = e % 32, i = e / 32;
-      int gk = k0 + kk, gi = m0 + i, gj = n0 + i;
-      As[kk][i] = (gk < K && gi < M) ? (ta ? A[gk + gi * lda] : A[gi + gk * lda]) : 0.0;
-      Bs[kk][i] = (gk < K && gj < N) ? (tb ? B[gj + gk * ldb] : B[gk + gj * ldb]) : 0.0;
+  TA acc = TA(0);
+  for (int k0 = 0; k0 < K; k0 += KP) {
+    for (int e = tid; e < KP * 16; e += 256) {
+      // consecutive threads along the operand's contiguous dimension
+      const int ka = ta ? e % KP : e / 16, ia = ta ? e / KP : e % 16;
+      const int gk = k0 + ka, gi = m0 + ia;
+      As[ka][ia] = (gk < K && gi < M) ? (TA)(ta ? A[gk + (size_t)gi * lda] : A[gi + (size_t)gk * lda]) : TA(0);
+      const int kb = tb ? e / 16 : e % KP, jb = tb ? e % 16 : e / KP;
+      const int gkb = k0 + kb, gj = n0 + jb;
+      Bs[kb][jb] = (gkb < K && gj < N) ? (TA)(tb ? B[gj + (size_t)gkb * ldb] : B[gkb + (size_t)gj * ldb]) : TA(0);
     }
     __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < 32; ++kk) acc = fma(As[kk][ti], Bs[kk][tj], acc);
+    const int kn = K - k0 < KP ? K - k0 : KP;
+#pragma unroll 8
+    for (int kk = 0; kk < kn; ++kk) acc = fma(As[kk][ti], Bs[kk][tj], acc);
     __syncthreads();
   }
-  int i = m0 + ti, j = n0 + tj;
+  const int i = m0 + ti, j = n0 + tj;
   if (i < M && j < N) {
-    double v = alpha * acc;
-    if (beta != 0.0) v += beta * C[i + j * ldc];
-    C[i + j * ldc] = v;
+    double v = alpha * (double)acc;
+    if (beta != 0.0) v += beta * C[i + (size_t)j * ldc];
+    C[i + (size_t)j * ldc] = v;
   }
 }
 
@@ -122,7 +132,14 @@ static void gemm_small(cudaStream_t s, int ta, int tb, int M, int N, int K, doub
                        const double* A, int lda, const double* B, int ldb, double beta, double* C,
                        int ldc) {
   dim3 g((M + 15) / 16, (N + 15) / 16);
-  k_gemm_f64_small<<<g, 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  k_gemm_small<double, 128><<<g, 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+}
+
+static void gemm_mixed(cudaStream_t s, int ta, int tb, int M, int N, int K, double alpha,
+                       const double* A, int lda, const double* B, int ldb, double beta, double* C,
+                       int ldc) {
+  dim3 g((M + 15) / 16, (N + 15) / 16);
+  k_gemm_small<float, 256><<<g, 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
 }
 
 // Symmetrise C, shift it to positive definite by a Gershgorin bound
@@ -345,8 +362,208 @@ __global__ void __launch_bounds__(kSmallThreads) k_chol_inv_f32(int b, const dou
   }
 }
 
-// E <- E - diag(kept)  (E = W^T G W, so E becomes W^T G W - I on the kept part)
-// then F = I - E/2 (+ 3/8 E2 if given)
+// Blocked variant for b <= 256 (the same factorisation, drop rule and
+// output), 32 x 32 tiles of the lower triangle in shared memory, one CTA:
+//   per 32-wide panel k: warp 0 factors the diagonal tile (warp-synchronous,
+//   the pivot test of the unblocked kernel per column); one thread per row
+//   solves the panel's tiles below against it (dropped columns zero); every
+//   warp applies tile products of the trailing update (register-blocked);
+//   inverse: diagonal tiles inverted by one warp each (column per lane), then
+//   block row I of L^-1 from X(I,K) = -X(I,I) sum_{J=K..I-1} L(I,J) X(J,K).
+// About 40 CTA barriers instead of 4 per column.
+constexpr int kCT = 32;      // tile
+constexpr int kCLd = 33;     // padded row length
+constexpr int kCTMax = 8;    // tiles per side (b <= 256)
+constexpr int kChThreads = 512;  // 128 registers per thread: the 32-entry row stays in registers
+__device__ __forceinline__ int ctile(int I, int J) { return I * (I + 1) / 2 + J; }
+
+// C[r][c] += sgn * sum_l A[r][l] * Bop(l, c) for 32 x 32 tiles, one warp,
+// lane = c.  btrans: Bop(l, c) = B[c][l] (A B^T), else B[l][c] (A B).
+__device__ __forceinline__ void warp_tile_mac(float* C, const float* A, const float* B, bool btrans,
+                                              float sgn, int lane) {
+  float bv[kCT];
+#pragma unroll
+  for (int l = 0; l < kCT; ++l) bv[l] = btrans ? B[lane * kCLd + l] : B[l * kCLd + lane];
+  for (int r = 0; r < kCT; ++r) {
+    float acc = 0.f;
+#pragma unroll
+    for (int l = 0; l < kCT; ++l) acc = fmaf(A[r * kCLd + l], bv[l], acc);
+    C[r * kCLd + lane] = fmaf(sgn, acc, C[r * kCLd + lane]);
+  }
+}
+
+__global__ void __launch_bounds__(kChThreads, 1) k_chol_inv_blocked(int b, const double* __restrict__ G, int ldg,
+                                                                    int* __restrict__ dropped,
+                                                                    double* __restrict__ W) {
+  extern __shared__ float cs_raw[];
+  const int nt = (b + kCT - 1) / kCT;
+  const int ntiles = nt * (nt + 1) / 2;
+  float* Ts = cs_raw;                                   // [ntiles][32][33]
+  float* Ss = Ts + (size_t)ntiles * kCT * kCLd;         // [nt - 1][32][33] scratch
+  float* gd = Ss + (size_t)(nt > 1 ? nt - 1 : 1) * kCT * kCLd;  // [32 nt]
+  int* sdrop = reinterpret_cast<int*>(gd + kCT * nt);   // [32 nt]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kChThreads / 32;
+  auto T = [&](int I, int J) { return Ts + (size_t)ctile(I, J) * kCT * kCLd; };
+  // symmetrised copy, thread = (r, c) of every tile (kCT x kCT / kChThreads
+  // passes); rows/columns beyond b padded with the identity
+  for (int rc = tid; rc < kCT * kCT; rc += kChThreads) {
+    const int r = rc % kCT, c = rc / kCT;
+    int I = 0, J = 0;
+#pragma unroll 4
+    for (int t = 0; t < ntiles; ++t) {
+      const int gi = I * kCT + r, gj = J * kCT + c;
+      float v;
+      if (gi < b && gj < b) v = (float)(0.5 * (G[gi + (size_t)gj * ldg] + G[gj + (size_t)gi * ldg]));
+      else v = (gi == gj) ? 1.f : 0.f;
+      Ts[(size_t)t * kCT * kCLd + r * kCLd + c] = v;
+      if (++J > I) {
+        ++I;
+        J = 0;
+      }
+    }
+  }
+  for (int i = tid; i < kCT * nt; i += kChThreads) gd[i] = i < b ? (float)G[i + (size_t)i * ldg] : 1.f;
+  __syncthreads();
+  for (int k = 0; k < nt; ++k) {
+    float* D = T(k, k);
+    if (warp == 0) {
+      // lane r holds the trailing part of row r (columns j..31 in a[0..31-j],
+      // shifted left after every column, so the current column is a[0] and
+      // the loop over j stays rolled); column j travels by shuffle
+      float a[kCT];
+#pragma unroll
+      for (int c = 0; c < kCT; ++c) a[c] = D[lane * kCLd + c];
+      for (int j = 0; j < kCT; ++j) {
+        const float d = __shfl_sync(0xffffffffu, a[0], j);
+        const float g0 = gd[k * kCT + j];
+        const bool keep = g0 > 0.f && d > 64.f * 0x1p-24f * g0;
+        const float ljj = keep ? sqrtf(d) : 1.f;
+        if (lane > j) a[0] = keep ? a[0] / ljj : 0.f;
+        if (lane == j) {
+          a[0] = ljj;
+          if (!keep)
+            for (int c = 0; c < j; ++c) D[j * kCLd + c] = 0.f;
+        }
+        if (lane == 0) sdrop[k * kCT + j] = keep ? 0 : 1;
+        if (lane >= j) D[lane * kCLd + j] = a[0];  // column j of L (and the diagonal)
+#pragma unroll
+        for (int u = 1; u < kCT; ++u) {
+          const float lcj = __shfl_sync(0xffffffffu, a[0], (j + u) & 31);
+          if (keep && j + u < kCT && lane >= j + u) a[u] = fmaf(-a[0], lcj, a[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < kCT - 1; ++u) a[u] = a[u + 1];
+      }
+    }
+    __syncthreads();
+    // dropped columns of this panel: zero their rows in the earlier panels
+    for (int e = tid; e < k * kCT * kCT; e += kChThreads) {
+      const int J = e / (kCT * kCT), rc = e % (kCT * kCT), r = rc / kCT, c = rc % kCT;
+      if (sdrop[k * kCT + r]) T(k, J)[r * kCLd + c] = 0.f;
+    }
+    // panel tiles below: row x of tile (I, k) solves x L(k,k)^T = a
+    for (int row = tid; row < (nt - 1 - k) * kCT; row += kChThreads) {
+      const int I = k + 1 + row / kCT, r = row % kCT;
+      float* a = T(I, k) + r * kCLd;
+      float x[kCT];
+#pragma unroll
+      for (int j = 0; j < kCT; ++j) {
+        float v = a[j];
+#pragma unroll
+        for (int l = 0; l < j; ++l) v = fmaf(-x[l], D[j * kCLd + l], v);
+        x[j] = sdrop[k * kCT + j] ? 0.f : v / D[j * kCLd + j];
+      }
+#pragma unroll
+      for (int j = 0; j < kCT; ++j) a[j] = x[j];
+    }
+    __syncthreads();
+    // trailing update A(I,J) -= L(I,k) L(J,k)^T, k < J <= I
+    {
+      const int m = nt - 1 - k;  // tiles below the panel
+      for (int t = warp; t < m * (m + 1) / 2; t += nw) {
+        int I = 0;
+        while ((I + 1) * (I + 2) / 2 <= t) ++I;
+        const int J = t - I * (I + 1) / 2;
+        warp_tile_mac(T(k + 1 + I, k + 1 + J), T(k + 1 + I, k), T(k + 1 + J, k), true, -1.f, lane);
+      }
+    }
+    __syncthreads();
+  }
+  // inverse of the diagonal tiles, one warp each, lane = column
+  for (int k = warp; k < nt; k += nw) {
+    float* D = T(k, k);
+    float x[kCT];
+#pragma unroll
+    for (int r = 0; r < kCT; ++r) {
+      float v = (r == lane) ? 1.f : 0.f;
+#pragma unroll
+      for (int l = 0; l < r; ++l) v = fmaf(-D[r * kCLd + l], x[l], v);
+      x[r] = (r < lane) ? 0.f : v / D[r * kCLd + r];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < kCT; ++r) D[r * kCLd + lane] = x[r];
+  }
+  __syncthreads();
+  // block rows of L^-1: S(K) = sum_{J=K..I-1} L(I,J) X(J,K), then
+  // X(I,K) = -X(I,I) S(K); one warp per (K, 8-row slice)
+  for (int I = 1; I < nt; ++I) {
+    for (int t = warp; t < I * 4; t += nw) {
+      const int K = t >> 2, r0 = (t & 3) * 8;
+      float* S = Ss + (size_t)K * kCT * kCLd;
+      float acc[8] = {};
+      for (int J = K; J < I; ++J) {
+        const float* A = T(I, J);
+        const float* B = T(J, K);
+        float bv[kCT];
+#pragma unroll
+        for (int l = 0; l < kCT; ++l) bv[l] = B[l * kCLd + lane];
+#pragma unroll
+        for (int rr = 0; rr < 8; ++rr) {
+#pragma unroll
+          for (int l = 0; l < kCT; ++l) acc[rr] = fmaf(A[(r0 + rr) * kCLd + l], bv[l], acc[rr]);
+        }
+      }
+#pragma unroll
+      for (int rr = 0; rr < 8; ++rr) S[(r0 + rr) * kCLd + lane] = acc[rr];
+    }
+    __syncthreads();
+    for (int t = warp; t < I * 4; t += nw) {
+      const int K = t >> 2, r0 = (t & 3) * 8;
+      const float* A = T(I, I);
+      const float* B = Ss + (size_t)K * kCT * kCLd;
+      float bv[kCT];
+#pragma unroll
+      for (int l = 0; l < kCT; ++l) bv[l] = B[l * kCLd + lane];
+      float* X = T(I, K);
+#pragma unroll
+      for (int rr = 0; rr < 8; ++rr) {
+        float acc = 0.f;
+#pragma unroll
+        for (int l = 0; l < kCT; ++l) acc = fmaf(A[(r0 + rr) * kCLd + l], bv[l], acc);
+        X[(r0 + rr) * kCLd + lane] = -acc;
+      }
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < b; i += kChThreads) dropped[i] = sdrop[i];
+  // W0 = (L^-1)^T, dropped columns zero
+  for (int e = tid; e < b * b; e += kChThreads) {
+    const int i = e % b, j = e / b;
+    float v = 0.f;
+    if (!sdrop[j] && j >= i) v = T(j / kCT, i / kCT)[(j % kCT) * kCLd + (i % kCT)];
+    W[i + (size_t)j * b] = (double)v;
+  }
+}
+
+static size_t chol_blocked_smem(int b) {
+  const int nt = (b + kCT - 1) / kCT;
+  return ((size_t)(nt * (nt + 1) / 2 + (nt > 1 ? nt - 1 : 1)) * kCT * kCLd + 2 * (size_t)kCT * nt) * sizeof(float);
+}
+
+// mode 0: E <- E - diag(kept)  (E = W^T G W, so E becomes W^T G W - I on the
+// kept part); mode 1: F = E/2 - 3/8 E2, the correction of
+// W <- W (I - E/2 + 3/8 E^2) = W - W F
 __global__ void k_whiten_corr(int b, double* __restrict__ E, const double* __restrict__ E2,
                               const int* __restrict__ dropped, double* __restrict__ F, int stage) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -358,9 +575,7 @@ __global__ void k_whiten_corr(int b, double* __restrict__ E, const double* __res
     E[e] = v;
     return;
   }
-  double f = (i == j ? 1.0 : 0.0) - 0.5 * v;
-  if (E2) f += 0.375 * E2[e];
-  F[e] = f;
+  F[e] = 0.5 * v - 0.375 * E2[e];
 }
 
 // One-sided block Jacobi (Hestenes) on the columns of M (r x cpad, FP32):
@@ -680,18 +895,11 @@ __global__ void k_v32_to_64(int c, int cpad, const float* __restrict__ V32, doub
   }
 }
 
-// F = 1.5 I - 0.5 T
-__global__ void k_ns_coef(int c, const double* __restrict__ T, double* __restrict__ F) {
-  int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= c * c) return;
-  int i = e % c, j = e / c;
-  F[e] = (i == j ? 1.5 : 0.0) - 0.5 * T[e];
-}
 
 struct PencilWs {
   double *W1, *W2, *T, *E, *E2, *F, *C, *V, *Vp, *M, *Mp, *sig, *mu;
   float *L32, *Li32, *M32, *V32, *fs;  // fs: [0] Jacobi norm floor, [1] scale
-  int *drop1, *drop2, *order, *nvalid, *rot, *err, *sweeps;
+  int *drop1, *drop2, *order, *nvalid, *rot, *err, *sweeps, *cid, *cst;
   GridBarrier* bar;
 };
 
@@ -746,35 +954,49 @@ static bool carve_pencil(Arena& ar, int b1, int b2, PencilWs& w) {
   w.rot = ar.take<int>(64);
   w.err = ar.take<int>(1);
   w.sweeps = ar.take<int>(2);
+  w.cid = ar.take<int>(cp);
+  w.cst = ar.take<int>(cp + 1);
   w.bar = ar.take<GridBarrier>(1);
   return !ar.overflow;
 }
 
 // Whitening matrix W (b x b) with W^T G W = I on the kept part: FP32
-// Cholesky for W0 = L^-T, then two steps of FP64 iterative refinement,
-// W <- W (I - E/2 + 3/8 E^2), E = W^T G W - I, whose error squares per step.
+// Cholesky for W0 = L^-T, then three steps of iterative refinement
+// W <- W (I - E/2 + 3/8 E^2), E = W^T G W - I, whose error cubes per step.
+// E is formed in FP64; the correction W (E/2 - 3/8 E^2) only needs FP32
+// relative accuracy (its rounding, u32 |E|, is what the next step removes),
+// so E^2 and W F are FP32 products.
 static void whiten(cudaStream_t s, int b, const double* G, PencilWs& w, int* dropped, double* Wout) {
   const int g1 = (b * b + 255) / 256;
-  const size_t sm = ((size_t)b * (b + 1) / 2 + 2 * (size_t)b) * sizeof(float);
-  if (sm > 48 * 1024)
-    cudaFuncSetAttribute(k_chol_inv_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_chol_inv_f32<<<1, kSmallThreads, sm, s>>>(b, G, b, dropped, w.W1);
-  // three refinement steps W <- W (I - E/2 + 3/8 E^2), E = W^T G W - I;
-  // each cubes the error (|E| ~ u32 cond(G) after the FP32 factorisation)
+  if (b <= kCT * kCTMax) {
+    const size_t sm = chol_blocked_smem(b);
+    if (sm > 48 * 1024)
+      cudaFuncSetAttribute(k_chol_inv_blocked, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_chol_inv_blocked<<<1, kChThreads, sm, s>>>(b, G, b, dropped, w.W1);
+  } else {
+    const size_t sm = ((size_t)b * (b + 1) / 2 + 2 * (size_t)b) * sizeof(float);
+    if (sm > 48 * 1024)
+      cudaFuncSetAttribute(k_chol_inv_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_chol_inv_f32<<<1, kSmallThreads, sm, s>>>(b, G, b, dropped, w.W1);
+  }
+  // every step writes the other buffer (the products never run in place);
+  // the result is copied to Wout at the end (which may be either buffer)
   double* Wc = w.W1;
   double* Wn = w.W2;
   for (int it = 0; it < 3; ++it) {
-    gemm_small(s, 0, 0, b, b, b, 1.0, G, b, Wc, b, 0.0, w.T, b);
-    gemm_small(s, 1, 0, b, b, b, 1.0, Wc, b, w.T, b, 0.0, w.E, b);
+    gemm_small(s, 0, 0, b, b, b, 1.0, G, b, Wc, b, 0.0, w.T, b);        // T = G W
+    gemm_small(s, 1, 0, b, b, b, 1.0, Wc, b, w.T, b, 0.0, w.E, b);      // E = W^T T
     k_whiten_corr<<<g1, 256, 0, s>>>(b, w.E, nullptr, dropped, nullptr, 0);
-    gemm_small(s, 0, 0, b, b, b, 1.0, w.E, b, w.E, b, 0.0, w.E2, b);
-    k_whiten_corr<<<g1, 256, 0, s>>>(b, w.E, w.E2, dropped, w.F, 1);
-    gemm_small(s, 0, 0, b, b, b, 1.0, Wc, b, w.F, b, 0.0, it == 2 ? Wout : Wn, b);
+    gemm_mixed(s, 0, 0, b, b, b, 1.0, w.E, b, w.E, b, 0.0, w.E2, b);    // E^2
+    k_whiten_corr<<<g1, 256, 0, s>>>(b, w.E, w.E2, dropped, w.F, 1);    // F = E/2 - 3/8 E^2
+    cudaMemcpyAsync(Wn, Wc, (size_t)b * b * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    gemm_mixed(s, 0, 0, b, b, b, -1.0, Wc, b, w.F, b, 1.0, Wn, b);      // W - W F
     double* t = Wc;
     Wc = Wn;
     Wn = t;
   }
-  note_launches(17);
+  if (Wc != Wout) cudaMemcpyAsync(Wout, Wc, (size_t)b * b * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  note_launches(16);
 }
 
 // floor[0] = scale * max_j |M(:, j)|^2 (one block)
@@ -832,56 +1054,223 @@ static rr_status launch_bj(cudaStream_t s, int r, int cpad, int w, int P, float*
   return RR_OK;
 }
 
-// Omega (c x c) from K = N^T N: for i < j the exact one-sided Jacobi angle
-// that makes columns i and j of N orthogonal, Omega_ij = phi, Omega_ji = -phi
-// (V <- V (I + Omega) to first order).  Zero columns are never rotated.
-__global__ void k_polish_angles(int c, const double* __restrict__ K, double* __restrict__ Om) {
-  int e = blockIdx.x * blockDim.x + threadIdx.x;
+// ---------------------------------------------------------------------------
+// FP64 refinement of the FP32 Jacobi result (a Newton-type correction built
+// from small GEMMs, in the manner of Ogita and Aishima's refinement of
+// eigenvector bases).  With N = C V, K = N^T N (FP64), T = V^T V,
+// lam_i = K_ii / T_ii and the coupling corrected for non-orthogonality
+// c_ij = K_ij - (lam_i + lam_j) T_ij / 2, the update is V <- V (I + E),
+//   E = (I - T)/2 + W,   W_ij = atan(2 c_ij / (lam_j - lam_i)) / 2 (skew),
+// the exact angle of each pair (first order in the pairs' interaction), which
+// orthogonalises V and diagonalises K with both defects squaring per step
+// (applied as V (I + (I - T)/2 + W), the cross term being second order).
+// Pairs that need a large rotation (|W_ij| > kBigAngle: close values with a
+// coupling above rounding level) interact, and composing such rotations
+// simultaneously diverges; they join clusters (runs of close values in sorted order, at
+// most kClMax), and each cluster's block is diagonalised exactly instead
+// (two-sided FP64 Jacobi, one warp per cluster), its rotation taking the
+// place of W on the block.
+// ---------------------------------------------------------------------------
+constexpr double kBigAngle = 0.003;
+// couplings at the rounding level of K (relative to the pair's lam) carry no
+// direction information: such pairs are neither rotated nor linked (for
+// (near-)equal lam their exact angle would be an arbitrary large rotation)
+constexpr double kCoupleNoise = 1e-13;
+constexpr int kClMax = 32;          // largest cluster resolved as one block
+constexpr int kClWarps = 8;         // clusters resolved at once
+
+__device__ __forceinline__ double oa_coupling(const double* K, const double* T, int c, int i, int j,
+                                              double li, double lj) {
+  return K[i + (size_t)j * c] - 0.5 * (li + lj) * T[i + (size_t)j * c];
+}
+
+// F1 = I + (I - T)/2 + W, W the exact pair angles outside the clusters
+// (cid: cluster ids, -1 none); within a cluster only the orthogonality part
+__global__ void k_oa_update(int c, const double* __restrict__ K, const double* __restrict__ T,
+                            const int* __restrict__ cid, double* __restrict__ F1) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= c * c) return;
-  int i = e % c, j = e / c;
-  if (i == j) {
-    Om[e] = 0.0;
+  const int i = e % c, j = e / c;
+  const double Tij = T[e];
+  double f = (i == j) ? 1.0 + 0.5 * (1.0 - Tij) : -0.5 * Tij;
+  if (i != j && !(cid[i] >= 0 && cid[i] == cid[j])) {
+    const double li = K[i + (size_t)i * c] / T[i + (size_t)i * c];
+    const double lj = K[j + (size_t)j * c] / T[j + (size_t)j * c];
+    const double cij = oa_coupling(K, T, c, i, j, li, lj);
+    if (fabs(cij) > kCoupleNoise * fmax(fabs(li), fabs(lj))) f += 0.5 * atan(2.0 * cij / (lj - li));
+  }
+  F1[e] = f;
+}
+
+// Cluster detection and resolution (one CTA).  Sorted by lam, a pair
+// needing |W_ij| > kBigAngle links every sorted position between its two
+// members; the linked runs (at most kClMax) are the clusters.  The ordering
+// and the link test are thresholds and run in FP32.  Each cluster's block
+// B - mean(lam) I (B_ab = c_ab, B_aa = lam_a, formed in FP64) has entries of
+// the size of the cluster's spread and couplings, so FP32 two-sided Jacobi on
+// it gives the rotation Q to FP32 relative accuracy (the next FP64 step
+// squares the rest away).  Outputs: cid (cluster id per index, -1 none),
+// ord / st (members of cluster q: ord[st[q] .. st[q+1]-1]) and Qb (c x c,
+// only the cluster blocks are written).
+__global__ void __launch_bounds__(1024) k_cluster_rot(int c, const double* __restrict__ K,
+                                                      const double* __restrict__ T,
+                                                      double* __restrict__ Qb, int* __restrict__ cid,
+                                                      int* __restrict__ ord, int* __restrict__ st) {
+  extern __shared__ double cl_smem[];
+  double* lam = cl_smem;                                       // [c]
+  float* Bw = reinterpret_cast<float*>(lam + c);               // [kClWarps][kClMax][kClMax + 1]
+  float* Qw = Bw + kClWarps * kClMax * (kClMax + 1);
+  float* lamf = Qw + kClWarps * kClMax * (kClMax + 1);         // [c]
+  int* order = reinterpret_cast<int*>(lamf + c);               // [c]
+  int* pos = order + c;                                        // [c]
+  int* link = pos + c;                                         // [c + 1] difference array of links
+  int* start = link + c + 1;                                   // [c + 1]
+  __shared__ int s_ncl;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < c; i += blockDim.x) {
+    lam[i] = K[i + (size_t)i * c] / T[i + (size_t)i * c];
+    lamf[i] = (float)lam[i];
+  }
+  for (int i = tid; i <= c; i += blockDim.x) link[i] = 0;
+  __syncthreads();
+  for (int i = tid; i < c; i += blockDim.x) {
+    const float li = lamf[i];
+    int rank = 0;
+    for (int j = 0; j < c; ++j) rank += (lamf[j] < li || (lamf[j] == li && j < i)) ? 1 : 0;
+    order[rank] = i;
+    pos[i] = rank;
+  }
+  __syncthreads();
+  const float tb = (float)tan(2.0 * kBigAngle);
+  for (int e = tid; e < c * c; e += blockDim.x) {
+    const int i = e % c, j = e / c;
+    if (i >= j) continue;
+    const float cij = (float)K[e] - 0.5f * (lamf[i] + lamf[j]) * (float)T[e];
+    if (fabsf(2.f * cij) > tb * fabsf(lamf[j] - lamf[i]) &&
+        fabsf(cij) > (float)kCoupleNoise * fmaxf(fabsf(lamf[i]), fabsf(lamf[j]))) {
+      const int a = min(pos[i], pos[j]), b = max(pos[i], pos[j]);
+      atomicAdd(&link[a], 1);
+      atomicAdd(&link[b], -1);
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int n = 0, len = 1, run = link[0];
+    start[0] = 0;
+    for (int k = 1; k < c; ++k) {
+      // positions k-1 and k are linked when a large pair spans them
+      if (run > 0 && len < kClMax) {
+        ++len;
+      } else {
+        start[++n] = k;
+        len = 1;
+      }
+      run += link[k];
+    }
+    start[++n] = c;
+    s_ncl = n;
+  }
+  __syncthreads();
+  const int ncl = s_ncl;
+  for (int q = tid; q < ncl; q += blockDim.x)
+    for (int k = start[q]; k < start[q + 1]; ++k) cid[order[k]] = (start[q + 1] - start[q] > 1) ? q : -1;
+  for (int k = tid; k < c; k += blockDim.x) ord[k] = order[k];
+  for (int q = tid; q <= ncl; q += blockDim.x) st[q] = start[q];
+  if (warp >= kClWarps) return;
+  float* B = Bw + (size_t)warp * kClMax * (kClMax + 1);
+  float* Q = Qw + (size_t)warp * kClMax * (kClMax + 1);
+  const int ld = kClMax + 1;
+  for (int q = warp; q < ncl; q += kClWarps) {
+    const int k0 = start[q], m = start[q + 1] - k0;
+    if (m < 2) continue;
+    double mean = 0.0;
+    for (int a = 0; a < m; ++a) mean += lam[order[k0 + a]];
+    mean /= m;
+    for (int a = 0; a < m; ++a)
+      if (lane < m) {
+        const int ia = order[k0 + a], ib = order[k0 + lane];
+        B[a * ld + lane] = (float)((a == lane) ? lam[ia] - mean : oa_coupling(K, T, c, ia, ib, lam[ia], lam[ib]));
+        Q[a * ld + lane] = (a == lane) ? 1.f : 0.f;
+      }
+    __syncwarp();
+    for (int sweep = 0; sweep < 12; ++sweep) {
+      float offm = 0.f, bm = 0.f;
+      for (int a = 0; a < m; ++a)
+        if (lane < m) {
+          if (lane != a) offm = fmaxf(offm, fabsf(B[a * ld + lane]));
+          bm = fmaxf(bm, fabsf(B[a * ld + lane]));
+        }
+      offm = warp_max(offm);
+      bm = warp_max(bm);
+      if (offm <= 0x1p-24f * bm) break;
+      for (int pp = 0; pp < m - 1; ++pp)
+        for (int qq = pp + 1; qq < m; ++qq) {
+          const float g = B[pp * ld + qq];
+          if (g == 0.f) continue;
+          const float zeta = (B[qq * ld + qq] - B[pp * ld + pp]) / (2.f * g);
+          const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+          const float cs = rsqrtf(1.f + t * t), sn = cs * t;
+          __syncwarp();
+          if (lane < m) {  // rows p, q
+            const float x = B[pp * ld + lane], y = B[qq * ld + lane];
+            B[pp * ld + lane] = cs * x - sn * y;
+            B[qq * ld + lane] = sn * x + cs * y;
+          }
+          __syncwarp();
+          if (lane < m) {  // columns p, q, and Q
+            const float x = B[lane * ld + pp], y = B[lane * ld + qq];
+            B[lane * ld + pp] = cs * x - sn * y;
+            B[lane * ld + qq] = sn * x + cs * y;
+            const float u = Q[lane * ld + pp], v = Q[lane * ld + qq];
+            Q[lane * ld + pp] = cs * u - sn * v;
+            Q[lane * ld + qq] = sn * u + cs * v;
+          }
+          __syncwarp();
+          if (lane == 0) {
+            B[pp * ld + qq] = 0.f;
+            B[qq * ld + pp] = 0.f;
+          }
+          __syncwarp();
+        }
+    }
+    for (int a = 0; a < m; ++a)
+      if (lane < m) Qb[order[k0 + a] + (size_t)order[k0 + lane] * c] = (double)Q[a * ld + lane];
+    __syncwarp();
+  }
+}
+
+// F = F1 Qb with Qb block-diagonal over the clusters (identity elsewhere):
+// a singleton column is copied, a cluster column mixes its members' columns
+__global__ void k_block_apply(int c, const double* __restrict__ F1, const double* __restrict__ Qb,
+                              const int* __restrict__ cid, const int* __restrict__ ord,
+                              const int* __restrict__ st, double* __restrict__ F) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= c * c) return;
+  const int i = e % c, j = e / c;
+  const int q = cid[j];
+  if (q < 0) {
+    F[e] = F1[e];
     return;
   }
-  int p = i < j ? i : j, q = i < j ? j : i;
-  double al = K[p + p * c], be = K[q + q * c], ga = K[p + q * c];
-  double phi = 0.0;
-  if (ga != 0.0 && al > 0.0 && be > 0.0) {
-    double zeta = (be - al) / (2.0 * ga);
-    double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-    phi = atan(t);
+  double acc = 0.0;
+  for (int k = st[q]; k < st[q + 1]; ++k) {
+    const int a = ord[k];
+    acc = fma(F1[i + (size_t)a * c], Qb[a + (size_t)j * c], acc);
   }
-  Om[e] = (i < j) ? phi : -phi;
+  F[e] = acc;
 }
 
-// F = I + Om + Om2/2
-__global__ void k_expm2(int c, const double* __restrict__ Om, const double* __restrict__ Om2,
-                        double* __restrict__ F) {
-  int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= c * c) return;
-  int i = e % c, j = e / c;
-  F[e] = (i == j ? 1.0 : 0.0) + Om[e] + 0.5 * Om2[e];
-}
-
-// V <- V (3I - V^T V)/2, twice (Newton-Schulz polar step; orthogonality error
-// d -> ~3d^2/4 per step).  Uses T, F, E as scratch.
-static void ns_orthonormalize(cudaStream_t s, int c, double* V, PencilWs& w) {
-  for (int it = 0; it < 2; ++it) {
-    gemm_small(s, 1, 0, c, c, c, 1.0, V, c, V, c, 0.0, w.T, c);
-    k_ns_coef<<<(c * c + 255) / 256, 256, 0, s>>>(c, w.T, w.F);
-    gemm_small(s, 0, 0, c, c, c, 1.0, V, c, w.F, c, 0.0, w.E, c);
-    cudaMemcpyAsync(V, w.E, (size_t)c * c * sizeof(double), cudaMemcpyDeviceToDevice, s);
-  }
-  note_launches(6);
+static size_t cluster_smem(int c) {
+  return (size_t)c * sizeof(double) + (2 * (size_t)kClWarps * kClMax * (kClMax + 1) + c) * sizeof(float) +
+         (4 * (size_t)c + 2) * sizeof(int);
 }
 
 // SVD of the r x c matrix C (FP64, ld r): on exit Mout (r x c) = C V with
 // orthogonal columns, Vout (c x c) orthogonal.  FP32 block one-sided Jacobi
 // (relative orthogonality 1e-4, column norms floored at 1e-10 of the largest
-// so rounding-level directions do not stall it), then an FP64 polish made
-// only of small parallel GEMMs: V <- NS(V); N = C V; K = N^T N; rotate every
-// pair by its exact Jacobi angle at once (V <- V (I + Om + Om^2/2)); three
-// times.  Each polish step roughly squares the relative off-diagonal of K.
+// so rounding-level directions do not stall it), then four FP64 refinement
+// steps (N = C V, K = N^T N, T = V^T V, clusters, V <- V (I + E)) and
+// M = C V.
 static rr_status jacobi_svd(cudaStream_t s, int r, int c, const double* C, PencilWs& w, double* Mout,
                             double* Vout) {
   int ww, P;
@@ -895,21 +1284,26 @@ static rr_status jacobi_svd(cudaStream_t s, int r, int c, const double* C, Penci
   k_colnorm_floor<float><<<1, 1024, 0, s>>>(r, cpad, w.M32, r, 1e-10f, fl);
   RR_TRY(launch_bj(s, r, cpad, ww, P, w.M32, w.V32, 1e-4f, 15, w, fl));
   k_v32_to_64<<<g, 256, 0, s>>>(c, cpad, w.V32, w.V);
-  for (int it = 0; it < 3; ++it) {
-    ns_orthonormalize(s, c, w.V, w);
+  const size_t csm = cluster_smem(c);
+  if (csm > 48 * 1024)
+    RR_CUDA(cudaFuncSetAttribute(k_cluster_rot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
+  for (int it = 0; it < 4; ++it) {
     gemm_small(s, 0, 0, r, c, c, 1.0, C, r, w.V, c, 0.0, w.Mp, r);          // N = C V
-    gemm_small(s, 1, 0, c, c, r, 1.0, w.Mp, r, w.Mp, r, 0.0, w.Vp, c);      // K = N^T N
-    k_polish_angles<<<gc, 256, 0, s>>>(c, w.Vp, w.E2);
-    gemm_small(s, 0, 0, c, c, c, 1.0, w.E2, c, w.E2, c, 0.0, w.T, c);       // Om^2
-    k_expm2<<<gc, 256, 0, s>>>(c, w.E2, w.T, w.F);
-    gemm_small(s, 0, 0, c, c, c, 1.0, w.V, c, w.F, c, 0.0, w.E, c);         // V (I + Om + Om^2/2)
+    gemm_small(s, 1, 0, c, c, r, 1.0, w.Mp, r, w.Mp, r, 0.0, w.E2, c);      // K = N^T N
+    gemm_small(s, 1, 0, c, c, c, 1.0, w.V, c, w.V, c, 0.0, w.T, c);         // T = V^T V
+    k_cluster_rot<<<1, 1024, csm, s>>>(c, w.E2, w.T, w.F, w.cid, w.order, w.cst);  // Qb
+    k_oa_update<<<gc, 256, 0, s>>>(c, w.E2, w.T, w.cid, w.Vp);              // F1
+    // V <- V (I + (I - T)/2 + W) Qb: orthogonalise, the small pair rotations,
+    // then the clusters' rotations
+    k_block_apply<<<gc, 256, 0, s>>>(c, w.Vp, w.F, w.cid, w.order, w.cst, w.T);  // F = F1 Qb
+    gemm_small(s, 0, 0, c, c, c, 1.0, w.V, c, w.T, c, 0.0, w.E, c);         // V F
     RR_CUDA(cudaMemcpyAsync(w.V, w.E, (size_t)c * c * sizeof(double), cudaMemcpyDeviceToDevice, s));
   }
-  ns_orthonormalize(s, c, w.V, w);
   gemm_small(s, 0, 0, r, c, c, 1.0, C, r, w.V, c, 0.0, Mout, r);            // M = C V
   if (Vout != w.V)
     RR_CUDA(cudaMemcpyAsync(Vout, w.V, (size_t)c * c * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  note_launches(22);  // 4 setup kernels, 3 x 6 polish kernels (+ the final product in check_launch)
+  // 5 setup kernels, 4 x 7 refinement kernels, the final product (in check_launch)
+  note_launches(33);
   return check_launch("jacobi_svd");
 }
 

@@ -272,6 +272,60 @@ def test_pencil_svd_matches_block_pencil(rr, b1, b2):
     assert np.abs(Vt.T @ Vt - np.eye(r)).max() < 1e-8
 
 
+def _clustered_spectrum(rng, b):
+    """Groups of 8 values 1e-6 apart (relative), one exactly degenerate
+    group, and well separated singletons: the degenerate case of the pencil
+    (the FP32 stage cannot resolve these pairs; the FP64 refinement must)."""
+    g = b // 16
+    centres = np.linspace(1.0, 3.0, g)
+    vals = [c0 * (1 + 1e-6 * rng.standard_normal(8)) for c0 in centres[:-1]]
+    vals.append(np.full(8, 3.5))
+    vals.append(np.linspace(4.0, 6.0, b - 8 * g))
+    return np.concatenate(vals)
+
+
+@pytest.mark.parametrize("b", [64, 200])
+def test_pencil_eig_clustered_spectrum(rr, b):
+    import scipy.linalg as sla
+    rng = np.random.default_rng(300 + b)
+    lam = _clustered_spectrum(rng, b) * rng.choice([-1.0, 1.0])
+    Q, _ = np.linalg.qr(rng.standard_normal((b, b)))
+    Bm = rng.standard_normal((3 * b, b))
+    G = Bm.T @ Bm / (3 * b)
+    Lc = np.linalg.cholesky(G)
+    H = Lc @ (Q * lam) @ Q.T @ Lc.T
+    H = 0.5 * (H + H.T)
+    th, Y, dropped = rr.rr_pencil_eig(dev(H), dev(G))
+    th, Yh = host(th), host(Y)
+    ref = sla.eigh(H, G, eigvals_only=True)
+    scale = np.abs(ref).max()
+    assert dropped == 0
+    assert np.all(np.isfinite(Yh))
+    # the same bounds as the unclustered pencil test (FP32-level failures of
+    # the refinement show up as 1e-7)
+    assert np.abs(np.sort(th) - ref).max() <= 1e-10 * scale
+    assert np.abs(Yh.T @ G @ Yh - np.eye(b)).max() < 1e-11
+    assert np.abs(H @ Yh - G @ Yh * th).max() < 1e-10 * scale
+
+
+def test_pencil_svd_clustered_spectrum(rr):
+    rng = np.random.default_rng(17)
+    b = 160
+    sig = _clustered_spectrum(rng, b)
+    P, _ = np.linalg.qr(rng.standard_normal((b, b)))
+    R, _ = np.linalg.qr(rng.standard_normal((b, b)))
+    Bm = (P * sig) @ R.T
+    Gu = np.eye(b)
+    Gv = np.eye(b)
+    s, Y, Z, dropped = rr.rr_pencil_svd(dev(Bm), dev(Gu), dev(Gv))
+    s, Yh, Zh = host(s), host(Y), host(Z)
+    assert np.all(np.isfinite(Yh)) and np.all(np.isfinite(Zh))
+    assert np.abs(s - np.sort(sig)[::-1]).max() <= 1e-10 * sig.max()
+    assert np.abs(Yh.T @ Yh - np.eye(b)).max() < 1e-11
+    assert np.abs(Zh.T @ Zh - np.eye(b)).max() < 1e-11
+    assert np.abs(Bm @ Zh - Yh * s).max() < 1e-10 * sig.max()
+
+
 # ---------------------------------------------------------------- a3
 def test_csr_spmm_and_chebyshev_step(rr):
     N, b = 40, 24
