@@ -32,12 +32,21 @@ struct HessWs {
   T* prow;      // [2][G][k] candidate row's entries
   T* pcolmax;   // [G][k] per-slab column inf-norms
   int* flags;   // [G] column steps published by each CTA (j + 1 after column j)
+  unsigned long long* cand;  // [2][G] packed candidates (FP32 path)
 };
 
 // Publish/await the per-column candidates: CTA g releases flags[g] = step once
 // its candidate is written; readers acquire every flag before reading.
 __device__ __forceinline__ void flag_release(int* f, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(f), "r"(v) : "memory");
+}
+__device__ __forceinline__ void word_release(unsigned long long* f, unsigned long long v) {
+  asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(f), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long word_acquire(const unsigned long long* f) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(f) : "memory");
+  return v;
 }
 __device__ __forceinline__ int flag_acquire(const int* f) {
   int v;
@@ -289,6 +298,349 @@ __global__ void __launch_bounds__(kHessThreads) k_hessenberg(
   }
 }
 
+// the block's argmax from the per-warp candidates (the same merge order as
+// the warp-shuffle reduction, so every warp gets the same row)
+template <typename T>
+__device__ __forceinline__ int bi_of_block(const T* red_v, const int* red_i, int nwarps) {
+  T bv = T(-1);
+  int bi = INT_MAX;
+  const int lane = threadIdx.x & 31;
+  bv = lane < nwarps ? red_v[lane] : T(-1);
+  bi = lane < nwarps ? red_i[lane] : INT_MAX;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+    int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    argmax_merge(bv, bi, ov, oi);
+  }
+  return bi;
+}
+
+// FP32-arithmetic variant (the basis step of the low-precision path), same
+// per-element arithmetic and results as k_hessenberg<float, TO>.  Two
+// changes to the per-column exchange:
+//   - a CTA's candidate is one 64-bit word (value bits, global row, column
+//     tag), written with a single release store and double-buffered by column
+//     parity, so the wait for the candidates also delivers them;
+//   - warp 0 reduces and publishes the next candidate (its row's trailing
+//     entries, updated, go both to the published copy and back to the slab)
+//     while the other warps apply the rank-1 update to every other row.
+// Needs n < 2^24 - 1 (row field of the word).
+constexpr unsigned kNoRow = 0xFFFFFFu;
+
+__device__ __forceinline__ unsigned long long pack_cand(float v, unsigned row, int col) {
+  return ((unsigned long long)__float_as_uint(v) << 32) | ((unsigned long long)(row & 0xFFFFFFu) << 8) |
+         (unsigned long long)((col + 1) & 0xFF);
+}
+
+template <typename TO>
+__global__ void __launch_bounds__(kHessThreads) k_hessenberg_f32(
+    int64_t n, int k, float* __restrict__ W, int64_t ldw, TO* __restrict__ Q, int64_t ldq,
+    int* __restrict__ piv, float tol, HessWs<float> ws, int slab) {
+  using T = float;
+  const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = kHessThreads / 32;
+  const int64_t rpc = (n + G - 1) / G;
+  const int64_t r0 = (int64_t)g * rpc;
+  const int64_t r1 = r0 + rpc < n ? r0 + rpc : n;
+  const int nr = r1 > r0 ? (int)(r1 - r0) : 0;
+
+  extern __shared__ unsigned char smem_raw[];
+  T* thr = reinterpret_cast<T*>(smem_raw);   // [k]
+  T* wgt = thr + k;                          // [2][k] weights, by column parity
+  T* slabp = wgt + 2 * k;                    // [k][rpc] in slab mode
+  T* const base = slab ? slabp : W + r0;
+  const int64_t ldv = slab ? rpc : ldw;
+  auto col = [&](int c) -> T* { return base + (int64_t)c * ldv; };
+  if (slab) {
+    for (int c = warp; c < k; c += nwarps) {
+      const T* src = W + r0 + (int64_t)c * ldw;
+      T* dst = col(c);
+      for (int i = lane; i < nr; i += 32) dst[i] = src[i];
+    }
+    __syncthreads();
+  }
+  __shared__ T red_v[32];
+  __shared__ int red_i[32];
+  __shared__ T s_qr;
+  __shared__ int s_r, s_win, s_keep;
+
+  for (int c = warp; c < k; c += nwarps) {
+    T m = T(0);
+    const T* cc = col(c);
+    for (int i = lane; i < nr; i += 32) m = fmax(m, fabs(cc[i]));
+    m = warp_max(m);
+    if (lane == 0) ws.pcolmax[(size_t)g * k + c] = m;
+  }
+  if (!grid_barrier(ws.bar, G, ws.err)) return;
+  for (int c = tid; c < k; c += kHessThreads) {
+    T m = T(0);
+    for (int h = 0; h < G; ++h) m = fmax(m, ld_cg(ws.pcolmax + (size_t)h * k + c));
+    thr[c] = rn_mul(tol, m);
+  }
+  __syncthreads();
+
+  // local argmax of |column jc| (first index on ties) -> s_r (local row or
+  // INT_MAX); two CTA barriers
+  auto local_argmax = [&](int jc) {
+    const T* cj = col(jc);
+    T bv = T(-1);
+    int bi = INT_MAX;
+    for (int i = tid; i < nr; i += kHessThreads) {
+      T v = fabs(cj[i]);
+      if (v > bv) {
+        bv = v;
+        bi = i;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      argmax_merge(bv, bi, ov, oi);
+    }
+    if (lane == 0) {
+      red_v[warp] = bv;
+      red_i[warp] = bi;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      bv = lane < nwarps ? red_v[lane] : T(-1);
+      bi = lane < nwarps ? red_i[lane] : INT_MAX;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        argmax_merge(bv, bi, ov, oi);
+      }
+      if (lane == 0) s_r = bi;
+    }
+    __syncthreads();
+  };
+  // warp 0: publish the candidate of column jc (row rl): its entries jc+1..
+  // after the pending update by column jc-1 (upd) go to the published row and
+  // back to the slab; then the packed word
+  auto publish_w0 = [&](int jc, bool upd, int rl) {
+    const int par = jc & 1;
+    T* prow = ws.prow + ((size_t)par * G + g) * k;
+    if (rl != INT_MAX) {
+      const T m = upd ? col(jc - 1)[rl] : T(0);
+      for (int c = jc + 1 + lane; c < k; c += 32) {
+        T v = col(c)[rl];
+        if (upd) {
+          v = rn_sub(v, rn_mul(wgt[c], m));
+          col(c)[rl] = v;
+        }
+        prow[c] = v;
+      }
+    }
+    __syncwarp();
+    if (lane == 0) {
+      const T v = rl != INT_MAX ? col(jc)[rl] : T(0);
+      const unsigned row = rl != INT_MAX ? (unsigned)(r0 + rl) : kNoRow;
+      __threadfence();
+      word_release(ws.cand + (size_t)par * G + g, pack_cand(v, row, jc));
+    }
+  };
+
+  // warp 0: wait (bounded) for every CTA's word for column jc, reduce to the
+  // pivot, and load the pivot row's entries jc+1.. into the weight buffer of
+  // column jc's parity; returns false on error
+  auto await_pivot = [&](int jc) -> bool {
+    const int par = jc & 1;
+    const unsigned tag = (unsigned)((jc + 1) & 0xFF);
+    const uint64_t t0 = global_timer_ns();
+    T av = T(-1), sv = T(0);
+    int ai = INT_MAX, ag = -1;
+    bool ok = true;
+    for (int h = lane; h < G; h += 32) {
+      unsigned long long wv;
+      while (((wv = word_acquire(ws.cand + (size_t)par * G + h)) & 0xFFull) != tag) {
+        if (*(volatile int*)ws.err != 0 || global_timer_ns() - t0 > kWaitLimitNs) {
+          atomicCAS(ws.err, 0, (int)RR_ERR_TIMEOUT);
+          ok = false;
+          break;
+        }
+      }
+      if (!ok) break;
+      const unsigned row = (unsigned)((wv >> 8) & 0xFFFFFFull);
+      if (row == kNoRow) continue;
+      const T hv = __uint_as_float((unsigned)(wv >> 32));
+      const T ah = fabs(hv);
+      if (ah > av || (ah == av && (int)row < ai)) {
+        av = ah;
+        ai = (int)row;
+        ag = h;
+        sv = hv;
+      }
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    if (!ok) return false;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      T ov = __shfl_xor_sync(0xffffffffu, av, o);
+      int oi = __shfl_xor_sync(0xffffffffu, ai, o);
+      int og = __shfl_xor_sync(0xffffffffu, ag, o);
+      T osv = __shfl_xor_sync(0xffffffffu, sv, o);
+      if (ov > av || (ov == av && oi < ai)) {
+        av = ov;
+        ai = oi;
+        ag = og;
+        sv = osv;
+      }
+    }
+    const bool kp = ag >= 0 && sv != T(0) && fabs(sv) >= thr[jc];
+    if (kp) {
+      const T* prow = ws.prow + ((size_t)par * G + ag) * k;
+      T* wb = wgt + (size_t)par * k;
+      for (int c = jc + 1 + lane; c < k; c += 32) wb[c] = ld_cg(prow + c);
+    }
+    if (lane == 0) {
+      s_qr = sv;
+      s_keep = kp ? 1 : 0;
+      if (g == 0) piv[jc] = kp ? ai : -1;
+    }
+    return true;
+  };
+
+  __shared__ int s_ok;
+  local_argmax(0);
+  if (warp == 0) {
+    publish_w0(0, false, s_r);
+    const bool ok = await_pivot(0);
+    if (lane == 0) s_ok = ok ? 1 : 0;
+  }
+  __syncthreads();
+  if (!s_ok) return;
+  for (int j = 0; j < k; ++j) {
+    const bool keep = s_keep != 0;
+    const T qr = s_qr;
+    const T* wj = wgt + (size_t)(j & 1) * k;  // weights of column j
+    T* cj = col(j);
+    // (d) scale column j and update column j+1 row by row, tracking the local
+    // argmax of the new column j+1 (first index on ties)
+    {
+      T* cn = j + 1 < k ? col(j + 1) : nullptr;
+      const T wn = (keep && cn) ? wj[j + 1] : T(0);
+      T bv = T(-1);
+      int bi = INT_MAX;
+      for (int i = tid; i < nr; i += kHessThreads) {
+        T v = T(0);
+        if (keep) v = rn_div(cj[i], qr);
+        cj[i] = v;
+        if (cn) {
+          T u = cn[i];
+          if (keep) u = rn_sub(u, rn_mul(wn, v));
+          cn[i] = u;
+          const T au = fabs(u);
+          if (au > bv) {
+            bv = au;
+            bi = i;
+          }
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        argmax_merge(bv, bi, ov, oi);
+      }
+      if (lane == 0) {
+        red_v[warp] = bv;
+        red_i[warp] = bi;
+      }
+    }
+    __syncthreads();
+    if (j + 1 < k) {
+      if (warp == 0) {
+        // reduce the candidate, publish it (its row takes column j's pending
+        // update, written back to the slab), then wait for the pivot of
+        // column j+1 while the other warps finish column j's update
+        T bv = lane < nwarps ? red_v[lane] : T(-1);
+        int bi = lane < nwarps ? red_i[lane] : INT_MAX;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+          int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          argmax_merge(bv, bi, ov, oi);
+        }
+        const int rl = bi;
+        const int par = (j + 1) & 1;
+        T* prow = ws.prow + ((size_t)par * G + g) * k;
+        if (rl != INT_MAX) {
+          const T m = cj[rl];
+          for (int c = j + 2 + lane; c < k; c += 32) {
+            T v = col(c)[rl];
+            if (keep) {
+              v = rn_sub(v, rn_mul(wj[c], m));
+              col(c)[rl] = v;
+            }
+            prow[c] = v;
+          }
+        }
+        __syncwarp();
+        if (lane == 0) {
+          const T v = rl != INT_MAX ? col(j + 1)[rl] : T(0);
+          const unsigned row = rl != INT_MAX ? (unsigned)(r0 + rl) : kNoRow;
+          __threadfence();
+          word_release(ws.cand + (size_t)par * G + g, pack_cand(v, row, j + 1));
+        }
+        const bool ok = await_pivot(j + 1);
+        if (lane == 0) s_ok = ok ? 1 : 0;
+      } else if (keep) {
+        // rank-1 update of columns j+2.. (all rows but the candidate's, which
+        // warp 0 updates): the multiplier column in registers, independent
+        // loads per target column
+        const T* cj_c = cj;
+        const int rl = bi_of_block(red_v, red_i, nwarps);
+        constexpr int kR = 16;  // rows per lane held in registers (nr <= 512)
+        if (nr <= 32 * kR) {
+          T xr[kR];
+#pragma unroll
+          for (int t = 0; t < kR; ++t) {
+            const int i = lane + 32 * t;
+            xr[t] = i < nr ? cj_c[i] : T(0);
+          }
+          for (int c = j + 2 + (warp - 1); c < k; c += nwarps - 1) {
+            T* cc = col(c);
+            const T wc = wj[c];
+            T yv[kR];
+#pragma unroll
+            for (int t = 0; t < kR; ++t) {
+              const int i = lane + 32 * t;
+              yv[t] = i < nr ? cc[i] : T(0);
+            }
+#pragma unroll
+            for (int t = 0; t < kR; ++t) {
+              const int i = lane + 32 * t;
+              if (i < nr && i != rl) cc[i] = rn_sub(yv[t], rn_mul(wc, xr[t]));
+            }
+          }
+        } else {
+          for (int c = j + 2 + (warp - 1); c < k; c += nwarps - 1) {
+            T* cc = col(c);
+            const T wc = wj[c];
+            for (int i = lane; i < nr; i += 32)
+              if (i != rl) cc[i] = rn_sub(cc[i], rn_mul(wc, cj_c[i]));
+          }
+        }
+      }
+      __syncthreads();
+      if (!s_ok) return;
+    }
+  }
+  for (int c = warp; c < k; c += nwarps) {
+    const T* src = col(c);
+    T* dw = W + r0 + (int64_t)c * ldw;
+    TO* dq = Q + r0 + (int64_t)c * ldq;
+    for (int i = lane; i < nr; i += 32) {
+      const T v = src[i];
+      if (slab) dw[i] = v;
+      if ((void*)Q != (void*)W) dq[i] = from_f64<TO>((double)v);
+    }
+  }
+}
+
 static int hess_grid(int64_t n, size_t smem, const void* fn) {
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kHessThreads, smem);
@@ -309,13 +661,16 @@ static size_t hess_ws_bytes(int64_t k, int G) {
   b += align_up(2 * (size_t)G * k * sizeof(T));
   b += align_up((size_t)G * k * sizeof(T));
   b += align_up((size_t)G * sizeof(int));
+  b += align_up(2 * (size_t)G * sizeof(unsigned long long));
   return b;
 }
 
 template <typename T, typename TO>
 static rr_status hess_launch(int64_t n, int64_t k, T* W, int64_t ldw, TO* Q, int64_t ldq, int* piv,
                              double tol, void* ws, size_t ws_bytes, cudaStream_t s, int max_grid) {
-  const void* fn = (const void*)k_hessenberg<T, TO>;
+  // FP32 arithmetic: the packed-candidate kernel (rows must fit its 24-bit field)
+  const bool packed = sizeof(T) == 4 && n < (int64_t)kNoRow;
+  const void* fn = packed ? (const void*)k_hessenberg_f32<TO> : (const void*)k_hessenberg<T, TO>;
   // Grid: about 256 rows per CTA (fewer CTAs make the per-column barrier and
   // candidate reduction cheaper), more CTAs if a slab would not fit in shared
   // memory; slab mode when the CTA's rows of all k columns fit in 200 KB.
@@ -333,8 +688,9 @@ static rr_status hess_launch(int64_t n, int64_t k, T* W, int64_t ldw, TO* Q, int
     G = (int)g;
   }
   const int64_t rpc = (n + G - 1) / G;
-  if ((size_t)rpc * k * sizeof(T) <= kSlabLimit) slab = 1;
-  size_t smem = 2 * (size_t)k * sizeof(T) + (slab ? (size_t)rpc * k * sizeof(T) : 0);
+  const size_t fixed = (packed ? 3 : 2) * (size_t)k * sizeof(T);  // thresholds and weights
+  if ((size_t)rpc * k * sizeof(T) <= kSlabLimit && (size_t)rpc * k * sizeof(T) + fixed <= 220 * 1024) slab = 1;
+  size_t smem = fixed + (slab ? (size_t)rpc * k * sizeof(T) : 0);
   if (smem > 48 * 1024)
     RR_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   if (ws_bytes < hess_ws_bytes<T>(k, G) || !ws) return RR_ERR_WORKSPACE;
@@ -347,15 +703,17 @@ static rr_status hess_launch(int64_t n, int64_t k, T* W, int64_t ldw, TO* Q, int
   h.prow = ar.take<T>(2 * (size_t)G * k);
   h.pcolmax = ar.take<T>((size_t)G * k);
   h.flags = ar.take<int>(G);
+  h.cand = ar.take<unsigned long long>(2 * (size_t)G);
   RR_CUDA(cudaMemsetAsync(ws, 0, 512, s));  // err + barrier
   RR_CUDA(cudaMemsetAsync(h.flags, 0, (size_t)G * sizeof(int), s));
+  RR_CUDA(cudaMemsetAsync(h.cand, 0, 2 * (size_t)G * sizeof(unsigned long long), s));
   T t = tol > 0 ? (T)tol : (T)(4.0 * (double)k * (sizeof(T) == 4 ? 0x1p-23 : 0x1p-52));
   int kk = (int)k;
   void* args[] = {&n, &kk, &W, &ldw, &Q, &ldq, &piv, &t, &h, &slab};
   if (G == 1) {
     // a single CTA never waits on another one: plain launch (graph-capturable,
     // safe to run concurrently with other work)
-    k_hessenberg<T, TO><<<1, kHessThreads, smem, s>>>(n, kk, W, ldw, Q, ldq, piv, t, h, slab);
+    RR_CUDA(cudaLaunchKernel(fn, dim3(1), dim3(kHessThreads), args, smem, s));
     return check_launch("rr_hessenberg");
   }
   RR_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kHessThreads), args, smem, s));
