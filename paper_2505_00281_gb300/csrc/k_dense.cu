@@ -127,6 +127,39 @@ __global__ void k_cast_operator(int64_t m, int64_t n, const double* __restrict__
 }
 }  // namespace rr
 
+namespace rr {
+// BF16 residual of the operator cast: lo = bf16(a - bf16(a)), column-major
+// and row-major copies (the second half of a split BF16 operator)
+__global__ void k_cast_operator_lo(int64_t m, int64_t n, const double* __restrict__ A, int64_t lda,
+                                   __nv_bfloat16* __restrict__ out_col, __nv_bfloat16* __restrict__ out_row) {
+  __shared__ __nv_bfloat16 tile[32][33];
+  int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
+  int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int r = ty; r < 32; r += 8) {
+    int64_t i = i0 + tx, j = j0 + r;
+    if (i < m && j < n) {
+      const double a = A[i + j * lda];
+      const __nv_bfloat16 v = __double2bfloat16(a - (double)__bfloat162float(__double2bfloat16(a)));
+      out_col[i + j * m] = v;
+      tile[r][tx] = v;
+    }
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    int64_t i = i0 + r, j = j0 + tx;
+    if (i < m && j < n) out_row[i * n + j] = tile[tx][r];
+  }
+}
+
+rr_status cast_operator_lo(int64_t m, int64_t n, const double* A, int64_t lda, void* lo_col, void* lo_row,
+                           cudaStream_t s) {
+  if (m == 0 || n == 0) return RR_OK;
+  dim3 g((unsigned)((m + 31) / 32), (unsigned)((n + 31) / 32)), b(32, 8);
+  k_cast_operator_lo<<<g, b, 0, s>>>(m, n, A, lda, (__nv_bfloat16*)lo_col, (__nv_bfloat16*)lo_row);
+  return check_launch("cast_operator_lo");
+}
+}  // namespace rr
+
 extern "C" rr_status rr_cast_operator(int64_t m, int64_t n, const double* A, int64_t lda,
                                       int32_t dtype, void* out_col, void* out_row, void* stream) {
   if (m < 0 || n < 0 || lda < m || !A || !out_col) return RR_ERR_ARG;

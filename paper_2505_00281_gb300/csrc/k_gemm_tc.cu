@@ -130,7 +130,9 @@ struct TcArgs {
   int tmem_cols;   // power of two >= max(32, npad)
   int stages;
   int ksteps_per_split;
-  int nk;          // total K steps
+  int nk;          // total K steps (all segments)
+  int nk1;         // K steps of one segment (K / 64 rounded up)
+  int segs;        // 1, or 3 for the split product A_hi B_hi + A_lo B_hi + A_hi B_lo
   float* C;
   int64_t ldc;
   const double* R;
@@ -168,6 +170,8 @@ __device__ __forceinline__ double mul_pow2(double d, int e) {
 
 __global__ void __launch_bounds__(128, 1) k_gemm_bf16_tc(const __grid_constant__ CUtensorMap tmA,
                                                           const __grid_constant__ CUtensorMap tmB,
+                                                          const __grid_constant__ CUtensorMap tmA2,
+                                                          const __grid_constant__ CUtensorMap tmB2,
                                                           TcArgs a) {
   extern __shared__ unsigned char smem_raw[];
   // 1024-byte alignment for the swizzled tiles
@@ -221,9 +225,11 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16_tc(const __grid_constant__
         unsigned char* sa = base + (size_t)s * stage_bytes;
         unsigned char* sb = sa + a_bytes;
         mbar_expect_tx(&full[s], stage_bytes);
-        const int kx = (ks0 + i) * kBK;
-        tma_load_2d(sa, &tmA, &full[s], kx, (int)m0 + a_off);
-        tma_load_2d(sb, &tmB, &full[s], kx, b_off);
+        // segment of this K step (split product: hi.hi, lo.hi, hi.lo)
+        const int kg = ks0 + i, seg = kg / a.nk1;
+        const int kx = (kg - seg * a.nk1) * kBK;
+        tma_load_2d(sa, seg == 1 ? &tmA2 : &tmA, &full[s], kx, (int)m0 + a_off);
+        tma_load_2d(sb, seg == 2 ? &tmB2 : &tmB, &full[s], kx, b_off);
         ++issued;
       }
       if (issued < nks) {
@@ -427,12 +433,24 @@ int tc_emu_partial_splits(int64_t M, int64_t K, int npairs, int max_kchunk) {
 static rr_status gemm_bf16_tc_impl(int64_t M, int64_t N, int64_t K, const __nv_bfloat16* A, int64_t lda,
                                    const __nv_bfloat16* B, int64_t ldb, float* C, int64_t ldc,
                                    const double* R, int64_t ldr, const double* coef, const TcEmu* emu,
-                                   cudaStream_t s);
+                                   cudaStream_t s, const __nv_bfloat16* A2 = nullptr,
+                                   const __nv_bfloat16* B2 = nullptr);
 
 rr_status gemm_bf16_tc(int64_t M, int64_t N, int64_t K, const __nv_bfloat16* A, int64_t lda,
                        const __nv_bfloat16* B, int64_t ldb, float* C, int64_t ldc, const double* R,
                        int64_t ldr, const double* coef, cudaStream_t s) {
   return gemm_bf16_tc_impl(M, N, K, A, lda, B, ldb, C, ldc, R, ldr, coef, nullptr, s);
+}
+
+// Split-BF16 product: C (M x N, FP32) = (A_hi + A_lo)^T (B_hi + B_lo) without
+// the lo.lo term (+ coef_j R(:, j)), FP32 accumulation; each operand pair is
+// the BF16 rounding of a wider value and its BF16 residual.
+rr_status gemm_bf16_tc_split(int64_t M, int64_t N, int64_t K, const __nv_bfloat16* A_hi,
+                             const __nv_bfloat16* A_lo, int64_t lda, const __nv_bfloat16* B_hi,
+                             const __nv_bfloat16* B_lo, int64_t ldb, float* C, int64_t ldc,
+                             const double* R, int64_t ldr, const double* coef, cudaStream_t s) {
+  if (!A_lo || !B_lo) return RR_ERR_ARG;
+  return gemm_bf16_tc_impl(M, N, K, A_hi, lda, B_hi, ldb, C, ldc, R, ldr, coef, nullptr, s, A_lo, B_lo);
 }
 
 // FP64 emulation launch (TcEmu in solver_kernels.cuh); N = nb or 2 nb
@@ -444,10 +462,14 @@ rr_status gemm_bf16_tc_emu(int64_t M, int64_t N, int64_t K, const __nv_bfloat16*
   return gemm_bf16_tc_impl(M, N, K, A, lda, B, ldb, nullptr, 0, nullptr, 0, nullptr, &e, s);
 }
 
+// Split product (A2, B2 non-null): C = A^T B + A2^T B + A^T B2 (+ coef R),
+// the three K ranges run as consecutive segments of one accumulation.
 static rr_status gemm_bf16_tc_impl(int64_t M, int64_t N, int64_t K, const __nv_bfloat16* A, int64_t lda,
                                    const __nv_bfloat16* B, int64_t ldb, float* C, int64_t ldc,
                                    const double* R, int64_t ldr, const double* coef, const TcEmu* emu,
-                                   cudaStream_t s) {
+                                   cudaStream_t s, const __nv_bfloat16* A2, const __nv_bfloat16* B2) {
+  const bool split = A2 && B2;
+  if ((A2 || B2) && (!split || emu)) return RR_ERR_ARG;
   const int npad = (int)((N + 15) / 16 * 16);
   // TMEM columns: the accumulator, and for a two-slice emulation launch the
   // epilogue's 32-column reads of the second slice up to nb + 32 ceil(nb / 32)
@@ -462,11 +484,20 @@ static rr_status gemm_bf16_tc_impl(int64_t M, int64_t N, int64_t K, const __nv_b
   // tensor maps over the whole slice stacks (emulation) or the operands
   const int64_t a_outer = emu && emu->a_slices > 1 ? (int64_t)emu->a_slices * emu->a_slice_rows : M;
   const int64_t b_outer = emu && emu->b_slices > 1 ? (int64_t)emu->b_slices * emu->b_slice_rows : N;
-  CUtensorMap ta, tb;
+  CUtensorMap ta, tb, ta2, tb2;
   if (!make_map(&ta, A, K, a_outer, lda, kBK, kBM)) return RR_ERR_ARG;
   if (!make_map(&tb, B, K, b_outer, ldb, kBK, (uint32_t)npad)) return RR_ERR_ARG;
+  if (split) {
+    if (!make_map(&ta2, A2, K, a_outer, lda, kBK, kBM)) return RR_ERR_ARG;
+    if (!make_map(&tb2, B2, K, b_outer, ldb, kBK, (uint32_t)npad)) return RR_ERR_ARG;
+  } else {
+    ta2 = ta;
+    tb2 = tb;
+  }
   const int64_t tiles = (M + kBM - 1) / kBM;
-  const int nk = (int)tc_nk(K);
+  const int nk1 = (int)tc_nk(K);
+  const int segs = split ? 3 : 1;
+  const int nk = nk1 * segs;
   const int sms = num_sms();
   const int npairs = emu ? emu->npairs : 1;
   int splits = 1;
@@ -498,6 +529,8 @@ static rr_status gemm_bf16_tc_impl(int64_t M, int64_t N, int64_t K, const __nv_b
   a.stages = stages;
   a.ksteps_per_split = per;
   a.nk = nk;
+  a.nk1 = nk1;
+  a.segs = segs;
   a.C = C;
   a.ldc = ldc;
   a.R = R;
@@ -520,7 +553,7 @@ static rr_status gemm_bf16_tc_impl(int64_t M, int64_t N, int64_t K, const __nv_b
     note_launches(1);
   }
   dim3 grid((unsigned)tiles, (unsigned)splits, (unsigned)npairs);
-  k_gemm_bf16_tc<<<grid, 128, smem, s>>>(ta, tb, a);
+  k_gemm_bf16_tc<<<grid, 128, smem, s>>>(ta, tb, ta2, tb2, a);
   return check_launch("gemm_bf16_tc");
 }
 

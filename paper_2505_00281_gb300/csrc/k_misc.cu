@@ -184,6 +184,44 @@ static rr_status scale_cast_t(cudaStream_t s, int64_t n, int64_t b, const TI* T,
   return check_launch("scale_cast");
 }
 
+// D_hi + D_lo = T(:, j) / mu_j to 16 bits: D_hi = bf16(v), D_lo = bf16(v - D_hi)
+template <typename TI>
+__global__ void k_scale_split(int64_t n, int64_t b, const TI* __restrict__ T, int64_t ldt,
+                              const double* __restrict__ mu, __nv_bfloat16* __restrict__ Dh,
+                              __nv_bfloat16* __restrict__ Dl, int64_t ldd) {
+  const int64_t j = blockIdx.y;
+  const double sc = mu ? 1.0 / mu[j] : 1.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = (double)T[i + j * ldt] * sc;
+    const __nv_bfloat16 h = __double2bfloat16(v);
+    Dh[i + j * ldd] = h;
+    Dl[i + j * ldd] = __double2bfloat16(v - (double)__bfloat162float(h));
+  }
+}
+
+rr_status scale_split(cudaStream_t s, int32_t ttype, int64_t n, int64_t b, const void* T, int64_t ldt,
+                      double* mu, void* D_hi, void* D_lo, int64_t ldd, double* coef, const double* sig) {
+  if (b == 0) return RR_OK;
+  dim3 g((unsigned)std::min<int64_t>((n + 255) / 256, 512), (unsigned)b);
+  if (ttype == RR_F64) {
+    if (mu) k_colmax_any<double><<<(unsigned)b, 512, 0, s>>>(n, (const double*)T, ldt, mu);
+    k_scale_split<double><<<g, 256, 0, s>>>(n, b, (const double*)T, ldt, mu, (__nv_bfloat16*)D_hi,
+                                            (__nv_bfloat16*)D_lo, ldd);
+  } else {
+    if (mu) k_colmax_any<float><<<(unsigned)b, 512, 0, s>>>(n, (const float*)T, ldt, mu);
+    k_scale_split<float><<<g, 256, 0, s>>>(n, b, (const float*)T, ldt, mu, (__nv_bfloat16*)D_hi,
+                                           (__nv_bfloat16*)D_lo, ldd);
+  }
+  note_launches(mu ? 1 : 0);
+  RR_TRY(check_launch("scale_split"));
+  if (coef && mu) {
+    k_coef_update<<<(unsigned)((b + 127) / 128), 128, 0, s>>>(b, mu, sig, coef);
+    return check_launch("coef_update");
+  }
+  return RR_OK;
+}
+
 rr_status scale_cast(cudaStream_t s, int32_t ttype, int64_t n, int64_t b, const void* T, int64_t ldt,
                      double* mu, int32_t dtype, void* D, int64_t ldd, double* coef,
                      const double* sig) {

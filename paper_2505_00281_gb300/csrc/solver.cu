@@ -34,6 +34,11 @@ struct Op {
   const float* va;
   void* lo_col;  // K-major operand of A^T X (column-major copy), dtype dt
   void* lo_row;  // K-major operand of A X (row-major copy), dtype dt
+  // split BF16 operator (refinement of a BF16 basis): the BF16 residuals
+  // A - bf16(A), same layouts, for the products of the correction recurrence
+  bool split;
+  void* lo2_col;
+  void* lo2_row;
   int32_t dt;    // basis dtype
   int32_t wt;    // product output type (F32, or F64 when dt is F64)
   // FP64-accurate products on the tensor cores (dense operator, refinement)
@@ -140,6 +145,24 @@ static rr_status apply_lowp_T(const Op& op, int64_t b, const void* X, int64_t ld
     return rr_gemm_f64(1, op.n, b, op.m, op.A, op.lda, (const double*)X, ldx, (double*)out, ldo, 0, s);
   }
   return rr_gemm_lowp(op.dt, op.n, b, op.m, op.lo_col, op.m, X, ldx, (float*)out, ldo, R, ldr, coef, s);
+}
+
+// Split-BF16 products for the correction recurrence: (A_hi + A_lo) applied to
+// a block stored as X_hi + X_lo (BF16 rounding and residual), lo.lo dropped:
+// out (m x b, FP32) = A X (+ coef_j R(:,j)); the _T form computes A^T X.
+static rr_status apply_lowp_split(const Op& op, int64_t b, const void* Xh, const void* Xl, int64_t ldx,
+                                  void* out, int64_t ldo, const double* R, int64_t ldr, const double* coef,
+                                  cudaStream_t s) {
+  return gemm_bf16_tc_split(op.m, b, op.n, (const __nv_bfloat16*)op.lo_row, (const __nv_bfloat16*)op.lo2_row,
+                            op.n, (const __nv_bfloat16*)Xh, (const __nv_bfloat16*)Xl, ldx, (float*)out, ldo,
+                            R, ldr, coef, s);
+}
+static rr_status apply_lowp_T_split(const Op& op, int64_t b, const void* Xh, const void* Xl, int64_t ldx,
+                                    void* out, int64_t ldo, const double* R, int64_t ldr,
+                                    const double* coef, cudaStream_t s) {
+  return gemm_bf16_tc_split(op.n, b, op.m, (const __nv_bfloat16*)op.lo_col, (const __nv_bfloat16*)op.lo2_col,
+                            op.m, (const __nv_bfloat16*)Xh, (const __nv_bfloat16*)Xl, ldx, (float*)out, ldo,
+                            R, ldr, coef, s);
 }
 
 // FP64-accurate products with the given operator: on the tensor cores by
@@ -252,6 +275,8 @@ struct SvdBufs {
   void *Ulo, *Vlo, *W, *Pw, *Elo, *Flo, *AF;
   double *Gu, *Gv, *Bm, *Ys, *Zs, *sig2;
   double *Ut, *Vt, *Ut2, *Vt2, *sig, *P, *Qm, *Rv, *Ru, *ss, *res, *mu, *coef;
+  // split mode: lo halves of the correction blocks, FP32 final blocks
+  void *Elo2, *Flo2, *E32, *F32;
 };
 
 static void carve_svd(Arena& ar, const Op& op, int64_t b, bool refine, SvdBufs& w) {
@@ -289,6 +314,13 @@ static void carve_svd(Arena& ar, const Op& op, int64_t b, bool refine, SvdBufs& 
     w.Ut2 = w.Vt2 = w.Rv = w.Ru = w.mu = w.coef = nullptr;
     w.Elo = w.Flo = w.AF = nullptr;
   }
+  w.Elo2 = w.Flo2 = w.E32 = w.F32 = nullptr;
+  if (refine && op.split) {
+    w.Elo2 = ar.take_bytes(m * b * 2);
+    w.Flo2 = ar.take_bytes(n * b * 2);
+    w.E32 = ar.take_bytes(m * b * 4);
+    w.F32 = ar.take_bytes(n * b * 4);
+  }
 }
 
 static void make_op(const rr_operator* A, int32_t dt, Op& op) {
@@ -301,6 +333,8 @@ static void make_op(const rr_operator* A, int32_t dt, Op& op) {
   op.ci = A->col_idx;
   op.va = (const float*)A->values;
   op.lo_col = op.lo_row = nullptr;
+  op.split = false;
+  op.lo2_col = op.lo2_row = nullptr;
   op.dt = dt;
   op.wt = dt == RR_F64 ? RR_F64 : RR_F32;
   op.has_emu = false;
@@ -315,6 +349,11 @@ static void carve_op(Arena& ar, Op& op, bool symmetric, bool refine, int64_t b) 
   if (op.kind != RR_DENSE || op.dt == RR_F64) return;
   op.lo_col = ar.take_bytes(op.m * op.n * dsz(op.dt));
   op.lo_row = symmetric ? op.lo_col : ar.take_bytes(op.m * op.n * dsz(op.dt));
+  if (refine && !symmetric && op.dt == RR_BF16 && op.m % 8 == 0 && op.n % 8 == 0 && b <= 256) {
+    op.split = true;
+    op.lo2_col = ar.take_bytes(op.m * op.n * 2);
+    op.lo2_row = symmetric ? op.lo2_col : ar.take_bytes(op.m * op.n * 2);
+  }
   if (refine && op.m % 8 == 0 && op.n % 8 == 0 && b <= 256) {
     op.has_emu = true;
     op.emu_mem = ar.take_bytes(emu_operator_bytes(op.m, op.n, kEmuSlices, true, !symmetric));
@@ -326,6 +365,7 @@ static rr_status prepare_op(const Op& op_in, Op& op, bool symmetric, cudaStream_
   (void)op_in;
   if (op.lo_col)
     RR_TRY(rr_cast_operator(op.m, op.n, op.A, op.lda, op.dt, op.lo_col, symmetric ? nullptr : op.lo_row, s));
+  if (op.split) RR_TRY(cast_operator_lo(op.m, op.n, op.A, op.lda, op.lo2_col, op.lo2_row, s));
   if (op.has_emu)
     RR_TRY(emu_prepare(s, op.A, op.m, op.n, op.lda, kEmuSlices, op.emu, op.emu_mem, true, !symmetric));
   return RR_OK;
@@ -450,41 +490,59 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
       // each block kept at unit column inf-norm, the injection coefficient
       // tracked per column (coef <- coef * sigma / mu after each scaling).
       STAGE(RR_STAGE_OTHER, fill(s, b, 1.0, w.coef));
-      STAGE(RR_STAGE_OTHER, scale_cast(s, RR_F64, m, b, w.Rv, m, w.mu, dt, w.Elo, m, w.coef, w.sig));
+      // split mode: blocks and operator carried as BF16 pairs (hi + lo), the
+      // final correction blocks kept in FP32 for the projection and the lift
+      const bool sp = op.split;
+      const int32_t et = sp ? RR_F32 : dt;
+      void* Eg = sp ? w.E32 : w.Elo;
+      void* Fg = sp ? w.F32 : w.Flo;
+      if (sp) STAGE(RR_STAGE_OTHER, scale_split(s, RR_F64, m, b, w.Rv, m, w.mu, w.Elo, w.Elo2, m, w.coef, w.sig));
+      else STAGE(RR_STAGE_OTHER, scale_cast(s, RR_F64, m, b, w.Rv, m, w.mu, dt, w.Elo, m, w.coef, w.sig));
       for (int j = 0; j < q; ++j) {
-        STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp_T(op, b, w.Elo, m, w.W, n, w.Ru, n, w.coef, s));
+        if (sp) STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp_T_split(op, b, w.Elo, w.Elo2, m, w.W, n, w.Ru, n, w.coef, s));
+        else STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp_T(op, b, w.Elo, m, w.W, n, w.Ru, n, w.coef, s));
         STAGE(RR_STAGE_GRAM, project_out(w.c, s, n, b, w.Vt, n, (float*)w.W, n, w.Ys));
-        STAGE(RR_STAGE_OTHER, scale_cast(s, op.wt, n, b, w.W, n, w.mu, dt, w.Flo, n, w.coef, w.sig));
-        STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp(op, b, w.Flo, n, w.AF, m, w.Rv, m, w.coef, s));
+        if (sp) STAGE(RR_STAGE_OTHER, scale_split(s, op.wt, n, b, w.W, n, w.mu, w.Flo, w.Flo2, n, w.coef, w.sig));
+        else STAGE(RR_STAGE_OTHER, scale_cast(s, op.wt, n, b, w.W, n, w.mu, dt, w.Flo, n, w.coef, w.sig));
+        if (sp) STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp_split(op, b, w.Flo, w.Flo2, n, w.AF, m, w.Rv, m, w.coef, s));
+        else STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp(op, b, w.Flo, n, w.AF, m, w.Rv, m, w.coef, s));
         STAGE(RR_STAGE_GRAM, project_out(w.c, s, m, b, w.Ut, m, (float*)w.AF, m, w.Ys));
-        if (j + 1 < q) STAGE(RR_STAGE_OTHER, scale_cast(s, op.wt, m, b, w.AF, m, w.mu, dt, w.Elo, m, w.coef, w.sig));
+        if (j + 1 < q) {
+          if (sp) STAGE(RR_STAGE_OTHER, scale_split(s, op.wt, m, b, w.AF, m, w.mu, w.Elo, w.Elo2, m, w.coef, w.sig));
+          else STAGE(RR_STAGE_OTHER, scale_cast(s, op.wt, m, b, w.AF, m, w.mu, dt, w.Elo, m, w.coef, w.sig));
+        }
       }
       // conditioning of the correction blocks (Algorithm 8), then A F for the
       // low-precision block of the projected matrix
-      STAGE(RR_STAGE_HESSENBERG, basis_step(w.c, hess, op.wt, dt, m, b, w.AF, m, w.Elo, m, s));
-      STAGE(RR_STAGE_HESSENBERG, basis_step(w.c, hess, op.wt, dt, n, b, w.W, n, w.Flo, n, s));
-      STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp(op, b, w.Flo, n, w.AF, m, nullptr, 0, nullptr, s));
+      STAGE(RR_STAGE_HESSENBERG, basis_step(w.c, hess, op.wt, et, m, b, w.AF, m, Eg, m, s));
+      STAGE(RR_STAGE_HESSENBERG, basis_step(w.c, hess, op.wt, et, n, b, w.W, n, Fg, n, s));
+      if (sp) {
+        STAGE(RR_STAGE_OTHER, scale_split(s, RR_F32, n, b, w.F32, n, nullptr, w.Flo, w.Flo2, n, nullptr, nullptr));
+        STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp_split(op, b, w.Flo, w.Flo2, n, w.AF, m, nullptr, 0, nullptr, s));
+      } else {
+        STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp(op, b, w.Flo, n, w.AF, m, nullptr, 0, nullptr, s));
+      }
       // projected blocks over S_u = [U~, E], S_v = [V~, F]  (ld 2b)
       double* B = w.Bm;
       STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, RR_F64, w.Ut, m, RR_F64, w.P, m, B, b2, s));                   // U~^T A V~
-      STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, RR_F64, w.Qm, n, dt, w.Flo, n, B + b * b2, b2, s));          // U~^T A F
-      STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, dt, w.Elo, m, RR_F64, w.P, m, B + b, b2, s));                // E^T A V~
-      STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, dt, w.Elo, m, op.wt, w.AF, m, B + b + b * b2, b2, s));       // E^T A F
+      STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, RR_F64, w.Qm, n, et, Fg, n, B + b * b2, b2, s));             // U~^T A F
+      STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, et, Eg, m, RR_F64, w.P, m, B + b, b2, s));                   // E^T A V~
+      STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, et, Eg, m, op.wt, w.AF, m, B + b + b * b2, b2, s));          // E^T A F
       STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, RR_F64, w.Ut, m, RR_F64, w.Ut, m, w.Gu, b2, s));
-      STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, RR_F64, w.Ut, m, dt, w.Elo, m, w.Gu + b * b2, b2, s));
+      STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, RR_F64, w.Ut, m, et, Eg, m, w.Gu + b * b2, b2, s));
       STAGE(RR_STAGE_OTHER, transpose(s, b, b, w.Gu + b * b2, b2, w.Gu + b, b2));
-      STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, dt, w.Elo, m, dt, w.Elo, m, w.Gu + b + b * b2, b2, s));
+      STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, et, Eg, m, et, Eg, m, w.Gu + b + b * b2, b2, s));
       STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, RR_F64, w.Vt, n, RR_F64, w.Vt, n, w.Gv, b2, s));
-      STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, RR_F64, w.Vt, n, dt, w.Flo, n, w.Gv + b * b2, b2, s));
+      STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, RR_F64, w.Vt, n, et, Fg, n, w.Gv + b * b2, b2, s));
       STAGE(RR_STAGE_OTHER, transpose(s, b, b, w.Gv + b * b2, b2, w.Gv + b, b2));
-      STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, dt, w.Flo, n, dt, w.Flo, n, w.Gv + b + b * b2, b2, s));
+      STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, et, Fg, n, et, Fg, n, w.Gv + b + b * b2, b2, s));
       STAGE(RR_STAGE_PENCIL, rr_pencil_svd(b2, b2, B, w.Gu, w.Gv, w.sig2, w.Ys, w.Zs, w.c.pen_ws, w.c.pen_bytes,
                            nullptr, s));
       // lift the leading b triplets
       STAGE(RR_STAGE_LIFT, lift(s, RR_F64, m, b, b, w.Ut, m, w.Ys, b2, w.Ut2, m, 0));
-      STAGE(RR_STAGE_LIFT, lift(s, dt, m, b, b, w.Elo, m, w.Ys + b, b2, w.Ut2, m, 1));
+      STAGE(RR_STAGE_LIFT, lift(s, et, m, b, b, Eg, m, w.Ys + b, b2, w.Ut2, m, 1));
       STAGE(RR_STAGE_LIFT, lift(s, RR_F64, n, b, b, w.Vt, n, w.Zs, b2, w.Vt2, n, 0));
-      STAGE(RR_STAGE_LIFT, lift(s, dt, n, b, b, w.Flo, n, w.Zs + b, b2, w.Vt2, n, 1));
+      STAGE(RR_STAGE_LIFT, lift(s, et, n, b, b, Fg, n, w.Zs + b, b2, w.Vt2, n, 1));
       std::swap(w.Ut, w.Ut2);
       std::swap(w.Vt, w.Vt2);
       RR_CUDA(cudaMemcpyAsync(w.sig, w.sig2, b * sizeof(double), cudaMemcpyDeviceToDevice, s));

@@ -12,6 +12,10 @@ rr_status res_finish(cudaStream_t s, int64_t b, const double* ss, const double* 
 rr_status scale_cast(cudaStream_t s, int32_t ttype, int64_t n, int64_t b, const void* T, int64_t ldt,
                      double* mu, int32_t dtype, void* D, int64_t ldd, double* coef,
                      const double* sig);
+rr_status scale_split(cudaStream_t s, int32_t ttype, int64_t n, int64_t b, const void* T, int64_t ldt,
+                      double* mu, void* D_hi, void* D_lo, int64_t ldd, double* coef, const double* sig);
+rr_status cast_operator_lo(int64_t m, int64_t n, const double* A, int64_t lda, void* lo_col, void* lo_row,
+                           cudaStream_t s);
 rr_status transpose(cudaStream_t s, int64_t p, int64_t q, const double* src, int64_t lds, double* dst,
                     int64_t ldd);
 rr_status select_eig(cudaStream_t s, int64_t nb, int64_t b, int which, const double* theta,
@@ -62,6 +66,10 @@ struct TcEmu {
 rr_status gemm_bf16_tc_emu(int64_t M, int64_t N, int64_t K, const __nv_bfloat16* A, int64_t lda,
                            const __nv_bfloat16* B, int64_t ldb, const TcEmu& e, cudaStream_t s);
 int tc_emu_partial_splits(int64_t M, int64_t K, int npairs, int max_kchunk);
+rr_status gemm_bf16_tc_split(int64_t M, int64_t N, int64_t K, const __nv_bfloat16* A_hi,
+                             const __nv_bfloat16* A_lo, int64_t lda, const __nv_bfloat16* B_hi,
+                             const __nv_bfloat16* B_lo, int64_t ldb, float* C, int64_t ldc,
+                             const double* R, int64_t ldr, const double* coef, cudaStream_t s);
 
 // FP64-accurate products on the tensor cores (k_f64emu.cu)
 struct EmuOperator {
