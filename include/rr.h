@@ -183,7 +183,20 @@ rr_status rr_gemm_lowp(int32_t dtype, int64_t M, int64_t N, int64_t K, const voi
                        int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc,
                        const double* R, int64_t ldr, const double* coef, void* stream);
 
-/* FP64 product C = op(A) * B (+ C if accumulate), op(A) = A (trans = 0, A is
+/* Split-BF16 block product (the correction recurrence of the refinement phase;
+ * Sec. 4.2's BF16 tensor-core products with each operand carried as the BF16
+ * rounding of a wider value plus its BF16 residual):
+ *   C (M x N, FP32) = A_hi^T B_hi + A_lo^T B_hi + A_hi^T B_lo  [+ coef[j] R(:,j)]
+ * (the lo.lo term, of relative size u_bf16^2, is dropped).  Layouts as for
+ * rr_gemm_lowp: A_hi, A_lo K x M K-contiguous (ld lda), B_hi, B_lo K x N
+ * column-major (ld ldb), all BF16; one tcgen05 launch accumulating the three
+ * K ranges in FP32.  Tensor cores only: RR_ERR_ARG unless N <= 256, lda and
+ * ldb are multiples of 8 and every base pointer is 16-byte aligned. */
+rr_status rr_gemm_lowp_split(int64_t M, int64_t N, int64_t K, const void* A_hi, const void* A_lo,
+                             int64_t lda, const void* B_hi, const void* B_lo, int64_t ldb, float* C,
+                             int64_t ldc, const double* R, int64_t ldr, const double* coef, void* stream);
+
+/* FP64 product C = op(A) * B (+ C if accumulate), op(A) = A (trans = 0, A is/* FP64 product C = op(A) * B (+ C if accumulate), op(A) = A (trans = 0, A is
  * M x K, ld lda) or A^T (trans = 1, A is K x M).  B is K x N FP64 (ld ldb).
  * Used for the FP64-accurate residual products and by the all-FP64 mode. */
 rr_status rr_gemm_f64(int32_t trans, int64_t M, int64_t N, int64_t K, const double* A,

@@ -62,6 +62,8 @@ _SIGS = {
     "rr_cast_operator": (c_i32, [c_i64, c_i64, c_vp, c_i64, c_i32, c_vp, c_vp, c_vp]),
     "rr_gemm_lowp": (c_i32, [c_i32, c_i64, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp,
                              c_i64, c_vp, c_vp]),
+    "rr_gemm_lowp_split": (c_i32, [c_i64, c_i64, c_i64, c_vp, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp, c_i64,
+                                   c_vp, c_i64, c_vp, c_vp]),
     "rr_gemm_f64": (c_i32, [c_i32, c_i64, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_i32,
                             c_vp]),
     "rr_gemm_f64_emulated_workspace_size": (c_sz, [c_i32, c_i64, c_i64, c_i64, c_i32]),

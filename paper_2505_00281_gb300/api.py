@@ -187,6 +187,16 @@ def rr_gemm_lowp(dtype, M, N, K, A_k, lda, B, ldb, C=None, R=None, coef=None, st
     return C
 
 
+def rr_gemm_lowp_split(M, N, K, A_hi, A_lo, lda, B_hi, B_lo, ldb, C=None, R=None, coef=None, stream=None):
+    if C is None:
+        C = fortran(torch.empty(M, N, dtype=torch.float32, device=B_hi.device))
+    check("rr_gemm_lowp_split", lib().rr_gemm_lowp_split(M, N, K, _p(A_hi), _p(A_lo), lda, _p(B_hi), _p(B_lo),
+                                                          ldb, _p(C), ld_of(C), _p(R),
+                                                          ld_of(R) if R is not None else 0, _p(coef),
+                                                          _stream(stream)))
+    return C
+
+
 def rr_gemm_f64(trans, A, B, C=None, accumulate=False, stream=None):
     M = A.shape[1] if trans else A.shape[0]
     K = A.shape[0] if trans else A.shape[1]

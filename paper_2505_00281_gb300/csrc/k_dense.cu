@@ -247,6 +247,23 @@ bool gemm_bf16_tc_supported(int64_t M, int64_t N, int64_t K, int64_t lda, int64_
 int& gemm_force_simt();
 }  // namespace rr
 
+extern "C" rr_status rr_gemm_lowp_split(int64_t M, int64_t N, int64_t K, const void* A_hi,
+                                        const void* A_lo, int64_t lda, const void* B_hi, const void* B_lo,
+                                        int64_t ldb, float* C, int64_t ldc, const double* R, int64_t ldr,
+                                        const double* coef, void* stream) {
+  if (M < 0 || N < 0 || K < 0 || lda < K || ldb < K || ldc < M || !C) return RR_ERR_ARG;
+  if (!A_hi || !A_lo || !B_hi || !B_lo) return RR_ERR_ARG;
+  if (M == 0 || N == 0) return RR_OK;
+  if ((R != nullptr) != (coef != nullptr)) return RR_ERR_ARG;
+  if (R && ldr < M) return RR_ERR_ARG;
+  if (!gemm_bf16_tc_supported(M, N, K, lda, ldb, A_hi, B_hi) ||
+      !gemm_bf16_tc_supported(M, N, K, lda, ldb, A_lo, B_lo))
+    return RR_ERR_ARG;
+  return gemm_bf16_tc_split(M, N, K, (const __nv_bfloat16*)A_hi, (const __nv_bfloat16*)A_lo, lda,
+                            (const __nv_bfloat16*)B_hi, (const __nv_bfloat16*)B_lo, ldb, C, ldc, R, ldr,
+                            coef, as_stream(stream));
+}
+
 extern "C" rr_status rr_gemm_lowp(int32_t dtype, int64_t M, int64_t N, int64_t K, const void* A_k,
                                   int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc,
                                   const double* R, int64_t ldr, const double* coef, void* stream) {

@@ -130,9 +130,9 @@ struct TcArgs {
   int tmem_cols;   // power of two >= max(32, npad)
   int stages;
   int ksteps_per_split;
-  int nk;          // total K steps (all segments)
-  int nk1;         // K steps of one segment (K / 64 rounded up)
-  int segs;        // 1, or 3 for the split product A_hi B_hi + A_lo B_hi + A_hi B_lo
+  int nk;          // K steps (K / 64 rounded up)
+  int nk1;         // same (kept for the launch record)
+  int segs;        // 1, or 3 for the split product: per K step A_hi B_hi + A_lo B_hi + A_hi B_lo
   float* C;
   int64_t ldc;
   const double* R;
@@ -178,7 +178,9 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16_tc(const __grid_constant__
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t a_bytes = kBM * kBK * 2;            // 16 KB
   const uint32_t b_bytes = (uint32_t)a.npad * kBK * 2;
-  const uint32_t stage_bytes = a_bytes + b_bytes;     // multiple of 1024 (npad % 16 == 0 -> b_bytes % 2048)
+  // split product: a stage holds A_hi, B_hi, A_lo, B_lo of one K step
+  const bool spl = a.segs > 1;
+  const uint32_t stage_bytes = (a_bytes + b_bytes) * (spl ? 2 : 1);  // multiple of 1024
   uint64_t* full = (uint64_t*)(base + (size_t)a.stages * stage_bytes);
   uint64_t* empty = full + a.stages;
   uint64_t* accum = empty + a.stages;
@@ -225,11 +227,13 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16_tc(const __grid_constant__
         unsigned char* sa = base + (size_t)s * stage_bytes;
         unsigned char* sb = sa + a_bytes;
         mbar_expect_tx(&full[s], stage_bytes);
-        // segment of this K step (split product: hi.hi, lo.hi, hi.lo)
-        const int kg = ks0 + i, seg = kg / a.nk1;
-        const int kx = (kg - seg * a.nk1) * kBK;
-        tma_load_2d(sa, seg == 1 ? &tmA2 : &tmA, &full[s], kx, (int)m0 + a_off);
-        tma_load_2d(sb, seg == 2 ? &tmB2 : &tmB, &full[s], kx, b_off);
+        const int kx = (ks0 + i) * kBK;
+        tma_load_2d(sa, &tmA, &full[s], kx, (int)m0 + a_off);
+        tma_load_2d(sb, &tmB, &full[s], kx, b_off);
+        if (spl) {
+          tma_load_2d(sb + b_bytes, &tmA2, &full[s], kx, (int)m0 + a_off);
+          tma_load_2d(sb + b_bytes + a_bytes, &tmB2, &full[s], kx, b_off);
+        }
         ++issued;
       }
       if (issued < nks) {
@@ -262,6 +266,15 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16_tc(const __grid_constant__
         for (int kk = 0; kk < kBK / 16; ++kk)  // K = 16 per instruction: +32 bytes
           umma_bf16(tmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc,
                     (i > 0 || kk > 0) ? 1u : 0u);
+        if (spl) {
+          // A_lo B_hi and A_hi B_lo from the same stage (each operand read once)
+          const uint64_t ad2 = sdesc_sw128(sb + b_bytes), bd2 = sdesc_sw128(sb + b_bytes + a_bytes);
+#pragma unroll
+          for (int kk = 0; kk < kBK / 16; ++kk) {
+            umma_bf16(tmem, ad2 + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc, 1u);
+            umma_bf16(tmem, ad + (uint64_t)(kk * 2), bd2 + (uint64_t)(kk * 2), idesc, 1u);
+          }
+        }
         umma_commit(&empty[s]);
       }
       // the final commit arrives once every MMA issued above has completed,
@@ -462,8 +475,9 @@ rr_status gemm_bf16_tc_emu(int64_t M, int64_t N, int64_t K, const __nv_bfloat16*
   return gemm_bf16_tc_impl(M, N, K, A, lda, B, ldb, nullptr, 0, nullptr, 0, nullptr, &e, s);
 }
 
-// Split product (A2, B2 non-null): C = A^T B + A2^T B + A^T B2 (+ coef R),
-// the three K ranges run as consecutive segments of one accumulation.
+// Split product (A2, B2 non-null): C = A^T B + A2^T B + A^T B2 (+ coef R);
+// every pipeline stage carries the four tiles of one K step and three MMAs
+// consume them, so each operand is read once.
 static rr_status gemm_bf16_tc_impl(int64_t M, int64_t N, int64_t K, const __nv_bfloat16* A, int64_t lda,
                                    const __nv_bfloat16* B, int64_t ldb, float* C, int64_t ldc,
                                    const double* R, int64_t ldr, const double* coef, const TcEmu* emu,
@@ -497,7 +511,7 @@ static rr_status gemm_bf16_tc_impl(int64_t M, int64_t N, int64_t K, const __nv_b
   const int64_t tiles = (M + kBM - 1) / kBM;
   const int nk1 = (int)tc_nk(K);
   const int segs = split ? 3 : 1;
-  const int nk = nk1 * segs;
+  const int nk = nk1;
   const int sms = num_sms();
   const int npairs = emu ? emu->npairs : 1;
   int splits = 1;
@@ -514,7 +528,7 @@ static rr_status gemm_bf16_tc_impl(int64_t M, int64_t N, int64_t K, const __nv_b
   if (per < 1) return RR_ERR_ARG;
   splits = (nk + per - 1) / per;
   if (emu && emu->part && splits != tc_emu_partial_splits(M, K, npairs, emu->max_kchunk)) return RR_ERR_ARG;
-  const uint32_t stage_bytes = kBM * kBK * 2 + (uint32_t)npad * kBK * 2;
+  const uint32_t stage_bytes = (kBM * kBK * 2 + (uint32_t)npad * kBK * 2) * (split ? 2 : 1);
   int stages = (int)((200 * 1024) / stage_bytes);
   if (stages > 8) stages = 8;
   if (stages < 2) return RR_ERR_ARG;

@@ -142,6 +142,29 @@ def test_f64_emulation_exact_on_integers(rr, trans):
     assert np.array_equal(host(G), (X.T @ B).astype(np.float64))
 
 
+@pytest.mark.parametrize("M,N,K", [(16384, 128, 4096), (4096, 128, 16384), (1000, 100, 777 + 7)])
+def test_gemm_lowp_split_two_term_accuracy(rr, M, N, K):
+    """Split-BF16 product (A_hi + A_lo)^T (B_hi + B_lo) without lo.lo, FP32
+    accumulation: the error against the exact product of the wide operands is
+    the dropped term plus the residual of the 16-bit pairs and FP32 rounding,
+    |err| <= (3 u_bf16^2 + 4 K u32) (|A|^T |B|), about 1000x below the plain
+    BF16 product's error; the K-split path is taken for small M."""
+    rng = np.random.default_rng(M + N + K)
+    K = K - K % 8
+    A = rng.standard_normal((K, M)).astype(np.float32).astype(np.float64)
+    B = rng.standard_normal((K, N)).astype(np.float32).astype(np.float64)
+    Ah, Bh = O.round_bf16(A), O.round_bf16(B)
+    Al, Bl = O.round_bf16(A - Ah), O.round_bf16(B - Bh)
+    dA = lambda X: rr.fortran(torch.from_numpy(np.asfortranarray(X)).to(DEV).to(torch.bfloat16))
+    C = rr.rr_gemm_lowp_split(M, N, K, dA(Ah), dA(Al), K, dA(Bh), dA(Bl), K)
+    ref = A.T @ B
+    absr = np.abs(A).T @ np.abs(B)
+    err = np.abs(host(C) - ref)
+    assert np.all(err <= (3 * 2.0 ** -16 + 4 * K * U24) * absr + 1e-30)
+    plain = np.abs(Ah.T @ Bh - ref)
+    assert np.median(err) < 0.05 * np.median(plain)
+
+
 # ---------------------------------------------------------------- a4 (Algorithm 8)
 @pytest.mark.parametrize("n,k", [(1000, 48), (20000, 32), (77, 77), (5, 3)])
 def test_hessenberg_bitexact_fp32(rr, n, k):
