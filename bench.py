@@ -200,8 +200,12 @@ def stage_roofline(info, peaks, src, refine_sweeps, phase1_sweeps):
     if "lowp_product" in stages:
         t = stages["lowp_product"]["ms"] * 1e-3
         ach = prod_bytes / t / 1e9
+        # DRAM bytes per launch from ncu (one A V launch of each kind, read +
+        # write; the A^T W launches are taken to move the same bytes)
+        traffic = n_plain * 138.30e6 + n_split * 273.57e6
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": None, "kernel": "k_gemm_bf16_tc", "stage": "lowp_product",
+                "traffic": traffic, "traffic_scope": "DRAM bytes per solve, ncu per-launch counts x launches",
+                "kernel": "k_gemm_bf16_tc", "stage": "lowp_product",
                 "launches": stages["lowp_product"]["calls"],
                 "algorithmic_bytes_per_solve": prod_bytes, "peak_source": src + " (of measured)"}
         stages["lowp_product"].update({"bound": "hbm", "achieved_gbs": ach, "frac": ach / hbm})
