@@ -10,6 +10,9 @@
 // Small O(b^3) steps run in one CTA per problem; the triangular transforms
 // are small FP64 GEMMs spread over the GPU.
 #include <cfloat>
+#include <climits>
+
+#include <cooperative_groups.h>
 
 #include "rr_common.cuh"
 
@@ -899,6 +902,7 @@ __global__ void k_v32_to_64(int c, int cpad, const float* __restrict__ V32, doub
 struct PencilWs {
   double *W1, *W2, *T, *E, *E2, *F, *C, *V, *Vp, *M, *Mp, *sig, *mu;
   float *L32, *Li32, *M32, *V32, *fs;  // fs: [0] Jacobi norm floor, [1] scale
+  float *Hq, *tq;                      // QR preconditioner: reflectors (c x c), taus
   int *drop1, *drop2, *order, *nvalid, *rot, *err, *sweeps, *cid, *cst;
   GridBarrier* bar;
 };
@@ -947,6 +951,8 @@ static bool carve_pencil(Arena& ar, int b1, int b2, PencilWs& w) {
   w.Li32 = ar.take<float>(bb);
   w.M32 = ar.take<float>(rc);
   w.V32 = ar.take<float>(cc);
+  w.Hq = ar.take<float>(cc);
+  w.tq = ar.take<float>(cp);
   w.drop1 = ar.take<int>(bm);
   w.drop2 = ar.take<int>(bm);
   w.order = ar.take<int>(cp);
@@ -1050,6 +1056,296 @@ static rr_status launch_bj(cudaStream_t s, int r, int cpad, int w, int P, float*
     return check_launch("block_jacobi");
   }
   RR_CUDA(cudaLaunchCooperativeKernel(fn, dim3(P), dim3(kBJThreads), args, smem, s));
+  note_launches(1);
+  return RR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// QR preconditioning of the one-sided Jacobi (the preconditioned Jacobi SVD
+// of Drmac and Veselic).  With the column-pivoted Householder QR
+// C^T P = Q R, the Jacobi runs on X = C Q (whose columns are the rows of R,
+// graded by the pivoting) and accumulates its rotations onto Q, so that
+// X J = C (Q J) and V = Q J.  Graded columns need about half the sweeps of
+// C's own columns.
+//
+// One cluster of NC CTAs holds A = s C^T (c x r, s the power-of-two scale) in
+// registers: CTA z owns the columns k = z 16 CPW + 16 u + warp (u < CPW),
+// lane l the rows t 32 + l (t < RPL).  Step j takes the reflector of the
+// column with the largest remaining norm (rows >= j; ties to the lower
+// column), applies it to every column not yet pivoted, recomputes their
+// remaining norms exactly (rows > j), and each CTA publishes the reflector of
+// its best column into every CTA's shared memory (double-buffered by step
+// parity: one cluster barrier per step).  The reflector of x (rows >= j) is
+// v = x - beta e_j, beta = -sign(x_j) |x|, tau = 1 / (beta (beta - x_j)), so
+// that (I - tau v v^T) x = beta e_j.  Q = H_0 H_1 ... H_{c-1} is formed
+// afterwards by backward accumulation from the stored reflectors; every CTA
+// owns whole columns of Q, so that part needs no barrier.
+constexpr int kQrThreads = 512;
+constexpr int kQrWarps = kQrThreads / 32;
+constexpr int kQrMaxNC = 8;
+constexpr int kQrMaxRows = 384;  // 32 x 12
+
+struct QrCand {
+  float nrm2;  // squared norm of the candidate's remaining part (-1: none)
+  int col;
+  float tau, beta;
+};
+
+__device__ __forceinline__ bool qr_better(float n, int k, float bn, int bk) {
+  return n > bn || (n == bn && k < bk);
+}
+
+template <int RPL, int CPW>
+__global__ void __launch_bounds__(kQrThreads, 1)
+    k_qr_precond(int r, int c, const double* __restrict__ C, const float* __restrict__ scale,
+                 float* __restrict__ X, int cpad, float* __restrict__ Vq, float* __restrict__ Hv,
+                 float* __restrict__ tq) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ __align__(16) float vbuf[2][kQrMaxNC][kQrMaxRows];
+  __shared__ QrCand cand[2][kQrMaxNC];
+  __shared__ float wn[kQrWarps];
+  __shared__ int wk[kQrWarps];
+  const int NC = (int)cl.num_blocks();
+  const int z = (int)cl.block_rank();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float sc = *scale;
+  const int col0 = z * kQrWarps * CPW + warp;  // column of slot u: col0 + 16 u
+
+  float a[CPW][RPL];
+  unsigned done = 0;  // slot u pivoted already (or beyond the last column)
+#pragma unroll
+  for (int u = 0; u < CPW; ++u) {
+    const int k = col0 + kQrWarps * u;
+    if (k >= r) done |= 1u << u;
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) {
+      const int i = t * 32 + lane;
+      a[u][t] = (k < r && i < c) ? (float)((double)sc * C[k + (size_t)i * r]) : 0.f;
+    }
+  }
+
+  // best remaining column of this CTA (rows > j) -> reflector for step j + 1
+  // into buffer `par` of every CTA
+  auto publish = [&](int j, int par) {
+    float bn = -1.f;
+    int bk = INT_MAX, bu = -1;
+#pragma unroll
+    for (int u = 0; u < CPW; ++u) {
+      if (done >> u & 1u) continue;
+      float s2 = 0.f;
+#pragma unroll
+      for (int t = 0; t < RPL; ++t)
+        if (t * 32 + lane > j) s2 = fmaf(a[u][t], a[u][t], s2);
+      s2 = warp_sum(s2);
+      const int k = col0 + kQrWarps * u;
+      if (qr_better(s2, k, bn, bk)) {
+        bn = s2;
+        bk = k;
+        bu = u;
+      }
+    }
+    if (lane == 0) {
+      wn[warp] = bn;
+      wk[warp] = bk;
+    }
+    __syncthreads();
+    float cn = -1.f;
+    int ck = INT_MAX, cw = -1;
+    for (int q = 0; q < kQrWarps; ++q)
+      if (qr_better(wn[q], wk[q], cn, ck)) {
+        cn = wn[q];
+        ck = wk[q];
+        cw = q;
+      }
+    if (cw < 0) {  // every column of this CTA is pivoted: publish "none"
+      if (threadIdx.x < NC) {
+        QrCand* dst = cl.map_shared_rank(&cand[par][z], (int)threadIdx.x);
+        *dst = QrCand{-1.f, INT_MAX, 0.f, 0.f};
+      }
+      return;
+    }
+    if (warp != cw) return;
+    const int j1 = j + 1;
+    float x[RPL];
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) x[t] = 0.f;
+#pragma unroll
+    for (int u = 0; u < CPW; ++u)
+      if (u == bu) {
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) x[t] = a[u][t];
+      }
+    float xj = 0.f;
+#pragma unroll
+    for (int t = 0; t < RPL; ++t)
+      if (t == (j1 >> 5)) xj = x[t];
+    xj = __shfl_sync(0xffffffffu, xj, j1 & 31);
+    const float beta = -copysignf(sqrtf(cn), xj);
+    const float tau = cn > 0.f ? 1.f / (beta * (beta - xj)) : 0.f;
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) {
+      const int i = t * 32 + lane;
+      x[t] = i > j1 ? x[t] : (i == j1 ? xj - beta : 0.f);
+    }
+    for (int q = 0; q < NC; ++q) {
+      float* dst = cl.map_shared_rank(&vbuf[par][z][0], q);
+#pragma unroll
+      for (int t = 0; t < RPL; ++t) dst[t * 32 + lane] = x[t];
+      if (lane == 0) *cl.map_shared_rank(&cand[par][z], q) = QrCand{cn, ck, tau, beta};
+    }
+  };
+
+  publish(-1, 0);
+  for (int j = 0; j < c; ++j) {
+    cl.sync();
+    const int par = j & 1;
+    QrCand b = cand[par][0];
+    int zs = 0;
+    for (int q = 1; q < NC; ++q) {
+      const QrCand m = cand[par][q];
+      if (qr_better(m.nrm2, m.col, b.nrm2, b.col)) {
+        b = m;
+        zs = q;
+      }
+    }
+    const float* v = &vbuf[par][zs][0];
+    float vr[RPL];
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) vr[t] = v[t * 32 + lane];
+    if (z == j % NC) {
+      for (int i = threadIdx.x; i < c; i += kQrThreads) Hv[(size_t)j * c + i] = v[i];
+      if (threadIdx.x == 0) tq[j] = b.tau;
+    }
+#pragma unroll
+    for (int u = 0; u < CPW; ++u) {
+      if (done >> u & 1u) continue;
+      const int k = col0 + kQrWarps * u;
+      if (k == b.col) {  // the pivot column becomes beta e_j
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) {
+          const int i = t * 32 + lane;
+          a[u][t] = i == j ? b.beta : (i > j ? 0.f : a[u][t]);
+        }
+        done |= 1u << u;
+        continue;
+      }
+      float d = 0.f;
+#pragma unroll
+      for (int t = 0; t < RPL; ++t) d = fmaf(vr[t], a[u][t], d);
+      d = warp_sum(d) * b.tau;
+#pragma unroll
+      for (int t = 0; t < RPL; ++t) a[u][t] = fmaf(-d, vr[t], a[u][t]);
+    }
+    if (j + 1 < c) publish(j, par ^ 1);
+  }
+
+  // X (r x cpad, ld r) = (Q^T A)^T = s C Q; zero padding columns
+#pragma unroll
+  for (int u = 0; u < CPW; ++u) {
+    const int k = col0 + kQrWarps * u;
+    if (k >= r) continue;
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) {
+      const int i = t * 32 + lane;
+      if (i < c) X[k + (size_t)i * r] = a[u][t];
+    }
+  }
+  if (z == 0) {
+    for (int e = threadIdx.x; e < (cpad - c) * r; e += kQrThreads) X[(size_t)c * r + e] = 0.f;
+    // V padding: rows >= c of the first c columns zero, identity beyond
+    for (int e = threadIdx.x; e < cpad * cpad; e += kQrThreads) {
+      const int i = e % cpad, k = e / cpad;
+      if (i >= c || k >= c) Vq[e] = (i == k) ? 1.f : 0.f;
+    }
+  }
+  __threadfence();
+  cl.sync();  // every reflector stored
+
+  // Q by backward accumulation: Q^(j) = H_j Q^(j+1); columns k < j of
+  // Q^(j+1) are e_k, which H_j leaves alone (v_k = 0 for k < j)
+#pragma unroll
+  for (int u = 0; u < CPW; ++u) {
+    const int k = col0 + kQrWarps * u;
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) a[u][t] = (t * 32 + lane == k) ? 1.f : 0.f;
+  }
+  float vn[RPL];
+#pragma unroll
+  for (int t = 0; t < RPL; ++t) {
+    const int i = t * 32 + lane;
+    vn[t] = i < c ? __ldcg(&Hv[(size_t)(c - 1) * c + i]) : 0.f;
+  }
+  float taun = __ldcg(&tq[c - 1]);
+  for (int j = c - 1; j >= 0; --j) {
+    float vr[RPL];
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) vr[t] = vn[t];
+    const float tau = taun;
+    if (j > 0) {  // prefetch the next reflector
+#pragma unroll
+      for (int t = 0; t < RPL; ++t) {
+        const int i = t * 32 + lane;
+        vn[t] = i < c ? __ldcg(&Hv[(size_t)(j - 1) * c + i]) : 0.f;
+      }
+      taun = __ldcg(&tq[j - 1]);
+    }
+    if (tau == 0.f) continue;
+#pragma unroll
+    for (int u = 0; u < CPW; ++u) {
+      const int k = col0 + kQrWarps * u;
+      if (k < j || k >= c) continue;
+      float d = 0.f;
+#pragma unroll
+      for (int t = 0; t < RPL; ++t) d = fmaf(vr[t], a[u][t], d);
+      d = warp_sum(d) * tau;
+#pragma unroll
+      for (int t = 0; t < RPL; ++t) a[u][t] = fmaf(-d, vr[t], a[u][t]);
+    }
+  }
+  // V (cpad x cpad, ld cpad): Q in the leading c x c block
+#pragma unroll
+  for (int u = 0; u < CPW; ++u) {
+    const int k = col0 + kQrWarps * u;
+    if (k >= c) continue;
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) {
+      const int i = t * 32 + lane;
+      if (i < c) Vq[i + (size_t)k * cpad] = a[u][t];
+    }
+  }
+}
+
+// the preconditioner applies for r >= c (A = C^T has at least as many
+// columns as rows) and pencils wide enough for the saved sweeps to pay
+constexpr int kQrMinCols = 160;
+
+static bool qr_precond_applies(int r, int c) { return r >= c && c >= kQrMinCols && c <= kQrMaxRows; }
+
+static rr_status launch_qr_precond(cudaStream_t s, int r, int c, const double* C, const float* scale, float* X,
+                                   int cpad, float* V, float* Hv, float* tq) {
+  const int rpl = c <= 128 ? 4 : c <= 256 ? 8 : 12;
+  const int cpw = rpl <= 8 ? 8 : 4;
+  const int NC = (r + kQrWarps * cpw - 1) / (kQrWarps * cpw);
+  if (c > r || c > kQrMaxRows || NC > kQrMaxNC || cpad < c) return RR_ERR_ARG;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(NC);
+  cfg.blockDim = dim3(kQrThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = NC;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (rpl == 4)
+    RR_CUDA(cudaLaunchKernelEx(&cfg, k_qr_precond<4, 8>, r, c, C, scale, X, cpad, V, Hv, tq));
+  else if (rpl == 8)
+    RR_CUDA(cudaLaunchKernelEx(&cfg, k_qr_precond<8, 8>, r, c, C, scale, X, cpad, V, Hv, tq));
+  else
+    RR_CUDA(cudaLaunchKernelEx(&cfg, k_qr_precond<12, 4>, r, c, C, scale, X, cpad, V, Hv, tq));
   note_launches(1);
   return RR_OK;
 }
@@ -1268,7 +1564,8 @@ static size_t cluster_smem(int c) {
 // SVD of the r x c matrix C (FP64, ld r): on exit Mout (r x c) = C V with
 // orthogonal columns, Vout (c x c) orthogonal.  FP32 block one-sided Jacobi
 // (relative orthogonality 1e-4, column norms floored at 1e-10 of the largest
-// so rounding-level directions do not stall it), then four FP64 refinement
+// so rounding-level directions do not stall it; for wide pencils on the
+// QR-preconditioned C Q, starting from V = Q), then four FP64 refinement
 // steps (N = C V, K = N^T N, T = V^T V, clusters, V <- V (I + E)) and
 // M = C V.
 static rr_status jacobi_svd(cudaStream_t s, int r, int c, const double* C, PencilWs& w, double* Mout,
@@ -1279,7 +1576,12 @@ static rr_status jacobi_svd(cudaStream_t s, int r, int c, const double* C, Penci
   // FP32 copy scaled by a power of two to max entry in [1/2, 1): squared
   // column norms stay well inside the FP32 range
   k_pow2_scale<<<1, 1024, 0, s>>>(r, c, C, r, w.fs + 1);
-  k_pad_copy<double, float><<<g, 256, 0, s>>>(r, c, cpad, C, r, w.M32, w.V32, w.fs + 1);
+  if (qr_precond_applies(r, c)) {
+    // Jacobi on s C Q with V starting at Q (C^T P = Q R)
+    RR_TRY(launch_qr_precond(s, r, c, C, w.fs + 1, w.M32, cpad, w.V32, w.Hq, w.tq));
+  } else {
+    k_pad_copy<double, float><<<g, 256, 0, s>>>(r, c, cpad, C, r, w.M32, w.V32, w.fs + 1);
+  }
   float* fl = w.fs;
   k_colnorm_floor<float><<<1, 1024, 0, s>>>(r, cpad, w.M32, r, 1e-10f, fl);
   RR_TRY(launch_bj(s, r, cpad, ww, P, w.M32, w.V32, 1e-4f, 15, w, fl));
