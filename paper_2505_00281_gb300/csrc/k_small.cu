@@ -593,14 +593,14 @@ __global__ void k_whiten_corr(int b, double* __restrict__ E, const double* __res
 // blocks (sub-round t pairs column i of block a with column (i + t) mod w of
 // block b), c - 1 sub-rounds per sweep in all.
 //
-// A sub-round has three phases separated by __syncthreads: (1) warp i forms
-// the inner product of its pair (in the cross rounds column i of block a
-// stays in warp i's registers for the whole round); (2) one warp computes the
-// w rotations, lane j for pair j, and carries the squared column norms
-// through them (|x'|^2 = |x|^2 - t g, |y'|^2 = |y|^2 + t g; the norms are
-// computed when the block is loaded); (3) warp i applies its rotation to the
-// pair and to the round's 2w x 2w accumulated rotation Q, which is applied to
-// the V block once at the end of the round (V_blk <- V_blk Q).  A pair whose
+// In a sub-round warp i forms the inner product of its pair (in the cross
+// rounds column i of block a stays in warp i's registers for the whole
+// round), computes the rotation, carries the squared column norms through it
+// (|x'|^2 = |x|^2 - t g, |y'|^2 = |y|^2 + t g; the norms are computed when
+// the block is loaded) and applies it to the pair and to the round's 2w x 2w
+// accumulated rotation Q, which is applied to the V block once at the end of
+// the round (V_blk <- V_blk Q); the pairs of a sub-round are disjoint, so one
+// __syncthreads separates sub-rounds.  A pair whose
 // inner product is exactly zero, or below tol relative to the column norms
 // (floored, so rounding-level columns count as converged against
 // everything), is not rotated; zero columns (dropped directions, padding)
@@ -629,9 +629,113 @@ __device__ __forceinline__ void bj_pair(int round, int pi, int sr, int w, int& p
   }
 }
 
+// One round's pair work on the 2w columns in shared memory (Ms [2w][rp],
+// tracked squared norms nrm, Q accumulated in Qs [2w][ldq]); every thread of
+// the block calls it, and it ends with the columns back in Ms.
+template <int NCH>
+__device__ __forceinline__ void bj_round(int round, int w, int rp, float* __restrict__ Ms, float* __restrict__ Qs,
+                                         int ldq, float* __restrict__ nrm, float nfloor, float tol2,
+                                         int* s_rot) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int w2 = 2 * w, rch = rp >> 2;
+  const bool resident = round > 0;  // column `warp` of block a lives in registers
+  float4 xr[NCH];
+  if (resident && warp < w) {
+    const float4* mp = reinterpret_cast<const float4*>(Ms + (size_t)warp * rp);
+#pragma unroll
+    for (int t = 0; t < NCH; ++t) {
+      const int c = lane + 32 * t;
+      xr[t] = c < rch ? mp[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  const int nsub = (round == 0) ? w2 - 1 : w;
+  for (int sr = 0; sr < nsub; ++sr) {
+    // warp `warp` owns pair `warp` of the sub-round: inner product, its
+    // rotation (every lane computes it from the reduced sums), the update
+    // of the two columns, their tracked norms and Q's two columns; pairs
+    // of a sub-round are disjoint, so one barrier per sub-round suffices
+    if (warp < w) {
+      int p, q;
+      bj_pair(round, warp, sr, w, p, q);
+      float4 x[NCH], y[NCH];
+      const float4* mp = reinterpret_cast<const float4*>(Ms + (size_t)p * rp);
+      const float4* mq = reinterpret_cast<const float4*>(Ms + (size_t)q * rp);
+      float ga = 0.f;
+#pragma unroll
+      for (int t = 0; t < NCH; ++t) {
+        const int c = lane + 32 * t;
+        x[t] = resident ? xr[t] : (c < rch ? mp[c] : make_float4(0.f, 0.f, 0.f, 0.f));
+        y[t] = c < rch ? mq[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+        ga = fmaf(x[t].x, y[t].x, ga);
+        ga = fmaf(x[t].y, y[t].y, ga);
+        ga = fmaf(x[t].z, y[t].z, ga);
+        ga = fmaf(x[t].w, y[t].w, ga);
+      }
+      ga = warp_sum(ga);
+      const float al = nrm[p], be = nrm[q];
+      const float fa = fmaxf(al, nfloor), fb = fmaxf(be, nfloor);
+      // rotate unless |g| <= tol |x| |y| (squared form; the block is scaled
+      // so that squared norms stay far from the FP32 range limits)
+      if (ga != 0.f && ga * ga > tol2 * fa * fb) {
+        // t the smaller root of t^2 + 2 zeta t - 1 = 0, zeta = (|y|^2 - |x|^2) / (2 g)
+        const float zeta = __fdividef(be - al, 2.f * ga);
+        const float az = fabsf(zeta);
+        float tt;
+        if (az > 1e18f) {
+          tt = __fdividef(0.5f, az);
+        } else {
+          const float s2 = fmaf(az, az, 1.f);
+          tt = __fdividef(1.f, az + s2 * rsqrtf(s2));
+        }
+        tt = copysignf(tt, zeta);
+        const float u = fmaf(tt, tt, 1.f);
+        float cs = rsqrtf(u);
+        cs = cs * fmaf(-0.5f * u, cs * cs, 1.5f);  // one Newton step: cs^2 (1 + t^2) = 1
+        const float sn = cs * tt;
+        float4* mpw = reinterpret_cast<float4*>(Ms + (size_t)p * rp);
+        float4* mqw = reinterpret_cast<float4*>(Ms + (size_t)q * rp);
+#pragma unroll
+        for (int t = 0; t < NCH; ++t) {
+          const int c = lane + 32 * t;
+          float4 a4, b4;
+          a4.x = cs * x[t].x - sn * y[t].x;
+          a4.y = cs * x[t].y - sn * y[t].y;
+          a4.z = cs * x[t].z - sn * y[t].z;
+          a4.w = cs * x[t].w - sn * y[t].w;
+          b4.x = sn * x[t].x + cs * y[t].x;
+          b4.y = sn * x[t].y + cs * y[t].y;
+          b4.z = sn * x[t].z + cs * y[t].z;
+          b4.w = sn * x[t].w + cs * y[t].w;
+          if (resident) xr[t] = a4;
+          else if (c < rch) mpw[c] = a4;
+          if (c < rch) mqw[c] = b4;
+        }
+        if (lane < w2) {
+          const float qp = Qs[lane * ldq + p], qq = Qs[lane * ldq + q];
+          Qs[lane * ldq + p] = cs * qp - sn * qq;
+          Qs[lane * ldq + q] = sn * qp + cs * qq;
+        }
+        if (lane == 0) {
+          nrm[p] = al - tt * ga;
+          nrm[q] = be + tt * ga;
+          *s_rot = 1;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (resident && warp < w) {
+    float4* mp = reinterpret_cast<float4*>(Ms + (size_t)warp * rp);
+#pragma unroll
+    for (int t = 0; t < NCH; ++t) {
+      const int c = lane + 32 * t;
+      if (c < rch) mp[c] = xr[t];
+    }
+  }
+}
+
 // Shared-memory layout: Ms [2w][rp] and Vs [2w][cp4] with rp, cp4 the row
-// counts rounded up to 4 (zero rows; float4 access), Qs [2w][ldq], nrm [2w],
-// gam / rc / rs [w] (inner products and rotations of the sub-round).
+// counts rounded up to 4 (zero rows; float4 access), Qs [2w][ldq], nrm [2w].
 // NCH = row chunks of 4 per lane (rp <= 128 NCH).
 template <int NCH>
 __global__ void __launch_bounds__(kBJThreads) k_block_jacobi(int r, int cpad, int w, float* __restrict__ M,
@@ -648,12 +752,8 @@ __global__ void __launch_bounds__(kBJThreads) k_block_jacobi(int r, int cpad, in
   float* Vs = Ms + (size_t)w2 * rp;
   float* Qs = Vs + (size_t)w2 * cp4;
   float* nrm = Qs + w2 * ldq;
-  float* gam = nrm + w2;
-  float* rc = gam + w;
-  float* rs = rc + w;
   const int P = gridDim.x, g = blockIdx.x, nblk = 2 * P;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kBJThreads / 32;
-  const int rch = rp >> 2;  // float4 chunks per M column
   const float nfloor = floor_ptr ? *floor_ptr : 0.f;
   const float tol2 = tol * tol;
   __shared__ int s_rot;
@@ -685,113 +785,7 @@ __global__ void __launch_bounds__(kBJThreads) k_block_jacobi(int r, int cpad, in
         Qs[e] = (i == j) ? 1.f : 0.f;
       }
       __syncthreads();
-      const bool resident = round > 0;  // column `warp` of block a lives in registers
-      float4 xr[NCH];
-      if (resident && warp < w) {
-        const float4* mp = reinterpret_cast<const float4*>(Ms + (size_t)warp * rp);
-#pragma unroll
-        for (int t = 0; t < NCH; ++t) {
-          const int c = lane + 32 * t;
-          xr[t] = c < rch ? mp[c] : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-      }
-      const int nsub = (round == 0) ? w2 - 1 : w;
-      for (int sr = 0; sr < nsub; ++sr) {
-        // (1) inner products
-        int p = 0, q = 0;
-        float4 x[NCH], y[NCH];
-        if (warp < w) {
-          bj_pair(round, warp, sr, w, p, q);
-          const float4* mp = reinterpret_cast<const float4*>(Ms + (size_t)p * rp);
-          const float4* mq = reinterpret_cast<const float4*>(Ms + (size_t)q * rp);
-          float ga = 0.f;
-#pragma unroll
-          for (int t = 0; t < NCH; ++t) {
-            const int c = lane + 32 * t;
-            x[t] = resident ? xr[t] : (c < rch ? mp[c] : make_float4(0.f, 0.f, 0.f, 0.f));
-            y[t] = c < rch ? mq[c] : make_float4(0.f, 0.f, 0.f, 0.f);
-            ga = fmaf(x[t].x, y[t].x, ga);
-            ga = fmaf(x[t].y, y[t].y, ga);
-            ga = fmaf(x[t].z, y[t].z, ga);
-            ga = fmaf(x[t].w, y[t].w, ga);
-          }
-          ga = warp_sum(ga);
-          if (lane == 0) gam[warp] = ga;
-        }
-        __syncthreads();
-        // (2) the rotations, lane j for pair j
-        if (warp == 0 && lane < w) {
-          int pj, qj;
-          bj_pair(round, lane, sr, w, pj, qj);
-          const float ga = gam[lane];
-          const float al = nrm[pj], be = nrm[qj];
-          const float fa = fmaxf(al, nfloor), fb = fmaxf(be, nfloor);
-          float cs = 1.f, sn = 0.f;
-          // rotate unless |g| <= tol |x| |y| (squared form; the block is scaled
-          // so that squared norms stay far from the FP32 range limits)
-          if (ga != 0.f && ga * ga > tol2 * fa * fb) {
-            // t the smaller root of t^2 + 2 zeta t - 1 = 0, zeta = (|y|^2 - |x|^2) / (2 g)
-            const float zeta = __fdividef(be - al, 2.f * ga);
-            const float az = fabsf(zeta);
-            float tt;
-            if (az > 1e18f) {
-              tt = __fdividef(0.5f, az);
-            } else {
-              const float s2 = fmaf(az, az, 1.f);
-              tt = __fdividef(1.f, az + s2 * rsqrtf(s2));
-            }
-            tt = copysignf(tt, zeta);
-            const float u = fmaf(tt, tt, 1.f);
-            cs = rsqrtf(u);
-            cs = cs * fmaf(-0.5f * u, cs * cs, 1.5f);  // one Newton step: cs^2 (1 + t^2) = 1
-            sn = cs * tt;
-            nrm[pj] = al - tt * ga;
-            nrm[qj] = be + tt * ga;
-            s_rot = 1;
-          }
-          rc[lane] = cs;
-          rs[lane] = sn;
-        }
-        __syncthreads();
-        // (3) apply
-        if (warp < w) {
-          const float cs = rc[warp], sn = rs[warp];
-          if (sn != 0.f) {
-            float4* mp = reinterpret_cast<float4*>(Ms + (size_t)p * rp);
-            float4* mq = reinterpret_cast<float4*>(Ms + (size_t)q * rp);
-#pragma unroll
-            for (int t = 0; t < NCH; ++t) {
-              const int c = lane + 32 * t;
-              float4 a4, b4;
-              a4.x = cs * x[t].x - sn * y[t].x;
-              a4.y = cs * x[t].y - sn * y[t].y;
-              a4.z = cs * x[t].z - sn * y[t].z;
-              a4.w = cs * x[t].w - sn * y[t].w;
-              b4.x = sn * x[t].x + cs * y[t].x;
-              b4.y = sn * x[t].y + cs * y[t].y;
-              b4.z = sn * x[t].z + cs * y[t].z;
-              b4.w = sn * x[t].w + cs * y[t].w;
-              if (resident) xr[t] = a4;
-              else if (c < rch) mp[c] = a4;
-              if (c < rch) mq[c] = b4;
-            }
-            if (lane < w2) {
-              const float qp = Qs[lane * ldq + p], qq = Qs[lane * ldq + q];
-              Qs[lane * ldq + p] = cs * qp - sn * qq;
-              Qs[lane * ldq + q] = sn * qp + cs * qq;
-            }
-          }
-        }
-        __syncthreads();
-      }
-      if (resident && warp < w) {
-        float4* mp = reinterpret_cast<float4*>(Ms + (size_t)warp * rp);
-#pragma unroll
-        for (int t = 0; t < NCH; ++t) {
-          const int c = lane + 32 * t;
-          if (c < rch) mp[c] = xr[t];
-        }
-      }
+      bj_round<NCH>(round, w, rp, Ms, Qs, ldq, nrm, nfloor, tol2, &s_rot);
       __syncthreads();
       // store back M
       for (int l = warp; l < w2; l += nw) {
@@ -850,6 +844,163 @@ __global__ void __launch_bounds__(kBJThreads) k_block_jacobi(int r, int cpad, in
       if (!s_rot) break;
     }
     __syncthreads();
+  }
+  if (g == 0 && tid == 0 && sweeps_out) *sweeps_out = sweep;
+}
+
+// The same block Jacobi on one thread-block cluster (P <= 8 CTAs): the
+// columns stay in shared memory for the whole solve.  At the end of a round
+// each CTA sends its two blocks straight into the shared memory of the CTAs
+// that take them in the next round (double-buffered by round parity), the V
+// block as V_blk Q, so a round costs one cluster barrier and no global
+// traffic.  Shared memory: Mb [2][2w][rp], Vb [2][2w][cp4], Qs [2w][ldq],
+// nrm [2w].
+constexpr int kBJMaxCluster = 8;
+
+__device__ __forceinline__ void bj_blocks(int g, int round, int nblk, int& ba, int& bb) {
+  ba = (g == 0) ? 0 : 1 + add_mod(g - 1, round, nblk - 1);
+  bb = 1 + add_mod(nblk - 2 - g, round, nblk - 1);
+}
+
+template <int NCH>
+__global__ void __launch_bounds__(kBJThreads) k_block_jacobi_cl(int r, int cpad, int w, float* __restrict__ M,
+                                                                int ldm, float* __restrict__ V, int ldv,
+                                                                float tol, int max_sweeps,
+                                                                int* __restrict__ sweeps_out,
+                                                                const float* __restrict__ floor_ptr) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int w2 = 2 * w;
+  const int rp = (r + 3) & ~3, cp4 = (cpad + 3) & ~3;
+  const int ldq = (w2 + 7) & ~3;
+  float* Mb = reinterpret_cast<float*>(smem_raw);
+  float* Vb = Mb + 2 * (size_t)w2 * rp;
+  float* Qs = Vb + 2 * (size_t)w2 * cp4;
+  float* nrm = Qs + w2 * ldq;
+  __shared__ int s_rot;
+  __shared__ int rotf[2][kBJMaxCluster];  // per-CTA "rotated" flags, by sweep parity
+  const int P = (int)cl.num_blocks(), g = (int)cl.block_rank(), nblk = 2 * P;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kBJThreads / 32;
+  const float nfloor = floor_ptr ? *floor_ptr : 0.f;
+  const float tol2 = tol * tol;
+  int ba, bb;
+  bj_blocks(g, 0, nblk, ba, bb);
+  // round 0's blocks into buffer 0
+  for (int l = warp; l < w2; l += nw) {
+    const int gc = (l < w ? ba * w + l : bb * w + (l - w));
+    const float* src = M + (size_t)gc * ldm;
+    float* dst = Mb + (size_t)l * rp;
+    for (int i = lane; i < rp; i += 32) dst[i] = i < r ? src[i] : 0.f;
+    const float* vsrc = V + (size_t)gc * ldv;
+    float* vdst = Vb + (size_t)l * cp4;
+    for (int i = lane; i < cp4; i += 32) vdst[i] = i < cpad ? vsrc[i] : 0.f;
+  }
+  __syncthreads();
+  int buf = 0, sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) s_rot = 0;
+    for (int round = 0; round < nblk - 1; ++round) {
+      bj_blocks(g, round, nblk, ba, bb);
+      float* Ms = Mb + (size_t)buf * w2 * rp;
+      float* Vs = Vb + (size_t)buf * w2 * cp4;
+      // squared norms of the 2w columns; Q = I
+      for (int l = warp; l < w2; l += nw) {
+        const float4* col = reinterpret_cast<const float4*>(Ms + (size_t)l * rp);
+        float s2 = 0.f;
+        for (int c = lane; c < (rp >> 2); c += 32) {
+          const float4 v = col[c];
+          s2 = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, s2))));
+        }
+        s2 = warp_sum(s2);
+        if (lane == 0) nrm[l] = s2;
+      }
+      for (int e = tid; e < w2 * ldq; e += kBJThreads) {
+        const int i = e / ldq, j = e - i * ldq;
+        Qs[e] = (i == j) ? 1.f : 0.f;
+      }
+      __syncthreads();
+      bj_round<NCH>(round, w, rp, Ms, Qs, ldq, nrm, nfloor, tol2, &s_rot);
+      __syncthreads();
+      // where this CTA's blocks go next (round 0 of the next sweep after the last round)
+      const int nr = (round + 1 == nblk - 1) ? 0 : round + 1;
+      int dst_cta[2], dst_slot[2];
+      {
+        const int mine[2] = {ba, bb};
+        for (int s = 0; s < 2; ++s) {
+          dst_cta[s] = 0;
+          dst_slot[s] = 0;
+          for (int q = 0; q < P; ++q) {
+            int qa, qb;
+            bj_blocks(q, nr, nblk, qa, qb);
+            if (qa == mine[s]) { dst_cta[s] = q; dst_slot[s] = 0; }
+            if (qb == mine[s]) { dst_cta[s] = q; dst_slot[s] = 1; }
+          }
+        }
+      }
+      float* Mn = Mb + (size_t)(buf ^ 1) * w2 * rp;
+      float* Vn = Vb + (size_t)(buf ^ 1) * w2 * cp4;
+      // M columns: copy into the receivers' next buffer
+      {
+        const int rch = rp >> 2;
+        for (int e = tid; e < w2 * rch; e += kBJThreads) {
+          const int l = e / rch, ch = e - l * rch, s = l < w ? 0 : 1, li = l - s * w;
+          float4* dst = reinterpret_cast<float4*>(
+              cl.map_shared_rank(Mn + (size_t)(dst_slot[s] * w + li) * rp, dst_cta[s]));
+          dst[ch] = reinterpret_cast<const float4*>(Ms + (size_t)l * rp)[ch];
+        }
+      }
+      // V columns: V_blk Q into the receivers' next buffer
+      {
+        const int vch = cp4 >> 2, ngrp = (w2 + 3) >> 2;
+        for (int e = tid; e < vch * ngrp; e += kBJThreads) {
+          const int ch = e % vch, c0 = (e / vch) * 4;
+          float4 acc[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+          for (int k2 = 0; k2 < w2; ++k2) {
+            const float4 v = reinterpret_cast<const float4*>(Vs + (size_t)k2 * cp4)[ch];
+            const float4 qv = *reinterpret_cast<const float4*>(Qs + k2 * ldq + c0);
+            const float qq[4] = {qv.x, qv.y, qv.z, qv.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              acc[j].x = fmaf(v.x, qq[j], acc[j].x);
+              acc[j].y = fmaf(v.y, qq[j], acc[j].y);
+              acc[j].z = fmaf(v.z, qq[j], acc[j].z);
+              acc[j].w = fmaf(v.w, qq[j], acc[j].w);
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int l = c0 + j;
+            if (l < w2) {
+              const int s = l < w ? 0 : 1, li = l - s * w;
+              float4* dst = reinterpret_cast<float4*>(
+                  cl.map_shared_rank(Vn + (size_t)(dst_slot[s] * w + li) * cp4, dst_cta[s]));
+              dst[ch] = acc[j];
+            }
+          }
+        }
+      }
+      if (round == nblk - 2 && tid < P) *cl.map_shared_rank(&rotf[sweep & 1][g], tid) = s_rot;
+      cl.sync();
+      buf ^= 1;
+    }
+    int any = 0;
+    for (int q = 0; q < P; ++q) any |= rotf[sweep & 1][q];
+    if (!any) break;
+  }
+  // the current buffer holds round 0's blocks
+  __syncthreads();
+  bj_blocks(g, 0, nblk, ba, bb);
+  const float* Ms = Mb + (size_t)buf * w2 * rp;
+  const float* Vs = Vb + (size_t)buf * w2 * cp4;
+  for (int l = warp; l < w2; l += nw) {
+    const int gc = (l < w ? ba * w + l : bb * w + (l - w));
+    float* dst = M + (size_t)gc * ldm;
+    for (int i = lane; i < r; i += 32) dst[i] = Ms[(size_t)l * rp + i];
+    float* vdst = V + (size_t)gc * ldv;
+    for (int i = lane; i < cpad; i += 32) vdst[i] = Vs[(size_t)l * cp4 + i];
   }
   if (g == 0 && tid == 0 && sweeps_out) *sweeps_out = sweep;
 }
@@ -1028,13 +1179,46 @@ __global__ void k_colnorm_floor(int r, int c, const T* __restrict__ M, int ldm, 
 static size_t bj_smem(int r, int cpad, int w) {
   const size_t rp = (r + 3) & ~3, cp4 = (cpad + 3) & ~3;
   const size_t ldq = (2 * w + 7) & ~3;
-  return ((size_t)2 * w * (rp + cp4) + (size_t)2 * w * ldq + 2 * w + 3 * (size_t)w) * sizeof(float);
+  return ((size_t)2 * w * (rp + cp4) + (size_t)2 * w * ldq + 2 * (size_t)w) * sizeof(float);
+}
+
+static size_t bj_cl_smem(int r, int cpad, int w) {
+  const size_t rp = (r + 3) & ~3, cp4 = (cpad + 3) & ~3;
+  const size_t ldq = (2 * w + 7) & ~3;
+  return ((size_t)4 * w * (rp + cp4) + (size_t)2 * w * ldq + 2 * (size_t)w) * sizeof(float);
 }
 
 static rr_status launch_bj(cudaStream_t s, int r, int cpad, int w, int P, float* M, float* V, float tol,
                            int max_sweeps, PencilWs& ws, const float* floor_ptr = nullptr) {
   const int rp = (r + 3) & ~3;
   if (rp > 128 * kBJMaxChunks || cpad > 128 * kBJMaxChunks || 2 * w > 32 || w < 1) return RR_ERR_ARG;
+  const size_t csm = bj_cl_smem(r, cpad, w);
+  if (P <= kBJMaxCluster && csm <= 220 * 1024) {
+    // one cluster: columns stay in shared memory, no global barrier
+    const void* fn = rp <= 128 ? (const void*)k_block_jacobi_cl<1>
+                     : rp <= 256 ? (const void*)k_block_jacobi_cl<2>
+                                 : (const void*)k_block_jacobi_cl<3>;
+    if (csm > 48 * 1024)
+      RR_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(P);
+    cfg.blockDim = dim3(kBJThreads);
+    cfg.dynamicSmemBytes = csm;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = P;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int ld = r, ldv = cpad;
+    int* sw = ws.sweeps;
+    void* args[] = {&r, &cpad, &w, &M, &ld, &V, &ldv, &tol, &max_sweeps, &sw, &floor_ptr};
+    RR_CUDA(cudaLaunchKernelExC(&cfg, fn, args));
+    note_launches(1);
+    return RR_OK;
+  }
   const size_t smem = bj_smem(r, cpad, w);
   const void* fn = rp <= 128 ? (const void*)k_block_jacobi<1>
                    : rp <= 256 ? (const void*)k_block_jacobi<2>
@@ -1381,21 +1565,27 @@ __device__ __forceinline__ double oa_coupling(const double* K, const double* T, 
 }
 
 // F1 = I + (I - T)/2 + W, W the exact pair angles outside the clusters
-// (cid: cluster ids, -1 none); within a cluster only the orthogonality part
+// (cid: cluster ids, -1 none); within a cluster only the orthogonality part.
+// W itself goes to Wout: the caller adds W^2 / 2, so that I + W + W^2 / 2
+// (exp(W) to second order) is orthogonal up to W^4 / 4 — with I + W alone
+// the rotations' own W^2 defect (up to c kBigAngle^2) would have to be
+// squared away by the following steps.
 __global__ void k_oa_update(int c, const double* __restrict__ K, const double* __restrict__ T,
-                            const int* __restrict__ cid, double* __restrict__ F1) {
+                            const int* __restrict__ cid, double* __restrict__ F1, double* __restrict__ Wout) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= c * c) return;
   const int i = e % c, j = e / c;
   const double Tij = T[e];
   double f = (i == j) ? 1.0 + 0.5 * (1.0 - Tij) : -0.5 * Tij;
+  double wij = 0.0;
   if (i != j && !(cid[i] >= 0 && cid[i] == cid[j])) {
     const double li = K[i + (size_t)i * c] / T[i + (size_t)i * c];
     const double lj = K[j + (size_t)j * c] / T[j + (size_t)j * c];
     const double cij = oa_coupling(K, T, c, i, j, li, lj);
-    if (fabs(cij) > kCoupleNoise * fmax(fabs(li), fabs(lj))) f += 0.5 * atan(2.0 * cij / (lj - li));
+    if (fabs(cij) > kCoupleNoise * fmax(fabs(li), fabs(lj))) wij = 0.5 * atan(2.0 * cij / (lj - li));
   }
-  F1[e] = f;
+  F1[e] = f + wij;
+  Wout[e] = wij;
 }
 
 // Cluster detection and resolution (one CTA).  Sorted by lam, a pair
@@ -1413,7 +1603,8 @@ __global__ void __launch_bounds__(1024) k_cluster_rot(int c, const double* __res
                                                       double* __restrict__ Qb, int* __restrict__ cid,
                                                       int* __restrict__ ord, int* __restrict__ st) {
   extern __shared__ double cl_smem[];
-  double* lam = cl_smem;                                       // [c]
+  double* Sw = cl_smem;                                        // [kClWarps][kClMax][kClMax + 1]
+  double* lam = Sw + kClWarps * kClMax * (kClMax + 1);         // [c]
   float* Bw = reinterpret_cast<float*>(lam + c);               // [kClWarps][kClMax][kClMax + 1]
   float* Qw = Bw + kClWarps * kClMax * (kClMax + 1);
   float* lamf = Qw + kClWarps * kClMax * (kClMax + 1);         // [c]
@@ -1529,8 +1720,24 @@ __global__ void __launch_bounds__(1024) k_cluster_rot(int c, const double* __res
           __syncwarp();
         }
     }
-    for (int a = 0; a < m; ++a)
-      if (lane < m) Qb[order[k0 + a] + (size_t)order[k0 + lane] * c] = (double)Q[a * ld + lane];
+    // FP64 polish of the FP32 rotation, Q <- Q (I - E/2) with E = Q^T Q - I
+    // (a Newton-Schulz step): its orthogonality defect (FP32 rounding times
+    // the rotation's size) squares, so a cluster rotation taken in the last
+    // refinement step leaves V orthogonal to FP64 accuracy
+    double* S = Sw + (size_t)warp * kClMax * (kClMax + 1);
+    if (lane < m)
+      for (int a = 0; a < m; ++a) {
+        double e = (a == lane) ? -1.0 : 0.0;
+        for (int k = 0; k < m; ++k) e = fma((double)Q[k * ld + a], (double)Q[k * ld + lane], e);
+        S[a * ld + lane] = e;
+      }
+    __syncwarp();
+    if (lane < m)
+      for (int k = 0; k < m; ++k) {
+        double acc = 0.0;
+        for (int a = 0; a < m; ++a) acc = fma((double)Q[k * ld + a], S[a * ld + lane], acc);
+        Qb[order[k0 + k] + (size_t)order[k0 + lane] * c] = (double)Q[k * ld + lane] - 0.5 * acc;
+      }
     __syncwarp();
   }
 }
@@ -1557,8 +1764,8 @@ __global__ void k_block_apply(int c, const double* __restrict__ F1, const double
 }
 
 static size_t cluster_smem(int c) {
-  return (size_t)c * sizeof(double) + (2 * (size_t)kClWarps * kClMax * (kClMax + 1) + c) * sizeof(float) +
-         (4 * (size_t)c + 2) * sizeof(int);
+  return ((size_t)kClWarps * kClMax * (kClMax + 1) + c) * sizeof(double) +
+         (2 * (size_t)kClWarps * kClMax * (kClMax + 1) + c) * sizeof(float) + (4 * (size_t)c + 2) * sizeof(int);
 }
 
 // SVD of the r x c matrix C (FP64, ld r): on exit Mout (r x c) = C V with
@@ -1576,7 +1783,8 @@ static rr_status jacobi_svd(cudaStream_t s, int r, int c, const double* C, Penci
   // FP32 copy scaled by a power of two to max entry in [1/2, 1): squared
   // column norms stay well inside the FP32 range
   k_pow2_scale<<<1, 1024, 0, s>>>(r, c, C, r, w.fs + 1);
-  if (qr_precond_applies(r, c)) {
+  const bool qr = qr_precond_applies(r, c);
+  if (qr) {
     // Jacobi on s C Q with V starting at Q (C^T P = Q R)
     RR_TRY(launch_qr_precond(s, r, c, C, w.fs + 1, w.M32, cpad, w.V32, w.Hq, w.tq));
   } else {
@@ -1594,7 +1802,8 @@ static rr_status jacobi_svd(cudaStream_t s, int r, int c, const double* C, Penci
     gemm_small(s, 1, 0, c, c, r, 1.0, w.Mp, r, w.Mp, r, 0.0, w.E2, c);      // K = N^T N
     gemm_small(s, 1, 0, c, c, c, 1.0, w.V, c, w.V, c, 0.0, w.T, c);         // T = V^T V
     k_cluster_rot<<<1, 1024, csm, s>>>(c, w.E2, w.T, w.F, w.cid, w.order, w.cst);  // Qb
-    k_oa_update<<<gc, 256, 0, s>>>(c, w.E2, w.T, w.cid, w.Vp);              // F1
+    k_oa_update<<<gc, 256, 0, s>>>(c, w.E2, w.T, w.cid, w.Vp, w.E);         // F1, W
+    gemm_mixed(s, 0, 0, c, c, c, 0.5, w.E, c, w.E, c, 1.0, w.Vp, c);        // F1 += W^2 / 2
     // V <- V (I + (I - T)/2 + W) Qb: orthogonalise, the small pair rotations,
     // then the clusters' rotations
     k_block_apply<<<gc, 256, 0, s>>>(c, w.Vp, w.F, w.cid, w.order, w.cst, w.T);  // F = F1 Qb
@@ -1604,8 +1813,10 @@ static rr_status jacobi_svd(cudaStream_t s, int r, int c, const double* C, Penci
   gemm_small(s, 0, 0, r, c, c, 1.0, C, r, w.V, c, 0.0, Mout, r);            // M = C V
   if (Vout != w.V)
     RR_CUDA(cudaMemcpyAsync(Vout, w.V, (size_t)c * c * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  // 5 setup kernels, 4 x 7 refinement kernels, the final product (in check_launch)
-  note_launches(33);
+  // setup (scale, pad copy unless the QR preconditioner ran, norm floor, V to
+  // FP64; the QR and Jacobi launchers count their own), 4 x 8 refinement
+  // kernels, the final product (in check_launch)
+  note_launches((qr ? 3 : 4) + 32);
   return check_launch("jacobi_svd");
 }
 
