@@ -430,6 +430,14 @@ def run_stage(args):
         Xl = rr.fortran((Xf - Xh.float()).to(torch.bfloat16))
         for _ in range(2):
             rr.rr_gemm_lowp_split(M, B, N, Ah, Al, N, Xh, Xl, N)
+    elif args.stage == "prep":
+        A = torch.randn(N, M, device="cuda", dtype=torch.float64).t()   # M x N column-major
+        X = rr.fortran(torch.randn(N, B, device="cuda", dtype=torch.float64))
+        Y = rr.fortran(torch.randn(M, B, device="cuda", dtype=torch.float64))
+        for _ in range(2):
+            rr.rr_split_operator(A)                  # BF16 hi / lo, both layouts
+            rr.rr_gemm_f64_emulated(0, A, X)         # row-scaled slices (+ products)
+            rr.rr_gemm_f64_emulated(1, A, Y)         # column-scaled slices (+ products)
     elif args.stage in ("gemm", "f64emu"):
         A = torch.randn(N, M, device="cuda", dtype=torch.float64).t()   # M x N column-major
         X = rr.fortran(torch.randn(N, B, device="cuda", dtype=torch.float64))
@@ -453,7 +461,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--stage", choices=["pencil", "hessenberg", "gemm", "split", "f64emu"],
+    ap.add_argument("--stage", choices=["pencil", "hessenberg", "gemm", "split", "f64emu", "prep"],
                     help="run one stage of the workload (profiling driver)")
     ap.add_argument("--b", type=int, default=256, help="pencil size for --stage pencil")
     args = ap.parse_args()

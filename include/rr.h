@@ -172,6 +172,16 @@ rr_status rr_colscale_cast(int64_t rows, int64_t cols, const double* X, int64_t 
 rr_status rr_cast_operator(int64_t m, int64_t n, const double* A, int64_t lda, int32_t dtype,
                            void* out_col, void* out_row, void* stream);
 
+/* Split BF16 copy of a dense FP64 m x n operator, for the FP32-accurate
+ * correction products of the refinement phase: hi = bf16(A) and
+ * lo = bf16(A - hi), both rounded to nearest even (A - hi is exact in FP64),
+ * so hi + lo carries about 16 significant bits of A.  Each of hi_col / lo_col
+ * (column-major, ld m) and hi_row / lo_row (row-major: element (i,j) at
+ * [i*n + j], the K-major operand of A * V) may be NULL.  One pass over A.
+ * RR_ERR_ARG: m, n < 0, lda < m, or A NULL. */
+rr_status rr_split_operator(int64_t m, int64_t n, const double* A, int64_t lda, void* hi_col,
+                            void* hi_row, void* lo_col, void* lo_row, void* stream);
+
 /* Low-precision block product (Eq. of Sec. 2, X_iter = A X; Fig. 4 "W = AV"):
  * C (M x N, FP32, ld ldc) = A_k^T * B + coef[j] * R(:,j)
  * where A_k is the K x M operand stored K-contiguous (element (kk,i) at

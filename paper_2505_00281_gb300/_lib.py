@@ -60,6 +60,7 @@ _SIGS = {
                              c_sz, c_i32p, ctypes.POINTER(RrInfo), c_vp]),
     "rr_colscale_cast": (c_i32, [c_i64, c_i64, c_vp, c_i64, c_i32, c_vp, c_i64, c_vp, c_vp]),
     "rr_cast_operator": (c_i32, [c_i64, c_i64, c_vp, c_i64, c_i32, c_vp, c_vp, c_vp]),
+    "rr_split_operator": (c_i32, [c_i64, c_i64, c_vp, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "rr_gemm_lowp": (c_i32, [c_i32, c_i64, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp,
                              c_i64, c_vp, c_vp]),
     "rr_gemm_lowp_split": (c_i32, [c_i64, c_i64, c_i64, c_vp, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp, c_i64,

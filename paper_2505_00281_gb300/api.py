@@ -14,7 +14,7 @@ from ._lib import RR, RrError, RrInfo, RrOperator, RrParams, check, lib
 
 __all__ = [
     "fortran", "ld_of", "dense_operator", "csr_operator", "make_params", "rr_eig", "rr_svd",
-    "rr_batch_svd", "rr_colscale_cast", "rr_cast_operator", "rr_gemm_lowp", "rr_gemm_f64",
+    "rr_batch_svd", "rr_colscale_cast", "rr_cast_operator", "rr_split_operator", "rr_gemm_lowp", "rr_gemm_f64",
     "rr_hessenberg", "rr_gram", "rr_gram_noalloc", "rr_pencil_eig", "rr_pencil_svd", "rr_csr_spmm",
     "rr_chebyshev_step", "RrParams", "RrOperator", "RrInfo", "DTYPES",
 ]
@@ -176,6 +176,18 @@ def rr_cast_operator(A, dtype, row_copy=True, stream=None):
     check("rr_cast_operator", lib().rr_cast_operator(m, n, _p(A), ld_of(A), DTYPES[dtype], _p(col),
                                                       _p(row), _stream(stream)))
     return col, row
+
+
+def rr_split_operator(A, row_copy=True, stream=None):
+    """hi = bf16(A), lo = bf16(A - hi): (hi_col, hi_row, lo_col, lo_row); row copies flat or None."""
+    m, n = A.shape
+    hc = fortran(torch.empty(m, n, dtype=torch.bfloat16, device=A.device))
+    lc = fortran(torch.empty(m, n, dtype=torch.bfloat16, device=A.device))
+    hr = torch.empty(m * n, dtype=torch.bfloat16, device=A.device) if row_copy else None
+    lr = torch.empty(m * n, dtype=torch.bfloat16, device=A.device) if row_copy else None
+    check("rr_split_operator", lib().rr_split_operator(m, n, _p(A), ld_of(A), _p(hc), _p(hr), _p(lc), _p(lr),
+                                                        _stream(stream)))
+    return hc, hr, lc, lr
 
 
 def rr_gemm_lowp(dtype, M, N, K, A_k, lda, B, ldb, C=None, R=None, coef=None, stream=None):

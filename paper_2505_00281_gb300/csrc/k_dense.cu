@@ -168,7 +168,9 @@ extern "C" rr_status rr_cast_operator(int64_t m, int64_t n, const double* A, int
   cudaStream_t s = as_stream(stream);
   switch (dtype) {
     case RR_F32: k_cast_operator<float><<<g, b, 0, s>>>(m, n, A, lda, (float*)out_col, (float*)out_row); break;
-    case RR_BF16: k_cast_operator<__nv_bfloat16><<<g, b, 0, s>>>(m, n, A, lda, (__nv_bfloat16*)out_col, (__nv_bfloat16*)out_row); break;
+    case RR_BF16:
+      return op_prepare(s, A, m, n, lda, (__nv_bfloat16*)out_col, (__nv_bfloat16*)out_row, nullptr, nullptr, 0,
+                        nullptr, nullptr, false, false);
     case RR_F64: k_cast_operator<double><<<g, b, 0, s>>>(m, n, A, lda, (double*)out_col, (double*)out_row); break;
     default: return RR_ERR_ARG;
   }

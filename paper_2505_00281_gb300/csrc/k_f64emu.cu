@@ -79,8 +79,10 @@ __device__ __forceinline__ void slice_value(double x, int e, int S, float* out) 
     if (sh >= 0) F = (long long)(M << sh);
     else if (sh > -63) F = (long long)((M + (1ull << (-sh - 1))) >> (-sh));
   }
+  // digits in 32-bit integers (a 64-bit integer to float conversion is not
+  // a full-rate instruction)
   for (int p = S - 1; p >= 1; --p) {
-    long long d = F & 63;
+    int d = (int)(F & 63);
     F >>= 6;
     if (d >= 32) {
       d -= 64;
@@ -88,9 +90,253 @@ __device__ __forceinline__ void slice_value(double x, int e, int S, float* out) 
     }
     out[p] = (float)d;
   }
-  out[0] = (float)F;
+  out[0] = (float)(int)F;
   if (u >> 63)
     for (int p = 0; p < S; ++p) out[p] = -out[p];
+}
+
+// BF16 bits of a small integer-valued float (|v| <= 256: exact)
+__device__ __forceinline__ unsigned bf16_bits_exact(float v) { return __float_as_uint(v) >> 16; }
+
+// BF16 bits (sign excluded) of v = k 2^s (0 < k < 2^62) rounded the way an
+// FP64 value is cast to BF16 here: to FP32 (nearest even), then the FP32
+// pattern to BF16 (nearest even; a carry may reach the exponent).  Integer
+// operations only (this GPU has few FP64 units).  False when the FP32
+// rounding is not a normal number (the caller then uses the conversion
+// instructions).
+__device__ __forceinline__ bool bf16_of_scaled(unsigned long long k, int s, unsigned& out) {
+  int msb = 63 - __clzll((long long)k);
+  unsigned long long k24;
+  if (msb > 23) {
+    const int sh = msb - 23;
+    k24 = k >> sh;
+    const unsigned long long rem = k & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (k24 & 1ull))) ++k24;
+    if (k24 == (1ull << 24)) {
+      k24 >>= 1;
+      ++msb;
+    }
+  } else {
+    k24 = k << (23 - msb);
+  }
+  const int e32 = msb + s + 127;  // v rounded = (k24 / 2^23) 2^(msb + s)
+  if (e32 < 1 || e32 > 254) return false;
+  const unsigned f = ((unsigned)e32 << 23) | (unsigned)(k24 & 0x7FFFFFull);
+  out = (f + 0x7FFFu + ((f >> 16) & 1u)) >> 16;
+  return true;
+}
+
+// hi = bf16(a) and lo = bf16(a - hi) with the cast above (a - hi is exact
+// in FP64), as BF16 bit patterns.
+__device__ __forceinline__ void bf16_split_bits(double a, unsigned& hi, unsigned& lo) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(a);
+  const unsigned sgn = (unsigned)(u >> 63);
+  const int E = (int)((u >> 52) & 0x7FF);
+  const unsigned long long M = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);  // a = M 2^(E - 1075)
+  unsigned hb, lb;
+  if (E == 0 || E == 0x7FF || !bf16_of_scaled(M, E - 1075, hb)) {
+    const __nv_bfloat16 h = __float2bfloat16_rn((float)a);
+    hi = __bfloat16_as_ushort(h);
+    lo = __bfloat16_as_ushort(__float2bfloat16_rn((float)(a - (double)__bfloat162float(h))));
+    return;
+  }
+  hi = (sgn << 15) | hb;
+  // hi in units of a's last place: (128 + m7) 2^(e8 - 134 - (E - 1075))
+  const int e8 = (int)(hb >> 7), sh = e8 + 941 - E;  // 45, or 46 after a carry
+  const long long d = (long long)M - (long long)((128ull + (hb & 127u)) << sh);
+  if (d == 0) {
+    lo = 0;
+    return;
+  }
+  if (!bf16_of_scaled((unsigned long long)(d < 0 ? -d : d), E - 1075, lb)) {
+    const double hv = (double)__bfloat162float(__ushort_as_bfloat16((unsigned short)hi));
+    lo = __bfloat16_as_ushort(__float2bfloat16_rn((float)(a - hv)));
+    return;
+  }
+  lo = ((sgn ^ (d < 0 ? 1u : 0u)) << 15) | lb;
+}
+
+// hi only (the same cast)
+__device__ __forceinline__ unsigned bf16_bits_of(double a) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(a);
+  const int E = (int)((u >> 52) & 0x7FF);
+  unsigned hb;
+  if (E == 0 || E == 0x7FF || !bf16_of_scaled((u & 0xFFFFFFFFFFFFFull) | (1ull << 52), E - 1075, hb))
+    return __bfloat16_as_ushort(__float2bfloat16_rn((float)a));
+  return ((unsigned)(u >> 63) << 15) | hb;
+}
+
+constexpr int kExpNone = -1100;  // exponent of zero (below every finite one)
+
+__global__ void k_exp_init(int64_t count, int* __restrict__ e) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    e[i] = kExpNone;
+}
+
+// First pass over a dense FP64 operator (m x n, column-major): the BF16 hi /
+// lo split in column-major and row-major copies, and the exponents of the
+// largest entry of every row and column (atomic max into rexp / cexp, which
+// start at kExpNone).  Every output may be null.  A block takes a 32-row x
+// 256-column tile, a warp 32 x 32 (lane = row): column loads are coalesced,
+// a lane writes its row's 32 entries of the row-major copies as four 16-byte
+// stores.
+__global__ void __launch_bounds__(256) k_op_pass1(int64_t m, int64_t n, const double* __restrict__ A, int64_t lda,
+                                                  __nv_bfloat16* __restrict__ hi_col, __nv_bfloat16* __restrict__ hi_row,
+                                                  __nv_bfloat16* __restrict__ lo_col, __nv_bfloat16* __restrict__ lo_row,
+                                                  int* __restrict__ rexp, int* __restrict__ cexp) {
+  __shared__ int rmax[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t i = (int64_t)blockIdx.x * 32 + lane;
+  const int64_t jw = (int64_t)blockIdx.y * 256 + warp * 32;
+  const bool rv = i < m;
+  const bool need_lo = lo_col || lo_row;
+  int emx = kExpNone;
+  unsigned hp[16], lp[16];
+  double av[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    const int64_t j = jw + c;
+    av[c] = (rv && j < n) ? A[i + j * lda] : 0.0;
+  }
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    const int64_t j = jw + c;
+    const double a = av[c];
+    const unsigned long long u = (unsigned long long)__double_as_longlong(a);
+    const int E = (int)((u >> 52) & 0x7FF);
+    const int e = E == 0 ? kExpNone : E - 1022;
+    emx = max(emx, e);
+    if (cexp) {
+      int ce = e;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) ce = max(ce, __shfl_xor_sync(0xffffffffu, ce, o));
+      if (lane == 0 && j < n) atomicMax(cexp + j, ce);
+    }
+    unsigned h = 0, l = 0;
+    if (need_lo) {
+      bf16_split_bits(a, h, l);
+    } else {
+      h = bf16_bits_of(a);
+    }
+    if (c & 1) {
+      hp[c >> 1] |= h << 16;
+      lp[c >> 1] |= l << 16;
+    } else {
+      hp[c >> 1] = h;
+      lp[c >> 1] = l;
+    }
+    if (rv && j < n) {
+      if (hi_col) hi_col[i + j * m] = __ushort_as_bfloat16((unsigned short)h);
+      if (lo_col) lo_col[i + j * m] = __ushort_as_bfloat16((unsigned short)l);
+    }
+  }
+  if (rv) {
+    const bool vec = (jw + 32 <= n) && (n % 8 == 0);
+    if (hi_row) {
+      if (vec) {
+        uint4* dst = reinterpret_cast<uint4*>(hi_row + i * n + jw);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dst[k] = make_uint4(hp[4 * k], hp[4 * k + 1], hp[4 * k + 2], hp[4 * k + 3]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+          if (jw + c < n) hi_row[i * n + jw + c] = __ushort_as_bfloat16((unsigned short)(hp[c >> 1] >> (16 * (c & 1))));
+      }
+    }
+    if (lo_row) {
+      if (vec) {
+        uint4* dst = reinterpret_cast<uint4*>(lo_row + i * n + jw);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dst[k] = make_uint4(lp[4 * k], lp[4 * k + 1], lp[4 * k + 2], lp[4 * k + 3]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+          if (jw + c < n) lo_row[i * n + jw + c] = __ushort_as_bfloat16((unsigned short)(lp[c >> 1] >> (16 * (c & 1))));
+      }
+    }
+  }
+  if (rexp) {
+    rmax[warp][lane] = emx;
+    __syncthreads();
+    if (warp == 0 && rv) {
+      int r = rmax[0][lane];
+#pragma unroll
+      for (int w = 1; w < 8; ++w) r = max(r, rmax[w][lane]);
+      atomicMax(rexp + i, r);
+    }
+  }
+}
+
+// Second pass: the S slices of every entry, row-scaled (2^rexp[i], written
+// row-major: element (i, j) of slice p at rows[p m n + i n + j]) and / or
+// column-scaled (2^cexp[j], column-major: cols[p m n + i + j m]).  Same
+// tiling as the first pass; a lane packs 8 consecutive row-major digits of
+// each slice into one 16-byte store.
+template <int S>
+__global__ void __launch_bounds__(256, 2) k_op_slices(int64_t m, int64_t n, const double* __restrict__ A, int64_t lda,
+                                                   const int* __restrict__ rexp, const int* __restrict__ cexp,
+                                                   __nv_bfloat16* __restrict__ rows, __nv_bfloat16* __restrict__ cols) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t i = (int64_t)blockIdx.x * 32 + lane;
+  const int64_t jw = (int64_t)blockIdx.y * 256 + warp * 32;
+  const bool rv = i < m;
+  const int er = (rows && rv) ? rexp[i] : 0;
+  const size_t plane = (size_t)m * n;
+  const bool vec = (n % 8 == 0);
+#pragma unroll 1
+  for (int g = 0; g < 4; ++g) {
+    const int64_t j0 = jw + 8 * g;
+    double av[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) av[c] = (rv && j0 + c < n) ? A[i + (j0 + c) * lda] : 0.0;
+    if (rows) {
+      unsigned pk[S][4];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        float sl[S];
+        slice_value(av[c], er, S, sl);
+#pragma unroll
+        for (int p = 0; p < S; ++p) {
+          const unsigned b = bf16_bits_exact(sl[p]);
+          if (c & 1) pk[p][c >> 1] |= b << 16;
+          else pk[p][c >> 1] = b;
+        }
+      }
+      if (rv && j0 < n) {
+        if (vec && j0 + 8 <= n) {
+#pragma unroll
+          for (int p = 0; p < S; ++p)
+            *reinterpret_cast<uint4*>(rows + (size_t)p * plane + i * n + j0) =
+                make_uint4(pk[p][0], pk[p][1], pk[p][2], pk[p][3]);
+        } else {
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            if (j0 + c < n) {
+#pragma unroll
+              for (int p = 0; p < S; ++p)
+                rows[(size_t)p * plane + i * n + j0 + c] =
+                    __ushort_as_bfloat16((unsigned short)(pk[p][c >> 1] >> (16 * (c & 1))));
+            }
+        }
+      }
+    }
+    if (cols) {
+      // the column-scaled digits re-read the entries (cache hits), which
+      // keeps the loop rolled and the register count low
+#pragma unroll 1
+      for (int c = 0; c < 8; ++c) {
+        const int64_t j = j0 + c;
+        if (j >= n) break;
+        float sl[S];
+        slice_value(rv ? A[i + j * lda] : 0.0, cexp[j], S, sl);
+        if (rv) {
+#pragma unroll
+          for (int p = 0; p < S; ++p)
+            cols[(size_t)p * plane + i + j * m] = __ushort_as_bfloat16((unsigned short)bf16_bits_exact(sl[p]));
+        }
+      }
+    }
+  }
 }
 
 // column-scaled slices, same layout as the input: out[p] (m x n, ld m)
@@ -148,11 +394,56 @@ size_t emu_block_bytes(int64_t K, int64_t N, int S) {
   return align_up((size_t)S * K * N * 2) + align_up((size_t)N * 4);
 }
 
+// All preparation of a dense FP64 operator in two passes over A: BF16 hi / lo
+// copies (any of the four may be null) and, when emu is given, the slices
+// for FP64-accurate products (row-scaled row-major for A X, column-scaled
+// column-major for A^T Y) in emu_mem.
+rr_status op_prepare(cudaStream_t s, const double* A, int64_t m, int64_t n, int64_t lda,
+                     __nv_bfloat16* hi_col, __nv_bfloat16* hi_row, __nv_bfloat16* lo_col, __nv_bfloat16* lo_row,
+                     int S, EmuOperator* emu, void* emu_mem, bool rows, bool cols) {
+  if (m <= 0 || n <= 0) return RR_OK;
+  int *rexp = nullptr, *cexp = nullptr;
+  if (emu) {
+    if (S != 8) return RR_ERR_ARG;
+    Arena ar(emu_mem, emu_operator_bytes(m, n, S, rows, cols));
+    emu->m = m;
+    emu->n = n;
+    emu->S = S;
+    emu->rows = nullptr;
+    emu->rexp = nullptr;
+    emu->cols = nullptr;
+    emu->cexp = nullptr;
+    if (rows) {
+      emu->rows = (__nv_bfloat16*)ar.take_bytes((size_t)S * m * n * 2);
+      emu->rexp = rexp = ar.take<int>(m);
+      k_exp_init<<<(unsigned)std::min<int64_t>((m + 255) / 256, 1024), 256, 0, s>>>(m, rexp);
+      note_launches(1);
+    }
+    if (cols) {
+      emu->cols = (__nv_bfloat16*)ar.take_bytes((size_t)S * m * n * 2);
+      emu->cexp = cexp = ar.take<int>(n);
+      k_exp_init<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, s>>>(n, cexp);
+      note_launches(1);
+    }
+  }
+  const dim3 g((unsigned)((m + 31) / 32), (unsigned)((n + 255) / 256));
+  if (hi_col || hi_row || lo_col || lo_row || rexp || cexp) {
+    k_op_pass1<<<g, 256, 0, s>>>(m, n, A, lda, hi_col, hi_row, lo_col, lo_row, rexp, cexp);
+    RR_TRY(check_launch("op_prepare pass 1"));
+  }
+  if (emu && (rows || cols)) {
+    k_op_slices<8><<<g, 256, 0, s>>>(m, n, A, lda, rexp, cexp, emu->rows, emu->cols);
+    RR_TRY(check_launch("op_prepare slices"));
+  }
+  return RR_OK;
+}
+
 // Slice the FP64 operator A (m x n, column-major) once: row-scaled slices
 // (row-major) for A X and/or column-scaled slices (column-major) for A^T Y.
 rr_status emu_prepare(cudaStream_t s, const double* A, int64_t m, int64_t n, int64_t lda, int S,
                       EmuOperator& op, void* mem, bool rows, bool cols) {
   if (S < 1 || S > kMaxSlices) return RR_ERR_ARG;
+  if (S == 8) return op_prepare(s, A, m, n, lda, nullptr, nullptr, nullptr, nullptr, S, &op, mem, rows, cols);
   Arena ar(mem, emu_operator_bytes(m, n, S, rows, cols));
   op.m = m;
   op.n = n;
@@ -344,6 +635,13 @@ rr_status emu_gram(cudaStream_t s, int64_t n, int64_t p, int64_t q, int32_t xt, 
 }  // namespace rr
 
 using namespace rr;
+
+extern "C" rr_status rr_split_operator(int64_t m, int64_t n, const double* A, int64_t lda, void* hi_col,
+                                       void* hi_row, void* lo_col, void* lo_row, void* stream) {
+  if (m < 0 || n < 0 || lda < m || !A) return RR_ERR_ARG;
+  return op_prepare(as_stream(stream), A, m, n, lda, (__nv_bfloat16*)hi_col, (__nv_bfloat16*)hi_row,
+                    (__nv_bfloat16*)lo_col, (__nv_bfloat16*)lo_row, 0, nullptr, nullptr, false, false);
+}
 
 extern "C" size_t rr_gemm_f64_emulated_workspace_size(int32_t trans, int64_t M, int64_t N, int64_t K,
                                                       int32_t slices) {

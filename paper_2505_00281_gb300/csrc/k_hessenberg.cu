@@ -641,16 +641,6 @@ __global__ void __launch_bounds__(kHessThreads) k_hessenberg_f32(
   }
 }
 
-static int hess_grid(int64_t n, size_t smem, const void* fn) {
-  int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kHessThreads, smem);
-  if (occ < 1) occ = 1;
-  int64_t maxg = (int64_t)num_sms() * (occ > 1 ? 1 : occ);  // one CTA per SM
-  int64_t want = (n + 63) / 64;  // at least 64 rows per CTA
-  int64_t g = want < maxg ? want : maxg;
-  return (int)(g < 1 ? 1 : g);
-}
-
 template <typename T>
 static size_t hess_ws_bytes(int64_t k, int G) {
   size_t b = 0;

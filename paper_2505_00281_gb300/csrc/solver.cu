@@ -363,6 +363,14 @@ static void carve_op(Arena& ar, Op& op, bool symmetric, bool refine, int64_t b) 
 
 static rr_status prepare_op(const Op& op_in, Op& op, bool symmetric, cudaStream_t s) {
   (void)op_in;
+  if (op.kind == RR_DENSE && op.dt == RR_BF16 && op.lo_col && (!op.has_emu || kEmuSlices == 8)) {
+    // every copy and slice of the operator from two passes over A
+    return op_prepare(s, op.A, op.m, op.n, op.lda, (__nv_bfloat16*)op.lo_col,
+                      symmetric ? nullptr : (__nv_bfloat16*)op.lo_row,
+                      op.split ? (__nv_bfloat16*)op.lo2_col : nullptr,
+                      op.split && !symmetric ? (__nv_bfloat16*)op.lo2_row : nullptr, kEmuSlices,
+                      op.has_emu ? &op.emu : nullptr, op.emu_mem, true, !symmetric);
+  }
   if (op.lo_col)
     RR_TRY(rr_cast_operator(op.m, op.n, op.A, op.lda, op.dt, op.lo_col, symmetric ? nullptr : op.lo_row, s));
   if (op.split) RR_TRY(cast_operator_lo(op.m, op.n, op.A, op.lda, op.lo2_col, op.lo2_row, s));

@@ -84,6 +84,9 @@ size_t emu_operator_bytes(int64_t m, int64_t n, int S, bool rows, bool cols);
 size_t emu_block_bytes(int64_t K, int64_t N, int S);
 rr_status emu_prepare(cudaStream_t s, const double* A, int64_t m, int64_t n, int64_t lda, int S,
                       EmuOperator& op, void* mem, bool rows, bool cols);
+rr_status op_prepare(cudaStream_t s, const double* A, int64_t m, int64_t n, int64_t lda,
+                     __nv_bfloat16* hi_col, __nv_bfloat16* hi_row, __nv_bfloat16* lo_col, __nv_bfloat16* lo_row,
+                     int S, EmuOperator* emu, void* emu_mem, bool rows, bool cols);
 rr_status emu_gemm(cudaStream_t s, const EmuOperator& op, int trans, int64_t N, const double* X,
                    int64_t ldx, double* C, int64_t ldc, void* mem);
 rr_status vec_scale(cudaStream_t s, int64_t n, double alpha, const double* a, double* d);

@@ -62,6 +62,35 @@ def test_cast_operator_bitexact(rr):
     assert np.array_equal(host(row).reshape(333, 130), ref)   # row-major copy
 
 
+def _bf16_bits_ref(x):
+    return (O.round_bf16(x).astype(np.float32).view(np.uint32) >> 16).astype(np.uint16)
+
+
+def _bf16_bits(t):
+    return t.contiguous().view(torch.int16).cpu().numpy().view(np.uint16)
+
+
+@pytest.mark.parametrize("m,n", [(300, 136), (77, 29)])
+def test_split_operator_bitexact(rr, m, n):
+    """hi = bf16(A), lo = bf16(A - hi) with the oracle's cast (FP64 -> FP32 -> BF16, nearest even
+    both times), bit for bit, column- and row-major: Gaussian entries plus ties at either rounding,
+    signed zeros, wide exponents and remainders below FP32's normal range."""
+    A = wl.gaussian(m, n, 11 + m)
+    t24, t8 = 2.0 ** -24, 2.0 ** -8
+    special = [1 + t8, 1 + 3 * t8, 1 + t8 + t24, 1 + t8 + t24 + 2.0 ** -40, -(1 + t8 + t24), 0.0, -0.0,
+               2.0 ** 100 * (1 + 2.0 ** -9 + 2.0 ** -30), 2.0 ** -120 * (1 + 2.0 ** -9 + 2.0 ** -30),
+               -(2.0 ** -118) * (1 + 2.0 ** -12 + 2.0 ** -33), 1.5 * 2.0 ** -126, 2.0 ** -130, 3.0e38, 1e-300]
+    A[: len(special), 0] = special
+    A[1, 1: 1 + len(special)] = special[: n - 1]
+    hc, hr, lc, lr = rr.rr_split_operator(dev(A))
+    hi = O.round_bf16(A)
+    hb, lb = _bf16_bits_ref(A), _bf16_bits_ref(A - hi)
+    assert np.array_equal(_bf16_bits(hc.t()).reshape(n, m).T, hb)
+    assert np.array_equal(_bf16_bits(lc.t()).reshape(n, m).T, lb)
+    assert np.array_equal(_bf16_bits(hr).reshape(m, n), hb)
+    assert np.array_equal(_bf16_bits(lr).reshape(m, n), lb)
+
+
 # ---------------------------------------------------------------- a2
 @pytest.mark.parametrize("M,N,K", [(300, 40, 700), (128, 128, 4096), (1000, 7, 33),
                                    # tcgen05 path: ragged M, K tail, N padded to 16, K-split
