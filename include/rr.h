@@ -182,6 +182,21 @@ rr_status rr_cast_operator(int64_t m, int64_t n, const double* A, int64_t lda, i
 rr_status rr_split_operator(int64_t m, int64_t n, const double* A, int64_t lda, void* hi_col,
                             void* hi_row, void* lo_col, void* lo_row, void* stream);
 
+/* Ritz lift (Alg. 3 "U~ = U Y"; Alg. 5 lifts both sides), FP64 result:
+ *   X (n x b, ld ldx) = S1 (n x p1, ld ld1) Y(0:p1, :) + S2 (n x p2, ld ld2) Y(p1:p1+p2, :)
+ * with Y FP64 (p1+p2) x b (ld ldy), all column-major; S1, S2 of type t1, t2
+ * (RR_F64, RR_F32 or RR_BF16); S2 may be NULL (p2 ignored).  FP64-accurate:
+ * when p1+p2 is a multiple of 8 and at most 512, b <= 256 and ws holds
+ * rr_lift_workspace_size(n, b, p1+p2) bytes, the product runs on the BF16
+ * tensor cores through error-free 6-bit slices of both operands (per-entry
+ * error below (p1+p2) 2^-47 max_k|S(i,k)| max_k|Y(k,j)|); otherwise in FP64
+ * arithmetic.  RR_ERR_ARG: negative sizes, p1 < 1, b < 1, bad type or NULL
+ * pointers. */
+size_t rr_lift_workspace_size(int64_t n, int64_t b, int64_t K);
+rr_status rr_lift(int64_t n, int64_t b, int32_t t1, const void* S1, int64_t ld1, int64_t p1,
+                  int32_t t2, const void* S2, int64_t ld2, int64_t p2, const double* Y, int64_t ldy,
+                  double* X, int64_t ldx, void* ws, size_t ws_bytes, void* stream);
+
 /* Low-precision block product (Eq. of Sec. 2, X_iter = A X; Fig. 4 "W = AV"):
  * C (M x N, FP32, ld ldc) = A_k^T * B + coef[j] * R(:,j)
  * where A_k is the K x M operand stored K-contiguous (element (kk,i) at

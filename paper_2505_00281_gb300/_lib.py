@@ -61,6 +61,9 @@ _SIGS = {
     "rr_colscale_cast": (c_i32, [c_i64, c_i64, c_vp, c_i64, c_i32, c_vp, c_i64, c_vp, c_vp]),
     "rr_cast_operator": (c_i32, [c_i64, c_i64, c_vp, c_i64, c_i32, c_vp, c_vp, c_vp]),
     "rr_split_operator": (c_i32, [c_i64, c_i64, c_vp, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "rr_lift_workspace_size": (c_sz, [c_i64, c_i64, c_i64]),
+    "rr_lift": (c_i32, [c_i64, c_i64, c_i32, c_vp, c_i64, c_i64, c_i32, c_vp, c_i64, c_i64, c_vp, c_i64, c_vp,
+                        c_i64, c_vp, c_sz, c_vp]),
     "rr_gemm_lowp": (c_i32, [c_i32, c_i64, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp,
                              c_i64, c_vp, c_vp]),
     "rr_gemm_lowp_split": (c_i32, [c_i64, c_i64, c_i64, c_vp, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp, c_i64,

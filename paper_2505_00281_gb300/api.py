@@ -14,7 +14,7 @@ from ._lib import RR, RrError, RrInfo, RrOperator, RrParams, check, lib
 
 __all__ = [
     "fortran", "ld_of", "dense_operator", "csr_operator", "make_params", "rr_eig", "rr_svd",
-    "rr_batch_svd", "rr_colscale_cast", "rr_cast_operator", "rr_split_operator", "rr_gemm_lowp", "rr_gemm_f64",
+    "rr_batch_svd", "rr_colscale_cast", "rr_cast_operator", "rr_split_operator", "rr_lift", "rr_gemm_lowp", "rr_gemm_f64",
     "rr_hessenberg", "rr_gram", "rr_gram_noalloc", "rr_pencil_eig", "rr_pencil_svd", "rr_csr_spmm",
     "rr_chebyshev_step", "RrParams", "RrOperator", "RrInfo", "DTYPES",
 ]
@@ -188,6 +188,21 @@ def rr_split_operator(A, row_copy=True, stream=None):
     check("rr_split_operator", lib().rr_split_operator(m, n, _p(A), ld_of(A), _p(hc), _p(hr), _p(lc), _p(lr),
                                                         _stream(stream)))
     return hc, hr, lc, lr
+
+
+def rr_lift(S1, Y, S2=None, X=None, stream=None):
+    """X = [S1 S2] Y (FP64 result; S1, S2 column-major FP64 / FP32 / BF16, Y FP64)."""
+    n, p1 = S1.shape
+    p2 = S2.shape[1] if S2 is not None else 0
+    b = Y.shape[1]
+    if X is None:
+        X = fortran(torch.empty(n, b, dtype=torch.float64, device=Y.device))
+    L = lib()
+    ws = _ws(L.rr_lift_workspace_size(n, b, p1 + p2), Y.device)
+    check("rr_lift", L.rr_lift(n, b, DTYPES[S1.dtype], _p(S1), ld_of(S1), p1,
+                               DTYPES[S2.dtype] if S2 is not None else 0, _p(S2), ld_of(S2) if S2 is not None else n,
+                               p2, _p(Y), ld_of(Y), _p(X), ld_of(X), _p(ws), ws.numel(), _stream(stream)))
+    return X
 
 
 def rr_gemm_lowp(dtype, M, N, K, A_k, lda, B, ldb, C=None, R=None, coef=None, stream=None):

@@ -518,6 +518,147 @@ rr_status emu_gemm(cudaStream_t s, const EmuOperator& op, int trans, int64_t N, 
 }
 
 // ---------------------------------------------------------------------------
+// FP64-accurate lift X = [S1 S2] Y (Alg. 3 / Alg. 5 "U~ = U Y": the n x K
+// basis, K = p1 + p2 columns from two blocks of any storage type, times the
+// K x b FP64 Ritz coefficients) on the tensor cores.  [S1 S2] is sliced by
+// rows (one exponent per row across both blocks) into A_cat (row-major, row i
+// = the S digit blocks of the row, most significant first), Y by columns into
+// Y_rev (column j = its digit blocks, least significant first).  With K small
+// every product sum of one anti-diagonal p + q = d of slice pairs is exact in
+// FP32 (at most 8 K 2^12 <= 2^24 for K <= 512), so diagonal d is one plain
+// product A_cat(:, 0:(d-1)K) Y_rev((S-d+1)K : S K, :) whose epilogue adds
+// 2^(e_row + e_col - 6d) times it into X: S launches instead of one per pair.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double f32_to_f64_exact(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned E = (u >> 23) & 0xFFu;
+  if (E == 0 || E == 255) return (double)f;  // zero, subnormal, Inf / NaN
+  return __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) |
+                                          ((unsigned long long)(E + 896) << 52) |
+                                          ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+template <typename T> __device__ __forceinline__ double exact_f64(T v);
+template <> __device__ __forceinline__ double exact_f64<double>(double v) { return v; }
+template <> __device__ __forceinline__ double exact_f64<float>(float v) { return f32_to_f64_exact(v); }
+template <> __device__ __forceinline__ double exact_f64<__nv_bfloat16>(__nv_bfloat16 v) {
+  return f32_to_f64_exact(__bfloat162float(v));
+}
+
+// one thread per row (lane = row: the column loads are coalesced); K % 8 == 0
+template <typename T1, typename T2>
+__global__ void __launch_bounds__(64) k_lift_slices(int64_t n, int p1, const T1* __restrict__ S1, int64_t ld1,
+                                                    int p2, const T2* __restrict__ S2, int64_t ld2,
+                                                    int* __restrict__ rexp, __nv_bfloat16* __restrict__ out) {
+  constexpr int S = 8;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int K = p1 + p2;
+  int e = kExpNone;
+  for (int kk = 0; kk < p1; ++kk) e = max(e, exp_bits(exact_f64<T1>(S1[i + kk * ld1])));
+  for (int kk = 0; kk < p2; ++kk) e = max(e, exp_bits(exact_f64<T2>(S2[i + kk * ld2])));
+  rexp[i] = e;
+  __nv_bfloat16* row = out + i * (int64_t)(S * K);
+  for (int k0 = 0; k0 < K; k0 += 8) {
+    unsigned pk[S][4];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int kk = k0 + c;
+      const double x = kk < p1 ? exact_f64<T1>(S1[i + kk * ld1]) : exact_f64<T2>(S2[i + (kk - p1) * ld2]);
+      float sl[S];
+      slice_value(x, e, S, sl);
+#pragma unroll
+      for (int q = 0; q < S; ++q) {
+        const unsigned bb = bf16_bits_exact(sl[q]);
+        if (c & 1) pk[q][c >> 1] |= bb << 16;
+        else pk[q][c >> 1] = bb;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < S; ++q)
+      *reinterpret_cast<uint4*>(row + q * K + k0) = make_uint4(pk[q][0], pk[q][1], pk[q][2], pk[q][3]);
+  }
+}
+
+// Y_rev (S K x b, column-major): column j holds Y(:, j)'s digit blocks,
+// least significant first, scaled by 2^cexp[j]
+__global__ void k_slice_cols_rev(int64_t K, int64_t b, const double* __restrict__ Y, int64_t ldy,
+                                 const int* __restrict__ cexp, __nv_bfloat16* __restrict__ out) {
+  constexpr int S = 8;
+  const int64_t j = blockIdx.y;
+  const int e = cexp[j];
+  for (int64_t kk = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; kk < K; kk += (int64_t)gridDim.x * blockDim.x) {
+    float sl[S];
+    slice_value(Y[kk + j * ldy], e, S, sl);
+#pragma unroll
+    for (int q = 0; q < S; ++q)
+      out[j * (S * K) + (S - 1 - q) * K + kk] = __ushort_as_bfloat16((unsigned short)bf16_bits_exact(sl[q]));
+  }
+}
+
+size_t lift_emu_bytes(int64_t n, int64_t b, int64_t K) {
+  return align_up((size_t)8 * n * K * 2) + align_up((size_t)8 * K * b * 2) + align_up((size_t)n * 4) +
+         align_up((size_t)b * 4) + 256;
+}
+
+template <typename T1>
+static void launch_lift_slices(cudaStream_t s, int64_t n, int p1, const T1* S1, int64_t ld1, int p2, int32_t t2,
+                               const void* S2, int64_t ld2, int* rexp, __nv_bfloat16* out) {
+  const unsigned g = (unsigned)((n + 63) / 64);
+  switch (t2) {
+    case RR_F32:
+      k_lift_slices<T1, float><<<g, 64, 0, s>>>(n, p1, S1, ld1, p2, (const float*)S2, ld2, rexp, out);
+      break;
+    case RR_BF16:
+      k_lift_slices<T1, __nv_bfloat16><<<g, 64, 0, s>>>(n, p1, S1, ld1, p2, (const __nv_bfloat16*)S2, ld2, rexp, out);
+      break;
+    default:
+      k_lift_slices<T1, double><<<g, 64, 0, s>>>(n, p1, S1, ld1, p2, (const double*)S2, ld2, rexp, out);
+      break;
+  }
+}
+
+// X (n x b FP64) = S1 (n x p1, type t1) Y(0:p1, :) + S2 (n x p2, type t2)
+// Y(p1:K, :); *done = false (nothing launched) when the shape is outside the
+// tensor-core path (the caller then lifts in FP64 arithmetic)
+rr_status lift_emu(cudaStream_t s, int64_t n, int64_t b, int32_t t1, const void* S1, int64_t ld1, int64_t p1,
+                   int32_t t2, const void* S2, int64_t ld2, int64_t p2, const double* Y, int64_t ldy, double* X,
+                   int64_t ldx, void* mem, size_t mem_bytes, bool* done) {
+  constexpr int S = 8;
+  *done = false;
+  const int64_t K = p1 + (S2 ? p2 : 0);
+  if (!mem || n <= 0 || b <= 0 || b > 256 || K <= 0 || K % 8 || K > 512 || p1 <= 0) return RR_OK;
+  if (mem_bytes < lift_emu_bytes(n, b, K)) return RR_OK;
+  Arena ar(mem, lift_emu_bytes(n, b, K));
+  __nv_bfloat16* Acat = (__nv_bfloat16*)ar.take_bytes((size_t)S * n * K * 2);
+  __nv_bfloat16* Yrev = (__nv_bfloat16*)ar.take_bytes((size_t)S * K * b * 2);
+  int* rexp = ar.take<int>(n);
+  int* yexp = ar.take<int>(b);
+  if (!gemm_bf16_tc_supported(n, b, (S - 1) * K, S * K, S * K, Acat, Yrev)) return RR_OK;
+  const int ip1 = (int)p1, ip2 = (int)(S2 ? p2 : 0);
+  switch (t1) {
+    case RR_F64: launch_lift_slices<double>(s, n, ip1, (const double*)S1, ld1, ip2, t2, S2, ld2, rexp, Acat); break;
+    case RR_F32: launch_lift_slices<float>(s, n, ip1, (const float*)S1, ld1, ip2, t2, S2, ld2, rexp, Acat); break;
+    case RR_BF16:
+      launch_lift_slices<__nv_bfloat16>(s, n, ip1, (const __nv_bfloat16*)S1, ld1, ip2, t2, S2, ld2, rexp, Acat);
+      break;
+    default: return RR_ERR_ARG;
+  }
+  k_col_exp<<<(unsigned)b, 512, 0, s>>>(K, Y, ldy, yexp);
+  k_slice_cols_rev<<<dim3((unsigned)((K + 255) / 256), (unsigned)b), 256, 0, s>>>(K, b, Y, ldy, yexp, Yrev);
+  dim3 gz((unsigned)std::min<int64_t>((n + 255) / 256, 1024), (unsigned)b);
+  k_zero_f64<<<gz, 256, 0, s>>>(n, b, X, ldx);
+  note_launches(3);
+  RR_TRY(check_launch("lift_emu slices"));
+  for (int d = 2; d <= S + 1; ++d) {
+    const uint32_t code = (uint32_t)(d - 2) | (1u << 16);  // p0 = d - 2, q0 = 0, nq = 1: scale 2^(-6d)
+    TcEmu e{X, ldx, nullptr, rexp, yexp, (int)b, 1, 1, 0, 0, 1, &code, 4096};
+    RR_TRY(gemm_bf16_tc_emu(n, b, (d - 1) * K, Acat, S * K, Yrev + (size_t)(S - d + 1) * K, S * K, e, s));
+  }
+  *done = true;
+  return RR_OK;
+}
+
+// ---------------------------------------------------------------------------
 // FP64-accurate Gram products G = X^T Y (X n x p, Y n x q, any storage type)
 // on the tensor cores: both operands sliced by columns, every slice pair in
 // one launch with exact FP32 sums over K chunks, FP64 partials per (pair, K
@@ -641,6 +782,29 @@ extern "C" rr_status rr_split_operator(int64_t m, int64_t n, const double* A, in
   if (m < 0 || n < 0 || lda < m || !A) return RR_ERR_ARG;
   return op_prepare(as_stream(stream), A, m, n, lda, (__nv_bfloat16*)hi_col, (__nv_bfloat16*)hi_row,
                     (__nv_bfloat16*)lo_col, (__nv_bfloat16*)lo_row, 0, nullptr, nullptr, false, false);
+}
+
+extern "C" size_t rr_lift_workspace_size(int64_t n, int64_t b, int64_t K) {
+  if (n < 0 || b < 0 || K < 0) return 0;
+  return lift_emu_bytes(n, b, K);
+}
+
+extern "C" rr_status rr_lift(int64_t n, int64_t b, int32_t t1, const void* S1, int64_t ld1, int64_t p1,
+                             int32_t t2, const void* S2, int64_t ld2, int64_t p2, const double* Y, int64_t ldy,
+                             double* X, int64_t ldx, void* ws, size_t ws_bytes, void* stream) {
+  auto ok_type = [](int32_t t) { return t == RR_F64 || t == RR_F32 || t == RR_BF16; };
+  if (n < 0 || b < 1 || p1 < 1 || !S1 || !Y || !X || !ok_type(t1) || ld1 < n || ldx < n) return RR_ERR_ARG;
+  if (S2 && (p2 < 0 || !ok_type(t2) || ld2 < n)) return RR_ERR_ARG;
+  const int64_t p2e = S2 ? p2 : 0;
+  if (ldy < p1 + p2e) return RR_ERR_ARG;
+  if (n == 0) return RR_OK;
+  cudaStream_t s = as_stream(stream);
+  bool done = false;
+  RR_TRY(lift_emu(s, n, b, t1, S1, ld1, p1, t2, S2, ld2, p2e, Y, ldy, X, ldx, ws, ws_bytes, &done));
+  if (done) return RR_OK;
+  RR_TRY(lift(s, t1, n, b, p1, S1, ld1, Y, ldy, X, ldx, 0));
+  if (S2 && p2e > 0) RR_TRY(lift(s, t2, n, b, p2e, S2, ld2, Y + p1, ldy, X, ldx, 1));
+  return RR_OK;
 }
 
 extern "C" size_t rr_gemm_f64_emulated_workspace_size(int32_t trans, int64_t M, int64_t N, int64_t K,

@@ -46,6 +46,9 @@ struct Op {
   EmuOperator emu;
   void* emu_mem;
   void* emu_blk;
+  // FP64-accurate lifts on the tensor cores (low-precision bases)
+  void* lift_mem;
+  size_t lift_bytes;
 };
 
 constexpr int kEmuSlices = 8;
@@ -339,6 +342,8 @@ static void make_op(const rr_operator* A, int32_t dt, Op& op) {
   op.wt = dt == RR_F64 ? RR_F64 : RR_F32;
   op.has_emu = false;
   op.emu_mem = op.emu_blk = nullptr;
+  op.lift_mem = nullptr;
+  op.lift_bytes = 0;
 }
 
 // The operator copies live at the front of the workspace: the low-precision
@@ -346,6 +351,11 @@ static void make_op(const rr_operator* A, int32_t dt, Op& op) {
 // operator for the FP64-accurate products (row-scaled for A X, and
 // column-scaled for A^T Y when the operator is not symmetric).
 static void carve_op(Arena& ar, Op& op, bool symmetric, bool refine, int64_t b) {
+  if (op.dt != RR_F64 && b <= 256) {
+    // lifts of up to 2b columns ([X, D] Y in the refinement)
+    op.lift_bytes = lift_emu_bytes(op.m > op.n ? op.m : op.n, b, 2 * b);
+    op.lift_mem = ar.take_bytes(op.lift_bytes);
+  }
   if (op.kind != RR_DENSE || op.dt == RR_F64) return;
   op.lo_col = ar.take_bytes(op.m * op.n * dsz(op.dt));
   op.lo_row = symmetric ? op.lo_col : ar.take_bytes(op.m * op.n * dsz(op.dt));
@@ -376,6 +386,19 @@ static rr_status prepare_op(const Op& op_in, Op& op, bool symmetric, cudaStream_
   if (op.split) RR_TRY(cast_operator_lo(op.m, op.n, op.A, op.lda, op.lo2_col, op.lo2_row, s));
   if (op.has_emu)
     RR_TRY(emu_prepare(s, op.A, op.m, op.n, op.lda, kEmuSlices, op.emu, op.emu_mem, true, !symmetric));
+  return RR_OK;
+}
+
+// X (n x b, FP64) = S1 Y(0:p1, :) + S2 Y(p1:p1+p2, :) (S2 may be null): the
+// FP64-accurate tensor-core lift when the shape allows, else FP64 arithmetic
+static rr_status lift2(const Op& op, cudaStream_t s, int64_t n, int64_t b, int32_t t1, const void* S1, int64_t ld1,
+                       int64_t p1, int32_t t2, const void* S2, int64_t ld2, int64_t p2, const double* Y, int64_t ldy,
+                       double* X, int64_t ldx) {
+  bool done = false;
+  RR_TRY(lift_emu(s, n, b, t1, S1, ld1, p1, t2, S2, ld2, p2, Y, ldy, X, ldx, op.lift_mem, op.lift_bytes, &done));
+  if (done) return RR_OK;
+  RR_TRY(lift(s, t1, n, b, p1, S1, ld1, Y, ldy, X, ldx, 0));
+  if (S2 && p2 > 0) RR_TRY(lift(s, t2, n, b, p2, S2, ld2, Y + p1, ldy, X, ldx, 1));
   return RR_OK;
 }
 
@@ -448,8 +471,8 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
     STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, dt, w.Ulo, m, op.wt, w.Pw, m, w.Bm, b, s));
     STAGE(RR_STAGE_PENCIL, rr_pencil_svd(b, b, w.Bm, w.Gu, w.Gv, w.sig2, w.Ys, w.Zs, w.c.pen_ws, w.c.pen_bytes,
                          nullptr, s));
-    STAGE(RR_STAGE_LIFT, lift(s, dt, m, b, b, w.Ulo, m, w.Ys, b, w.Ut, m, 0));
-    STAGE(RR_STAGE_LIFT, lift(s, dt, n, b, b, w.Vlo, n, w.Zs, b, w.Vt, n, 0));
+    STAGE(RR_STAGE_LIFT, lift2(op, s, m, b, dt, w.Ulo, m, b, 0, nullptr, 0, 0, w.Ys, b, w.Ut, m));
+    STAGE(RR_STAGE_LIFT, lift2(op, s, n, b, dt, w.Vlo, n, b, 0, nullptr, 0, 0, w.Zs, b, w.Vt, n));
     RR_CUDA(cudaMemcpyAsync(w.sig, w.sig2, b * sizeof(double), cudaMemcpyDeviceToDevice, s));
     ++sweep;
     if (!refine && !batch_mode) {
@@ -547,10 +570,8 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
       STAGE(RR_STAGE_PENCIL, rr_pencil_svd(b2, b2, B, w.Gu, w.Gv, w.sig2, w.Ys, w.Zs, w.c.pen_ws, w.c.pen_bytes,
                            nullptr, s));
       // lift the leading b triplets
-      STAGE(RR_STAGE_LIFT, lift(s, RR_F64, m, b, b, w.Ut, m, w.Ys, b2, w.Ut2, m, 0));
-      STAGE(RR_STAGE_LIFT, lift(s, et, m, b, b, Eg, m, w.Ys + b, b2, w.Ut2, m, 1));
-      STAGE(RR_STAGE_LIFT, lift(s, RR_F64, n, b, b, w.Vt, n, w.Zs, b2, w.Vt2, n, 0));
-      STAGE(RR_STAGE_LIFT, lift(s, et, n, b, b, Fg, n, w.Zs + b, b2, w.Vt2, n, 1));
+      STAGE(RR_STAGE_LIFT, lift2(op, s, m, b, RR_F64, w.Ut, m, b, et, Eg, m, b, w.Ys, b2, w.Ut2, m));
+      STAGE(RR_STAGE_LIFT, lift2(op, s, n, b, RR_F64, w.Vt, n, b, et, Fg, n, b, w.Zs, b2, w.Vt2, n));
       std::swap(w.Ut, w.Ut2);
       std::swap(w.Vt, w.Vt2);
       RR_CUDA(cudaMemcpyAsync(w.sig, w.sig2, b * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -755,7 +776,7 @@ static rr_status eig_run(const rr_operator* Aop, const rr_params* p, double* the
     STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, dt, w.Vlo, n, op.wt, w.Pw, n, w.H, b, s));
     STAGE(RR_STAGE_PENCIL, rr_pencil_eig(b, w.H, w.G, w.th2, w.Y, w.c.pen_ws, w.c.pen_bytes, nullptr, s));
     STAGE(RR_STAGE_PENCIL, select_eig(s, b, b, p->which, w.th2, w.Y, b, w.theta, w.Ysel, b));
-    STAGE(RR_STAGE_LIFT, lift(s, dt, n, b, b, w.Vlo, n, w.Ysel, b, w.X, n, 0));
+    STAGE(RR_STAGE_LIFT, lift2(op, s, n, b, dt, w.Vlo, n, b, 0, nullptr, 0, 0, w.Ysel, b, w.X, n));
     ++sweep;
     STAGE(RR_STAGE_OTHER, update_bounds());
     if (!refine) {
@@ -861,8 +882,7 @@ static rr_status eig_run(const rr_operator* Aop, const rr_params* p, double* the
       STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, dt, w.Dlo, n, op.wt, w.AD, n, w.H + b + b * b2, b2, s));
       STAGE(RR_STAGE_PENCIL, rr_pencil_eig(b2, w.H, w.G, w.th2, w.Y, w.c.pen_ws, w.c.pen_bytes, nullptr, s));
       STAGE(RR_STAGE_PENCIL, select_eig(s, b2, b, p->which, w.th2, w.Y, b2, w.theta, w.Ysel, b2));
-      STAGE(RR_STAGE_LIFT, lift(s, RR_F64, n, b, b, w.X, n, w.Ysel, b2, w.X2, n, 0));
-      STAGE(RR_STAGE_LIFT, lift(s, dt, n, b, b, w.Dlo, n, w.Ysel + b, b2, w.X2, n, 1));
+      STAGE(RR_STAGE_LIFT, lift2(op, s, n, b, RR_F64, w.X, n, b, dt, w.Dlo, n, b, w.Ysel, b2, w.X2, n));
       std::swap(w.X, w.X2);
       ++sweep;
       ++inf.refine_sweeps;

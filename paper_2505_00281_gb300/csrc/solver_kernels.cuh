@@ -84,6 +84,10 @@ size_t emu_operator_bytes(int64_t m, int64_t n, int S, bool rows, bool cols);
 size_t emu_block_bytes(int64_t K, int64_t N, int S);
 rr_status emu_prepare(cudaStream_t s, const double* A, int64_t m, int64_t n, int64_t lda, int S,
                       EmuOperator& op, void* mem, bool rows, bool cols);
+size_t lift_emu_bytes(int64_t n, int64_t b, int64_t K);
+rr_status lift_emu(cudaStream_t s, int64_t n, int64_t b, int32_t t1, const void* S1, int64_t ld1, int64_t p1,
+                   int32_t t2, const void* S2, int64_t ld2, int64_t p2, const double* Y, int64_t ldy, double* X,
+                   int64_t ldx, void* mem, size_t mem_bytes, bool* done);
 rr_status op_prepare(cudaStream_t s, const double* A, int64_t m, int64_t n, int64_t lda,
                      __nv_bfloat16* hi_col, __nv_bfloat16* hi_row, __nv_bfloat16* lo_col, __nv_bfloat16* lo_row,
                      int S, EmuOperator* emu, void* emu_mem, bool rows, bool cols);

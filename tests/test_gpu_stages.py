@@ -91,6 +91,41 @@ def test_split_operator_bitexact(rr, m, n):
     assert np.array_equal(_bf16_bits(lr).reshape(m, n), lb)
 
 
+_TDT = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}
+
+
+@pytest.mark.parametrize("n,p1,p2,b,t1,t2", [
+    (16384, 128, 128, 128, "f64", "f32"),   # the refinement's [X, D] Y at the SVD workload's size
+    (4096, 128, 0, 128, "bf16", None),      # phase-1 lift of a BF16 basis
+    (1000, 64, 40, 72, "f64", "bf16"),      # ragged rows and columns
+    (777, 30, 5, 17, "f32", "f64")])        # K = 35 (not a multiple of 8): FP64-arithmetic path
+def test_lift_fp64_accurate(rr, n, p1, p2, b, t1, t2):
+    """X = [S1 S2] Y against an FP64 reference: exact on integer data (every slice product and sum
+    is exact, so the tensor-core lift must reproduce the exact result), and within K 2^-40 of
+    max|row| max|col| on full-mantissa data with row and column scales spread over 2^+-20."""
+    rng = np.random.default_rng(n + p1 + b)
+    K = p1 + p2
+    for integer in (True, False):
+        if integer:
+            S = rng.integers(-2 ** 20, 2 ** 20, size=(n, K)).astype(np.float64)
+            Y = rng.integers(-2 ** 20, 2 ** 20, size=(K, b)).astype(np.float64)
+            if t1 == "bf16" or t2 == "bf16":
+                S = np.round(S / 2 ** 13)          # 8 significant bits: exact in BF16
+        else:
+            S = rng.standard_normal((n, K)) * np.exp2(rng.integers(-20, 21, size=(n, 1)))
+            Y = rng.standard_normal((K, b)) * np.exp2(rng.integers(-20, 21, size=(1, b)))
+        S1d = dev(S[:, :p1], _TDT[t1])
+        S2d = dev(S[:, p1:], _TDT[t2]) if t2 else None
+        Sh = np.hstack([host(S1d)] + ([host(S2d)] if t2 else []))   # the values as stored
+        X = host(rr.rr_lift(S1d, dev(Y), S2d))
+        ref = Sh @ Y
+        if integer:
+            assert np.array_equal(X, ref)
+        else:
+            bound = K * 2.0 ** -40 * np.abs(Sh).max(axis=1)[:, None] * np.abs(Y).max(axis=0)[None, :]
+            assert np.all(np.abs(X - ref) <= bound)
+
+
 # ---------------------------------------------------------------- a2
 @pytest.mark.parametrize("M,N,K", [(300, 40, 700), (128, 128, 4096), (1000, 7, 33),
                                    # tcgen05 path: ragged M, K tail, N padded to 16, K-split
