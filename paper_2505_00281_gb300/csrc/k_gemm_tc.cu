@@ -251,11 +251,9 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16_tc(const __grid_constant__
                              | (1u << 7) | (1u << 10)            // A, B: BF16
                              | ((uint32_t)(a.npad >> 3) << 17)  // N / 8
                              | ((uint32_t)(kBM >> 4) << 24);    // M / 16
-      bool ok = true;
       for (int i = 0; i < nks; ++i) {
         const int s = i % a.stages;
         if (!mbar_wait(&full[s], (i / a.stages) & 1)) {
-          ok = false;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -280,7 +278,6 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16_tc(const __grid_constant__
       // the final commit arrives once every MMA issued above has completed,
       // also after an error, so TMEM is never freed under a running MMA
       umma_commit(accum);
-      (void)ok;
     }
     // ---------------- epilogue (all 4 warps) ----------------
     __syncwarp();

@@ -18,6 +18,9 @@
 // multiply and subtract, each rounded separately (no FMA contraction), so the
 // result is bit-reproducible and equals a plain FP32/FP64 loop.
 #include <climits>
+#include <type_traits>
+
+#include <cooperative_groups.h>
 
 #include "rr_common.cuh"
 
@@ -33,6 +36,7 @@ struct HessWs {
   T* pcolmax;   // [G][k] per-slab column inf-norms
   int* flags;   // [G] column steps published by each CTA (j + 1 after column j)
   unsigned long long* cand;  // [2][G] packed candidates (FP32 path)
+  int64_t rpc;               // rows per CTA (FP32 path; 0: ceil(n / G))
 };
 
 // Publish/await the per-column candidates: CTA g releases flags[g] = step once
@@ -51,6 +55,19 @@ __device__ __forceinline__ unsigned long long word_acquire(const unsigned long l
 __device__ __forceinline__ int flag_acquire(const int* f) {
   int v;
   asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+  return v;
+}
+
+// the same exchange through distributed shared memory (one thread-block
+// cluster): release / acquire at cluster scope on generic addresses
+// (the publishing lanes' row writes reach the releasing lane through
+// __syncwarp; a release store is cumulative over them)
+__device__ __forceinline__ void word_release_cl(unsigned long long* f, unsigned long long v) {
+  asm volatile("st.release.cluster.b64 [%0], %1;" ::"l"(f), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long word_acquire_cl(const unsigned long long* f) {
+  unsigned long long v;
+  asm volatile("ld.acquire.cluster.b64 %0, [%1];" : "=l"(v) : "l"(f) : "memory");
   return v;
 }
 
@@ -333,50 +350,99 @@ __device__ __forceinline__ unsigned long long pack_cand(float v, unsigned row, i
          (unsigned long long)((col + 1) & 0xFF);
 }
 
-template <typename TO>
+// Block argmax of (|value|, local row) with ties to the lower row as one
+// 64-bit key: |value| bits above the complemented row (0: no candidate;
+// value < 0 marks "none", NaN never wins).  A warp reduces with redux.sync,
+// lane 0 folds the warp's key into a shared atomicMax.
+__device__ __forceinline__ unsigned long long am_key(float av, int row) {
+  return av >= 0.f ? ((unsigned long long)__float_as_uint(av) << 32) | (unsigned)(~row) : 0ull;
+}
+__device__ __forceinline__ unsigned long long warp_key_max(unsigned long long key) {
+  const unsigned hi = (unsigned)(key >> 32), lo = (unsigned)key;
+  const unsigned mhi = __reduce_max_sync(0xffffffffu, hi);
+  const unsigned mlo = __reduce_max_sync(0xffffffffu, hi == mhi ? lo : 0u);
+  return ((unsigned long long)mhi << 32) | mlo;
+}
+
+// CL: the CTAs form one thread-block cluster (G <= kHessMaxCluster): the
+// candidate words and rows go through distributed shared memory instead of
+// global memory (the same arithmetic, pivots and results).
+constexpr int kHessMaxCluster = 16;
+
+template <typename TO, bool CL>
 __global__ void __launch_bounds__(kHessThreads) k_hessenberg_f32(
     int64_t n, int k, float* __restrict__ W, int64_t ldw, TO* __restrict__ Q, int64_t ldq,
     int* __restrict__ piv, float tol, HessWs<float> ws, int slab) {
   using T = float;
+  namespace cg = cooperative_groups;
   const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = kHessThreads / 32;
-  const int64_t rpc = (n + G - 1) / G;
+  const int64_t rpc = ws.rpc > 0 ? ws.rpc : (n + G - 1) / G;
   const int64_t r0 = (int64_t)g * rpc;
   const int64_t r1 = r0 + rpc < n ? r0 + rpc : n;
   const int nr = r1 > r0 ? (int)(r1 - r0) : 0;
 
   extern __shared__ unsigned char smem_raw[];
-  T* thr = reinterpret_cast<T*>(smem_raw);   // [k]
+  // cluster exchange buffers first (8-byte aligned): candidate words
+  // [2][kHessMaxCluster], candidate rows [2][k], column maxima [k]
+  unsigned long long* cw = reinterpret_cast<unsigned long long*>(smem_raw);
+  T* prs = reinterpret_cast<T*>(cw + (CL ? 2 * kHessMaxCluster : 0));
+  T* cmx = prs + (CL ? 2 * k : 0);
+  T* thr = cmx + (CL ? k : 0);               // [k]
   T* wgt = thr + k;                          // [2][k] weights, by column parity
-  T* slabp = wgt + 2 * k;                    // [k][rpc] in slab mode
+  // [k][ldv] in slab mode, 16-byte aligned; with rpc a multiple of 128 the
+  // stride is rpc + 4 (column starts 4 banks apart: the candidate row's
+  // entries, read across columns, meet 4-way instead of 32-way conflicts)
+  // and the rank-1 update moves float4 chunks
+  T* slabp = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(wgt + 2 * k) + 15) & ~(uintptr_t)15);
   T* const base = slab ? slabp : W + r0;
-  const int64_t ldv = slab ? rpc : ldw;
+  const bool vec = slab && rpc % 128 == 0 && rpc <= 512;
+  const int64_t ldv = slab ? (vec ? rpc + 4 : rpc) : ldw;
   auto col = [&](int c) -> T* { return base + (int64_t)c * ldv; };
+  if constexpr (CL) {
+    // word slots start at 0 (no column tag); the cluster barrier below orders
+    // this before any other CTA's first word
+    for (int i = tid; i < 2 * kHessMaxCluster; i += kHessThreads) cw[i] = 0ull;
+  }
   if (slab) {
     for (int c = warp; c < k; c += nwarps) {
       const T* src = W + r0 + (int64_t)c * ldw;
       T* dst = col(c);
-      for (int i = lane; i < nr; i += 32) dst[i] = src[i];
+      for (int i = lane; i < (int)ldv; i += 32) dst[i] = i < nr ? src[i] : T(0);  // zero padding rows
     }
     __syncthreads();
   }
   __shared__ T red_v[32];
   __shared__ int red_i[32];
   __shared__ T s_qr;
-  __shared__ int s_r, s_win, s_keep;
+  __shared__ int s_r, s_keep;
+  __shared__ unsigned long long s_key[2];  // block argmax keys, by column parity
+  if (tid < 2) s_key[tid] = 0ull;
 
   for (int c = warp; c < k; c += nwarps) {
     T m = T(0);
     const T* cc = col(c);
     for (int i = lane; i < nr; i += 32) m = fmax(m, fabs(cc[i]));
     m = warp_max(m);
-    if (lane == 0) ws.pcolmax[(size_t)g * k + c] = m;
+    if (lane == 0) {
+      if constexpr (CL) cmx[c] = m;
+      else ws.pcolmax[(size_t)g * k + c] = m;
+    }
   }
-  if (!grid_barrier(ws.bar, G, ws.err)) return;
-  for (int c = tid; c < k; c += kHessThreads) {
-    T m = T(0);
-    for (int h = 0; h < G; ++h) m = fmax(m, ld_cg(ws.pcolmax + (size_t)h * k + c));
-    thr[c] = rn_mul(tol, m);
+  if constexpr (CL) {
+    cg::this_cluster().sync();
+    for (int c = tid; c < k; c += kHessThreads) {
+      T m = T(0);
+      for (int h = 0; h < G; ++h) m = fmax(m, cg::this_cluster().map_shared_rank(cmx, h)[c]);
+      thr[c] = rn_mul(tol, m);
+    }
+  } else {
+    if (!grid_barrier(ws.bar, G, ws.err)) return;
+    for (int c = tid; c < k; c += kHessThreads) {
+      T m = T(0);
+      for (int h = 0; h < G; ++h) m = fmax(m, ld_cg(ws.pcolmax + (size_t)h * k + c));
+      thr[c] = rn_mul(tol, m);
+    }
   }
   __syncthreads();
 
@@ -422,7 +488,7 @@ __global__ void __launch_bounds__(kHessThreads) k_hessenberg_f32(
   // back to the slab; then the packed word
   auto publish_w0 = [&](int jc, bool upd, int rl) {
     const int par = jc & 1;
-    T* prow = ws.prow + ((size_t)par * G + g) * k;
+    T* prow = CL ? prs + (size_t)par * k : ws.prow + ((size_t)par * G + g) * k;
     if (rl != INT_MAX) {
       const T m = upd ? col(jc - 1)[rl] : T(0);
       for (int c = jc + 1 + lane; c < k; c += 32) {
@@ -435,7 +501,14 @@ __global__ void __launch_bounds__(kHessThreads) k_hessenberg_f32(
       }
     }
     __syncwarp();
-    if (lane == 0) {
+    if constexpr (CL) {
+      if (lane < G) {  // into every CTA's word slot g
+        const T v = rl != INT_MAX ? col(jc)[rl] : T(0);
+        const unsigned row = rl != INT_MAX ? (unsigned)(r0 + rl) : kNoRow;
+        word_release_cl(cg::this_cluster().map_shared_rank(cw + par * kHessMaxCluster + g, lane),
+                        pack_cand(v, row, jc));
+      }
+    } else if (lane == 0) {
       const T v = rl != INT_MAX ? col(jc)[rl] : T(0);
       const unsigned row = rl != INT_MAX ? (unsigned)(r0 + rl) : kNoRow;
       __threadfence();
@@ -455,7 +528,8 @@ __global__ void __launch_bounds__(kHessThreads) k_hessenberg_f32(
     bool ok = true;
     for (int h = lane; h < G; h += 32) {
       unsigned long long wv;
-      while (((wv = word_acquire(ws.cand + (size_t)par * G + h)) & 0xFFull) != tag) {
+      while (((wv = CL ? word_acquire_cl(cw + par * kHessMaxCluster + h)
+                       : word_acquire(ws.cand + (size_t)par * G + h)) & 0xFFull) != tag) {
         if (*(volatile int*)ws.err != 0 || global_timer_ns() - t0 > kWaitLimitNs) {
           atomicCAS(ws.err, 0, (int)RR_ERR_TIMEOUT);
           ok = false;
@@ -491,9 +565,15 @@ __global__ void __launch_bounds__(kHessThreads) k_hessenberg_f32(
     }
     const bool kp = ag >= 0 && sv != T(0) && fabs(sv) >= thr[jc];
     if (kp) {
-      const T* prow = ws.prow + ((size_t)par * G + ag) * k;
       T* wb = wgt + (size_t)par * k;
-      for (int c = jc + 1 + lane; c < k; c += 32) wb[c] = ld_cg(prow + c);
+      if constexpr (CL) {
+        __syncwarp();  // the acquiring lane's order for the whole warp
+        const T* prow = cg::this_cluster().map_shared_rank(prs + (size_t)par * k, ag);
+        for (int c = jc + 1 + lane; c < k; c += 32) wb[c] = prow[c];
+      } else {
+        const T* prow = ws.prow + ((size_t)par * G + ag) * k;
+        for (int c = jc + 1 + lane; c < k; c += 32) wb[c] = ld_cg(prow + c);
+      }
     }
     if (lane == 0) {
       s_qr = sv;
@@ -511,8 +591,8 @@ __global__ void __launch_bounds__(kHessThreads) k_hessenberg_f32(
     if (lane == 0) s_ok = ok ? 1 : 0;
   }
   __syncthreads();
-  if (!s_ok) return;
-  for (int j = 0; j < k; ++j) {
+  bool failed = !s_ok;
+  for (int j = 0; j < k && !failed; ++j) {
     const bool keep = s_keep != 0;
     const T qr = s_qr;
     const T* wj = wgt + (size_t)(j & 1) * k;  // weights of column j
@@ -539,34 +619,21 @@ __global__ void __launch_bounds__(kHessThreads) k_hessenberg_f32(
           }
         }
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        T ov = __shfl_xor_sync(0xffffffffu, bv, o);
-        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        argmax_merge(bv, bi, ov, oi);
-      }
-      if (lane == 0) {
-        red_v[warp] = bv;
-        red_i[warp] = bi;
-      }
+      const unsigned long long wk = warp_key_max(am_key(bv, bi));
+      if (lane == 0 && wk) atomicMax(&s_key[j & 1], wk);
     }
     __syncthreads();
+    const unsigned long long bkey = s_key[j & 1];
+    const int bcand = bkey ? (int)(~(unsigned)bkey) : INT_MAX;  // the CTA's candidate row
+    if (tid == 0) s_key[(j + 1) & 1] = 0ull;                    // read last in step j - 1
     if (j + 1 < k) {
       if (warp == 0) {
-        // reduce the candidate, publish it (its row takes column j's pending
-        // update, written back to the slab), then wait for the pivot of
-        // column j+1 while the other warps finish column j's update
-        T bv = lane < nwarps ? red_v[lane] : T(-1);
-        int bi = lane < nwarps ? red_i[lane] : INT_MAX;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          T ov = __shfl_xor_sync(0xffffffffu, bv, o);
-          int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-          argmax_merge(bv, bi, ov, oi);
-        }
-        const int rl = bi;
+        // publish the candidate (its row takes column j's pending update,
+        // written back to the slab), then wait for the pivot of column j+1
+        // while the other warps apply column j's update
+        const int rl = bcand;
         const int par = (j + 1) & 1;
-        T* prow = ws.prow + ((size_t)par * G + g) * k;
+        T* prow = CL ? prs + (size_t)par * k : ws.prow + ((size_t)par * G + g) * k;
         if (rl != INT_MAX) {
           const T m = cj[rl];
           for (int c = j + 2 + lane; c < k; c += 32) {
@@ -579,22 +646,77 @@ __global__ void __launch_bounds__(kHessThreads) k_hessenberg_f32(
           }
         }
         __syncwarp();
-        if (lane == 0) {
+        if constexpr (CL) {
+          if (lane < G) {
+            const T v = rl != INT_MAX ? col(j + 1)[rl] : T(0);
+            const unsigned row = rl != INT_MAX ? (unsigned)(r0 + rl) : kNoRow;
+            word_release_cl(cg::this_cluster().map_shared_rank(cw + par * kHessMaxCluster + g, lane),
+                            pack_cand(v, row, j + 1));
+          }
+        } else if (lane == 0) {
           const T v = rl != INT_MAX ? col(j + 1)[rl] : T(0);
           const unsigned row = rl != INT_MAX ? (unsigned)(r0 + rl) : kNoRow;
           __threadfence();
           word_release(ws.cand + (size_t)par * G + g, pack_cand(v, row, j + 1));
         }
+        // the published candidate is what the other CTAs wait for: the bulk
+        // update starts only now, so its shared-memory traffic does not delay it
+        asm volatile("bar.arrive 1, %0;" ::"r"(kHessThreads) : "memory");
         const bool ok = await_pivot(j + 1);
         if (lane == 0) s_ok = ok ? 1 : 0;
-      } else if (keep) {
+      } else {
+        asm volatile("bar.sync 1, %0;" ::"r"(kHessThreads) : "memory");
+      }
+      if (warp != 0 && keep) {
         // rank-1 update of columns j+2.. (all rows but the candidate's, which
         // warp 0 updates): the multiplier column in registers, independent
         // loads per target column
         const T* cj_c = cj;
-        const int rl = bi_of_block(red_v, red_i, nwarps);
+        const int rl = bcand;
         constexpr int kR = 16;  // rows per lane held in registers (nr <= 512)
-        if (nr <= 32 * kR) {
+        // float4 chunks: lane rows 4 lane + 128 t (t < NC = rpc / 128); the
+        // padding rows beyond nr are zero and stay finite
+        auto upd4 = [&](auto nc) {
+          constexpr int NC = decltype(nc)::value;
+          float4 xr[NC];
+#pragma unroll
+          for (int t = 0; t < NC; ++t) xr[t] = reinterpret_cast<const float4*>(cj_c)[lane + 32 * t];
+          for (int c = j + 2 + (warp - 1); c < k; c += nwarps - 1) {
+            float4* cc = reinterpret_cast<float4*>(col(c));
+            const T wc = wj[c];
+            float4 yv[NC];
+#pragma unroll
+            for (int t = 0; t < NC; ++t) yv[t] = cc[lane + 32 * t];
+#pragma unroll
+            for (int t = 0; t < NC; ++t) {
+              const int i0 = 4 * lane + 128 * t;
+              float4 o = yv[t];
+              o.x = i0 == rl ? yv[t].x : rn_sub(yv[t].x, rn_mul(wc, xr[t].x));
+              o.y = i0 + 1 == rl ? yv[t].y : rn_sub(yv[t].y, rn_mul(wc, xr[t].y));
+              o.z = i0 + 2 == rl ? yv[t].z : rn_sub(yv[t].z, rn_mul(wc, xr[t].z));
+              o.w = i0 + 3 == rl ? yv[t].w : rn_sub(yv[t].w, rn_mul(wc, xr[t].w));
+              if ((rl >> 2) == lane + 32 * t) {
+                // the candidate's chunk: warp 0 writes row rl concurrently,
+                // so only the other three rows are stored
+                float* cs = reinterpret_cast<float*>(cc + lane + 32 * t);
+                if (i0 != rl) cs[0] = o.x;
+                if (i0 + 1 != rl) cs[1] = o.y;
+                if (i0 + 2 != rl) cs[2] = o.z;
+                if (i0 + 3 != rl) cs[3] = o.w;
+              } else {
+                cc[lane + 32 * t] = o;
+              }
+            }
+          }
+        };
+        if (vec) {
+          switch (rpc / 128) {
+            case 1: upd4(std::integral_constant<int, 1>{}); break;
+            case 2: upd4(std::integral_constant<int, 2>{}); break;
+            case 3: upd4(std::integral_constant<int, 3>{}); break;
+            default: upd4(std::integral_constant<int, 4>{}); break;
+          }
+        } else if (nr <= 32 * kR) {
           T xr[kR];
 #pragma unroll
           for (int t = 0; t < kR; ++t) {
@@ -626,9 +748,14 @@ __global__ void __launch_bounds__(kHessThreads) k_hessenberg_f32(
         }
       }
       __syncthreads();
-      if (!s_ok) return;
+      if (!s_ok) failed = true;
     }
   }
+  if constexpr (CL) {
+    // no CTA leaves while another may still read its shared memory
+    cg::this_cluster().sync();
+  }
+  if (failed) return;
   for (int c = warp; c < k; c += nwarps) {
     const T* src = col(c);
     T* dw = W + r0 + (int64_t)c * ldw;
@@ -660,7 +787,7 @@ static rr_status hess_launch(int64_t n, int64_t k, T* W, int64_t ldw, TO* Q, int
                              double tol, void* ws, size_t ws_bytes, cudaStream_t s, int max_grid) {
   // FP32 arithmetic: the packed-candidate kernel (rows must fit its 24-bit field)
   const bool packed = sizeof(T) == 4 && n < (int64_t)kNoRow;
-  const void* fn = packed ? (const void*)k_hessenberg_f32<TO> : (const void*)k_hessenberg<T, TO>;
+  const void* fn = packed ? (const void*)k_hessenberg_f32<TO, false> : (const void*)k_hessenberg<T, TO>;
   // Grid: about 256 rows per CTA (fewer CTAs make the per-column barrier and
   // candidate reduction cheaper), more CTAs if a slab would not fit in shared
   // memory; slab mode when the CTA's rows of all k columns fit in 200 KB.
@@ -677,10 +804,50 @@ static rr_status hess_launch(int64_t n, int64_t k, T* W, int64_t ldw, TO* Q, int
     if (g < 1) g = 1;
     G = (int)g;
   }
-  const int64_t rpc = (n + G - 1) / G;
-  const size_t fixed = (packed ? 3 : 2) * (size_t)k * sizeof(T);  // thresholds and weights
-  if ((size_t)rpc * k * sizeof(T) <= kSlabLimit && (size_t)rpc * k * sizeof(T) + fixed <= 220 * 1024) slab = 1;
-  size_t smem = fixed + (slab ? (size_t)rpc * k * sizeof(T) : 0);
+  int64_t rpc = (n + G - 1) / G;
+  if (packed) {
+    // rows per CTA a multiple of 128 where the slab still fits: the FP32
+    // kernel's float4 update and padded stride (fewer CTAs when it rounds up)
+    const int64_t r128 = (rpc + 127) / 128 * 128;
+    if (r128 <= 512 && (size_t)(r128 + 4) * k * sizeof(T) <= kSlabLimit) {
+      rpc = r128;
+      G = (int)((n + rpc - 1) / rpc);
+    }
+  }
+  const int64_t ldv = (packed && rpc % 128 == 0 && rpc <= 512) ? rpc + 4 : rpc;
+  const size_t fixed = (packed ? 3 : 2) * (size_t)k * sizeof(T) + 16;  // thresholds, weights, alignment
+  if ((size_t)ldv * k * sizeof(T) <= kSlabLimit && (size_t)ldv * k * sizeof(T) + fixed <= 220 * 1024) slab = 1;
+  size_t smem = fixed + (slab ? (size_t)ldv * k * sizeof(T) : 0);
+  // one thread-block cluster when every CTA's rows fit in shared memory and
+  // the CTAs fit one cluster: the exchange goes through distributed shared
+  // memory (checked against the GPU's cluster occupancy; otherwise the
+  // cooperative grid)
+  bool cl = false;
+  const size_t clbytes = 2 * kHessMaxCluster * sizeof(unsigned long long) + 3 * (size_t)k * sizeof(T);
+  if (packed && slab && G <= kHessMaxCluster && smem + clbytes <= 227 * 1024) {
+    const void* fcl = (const void*)k_hessenberg_f32<TO, true>;
+    RR_CUDA(cudaFuncSetAttribute(fcl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(smem + clbytes)));
+    if (G > 8) RR_CUDA(cudaFuncSetAttribute(fcl, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cudaLaunchConfig_t q = {};
+    q.gridDim = dim3(G);
+    q.blockDim = dim3(kHessThreads);
+    q.dynamicSmemBytes = smem + clbytes;
+    cudaLaunchAttribute qa[1];
+    qa[0].id = cudaLaunchAttributeClusterDimension;
+    qa[0].val.clusterDim.x = G;
+    qa[0].val.clusterDim.y = 1;
+    qa[0].val.clusterDim.z = 1;
+    q.attrs = qa;
+    q.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, fcl, &q) == cudaSuccess && nclusters >= 1) {
+      cl = true;
+      fn = fcl;
+      smem += clbytes;
+    } else {
+      (void)cudaGetLastError();
+    }
+  }
   if (smem > 48 * 1024)
     RR_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   if (ws_bytes < hess_ws_bytes<T>(k, G) || !ws) return RR_ERR_WORKSPACE;
@@ -694,12 +861,30 @@ static rr_status hess_launch(int64_t n, int64_t k, T* W, int64_t ldw, TO* Q, int
   h.pcolmax = ar.take<T>((size_t)G * k);
   h.flags = ar.take<int>(G);
   h.cand = ar.take<unsigned long long>(2 * (size_t)G);
+  h.rpc = packed ? rpc : 0;
   RR_CUDA(cudaMemsetAsync(ws, 0, 512, s));  // err + barrier
   RR_CUDA(cudaMemsetAsync(h.flags, 0, (size_t)G * sizeof(int), s));
   RR_CUDA(cudaMemsetAsync(h.cand, 0, 2 * (size_t)G * sizeof(unsigned long long), s));
   T t = tol > 0 ? (T)tol : (T)(4.0 * (double)k * (sizeof(T) == 4 ? 0x1p-23 : 0x1p-52));
   int kk = (int)k;
   void* args[] = {&n, &kk, &W, &ldw, &Q, &ldq, &piv, &t, &h, &slab};
+  if (cl) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(G);
+    cfg.blockDim = dim3(kHessThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = G;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    RR_CUDA(cudaLaunchKernelExC(&cfg, fn, args));
+    note_launches(1);
+    return RR_OK;
+  }
   if (G == 1) {
     // a single CTA never waits on another one: plain launch (graph-capturable,
     // safe to run concurrently with other work)
