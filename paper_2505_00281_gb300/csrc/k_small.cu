@@ -1279,6 +1279,41 @@ __device__ __forceinline__ bool qr_better(float n, int k, float bn, int bk) {
   return n > bn || (n == bn && k < bk);
 }
 
+// Warp sums of N (a power of two <= 32) per-lane values at once
+// (reduce-scatter: halving exchanges over the top lane bits, then butterflies
+// over the rest): on return lane l holds the sum of value l >> (5 - log2 N).
+template <int N>
+__device__ __forceinline__ float qr_rs(float d[N]) {
+  static_assert(N >= 1 && N <= 32 && (N & (N - 1)) == 0, "power of two");
+  constexpr int L = N >= 32 ? 5 : N >= 16 ? 4 : N >= 8 ? 3 : N >= 4 ? 2 : N >= 2 ? 1 : 0;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int st = 0; st < L; ++st) {
+    const int h = N >> (st + 1), b = 16 >> st;
+    const bool up = lane & b;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const float send = up ? d[i] : d[i + h], keep = up ? d[i + h] : d[i];
+      d[i] = keep + __shfl_xor_sync(0xffffffffu, send, b);
+    }
+  }
+  float v = d[0];
+#pragma unroll
+  for (int b = 16 >> L; b >= 1; b >>= 1) v += __shfl_xor_sync(0xffffffffu, v, b);
+  return v;
+}
+// lane holding value u after qr_rs<N>
+template <int N>
+__device__ __forceinline__ int qr_rs_lane(int u) {
+  return u * (32 / N);
+}
+
+// (squared norm, column) as one key, larger norm first, then lower column;
+// 0 = no candidate
+__device__ __forceinline__ unsigned long long qr_key(float n2, int col) {
+  return ((unsigned long long)__float_as_uint(n2) << 32) | (unsigned)(~col);
+}
+
 template <int RPL, int CPW>
 __global__ void __launch_bounds__(kQrThreads, 1)
     k_qr_precond(int r, int c, const double* __restrict__ C, const float* __restrict__ scale,
@@ -1288,13 +1323,13 @@ __global__ void __launch_bounds__(kQrThreads, 1)
   cg::cluster_group cl = cg::this_cluster();
   __shared__ __align__(16) float vbuf[2][kQrMaxNC][kQrMaxRows];
   __shared__ QrCand cand[2][kQrMaxNC];
-  __shared__ float wn[kQrWarps];
-  __shared__ int wk[kQrWarps];
+  __shared__ unsigned long long s_key[2];
   const int NC = (int)cl.num_blocks();
   const int z = (int)cl.block_rank();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float sc = *scale;
   const int col0 = z * kQrWarps * CPW + warp;  // column of slot u: col0 + 16 u
+  if (threadIdx.x < 2) s_key[threadIdx.x] = 0ull;
 
   float a[CPW][RPL];
   unsigned done = 0;  // slot u pivoted already (or beyond the last column)
@@ -1308,48 +1343,43 @@ __global__ void __launch_bounds__(kQrThreads, 1)
       a[u][t] = (k < r && i < c) ? (float)((double)sc * C[k + (size_t)i * r]) : 0.f;
     }
   }
+  __syncthreads();
 
   // best remaining column of this CTA (rows > j) -> reflector for step j + 1
   // into buffer `par` of every CTA
   auto publish = [&](int j, int par) {
-    float bn = -1.f;
-    int bk = INT_MAX, bu = -1;
+    float d[CPW];
 #pragma unroll
     for (int u = 0; u < CPW; ++u) {
-      if (done >> u & 1u) continue;
       float s2 = 0.f;
 #pragma unroll
       for (int t = 0; t < RPL; ++t)
         if (t * 32 + lane > j) s2 = fmaf(a[u][t], a[u][t], s2);
-      s2 = warp_sum(s2);
-      const int k = col0 + kQrWarps * u;
-      if (qr_better(s2, k, bn, bk)) {
-        bn = s2;
-        bk = k;
-        bu = u;
-      }
+      d[u] = s2;
     }
-    if (lane == 0) {
-      wn[warp] = bn;
-      wk[warp] = bk;
-    }
+    const float n2 = qr_rs<CPW>(d);          // lane l: slot l / (32 / CPW)
+    const int us = lane / (32 / CPW);
+    const bool live = !((done >> us) & 1u);
+    const unsigned long long key = live ? qr_key(n2, col0 + kQrWarps * us) : 0ull;
+    const unsigned hi = (unsigned)(key >> 32), lo = (unsigned)key;
+    const unsigned mhi = __reduce_max_sync(0xffffffffu, hi);
+    const unsigned mlo = __reduce_max_sync(0xffffffffu, hi == mhi ? lo : 0u);
+    const unsigned long long wk = ((unsigned long long)mhi << 32) | mlo;
+    if (lane == 0 && wk) atomicMax(&s_key[par], wk);
     __syncthreads();
-    float cn = -1.f;
-    int ck = INT_MAX, cw = -1;
-    for (int q = 0; q < kQrWarps; ++q)
-      if (qr_better(wn[q], wk[q], cn, ck)) {
-        cn = wn[q];
-        ck = wk[q];
-        cw = q;
-      }
-    if (cw < 0) {  // every column of this CTA is pivoted: publish "none"
+    const unsigned long long bk = s_key[par];
+    if (bk == 0ull) {  // every column of this CTA is pivoted: publish "none"
       if (threadIdx.x < NC) {
         QrCand* dst = cl.map_shared_rank(&cand[par][z], (int)threadIdx.x);
         *dst = QrCand{-1.f, INT_MAX, 0.f, 0.f};
       }
       return;
     }
-    if (warp != cw) return;
+    const int ck = (int)(~(unsigned)bk);
+    const float cn = __uint_as_float((unsigned)(bk >> 32));
+    const int rel = ck - z * kQrWarps * CPW;
+    if (warp != rel % kQrWarps) return;
+    const int bu = rel / kQrWarps;
     const int j1 = j + 1;
     float x[RPL];
 #pragma unroll
@@ -1384,6 +1414,9 @@ __global__ void __launch_bounds__(kQrThreads, 1)
   for (int j = 0; j < c; ++j) {
     cl.sync();
     const int par = j & 1;
+    // the key publish(j - 1) filled (read before this step's cluster barrier;
+    // filled next by publish(j + 1), after the next one)
+    if (threadIdx.x == 0) s_key[par] = 0ull;
     QrCand b = cand[par][0];
     int zs = 0;
     for (int q = 1; q < NC; ++q) {
@@ -1401,9 +1434,20 @@ __global__ void __launch_bounds__(kQrThreads, 1)
       for (int i = threadIdx.x; i < c; i += kQrThreads) Hv[(size_t)j * c + i] = v[i];
       if (threadIdx.x == 0) tq[j] = b.tau;
     }
+    // w_u = tau v^T a_u for the warp's 8 columns at once, then a_u -= w_u v
+    // (pivoted columns have zero entries at rows >= j: no change)
+    float d[CPW];
 #pragma unroll
     for (int u = 0; u < CPW; ++u) {
-      if (done >> u & 1u) continue;
+      float s2 = 0.f;
+#pragma unroll
+      for (int t = 0; t < RPL; ++t) s2 = fmaf(vr[t], a[u][t], s2);
+      d[u] = s2;
+    }
+    const float wsum = qr_rs<CPW>(d) * b.tau;
+#pragma unroll
+    for (int u = 0; u < CPW; ++u) {
+      const float wu = __shfl_sync(0xffffffffu, wsum, qr_rs_lane<CPW>(u));
       const int k = col0 + kQrWarps * u;
       if (k == b.col) {  // the pivot column becomes beta e_j
 #pragma unroll
@@ -1412,14 +1456,10 @@ __global__ void __launch_bounds__(kQrThreads, 1)
           a[u][t] = i == j ? b.beta : (i > j ? 0.f : a[u][t]);
         }
         done |= 1u << u;
-        continue;
+      } else if (!((done >> u) & 1u)) {
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) a[u][t] = fmaf(-wu, vr[t], a[u][t]);
       }
-      float d = 0.f;
-#pragma unroll
-      for (int t = 0; t < RPL; ++t) d = fmaf(vr[t], a[u][t], d);
-      d = warp_sum(d) * b.tau;
-#pragma unroll
-      for (int t = 0; t < RPL; ++t) a[u][t] = fmaf(-d, vr[t], a[u][t]);
     }
     if (j + 1 < c) publish(j, par ^ 1);
   }
@@ -1475,16 +1515,22 @@ __global__ void __launch_bounds__(kQrThreads, 1)
       taun = __ldcg(&tq[j - 1]);
     }
     if (tau == 0.f) continue;
+    float d[CPW];
+#pragma unroll
+    for (int u = 0; u < CPW; ++u) {
+      float s2 = 0.f;
+#pragma unroll
+      for (int t = 0; t < RPL; ++t) s2 = fmaf(vr[t], a[u][t], s2);
+      d[u] = s2;
+    }
+    const float wsum = qr_rs<CPW>(d) * tau;
 #pragma unroll
     for (int u = 0; u < CPW; ++u) {
       const int k = col0 + kQrWarps * u;
+      const float wu = __shfl_sync(0xffffffffu, wsum, qr_rs_lane<CPW>(u));
       if (k < j || k >= c) continue;
-      float d = 0.f;
 #pragma unroll
-      for (int t = 0; t < RPL; ++t) d = fmaf(vr[t], a[u][t], d);
-      d = warp_sum(d) * tau;
-#pragma unroll
-      for (int t = 0; t < RPL; ++t) a[u][t] = fmaf(-d, vr[t], a[u][t]);
+      for (int t = 0; t < RPL; ++t) a[u][t] = fmaf(-wu, vr[t], a[u][t]);
     }
   }
   // V (cpad x cpad, ld cpad): Q in the leading c x c block
