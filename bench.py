@@ -202,7 +202,7 @@ def stage_roofline(info, peaks, src, refine_sweeps, phase1_sweeps):
         ach = prod_bytes / t / 1e9
         # DRAM bytes per launch from ncu (one A V launch of each kind, read +
         # write; the A^T W launches are taken to move the same bytes)
-        traffic = n_plain * 138.30e6 + n_split * 273.57e6
+        traffic = n_plain * 138.27e6 + n_split * 273.98e6
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                 "traffic": traffic, "traffic_scope": "DRAM bytes per solve, ncu per-launch counts x launches",
                 "kernel": "k_gemm_bf16_tc", "stage": "lowp_product",
@@ -418,7 +418,7 @@ def run_stage(args):
         for _ in range(2):
             rr.rr_pencil_svd(Bp, Gu, Gv)
     elif args.stage == "hessenberg":
-        W0 = torch.randn(b, M, device="cuda", dtype=torch.float32).t()  # M x b column-major
+        W0 = torch.randn(b, args.rows, device="cuda", dtype=torch.float32).t()  # rows x b column-major
         for _ in range(2):
             rr.rr_hessenberg(W0.clone(), qtype=torch.bfloat16)
     elif args.stage == "split":
@@ -463,7 +463,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--stage", choices=["pencil", "hessenberg", "gemm", "split", "f64emu", "prep"],
                     help="run one stage of the workload (profiling driver)")
-    ap.add_argument("--b", type=int, default=256, help="pencil size for --stage pencil")
+    ap.add_argument("--b", type=int, default=256, help="pencil size for --stage pencil, columns for hessenberg")
+    ap.add_argument("--rows", type=int, default=M, help="rows of the block for --stage hessenberg")
     args = ap.parse_args()
     if args.stage:
         return run_stage(args)
