@@ -664,34 +664,6 @@ rr_status lift_emu(cudaStream_t s, int64_t n, int64_t b, int32_t t1, const void*
 // one launch with exact FP32 sums over K chunks, FP64 partials per (pair, K
 // chunk), then a fixed-order FP64 reduction.
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void k_col_exp_t(int64_t m, const T* __restrict__ A, int64_t lda, int* __restrict__ e) {
-  const int64_t j = blockIdx.x;
-  int mx = -1100;
-  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) mx = max(mx, exp_bits(Ld<T>::f64(A + i + j * lda)));
-  __shared__ int sm[32];
-  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = mx;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    mx = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : -1100;
-    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (threadIdx.x == 0) e[j] = mx;
-  }
-}
-
-template <typename T>
-__global__ void k_slice_cols_t(int64_t m, int64_t n, const T* __restrict__ A, int64_t lda,
-                               const int* __restrict__ cexp, int S, __nv_bfloat16* __restrict__ out) {
-  const int64_t j = blockIdx.y;
-  const int e = cexp[j];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-    float sl[kMaxSlices];
-    slice_value(Ld<T>::f64(A + i + j * lda), e, S, sl);
-    for (int p = 0; p < S; ++p) out[(size_t)p * m * n + i + j * m] = __float2bfloat16_rn(sl[p]);
-  }
-}
-
 __global__ void k_emu_reduce(int64_t p, int64_t q, int64_t nparts, const double* __restrict__ part,
                              double* __restrict__ G, int64_t ldg, int accum) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -730,12 +702,59 @@ size_t emu_gram_bytes(int64_t n, int64_t p, int64_t q) {
          align_up((size_t)q * 4) + align_up((size_t)(np * smax) * p * q * 8) + 256;
 }
 
+// Column exponents and column-scaled slices of a Gram operand (n x c, any
+// storage type, n % 8 == 0): a thread takes 8 consecutive rows of one column,
+// the values reach FP64 exactly through integer operations (exact_f64), and
+// each slice's 8 digits leave as one 16-byte store.
+template <typename T>
+__global__ void k_col_exp8(int64_t n, const T* __restrict__ X, int64_t ldx, int* __restrict__ e) {
+  const int64_t j = blockIdx.x;
+  int mx = kExpNone;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) mx = max(mx, exp_bits(exact_f64<T>(X[i + j * ldx])));
+  __shared__ int sm[32];
+  mx = __reduce_max_sync(0xffffffffu, mx);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    mx = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : kExpNone;
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if (threadIdx.x == 0) e[j] = mx;
+  }
+}
+
+template <typename T>
+__global__ void k_slice_cols8(int64_t n, int64_t c, const T* __restrict__ X, int64_t ldx,
+                              const int* __restrict__ cexp, __nv_bfloat16* __restrict__ out) {
+  constexpr int S = kGramSlices;
+  const int64_t j = blockIdx.y;
+  const int e = cexp[j];
+  const size_t plane = (size_t)n * c;
+  for (int64_t i0 = 8 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x); i0 < n;
+       i0 += 8 * (int64_t)gridDim.x * blockDim.x) {
+    unsigned pk[S][4];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      float sl[S];
+      slice_value(exact_f64<T>(X[i0 + r + j * ldx]), e, S, sl);
+#pragma unroll
+      for (int q = 0; q < S; ++q) {
+        const unsigned bb = bf16_bits_exact(sl[q]);
+        if (r & 1) pk[q][r >> 1] |= bb << 16;
+        else pk[q][r >> 1] = bb;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < S; ++q)
+      *reinterpret_cast<uint4*>(out + q * plane + j * n + i0) = make_uint4(pk[q][0], pk[q][1], pk[q][2], pk[q][3]);
+  }
+}
+
 template <typename T>
 static void emu_slice_block(cudaStream_t s, int64_t n, int64_t c, const T* X, int64_t ldx, int* e,
                             __nv_bfloat16* out) {
-  k_col_exp_t<T><<<(unsigned)c, 512, 0, s>>>(n, X, ldx, e);
-  dim3 g((unsigned)std::min<int64_t>((n + 255) / 256, 1024), (unsigned)c);
-  k_slice_cols_t<T><<<g, 256, 0, s>>>(n, c, X, ldx, e, kGramSlices, out);
+  k_col_exp8<T><<<(unsigned)c, 512, 0, s>>>(n, X, ldx, e);
+  dim3 g((unsigned)std::min<int64_t>((n / 8 + 127) / 128, 1024), (unsigned)c);
+  k_slice_cols8<T><<<g, 128, 0, s>>>(n, c, X, ldx, e, out);
 }
 
 static void emu_slice_any(cudaStream_t s, int32_t t, int64_t n, int64_t c, const void* X, int64_t ldx,
@@ -764,11 +783,12 @@ rr_status emu_gram(cudaStream_t s, int64_t n, int64_t p, int64_t q, int32_t xt, 
   double* part = ar.take<double>((size_t)np * splits * p * q);
   if (ar.overflow) return RR_ERR_WORKSPACE;
   emu_slice_any(s, xt, n, p, X, ldx, ex, Xs);
-  emu_slice_any(s, yt, n, q, Y, ldy, ey, Ys);
-  note_launches(3);
+  const bool same = X == Y && xt == yt && ldx == ldy && p == q;  // X^T X: slice once
+  if (!same) emu_slice_any(s, yt, n, q, Y, ldy, ey, Ys);
+  note_launches(same ? 1 : 3);
   RR_TRY(check_launch("emu_gram slices"));
-  TcEmu e{nullptr, 0, part, ex, ey, (int)q, S, S, (int)p, (int)q, np, pairs, kGramKChunk};
-  RR_TRY(gemm_bf16_tc_emu(p, 2 * q, n, Xs, n, Ys, n, e, s));
+  TcEmu e{nullptr, 0, part, ex, same ? ex : ey, (int)q, S, S, (int)p, (int)q, np, pairs, kGramKChunk};
+  RR_TRY(gemm_bf16_tc_emu(p, 2 * q, n, Xs, n, same ? Xs : Ys, n, e, s));
   k_emu_reduce<<<(unsigned)((p * q + 255) / 256), 256, 0, s>>>(p, q, (int64_t)np * splits, part, G, ldg, accum);
   return check_launch("emu_gram reduce");
 }

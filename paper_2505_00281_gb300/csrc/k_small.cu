@@ -88,61 +88,119 @@ __global__ void __launch_bounds__(kSmallThreads) k_tri_inv_lower(int b, const do
   }
 }
 
-// C = alpha op(A) op(B) + beta C for the small projected matrices (FP64
-// operands and result).  TA is the arithmetic: double, or float for
-// correction terms whose own size is small, so that FP32 relative accuracy
-// of the product is FP64 accuracy of the result (operands rounded to FP32,
-// FP32 accumulation, FP64 combination with beta C).  16 x 16 output tiles,
-// one output per thread, so a 256 x 256 product spreads over 256 CTAs (FP64
-// issue rate per SM is the limit on GB300, so the work must cover the GPU);
-// K in panels of KP staged in shared memory with all of a panel's loads in
-// flight at once.
+// Small products C = alpha op(A) op(B) + beta C (op = transpose when ta / tb),
+// 16 x 16 output tiles, one output per thread, K in panels of KP staged in
+// shared memory with all of a panel's loads in flight at once.  On GB300 the
+// FP64 units of an SM are the limit (a 16 x 16 x 256 tile is 65k FP64 FMAs,
+// ~16 us on one SM), so the work is cut into (tile, K-range) pieces spread
+// evenly over the SMs: 1-D grid of ntiles x ks CTAs; with ks > 1 (beta = 0)
+// the K ranges' partial sums add into a zeroed C with FP64 atomics.  sym:
+// the result is symmetric (M == N): only tiles with bx <= by are computed,
+// the off-diagonal ones write their mirror image too.
 template <typename TA, int KP>
 __global__ void __launch_bounds__(256) k_gemm_small(int ta, int tb, int M, int N, int K, double alpha,
                                                     const double* __restrict__ A, int lda,
                                                     const double* __restrict__ B, int ldb, double beta,
-                                                    double* __restrict__ C, int ldc) {
+                                                    double* __restrict__ C, int ldc, int sym, int ks, int kc) {
+  const int tm = (M + 15) / 16;
+  const int tile = blockIdx.x / ks, split = blockIdx.x - tile * ks;
+  int bx, by;
+  if (sym) {  // tile = by (by + 1) / 2 + bx, bx <= by
+    by = (int)((sqrtf(8.f * (float)tile + 1.f) - 1.f) * 0.5f);
+    while ((by + 1) * (by + 2) / 2 <= tile) ++by;
+    while (by * (by + 1) / 2 > tile) --by;
+    bx = tile - by * (by + 1) / 2;
+  } else {
+    bx = tile % tm;
+    by = tile / tm;
+  }
   __shared__ TA As[KP][17];
   __shared__ TA Bs[KP][17];
-  const int m0 = blockIdx.x * 16, n0 = blockIdx.y * 16;
+  const int m0 = bx * 16, n0 = by * 16;
+  const int kbeg = split * kc, kend = min(K, kbeg + kc);
   const int tid = threadIdx.x, ti = tid % 16, tj = tid / 16;
   TA acc = TA(0);
-  for (int k0 = 0; k0 < K; k0 += KP) {
+  for (int k0 = kbeg; k0 < kend; k0 += KP) {
     for (int e = tid; e < KP * 16; e += 256) {
       // consecutive threads along the operand's contiguous dimension
       const int ka = ta ? e % KP : e / 16, ia = ta ? e / KP : e % 16;
       const int gk = k0 + ka, gi = m0 + ia;
-      As[ka][ia] = (gk < K && gi < M) ? (TA)(ta ? A[gk + (size_t)gi * lda] : A[gi + (size_t)gk * lda]) : TA(0);
+      As[ka][ia] = (gk < kend && gi < M) ? (TA)(ta ? A[gk + (size_t)gi * lda] : A[gi + (size_t)gk * lda]) : TA(0);
       const int kb = tb ? e / 16 : e % KP, jb = tb ? e % 16 : e / KP;
       const int gkb = k0 + kb, gj = n0 + jb;
-      Bs[kb][jb] = (gkb < K && gj < N) ? (TA)(tb ? B[gj + (size_t)gkb * ldb] : B[gkb + (size_t)gj * ldb]) : TA(0);
+      Bs[kb][jb] = (gkb < kend && gj < N) ? (TA)(tb ? B[gj + (size_t)gkb * ldb] : B[gkb + (size_t)gj * ldb]) : TA(0);
     }
     __syncthreads();
-    const int kn = K - k0 < KP ? K - k0 : KP;
+    const int kn = kend - k0 < KP ? kend - k0 : KP;
 #pragma unroll 8
     for (int kk = 0; kk < kn; ++kk) acc = fma(As[kk][ti], Bs[kk][tj], acc);
     __syncthreads();
   }
   const int i = m0 + ti, j = n0 + tj;
   if (i < M && j < N) {
-    double v = alpha * (double)acc;
-    if (beta != 0.0) v += beta * C[i + (size_t)j * ldc];
-    C[i + (size_t)j * ldc] = v;
+    const double v0 = alpha * (double)acc;
+    if (ks > 1) {
+      atomicAdd(C + i + (size_t)j * ldc, v0);
+      if (sym && bx != by) atomicAdd(C + j + (size_t)i * ldc, v0);
+    } else {
+      double v = v0;
+      if (beta != 0.0) v += beta * C[i + (size_t)j * ldc];
+      C[i + (size_t)j * ldc] = v;
+      if (sym && bx != by) C[j + (size_t)i * ldc] = v;
+    }
   }
+}
+
+__global__ void k_zero_small(int M, int N, double* __restrict__ C, int ldc) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < M * N; e += gridDim.x * blockDim.x)
+    C[e % M + (size_t)(e / M) * ldc] = 0.0;
+}
+
+template <typename TA, int KP>
+static void gemm_small_launch(cudaStream_t s, int ta, int tb, int M, int N, int K, double alpha,
+                              const double* A, int lda, const double* B, int ldb, double beta, double* C,
+                              int ldc, int sym) {
+  const int tm = (M + 15) / 16, tn = (N + 15) / 16;
+  const int ntiles = sym ? tm * (tm + 1) / 2 : tm * tn;
+  // about six CTAs per SM, each K range at least 64 long
+  int ks = 1;
+  if (beta == 0.0) {
+    const int want = (6 * num_sms() + ntiles - 1) / ntiles;
+    const int most = K / 64 > 1 ? K / 64 : 1;
+    ks = want < most ? want : most;
+    if (ks < 1) ks = 1;
+  }
+  const int kc = (K + ks - 1) / ks;
+  ks = (K + kc - 1) / kc;
+  if (ks > 1) {
+    k_zero_small<<<(M * N + 255) / 256, 256, 0, s>>>(M, N, C, ldc);
+    note_launches(1);
+  }
+  k_gemm_small<TA, KP><<<ntiles * ks, 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sym, ks,
+                                                   kc);
 }
 
 static void gemm_small(cudaStream_t s, int ta, int tb, int M, int N, int K, double alpha,
                        const double* A, int lda, const double* B, int ldb, double beta, double* C,
                        int ldc) {
-  dim3 g((M + 15) / 16, (N + 15) / 16);
-  k_gemm_small<double, 128><<<g, 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  gemm_small_launch<double, 128>(s, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, 0);
+}
+
+// C (n x n) = A^T B for a product known to be symmetric (W^T G W, N^T N,
+// V^T V): half the tiles
+static void gemm_small_sym(cudaStream_t s, int n, int K, const double* A, int lda, const double* B, int ldb,
+                           double* C, int ldc) {
+  gemm_small_launch<double, 128>(s, 1, 0, n, n, K, 1.0, A, lda, B, ldb, 0.0, C, ldc, 1);
 }
 
 static void gemm_mixed(cudaStream_t s, int ta, int tb, int M, int N, int K, double alpha,
                        const double* A, int lda, const double* B, int ldb, double beta, double* C,
                        int ldc) {
-  dim3 g((M + 15) / 16, (N + 15) / 16);
-  k_gemm_small<float, 256><<<g, 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  // FP32 products are not FP64-unit bound: whole-K tiles
+  dim3 g((unsigned)(((M + 15) / 16) * ((N + 15) / 16)));
+  const int tm = (M + 15) / 16;
+  (void)tm;
+  k_gemm_small<float, 256><<<g, 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, 0, 1, K);
 }
 
 // Symmetrise C, shift it to positive definite by a Gershgorin bound
@@ -1142,7 +1200,7 @@ static void whiten(cudaStream_t s, int b, const double* G, PencilWs& w, int* dro
   double* Wn = w.W2;
   for (int it = 0; it < 3; ++it) {
     gemm_small(s, 0, 0, b, b, b, 1.0, G, b, Wc, b, 0.0, w.T, b);        // T = G W
-    gemm_small(s, 1, 0, b, b, b, 1.0, Wc, b, w.T, b, 0.0, w.E, b);      // E = W^T T
+    gemm_small_sym(s, b, b, Wc, b, w.T, b, w.E, b);                       // E = W^T T (symmetric)
     k_whiten_corr<<<g1, 256, 0, s>>>(b, w.E, nullptr, dropped, nullptr, 0);
     gemm_mixed(s, 0, 0, b, b, b, 1.0, w.E, b, w.E, b, 0.0, w.E2, b);    // E^2
     k_whiten_corr<<<g1, 256, 0, s>>>(b, w.E, w.E2, dropped, w.F, 1);    // F = E/2 - 3/8 E^2
@@ -1845,8 +1903,8 @@ static rr_status jacobi_svd(cudaStream_t s, int r, int c, const double* C, Penci
     RR_CUDA(cudaFuncSetAttribute(k_cluster_rot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
   for (int it = 0; it < 4; ++it) {
     gemm_small(s, 0, 0, r, c, c, 1.0, C, r, w.V, c, 0.0, w.Mp, r);          // N = C V
-    gemm_small(s, 1, 0, c, c, r, 1.0, w.Mp, r, w.Mp, r, 0.0, w.E2, c);      // K = N^T N
-    gemm_small(s, 1, 0, c, c, c, 1.0, w.V, c, w.V, c, 0.0, w.T, c);         // T = V^T V
+    gemm_small_sym(s, c, r, w.Mp, r, w.Mp, r, w.E2, c);                     // K = N^T N
+    gemm_small_sym(s, c, c, w.V, c, w.V, c, w.T, c);                        // T = V^T V
     k_cluster_rot<<<1, 1024, csm, s>>>(c, w.E2, w.T, w.F, w.cid, w.order, w.cst);  // Qb
     k_oa_update<<<gc, 256, 0, s>>>(c, w.E2, w.T, w.cid, w.Vp, w.E);         // F1, W
     gemm_mixed(s, 0, 0, c, c, c, 0.5, w.E, c, w.E, c, 1.0, w.Vp, c);        // F1 += W^2 / 2
@@ -1901,7 +1959,7 @@ extern "C" rr_status rr_pencil_eig(int64_t b, const double* H, const double* G, 
   whiten(s, n, G, w, w.drop1, w.W1);
   // C = W^T H W, symmetrised and shifted positive definite (C - mu I)
   gemm_small(s, 0, 0, n, n, n, 1.0, H, n, w.W1, n, 0.0, w.T, n);
-  gemm_small(s, 1, 0, n, n, n, 1.0, w.W1, n, w.T, n, 0.0, w.C, n);
+  gemm_small_sym(s, n, n, w.W1, n, w.T, n, w.C, n);  // W^T H W (symmetric)
   k_eig_prep<<<1, kSmallThreads, 0, s>>>(n, w.C, w.drop1, w.mu);
   RR_TRY(jacobi_svd(s, n, n, w.C, w, w.M, w.V));
   k_colnorm_sort<<<1, kSmallThreads, n * sizeof(double), s>>>(n, n, w.M, n, w.sig, w.order);
