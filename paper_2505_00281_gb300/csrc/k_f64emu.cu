@@ -473,6 +473,81 @@ rr_status emu_prepare(cudaStream_t s, const double* A, int64_t m, int64_t n, int
   return RR_OK;
 }
 
+// exact FP64 value of a stored entry, through integer operations (FP32 / BF16
+// to FP64 conversions would use the few FP64 units)
+__device__ __forceinline__ double f32_to_f64_exact(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned E = (u >> 23) & 0xFFu;
+  if (E == 0 || E == 255) return (double)f;  // zero, subnormal, Inf / NaN
+  return __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) |
+                                          ((unsigned long long)(E + 896) << 52) |
+                                          ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+template <typename T> __device__ __forceinline__ double exact_f64(T v);
+template <> __device__ __forceinline__ double exact_f64<double>(double v) { return v; }
+template <> __device__ __forceinline__ double exact_f64<float>(float v) { return f32_to_f64_exact(v); }
+template <> __device__ __forceinline__ double exact_f64<__nv_bfloat16>(__nv_bfloat16 v) {
+  return f32_to_f64_exact(__bfloat162float(v));
+}
+
+constexpr int kGramSlices = 8;
+constexpr int kGramKChunk = 4096;
+
+// Column exponents and column-scaled slices of a Gram operand (n x c, any
+// storage type, n % 8 == 0): a thread takes 8 consecutive rows of one column,
+// the values reach FP64 exactly through integer operations (exact_f64), and
+// each slice's 8 digits leave as one 16-byte store.
+template <typename T>
+__global__ void k_col_exp8(int64_t n, const T* __restrict__ X, int64_t ldx, int* __restrict__ e) {
+  const int64_t j = blockIdx.x;
+  int mx = kExpNone;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) mx = max(mx, exp_bits(exact_f64<T>(X[i + j * ldx])));
+  __shared__ int sm[32];
+  mx = __reduce_max_sync(0xffffffffu, mx);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    mx = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : kExpNone;
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if (threadIdx.x == 0) e[j] = mx;
+  }
+}
+
+template <typename T>
+__global__ void k_slice_cols8(int64_t n, int64_t c, const T* __restrict__ X, int64_t ldx,
+                              const int* __restrict__ cexp, __nv_bfloat16* __restrict__ out) {
+  constexpr int S = kGramSlices;
+  const int64_t j = blockIdx.y;
+  const int e = cexp[j];
+  const size_t plane = (size_t)n * c;
+  for (int64_t i0 = 8 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x); i0 < n;
+       i0 += 8 * (int64_t)gridDim.x * blockDim.x) {
+    unsigned pk[S][4];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      float sl[S];
+      slice_value(exact_f64<T>(X[i0 + r + j * ldx]), e, S, sl);
+#pragma unroll
+      for (int q = 0; q < S; ++q) {
+        const unsigned bb = bf16_bits_exact(sl[q]);
+        if (r & 1) pk[q][r >> 1] |= bb << 16;
+        else pk[q][r >> 1] = bb;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < S; ++q)
+      *reinterpret_cast<uint4*>(out + q * plane + j * n + i0) = make_uint4(pk[q][0], pk[q][1], pk[q][2], pk[q][3]);
+  }
+}
+
+template <typename T>
+static void emu_slice_block(cudaStream_t s, int64_t n, int64_t c, const T* X, int64_t ldx, int* e,
+                            __nv_bfloat16* out) {
+  k_col_exp8<T><<<(unsigned)c, 512, 0, s>>>(n, X, ldx, e);
+  dim3 g((unsigned)std::min<int64_t>((n / 8 + 127) / 128, 1024), (unsigned)c);
+  k_slice_cols8<T><<<g, 128, 0, s>>>(n, c, X, ldx, e, out);
+}
+
 // The slice pairs (p, q), p + q <= S + 1 (1-based), grouped by p into runs
 // of one or two consecutive q: pair codes p0 | q0 << 8 | nq << 16 (0-based).
 static int emu_pairs(int S, bool two, uint32_t* out) {
@@ -498,9 +573,13 @@ rr_status emu_gemm(cudaStream_t s, const EmuOperator& op, int trans, int64_t N, 
   Arena ar(mem, emu_block_bytes(K, N, S));
   __nv_bfloat16* T = (__nv_bfloat16*)ar.take_bytes((size_t)S * K * N * 2);
   int* xe = ar.take<int>(N);
-  k_col_exp<<<(unsigned)N, 512, 0, s>>>(K, X, ldx, xe);
-  dim3 g((unsigned)std::min<int64_t>((K + 255) / 256, 1024), (unsigned)N);
-  k_slice_cols<<<g, 256, 0, s>>>(K, N, X, ldx, xe, S, T);
+  if (S == kGramSlices && K % 8 == 0) {
+    emu_slice_block<double>(s, K, N, X, ldx, xe, T);
+  } else {
+    k_col_exp<<<(unsigned)N, 512, 0, s>>>(K, X, ldx, xe);
+    dim3 g((unsigned)std::min<int64_t>((K + 255) / 256, 1024), (unsigned)N);
+    k_slice_cols<<<g, 256, 0, s>>>(K, N, X, ldx, xe, S, T);
+  }
   dim3 gz((unsigned)std::min<int64_t>((M + 255) / 256, 1024), (unsigned)N);
   k_zero_f64<<<gz, 256, 0, s>>>(M, N, C, ldc);
   note_launches(2);
@@ -529,54 +608,50 @@ rr_status emu_gemm(cudaStream_t s, const EmuOperator& op, int trans, int64_t N, 
 // product A_cat(:, 0:(d-1)K) Y_rev((S-d+1)K : S K, :) whose epilogue adds
 // 2^(e_row + e_col - 6d) times it into X: S launches instead of one per pair.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double f32_to_f64_exact(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned E = (u >> 23) & 0xFFu;
-  if (E == 0 || E == 255) return (double)f;  // zero, subnormal, Inf / NaN
-  return __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) |
-                                          ((unsigned long long)(E + 896) << 52) |
-                                          ((unsigned long long)(u & 0x7FFFFFu) << 29)));
-}
-template <typename T> __device__ __forceinline__ double exact_f64(T v);
-template <> __device__ __forceinline__ double exact_f64<double>(double v) { return v; }
-template <> __device__ __forceinline__ double exact_f64<float>(float v) { return f32_to_f64_exact(v); }
-template <> __device__ __forceinline__ double exact_f64<__nv_bfloat16>(__nv_bfloat16 v) {
-  return f32_to_f64_exact(__bfloat162float(v));
+
+// Row exponents of [S1 S2] (atomic max over 32-column chunks; rexp starts at
+// kExpNone), then the row-scaled slices: a thread takes 8 rows of an
+// 8-column group, lane = row (coalesced column loads), and writes each
+// slice's 8 digits of a row as one 16-byte store.  K % 8 == 0.
+template <typename T1, typename T2>
+__global__ void k_lift_rexp(int64_t n, int p1, const T1* __restrict__ S1, int64_t ld1, int p2,
+                            const T2* __restrict__ S2, int64_t ld2, int* __restrict__ rexp) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int K = p1 + p2, k0 = blockIdx.y * 32, k1 = min(K, k0 + 32);
+  int e = kExpNone;
+  for (int kk = k0; kk < k1; ++kk)
+    e = max(e, exp_bits(kk < p1 ? exact_f64<T1>(S1[i + kk * ld1]) : exact_f64<T2>(S2[i + (kk - p1) * ld2])));
+  atomicMax(rexp + i, e);
 }
 
-// one thread per row (lane = row: the column loads are coalesced); K % 8 == 0
 template <typename T1, typename T2>
-__global__ void __launch_bounds__(64) k_lift_slices(int64_t n, int p1, const T1* __restrict__ S1, int64_t ld1,
-                                                    int p2, const T2* __restrict__ S2, int64_t ld2,
-                                                    int* __restrict__ rexp, __nv_bfloat16* __restrict__ out) {
+__global__ void __launch_bounds__(128) k_lift_slices(int64_t n, int p1, const T1* __restrict__ S1, int64_t ld1,
+                                                     int p2, const T2* __restrict__ S2, int64_t ld2,
+                                                     const int* __restrict__ rexp, __nv_bfloat16* __restrict__ out) {
   constexpr int S = 8;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int K = p1 + p2;
-  int e = kExpNone;
-  for (int kk = 0; kk < p1; ++kk) e = max(e, exp_bits(exact_f64<T1>(S1[i + kk * ld1])));
-  for (int kk = 0; kk < p2; ++kk) e = max(e, exp_bits(exact_f64<T2>(S2[i + kk * ld2])));
-  rexp[i] = e;
-  __nv_bfloat16* row = out + i * (int64_t)(S * K);
-  for (int k0 = 0; k0 < K; k0 += 8) {
-    unsigned pk[S][4];
+  const int K = p1 + p2, k0 = blockIdx.y * 8;
+  const int e = rexp[i];
+  unsigned pk[S][4];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const int kk = k0 + c;
-      const double x = kk < p1 ? exact_f64<T1>(S1[i + kk * ld1]) : exact_f64<T2>(S2[i + (kk - p1) * ld2]);
-      float sl[S];
-      slice_value(x, e, S, sl);
+  for (int c = 0; c < 8; ++c) {
+    const int kk = k0 + c;
+    const double x = kk < p1 ? exact_f64<T1>(S1[i + kk * ld1]) : exact_f64<T2>(S2[i + (kk - p1) * ld2]);
+    float sl[S];
+    slice_value(x, e, S, sl);
 #pragma unroll
-      for (int q = 0; q < S; ++q) {
-        const unsigned bb = bf16_bits_exact(sl[q]);
-        if (c & 1) pk[q][c >> 1] |= bb << 16;
-        else pk[q][c >> 1] = bb;
-      }
+    for (int q = 0; q < S; ++q) {
+      const unsigned bb = bf16_bits_exact(sl[q]);
+      if (c & 1) pk[q][c >> 1] |= bb << 16;
+      else pk[q][c >> 1] = bb;
     }
-#pragma unroll
-    for (int q = 0; q < S; ++q)
-      *reinterpret_cast<uint4*>(row + q * K + k0) = make_uint4(pk[q][0], pk[q][1], pk[q][2], pk[q][3]);
   }
+  __nv_bfloat16* row = out + i * (int64_t)(S * K);
+#pragma unroll
+  for (int q = 0; q < S; ++q)
+    *reinterpret_cast<uint4*>(row + q * K + k0) = make_uint4(pk[q][0], pk[q][1], pk[q][2], pk[q][3]);
 }
 
 // Y_rev (S K x b, column-major): column j holds Y(:, j)'s digit blocks,
@@ -600,20 +675,27 @@ size_t lift_emu_bytes(int64_t n, int64_t b, int64_t K) {
          align_up((size_t)b * 4) + 256;
 }
 
+template <typename T1, typename T2>
+static void launch_lift_slices2(cudaStream_t s, int64_t n, int p1, const T1* S1, int64_t ld1, int p2, const T2* S2,
+                                int64_t ld2, int* rexp, __nv_bfloat16* out) {
+  const int K = p1 + p2;
+  k_exp_init<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, s>>>(n, rexp);
+  k_lift_rexp<T1, T2><<<dim3((unsigned)((n + 255) / 256), (unsigned)((K + 31) / 32)), 256, 0, s>>>(
+      n, p1, S1, ld1, p2, S2, ld2, rexp);
+  k_lift_slices<T1, T2><<<dim3((unsigned)((n + 127) / 128), (unsigned)(K / 8)), 128, 0, s>>>(n, p1, S1, ld1, p2, S2,
+                                                                                              ld2, rexp, out);
+  note_launches(2);
+}
+
 template <typename T1>
 static void launch_lift_slices(cudaStream_t s, int64_t n, int p1, const T1* S1, int64_t ld1, int p2, int32_t t2,
                                const void* S2, int64_t ld2, int* rexp, __nv_bfloat16* out) {
-  const unsigned g = (unsigned)((n + 63) / 64);
   switch (t2) {
-    case RR_F32:
-      k_lift_slices<T1, float><<<g, 64, 0, s>>>(n, p1, S1, ld1, p2, (const float*)S2, ld2, rexp, out);
-      break;
+    case RR_F32: launch_lift_slices2<T1, float>(s, n, p1, S1, ld1, p2, (const float*)S2, ld2, rexp, out); break;
     case RR_BF16:
-      k_lift_slices<T1, __nv_bfloat16><<<g, 64, 0, s>>>(n, p1, S1, ld1, p2, (const __nv_bfloat16*)S2, ld2, rexp, out);
+      launch_lift_slices2<T1, __nv_bfloat16>(s, n, p1, S1, ld1, p2, (const __nv_bfloat16*)S2, ld2, rexp, out);
       break;
-    default:
-      k_lift_slices<T1, double><<<g, 64, 0, s>>>(n, p1, S1, ld1, p2, (const double*)S2, ld2, rexp, out);
-      break;
+    default: launch_lift_slices2<T1, double>(s, n, p1, S1, ld1, p2, (const double*)S2, ld2, rexp, out); break;
   }
 }
 
@@ -675,8 +757,6 @@ __global__ void k_emu_reduce(int64_t p, int64_t q, int64_t nparts, const double*
   G[i + j * ldg] = s;
 }
 
-constexpr int kGramSlices = 8;
-constexpr int kGramKChunk = 4096;
 
 static int emu_gram_npairs() {
   uint32_t pr[64];
@@ -700,61 +780,6 @@ size_t emu_gram_bytes(int64_t n, int64_t p, int64_t q) {
   if (smax > nk) smax = nk;
   return align_up((size_t)S * n * p * 2) + align_up((size_t)S * n * q * 2) + align_up((size_t)p * 4) +
          align_up((size_t)q * 4) + align_up((size_t)(np * smax) * p * q * 8) + 256;
-}
-
-// Column exponents and column-scaled slices of a Gram operand (n x c, any
-// storage type, n % 8 == 0): a thread takes 8 consecutive rows of one column,
-// the values reach FP64 exactly through integer operations (exact_f64), and
-// each slice's 8 digits leave as one 16-byte store.
-template <typename T>
-__global__ void k_col_exp8(int64_t n, const T* __restrict__ X, int64_t ldx, int* __restrict__ e) {
-  const int64_t j = blockIdx.x;
-  int mx = kExpNone;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) mx = max(mx, exp_bits(exact_f64<T>(X[i + j * ldx])));
-  __shared__ int sm[32];
-  mx = __reduce_max_sync(0xffffffffu, mx);
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = mx;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    mx = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : kExpNone;
-    mx = __reduce_max_sync(0xffffffffu, mx);
-    if (threadIdx.x == 0) e[j] = mx;
-  }
-}
-
-template <typename T>
-__global__ void k_slice_cols8(int64_t n, int64_t c, const T* __restrict__ X, int64_t ldx,
-                              const int* __restrict__ cexp, __nv_bfloat16* __restrict__ out) {
-  constexpr int S = kGramSlices;
-  const int64_t j = blockIdx.y;
-  const int e = cexp[j];
-  const size_t plane = (size_t)n * c;
-  for (int64_t i0 = 8 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x); i0 < n;
-       i0 += 8 * (int64_t)gridDim.x * blockDim.x) {
-    unsigned pk[S][4];
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      float sl[S];
-      slice_value(exact_f64<T>(X[i0 + r + j * ldx]), e, S, sl);
-#pragma unroll
-      for (int q = 0; q < S; ++q) {
-        const unsigned bb = bf16_bits_exact(sl[q]);
-        if (r & 1) pk[q][r >> 1] |= bb << 16;
-        else pk[q][r >> 1] = bb;
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < S; ++q)
-      *reinterpret_cast<uint4*>(out + q * plane + j * n + i0) = make_uint4(pk[q][0], pk[q][1], pk[q][2], pk[q][3]);
-  }
-}
-
-template <typename T>
-static void emu_slice_block(cudaStream_t s, int64_t n, int64_t c, const T* X, int64_t ldx, int* e,
-                            __nv_bfloat16* out) {
-  k_col_exp8<T><<<(unsigned)c, 512, 0, s>>>(n, X, ldx, e);
-  dim3 g((unsigned)std::min<int64_t>((n / 8 + 127) / 128, 1024), (unsigned)c);
-  k_slice_cols8<T><<<g, 128, 0, s>>>(n, c, X, ldx, e, out);
 }
 
 static void emu_slice_any(cudaStream_t s, int32_t t, int64_t n, int64_t c, const void* X, int64_t ldx,
