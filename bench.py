@@ -430,6 +430,41 @@ def run_stage(args):
         Xl = rr.fortran((Xf - Xh.float()).to(torch.bfloat16))
         for _ in range(2):
             rr.rr_gemm_lowp_split(M, B, N, Ah, Al, N, Xh, Xl, N)
+    elif args.stage == "cheb":
+        # the sparse workload's filter step: H = -Lap + diag(v) on the 1024 x 1024 grid
+        # (n = 1,048,576, 5-point stencil, FP32 values), block 160 in BF16
+        Ng, bs = 1024, 160
+        rp, ci, va, _ = wl.grid_schrodinger_csr(Ng, 10.0, 3001)
+        n = Ng * Ng
+        d_rp, d_ci, d_va = (torch.from_numpy(a).cuda() for a in (rp, ci, va))
+        Y0 = rr.fortran(torch.randn(bs, n, device="cuda", dtype=torch.float32).t().to(torch.bfloat16))
+        Y1 = rr.fortran(torch.randn(bs, n, device="cuda", dtype=torch.float32).t().to(torch.bfloat16))
+        Y2 = rr.fortran(torch.empty(bs, n, device="cuda", dtype=torch.bfloat16).t())
+        L = rr.lib()
+        bf = rr.api.DTYPES[torch.bfloat16]
+        stream = torch.cuda.current_stream().cuda_stream
+
+        def step():  # the C entry point on preallocated blocks (no allocation in the timed loop)
+            rc = L.rr_chebyshev_step(n, bs, d_rp.data_ptr(), d_ci.data_ptr(), d_va.data_ptr(), bf, Y1.data_ptr(),
+                                     Y0.data_ptr(), n, 0.1, 6.0, 0.5, None, None, 0, None, bf, Y2.data_ptr(), n,
+                                     stream)
+            assert rc == 0, rc
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        reps = 10
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) * 1e3 / reps
+        nbytes = 4 * (n + 1) + 8 * len(ci) + 3 * 2 * n * bs  # CSR, Y_cur, Y_prev, Y_next
+        print(json.dumps({"stage": "cheb", "n": n, "nnz": int(len(ci)), "b": bs, "us_per_step": us,
+                          "algorithmic_bytes": nbytes, "achieved_gbs": nbytes / us / 1e3}))
+        del Y2
     elif args.stage == "prep":
         A = torch.randn(N, M, device="cuda", dtype=torch.float64).t()   # M x N column-major
         X = rr.fortran(torch.randn(N, B, device="cuda", dtype=torch.float64))
@@ -461,7 +496,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--stage", choices=["pencil", "hessenberg", "gemm", "split", "f64emu", "prep"],
+    ap.add_argument("--stage", choices=["pencil", "hessenberg", "gemm", "split", "f64emu", "prep", "cheb"],
                     help="run one stage of the workload (profiling driver)")
     ap.add_argument("--b", type=int, default=256, help="pencil size for --stage pencil, columns for hessenberg")
     ap.add_argument("--rows", type=int, default=M, help="rows of the block for --stage hessenberg")

@@ -30,6 +30,11 @@ def fortran(t: torch.Tensor) -> torch.Tensor:
     return t.t().contiguous().t()
 
 
+def empty_f(rows: int, cols: int, dtype, device) -> torch.Tensor:
+    """Uninitialised column-major (stride (1, rows)) tensor, allocated as such (no copy)."""
+    return torch.empty(cols, rows, dtype=dtype, device=device).t()
+
+
 def ld_of(t: torch.Tensor) -> int:
     if t.dim() == 1:
         return max(1, t.shape[0])
@@ -101,7 +106,7 @@ def rr_eig(op: RrOperator, params: RrParams, n: int, device="cuda", stream=None,
     L = lib()
     k = params.k
     theta = torch.empty(k, dtype=torch.float64, device=device)
-    X = fortran(torch.empty(n, k, dtype=torch.float64, device=device))
+    X = empty_f(n, k, torch.float64, device)
     wsb = L.rr_workspace_size(ctypes.byref(op), ctypes.byref(params), 0)
     if wsb == 0:
         raise RrError("rr_workspace_size", RR.ERR_ARG)
@@ -119,8 +124,8 @@ def rr_svd(op: RrOperator, params: RrParams, device="cuda", stream=None, ws=None
     L = lib()
     k, m, n = params.k, op.m, op.n
     sigma = torch.empty(k, dtype=torch.float64, device=device)
-    U = fortran(torch.empty(m, k, dtype=torch.float64, device=device))
-    V = fortran(torch.empty(n, k, dtype=torch.float64, device=device))
+    U = empty_f(m, k, torch.float64, device)
+    V = empty_f(n, k, torch.float64, device)
     wsb = L.rr_workspace_size(ctypes.byref(op), ctypes.byref(params), 1)
     if wsb == 0:
         raise RrError("rr_workspace_size", RR.ERR_ARG)
@@ -141,8 +146,8 @@ def rr_batch_svd(ops, params: RrParams, seed: int, device="cuda", stream=None):
     arr = (RrOperator * cnt)(*ops)
     k = params.k
     outs = [(torch.empty(k, dtype=torch.float64, device=device),
-             fortran(torch.empty(o.m, k, dtype=torch.float64, device=device)),
-             fortran(torch.empty(o.n, k, dtype=torch.float64, device=device))) for o in ops]
+             empty_f(o.m, k, torch.float64, device),
+             empty_f(o.n, k, torch.float64, device)) for o in ops]
     S = (ctypes.c_void_p * cnt)(*[o[0].data_ptr() for o in outs])
     U = (ctypes.c_void_p * cnt)(*[o[1].data_ptr() for o in outs])
     V = (ctypes.c_void_p * cnt)(*[o[2].data_ptr() for o in outs])
@@ -162,7 +167,7 @@ def rr_batch_svd(ops, params: RrParams, seed: int, device="cuda", stream=None):
 # ---------------------------------------------------------------- stages
 def rr_colscale_cast(X, dtype, stream=None):
     rows, cols = X.shape
-    Y = fortran(torch.empty(rows, cols, dtype=dtype, device=X.device))
+    Y = empty_f(rows, cols, dtype, X.device)
     scale = torch.empty(cols, dtype=torch.float64, device=X.device)
     check("rr_colscale_cast", lib().rr_colscale_cast(rows, cols, _p(X), ld_of(X), DTYPES[dtype], _p(Y),
                                                       ld_of(Y), _p(scale), _stream(stream)))
@@ -171,7 +176,7 @@ def rr_colscale_cast(X, dtype, stream=None):
 
 def rr_cast_operator(A, dtype, row_copy=True, stream=None):
     m, n = A.shape
-    col = fortran(torch.empty(m, n, dtype=dtype, device=A.device))
+    col = empty_f(m, n, dtype, A.device)
     row = torch.empty(m * n, dtype=dtype, device=A.device) if row_copy else None
     check("rr_cast_operator", lib().rr_cast_operator(m, n, _p(A), ld_of(A), DTYPES[dtype], _p(col),
                                                       _p(row), _stream(stream)))
@@ -181,8 +186,8 @@ def rr_cast_operator(A, dtype, row_copy=True, stream=None):
 def rr_split_operator(A, row_copy=True, stream=None):
     """hi = bf16(A), lo = bf16(A - hi): (hi_col, hi_row, lo_col, lo_row); row copies flat or None."""
     m, n = A.shape
-    hc = fortran(torch.empty(m, n, dtype=torch.bfloat16, device=A.device))
-    lc = fortran(torch.empty(m, n, dtype=torch.bfloat16, device=A.device))
+    hc = empty_f(m, n, torch.bfloat16, A.device)
+    lc = empty_f(m, n, torch.bfloat16, A.device)
     hr = torch.empty(m * n, dtype=torch.bfloat16, device=A.device) if row_copy else None
     lr = torch.empty(m * n, dtype=torch.bfloat16, device=A.device) if row_copy else None
     check("rr_split_operator", lib().rr_split_operator(m, n, _p(A), ld_of(A), _p(hc), _p(hr), _p(lc), _p(lr),
@@ -196,7 +201,7 @@ def rr_lift(S1, Y, S2=None, X=None, stream=None):
     p2 = S2.shape[1] if S2 is not None else 0
     b = Y.shape[1]
     if X is None:
-        X = fortran(torch.empty(n, b, dtype=torch.float64, device=Y.device))
+        X = empty_f(n, b, torch.float64, Y.device)
     L = lib()
     ws = _ws(L.rr_lift_workspace_size(n, b, p1 + p2), Y.device)
     check("rr_lift", L.rr_lift(n, b, DTYPES[S1.dtype], _p(S1), ld_of(S1), p1,
@@ -207,7 +212,7 @@ def rr_lift(S1, Y, S2=None, X=None, stream=None):
 
 def rr_gemm_lowp(dtype, M, N, K, A_k, lda, B, ldb, C=None, R=None, coef=None, stream=None):
     if C is None:
-        C = fortran(torch.empty(M, N, dtype=torch.float32, device=B.device))
+        C = empty_f(M, N, torch.float32, B.device)
     check("rr_gemm_lowp", lib().rr_gemm_lowp(dtype, M, N, K, _p(A_k), lda, _p(B), ldb, _p(C), ld_of(C),
                                               _p(R), ld_of(R) if R is not None else 0, _p(coef),
                                               _stream(stream)))
@@ -216,7 +221,7 @@ def rr_gemm_lowp(dtype, M, N, K, A_k, lda, B, ldb, C=None, R=None, coef=None, st
 
 def rr_gemm_lowp_split(M, N, K, A_hi, A_lo, lda, B_hi, B_lo, ldb, C=None, R=None, coef=None, stream=None):
     if C is None:
-        C = fortran(torch.empty(M, N, dtype=torch.float32, device=B_hi.device))
+        C = empty_f(M, N, torch.float32, B_hi.device)
     check("rr_gemm_lowp_split", lib().rr_gemm_lowp_split(M, N, K, _p(A_hi), _p(A_lo), lda, _p(B_hi), _p(B_lo),
                                                           ldb, _p(C), ld_of(C), _p(R),
                                                           ld_of(R) if R is not None else 0, _p(coef),
@@ -240,7 +245,7 @@ def rr_gemm_f64_emulated(trans, A, B, slices=8, C=None, stream=None):
     K = A.shape[0] if trans else A.shape[1]
     N = B.shape[1]
     if C is None:
-        C = fortran(torch.empty(M, N, dtype=torch.float64, device=B.device))
+        C = empty_f(M, N, torch.float64, B.device)
     L = lib()
     ws = _ws(L.rr_gemm_f64_emulated_workspace_size(int(trans), M, N, K, slices), B.device)
     check("rr_gemm_f64_emulated", L.rr_gemm_f64_emulated(int(trans), M, N, K, _p(A), ld_of(A), _p(B),
@@ -253,7 +258,7 @@ def rr_hessenberg(W, qtype=torch.bfloat16, tol=0.0, stream=None):
     """Algorithm 8 on W (FP32 or FP64, modified in place).  Returns (Q, piv, err)."""
     n, k = W.shape
     arith = DTYPES[W.dtype]
-    Q = fortran(torch.empty(n, k, dtype=qtype, device=W.device))
+    Q = empty_f(n, k, qtype, W.device)
     piv = torch.empty(k, dtype=torch.int32, device=W.device)
     L = lib()
     wsb = L.rr_hessenberg_workspace_size(n, k, arith)
@@ -291,7 +296,7 @@ def rr_gram_noalloc(X, Y, G=None, accumulate=False, stream=None):
 def rr_pencil_eig(H, G, stream=None):
     b = H.shape[0]
     theta = torch.empty(b, dtype=torch.float64, device=H.device)
-    Y = fortran(torch.empty(b, b, dtype=torch.float64, device=H.device))
+    Y = empty_f(b, b, torch.float64, H.device)
     L = lib()
     ws = _ws(L.rr_pencil_workspace_size(b, b), H.device)
     dropped = ctypes.c_int32(0)
@@ -304,8 +309,8 @@ def rr_pencil_svd(B, Gu, Gv, stream=None):
     b1, b2 = B.shape
     r = min(b1, b2)
     s = torch.empty(r, dtype=torch.float64, device=B.device)
-    Y = fortran(torch.empty(b1, r, dtype=torch.float64, device=B.device))
-    Z = fortran(torch.empty(b2, r, dtype=torch.float64, device=B.device))
+    Y = empty_f(b1, r, torch.float64, B.device)
+    Z = empty_f(b2, r, torch.float64, B.device)
     L = lib()
     ws = _ws(L.rr_pencil_workspace_size(b1, b2), B.device)
     dropped = ctypes.c_int32(0)
@@ -316,7 +321,7 @@ def rr_pencil_svd(B, Gu, Gv, stream=None):
 
 def rr_csr_spmm(row_ptr, col_idx, values, X, out_dtype=torch.float32, stream=None):
     n, b = X.shape
-    Y = fortran(torch.empty(n, b, dtype=out_dtype, device=X.device))
+    Y = empty_f(n, b, out_dtype, X.device)
     check("rr_csr_spmm", lib().rr_csr_spmm(n, b, _p(row_ptr), _p(col_idx), _p(values), DTYPES[X.dtype],
                                            _p(X), ld_of(X), DTYPES[out_dtype], _p(Y), ld_of(Y),
                                            _stream(stream)))
@@ -327,7 +332,7 @@ def rr_chebyshev_step(row_ptr, col_idx, values, Y_cur, Y_prev, alpha, c, beta, b
                       gamma=None, out_dtype=None, stream=None):
     n, b = Y_cur.shape
     out_dtype = out_dtype or Y_cur.dtype
-    Yn = fortran(torch.empty(n, b, dtype=out_dtype, device=Y_cur.device))
+    Yn = empty_f(n, b, out_dtype, Y_cur.device)
     check("rr_chebyshev_step", lib().rr_chebyshev_step(
         n, b, _p(row_ptr), _p(col_idx), _p(values), DTYPES[Y_cur.dtype], _p(Y_cur), _p(Y_prev),
         ld_of(Y_cur), alpha, c, beta, _p(beta_col), _p(R), ld_of(R) if R is not None else 0, _p(gamma),

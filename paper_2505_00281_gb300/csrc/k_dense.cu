@@ -393,8 +393,8 @@ __global__ void __launch_bounds__(256) k_gram_partial(
     for (int e = tid; e < GROWS * GT; e += 256) {
       int rr_ = e % GROWS, c = e / GROWS;
       int64_t row = rs + rr_;
-      Xs[rr_][c] = (row < r1 && p0 + c < p) ? (TA)Ld<TX>::f64(X + row + (p0 + c) * ldx) : TA(0);
-      Ys[rr_][c] = (row < r1 && q0 + c < q) ? (TA)Ld<TY>::f64(Y + row + (q0 + c) * ldy) : TA(0);
+      Xs[rr_][c] = (row < r1 && p0 + c < p) ? LdAs<TA, TX>::get(X + row + (p0 + c) * ldx) : TA(0);
+      Ys[rr_][c] = (row < r1 && q0 + c < q) ? LdAs<TA, TY>::get(Y + row + (q0 + c) * ldy) : TA(0);
     }
     __syncthreads();
 #pragma unroll 8

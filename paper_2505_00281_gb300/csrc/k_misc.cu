@@ -3,6 +3,8 @@
 // blocks, selection and output normalisation.
 #include <cfloat>
 
+#include <type_traits>
+
 #include "rr_common.cuh"
 #include "solver_kernels.cuh"
 
@@ -23,12 +25,12 @@ __global__ void __launch_bounds__(256) k_lift(int64_t n, int64_t b, int64_t p, c
     for (int e = tid; e < LBK * LBM; e += 256) {
       int i = e % LBM, kk = e / LBM;
       int64_t gi = m0 + i, gk = k0 + kk;
-      Ss[kk][i] = (gi < n && gk < p) ? (TA)Ld<TS>::f64(S + gi + gk * lds) : TA(0);
+      Ss[kk][i] = (gi < n && gk < p) ? LdAs<TA, TS>::get(S + gi + gk * lds) : TA(0);
     }
     for (int e = tid; e < LBK * LBN; e += 256) {
       int kk = e % LBK, j = e / LBK;
       int64_t gk = k0 + kk, gj = n0 + j;
-      Ys[kk][j] = (gk < p && gj < b) ? (TA)Y[gk + gj * ldy] : TA(0);
+      Ys[kk][j] = (gk < p && gj < b) ? LdAs<TA, double>::get(Y + gk + gj * ldy) : TA(0);
     }
     __syncthreads();
 #pragma unroll
@@ -53,9 +55,16 @@ __global__ void __launch_bounds__(256) k_lift(int64_t n, int64_t b, int64_t p, c
     for (int r = 0; r < 4; ++r) {
       int64_t i = m0 + tm + 16 * r;
       if (i >= n) continue;
-      double v = alpha * (double)acc[r][q];
-      if (accum) v += (double)X[i + j * ldx];
-      X[i + j * ldx] = (TO)v;
+      if constexpr (std::is_same<TA, float>::value && std::is_same<TO, float>::value) {
+        // FP32 result of an FP32 product (alpha = +-1, exact in FP32): one
+        // rounding, as through FP64, without FP64 instructions
+        const float v = fmaf((float)alpha, acc[r][q], accum ? (float)X[i + j * ldx] : 0.f);
+        X[i + j * ldx] = (TO)v;
+      } else {
+        double v = alpha * (double)acc[r][q];
+        if (accum) v += (double)X[i + j * ldx];
+        X[i + j * ldx] = (TO)v;
+      }
     }
   }
 }

@@ -11,7 +11,34 @@ namespace rr {
 template <typename TA> struct AccT { using type = float; };
 template <> struct AccT<double> { using type = double; };
 
+// Thread per row, lanes on consecutive rows: with column-major blocks a
+// warp's load of Y(i, j) for 32 consecutive rows is contiguous, and so are the
+// gathers Y(col_e, j) of a stencil's neighbours.  The row's first kRowE CSR
+// entries stay in registers for all b columns (longer rows loop over the
+// rest).  Arithmetic in the accumulation type (FP32 for FP32 / BF16 blocks,
+// FP64 for FP64 ones: no FP64 instruction on the low-precision path).
+constexpr int kRowE = 8;
+
+template <typename A, typename T>
+__device__ __forceinline__ A ld_acc(const T* p) {
+  return LdAs<A, T>::get(p);
+}
+template <typename TO, typename A> __device__ __forceinline__ TO st_cvt(A v);
+template <> __device__ __forceinline__ float st_cvt<float, float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 st_cvt<__nv_bfloat16, float>(float v) {
+  return __float2bfloat16_rn(v);
+}
+template <> __device__ __forceinline__ double st_cvt<double, float>(float v) { return (double)v; }
+template <> __device__ __forceinline__ double st_cvt<double, double>(double v) { return v; }
+template <> __device__ __forceinline__ float st_cvt<float, double>(double v) { return (float)v; }
+template <> __device__ __forceinline__ __nv_bfloat16 st_cvt<__nv_bfloat16, double>(double v) {
+  return __double2bfloat16(v);
+}
+
 // Y_next(i,j) = alpha*(sum_e v_e Y_cur(col_e, j) - c*Y_cur(i,j)) - beta*bc_j*Y_prev(i,j) + g_j R(i,j)
+// The shift folds into the row's diagonal entry (held in registers), so the
+// row's own Y_cur(i, j) is not loaded again; eight columns per iteration give
+// eight independent sums and more loads in flight.
 template <typename TY, typename TO>
 __global__ void __launch_bounds__(256) k_csr_cheb(
     int64_t n, int64_t b, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
@@ -20,22 +47,68 @@ __global__ void __launch_bounds__(256) k_csr_cheb(
     const double* __restrict__ R, int64_t ldr, const double* __restrict__ gam, TO* __restrict__ Yn,
     int64_t ldn) {
   using A = typename AccT<TY>::type;
-  const int lane = threadIdx.x & 31;
-  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= n) return;
   const int e0 = rp[row], e1 = rp[row + 1];
-  for (int64_t j = lane; j < b; j += 32) {
+  const int ne = e1 - e0 < kRowE ? e1 - e0 : kRowE;
+  int cie[kRowE];
+  A vae[kRowE];
+  bool diag = false;  // the shift folded into a diagonal entry in registers
+#pragma unroll
+  for (int t = 0; t < kRowE; ++t) {
+    cie[t] = t < ne ? ci[e0 + t] : (int)row;
+    vae[t] = t < ne ? (A)va[e0 + t] : A(0);
+    if (t < ne && cie[t] == (int)row && !diag) {
+      vae[t] -= (A)cshift;
+      diag = true;
+    }
+  }
+  const A shift = diag ? A(0) : (A)cshift;  // no diagonal among the first entries
+  const A al = (A)alpha;
+  int64_t j = 0;
+  constexpr int kC = 8;  // columns per iteration
+  for (; j + kC <= b; j += kC) {
+    A acc[kC];
+#pragma unroll
+    for (int u = 0; u < kC; ++u) acc[u] = A(0);
+#pragma unroll
+    for (int t = 0; t < kRowE; ++t)
+      if (t < ne) {
+#pragma unroll
+        for (int u = 0; u < kC; ++u) acc[u] += vae[t] * ld_acc<A>(Yc + (j + u) * ld + cie[t]);
+      }
+    for (int e = e0 + kRowE; e < e1; ++e) {
+      const A ve = (A)va[e];
+#pragma unroll
+      for (int u = 0; u < kC; ++u) acc[u] += ve * ld_acc<A>(Yc + (j + u) * ld + ci[e]);
+    }
+#pragma unroll
+    for (int u = 0; u < kC; ++u) {
+      const int64_t jj = j + u;
+      A a = acc[u];
+      if (!diag) a -= shift * ld_acc<A>(Yc + jj * ld + row);
+      A v = al * a;
+      if (Yp) v -= (A)(beta * (bc ? bc[jj] : 1.0)) * ld_acc<A>(Yp + row + jj * ld);
+      if (R && gam) v += (A)gam[jj] * ld_acc<A>(R + row + jj * ldr);
+      Yn[row + jj * ldn] = st_cvt<TO, A>(v);
+    }
+  }
+  for (; j < b; ++j) {
+    const TY* yc = Yc + j * ld;
     A acc = A(0);
-    for (int e = e0; e < e1; ++e) acc += (A)va[e] * (A)Ld<TY>::f64(Yc + ci[e] + j * ld);
-    A yc = (A)Ld<TY>::f64(Yc + row + j * ld);
-    double v = alpha * (double)(acc - (A)cshift * yc);
-    if (Yp) v -= beta * (bc ? bc[j] : 1.0) * Ld<TY>::f64(Yp + row + j * ld);
-    if (R && gam) v += gam[j] * R[row + j * ldr];
-    Yn[row + j * ldn] = from_f64<TO>(v);
+#pragma unroll
+    for (int t = 0; t < kRowE; ++t)
+      if (t < ne) acc += vae[t] * ld_acc<A>(yc + cie[t]);
+    for (int e = e0 + kRowE; e < e1; ++e) acc += (A)va[e] * ld_acc<A>(yc + ci[e]);
+    if (!diag) acc -= shift * ld_acc<A>(yc + row);
+    A v = al * acc;
+    if (Yp) v -= (A)(beta * (bc ? bc[j] : 1.0)) * ld_acc<A>(Yp + row + j * ld);
+    if (R && gam) v += (A)gam[j] * ld_acc<A>(R + row + j * ldr);
+    Yn[row + j * ldn] = st_cvt<TO, A>(v);
   }
 }
 
-// Y = A X, warp per row
+// Y = A X, thread per row (same access pattern)
 template <typename TX, typename TO>
 __global__ void __launch_bounds__(256) k_csr_spmm(int64_t n, int64_t b, const int32_t* __restrict__ rp,
                                                   const int32_t* __restrict__ ci,
@@ -43,14 +116,24 @@ __global__ void __launch_bounds__(256) k_csr_spmm(int64_t n, int64_t b, const in
                                                   const TX* __restrict__ X, int64_t ldx,
                                                   TO* __restrict__ Y, int64_t ldy) {
   using A = typename AccT<TX>::type;
-  const int lane = threadIdx.x & 31;
-  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= n) return;
   const int e0 = rp[row], e1 = rp[row + 1];
-  for (int64_t j = lane; j < b; j += 32) {
+  const int ne = e1 - e0 < kRowE ? e1 - e0 : kRowE;
+  int cie[kRowE];
+  A vae[kRowE];
+#pragma unroll
+  for (int t = 0; t < kRowE; ++t) {
+    cie[t] = t < ne ? ci[e0 + t] : (int)row;
+    vae[t] = t < ne ? (A)va[e0 + t] : A(0);
+  }
+  for (int64_t j = 0; j < b; ++j) {
+    const TX* x = X + j * ldx;
     A acc = A(0);
-    for (int e = e0; e < e1; ++e) acc += (A)va[e] * (A)Ld<TX>::f64(X + ci[e] + j * ldx);
-    Y[row + j * ldy] = from_f64<TO>((double)acc);
+#pragma unroll
+    for (int t = 0; t < kRowE; ++t) acc += vae[t] * ld_acc<A>(x + cie[t]);
+    for (int e = e0 + kRowE; e < e1; ++e) acc += (A)va[e] * ld_acc<A>(x + ci[e]);
+    Y[row + j * ldy] = st_cvt<TO, A>(acc);
   }
 }
 
@@ -169,7 +252,7 @@ extern "C" rr_status rr_csr_spmm(int64_t n, int64_t b, const int32_t* row_ptr, c
                                  int32_t ytype, void* Y, int64_t ldy, void* stream) {
   if (n < 0 || b < 0 || ldx < n || ldy < n || !row_ptr || !X || !Y) return RR_ERR_ARG;
   if (n == 0 || b == 0) return RR_OK;
-  dim3 g((unsigned)((n + 7) / 8));
+  dim3 g((unsigned)((n + 255) / 256));
   cudaStream_t s = as_stream(stream);
   switch (xtype) {
     case RR_F64: return spmm_out<double>(ytype, g, s, n, b, row_ptr, col_idx, values, (const double*)X, ldx, Y, ldy);
@@ -188,7 +271,7 @@ extern "C" rr_status rr_chebyshev_step(int64_t n, int64_t b, const int32_t* row_
   if (n < 0 || b < 0 || ld < n || ld_next < n || !row_ptr || !Y_cur || !Y_next) return RR_ERR_ARG;
   if ((R != nullptr) != (gamma != nullptr)) return RR_ERR_ARG;
   if (n == 0 || b == 0) return RR_OK;
-  dim3 g((unsigned)((n + 7) / 8));
+  dim3 g((unsigned)((n + 255) / 256));
   cudaStream_t s = as_stream(stream);
   switch (ytype) {
     case RR_F64: return cheb_out<double>(out_type, g, s, n, b, row_ptr, col_idx, values, (const double*)Y_cur, (const double*)Y_prev, ld, alpha, c, beta, beta_col, R, ldr, gamma, Y_next, ld_next);

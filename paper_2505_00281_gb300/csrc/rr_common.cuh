@@ -101,10 +101,22 @@ __device__ __forceinline__ T warp_max(T v) {
 }
 
 // load/store with conversion for the basis storage types
+// FP64 -> FP32, round to nearest even, on the bit pattern (the conversion
+// instruction runs on the FP64 units, of which this GPU has few); values
+// outside FP32's normal range (and zero, Inf, NaN) take the instruction
+__device__ __forceinline__ float f64_to_f32_rn(double d) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+  const int E = (int)((u >> 52) & 0x7FF);
+  if (E < 897 || E > 1150) return (float)d;
+  const unsigned long long m = u & 0xFFFFFFFFFFFFFull;
+  const unsigned q = (unsigned)((m + 0xFFFFFFFull + ((m >> 29) & 1ull)) >> 29);  // may carry into the exponent
+  return __uint_as_float(((unsigned)(u >> 63) << 31) | (((unsigned)(E - 896) << 23) + q));
+}
+
 template <typename T> struct Ld;
 template <> struct Ld<double> {
   static __device__ __forceinline__ double f64(const double* p) { return *p; }
-  static __device__ __forceinline__ float f32(const double* p) { return (float)*p; }
+  static __device__ __forceinline__ float f32(const double* p) { return f64_to_f32_rn(*p); }
 };
 template <> struct Ld<float> {
   static __device__ __forceinline__ double f64(const float* p) { return (double)*p; }
@@ -117,6 +129,15 @@ template <> struct Ld<__nv_bfloat16> {
   static __device__ __forceinline__ float f32(const __nv_bfloat16* p) {
     return __bfloat162float(*p);
   }
+};
+
+// load a stored entry as the arithmetic type TA (FP32: no FP64 instruction)
+template <typename TA, typename T> struct LdAs;
+template <typename T> struct LdAs<float, T> {
+  static __device__ __forceinline__ float get(const T* p) { return Ld<T>::f32(p); }
+};
+template <typename T> struct LdAs<double, T> {
+  static __device__ __forceinline__ double get(const T* p) { return Ld<T>::f64(p); }
 };
 
 template <typename T> __device__ __forceinline__ T from_f64(double v);
