@@ -1,0 +1,78 @@
+"""Pins of the learned-warm-start oracle (CPU only): the convolution against scipy's
+correlation, every gradient against central finite differences, the Procrustes loss
+against its closed form on a rotated copy, and Adam's first step against its formula."""
+import numpy as np
+import pytest
+from scipy.signal import correlate
+
+import workloads as wl
+from oracle import warmstart as W
+
+
+def test_conv3x3_matches_scipy_correlate():
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((2, 3, 7, 9))
+    Wt = rng.standard_normal((4, 3, 3, 3))
+    b = rng.standard_normal(4)
+    y = W.conv3x3(x, Wt, b)
+    for n in range(2):
+        for o in range(4):
+            ref = b[o] + sum(correlate(x[n, c], Wt[o, c], mode="same") for c in range(3))
+            assert np.allclose(y[n, o], ref, atol=1e-12)
+
+
+def _num_grad(f, a, eps=1e-6):
+    g = np.zeros_like(a)
+    it = np.nditer(a, flags=["multi_index"])
+    for _ in it:
+        i = it.multi_index
+        old = a[i]
+        a[i] = old + eps
+        fp = f()
+        a[i] = old - eps
+        fm = f()
+        a[i] = old
+        g[i] = (fp - fm) / (2 * eps)
+    return g
+
+
+def test_network_gradients_match_finite_differences():
+    rng = np.random.default_rng(2)
+    params = [(rng.standard_normal((3, 1, 3, 3)) * 0.5, rng.standard_normal(3) * 0.1),
+              (rng.standard_normal((2, 3, 3, 3)) * 0.5, rng.standard_normal(2) * 0.1)]
+    x = rng.standard_normal((1, 1, 5, 6))
+    target = rng.standard_normal((1, 2, 5, 6))
+
+    def loss():
+        out = W.net_forward(params, x)[-1]
+        return 0.5 * float(np.sum((out - target) ** 2))
+
+    acts = W.net_forward(params, x)
+    grads = W.net_backward(params, acts, acts[-1] - target)
+    for (Wl, bl), (dW, db) in zip(params, grads):
+        assert np.allclose(dW, _num_grad(loss, Wl), rtol=1e-5, atol=1e-7)
+        assert np.allclose(db, _num_grad(loss, bl), rtol=1e-5, atol=1e-7)
+
+
+def test_procrustes_loss_closed_form_and_gradient():
+    rng = np.random.default_rng(3)
+    Vs, _ = np.linalg.qr(rng.standard_normal((40, 5)))
+    Q, _ = np.linalg.qr(rng.standard_normal((5, 5)))
+    L, g = W.procrustes_loss(Vs @ Q, Vs)                # an exact rotation: zero loss
+    assert L < 1e-24 and np.abs(g).max() < 1e-12
+    V = Vs @ Q * 0.7 + 0.01 * rng.standard_normal((40, 5))
+    L, g = W.procrustes_loss(V, Vs)
+    gn = _num_grad(lambda: W.procrustes_loss(V, Vs)[0], V)
+    assert np.allclose(g, gn, rtol=1e-5, atol=1e-8)
+
+
+def test_adam_first_step_is_a_signed_lr_step():
+    p, g = np.array([1.0, -2.0, 3.0]), np.array([0.5, -0.1, 4.0])
+    p1, m, v = W.adam_step(p, g, np.zeros(3), np.zeros(3), 1, lr=0.01)
+    assert np.allclose(p1, p - 0.01 * np.sign(g), atol=1e-7)   # bias-corrected m/sqrt(v) = sign(g)
+
+
+def test_gaussian_potential_recipe():
+    v = wl.gaussian_potential(64, 5)
+    assert v.shape == (64, 64) and v.min() >= 0.0 and v.max() <= 8 * 20.0
+    assert not np.array_equal(v, wl.gaussian_potential(64, 6))

@@ -165,3 +165,31 @@ def config4_shapes(count: int = 512, seed: int = 4000):
 
 def config4_sigma(n: int) -> np.ndarray:
     return np.arange(1, n + 1, dtype=np.float64) ** -1.5
+
+
+def gaussian_potential(N: int, seed: int, count: int = 8) -> np.ndarray:
+    """Learned-warm-start family: V_p on an N x N grid (row index p = y*N + x), a sum of
+    `count` Gaussians a_g exp(-|x - c_g|^2 / (2 w_g^2)) with centres uniform in the grid,
+    widths uniform in [4, 32] cells and amplitudes uniform in [0, 20].  Returns (N, N) FP64."""
+    r = _rng(seed)
+    cx = r.uniform(0.0, N, size=count)
+    cy = r.uniform(0.0, N, size=count)
+    w = r.uniform(4.0, 32.0, size=count)
+    a = r.uniform(0.0, 20.0, size=count)
+    y, x = np.mgrid[0:N, 0:N].astype(np.float64)
+    v = np.zeros((N, N))
+    for g in range(count):
+        v += a[g] * np.exp(-((x - cx[g]) ** 2 + (y - cy[g]) ** 2) / (2.0 * w[g] ** 2))
+    return v
+
+
+def conv_params(layers, seed: int):
+    """He-uniform initial weights and zero biases for a stack of 3x3 convolutions:
+    layers = [(cin, cout), ...]; returns [(W (cout, cin, 3, 3) FP32, b (cout,) FP32), ...]."""
+    r = _rng(seed)
+    out = []
+    for cin, cout in layers:
+        lim = math.sqrt(6.0 / (cin * 9))
+        out.append((r.uniform(-lim, lim, size=(cout, cin, 3, 3)).astype(np.float32),
+                    np.zeros(cout, dtype=np.float32)))
+    return out
