@@ -340,6 +340,47 @@ rr_status rr_chebyshev_step(int64_t n, int64_t b, const int32_t* row_ptr,
                             int64_t ldr, const double* gamma, int32_t out_type, void* Y_next,
                             int64_t ld_next, void* stream);
 
+/* Learned warm start (the start block V of Alg. 1, which the paper draws at
+ * random, proposed instead by a small convolutional network of the operator's
+ * potential and trained on converged Ritz vectors).  All FP32, NCHW layout on
+ * the device: x[n, c, i, j] at ((n*C + c)*H + i)*W + j, so one image with C
+ * channels is an (H*W) x C column-major block.  Pointers are device pointers
+ * owned by the caller; every call is asynchronous on `stream`.
+ *
+ * rr_conv3x3_forward: y (N, O, H, W) = correlation of x (N, C, H, W) with
+ *   w (O, C, 3, 3), zero padding 1, plus bias b (O), plus the image `add`
+ *   (O, H, W per sample, samples add_nstride floats apart; NULL: nothing
+ *   added); relu != 0 clamps the sum at 0.
+ * rr_conv3x3_backward: given g = dL/dy, ADDS dL/dw to dw (O, C, 3, 3) and
+ *   dL/db to db (O) (zero them first), and writes dL/dx to dx (N, C, H, W)
+ *   unless dx is NULL.
+ * rr_relu_mask: g[e] = 0 wherever act[e] <= 0 (the ReLU derivative taken at
+ *   the layer's output).
+ * rr_procrustes_grad: net output `out` (n x k, column-major, ld n) scaled by
+ *   `scale` gives V; with R = U W^T (U, W k x k FP64 column-major, from the
+ *   SVD of V^T V*), writes grad = scale * 2 (V R - V*) R^T (dL/d out) and
+ *   ADDS |V R - V*|_F^2 to *loss (FP64).  k <= 64.
+ * rr_adam: one Adam update of `count` parameters at step t >= 1 (moments m,
+ *   v updated in place, bias corrections 1 - b1^t, 1 - b2^t).
+ * rr_net_block: V[:, 0:k] (FP64, ld ldv >= n) = scale * out (n x k FP32,
+ *   ld n): the network output as the leading columns of a start block.
+ * Errors: RR_ERR_ARG for negative sizes, null pointers or k out of range;
+ * empty sizes return RR_OK without a launch. */
+rr_status rr_conv3x3_forward(int32_t N, int32_t C, int32_t H, int32_t W, int32_t O, const float* x,
+                             const float* w, const float* b, const float* add, int64_t add_nstride,
+                             int32_t relu, float* y, void* stream);
+rr_status rr_conv3x3_backward(int32_t N, int32_t C, int32_t H, int32_t W, int32_t O, const float* x,
+                              const float* w, const float* g, float* dx, float* dw, float* db,
+                              void* stream);
+rr_status rr_relu_mask(int64_t count, float* g, const float* act, void* stream);
+rr_status rr_procrustes_grad(int64_t n, int32_t k, const float* out, const double* Vstar,
+                             const double* U, const double* Wm, float scale, float* grad,
+                             double* loss, void* stream);
+rr_status rr_adam(int64_t count, float* p, const float* g, float* m, float* v, float lr, float b1,
+                  float b2, float eps, int32_t t, void* stream);
+rr_status rr_net_block(int64_t n, int32_t k, const float* out, float scale, double* V, int64_t ldv,
+                       void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -89,6 +89,15 @@ _SIGS = {
                             c_vp]),
     "rr_chebyshev_step": (c_i32, [c_i64, c_i64, c_vp, c_vp, c_vp, c_i32, c_vp, c_vp, c_i64, c_dbl,
                                   c_dbl, c_dbl, c_vp, c_vp, c_i64, c_vp, c_i32, c_vp, c_i64, c_vp]),
+    "rr_conv3x3_forward": (c_i32, [c_i32, c_i32, c_i32, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, c_i64, c_i32,
+                                   c_vp, c_vp]),
+    "rr_conv3x3_backward": (c_i32, [c_i32, c_i32, c_i32, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,
+                                    c_vp]),
+    "rr_relu_mask": (c_i32, [c_i64, c_vp, c_vp, c_vp]),
+    "rr_procrustes_grad": (c_i32, [c_i64, c_i32, c_vp, c_vp, c_vp, c_vp, ctypes.c_float, c_vp, c_vp, c_vp]),
+    "rr_adam": (c_i32, [c_i64, c_vp, c_vp, c_vp, c_vp, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                        ctypes.c_float, c_i32, c_vp]),
+    "rr_net_block": (c_i32, [c_i64, c_i32, c_vp, ctypes.c_float, c_vp, c_i64, c_vp]),
 }
 
 EXPORTED = tuple(_SIGS)

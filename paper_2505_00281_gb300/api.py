@@ -16,7 +16,8 @@ __all__ = [
     "fortran", "ld_of", "dense_operator", "csr_operator", "make_params", "rr_eig", "rr_svd",
     "rr_batch_svd", "rr_colscale_cast", "rr_cast_operator", "rr_split_operator", "rr_lift", "rr_gemm_lowp", "rr_gemm_f64",
     "rr_hessenberg", "rr_gram", "rr_gram_noalloc", "rr_pencil_eig", "rr_pencil_svd", "rr_csr_spmm",
-    "rr_chebyshev_step", "RrParams", "RrOperator", "RrInfo", "DTYPES",
+    "rr_chebyshev_step", "rr_conv3x3_forward", "rr_conv3x3_backward", "rr_relu_mask", "rr_procrustes_grad",
+    "rr_adam", "rr_net_block", "RrParams", "RrOperator", "RrInfo", "DTYPES",
 ]
 
 DTYPES = {torch.float64: RR.F64, torch.float32: RR.F32, torch.bfloat16: RR.BF16}
@@ -338,3 +339,60 @@ def rr_chebyshev_step(row_ptr, col_idx, values, Y_cur, Y_prev, alpha, c, beta, b
         ld_of(Y_cur), alpha, c, beta, _p(beta_col), _p(R), ld_of(R) if R is not None else 0, _p(gamma),
         DTYPES[out_dtype], _p(Yn), ld_of(Yn), _stream(stream)))
     return Yn
+
+
+def _nchw(t):
+    if t.dtype != torch.float32 or not t.is_contiguous() or t.dim() != 4:
+        raise ValueError("expected a contiguous FP32 (N, C, H, W) tensor")
+    return t
+
+
+def rr_conv3x3_forward(x, w, b, relu=False, add=None, y=None, stream=None):
+    """y = [relu](conv3x3(x, w) + b [+ add]); `add` is (N, O, H, W) or a view with that shape."""
+    N, C, H, W = _nchw(x).shape
+    O = w.shape[0]
+    if y is None:
+        y = torch.empty(N, O, H, W, dtype=torch.float32, device=x.device)
+    nstride = add.stride(0) if add is not None else 0
+    check("rr_conv3x3_forward", lib().rr_conv3x3_forward(N, C, H, W, O, _p(x), _p(w), _p(b), _p(add), nstride,
+                                                         int(relu), _p(y), _stream(stream)))
+    return y
+
+
+def rr_conv3x3_backward(x, w, g, dw, db, need_dx=True, stream=None):
+    """Adds dL/dw, dL/db into dw, db; returns dL/dx (or None)."""
+    N, C, H, W = _nchw(x).shape
+    O = w.shape[0]
+    dx = torch.empty_like(x) if need_dx else None
+    check("rr_conv3x3_backward", lib().rr_conv3x3_backward(N, C, H, W, O, _p(x), _p(w), _p(_nchw(g)), _p(dx),
+                                                           _p(dw), _p(db), _stream(stream)))
+    return dx
+
+
+def rr_relu_mask(g, act, stream=None):
+    check("rr_relu_mask", lib().rr_relu_mask(g.numel(), _p(g), _p(act), _stream(stream)))
+    return g
+
+
+def rr_procrustes_grad(out, Vstar, U, Wm, scale, grad=None, loss=None, stream=None):
+    """out: network output (k, n) rows = channels (any contiguous view); returns (grad like out, loss[1] FP64)."""
+    k = Vstar.shape[1]
+    n = Vstar.shape[0]
+    grad = torch.empty_like(out) if grad is None else grad
+    loss = torch.zeros(1, dtype=torch.float64, device=out.device) if loss is None else loss
+    check("rr_procrustes_grad", lib().rr_procrustes_grad(n, k, _p(out), _p(Vstar), _p(U), _p(Wm),
+                                                         float(scale), _p(grad), _p(loss), _stream(stream)))
+    return grad, loss
+
+
+def rr_adam(p, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8, stream=None):
+    check("rr_adam", lib().rr_adam(p.numel(), _p(p), _p(g), _p(m), _p(v), float(lr), float(b1), float(b2),
+                                   float(eps), int(t), _stream(stream)))
+
+
+def rr_net_block(out, scale, V, stream=None):
+    """V[:, :k] = scale * out, out the (k, n) channel-major network output."""
+    k = out.shape[0] if out.dim() == 2 else out.shape[-3]
+    n = V.shape[0]
+    check("rr_net_block", lib().rr_net_block(n, k, _p(out), float(scale), _p(V), ld_of(V), _stream(stream)))
+    return V

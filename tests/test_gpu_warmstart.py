@@ -1,0 +1,173 @@
+"""Learned warm start on the GPU: parity of its kernels (convolutions, ReLU,
+Procrustes gradient, Adam) with the FP64 oracle, gradients of the whole
+network through the C ABI, and the gain of a trained start over a random one.
+
+FP32 kernels are compared against the FP64 oracle run on the same FP32 inputs,
+within bounds of FP32 accumulation: |err| <= c * 2^-24 * (the same sums over
+absolute values), c stated per test.
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import warmstart as OW
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U24 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def rr():
+    import paper_2505_00281_gb300 as pkg
+    from paper_2505_00281_gb300 import build
+
+    build.build()
+    pkg.lib()
+    return pkg
+
+
+def f32(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to("cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("N,C,H,W,O,relu,skip", [(2, 5, 19, 37, 11, True, True), (1, 33, 16, 16, 8, False, False),
+                                                 (3, 1, 5, 3, 2, True, False)])
+def test_conv3x3_forward(rr, N, C, H, W, O, relu, skip):
+    rng = np.random.default_rng(10 + C)
+    x = rng.standard_normal((N, C, H, W)).astype(np.float32)
+    Wt = rng.standard_normal((O, C, 3, 3)).astype(np.float32)
+    b = rng.standard_normal(O).astype(np.float32)
+    add = rng.standard_normal((N, O, H, W)).astype(np.float32) if skip else None
+    y = rr.rr_conv3x3_forward(f32(x), f32(Wt), f32(b), relu=relu, add=f32(add) if skip else None)
+    z = OW.conv3x3(x, Wt, b) + (add if skip else 0)
+    ref = OW.relu(z) if relu else z
+    bound = OW.conv3x3(np.abs(x), np.abs(Wt), np.abs(b)) + (np.abs(add) if skip else 0)
+    assert np.all(np.abs(host(y) - ref) <= 4 * (C * 9 + 2) * U24 * bound)
+
+
+@pytest.mark.parametrize("N,C,H,W,O", [(2, 5, 19, 37, 11), (1, 16, 33, 40, 9)])
+def test_conv3x3_backward(rr, N, C, H, W, O):
+    rng = np.random.default_rng(20 + C)
+    x = rng.standard_normal((N, C, H, W)).astype(np.float32)
+    Wt = rng.standard_normal((O, C, 3, 3)).astype(np.float32)
+    g = rng.standard_normal((N, O, H, W)).astype(np.float32)
+    dw = torch.zeros(O, C, 3, 3, device="cuda")
+    db = torch.zeros(O, device="cuda")
+    dx = rr.rr_conv3x3_backward(f32(x), f32(Wt), f32(g), dw, db)
+    rdx, rdw, rdb = OW.conv3x3_backward(x, Wt, g)
+    bdx, bdw, bdb = OW.conv3x3_backward(np.abs(x), np.abs(Wt), np.abs(g))
+    assert np.all(np.abs(host(dx) - rdx) <= 4 * (O * 9 + 1) * U24 * bdx)
+    terms = N * H * W
+    assert np.all(np.abs(host(dw) - rdw) <= 4 * terms * U24 * bdw)
+    assert np.all(np.abs(host(db) - rdb) <= 4 * terms * U24 * bdb)
+    # accumulation: a second call adds the same gradients again
+    rr.rr_conv3x3_backward(f32(x), f32(Wt), f32(g), dw, db, need_dx=False)
+    assert np.all(np.abs(host(dw) - 2 * rdw) <= 8 * terms * U24 * bdw)
+
+
+def test_relu_mask(rr):
+    rng = np.random.default_rng(5)
+    act = np.maximum(rng.standard_normal(1000), 0).astype(np.float32)
+    g = rng.standard_normal(1000).astype(np.float32)
+    gt = f32(g)
+    rr.rr_relu_mask(gt, f32(act))
+    assert np.array_equal(host(gt), np.where(act > 0, g, 0).astype(np.float64))
+
+
+@pytest.mark.parametrize("n,k", [(1000, 5), (777, 20), (300, 40)])
+def test_procrustes_grad(rr, n, k):
+    rng = np.random.default_rng(30 + k)
+    out = rng.standard_normal((k, n)).astype(np.float32)        # channel-major network output
+    Vs = wl.haar(n, k, 31 + k)
+    scale = 0.25
+    V = scale * out.astype(np.float64).T
+    L, dV = OW.procrustes_loss(V, Vs)
+    Ut, S, Wt = np.linalg.svd(V.T @ Vs)
+    grad, loss = rr.rr_procrustes_grad(f32(out), torch.from_numpy(np.asfortranarray(Vs)).cuda().t().contiguous().t(),
+                                       torch.from_numpy(np.asfortranarray(Ut)).cuda().t().contiguous().t(),
+                                       torch.from_numpy(np.asfortranarray(Wt.T)).cuda().t().contiguous().t(), scale)
+    assert abs(loss.item() - L) <= 1e-4 * L
+    ref = scale * dV.T
+    assert np.abs(host(grad) - ref).max() <= 4 * k * U24 * (2 * scale * (np.abs(V).max() * k + 1) * k)
+
+
+def test_adam(rr):
+    rng = np.random.default_rng(7)
+    p = rng.standard_normal(5000).astype(np.float32)
+    pt, mt, vt = f32(p), torch.zeros(5000, device="cuda"), torch.zeros(5000, device="cuda")
+    pr, mr, vr = p.astype(np.float64), np.zeros(5000), np.zeros(5000)
+    for t in range(1, 4):
+        g = rng.standard_normal(5000).astype(np.float32)
+        rr.rr_adam(pt, f32(g), mt, vt, t, 1e-2)
+        pr, mr, vr = OW.adam_step(pr, g.astype(np.float64), mr, vr, t, 1e-2)
+    assert np.abs(host(pt) - pr).max() <= 1e-6 * (1 + np.abs(pr).max())
+
+
+def _oracle_net_grads(params, pot, Vs, N, k):
+    from paper_2505_00281_gb300.warmstart import POTENTIAL_SCALE, free_modes
+    x = np.concatenate([(pot * POTENTIAL_SCALE).astype(np.float32)[None], free_modes(N, k)])[None]
+    x = x.astype(np.float64)
+    p64 = [(W.astype(np.float64), b.astype(np.float64)) for W, b in params]
+    acts = OW.net_forward(p64, x)
+    out = acts[-1] + x[:, 1:]
+    scale = 1.0 / N
+    V = scale * out[0].reshape(k, N * N).T
+    L, dV = OW.procrustes_loss(V, Vs)
+    dout = (scale * dV).T.reshape(1, k, N, N)
+    return L, OW.net_backward(p64, acts, dout)
+
+
+def test_network_gradients_vs_oracle(rr):
+    """Forward, Procrustes loss (projected SVD on the GPU), ReLU masks and every
+    layer's backward through the C ABI, against the oracle's chain rule."""
+    from paper_2505_00281_gb300.warmstart import POTENTIAL_SCALE, StartBlockNet, layer_shapes
+    N, k = 24, 6
+    params = wl.conv_params(layer_shapes(k, 10, 3), 40)
+    params = [(W, (0.1 * np.random.default_rng(41 + i).standard_normal(b.shape)).astype(np.float32))
+              for i, (W, b) in enumerate(params)]
+    pot = wl.gaussian_potential(N, 42)
+    Vs = wl.haar(N * N, k, 43)
+    net = StartBlockNet(N, k, params)
+    net.set_potential(f32(pot * POTENTIAL_SCALE))
+    acts = net.forward()
+    loss, g = net.loss_grad(acts[-1], torch.from_numpy(Vs).cuda().t().contiguous().t())
+    net.grad.zero_()
+    net.backward(acts, g)
+    L, ref = _oracle_net_grads(params, pot.astype(np.float32).astype(np.float64), Vs, N, k)
+    assert abs(loss.item() - L) <= 1e-4 * L
+    for li, (rdW, rdb) in enumerate(ref):
+        tol = 1e-3 * max(np.abs(rdW).max(), np.abs(rdb).max())
+        assert np.abs(host(net.dW[li]) - rdW).max() <= tol, li
+        assert np.abs(host(net.db[li]) - rdb).max() <= tol, li
+
+
+def _problems(N, k, block, seeds):
+    for s in seeds:
+        pot = wl.gaussian_potential(N, s)
+        rp, ci, va = wl.grid_potential_csr(N, pot.ravel())
+        yield pot, rp, ci, va, wl.uniform_block(N * N, block, s + 1)
+
+
+def test_trained_start_beats_random(rr):
+    """Train on converged Ritz vectors of one family, then solve held-out
+    members from the trained start and from the random start."""
+    from paper_2505_00281_gb300 import warmstart as WS
+    N, k, block, degree = 64, 16, 24, 10
+    train_seeds = range(70000, 70048)
+    test_seeds = range(71000, 71008)
+    data = WS.eigen_targets(_problems(N, k, block, train_seeds), k, block, degree)
+    net = WS.StartBlockNet(N, k, [(W * (0.1 if i == 2 else 1.0), b) for i, (W, b) in
+                                  enumerate(wl.conv_params(WS.layer_shapes(k, 24, 3), 44))])
+    hist = WS.train(net, [(P, X) for P, X, _ in data], epochs=20, lr=2e-3, batch=8)
+    assert hist[-1] < 0.7 * hist[0], hist
+    rows = WS.evaluate(net, _problems(N, k, block, test_seeds), k, block, degree)
+    rnd = np.mean([r["random"]["sweeps"] for r in rows])
+    lrn = np.mean([r["learned"]["sweeps"] for r in rows])
+    assert all(r["learned"]["n_converged"] == k for r in rows)
+    assert lrn < rnd, (lrn, rnd, rows)
