@@ -461,10 +461,99 @@ def run_stage(args):
         e1.record()
         torch.cuda.synchronize()
         us = e0.elapsed_time(e1) * 1e3 / reps
-        nbytes = 4 * (n + 1) + 8 * len(ci) + 3 * 2 * n * bs  # CSR, Y_cur, Y_prev, Y_next
-        print(json.dumps({"stage": "cheb", "n": n, "nnz": int(len(ci)), "b": bs, "us_per_step": us,
-                          "algorithmic_bytes": nbytes, "achieved_gbs": nbytes / us / 1e3}))
         del Y2
+        # the same step on row-major blocks (the eigensolver's filter layout)
+        R0 = torch.randn(n, bs, device="cuda", dtype=torch.float32).to(torch.bfloat16)
+        R1 = torch.randn(n, bs, device="cuda", dtype=torch.float32).to(torch.bfloat16)
+        R2 = torch.empty(n, bs, device="cuda", dtype=torch.bfloat16)
+
+        def step_rows():
+            rc = L.rr_chebyshev_step_rows(n, bs, d_rp.data_ptr(), d_ci.data_ptr(), d_va.data_ptr(), bf,
+                                          R1.data_ptr(), R0.data_ptr(), bs, 0.1, 6.0, 0.5, bf, R2.data_ptr(), bs,
+                                          stream)
+            assert rc == 0, rc
+        for _ in range(3):
+            step_rows()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            step_rows()
+        e1.record()
+        torch.cuda.synchronize()
+        us_rows = e0.elapsed_time(e1) * 1e3 / reps
+        nbytes = 4 * (n + 1) + 8 * len(ci) + 3 * 2 * n * bs  # CSR, Y_cur, Y_prev, Y_next
+        peaks, src = load_peaks()
+        print(json.dumps({"stage": "cheb", "n": n, "nnz": int(len(ci)), "b": bs, "algorithmic_bytes": nbytes,
+                          "columns": {"us_per_step": us, "achieved_gbs": nbytes / us / 1e3},
+                          "rows": {"us_per_step": us_rows, "achieved_gbs": nbytes / us_rows / 1e3,
+                                   "frac": nbytes / us_rows / 1e3 / peaks["hbm_gbs"]},
+                          "peak_gbs": peaks["hbm_gbs"], "peak_source": src}))
+    elif args.stage == "sparse":
+        # the sparse eigenproblem: H = -Lap + diag(v), v_j ~ U[0, 10], 1024 x 1024 grid (n = 1,048,576),
+        # lowest 100 pairs, Chebyshev degree 20, block 160, BF16 basis, FP64 projection, residual <= 1e-8
+        Ng, k, bs, deg = 1024, 100, 160, 20
+        rp, ci, va, _ = wl.grid_schrodinger_csr(Ng, 10.0, wl.seed_for(3))
+        n = Ng * Ng
+        d = [torch.from_numpy(a).cuda() for a in (rp, ci, va)]
+        op = rr.api.csr_operator(*d)
+        V0 = rr.fortran(torch.from_numpy(wl.uniform_block(n, bs, wl.seed_for(3) + 1)).cuda())
+        p = rr.api.make_params(k, bs, deg, args.sweeps, 1e-8, basis="bf16", v0=V0, filter=rr.RR.CHEBYSHEV,
+                               which=rr.RR.SMALLEST, refine=True, phase1_sweeps=2, profile=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        th, X, info = rr.rr_eig(op, p, n)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        names = ["lowp_product", "f64_product", "hessenberg", "gram", "pencil", "lift", "other"]
+        print(json.dumps({"stage": "sparse", "n": n, "k": k, "block": bs, "degree": deg, "seconds": sec,
+                          "n_converged": info["n_converged"], "pairs_per_s": info["n_converged"] / sec,
+                          "sweeps": info["sweeps"], "refine_sweeps": info["refine_sweeps"],
+                          "max_res": info["max_res"], "res_history": info["res_history"],
+                          "theta_first": float(th[0].item()), "theta_last": float(th[-1].item()),
+                          "stages_ms": dict(zip(names, info["stage_ms"][:7])),
+                          "stage_calls": dict(zip(names, info["stage_calls"][:7]))}))
+    elif args.stage == "warm":
+        # learned warm start: H(p) = -Lap + V_p (8 Gaussian bumps) on a grid x grid mesh,
+        # lowest k pairs; train on solves of `train` family members, then solve `test`
+        # held-out members from the random, free-mode and learned start blocks
+        from paper_2505_00281_gb300 import warmstart as WS
+        Ng = args.grid
+        k, bs, deg, hidden, depth = (16, 24, 10, 24, 3) if Ng <= 64 else (32, 48, 20, 32, 4)
+
+        def problems(seeds):
+            for sd in seeds:
+                pot = wl.gaussian_potential(Ng, sd)
+                rp, ci, va = wl.grid_potential_csr(Ng, pot.ravel())
+                yield pot, rp, ci, va, wl.uniform_block(Ng * Ng, bs, sd + 1)
+        t0 = time.perf_counter()
+        data = WS.eigen_targets(problems(range(70000, 70000 + args.train)), k, bs, deg)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        params = wl.conv_params(WS.layer_shapes(k, hidden, depth), 44)
+        params = [(W * (0.1 if i == depth - 1 else 1.0), b) for i, (W, b) in enumerate(params)]
+        net = WS.StartBlockNet(Ng, k, params)
+        hist = WS.train(net, [(P, X) for P, X, _ in data], epochs=args.epochs, lr=2e-3, batch=8)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        rows = WS.evaluate(net, problems(range(71000, 71000 + args.test)), k, bs, deg)
+
+        def gmean(v):
+            return float(np.exp(np.mean(np.log(np.maximum(v, 1e-300)))))
+        arms = {}
+        for arm in WS.ARMS:
+            arms[arm] = {
+                "sweeps": float(np.mean([r[arm]["sweeps"] for r in rows])),
+                "ms": float(np.mean([r[arm]["ms"] for r in rows])),
+                "res_after_1": gmean([r[arm]["res"][0] for r in rows]),
+                "res_after_3": gmean([r[arm]["res"][min(2, len(r[arm]["res"]) - 1)] for r in rows]),
+                "converged": [r[arm]["n_converged"] for r in rows]}
+        print(json.dumps({"stage": "warm", "grid": Ng, "k": k, "block": bs, "degree": deg,
+                          "params": int(sum(W.size + b.size for W, b in params)), "train": args.train,
+                          "test": args.test, "epochs": args.epochs,
+                          "target_ms_per_solve": 1e3 * (t1 - t0) / max(1, args.train),
+                          "train_ms_per_sample_step": 1e3 * (t2 - t1) / max(1, args.epochs * args.train),
+                          "loss_first": hist[0] if hist else None, "loss_last": hist[-1] if hist else None,
+                          "arms": arms}))
     elif args.stage == "prep":
         A = torch.randn(N, M, device="cuda", dtype=torch.float64).t()   # M x N column-major
         X = rr.fortran(torch.randn(N, B, device="cuda", dtype=torch.float64))
@@ -496,10 +585,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--stage", choices=["pencil", "hessenberg", "gemm", "split", "f64emu", "prep", "cheb"],
+    ap.add_argument("--stage", choices=["pencil", "hessenberg", "gemm", "split", "f64emu", "prep", "cheb", "warm", "sparse"],
                     help="run one stage of the workload (profiling driver)")
     ap.add_argument("--b", type=int, default=256, help="pencil size for --stage pencil, columns for hessenberg")
     ap.add_argument("--rows", type=int, default=M, help="rows of the block for --stage hessenberg")
+    ap.add_argument("--grid", type=int, default=64, help="grid side for --stage warm")
+    ap.add_argument("--sweeps", type=int, default=60, help="sweep limit for --stage sparse")
+    ap.add_argument("--train", type=int, default=48, help="training solves for --stage warm")
+    ap.add_argument("--test", type=int, default=8, help="held-out solves for --stage warm")
+    ap.add_argument("--epochs", type=int, default=40, help="training epochs for --stage warm")
     args = ap.parse_args()
     if args.stage:
         return run_stage(args)

@@ -123,7 +123,9 @@ const char* rr_last_error(void);
  * Solvers
  * ------------------------------------------------------------------------- */
 
-/* Bytes of device workspace rr_eig (svd = 0) or rr_svd (svd = 1) needs. */
+/* Bytes of device workspace rr_eig (svd = 0) or rr_svd (svd = 1) needs.
+ * The workspace must start on a 256-byte boundary (as cudaMalloc's blocks do;
+ * RR_ERR_WORKSPACE otherwise). */
 size_t rr_workspace_size(const rr_operator* A, const rr_params* p, int svd);
 
 /* Wanted eigenpairs of a symmetric operator (dense n x n or CSR).
@@ -263,8 +265,9 @@ rr_status rr_hessenberg(int32_t arith, int64_t n, int64_t k, void* W, int64_t ld
 /* Projection products (Alg. 3: B = U^T A U, M = U^T U; Alg. 5: U^T A V,
  * U^T U, V^T V): G (p x q FP64, ld ldg) = X^T Y (+ G if accumulate) for tall
  * X (n x p) and Y (n x q) of types xtype/ytype (RR_F64, RR_F32, RR_BF16).
- * FP64-accurate: when n >= 64, n % 8 == 0 and q <= 128 the products run on
- * the tensor cores from 8 column-scaled 6-bit slices of each operand with
+ * FP64-accurate: when n >= 64 and n % 8 == 0 the products run on the tensor
+ * cores (in column chunks of at most 128 of Y) from 8 column-scaled 6-bit
+ * slices of each operand with
  * exact FP32 sums over 4096-long K chunks (error per entry below
  * 2^-47 n max|X(:,i)| max|Y(:,j)|); otherwise FP64 accumulation on the CUDA
  * cores.  Needs rr_gram_workspace_size(n, p, q) bytes (slices and
@@ -332,13 +335,29 @@ rr_status rr_csr_spmm(int64_t n, int64_t b, const int32_t* row_ptr, const int32_
  * ld ld), FP32 accumulation (FP64 when ytype is RR_F64).  Y_next is written
  * as out_type (ytype or RR_F32; ld ld_next).  Y_prev may be NULL (first step).
  * bc (beta_col) may be NULL (bc_j = 1); R (FP64, ld ldr) and gamma may be
- * NULL (no added term). */
+ * NULL (no added term).  b <= 3072 (RR_ERR_ARG above). */
 rr_status rr_chebyshev_step(int64_t n, int64_t b, const int32_t* row_ptr,
                             const int32_t* col_idx, const float* values, int32_t ytype,
                             const void* Y_cur, const void* Y_prev, int64_t ld, double alpha,
                             double c, double beta, const double* beta_col, const double* R,
                             int64_t ldr, const double* gamma, int32_t out_type, void* Y_next,
                             int64_t ld_next, void* stream);
+
+/* The same step on row-major blocks (element (i, j) at Y[i * ldr + j]), the
+ * layout of the eigensolver's plain Chebyshev filter: one 16-byte gather per
+ * neighbour row and 16 / sizeof(ytype) columns.  Y_next = alpha (A - c I)
+ * Y_cur - beta Y_prev (Y_prev may be NULL).  (ytype, out_type) is one of
+ * (RR_BF16, RR_BF16), (RR_BF16, RR_F32), (RR_F32, RR_F32), (RR_F64, RR_F64).
+ * Columns are processed in vectors of 16 / sizeof(ytype): the row strides
+ * ldr, ldr_next must be at least b rounded up to that width, multiples of 16
+ * bytes, and the pointers 16-byte aligned (RR_ERR_ARG otherwise); pad
+ * columns up to the rounded width are read and written like the others.
+ * At most 256 vectors per row (b <= 2048 BF16, 1024 FP32, 512 FP64). */
+rr_status rr_chebyshev_step_rows(int64_t n, int64_t b, const int32_t* row_ptr,
+                                 const int32_t* col_idx, const float* values, int32_t ytype,
+                                 const void* Y_cur, const void* Y_prev, int64_t ldr, double alpha,
+                                 double c, double beta, int32_t out_type, void* Y_next,
+                                 int64_t ldr_next, void* stream);
 
 /* Learned warm start (the start block V of Alg. 1, which the paper draws at
  * random, proposed instead by a small convolutional network of the operator's

@@ -16,7 +16,7 @@ __all__ = [
     "fortran", "ld_of", "dense_operator", "csr_operator", "make_params", "rr_eig", "rr_svd",
     "rr_batch_svd", "rr_colscale_cast", "rr_cast_operator", "rr_split_operator", "rr_lift", "rr_gemm_lowp", "rr_gemm_f64",
     "rr_hessenberg", "rr_gram", "rr_gram_noalloc", "rr_pencil_eig", "rr_pencil_svd", "rr_csr_spmm",
-    "rr_chebyshev_step", "rr_conv3x3_forward", "rr_conv3x3_backward", "rr_relu_mask", "rr_procrustes_grad",
+    "rr_chebyshev_step", "rr_chebyshev_step_rows", "rr_conv3x3_forward", "rr_conv3x3_backward", "rr_relu_mask", "rr_procrustes_grad",
     "rr_adam", "rr_net_block", "RrParams", "RrOperator", "RrInfo", "DTYPES",
 ]
 
@@ -338,6 +338,18 @@ def rr_chebyshev_step(row_ptr, col_idx, values, Y_cur, Y_prev, alpha, c, beta, b
         n, b, _p(row_ptr), _p(col_idx), _p(values), DTYPES[Y_cur.dtype], _p(Y_cur), _p(Y_prev),
         ld_of(Y_cur), alpha, c, beta, _p(beta_col), _p(R), ld_of(R) if R is not None else 0, _p(gamma),
         DTYPES[out_dtype], _p(Yn), ld_of(Yn), _stream(stream)))
+    return Yn
+
+
+def rr_chebyshev_step_rows(row_ptr, col_idx, values, Y_cur, Y_prev, b, alpha, c, beta, out_dtype=None,
+                           stream=None):
+    """Row-major step: Y_cur, Y_prev (n, ldr) contiguous, columns 0 .. b-1 used (pad columns too)."""
+    n, ldr = Y_cur.shape
+    out_dtype = out_dtype or Y_cur.dtype
+    Yn = torch.empty(n, ldr, dtype=out_dtype, device=Y_cur.device)
+    check("rr_chebyshev_step_rows", lib().rr_chebyshev_step_rows(
+        n, b, _p(row_ptr), _p(col_idx), _p(values), DTYPES[Y_cur.dtype], _p(Y_cur), _p(Y_prev), ldr, alpha, c,
+        beta, DTYPES[out_dtype], _p(Yn), ldr, _stream(stream)))
     return Yn
 
 

@@ -503,6 +503,17 @@ extern "C" rr_status rr_gram(int64_t n, int64_t p, int64_t q, int32_t xtype, con
   // the workspace holds the slices
   if (emu_gram_supported(n, p, q) && ws && ws_bytes >= emu_gram_bytes(n, p, q))
     return emu_gram(s, n, p, q, xtype, X, ldx, ytype, Y, ldy, G, ldg, accumulate, ws, ws_bytes);
+  // wider Y: the same products on column chunks of at most 128
+  constexpr int64_t kQc = 128;
+  if (q > kQc && emu_gram_supported(n, p, kQc) && ws && ws_bytes >= emu_gram_bytes(n, p, kQc)) {
+    const size_t ys = dtype_size(ytype);
+    for (int64_t j0 = 0; j0 < q; j0 += kQc) {
+      const int64_t qc = std::min<int64_t>(kQc, q - j0);
+      RR_TRY(emu_gram(s, n, p, qc, xtype, X, ldx, ytype, (const char*)Y + (size_t)j0 * ldy * ys, ldy, G + j0 * ldg,
+                      ldg, accumulate, ws, ws_bytes));
+    }
+    return RR_OK;
+  }
   int64_t chunks = gram_chunks(n, p, q);
   if (ws_bytes < (size_t)chunks * p * q * sizeof(double) || !ws) return RR_ERR_WORKSPACE;
   int64_t rpc = (n + chunks - 1) / chunks;

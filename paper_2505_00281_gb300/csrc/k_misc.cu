@@ -146,11 +146,14 @@ rr_status res_finish(cudaStream_t s, int64_t b, const double* ss, const double* 
 // Column inf-norm of a block T (FP32 or FP64), then D = T / mu cast to TO.
 // If coef/sig given: coef[j] *= sig[j] / mu[j] (the correction recurrence's
 // injection coefficient, see solver.cu).  Zero columns: mu = 1.
+// FP32 blocks take the maximum in FP32 (exact) and convert once: no FP64
+// instruction per element on the low-precision path.
 template <typename TI>
 __global__ void k_colmax_any(int64_t n, const TI* __restrict__ T, int64_t ldt, double* __restrict__ mu) {
   const int64_t j = blockIdx.x;
-  double m = 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, fabs((double)T[i + j * ldt]));
+  TI mt = TI(0);
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) mt = fmax(mt, fabs(T[i + j * ldt]));
+  double m = (double)mt;
   __shared__ double sm[32];
   m = warp_max(m);
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
@@ -162,14 +165,21 @@ __global__ void k_colmax_any(int64_t n, const TI* __restrict__ T, int64_t ldt, d
   }
 }
 
+// Column scale 1 / mu_j formed once per CTA; an FP32 block is scaled and
+// rounded in FP32 (one FP32 multiply, one rounding to TO per element).
 template <typename TI, typename TO>
 __global__ void k_scale_cast2(int64_t n, int64_t b, const TI* __restrict__ T, int64_t ldt,
                               const double* __restrict__ mu, TO* __restrict__ D, int64_t ldd) {
   const int64_t j = blockIdx.y;
-  const double s = 1.0 / mu[j];
+  __shared__ TI s_sc;
+  if (threadIdx.x == 0) s_sc = (TI)(1.0 / mu[j]);
+  __syncthreads();
+  const TI sc = s_sc;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    D[i + j * ldd] = from_f64<TO>((double)T[i + j * ldt] * s);
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if constexpr (std::is_same<TI, float>::value) D[i + j * ldd] = from_f32<TO>(T[i + j * ldt] * sc);
+    else D[i + j * ldd] = from_f64<TO>(T[i + j * ldt] * sc);
+  }
 }
 
 __global__ void k_coef_update(int64_t b, const double* __restrict__ mu, const double* __restrict__ sig,
@@ -199,13 +209,23 @@ __global__ void k_scale_split(int64_t n, int64_t b, const TI* __restrict__ T, in
                               const double* __restrict__ mu, __nv_bfloat16* __restrict__ Dh,
                               __nv_bfloat16* __restrict__ Dl, int64_t ldd) {
   const int64_t j = blockIdx.y;
-  const double sc = mu ? 1.0 / mu[j] : 1.0;
+  __shared__ TI s_sc;
+  if (threadIdx.x == 0) s_sc = (TI)(mu ? 1.0 / mu[j] : 1.0);
+  __syncthreads();
+  const TI sc = s_sc;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const double v = (double)T[i + j * ldt] * sc;
-    const __nv_bfloat16 h = __double2bfloat16(v);
-    Dh[i + j * ldd] = h;
-    Dl[i + j * ldd] = __double2bfloat16(v - (double)__bfloat162float(h));
+    const TI v = T[i + j * ldt] * sc;
+    if constexpr (std::is_same<TI, float>::value) {
+      // FP32 split: v - hi is exact in FP32 (hi is v rounded to 8 bits)
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      Dh[i + j * ldd] = h;
+      Dl[i + j * ldd] = __float2bfloat16_rn(v - __bfloat162float(h));
+    } else {
+      const __nv_bfloat16 h = __double2bfloat16(v);
+      Dh[i + j * ldd] = h;
+      Dl[i + j * ldd] = __double2bfloat16(v - (double)__bfloat162float(h));
+    }
   }
 }
 

@@ -626,14 +626,19 @@ struct EigBufs {
   double *X, *X2, *theta, *P, *R, *ss, *res, *mu, *coef, *kap, *kap_prev, *rho, *gam, *gersh;
 };
 
+// Row stride of the filter's row-major blocks: b rounded up to 8 columns
+// (one 16-byte vector of BF16; a multiple of the FP32 and FP64 widths too).
+static inline int64_t rows_width(int64_t b) { return (b + 7) / 8 * 8; }
+
 static void carve_eig(Arena& ar, const Op& op, int64_t b, bool refine, EigBufs& w) {
   const int64_t n = op.n, b2 = refine ? 2 * b : b;
   const size_t ds = dsz(op.dt), ws_ = dsz(op.wt);
+  const int64_t bp = rows_width(b);  // the filter's row-major blocks use these buffers too
   carve_common(ar, n, b2, op.wt, w.c);
-  w.Vlo = ar.take_bytes(n * b * ds);
-  w.W = ar.take_bytes(n * b * ws_);
-  w.Pw = ar.take_bytes(n * b * ws_);
-  w.Dprev = ar.take_bytes(n * b * ds);
+  w.Vlo = ar.take_bytes(n * bp * ds);
+  w.W = ar.take_bytes(n * bp * ws_);
+  w.Pw = ar.take_bytes(n * bp * ws_);
+  w.Dprev = ar.take_bytes(n * bp * ds);
   w.G = ar.take<double>(b2 * b2);
   w.H = ar.take<double>(b2 * b2);
   w.Y = ar.take<double>(b2 * b2);
@@ -662,42 +667,39 @@ static void carve_eig(Arena& ar, const Op& op, int64_t b, bool refine, EigBufs& 
   }
 }
 
-// Plain scaled Chebyshev filter of the block V (dt) into the wt buffer `out`
-// (Y_d, unscaled); Y_j in dt ping-pong buffers.  Bounds: damp [a, up],
-// normalised at a0.
+// Plain scaled Chebyshev filter of the block V (dt) into W (wt, Y_d,
+// unscaled).  Bounds: damp [a, up], normalised at a0.  The d steps run on
+// row-major copies (row stride bp = b rounded up to 8 columns): V is
+// transposed once into Dprev, the steps ping-pong among Dprev, Vlo and W
+// (Vlo is rewritten by the basis step afterwards), the last step writes Pw
+// in wt, and Pw is transposed back into W.
 static rr_status cheb_filter(const Op& op, EigBufs& w, int64_t b, int d, double a, double up,
                              double a0, cudaStream_t s) {
   const int64_t n = op.n;
   const double e = (up - a) / 2, c = (up + a) / 2, s1 = e / (a0 - c);
-  void* y0 = w.Vlo;   // Y_0 (kept: Vlo is overwritten later by the basis step)
-  void* y1 = w.Dprev;
-  void* y2 = w.Pw;    // scratch in wt; reuse only when wt == dt
-  // Y_1 = (s1/e)(A - cI) Y_0
-  if (d == 1) return rr_chebyshev_step(n, b, op.rp, op.ci, op.va, op.dt, y0, nullptr, n, s1 / e, c,
-                                       0.0, nullptr, nullptr, 0, nullptr, op.wt, w.W, n, s);
-  RR_TRY(rr_chebyshev_step(n, b, op.rp, op.ci, op.va, op.dt, y0, nullptr, n, s1 / e, c, 0.0, nullptr,
-                           nullptr, 0, nullptr, op.dt, y1, n, s));
-  // ping-pong among three dt buffers: y0 (Vlo), y1 (Dprev), y2 (needs dt storage)
-  // use W's storage as the third dt buffer when dt is narrower than wt
-  y2 = w.W;
-  double sg = s1;
-  void *pm1 = y0, *p0 = y1, *p1 = y2;
-  for (int j = 2; j <= d; ++j) {
-    const double sn = 1.0 / (2.0 / s1 - sg);
-    const bool last = (j == d);
-    void* outp = last ? w.Pw : p1;  // final step written in wt to Pw
-    RR_TRY(rr_chebyshev_step(n, b, op.rp, op.ci, op.va, op.dt, p0, pm1, n, 2.0 * sn / e, c, sg * sn,
-                             nullptr, nullptr, 0, nullptr, last ? op.wt : op.dt, outp, n, s));
-    void* t = pm1;
-    pm1 = p0;
-    p0 = p1;
-    p1 = t;
-    sg = sn;
+  const int64_t bp = rows_width(b);
+  RR_TRY(block_to_rows(s, op.dt, n, b, bp, w.Vlo, n, w.Dprev, bp));
+  if (d == 1) {
+    RR_TRY(cheb_rows(s, n, b, op.rp, op.ci, op.va, op.dt, w.Dprev, nullptr, bp, s1 / e, c, 0.0, op.wt, w.Pw, bp));
+  } else {
+    RR_TRY(cheb_rows(s, n, b, op.rp, op.ci, op.va, op.dt, w.Dprev, nullptr, bp, s1 / e, c, 0.0, op.dt, w.Vlo, bp));
+    double sg = s1;
+    void *pm1 = w.Dprev, *p0 = w.Vlo, *p1 = w.W;
+    for (int j = 2; j <= d; ++j) {
+      const double sn = 1.0 / (2.0 / s1 - sg);
+      const bool last = (j == d);
+      RR_TRY(cheb_rows(s, n, b, op.rp, op.ci, op.va, op.dt, p0, pm1, bp, 2.0 * sn / e, c, sg * sn,
+                       last ? op.wt : op.dt, last ? w.Pw : p1, bp));
+      void* t = pm1;
+      pm1 = p0;
+      p0 = p1;
+      p1 = t;
+      sg = sn;
+    }
   }
-  // result Y_d is in Pw (wt); move to W for the basis step
-  RR_CUDA(cudaMemcpyAsync(w.W, w.Pw, n * b * dsz(op.wt), cudaMemcpyDeviceToDevice, s));
-  return RR_OK;
+  return block_from_rows(s, op.wt, n, b, w.Pw, bp, w.W, n);
 }
+
 
 static rr_status eig_run(const rr_operator* Aop, const rr_params* p, double* theta_out,
                          double* X_out, void* ws, size_t ws_bytes, rr_info* info, cudaStream_t s) {
@@ -943,7 +945,7 @@ extern "C" rr_status rr_eig(const rr_operator* A, const rr_params* p, double* th
   RR_TRY(check_op(A, false));
   RR_TRY(check_params(p, A->n));
   if (!theta || !X || !p->v0) return RR_ERR_ARG;
-  if (!ws || ws_bytes < eig_ws(A, p)) return RR_ERR_WORKSPACE;
+  if (!ws || ws_bytes < eig_ws(A, p) || ((uintptr_t)ws & 255)) return RR_ERR_WORKSPACE;
   return eig_run(A, p, theta, X, ws, ws_bytes, info, as_stream(stream));
 }
 
@@ -952,7 +954,7 @@ extern "C" rr_status rr_svd(const rr_operator* A, const rr_params* p, double* si
   RR_TRY(check_op(A, true));
   RR_TRY(check_params(p, A->n));
   if (!sigma || !U || !V || !p->v0) return RR_ERR_ARG;
-  if (!ws || ws_bytes < svd_ws(A, p, false)) return RR_ERR_WORKSPACE;
+  if (!ws || ws_bytes < svd_ws(A, p, false) || ((uintptr_t)ws & 255)) return RR_ERR_WORKSPACE;
   return svd_run(A, p, sigma, U, V, ws, ws_bytes, info, as_stream(stream), false, 0, 0);
 }
 

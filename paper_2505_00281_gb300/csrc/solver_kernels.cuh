@@ -30,6 +30,15 @@ rr_status cheb_coef_update(cudaStream_t s, int64_t b, const double* theta, const
                            double* kappa_prev, double* rho);
 void small_gemm(cudaStream_t s, int ta, int tb, int M, int N, int K, double alpha, const double* A,
                 int lda, const double* B, int ldb, double beta, double* C, int ldc);
+// row-major blocks for the plain Chebyshev filter (k_sparse.cu): transposes
+// (pad columns b .. bp - 1 zeroed) and the row-major fused step
+rr_status block_to_rows(cudaStream_t s, int32_t t, int64_t n, int64_t b, int64_t bp, const void* src,
+                        int64_t ld, void* dst, int64_t ldr);
+rr_status block_from_rows(cudaStream_t s, int32_t t, int64_t n, int64_t b, const void* src, int64_t ldr, void* dst,
+                          int64_t ld);
+rr_status cheb_rows(cudaStream_t s, int64_t n, int64_t b, const int32_t* rp, const int32_t* ci, const float* va,
+                    int32_t ytype, const void* Yc, const void* Yp, int64_t ldr, double alpha, double c, double beta,
+                    int32_t out_type, void* Yn, int64_t ldn);
 rr_status csr_gershgorin(cudaStream_t s, int64_t n, const int32_t* rp, const int32_t* ci,
                          const float* va, double* out2);
 }  // namespace rr

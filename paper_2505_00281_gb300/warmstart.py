@@ -19,8 +19,9 @@ fully convolutional network maps the potential to the k wanted directions:
 
 Every step runs in librr.so kernels (convolutions, ReLU masks, the Procrustes
 gradient and its projected SVD, Adam); tensors here are device memory only.
-A start block is k network columns plus random U(0,1) columns up to the block
-size; a random block remains the fallback when no trained network is given.
+A start block is the k network columns followed by random U(0,1) columns up
+to the block size; the random block remains the fallback when no trained
+network is given.
 """
 from __future__ import annotations
 
@@ -131,8 +132,9 @@ def _params(k, block, degree, tol, v0, basis, phase1, max_sweeps):
                            which=RR.SMALLEST, refine=True, phase1_sweeps=phase1)
 
 
-def eigen_targets(problems, k, block, degree, tol=1e-10, basis="bf16", phase1=2, max_sweeps=60):
-    """Converged Ritz vectors of each problem (from random starts): a list of
+def eigen_targets(problems, k, block, degree, tol=1e-6, basis="bf16", phase1=1, max_sweeps=60):
+    """Ritz vectors of each problem from random starts, to residual `tol` (the
+    targets need not be more accurate than the network can be): a list of
     (potential (N, N) FP32 device, V* (n x k FP64), sweeps).  `problems` yields
     (potential (N, N) host FP64, CSR row_ptr / col_idx / values, V0 (n x block) host FP64)."""
     out = []
@@ -169,29 +171,40 @@ def train(net: StartBlockNet, data, epochs: int, lr: float, batch: int = 8, log=
     return hist
 
 
-def evaluate(net, problems, k, block, degree, tol=1e-10, basis="bf16", phase1=2, max_sweeps=60):
-    """Per held-out problem: sweeps and wall time (ms) to residual tol from the
-    random start and from the network's start (its inference included).
-    `net` None evaluates the random start only."""
+ARMS = ("random", "modes", "learned")
+
+
+def evaluate(net, problems, k, block, degree, tol=1e-10, basis="bf16", phase1=1, max_sweeps=60, arms=ARMS):
+    """Solve each held-out problem from several start blocks and record sweeps,
+    wall time (ms, the network's inference included) and the largest residual
+    of the wanted pairs after each projection (Rayleigh-Ritz residuals):
+      random:  U(0,1) (the paper's start);
+      modes:   the `block` lowest free Dirichlet modes (no network);
+      learned: the network's k columns, then the random start's columns k .. block - 1."""
     rows = []
+    N = net.N
+    modes = torch.from_numpy(free_modes(N, block)).to("cuda")
     for pot, rp, ci, va, V0 in problems:
         n = pot.size
         d = [torch.from_numpy(a).to("cuda") for a in (rp, ci, va)]
         op = api.csr_operator(*d)
         v_rand = api.fortran(torch.from_numpy(V0).to("cuda"))
+        P = torch.from_numpy((pot * POTENTIAL_SCALE).astype(np.float32)).to("cuda")
         row = {}
-        arms = [("random", None)] + ([("learned", net)] if net is not None else [])
-        for name, nt in arms:
+        for name in arms:
             v0 = v_rand.clone()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            if nt is not None:
-                nt.set_potential(torch.from_numpy((pot * POTENTIAL_SCALE).astype(np.float32)).to("cuda"))
-                nt.propose(v0)
+            if name == "modes":
+                api.rr_net_block(modes, net.scale, v0)
+            elif name == "learned":
+                net.set_potential(P)
+                net.propose(v0)
             p = _params(k, block, degree, tol, v0, basis, phase1, max_sweeps)
             _, _, info = api.rr_eig(op, p, n)
             torch.cuda.synchronize()
             row[name] = {"sweeps": info["sweeps"], "refine_sweeps": info["refine_sweeps"],
-                         "n_converged": info["n_converged"], "ms": 1e3 * (time.perf_counter() - t0)}
+                         "n_converged": info["n_converged"], "ms": 1e3 * (time.perf_counter() - t0),
+                         "res": info["res_history"][:info["sweeps"]]}
         rows.append(row)
     return rows

@@ -278,14 +278,14 @@ def test_gram_fp64_accurate_mixed_types(rr):
     assert np.all(np.abs(host(G2) - Y.T @ Y) <= 2 * n * U53 * (np.abs(Y).T @ np.abs(Y)))
 
 
-def test_gram_tensor_core_path_wide_range(rr):
-    """The tensor-core Gram path (n % 8 == 0, q <= 128): ragged tiles, a K
-    range that is not a multiple of the 4096-long exact chunks, columns
-    spanning many binades and rows far below the column maxima, mixed storage
-    types and accumulation.  Bound: the slice truncation (2^-47 n times the
-    column maxima) plus the FP64 reference's own rounding."""
+@pytest.mark.parametrize("n,p,q", [(8200, 130, 100), (4104, 40, 300)])
+def test_gram_tensor_core_path_wide_range(rr, n, p, q):
+    """The tensor-core Gram path (n % 8 == 0; Y in column chunks of at most
+    128): ragged tiles, a K range that is not a multiple of the 4096-long
+    exact chunks, columns spanning many binades and rows far below the column
+    maxima, mixed storage types and accumulation.  Bound: the slice truncation
+    (2^-47 n times the column maxima) plus the FP64 reference's own rounding."""
     rng = np.random.default_rng(31)
-    n, p, q = 8200, 130, 100
     X = rng.standard_normal((n, p)) * np.exp2(rng.integers(-30, 30, p))[None, :]
     X[rng.random((n, p)) < 0.3] *= 1e-9
     Y = rng.standard_normal((n, q)) * np.exp2(rng.integers(-20, 20, q))[None, :]
@@ -414,6 +414,59 @@ def test_pencil_svd_clustered_spectrum(rr):
 
 
 # ---------------------------------------------------------------- a3
+@pytest.mark.parametrize("ytype,otype,b", [("bf16", "bf16", 20), ("bf16", "f32", 160), ("f32", "f32", 13),
+                                           ("f64", "f64", 7)])
+def test_chebyshev_step_rows(rr, ytype, otype, b):
+    """Row-major fused step against the oracle's CSR product, ragged b (pad
+    columns up to the 16-byte vector width stay zero), rows without a stored
+    diagonal among them (a shift-only row)."""
+    N = 40
+    rp, ci, va, v = wl.grid_schrodinger_csr(N, 10.0, 3000)
+    n = N * N
+    # drop the stored diagonal of every seventh row
+    keep = np.ones(len(ci), dtype=bool)
+    for i in range(0, n, 7):
+        e = rp[i] + int(np.nonzero(ci[rp[i]:rp[i + 1]] == i)[0][0])
+        keep[e] = False
+    ci, va = ci[keep], va[keep]
+    rp = np.concatenate([[0], np.cumsum([keep[rp[i]:rp[i + 1]].sum() for i in range(n)])]).astype(rp.dtype)
+    tt = {"bf16": torch.bfloat16, "f32": torch.float32, "f64": torch.float64}
+    width = 16 // {"bf16": 2, "f32": 4, "f64": 8}[ytype]
+    bp = -(-b // width) * width
+    rnd = {"bf16": O.round_bf16, "f32": lambda a: a.astype(np.float32).astype(np.float64),
+           "f64": lambda a: a}[ytype]
+    X = rnd(np.random.default_rng(11).standard_normal((n, b)))
+    Xp = rnd(np.random.default_rng(12).standard_normal((n, b)))
+
+    def rows(a):
+        t = torch.zeros(n, bp, dtype=torch.float64)
+        t[:, :b] = torch.from_numpy(a)
+        return t.to(tt[ytype]).to(DEV)
+    d_rp, d_ci, d_va = (torch.from_numpy(a).to(DEV) for a in (rp, ci, va))
+    alpha, c, beta = 0.7, 3.0, 0.4
+    Yn = rr.rr_chebyshev_step_rows(d_rp, d_ci, d_va, rows(X), rows(Xp), b, alpha, c, beta, out_dtype=tt[otype])
+    Amul = O.csr_apply(rp, ci, va)
+    ref = alpha * (Amul(X) - c * X) - beta * Xp
+    got = host(Yn)
+    Aabs = O.csr_apply(rp, ci, np.abs(va))           # |A| |X| bounds the rounding of the sums
+    absb = alpha * (Aabs(np.abs(X)) + c * np.abs(X)) + beta * np.abs(Xp)
+    if ytype == "f64":
+        tol = 16 * U53 * absb
+    else:
+        tol = 16 * U24 * absb + (2.0 ** -8 * np.abs(ref) if otype == "bf16" else 0)
+    assert np.all(np.abs(got[:, :b] - ref) <= tol)
+    assert np.all(got[:, b:] == 0)
+    # first step (no Y_prev)
+    Y1 = rr.rr_chebyshev_step_rows(d_rp, d_ci, d_va, rows(X), None, b, alpha, c, 0.0, out_dtype=tt[otype])
+    ref1 = alpha * (Amul(X) - c * X)
+    absb1 = alpha * (Aabs(np.abs(X)) + c * np.abs(X))
+    if ytype == "f64":
+        tol1 = 16 * U53 * absb1
+    else:
+        tol1 = 16 * U24 * absb1 + (2.0 ** -8 * np.abs(ref1) if otype == "bf16" else 0)
+    assert np.all(np.abs(host(Y1)[:, :b] - ref1) <= tol1)
+
+
 def test_csr_spmm_and_chebyshev_step(rr):
     N, b = 40, 24
     rp, ci, va, v = wl.grid_schrodinger_csr(N, 10.0, 3000)
