@@ -554,6 +554,40 @@ def run_stage(args):
                           "train_ms_per_sample_step": 1e3 * (t2 - t1) / max(1, args.epochs * args.train),
                           "loss_first": hist[0] if hist else None, "loss_last": hist[-1] if hist else None,
                           "arms": arms}))
+    elif args.stage == "fp8":
+        # the dense workload's block product A V (16384 x 4096 operator, block 128) with BF16
+        # operands and with E4M3 operands (power-of-two row / column scales), CUDA events
+        A = torch.randn(N, M, device="cuda", dtype=torch.float64).t()   # M x N column-major
+        V = rr.fortran(torch.randn(N, B, device="cuda", dtype=torch.float64))
+        A_row = A.to(torch.bfloat16).contiguous()
+        Vb = rr.fortran(V.to(torch.bfloat16))
+        Aq, ia = rr.rr_quantize_e4m3(A, by_rows=True)
+        Vq, iv = rr.rr_quantize_e4m3(V, by_rows=False)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        out = {}
+        for name, fn, nbytes in (("bf16", lambda: rr.rr_gemm_lowp(2, M, B, N, A_row, N, Vb, N), M * N * 2),
+                                 ("e4m3", lambda: rr.rr_gemm_e4m3(M, B, N, Aq, ia, Vq, iv), M * N)):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            reps = 20
+            e0.record()
+            for _ in range(reps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            us = e0.elapsed_time(e1) * 1e3 / reps
+            out[name] = {"us": us, "operator_gbs": nbytes / us / 1e3, "tflops": 2.0 * M * N * B / us / 1e6}
+        Cb = rr.rr_gemm_lowp(2, M, B, N, A_row, N, Vb, N)
+        C8 = rr.rr_gemm_e4m3(M, B, N, Aq, ia, Vq, iv)
+        ref = A @ V
+        scale = ref.abs().max().item()
+        peaks, src = load_peaks()
+        print(json.dumps({"stage": "fp8", "M": M, "N": B, "K": N, **out, "peak_gbs": peaks["hbm_gbs"],
+                          "peak_source": src,
+                          "max_err_rel": {"bf16": (Cb.double() - ref).abs().max().item() / scale,
+                                          "e4m3": (C8.double() - ref).abs().max().item() / scale}}))
     elif args.stage == "prep":
         A = torch.randn(N, M, device="cuda", dtype=torch.float64).t()   # M x N column-major
         X = rr.fortran(torch.randn(N, B, device="cuda", dtype=torch.float64))
@@ -585,7 +619,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--stage", choices=["pencil", "hessenberg", "gemm", "split", "f64emu", "prep", "cheb", "warm", "sparse"],
+    ap.add_argument("--stage", choices=["pencil", "hessenberg", "gemm", "split", "f64emu", "prep", "cheb", "warm", "sparse", "fp8"],
                     help="run one stage of the workload (profiling driver)")
     ap.add_argument("--b", type=int, default=256, help="pencil size for --stage pencil, columns for hessenberg")
     ap.add_argument("--rows", type=int, default=M, help="rows of the block for --stage hessenberg")

@@ -359,6 +359,28 @@ rr_status rr_chebyshev_step_rows(int64_t n, int64_t b, const int32_t* row_ptr,
                                  double c, double beta, int32_t out_type, void* Y_next,
                                  int64_t ldr_next, void* stream);
 
+/* FP8-E4M3 operands and their block product (the FP8 storage option of the
+ * precision map, Sec. 4.2 / Fig. 4, with FP32 accumulation).
+ * rr_quantize_e4m3: X (rows x cols FP64, column-major, ld ldx) -> Q (E4M3
+ *   bytes).  by_rows = 0: one scale per column, Q column-major (ldq >= rows);
+ *   by_rows = 1: one scale per row, Q row-major, Q[i * ldq + j] (ldq >= cols).
+ *   Each scale is the power of two 2^e, the largest with max|x| 2^e <= 448
+ *   (e clamped to [-126, 126]; an all-zero line gets 2^0), applied exactly;
+ *   Q = e4m3_rn(fp32_rn(x 2^e)), round to nearest even, saturating at 448.
+ *   inv_scale (cols or rows FP32) receives 2^-e.  scratch: 8 max(rows, cols)
+ *   bytes of device memory.
+ * rr_gemm_e4m3: C (M x N FP32, column-major) = diag(a_scale) A_k^T B
+ *   diag(b_scale), A_k (K x M) and B (K x N) E4M3 with K contiguous (ld in
+ *   elements: multiples of 16, bases 16-byte aligned), N <= 256; tcgen05
+ *   kind::f8f6f4 on the tensor cores, FP32 accumulation.  For W = A V: A_k is
+ *   A quantised by rows (row-major), B the block V quantised by columns.
+ * Errors: RR_ERR_ARG for bad sizes, strides, alignment or null pointers. */
+rr_status rr_quantize_e4m3(int64_t rows, int64_t cols, const double* X, int64_t ldx, int32_t by_rows,
+                           void* Q, int64_t ldq, float* inv_scale, void* scratch, void* stream);
+rr_status rr_gemm_e4m3(int64_t M, int64_t N, int64_t K, const void* A_k, int64_t lda,
+                       const float* a_scale, const void* B, int64_t ldb, const float* b_scale, float* C,
+                       int64_t ldc, void* stream);
+
 /* Learned warm start (the start block V of Alg. 1, which the paper draws at
  * random, proposed instead by a small convolutional network of the operator's
  * potential and trained on converged Ritz vectors).  All FP32, NCHW layout on

@@ -5,7 +5,7 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 Paper: "Mixed Precision Orthogonalization-Free Projection Methods for
 Eigenvalue and Singular Value Problems" (arXiv 2505.00281).  Each function
 names the passage it follows.  Readings of passages that are silent, garbled
-or ambiguous are marked READING and listed in the design doc.
+or ambiguous are marked READING.
 """
 from __future__ import annotations
 
@@ -16,7 +16,7 @@ import numpy as np
 import scipy.linalg as sla
 
 __all__ = [
-    "round_bf16", "colscale_inf", "hessenberg", "hessenberg_tol",
+    "round_bf16", "round_e4m3", "e4m3_decode", "e4m3_scale_exp", "quantize_e4m3", "colscale_inf", "hessenberg", "hessenberg_tol",
     "gram", "dense_apply", "csr_apply", "csr_gershgorin",
     "pencil_eig", "pencil_svd", "rayleigh_ritz_eig", "rayleigh_ritz_svd",
     "chebyshev_filter", "residual_eig", "residual_svd",
@@ -43,6 +43,55 @@ def round_bf16(x) -> np.ndarray:
     r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
     out = r.astype(np.uint32).view(np.float32).astype(np.float64)
     return out.reshape(np.shape(x))
+
+
+E4M3_MAX = 448.0
+
+
+def e4m3_decode(code) -> np.ndarray:
+    """Value of an FP8-E4M3 byte (OCP 8-bit float, 'fn' variant): sign bit, 4
+    exponent bits (bias 7), 3 mantissa bits; exponent 0 is subnormal (m/8 2^-6);
+    S.1111.111 is NaN, there is no infinity.  FP64 output."""
+    c = np.asarray(code, dtype=np.int64)
+    sgn = np.where(c & 0x80, -1.0, 1.0)
+    e = (c >> 3) & 0xF
+    m = (c & 7).astype(np.float64)
+    val = np.where(e == 0, m / 8.0 * 2.0 ** -6, (1.0 + m / 8.0) * np.exp2(e.astype(np.float64) - 7.0))
+    val = np.where((c & 0x7F) == 0x7F, np.nan, val)
+    return sgn * val
+
+
+def round_e4m3(x) -> np.ndarray:
+    """Round to FP8-E4M3 as the FP8 path does (READING: the GPU converts FP64 to
+    FP32 first, so both sides take the same two steps): FP32 round-to-nearest-even,
+    then to the nearest E4M3 value, ties to even mantissa, saturating at +-448.
+    The spacing is 2^(E-3) for |f| in [2^E, 2^(E+1)), E >= -6, and 2^-9 below 2^-6."""
+    f = np.asarray(np.asarray(x, dtype=np.float32), dtype=np.float64)
+    a = np.abs(f)
+    E = np.floor(np.log2(np.where(a > 0, a, 1.0)))
+    q = np.exp2(np.maximum(E, -6.0) - 3.0)
+    r = np.rint(f / q) * q                       # f / q is exact (q a power of two)
+    return np.clip(r, -E4M3_MAX, E4M3_MAX)
+
+
+def e4m3_scale_exp(m):
+    """Largest e with m 2^e <= 448, clamped to [-126, 126]; 0 where m = 0."""
+    m = np.asarray(m, dtype=np.float64)
+    fr, ex = np.frexp(np.where(m > 0, m, 1.0))     # m = fr 2^ex, fr in [0.5, 1)
+    e = 8 - (ex - 1) - (2.0 * fr > 1.75)
+    e = np.clip(e, -126, 126)
+    return np.where(m > 0, e, 0).astype(np.int64)
+
+
+def quantize_e4m3(X, by_rows: bool):
+    """E4M3 values of X with one power-of-two scale per column (or per row):
+    returns (values of the E4M3 codes, FP64, same shape as X; inverse scales 2^-e)."""
+    X = np.asarray(X, dtype=np.float64)
+    m = np.max(np.abs(X), axis=1 if by_rows else 0) if X.size else np.zeros(0)
+    e = e4m3_scale_exp(m)
+    s = np.exp2(e.astype(np.float64))
+    Xs = X * (s[:, None] if by_rows else s[None, :])
+    return round_e4m3(Xs), np.exp2(-e.astype(np.float64))
 
 
 # --------------------------------------------------------------------------

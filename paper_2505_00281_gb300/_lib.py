@@ -91,6 +91,8 @@ _SIGS = {
                                   c_dbl, c_dbl, c_vp, c_vp, c_i64, c_vp, c_i32, c_vp, c_i64, c_vp]),
     "rr_chebyshev_step_rows": (c_i32, [c_i64, c_i64, c_vp, c_vp, c_vp, c_i32, c_vp, c_vp, c_i64, c_dbl, c_dbl,
                                        c_dbl, c_i32, c_vp, c_i64, c_vp]),
+    "rr_quantize_e4m3": (c_i32, [c_i64, c_i64, c_vp, c_i64, c_i32, c_vp, c_i64, c_vp, c_vp, c_vp]),
+    "rr_gemm_e4m3": (c_i32, [c_i64, c_i64, c_i64, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp]),
     "rr_conv3x3_forward": (c_i32, [c_i32, c_i32, c_i32, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, c_i64, c_i32,
                                    c_vp, c_vp]),
     "rr_conv3x3_backward": (c_i32, [c_i32, c_i32, c_i32, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,

@@ -16,7 +16,7 @@ __all__ = [
     "fortran", "ld_of", "dense_operator", "csr_operator", "make_params", "rr_eig", "rr_svd",
     "rr_batch_svd", "rr_colscale_cast", "rr_cast_operator", "rr_split_operator", "rr_lift", "rr_gemm_lowp", "rr_gemm_f64",
     "rr_hessenberg", "rr_gram", "rr_gram_noalloc", "rr_pencil_eig", "rr_pencil_svd", "rr_csr_spmm",
-    "rr_chebyshev_step", "rr_chebyshev_step_rows", "rr_conv3x3_forward", "rr_conv3x3_backward", "rr_relu_mask", "rr_procrustes_grad",
+    "rr_chebyshev_step", "rr_chebyshev_step_rows", "rr_quantize_e4m3", "rr_gemm_e4m3", "rr_conv3x3_forward", "rr_conv3x3_backward", "rr_relu_mask", "rr_procrustes_grad",
     "rr_adam", "rr_net_block", "RrParams", "RrOperator", "RrInfo", "DTYPES",
 ]
 
@@ -351,6 +351,31 @@ def rr_chebyshev_step_rows(row_ptr, col_idx, values, Y_cur, Y_prev, b, alpha, c,
         n, b, _p(row_ptr), _p(col_idx), _p(values), DTYPES[Y_cur.dtype], _p(Y_cur), _p(Y_prev), ldr, alpha, c,
         beta, DTYPES[out_dtype], _p(Yn), ldr, _stream(stream)))
     return Yn
+
+
+def rr_quantize_e4m3(X, by_rows=False, stream=None):
+    """E4M3 copy of the FP64 column-major X with power-of-two scales per column
+    (Q column-major, (rows, ldq) uint8 view) or per row (Q row-major).
+    Returns (Q uint8 tensor, inv_scale FP32).  ld is rounded up to 16 bytes."""
+    rows, cols = X.shape
+    inner = cols if by_rows else rows
+    ldq = -(-max(inner, 1) // 16) * 16
+    outer = rows if by_rows else cols
+    Q = torch.zeros(outer, ldq, dtype=torch.uint8, device=X.device)   # each line contiguous
+    inv = torch.empty(outer, dtype=torch.float32, device=X.device)
+    scratch = torch.empty(max(rows, cols, 1), dtype=torch.int64, device=X.device)
+    check("rr_quantize_e4m3", lib().rr_quantize_e4m3(rows, cols, _p(X), ld_of(X), int(by_rows), _p(Q), ldq,
+                                                     _p(inv), _p(scratch), _stream(stream)))
+    return Q, inv
+
+
+def rr_gemm_e4m3(M, N, K, A_q, a_scale, B_q, b_scale, stream=None):
+    """C (M x N FP32, column-major) = diag(a_scale) A_q^T B_q diag(b_scale); A_q (M, lda) and
+    B_q (N, ldb) uint8 tensors whose lines are the K-contiguous rows of A and columns of B."""
+    C = empty_f(M, N, torch.float32, A_q.device)
+    check("rr_gemm_e4m3", lib().rr_gemm_e4m3(M, N, K, _p(A_q), A_q.stride(0), _p(a_scale), _p(B_q), B_q.stride(0),
+                                             _p(b_scale), _p(C), ld_of(C), _stream(stream)))
+    return C
 
 
 def _nchw(t):

@@ -15,6 +15,9 @@
 //                      lanes 32w..32w+31 = rows), coalesced column stores.
 // K splits (small M) add their partial tiles with FP32 atomics into a C
 // pre-initialised to the added term.
+// FP8 variant (kF8): E4M3 x E4M3 -> FP32 (tcgen05 kind::f8f6f4, K = 32 per
+// instruction), the same 128-byte swizzle rows (128 elements per K step); the
+// epilogue multiplies by a per-row scale of A and a per-column scale of B.
 // Every mbarrier wait is bounded (2 s); on expiry the kernel records an error
 // (read by the host), stops issuing, waits (bounded) for its in-flight copies,
 // frees its TMEM and returns.
@@ -102,6 +105,23 @@ __device__ __forceinline__ void umma_bf16(uint32_t dtmem, uint64_t adesc, uint64
       : "memory");
 }
 
+__device__ __forceinline__ void umma_e4m3(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+template <bool kF8>
+__device__ __forceinline__ void umma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                     uint32_t accumulate) {
+  if constexpr (kF8) umma_e4m3(dtmem, adesc, bdesc, idesc, accumulate);
+  else umma_bf16(dtmem, adesc, bdesc, idesc, accumulate);
+}
+
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                    smem_u32(bar))
@@ -139,6 +159,8 @@ struct TcArgs {
   int64_t ldr;
   const double* coef;
   int atomic;      // 1: K-split, add into C
+  const float* rscale;  // FP8: C(i, j) = rscale[i] cscale[j] acc(i, j)
+  const float* cscale;
   // FP64-emulation epilogue (Ozaki-style slices, see k_f64emu.cu).  Launch z
   // multiplies A slice p0 by nq = 1 or 2 consecutive B slices q0, q0 + 1
   // (pair[z] = p0 | q0 << 8 | nq << 16, 0-based); A rows / B rows of slice s
@@ -168,6 +190,7 @@ __device__ __forceinline__ double mul_pow2(double d, int e) {
   return d == 0.0 ? d : ldexp(d, e);
 }
 
+template <bool kF8>
 __global__ void __launch_bounds__(128, 1) k_gemm_bf16_tc(const __grid_constant__ CUtensorMap tmA,
                                                           const __grid_constant__ CUtensorMap tmB,
                                                           const __grid_constant__ CUtensorMap tmA2,
@@ -227,7 +250,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16_tc(const __grid_constant__
         unsigned char* sa = base + (size_t)s * stage_bytes;
         unsigned char* sb = sa + a_bytes;
         mbar_expect_tx(&full[s], stage_bytes);
-        const int kx = (ks0 + i) * kBK;
+        const int kx = (ks0 + i) * (kF8 ? 2 * kBK : kBK);  // elements per 128-byte row
         tma_load_2d(sa, &tmA, &full[s], kx, (int)m0 + a_off);
         tma_load_2d(sb, &tmB, &full[s], kx, b_off);
         if (spl) {
@@ -247,10 +270,10 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16_tc(const __grid_constant__
       }
     } else if (warp == 1 && lane == 0) {
       // ---------------- MMA issuer ----------------
-      const uint32_t idesc = (1u << 4)                          // D: FP32
-                             | (1u << 7) | (1u << 10)            // A, B: BF16
-                             | ((uint32_t)(a.npad >> 3) << 17)  // N / 8
-                             | ((uint32_t)(kBM >> 4) << 24);    // M / 16
+      const uint32_t idesc = (1u << 4)                                  // D: FP32
+                             | (kF8 ? 0u : (1u << 7) | (1u << 10))       // A, B: BF16 (kind::f16) or E4M3 (0)
+                             | ((uint32_t)(a.npad >> 3) << 17)          // N / 8
+                             | ((uint32_t)(kBM >> 4) << 24);            // M / 16
       for (int i = 0; i < nks; ++i) {
         const int s = i % a.stages;
         if (!mbar_wait(&full[s], (i / a.stages) & 1)) {
@@ -261,9 +284,8 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16_tc(const __grid_constant__
         const uint32_t sb = sa + a_bytes;
         const uint64_t ad = sdesc_sw128(sa), bd = sdesc_sw128(sb);
 #pragma unroll
-        for (int kk = 0; kk < kBK / 16; ++kk)  // K = 16 per instruction: +32 bytes
-          umma_bf16(tmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc,
-                    (i > 0 || kk > 0) ? 1u : 0u);
+        for (int kk = 0; kk < kBK / 16; ++kk)  // 32 bytes of K per instruction (16 BF16 / 32 E4M3)
+          umma<kF8>(tmem, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2), idesc, (i > 0 || kk > 0) ? 1u : 0u);
         if (spl) {
           // A_lo B_hi and A_hi B_lo from the same stage (each operand read once)
           const uint64_t ad2 = sdesc_sw128(sb + b_bytes), bd2 = sdesc_sw128(sb + b_bytes + a_bytes);
@@ -327,6 +349,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16_tc(const __grid_constant__
       }
     } else if (ready) {
       const int64_t row = m0 + warp * 32 + lane;
+      const float rs = (kF8 && row < a.M) ? __ldg(a.rscale + row) : 1.f;
       for (int c0 = 0; c0 < a.npad; c0 += 32) {
         uint32_t r[32];
         tmem_ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
@@ -336,6 +359,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16_tc(const __grid_constant__
             const int64_t col = c0 + j;
             if (col < a.N) {
               float v = __uint_as_float(r[j]);
+              if constexpr (kF8) v = v * rs * __ldg(a.cscale + col);
               float* dst = a.C + row + col * a.ldc;
               if (a.atomic) {
                 atomicAdd(dst, v);
@@ -379,7 +403,8 @@ int& gemm_force_simt() {
 rr_status tc_prepare_attributes() {
   static bool done = false;
   if (!done) {
-    RR_CUDA(cudaFuncSetAttribute(k_gemm_bf16_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    RR_CUDA(cudaFuncSetAttribute(k_gemm_bf16_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    RR_CUDA(cudaFuncSetAttribute(k_gemm_bf16_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
     done = true;
   }
   return RR_OK;
@@ -414,12 +439,13 @@ bool gemm_bf16_tc_supported(int64_t M, int64_t N, int64_t K, int64_t lda, int64_
 }
 
 static bool make_map(CUtensorMap* m, const void* base, int64_t inner, int64_t outer, int64_t ld_elems,
-                     uint32_t box_inner, uint32_t box_outer) {
+                     uint32_t box_inner, uint32_t box_outer, bool f8 = false) {
   cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
-  cuuint64_t strides[1] = {(cuuint64_t)ld_elems * 2};
+  cuuint64_t strides[1] = {(cuuint64_t)ld_elems * (f8 ? 1 : 2)};
   cuuint32_t box[2] = {box_inner, box_outer};
   cuuint32_t es[2] = {1, 1};
-  CUresult r = encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides,
+  CUresult r = encode_fn()(m, f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                           const_cast<void*>(base), dims, strides,
                            box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -564,8 +590,67 @@ static rr_status gemm_bf16_tc_impl(int64_t M, int64_t N, int64_t K, const __nv_b
     note_launches(1);
   }
   dim3 grid((unsigned)tiles, (unsigned)splits, (unsigned)npairs);
-  k_gemm_bf16_tc<<<grid, 128, smem, s>>>(ta, tb, ta2, tb2, a);
+  a.rscale = a.cscale = nullptr;
+  k_gemm_bf16_tc<false><<<grid, 128, smem, s>>>(ta, tb, ta2, tb2, a);
   return check_launch("gemm_bf16_tc");
+}
+
+// E4M3 product: C (M x N, FP32) = diag(rscale) A_k^T B diag(cscale), A_k
+// K x M and B K x N E4M3 with K contiguous (ld in elements, multiples of 16),
+// FP32 accumulation.
+rr_status gemm_e4m3_tc(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, const float* rscale,
+                       const void* B, int64_t ldb, const float* cscale, float* C, int64_t ldc, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || N > 256 || K <= 0 || !rscale || !cscale || !C) return RR_ERR_ARG;
+  if (lda % 16 || ldb % 16 || ((uintptr_t)A & 15) || ((uintptr_t)B & 15)) return RR_ERR_ARG;
+  if (M > 0x7fffffff || K > 0x7fffffff || !encode_fn()) return RR_ERR_ARG;
+  constexpr int kBK8 = 2 * kBK;  // E4M3 elements per 128-byte row
+  const int npad = (int)((N + 15) / 16 * 16);
+  int tcols = 32;
+  while (tcols < npad) tcols <<= 1;
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, A, K, M, lda, kBK8, kBM, true)) return RR_ERR_ARG;
+  if (!make_map(&tb, B, K, N, ldb, kBK8, (uint32_t)npad, true)) return RR_ERR_ARG;
+  const int64_t tiles = (M + kBM - 1) / kBM;
+  const int nk = (int)((K + kBK8 - 1) / kBK8);
+  const int sms = num_sms();
+  int splits = 1;
+  if (tiles < sms) {
+    splits = (int)(sms / tiles);
+    if (splits > nk) splits = nk;
+    if (splits < 1) splits = 1;
+  }
+  const int per = (nk + splits - 1) / splits;
+  splits = (nk + per - 1) / per;
+  const uint32_t stage_bytes = kBM * kBK8 + (uint32_t)npad * kBK8;
+  int stages = (int)((200 * 1024) / stage_bytes);
+  if (stages > 8) stages = 8;
+  if (stages < 2) return RR_ERR_ARG;
+  const size_t smem = 1024 + (size_t)stages * stage_bytes + (2 * stages + 1) * sizeof(uint64_t);
+  RR_TRY(tc_prepare_attributes());
+  TcArgs a{};
+  a.M = M;
+  a.N = N;
+  a.K = K;
+  a.npad = npad;
+  a.tmem_cols = tcols;
+  a.stages = stages;
+  a.ksteps_per_split = per;
+  a.nk = nk;
+  a.nk1 = nk;
+  a.segs = 1;
+  a.C = C;
+  a.ldc = ldc;
+  a.atomic = splits > 1;
+  a.rscale = rscale;
+  a.cscale = cscale;
+  if (splits > 1) {
+    dim3 gi((unsigned)std::min<int64_t>((M + 255) / 256, 256), (unsigned)N);
+    k_tc_init_c<<<gi, 256, 0, s>>>(M, N, C, ldc, nullptr, 0, nullptr);
+    note_launches(1);
+  }
+  dim3 grid((unsigned)tiles, (unsigned)splits, 1u);
+  k_gemm_bf16_tc<true><<<grid, 128, smem, s>>>(ta, tb, ta, tb, a);
+  return check_launch("gemm_e4m3_tc");
 }
 
 // error word of the tensor-core kernels (0 = ok); cleared on read

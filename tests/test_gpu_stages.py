@@ -490,3 +490,48 @@ def test_csr_spmm_and_chebyshev_step(rr):
     Xd = np.random.default_rng(6).standard_normal((n, b))
     Y64 = rr.rr_csr_spmm(d_rp, d_ci, d_va, dev(Xd), out_dtype=torch.float64)
     assert np.abs(host(Y64) - Amul(Xd)).max() < 1e-13 * (np.abs(Xd).max() * 20)
+
+
+# ---------------------------------------------------------------- FP8-E4M3 operands and product
+@pytest.mark.parametrize("by_rows", [False, True])
+def test_quantize_e4m3_bitexact(rr, by_rows):
+    """E4M3 codes and power-of-two scales bit for bit against the oracle's
+    rounding (FP32 then E4M3, ties to even, saturation), columns / rows spanning
+    many binades, a zero line, a line whose maximum is exactly 448 2^k."""
+    rng = np.random.default_rng(41)
+    rows, cols = 1000, 37
+    X = rng.standard_normal((rows, cols)) * np.exp2(rng.integers(-40, 40, (rows, cols)) // 8)
+    X *= np.exp2(rng.integers(-30, 30, cols))[None, :] if not by_rows else np.exp2(rng.integers(-30, 30, rows))[:, None]
+    if by_rows:
+        X[5, :] = 0.0
+        X[7, 3] = 448.0 * 2.0 ** 5
+    else:
+        X[:, 5] = 0.0
+        X[3, 7] = 448.0 * 2.0 ** 5
+    Q, inv = rr.rr_quantize_e4m3(dev(X), by_rows=by_rows)
+    ref, rinv = O.quantize_e4m3(X, by_rows)
+    assert np.array_equal(host(inv), rinv)
+    codes = Q.cpu().numpy()
+    got = O.e4m3_decode(codes[:, :(cols if by_rows else rows)])
+    assert np.array_equal(got, ref if by_rows else ref.T)
+
+
+@pytest.mark.parametrize("M,N,K", [(300, 40, 1000), (256, 128, 4096)])
+def test_gemm_e4m3(rr, M, N, K):
+    """tcgen05 kind::f8f6f4 product of E4M3 operands with row / column scales
+    against the exact product of the same E4M3 values (FP64), within FP32
+    accumulation: K u32 |Q_A| |Q_B| + the two FP32 scale multiplications.
+    Ragged M and N tiles, a K tail, and K splits with atomic accumulation."""
+    rng = np.random.default_rng(M + K)
+    A = rng.standard_normal((M, K)) * np.exp2(rng.integers(-8, 8, M))[:, None]
+    B = rng.standard_normal((K, N))
+    Aq, ia = rr.rr_quantize_e4m3(dev(A), by_rows=True)       # rows of A, K contiguous
+    Bq, ib = rr.rr_quantize_e4m3(dev(B), by_rows=False)      # columns of B, K contiguous
+    C = host(rr.rr_gemm_e4m3(M, N, K, Aq, ia, Bq, ib))
+    qa, ra = O.quantize_e4m3(A, True)
+    qb, rb = O.quantize_e4m3(B, False)
+    ref = ra[:, None] * (qa @ qb) * rb[None, :]
+    bound = ra[:, None] * (np.abs(qa) @ np.abs(qb)) * rb[None, :] * K * U24 + 4 * U24 * np.abs(ref)
+    assert np.all(np.abs(C - ref) <= bound)
+    # the FP8 product approximates the FP64 one to the E4M3 rounding (2^-4 relative per factor)
+    assert np.abs(C - A @ B).max() <= 0.25 * (np.abs(A) @ np.abs(B)).max()

@@ -264,3 +264,36 @@ def test_solve_svd_converges_to_prescribed_sigma():
     assert r.n_converged == k
     assert np.allclose(r.values, sig[:k], rtol=1e-10)
     assert np.abs(r.U.T @ r.U - np.eye(k)).max() < 1e-10
+
+
+# ---------------------------------------------------------------- FP8-E4M3 rounding
+def test_e4m3_rounding_pins():
+    """round_e4m3 against values fixed by the E4M3 format: the 254 finite codes
+    (decoded from their bit fields), idempotence on every one of them, ties to
+    the even mantissa at every midpoint, saturation, and hand-worked values."""
+    codes = np.array([c for c in range(256) if (c & 0x7F) != 0x7F])
+    vals = O.e4m3_decode(codes)
+    assert len(np.unique(vals)) == 253                      # +0 and -0 coincide
+    assert np.max(vals) == 448.0 and np.min(vals[vals > 0]) == 2.0 ** -9
+    assert np.array_equal(O.round_e4m3(vals), vals)
+    pos = np.sort(np.unique(vals[vals >= 0]))
+    mid = (pos[:-1] + pos[1:]) / 2
+    rounded = O.round_e4m3(mid)
+    lo_code = np.array([int(np.nonzero(O.e4m3_decode(np.arange(128)) == v)[0][0]) for v in pos[:-1]])
+    expect = np.where(lo_code % 2 == 0, pos[:-1], pos[1:])  # even mantissa wins the tie
+    assert np.array_equal(rounded, expect)
+    assert O.round_e4m3(1.0625) == 1.0 and O.round_e4m3(1.1875) == 1.25
+    assert O.round_e4m3(0.3) == 0.3125 and O.round_e4m3(2.0 ** -10) == 0.0
+    assert O.round_e4m3(3 * 2.0 ** -10) == 2.0 ** -8
+    assert O.round_e4m3(449.0) == 448.0 and O.round_e4m3(-1e6) == -448.0 and O.round_e4m3(470.0) == 448.0
+
+
+def test_e4m3_scale_exponent():
+    rng = np.random.default_rng(8)
+    m = np.concatenate([np.exp2(rng.uniform(-100, 100, 2000)), 448.0 * np.exp2(np.arange(-5, 6.0)),
+                        [448.0 * (1 + 2.0 ** -52), 1.75, 1.75 * (1 + 2.0 ** -52)]])
+    e = O.e4m3_scale_exp(m)
+    assert np.all(m * np.exp2(e) <= 448.0) and np.all(m * np.exp2(e + 1) > 448.0)
+    assert O.e4m3_scale_exp(0.0) == 0 and O.e4m3_scale_exp(1e-300) == 126 and O.e4m3_scale_exp(1e300) == -126
+    Xv, inv = O.quantize_e4m3(np.array([[1.0, 0.0], [-3.0, 0.0]]), by_rows=False)
+    assert np.array_equal(inv, [2.0 ** -7, 1.0]) and np.array_equal(Xv[:, 0], [128.0, -384.0])
