@@ -327,6 +327,30 @@ def run_ours(args):
                 "sigma_max_rel_err": float(np.max(np.abs(s64_h - sigma[:K]) / sigma[:K])),
                 "sigma_max_rel_diff_mixed": float(np.max(np.abs(s_h - s64_h) / s64_h))}
 
+    # the second run of the workload with an FP8-E4M3 phase-1 basis (operator and basis
+    # in E4M3 with power-of-two scales, tcgen05 kind::f8f6f4 products), refined to the same
+    # tolerance on BF16 correction blocks: one warm-up solve and one timed solve
+    e4m3 = None
+    if not args.no_fp8:
+        p8 = params("e4m3")
+        ws8 = torch.empty(L.rr_workspace_size(rr.api.ctypes.byref(op), rr.api.ctypes.byref(p8), 1),
+                          dtype=torch.uint8, device=dev)
+        rr.rr_svd(op, p8, device=dev, ws=ws8)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s8, _, _, info8 = rr.rr_svd(op, p8, device=dev, ws=ws8)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t8 = e0.elapsed_time(e1) / 1e3
+        s8_h = s8.cpu().numpy()
+        e4m3 = {"value": info8["n_converged"] / t8, "unit": "pairs/s", "seconds": t8,
+                "n_converged": info8["n_converged"], "sweeps": info8["sweeps"],
+                "refine_sweeps": info8["refine_sweeps"], "res_history": info8["res_history"],
+                "sigma_max_rel_err": float(np.max(np.abs(s8_h - sigma[:K]) / sigma[:K]))}
+        del ws8
+
     # end to end through host buffers: H2D of A and V0 from pinned memory,
     # the solve, D2H of sigma, U, V every step
     A_host = torch.empty((N, M), dtype=torch.float64, pin_memory=True)
@@ -384,7 +408,7 @@ def run_ours(args):
             "converged": conv, "sigma_max_rel_err": sig_err,
             "sweeps": infos[-1]["sweeps"], "refine_sweeps": infos[-1]["refine_sweeps"],
             "res_history": infos[-1]["res_history"],
-            "fp64": fp64, "stages": stages, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "fp64": fp64, "e4m3": e4m3, "stages": stages, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clk, "gpu_launches": int(launches),
         }
         print(json.dumps(line))
@@ -619,6 +643,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp8", action="store_true", help="skip the FP8-E4M3 basis run")
     ap.add_argument("--stage", choices=["pencil", "hessenberg", "gemm", "split", "f64emu", "prep", "cheb", "warm", "sparse", "fp8"],
                     help="run one stage of the workload (profiling driver)")
     ap.add_argument("--b", type=int, default=256, help="pencil size for --stage pencil, columns for hessenberg")

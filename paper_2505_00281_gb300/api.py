@@ -21,7 +21,7 @@ __all__ = [
 ]
 
 DTYPES = {torch.float64: RR.F64, torch.float32: RR.F32, torch.bfloat16: RR.BF16}
-_BASIS = {"f64": RR.F64, "f32": RR.F32, "bf16": RR.BF16}
+_BASIS = {"f64": RR.F64, "f32": RR.F32, "bf16": RR.BF16, "e4m3": RR.E4M3}
 
 
 def fortran(t: torch.Tensor) -> torch.Tensor:

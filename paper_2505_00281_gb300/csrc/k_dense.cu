@@ -92,6 +92,7 @@ extern "C" rr_status rr_colscale_cast(int64_t rows, int64_t cols, const double* 
     case RR_F64: k_scale_cast<double><<<g, 256, 0, s>>>(rows, cols, X, ldx, scale, (double*)Y, ldy); break;
     case RR_F32: k_scale_cast<float><<<g, 256, 0, s>>>(rows, cols, X, ldx, scale, (float*)Y, ldy); break;
     case RR_BF16: k_scale_cast<__nv_bfloat16><<<g, 256, 0, s>>>(rows, cols, X, ldx, scale, (__nv_bfloat16*)Y, ldy); break;
+    case RR_E4M3: k_scale_cast<e4m3b_t><<<g, 256, 0, s>>>(rows, cols, X, ldx, scale, (e4m3b_t*)Y, ldy); break;
     default: return RR_ERR_ARG;
   }
   note_launches(1);
@@ -460,6 +461,7 @@ static rr_status gram_dispatch_y(int32_t ytype, dim3 g, cudaStream_t s, int64_t 
     case RR_F64: k_gram_partial<TX, double><<<g, 256, 0, s>>>(n, p, q, X, ldx, (const double*)Y, ldy, rpc, part); break;
     case RR_F32: k_gram_partial<TX, float><<<g, 256, 0, s>>>(n, p, q, X, ldx, (const float*)Y, ldy, rpc, part); break;
     case RR_BF16: k_gram_partial<TX, __nv_bfloat16><<<g, 256, 0, s>>>(n, p, q, X, ldx, (const __nv_bfloat16*)Y, ldy, rpc, part); break;
+    case RR_E4M3: k_gram_partial<TX, e4m3b_t><<<g, 256, 0, s>>>(n, p, q, X, ldx, (const e4m3b_t*)Y, ldy, rpc, part); break;
     default: return RR_ERR_ARG;
   }
   return RR_OK;
@@ -490,7 +492,7 @@ extern "C" rr_status rr_gram(int64_t n, int64_t p, int64_t q, int32_t xtype, con
                              int64_t ldg, int32_t accumulate, void* ws, size_t ws_bytes,
                              void* stream) {
   if (n < 0 || p < 0 || q < 0 || ldx < n || ldy < n || ldg < p || !G) return RR_ERR_ARG;
-  auto valid = [](int32_t t) { return t == RR_F64 || t == RR_F32 || t == RR_BF16; };
+  auto valid = [](int32_t t) { return t == RR_F64 || t == RR_F32 || t == RR_BF16 || t == RR_E4M3; };
   if (!valid(xtype) || !valid(ytype)) return RR_ERR_ARG;
   if (p == 0 || q == 0) return RR_OK;
   cudaStream_t s = as_stream(stream);
@@ -525,6 +527,7 @@ extern "C" rr_status rr_gram(int64_t n, int64_t p, int64_t q, int32_t xtype, con
     case RR_F64: st = gram_dispatch_y<double>(ytype, g, s, n, p, q, (const double*)X, ldx, Y, ldy, rpc, part); break;
     case RR_F32: st = gram_dispatch_y<float>(ytype, g, s, n, p, q, (const float*)X, ldx, Y, ldy, rpc, part); break;
     case RR_BF16: st = gram_dispatch_y<__nv_bfloat16>(ytype, g, s, n, p, q, (const __nv_bfloat16*)X, ldx, Y, ldy, rpc, part); break;
+    case RR_E4M3: st = gram_dispatch_y<e4m3b_t>(ytype, g, s, n, p, q, (const e4m3b_t*)X, ldx, Y, ldy, rpc, part); break;
     default: return RR_ERR_ARG;
   }
   if (st != RR_OK) return st;
@@ -595,6 +598,7 @@ extern "C" rr_status rr_gram_noalloc(int64_t n, int64_t p, int64_t q, int32_t xt
     case RR_F64: st = gram_dispatch_y<double>(ytype, g, s, n, p, q, (const double*)X, ldx, Y, ldy, rpc, scratch); break;
     case RR_F32: st = gram_dispatch_y<float>(ytype, g, s, n, p, q, (const float*)X, ldx, Y, ldy, rpc, scratch); break;
     case RR_BF16: st = gram_dispatch_y<__nv_bfloat16>(ytype, g, s, n, p, q, (const __nv_bfloat16*)X, ldx, Y, ldy, rpc, scratch); break;
+    case RR_E4M3: st = gram_dispatch_y<e4m3b_t>(ytype, g, s, n, p, q, (const e4m3b_t*)X, ldx, Y, ldy, rpc, scratch); break;
     default: return RR_ERR_ARG;
   }
   if (st != RR_OK) return st;

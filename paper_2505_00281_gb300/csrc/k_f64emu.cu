@@ -489,6 +489,9 @@ template <> __device__ __forceinline__ double exact_f64<float>(float v) { return
 template <> __device__ __forceinline__ double exact_f64<__nv_bfloat16>(__nv_bfloat16 v) {
   return f32_to_f64_exact(__bfloat162float(v));
 }
+template <> __device__ __forceinline__ double exact_f64<e4m3b_t>(e4m3b_t v) {
+  return f32_to_f64_exact(e4m3b_value(v.c));
+}
 
 constexpr int kGramSlices = 8;
 constexpr int kGramKChunk = 4096;
@@ -720,6 +723,9 @@ rr_status lift_emu(cudaStream_t s, int64_t n, int64_t b, int32_t t1, const void*
   switch (t1) {
     case RR_F64: launch_lift_slices<double>(s, n, ip1, (const double*)S1, ld1, ip2, t2, S2, ld2, rexp, Acat); break;
     case RR_F32: launch_lift_slices<float>(s, n, ip1, (const float*)S1, ld1, ip2, t2, S2, ld2, rexp, Acat); break;
+    case RR_E4M3:
+      launch_lift_slices<e4m3b_t>(s, n, ip1, (const e4m3b_t*)S1, ld1, ip2, t2, S2, ld2, rexp, Acat);
+      break;
     case RR_BF16:
       launch_lift_slices<__nv_bfloat16>(s, n, ip1, (const __nv_bfloat16*)S1, ld1, ip2, t2, S2, ld2, rexp, Acat);
       break;
@@ -787,6 +793,7 @@ static void emu_slice_any(cudaStream_t s, int32_t t, int64_t n, int64_t c, const
   switch (t) {
     case RR_F64: emu_slice_block<double>(s, n, c, (const double*)X, ldx, e, out); break;
     case RR_F32: emu_slice_block<float>(s, n, c, (const float*)X, ldx, e, out); break;
+    case RR_E4M3: emu_slice_block<e4m3b_t>(s, n, c, (const e4m3b_t*)X, ldx, e, out); break;
     default: emu_slice_block<__nv_bfloat16>(s, n, c, (const __nv_bfloat16*)X, ldx, e, out); break;
   }
 }

@@ -119,6 +119,17 @@ __global__ void k_e4m3_rows(int64_t rows, int64_t cols, const double* __restrict
   }
 }
 
+__global__ void k_fill_f32(int64_t n, float v, float* __restrict__ d) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) d[t] = v;
+}
+
+rr_status fill_f32(cudaStream_t s, int64_t n, float v, float* d) {
+  if (n <= 0) return RR_OK;
+  k_fill_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, v, d);
+  return check_launch("fill_f32");
+}
+
 }  // namespace rr
 
 using namespace rr;

@@ -763,7 +763,7 @@ __global__ void __launch_bounds__(kHessThreads) k_hessenberg_f32(
     for (int i = lane; i < nr; i += 32) {
       const T v = src[i];
       if (slab) dw[i] = v;
-      if ((void*)Q != (void*)W) dq[i] = from_f64<TO>((double)v);
+      if ((void*)Q != (void*)W) dq[i] = from_f32<TO>(v);
     }
   }
 }
@@ -928,6 +928,7 @@ rr_status rr::hessenberg_ex(int32_t arith, int64_t n, int64_t k, void* W, int64_
     switch (qtype) {
       case RR_F32: return hess_launch<float, float>(n, k, w, ldw, (float*)Q, ldq, piv, tol, ws, ws_bytes, s, max_grid);
       case RR_BF16: return hess_launch<float, __nv_bfloat16>(n, k, w, ldw, (__nv_bfloat16*)Q, ldq, piv, tol, ws, ws_bytes, s, max_grid);
+      case RR_E4M3: return hess_launch<float, e4m3b_t>(n, k, w, ldw, (e4m3b_t*)Q, ldq, piv, tol, ws, ws_bytes, s, max_grid);
       case RR_F64: return hess_launch<float, double>(n, k, w, ldw, (double*)Q, ldq, piv, tol, ws, ws_bytes, s, max_grid);
     }
   } else if (arith == RR_F64) {

@@ -91,6 +91,7 @@ rr_status lift(cudaStream_t s, int32_t stype, int64_t n, int64_t b, int64_t p, c
     case RR_F64: k_lift<double><<<g, 256, 0, s>>>(n, b, p, (const double*)S, lds, Y, ldy, X, ldx, accum); break;
     case RR_F32: k_lift<float><<<g, 256, 0, s>>>(n, b, p, (const float*)S, lds, Y, ldy, X, ldx, accum); break;
     case RR_BF16: k_lift<__nv_bfloat16><<<g, 256, 0, s>>>(n, b, p, (const __nv_bfloat16*)S, lds, Y, ldy, X, ldx, accum); break;
+    case RR_E4M3: k_lift<e4m3b_t><<<g, 256, 0, s>>>(n, b, p, (const e4m3b_t*)S, lds, Y, ldy, X, ldx, accum); break;
     default: return RR_ERR_ARG;
   }
   return check_launch("lift");
@@ -197,6 +198,7 @@ static rr_status scale_cast_t(cudaStream_t s, int64_t n, int64_t b, const TI* T,
     case RR_F64: k_scale_cast2<TI, double><<<g, 256, 0, s>>>(n, b, T, ldt, mu, (double*)D, ldd); break;
     case RR_F32: k_scale_cast2<TI, float><<<g, 256, 0, s>>>(n, b, T, ldt, mu, (float*)D, ldd); break;
     case RR_BF16: k_scale_cast2<TI, __nv_bfloat16><<<g, 256, 0, s>>>(n, b, T, ldt, mu, (__nv_bfloat16*)D, ldd); break;
+    case RR_E4M3: k_scale_cast2<TI, e4m3b_t><<<g, 256, 0, s>>>(n, b, T, ldt, mu, (e4m3b_t*)D, ldd); break;
     default: return RR_ERR_ARG;
   }
   note_launches(1);

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <stdint.h>
 #include <math.h>
 
@@ -113,7 +114,27 @@ __device__ __forceinline__ float f64_to_f32_rn(double d) {
   return __uint_as_float(((unsigned)(u >> 63) << 31) | (((unsigned)(E - 896) << 23) + q));
 }
 
+// FP8-E4M3 basis entry.  The stored code is e4m3_rn(256 v): Alg. 8's basis
+// columns and the infinity-normalised start block have |v| <= 1, so 256 |v| <=
+// 448 (the E4M3 maximum) without a per-column scale; a load returns code 2^-8.
+struct e4m3b_t {
+  unsigned char c;
+};
+__device__ __forceinline__ float e4m3b_value(unsigned char c) {
+  const unsigned e = (c >> 3) & 15u, m = c & 7u;
+  // normal: (1 + m/8) 2^(e - 7) 2^-8 -> FP32 exponent field e + 112; subnormal: m 2^-9 2^-8
+  const float v = e ? __uint_as_float(((e + 112u) << 23) | (m << 20)) : (float)m * 7.62939453125e-06f;
+  return (c & 0x80u) ? -v : v;
+}
+__device__ __forceinline__ e4m3b_t e4m3b_from_f32(float v) {
+  return e4m3b_t{(unsigned char)__nv_cvt_float_to_fp8(v * 256.f, __NV_SATFINITE, __NV_E4M3)};
+}
+
 template <typename T> struct Ld;
+template <> struct Ld<e4m3b_t> {
+  static __device__ __forceinline__ double f64(const e4m3b_t* p) { return (double)e4m3b_value(p->c); }
+  static __device__ __forceinline__ float f32(const e4m3b_t* p) { return e4m3b_value(p->c); }
+};
 template <> struct Ld<double> {
   static __device__ __forceinline__ double f64(const double* p) { return *p; }
   static __device__ __forceinline__ float f32(const double* p) { return f64_to_f32_rn(*p); }
@@ -146,7 +167,9 @@ template <> __device__ __forceinline__ float from_f64<float>(double v) { return 
 template <> __device__ __forceinline__ __nv_bfloat16 from_f64<__nv_bfloat16>(double v) {
   return __float2bfloat16_rn((float)v);
 }
+template <> __device__ __forceinline__ e4m3b_t from_f64<e4m3b_t>(double v) { return e4m3b_from_f32(f64_to_f32_rn(v)); }
 template <typename T> __device__ __forceinline__ T from_f32(float v);
+template <> __device__ __forceinline__ e4m3b_t from_f32<e4m3b_t>(float v) { return e4m3b_from_f32(v); }
 template <> __device__ __forceinline__ double from_f32<double>(float v) { return v; }
 template <> __device__ __forceinline__ float from_f32<float>(float v) { return v; }
 template <> __device__ __forceinline__ __nv_bfloat16 from_f32<__nv_bfloat16>(float v) {

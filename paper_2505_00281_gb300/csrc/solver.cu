@@ -49,6 +49,18 @@ struct Op {
   // FP64-accurate lifts on the tensor cores (low-precision bases)
   void* lift_mem;
   size_t lift_bytes;
+  // FP8-E4M3 basis (dense SVD, phase 1): E4M3 copies of the operator with one
+  // power-of-two scale per row (row-major, for A V) and per column (column-
+  // major, for A^T U), the inverse scales, and the basis scale 2^-8 per column.
+  // dt stays BF16 for the refinement phase.
+  bool f8;
+  void* f8_row;
+  void* f8_col;
+  int64_t f8_ldr, f8_ldc;
+  float* f8_rs;
+  float* f8_cs;
+  float* f8_bs;
+  void* f8_scratch;
 };
 
 constexpr int kEmuSlices = 8;
@@ -138,6 +150,14 @@ static rr_status apply_lowp(const Op& op, int64_t b, const void* X, int64_t ldx,
                            nullptr, R, ldr, coef, op.wt, out, ldo, s);
 }
 
+// Phase-1 products of the SVD: E4M3 operands when the basis is E4M3 (X holds
+// codes of 256 x, the basis scale 2^-8 undoes it), else as apply_lowp(_T).
+static rr_status apply_ph1(const Op& op, int64_t b, const void* X, int64_t ldx, float* out, int64_t ldo,
+                           cudaStream_t s) {
+  if (!op.f8) return apply_lowp(op, b, X, ldx, out, ldo, nullptr, 0, nullptr, s);
+  return gemm_e4m3_tc(op.m, b, op.n, op.f8_row, op.f8_ldr, op.f8_rs, X, ldx, op.f8_bs, out, ldo, s);
+}
+
 // out (n x b, wt) = A^T X (+ coef_j R(:,j)),  X (m x b, dt)
 static rr_status apply_lowp_T(const Op& op, int64_t b, const void* X, int64_t ldx, void* out,
                               int64_t ldo, const double* R, int64_t ldr, const double* coef,
@@ -148,6 +168,12 @@ static rr_status apply_lowp_T(const Op& op, int64_t b, const void* X, int64_t ld
     return rr_gemm_f64(1, op.n, b, op.m, op.A, op.lda, (const double*)X, ldx, (double*)out, ldo, 0, s);
   }
   return rr_gemm_lowp(op.dt, op.n, b, op.m, op.lo_col, op.m, X, ldx, (float*)out, ldo, R, ldr, coef, s);
+}
+
+static rr_status apply_ph1_T(const Op& op, int64_t b, const void* X, int64_t ldx, float* out, int64_t ldo,
+                             cudaStream_t s) {
+  if (!op.f8) return apply_lowp_T(op, b, X, ldx, out, ldo, nullptr, 0, nullptr, s);
+  return gemm_e4m3_tc(op.n, b, op.m, op.f8_col, op.f8_ldc, op.f8_cs, X, ldx, op.f8_bs, out, ldo, s);
 }
 
 // Split-BF16 products for the correction recurrence: (A_hi + A_lo) applied to
@@ -263,7 +289,7 @@ static rr_status check_params(const rr_params* p, int64_t rows_min) {
   if (!p) return RR_ERR_ARG;
   if (p->k <= 0 || p->block < p->k || p->block > rows_min || p->block > 1024) return RR_ERR_ARG;
   if (p->degree <= 0 || p->max_sweeps <= 0 || p->max_sweeps > 10000) return RR_ERR_ARG;
-  if (p->basis != RR_F64 && p->basis != RR_F32 && p->basis != RR_BF16) return RR_ERR_ARG;
+  if (p->basis != RR_F64 && p->basis != RR_F32 && p->basis != RR_BF16 && p->basis != RR_E4M3) return RR_ERR_ARG;
   // the projected pencil (2 block with refinement) must fit the small solver
   const bool refine = p->refine != 0 && p->basis != RR_F64;
   if ((refine ? 2 * p->block : p->block) > 335) return RR_ERR_ARG;
@@ -326,7 +352,12 @@ static void carve_svd(Arena& ar, const Op& op, int64_t b, bool refine, SvdBufs& 
   }
 }
 
-static void make_op(const rr_operator* A, int32_t dt, Op& op) {
+static void make_op(const rr_operator* A, int32_t basis, Op& op) {
+  const int32_t dt = basis == RR_E4M3 ? RR_BF16 : basis;
+  op.f8 = basis == RR_E4M3;
+  op.f8_row = op.f8_col = op.f8_scratch = nullptr;
+  op.f8_rs = op.f8_cs = op.f8_bs = nullptr;
+  op.f8_ldr = op.f8_ldc = 0;
   op.kind = A->kind;
   op.m = A->kind == RR_DENSE ? A->m : A->n;
   op.n = A->n;
@@ -357,6 +388,16 @@ static void carve_op(Arena& ar, Op& op, bool symmetric, bool refine, int64_t b) 
     op.lift_mem = ar.take_bytes(op.lift_bytes);
   }
   if (op.kind != RR_DENSE || op.dt == RR_F64) return;
+  if (op.f8) {
+    op.f8_ldr = (op.n + 15) / 16 * 16;
+    op.f8_ldc = (op.m + 15) / 16 * 16;
+    op.f8_row = ar.take_bytes(op.m * op.f8_ldr);
+    op.f8_col = ar.take_bytes(op.n * op.f8_ldc);
+    op.f8_rs = ar.take<float>(op.m);
+    op.f8_cs = ar.take<float>(op.n);
+    op.f8_bs = ar.take<float>(b);
+    op.f8_scratch = ar.take<uint64_t>(op.m > op.n ? op.m : op.n);
+  }
   op.lo_col = ar.take_bytes(op.m * op.n * dsz(op.dt));
   op.lo_row = symmetric ? op.lo_col : ar.take_bytes(op.m * op.n * dsz(op.dt));
   if (refine && !symmetric && op.dt == RR_BF16 && op.m % 8 == 0 && op.n % 8 == 0 && b <= 256) {
@@ -369,6 +410,12 @@ static void carve_op(Arena& ar, Op& op, bool symmetric, bool refine, int64_t b) 
     op.emu_mem = ar.take_bytes(emu_operator_bytes(op.m, op.n, kEmuSlices, true, !symmetric));
     op.emu_blk = ar.take_bytes(emu_block_bytes(op.m > op.n ? op.m : op.n, b, kEmuSlices));
   }
+}
+
+static rr_status prepare_f8(const Op& op, int64_t b, cudaStream_t s) {
+  RR_TRY(rr_quantize_e4m3(op.m, op.n, op.A, op.lda, 1, op.f8_row, op.f8_ldr, op.f8_rs, op.f8_scratch, s));
+  RR_TRY(rr_quantize_e4m3(op.m, op.n, op.A, op.lda, 0, op.f8_col, op.f8_ldc, op.f8_cs, op.f8_scratch, s));
+  return fill_f32(s, b, 1.0f / 256.0f, op.f8_bs);
 }
 
 static rr_status prepare_op(const Op& op_in, Op& op, bool symmetric, cudaStream_t s) {
@@ -416,9 +463,11 @@ static rr_status svd_residual(const Op& op, SvdBufs& w, int64_t kk, double* R1, 
 static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sigma_out,
                          double* U_out, double* V_out, void* ws, size_t ws_bytes, rr_info* info,
                          cudaStream_t s, bool batch_mode, int hess_grid, uint64_t seed) {
-  const int32_t dt = p->basis;
   Op op;
-  make_op(Aop, dt, op);
+  make_op(Aop, p->basis, op);
+  const int32_t dt = op.dt;                 // refinement blocks (BF16 for an E4M3 basis)
+  const int32_t dt1 = p->basis;             // phase-1 basis
+  if (op.f8 && (batch_mode || op.m % 16 || op.n % 16)) return RR_ERR_ARG;
   const int64_t m = op.m, n = op.n, b = p->block, k = p->k;
   const int q = p->degree;
   const bool hess = p->hessenberg != 0;
@@ -440,6 +489,7 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
 
   // one-time operator casts and slicing (counted in the solve time)
   STAGE(RR_STAGE_OTHER, prepare_op(op, op, false, s));
+  if (op.f8) STAGE(RR_STAGE_OTHER, prepare_f8(op, b, s));
 
   // a1: start block
   const double* v0 = p->v0;
@@ -447,7 +497,7 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
     STAGE(RR_STAGE_OTHER, uniform_block(s, n, b, seed, v0buf, n));
     v0 = v0buf;
   }
-  STAGE(RR_STAGE_OTHER, rr_colscale_cast(n, b, v0, n, dt, w.Vlo, n, w.c.scale, s));
+  STAGE(RR_STAGE_OTHER, rr_colscale_cast(n, b, v0, n, dt1, w.Vlo, n, w.c.scale, s));
 
   rr_info inf;
   memset(&inf, 0, sizeof(inf));
@@ -457,22 +507,22 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
 
   // ---------------- phase 1: the paper's method ----------------
   for (int ps = 0; ps < ph1 && sweep < p->max_sweeps; ++ps) {
-    if (ps > 0) STAGE(RR_STAGE_OTHER, rr_colscale_cast(n, b, w.Vt, n, dt, w.Vlo, n, w.c.scale, s));
+    if (ps > 0) STAGE(RR_STAGE_OTHER, rr_colscale_cast(n, b, w.Vt, n, dt1, w.Vlo, n, w.c.scale, s));
     for (int it = 0; it < q; ++it) {
-      STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp(op, b, w.Vlo, n, w.W, m, nullptr, 0, nullptr, s));        // W = A V
-      STAGE(RR_STAGE_HESSENBERG, basis_step(w.c, hess, op.wt, dt, m, b, w.W, m, w.Ulo, m, s));          // U = basis(W)
-      STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp_T(op, b, w.Ulo, m, w.W, n, nullptr, 0, nullptr, s));       // Z = A^T U
-      STAGE(RR_STAGE_HESSENBERG, basis_step(w.c, hess, op.wt, dt, n, b, w.W, n, w.Vlo, n, s));          // V = basis(Z)
+      STAGE(RR_STAGE_LOWP_PRODUCT, apply_ph1(op, b, w.Vlo, n, (float*)w.W, m, s));                      // W = A V
+      STAGE(RR_STAGE_HESSENBERG, basis_step(w.c, hess, op.wt, dt1, m, b, w.W, m, w.Ulo, m, s));         // U = basis(W)
+      STAGE(RR_STAGE_LOWP_PRODUCT, apply_ph1_T(op, b, w.Ulo, m, (float*)w.W, n, s));                    // Z = A^T U
+      STAGE(RR_STAGE_HESSENBERG, basis_step(w.c, hess, op.wt, dt1, n, b, w.W, n, w.Vlo, n, s));         // V = basis(Z)
     }
     // Algorithm 5: B = U^T (A V), Gu = U^T U, Gv = V^T V (FP64 accumulation)
-    STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp(op, b, w.Vlo, n, w.Pw, m, nullptr, 0, nullptr, s));
-    STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, dt, w.Ulo, m, dt, w.Ulo, m, w.Gu, b, s));
-    STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, dt, w.Vlo, n, dt, w.Vlo, n, w.Gv, b, s));
-    STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, dt, w.Ulo, m, op.wt, w.Pw, m, w.Bm, b, s));
+    STAGE(RR_STAGE_LOWP_PRODUCT, apply_ph1(op, b, w.Vlo, n, (float*)w.Pw, m, s));
+    STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, dt1, w.Ulo, m, dt1, w.Ulo, m, w.Gu, b, s));
+    STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, dt1, w.Vlo, n, dt1, w.Vlo, n, w.Gv, b, s));
+    STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, dt1, w.Ulo, m, op.wt, w.Pw, m, w.Bm, b, s));
     STAGE(RR_STAGE_PENCIL, rr_pencil_svd(b, b, w.Bm, w.Gu, w.Gv, w.sig2, w.Ys, w.Zs, w.c.pen_ws, w.c.pen_bytes,
                          nullptr, s));
-    STAGE(RR_STAGE_LIFT, lift2(op, s, m, b, dt, w.Ulo, m, b, 0, nullptr, 0, 0, w.Ys, b, w.Ut, m));
-    STAGE(RR_STAGE_LIFT, lift2(op, s, n, b, dt, w.Vlo, n, b, 0, nullptr, 0, 0, w.Zs, b, w.Vt, n));
+    STAGE(RR_STAGE_LIFT, lift2(op, s, m, b, dt1, w.Ulo, m, b, 0, nullptr, 0, 0, w.Ys, b, w.Ut, m));
+    STAGE(RR_STAGE_LIFT, lift2(op, s, n, b, dt1, w.Vlo, n, b, 0, nullptr, 0, 0, w.Zs, b, w.Vt, n));
     RR_CUDA(cudaMemcpyAsync(w.sig, w.sig2, b * sizeof(double), cudaMemcpyDeviceToDevice, s));
     ++sweep;
     if (!refine && !batch_mode) {
@@ -704,6 +754,7 @@ static rr_status cheb_filter(const Op& op, EigBufs& w, int64_t b, int d, double 
 static rr_status eig_run(const rr_operator* Aop, const rr_params* p, double* theta_out,
                          double* X_out, void* ws, size_t ws_bytes, rr_info* info, cudaStream_t s) {
   const int32_t dt = p->basis;
+  if (dt == RR_E4M3) return RR_ERR_ARG;  // the FP8 basis is built for the SVD
   Op op;
   make_op(Aop, dt, op);
   const int64_t n = op.n, b = p->block, k = p->k;
@@ -944,6 +995,7 @@ extern "C" rr_status rr_eig(const rr_operator* A, const rr_params* p, double* th
                             void* ws, size_t ws_bytes, rr_info* info, void* stream) {
   RR_TRY(check_op(A, false));
   RR_TRY(check_params(p, A->n));
+  if (p->basis == RR_E4M3) return RR_ERR_ARG;
   if (!theta || !X || !p->v0) return RR_ERR_ARG;
   if (!ws || ws_bytes < eig_ws(A, p) || ((uintptr_t)ws & 255)) return RR_ERR_WORKSPACE;
   return eig_run(A, p, theta, X, ws, ws_bytes, info, as_stream(stream));
@@ -977,7 +1029,7 @@ extern "C" rr_status rr_batch_svd(int32_t count, const rr_operator* A, const rr_
                                   uint64_t seed, double* const* sigma, double* const* U,
                                   double* const* V, void* ws, size_t ws_bytes,
                                   rr_status* per_problem, rr_info* info, void* stream) {
-  if (count <= 0 || !A || !p || !sigma || !U || !V || !ws) return RR_ERR_ARG;
+  if (count <= 0 || !A || !p || !sigma || !U || !V || !ws || p->basis == RR_E4M3) return RR_ERR_ARG;
   for (int i = 0; i < count; ++i) {
     RR_TRY(check_op(&A[i], true));
     RR_TRY(check_params(p, A[i].n));

@@ -30,6 +30,7 @@ rr_status cheb_coef_update(cudaStream_t s, int64_t b, const double* theta, const
                            double* kappa_prev, double* rho);
 void small_gemm(cudaStream_t s, int ta, int tb, int M, int N, int K, double alpha, const double* A,
                 int lda, const double* B, int ldb, double beta, double* C, int ldc);
+rr_status fill_f32(cudaStream_t s, int64_t n, float v, float* d);
 // E4M3 x E4M3 tensor-core product with row / column scales (k_gemm_tc.cu)
 rr_status gemm_e4m3_tc(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, const float* rscale,
                        const void* B, int64_t ldb, const float* cscale, float* C, int64_t ldc, cudaStream_t s);

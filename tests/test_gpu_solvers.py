@@ -90,6 +90,24 @@ def test_svd_dense_bf16_refined(rr):
         assert min(np.abs(V[:, j] - ref.X[:, j]).max(), np.abs(V[:, j] + ref.X[:, j]).max()) < 1e-8
 
 
+def test_svd_dense_e4m3_refined(rr):
+    """The same SVD with an FP8-E4M3 phase-1 basis (operator and basis in E4M3,
+    tcgen05 kind::f8f6f4 products), refined to 1e-10 on BF16 correction blocks."""
+    m, n, b, k = 2048, 512, 32, 16
+    sig = wl.config2_sigma(n)
+    A = wl.dense_svd(m, n, sig, 2000)
+    V0 = wl.uniform_block(n, b, 2001)
+    p = rr.api.make_params(k, b, 4, 30, 1e-10, basis="e4m3", v0=dev(V0), refine=True, phase1_sweeps=1)
+    s, U, V, info = rr.rr_svd(rr.api.dense_operator(dev(A)), p)
+    s, U, V = host(s), host(U), host(V)
+    assert info["n_converged"] == k, info
+    assert np.max(np.abs(s - sig[:k]) / sig[:k]) <= 1e-10
+    Amul, Atmul = O.dense_apply(A)
+    assert O.residual_svd(Amul, Atmul, U, V, s).max() <= 1.5e-10
+    assert np.abs(U.T @ U - np.eye(k)).max() < 1e-10
+    assert np.abs(V.T @ V - np.eye(k)).max() < 1e-10
+
+
 def test_svd_dense_fp64_plain_method(rr):
     m, n, b, k = 800, 200, 24, 8
     sig = wl.config2_sigma(n)
