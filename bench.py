@@ -8,7 +8,8 @@ sweeps per projection, BF16 basis with FP32 accumulation, FP64 projection,
 refinement to relative residual <= 1e-10 (synthetic data, seeded).
 
 Reported: the mixed-precision solve's converged triplets/s (``value``), the
-same algorithm all-FP64 on the same GPU (``fp64``), per-stage device times
+same algorithm all-FP64 on the same GPU (``fp64``), the second run with an
+FP8-E4M3 phase-1 basis (``e4m3``), per-stage device times
 from CUDA events inside the timed solves (``stages``) and the roofline of the
 dominant stage, an end-to-end number through host buffers (``e2e``), and the
 FP64 oracle timed on the host cores (``cpu_baseline``).
