@@ -613,6 +613,53 @@ def run_stage(args):
                           "peak_source": src,
                           "max_err_rel": {"bf16": (Cb.double() - ref).abs().max().item() / scale,
                                           "e4m3": (C8.double() - ref).abs().max().item() / scale}}))
+    elif args.stage == "batch":
+        # the batched workload: 512 SVDs, m_i = 4 round(64 16^u_i), n_i = m_i / 4, sigma_j = j^-1.5,
+        # top 16 triplets, block 32, BF16 basis refined to 1e-10; autotuned per size class
+        from paper_2505_00281_gb300 import autotune as AT
+        shapes = wl.config4_shapes(args.count)
+        mats = [wl.dense_svd_torch(m, n, wl.config4_sigma(n), 4000 + i) for i, (m, n) in enumerate(shapes)]
+        ops = [rr.api.dense_operator(t.t()) for t in mats]
+        params = rr.api.make_params(16, 32, 4, args.batch_sweeps, 1e-10, basis="bf16", refine=True,
+                                    phase1_sweeps=1)
+        by_class = {}
+        for op_ in ops:
+            by_class.setdefault(AT.size_class(op_.m, op_.n), []).append(op_)
+        samples = {k: v[:8] for k, v in by_class.items()}
+        cands = [{"branches": b_, "max_splits": c_, "order": 1} for b_ in (8, 32) for c_ in (0, 1, 4)]
+        t0 = time.perf_counter()
+        table = AT.tune(samples, params, candidates=cands, reps=1)
+        t_tune = time.perf_counter() - t0
+        if args.table:
+            AT.save(table, args.table)
+
+        def run(fn):
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            _, st, infos = fn()
+            torch.cuda.synchronize()
+            return time.perf_counter() - t1, st, infos
+        t_def, st_def, inf_def = run(lambda: rr.rr_batch_svd(ops, params, 7))
+        t_tuned, st_tuned, inf_tuned = run(lambda: AT.batch_svd(ops, params, 7, table))
+        conv = lambda infos: int(sum(i["n_converged"] for i in infos))
+
+        def failures(st):
+            out = {}
+            for op_, x in zip(ops, st):
+                if x != 0:
+                    key = AT.size_class(op_.m, op_.n)
+                    out[key] = out.get(key, 0) + 1
+            return out
+        print(json.dumps({"stage": "batch", "count": len(ops), "sweeps": args.batch_sweeps,
+                          "classes": {k: len(v) for k, v in by_class.items()}, "tune_seconds": t_tune,
+                          "default": {"seconds": t_def, "problems_per_s": len(ops) / t_def,
+                                      "pairs_per_s": conv(inf_def) / t_def, "failed_by_class": failures(st_def),
+                                      "max_res_by_class": {k: max(i["max_res"] for op_, i in zip(ops, inf_def)
+                                                                  if AT.size_class(op_.m, op_.n) == k)
+                                                           for k in by_class}},
+                          "tuned": {"seconds": t_tuned, "problems_per_s": len(ops) / t_tuned,
+                                    "pairs_per_s": conv(inf_tuned) / t_tuned, "failed_by_class": failures(st_tuned)},
+                          "table": table}))
     elif args.stage == "prep":
         A = torch.randn(N, M, device="cuda", dtype=torch.float64).t()   # M x N column-major
         X = rr.fortran(torch.randn(N, B, device="cuda", dtype=torch.float64))
@@ -645,12 +692,15 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp8", action="store_true", help="skip the FP8-E4M3 basis run")
-    ap.add_argument("--stage", choices=["pencil", "hessenberg", "gemm", "split", "f64emu", "prep", "cheb", "warm", "sparse", "fp8"],
+    ap.add_argument("--stage", choices=["pencil", "hessenberg", "gemm", "split", "f64emu", "prep", "cheb", "warm", "sparse", "fp8", "batch"],
                     help="run one stage of the workload (profiling driver)")
     ap.add_argument("--b", type=int, default=256, help="pencil size for --stage pencil, columns for hessenberg")
     ap.add_argument("--rows", type=int, default=M, help="rows of the block for --stage hessenberg")
     ap.add_argument("--grid", type=int, default=64, help="grid side for --stage warm")
     ap.add_argument("--sweeps", type=int, default=60, help="sweep limit for --stage sparse")
+    ap.add_argument("--count", type=int, default=512, help="problems for --stage batch")
+    ap.add_argument("--batch-sweeps", type=int, default=30, help="sweeps of every problem for --stage batch")
+    ap.add_argument("--table", default="", help="--stage batch: write the tuned table (JSON) here")
     ap.add_argument("--train", type=int, default=48, help="training solves for --stage warm")
     ap.add_argument("--test", type=int, default=8, help="held-out solves for --stage warm")
     ap.add_argument("--epochs", type=int, default=40, help="training epochs for --stage warm")

@@ -142,6 +142,17 @@ rr_status rr_eig(const rr_operator* A, const rr_params* p, double* theta, double
 rr_status rr_svd(const rr_operator* A, const rr_params* p, double* sigma, double* U,
                  double* V, void* ws, size_t ws_bytes, rr_info* info, void* stream);
 
+/* Launch parameters of the batched SVD (chosen per size class by the
+ * package's autotuner): branches = concurrent graph branches (1..64, default
+ * 16), max_splits = upper bound on the K splits of each tensor-core product
+ * (0 = as many as fill the GPU, the single-problem choice), order = 0 (as
+ * given) or 1 (largest m n first). */
+typedef struct {
+  int32_t branches;
+  int32_t max_splits;
+  int32_t order;
+} rr_batch_tuning;
+
 /* Bytes of device workspace rr_batch_svd needs for `count` operators. */
 size_t rr_batch_workspace_size(int32_t count, const rr_operator* A, const rr_params* p);
 
@@ -149,12 +160,21 @@ size_t rr_batch_workspace_size(int32_t count, const rr_operator* A, const rr_par
  * output pointers).  One parameter set for all (p->v0 is ignored; each problem
  * draws its start block from U(0,1) with a counter-based generator seeded by
  * `seed` + problem index).  per_problem (host, count entries) and info (host,
- * count entries) receive each problem's status and counts.  The whole batch
- * runs as one captured CUDA graph launch on `stream`.  Synchronises. */
+ * count entries) receive each problem's status and counts.  The batch runs
+ * as captured CUDA graphs launched on `stream` (one graph for up to 4096
+ * problem-sweeps, i.e. 4096 / max_sweeps problems), every problem for exactly
+ * max_sweeps sweeps; a problem whose k wanted residuals reached tol keeps
+ * those Ritz triplets through its remaining sweeps.  Synchronises. */
 rr_status rr_batch_svd(int32_t count, const rr_operator* A, const rr_params* p, uint64_t seed,
                        double* const* sigma, double* const* U, double* const* V,
                        void* ws, size_t ws_bytes, rr_status* per_problem, rr_info* info,
                        void* stream);
+/* rr_batch_svd with explicit launch parameters (NULL: the defaults above);
+ * RR_ERR_ARG for parameters out of range. */
+rr_status rr_batch_svd_tuned(int32_t count, const rr_operator* A, const rr_params* p, uint64_t seed,
+                             double* const* sigma, double* const* U, double* const* V, void* ws,
+                             size_t ws_bytes, const rr_batch_tuning* tuning, rr_status* per_problem,
+                             rr_info* info, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Stage entry points (the hot-path steps, callable on their own)

@@ -40,6 +40,10 @@ class RrParams(ctypes.Structure):
                 ("bounds", c_dbl * 2), ("v0", c_vp), ("profile", c_i32)]
 
 
+class RrBatchTuning(ctypes.Structure):
+    _fields_ = [("branches", c_i32), ("max_splits", c_i32), ("order", c_i32)]
+
+
 class RrInfo(ctypes.Structure):
     _fields_ = [("n_converged", c_i32), ("sweeps", c_i32), ("refine_sweeps", c_i32),
                 ("cols_dropped", c_i32), ("max_res", c_dbl), ("res_history", c_dbl * 64),
@@ -58,6 +62,9 @@ _SIGS = {
     "rr_batch_svd": (c_i32, [c_i32, ctypes.POINTER(RrOperator), ctypes.POINTER(RrParams), c_u64,
                              ctypes.POINTER(c_vp), ctypes.POINTER(c_vp), ctypes.POINTER(c_vp), c_vp,
                              c_sz, c_i32p, ctypes.POINTER(RrInfo), c_vp]),
+    "rr_batch_svd_tuned": (c_i32, [c_i32, ctypes.POINTER(RrOperator), ctypes.POINTER(RrParams), c_u64,
+                                   ctypes.POINTER(c_vp), ctypes.POINTER(c_vp), ctypes.POINTER(c_vp), c_vp,
+                                   c_sz, ctypes.POINTER(RrBatchTuning), c_i32p, ctypes.POINTER(RrInfo), c_vp]),
     "rr_colscale_cast": (c_i32, [c_i64, c_i64, c_vp, c_i64, c_i32, c_vp, c_i64, c_vp, c_vp]),
     "rr_cast_operator": (c_i32, [c_i64, c_i64, c_vp, c_i64, c_i32, c_vp, c_vp, c_vp]),
     "rr_split_operator": (c_i32, [c_i64, c_i64, c_vp, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]),

@@ -10,7 +10,7 @@ import ctypes
 
 import torch
 
-from ._lib import RR, RrError, RrInfo, RrOperator, RrParams, check, lib
+from ._lib import RR, RrBatchTuning, RrError, RrInfo, RrOperator, RrParams, check, lib
 
 __all__ = [
     "fortran", "ld_of", "dense_operator", "csr_operator", "make_params", "rr_eig", "rr_svd",
@@ -140,8 +140,9 @@ def rr_svd(op: RrOperator, params: RrParams, device="cuda", stream=None, ws=None
     return sigma, U, V, _info_dict(info, st)
 
 
-def rr_batch_svd(ops, params: RrParams, seed: int, device="cuda", stream=None):
-    """Batched SVDs in one graph launch.  Returns (list of (sigma, U, V), statuses, infos)."""
+def rr_batch_svd(ops, params: RrParams, seed: int, device="cuda", stream=None, tuning=None):
+    """Batched SVDs in one graph launch.  Returns (list of (sigma, U, V), statuses, infos).
+    tuning: None (library defaults) or a dict with branches, max_splits, order."""
     L = lib()
     cnt = len(ops)
     arr = (RrOperator * cnt)(*ops)
@@ -158,8 +159,13 @@ def rr_batch_svd(ops, params: RrParams, seed: int, device="cuda", stream=None):
     ws = _ws(wsb, device)
     per = (ctypes.c_int32 * cnt)()
     infos = (RrInfo * cnt)()
-    st = L.rr_batch_svd(cnt, arr, ctypes.byref(params), seed, S, U, V, _p(ws), ws.numel(), per, infos,
-                        _stream(stream))
+    if tuning is None:
+        st = L.rr_batch_svd(cnt, arr, ctypes.byref(params), seed, S, U, V, _p(ws), ws.numel(), per, infos,
+                            _stream(stream))
+    else:
+        t = RrBatchTuning(int(tuning["branches"]), int(tuning["max_splits"]), int(tuning["order"]))
+        st = L.rr_batch_svd_tuned(cnt, arr, ctypes.byref(params), seed, S, U, V, _p(ws), ws.numel(),
+                                  ctypes.byref(t), per, infos, _stream(stream))
     if st not in (RR.OK, RR.ERR_NO_CONV):
         check("rr_batch_svd", st)
     return outs, [int(x) for x in per], [_info_dict(infos[i], per[i]) for i in range(cnt)]

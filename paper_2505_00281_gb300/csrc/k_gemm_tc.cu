@@ -398,6 +398,11 @@ int& gemm_force_simt() {
   return v;
 }
 
+int& gemm_split_cap() {
+  static thread_local int v = 0;
+  return v;
+}
+
 // Raise the kernel's dynamic shared-memory limit once (outside any stream
 // capture: rr_batch_svd calls this before it starts capturing).
 rr_status tc_prepare_attributes() {
@@ -544,6 +549,7 @@ static rr_status gemm_bf16_tc_impl(int64_t M, int64_t N, int64_t K, const __nv_b
   } else if (tiles * npairs < sms) {
     splits = (int)(sms / (tiles * npairs));
     if (splits > nk) splits = nk;
+    if (gemm_split_cap() > 0 && splits > gemm_split_cap()) splits = gemm_split_cap();
     if (splits < 1) splits = 1;
   }
   int per = (nk + splits - 1) / splits;

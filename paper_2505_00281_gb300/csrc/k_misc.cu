@@ -421,6 +421,44 @@ __global__ void k_fill(int64_t n, double v, double* __restrict__ d) {
   if (j < n) d[j] = v;
 }
 
+// Batched solves run a fixed number of sweeps inside one graph: a problem
+// whose k wanted residuals all reached tol is frozen (the flag only rises),
+// and every later lift is replaced by the frozen Ritz vectors and values.
+__global__ void k_freeze(int64_t k, const double* __restrict__ res, double tol, int* __restrict__ frozen) {
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < k; i += blockDim.x)
+    if (!(res[i] <= tol)) bad = 1;  // NaN fails the test
+  __syncthreads();
+  if (threadIdx.x == 0 && !bad) *frozen = 1;
+}
+
+__global__ void k_keep_frozen(const int* __restrict__ frozen, int64_t m, int64_t n, int64_t b,
+                              const double* __restrict__ U, double* __restrict__ U2, const double* __restrict__ V,
+                              double* __restrict__ V2, const double* __restrict__ sig, double* __restrict__ sig2) {
+  if (!*frozen) return;
+  const int64_t nu = m * b, nv = n * b, tot = nu + nv + b;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    if (e < nu) U2[e] = U[e];
+    else if (e < nu + nv) V2[e - nu] = V[e - nu];
+    else sig2[e - nu - nv] = sig[e - nu - nv];
+  }
+}
+
+rr_status freeze_update(cudaStream_t s, int64_t k, const double* res, double tol, int* frozen) {
+  k_freeze<<<1, 128, 0, s>>>(k, res, tol, frozen);
+  return check_launch("freeze_update");
+}
+
+rr_status keep_frozen(cudaStream_t s, const int* frozen, int64_t m, int64_t n, int64_t b, const double* U, double* U2,
+                      const double* V, double* V2, const double* sig, double* sig2) {
+  const int64_t tot = (m + n) * b + b;
+  k_keep_frozen<<<(unsigned)std::min<int64_t>((tot + 255) / 256, 1024), 256, 0, s>>>(frozen, m, n, b, U, U2, V, V2,
+                                                                                   sig, sig2);
+  return check_launch("keep_frozen");
+}
+
 rr_status fill(cudaStream_t s, int64_t n, double v, double* d) {
   if (n == 0) return RR_OK;
   k_fill<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, v, d);

@@ -283,15 +283,17 @@ __global__ void __launch_bounds__(kSmallThreads) k_colnorm_sort(int r, int c, co
     if (lane == 0) nrm[j] = sqrt(s);
   }
   __syncthreads();
+  // a total order (a NaN norm counts as -1: last, flagged invalid with 0), so
+  // the ranks form a permutation whatever the data
   for (int j = tid; j < c; j += kSmallThreads) {
-    double v = nrm[j];
+    const double v = nrm[j] >= 0.0 ? nrm[j] : -1.0;
     int rank = 0;
     for (int l = 0; l < c; ++l) {
-      double w = nrm[l];
+      const double w = nrm[l] >= 0.0 ? nrm[l] : -1.0;
       if (w > v || (w == v && l < j)) ++rank;
     }
     order[rank] = j;
-    sig[rank] = v;
+    sig[rank] = v >= 0.0 ? v : 0.0;
   }
 }
 
@@ -1719,7 +1721,9 @@ __global__ void __launch_bounds__(1024) k_cluster_rot(int c, const double* __res
   __shared__ int s_ncl;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < c; i += blockDim.x) {
-    lam[i] = K[i + (size_t)i * c] / T[i + (size_t)i * c];
+    // a zero (dropped) column has T_ii = 0: lambda 0 keeps the ranks below a permutation
+    const double t = T[i + (size_t)i * c], li = t > 0.0 ? K[i + (size_t)i * c] / t : 0.0;
+    lam[i] = isfinite(li) ? li : 0.0;
     lamf[i] = (float)lam[i];
   }
   for (int i = tid; i <= c; i += blockDim.x) link[i] = 0;

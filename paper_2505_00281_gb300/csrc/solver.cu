@@ -17,6 +17,7 @@
 // by the filter rate, limited below by the low precision's unit roundoff.
 #include <cmath>
 #include <cstring>
+#include <algorithm>
 #include <vector>
 
 #include "rr_common.cuh"
@@ -306,6 +307,7 @@ struct SvdBufs {
   double *Ut, *Vt, *Ut2, *Vt2, *sig, *P, *Qm, *Rv, *Ru, *ss, *res, *mu, *coef;
   // split mode: lo halves of the correction blocks, FP32 final blocks
   void *Elo2, *Flo2, *E32, *F32;
+  int* frozen;  // batch mode: the problem reached tol (later lifts are undone)
 };
 
 static void carve_svd(Arena& ar, const Op& op, int64_t b, bool refine, SvdBufs& w) {
@@ -324,6 +326,7 @@ static void carve_svd(Arena& ar, const Op& op, int64_t b, bool refine, SvdBufs& 
   w.sig2 = ar.take<double>(b2);
   w.Ut = ar.take<double>(m * b);
   w.Vt = ar.take<double>(n * b);
+  w.frozen = ar.take<int>(1);
   w.sig = ar.take<double>(b);
   w.P = ar.take<double>(m * b);
   w.Qm = ar.take<double>(n * b);
@@ -484,6 +487,7 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
   prof.s = s;
   w.c.hess_grid = hess_grid;
   RR_CUDA(cudaMemsetAsync(w.c.hess_ws, 0, 512, s));
+  RR_CUDA(cudaMemsetAsync(w.frozen, 0, sizeof(int), s));
   const size_t ds = dsz(dt);
   (void)ds;
 
@@ -552,6 +556,7 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
       STAGE(RR_STAGE_OTHER, residual_block(s, m, b, w.P, m, w.Ut, m, w.sig, w.Rv, m, w.ss, 0));
       STAGE(RR_STAGE_OTHER, residual_block(s, n, b, w.Qm, n, w.Vt, n, w.sig, w.Ru, n, w.ss, 1));
       STAGE(RR_STAGE_OTHER, res_finish(s, b, w.ss, w.sig, w.res));
+      if (batch_mode) STAGE(RR_STAGE_OTHER, freeze_update(s, k, w.res, p->tol, w.frozen));
       if (!batch_mode) {
         RR_CUDA(cudaMemcpyAsync(hres.data(), w.res, k * sizeof(double), cudaMemcpyDeviceToHost, s));
         RR_CUDA(cudaStreamSynchronize(s));
@@ -622,6 +627,8 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
       // lift the leading b triplets
       STAGE(RR_STAGE_LIFT, lift2(op, s, m, b, RR_F64, w.Ut, m, b, et, Eg, m, b, w.Ys, b2, w.Ut2, m));
       STAGE(RR_STAGE_LIFT, lift2(op, s, n, b, RR_F64, w.Vt, n, b, et, Fg, n, b, w.Zs, b2, w.Vt2, n));
+      if (batch_mode)
+        STAGE(RR_STAGE_OTHER, keep_frozen(s, w.frozen, m, n, b, w.Ut, w.Ut2, w.Vt, w.Vt2, w.sig, w.sig2));
       std::swap(w.Ut, w.Ut2);
       std::swap(w.Vt, w.Vt2);
       RR_CUDA(cudaMemcpyAsync(w.sig, w.sig2, b * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -1029,7 +1036,18 @@ extern "C" rr_status rr_batch_svd(int32_t count, const rr_operator* A, const rr_
                                   uint64_t seed, double* const* sigma, double* const* U,
                                   double* const* V, void* ws, size_t ws_bytes,
                                   rr_status* per_problem, rr_info* info, void* stream) {
+  return rr_batch_svd_tuned(count, A, p, seed, sigma, U, V, ws, ws_bytes, nullptr, per_problem, info, stream);
+}
+
+extern "C" rr_status rr_batch_svd_tuned(int32_t count, const rr_operator* A, const rr_params* p, uint64_t seed,
+                                        double* const* sigma, double* const* U, double* const* V, void* ws,
+                                        size_t ws_bytes, const rr_batch_tuning* tuning, rr_status* per_problem,
+                                        rr_info* info, void* stream) {
   if (count <= 0 || !A || !p || !sigma || !U || !V || !ws || p->basis == RR_E4M3) return RR_ERR_ARG;
+  const rr_batch_tuning tune = tuning ? *tuning : rr_batch_tuning{16, 0, 0};
+  if (tune.branches < 1 || tune.branches > kBatchMaxBranches || tune.max_splits < 0 ||
+      (tune.order != 0 && tune.order != 1))
+    return RR_ERR_ARG;
   for (int i = 0; i < count; ++i) {
     RR_TRY(check_op(&A[i], true));
     RR_TRY(check_params(p, A[i].n));
@@ -1037,15 +1055,22 @@ extern "C" rr_status rr_batch_svd(int32_t count, const rr_operator* A, const rr_
   if (ws_bytes < rr_batch_workspace_size(count, A, p)) return RR_ERR_WORKSPACE;
   RR_TRY(tc_prepare_attributes());
   cudaStream_t s = as_stream(stream);
-  const int NS = 16;
+  const int NS = tune.branches;
+  // launch order: as given, or largest problems first (each branch then
+  // finishes its big problems before its small ones)
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  if (tune.order == 1)
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return A[a].m * A[a].n > A[b].m * A[b].n; });
   // Capture on a private stream (the legacy default stream cannot be
   // captured); the instantiated graph is launched on the caller's stream.
   cudaStream_t cap = nullptr;
-  cudaStream_t br[NS] = {};
-  cudaEvent_t fork = nullptr, join[NS] = {};
+  cudaStream_t br[kBatchMaxBranches] = {};
+  cudaEvent_t fork = nullptr, join[kBatchMaxBranches] = {};
   rr_params pp = *p;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  std::vector<cudaGraphExec_t> execs;
   rr_status st = RR_OK;
   std::vector<size_t> offs(count);
   size_t off = 0;
@@ -1069,37 +1094,46 @@ extern "C" rr_status rr_batch_svd(int32_t count, const rr_operator* A, const rr_
   // the graph must see the caller's prior work on `s`: order cap after s
   cudaEvent_t pre = nullptr;
   cu(cudaEventCreateWithFlags(&pre, cudaEventDisableTiming), "rr_batch_svd event");
-  if (st == RR_OK) {
+  // one graph per chunk of problems, at most kBatchSweepBudget problem-sweeps
+  // each (graphs of a few hundred thousand nodes), launched in order on `s`
+  const int per_graph = std::max(1, kBatchSweepBudget / std::max(1, (int)p->max_sweeps));
+  for (int r0 = 0; r0 < count && st == RR_OK; r0 += per_graph) {
+    const int r1 = std::min(count, r0 + per_graph);
     cu(cudaEventRecord(pre, s), "rr_batch_svd record");
     cu(cudaStreamWaitEvent(cap, pre, 0), "rr_batch_svd wait");
-  }
-  bool capturing = false;
-  if (st == RR_OK) {
-    cu(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "rr_batch_svd capture");
-    capturing = st == RR_OK;
-  }
-  if (capturing) {
-    cu(cudaEventRecord(fork, cap), "rr_batch_svd fork");
-    for (int i = 0; i < NS; ++i) cu(cudaStreamWaitEvent(br[i], fork, 0), "rr_batch_svd fork wait");
-    for (int i = 0; i < count && st == RR_OK; ++i) {
-      size_t need = align_up(svd_ws(&A[i], p, true), 4096);
-      st = svd_run(&A[i], &pp, sigma[i], U[i], V[i], (char*)ws + offs[i], need, &infos[i], br[i % NS],
-                   true, 1, seed + (uint64_t)i);
+    bool capturing = false;
+    if (st == RR_OK) {
+      cu(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "rr_batch_svd capture");
+      capturing = st == RR_OK;
     }
-    for (int i = 0; i < NS; ++i) {
-      cudaEventRecord(join[i], br[i]);
-      cudaStreamWaitEvent(cap, join[i], 0);
+    if (capturing) {
+      cu(cudaEventRecord(fork, cap), "rr_batch_svd fork");
+      for (int i = 0; i < NS; ++i) cu(cudaStreamWaitEvent(br[i], fork, 0), "rr_batch_svd fork wait");
+      GemmSplitCap cap_scope(tune.max_splits);  // K splits of the products captured below
+      for (int r = r0; r < r1 && st == RR_OK; ++r) {
+        const int i = order[r];
+        size_t need = align_up(svd_ws(&A[i], p, true), 4096);
+        st = svd_run(&A[i], &pp, sigma[i], U[i], V[i], (char*)ws + offs[i], need, &infos[i], br[(r - r0) % NS],
+                     true, 1, seed + (uint64_t)i);
+      }
+      for (int i = 0; i < NS; ++i) {
+        cudaEventRecord(join[i], br[i]);
+        cudaStreamWaitEvent(cap, join[i], 0);
+      }
+      cudaError_t ce = cudaStreamEndCapture(cap, &graph);
+      cu(ce, "rr_batch_svd end capture");
     }
-    cudaError_t ce = cudaStreamEndCapture(cap, &graph);
-    cu(ce, "rr_batch_svd end capture");
+    if (st == RR_OK) cu(cudaGraphInstantiate(&exec, graph, 0), "rr_batch_svd instantiate");
+    if (st == RR_OK) cu(cudaGraphLaunch(exec, s), "rr_batch_svd launch");
+    if (exec) execs.push_back(exec);  // destroyed after the final synchronisation
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
   }
-  if (st == RR_OK) cu(cudaGraphInstantiate(&exec, graph, 0), "rr_batch_svd instantiate");
-  if (st == RR_OK) cu(cudaGraphLaunch(exec, s), "rr_batch_svd launch");
-  if (st == RR_OK) cu(cudaStreamSynchronize(s), "rr_batch_svd sync");
+  cu(cudaStreamSynchronize(s), "rr_batch_svd sync");
+  for (cudaGraphExec_t e : execs) cudaGraphExecDestroy(e);
   if (pre) cudaEventDestroy(pre);
   if (cap) cudaStreamDestroy(cap);
-  if (exec) cudaGraphExecDestroy(exec);
-  if (graph) cudaGraphDestroy(graph);
   for (int i = 0; i < NS; ++i) {
     if (br[i]) cudaStreamDestroy(br[i]);
     if (join[i]) cudaEventDestroy(join[i]);

@@ -24,6 +24,9 @@ rr_status normalize_sign(cudaStream_t s, int64_t n, int64_t k, double* X, int64_
                          double* U, int64_t ldu);
 rr_status vec_mul(cudaStream_t s, int64_t n, const double* a, const double* b, double* d);
 rr_status fill(cudaStream_t s, int64_t n, double v, double* d);
+rr_status freeze_update(cudaStream_t s, int64_t k, const double* res, double tol, int* frozen);
+rr_status keep_frozen(cudaStream_t s, const int* frozen, int64_t m, int64_t n, int64_t b, const double* U, double* U2,
+                      const double* V, double* V2, const double* sig, double* sig2);
 rr_status uniform_block(cudaStream_t s, int64_t n, int64_t b, uint64_t seed, double* V, int64_t ldv);
 rr_status cheb_coef_update(cudaStream_t s, int64_t b, const double* theta, const double* mu,
                            double alpha_next, double cshift, double beta_next, double* kappa,
@@ -31,6 +34,17 @@ rr_status cheb_coef_update(cudaStream_t s, int64_t b, const double* theta, const
 void small_gemm(cudaStream_t s, int ta, int tb, int M, int N, int K, double alpha, const double* A,
                 int lda, const double* B, int ldb, double beta, double* C, int ldc);
 rr_status fill_f32(cudaStream_t s, int64_t n, float v, float* d);
+// Upper bound on the K splits of the plain / split tensor-core products
+// (0: none) while an instance is alive on this thread; the batched solver
+// sets it around its graph capture.
+int& gemm_split_cap();
+struct GemmSplitCap {
+  int prev;
+  explicit GemmSplitCap(int cap) : prev(gemm_split_cap()) { gemm_split_cap() = cap; }
+  ~GemmSplitCap() { gemm_split_cap() = prev; }
+};
+constexpr int kBatchMaxBranches = 64;
+constexpr int kBatchSweepBudget = 4096;  // problem-sweeps captured in one graph of the batched SVD
 // E4M3 x E4M3 tensor-core product with row / column scales (k_gemm_tc.cu)
 rr_status gemm_e4m3_tc(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, const float* rscale,
                        const void* B, int64_t ldb, const float* cscale, float* C, int64_t ldc, cudaStream_t s);

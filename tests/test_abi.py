@@ -46,3 +46,20 @@ def test_workspace_queries_run_without_gpu():
     assert L.rr_workspace_size(ctypes.byref(op), ctypes.byref(p), 1) > 0
     bad = _lib.RrOperator(0, 0, 100, 200, 100, 0, 1, None, None)   # m < n for the SVD
     assert L.rr_workspace_size(ctypes.byref(bad), ctypes.byref(p), 1) == 0
+
+
+def test_autotune_table_host_logic(tmp_path):
+    """Size classes and the persisted table (host only)."""
+    from paper_2505_00281_gb300 import autotune as AT
+    assert AT.size_class(512, 128) == "9,7,bf16" and AT.size_class(1023, 255) == "9,7,bf16"
+    assert AT.size_class(1024, 256) == "10,8,bf16"
+    t = {"9,7,bf16": {"branches": 8, "max_splits": 1, "order": 1, "ms": 1.0, "default_ms": 2.0}}
+    AT.save(t, tmp_path / "t.json")
+    assert AT.load(tmp_path / "t.json") == t
+    assert all(1 <= c["branches"] <= 64 and c["max_splits"] >= 0 and c["order"] in (0, 1) for c in AT.CANDIDATES)
+
+
+def test_shipped_tuning_table():
+    from paper_2505_00281_gb300 import autotune as AT
+    t = AT.load()
+    assert t and all(set(v) >= {"branches", "max_splits", "order"} for v in t.values())

@@ -171,3 +171,57 @@ def test_batch_svd_small(rr):
         assert np.max(np.abs(s - sigs[i][:8]) / sigs[i][:8]) <= 1e-10, (i, s, sigs[i][:8], infos[i])
         Amul, Atmul = O.dense_apply(A)
         assert O.residual_svd(Amul, Atmul, host(U), host(V), s).max() <= 1.5e-10
+
+
+def test_batch_autotune_and_tuned_launches(rr):
+    """Every launch-parameter choice of the batched SVD gives the converged
+    result (sigma to the closed form), and the autotuner's table drives a
+    per-class run of a mixed batch."""
+    from paper_2505_00281_gb300 import autotune as AT
+    shapes = [(256, 64), (300, 75), (512, 128), (520, 130), (1024, 256), (1040, 260)]
+    ops, sigs, keep = [], [], []
+    for i, (m, n) in enumerate(shapes):
+        sg = wl.config4_sigma(n)
+        A = dev(wl.dense_svd(m, n, sg, 4100 + i))
+        keep.append(A)
+        ops.append(rr.api.dense_operator(A))
+        sigs.append(sg)
+    p = rr.api.make_params(8, 16, 4, 12, 1e-10, basis="bf16", refine=True, phase1_sweeps=1)
+    for tuning in ({"branches": 1, "max_splits": 1, "order": 0}, {"branches": 4, "max_splits": 0, "order": 1},
+                   {"branches": 64, "max_splits": 2, "order": 1}):
+        outs, st, _ = rr.rr_batch_svd(ops, p, 5, tuning=tuning)
+        assert all(x == 0 for x in st), (tuning, st)
+        for (s, U, V), sg in zip(outs, sigs):
+            assert np.max(np.abs(host(s) - sg[:8]) / sg[:8]) <= 1e-10
+    samples = {}
+    for op in ops:
+        samples.setdefault(AT.size_class(op.m, op.n), []).append(op)
+    table = AT.tune(samples, p, candidates=[{"branches": 2, "max_splits": 1, "order": 0},
+                                            {"branches": 8, "max_splits": 0, "order": 1}], reps=1)
+    assert set(table) == set(samples)
+    outs, st, infos = AT.batch_svd(ops, p, 5, table)
+    assert all(x == 0 for x in st)
+    for (s, U, V), sg in zip(outs, sigs):
+        assert np.max(np.abs(host(s) - sg[:8]) / sg[:8]) <= 1e-10
+
+
+def test_batch_problems_keep_converged_triplets(rr):
+    """Batched problems iterate for a fixed sweep count: easy problems converge
+    within a few sweeps and then run 30 more; their converged triplets must be
+    what comes out (no degenerate post-convergence sweep reaches the result)."""
+    shapes = [(256, 64), (264, 66), (320, 80), (256, 64)]
+    ops, sigs, keep = [], [], []
+    for i, (m, n) in enumerate(shapes):
+        sg = np.exp(-np.arange(1, n + 1) / 4.0)          # wide gaps: converges in a few sweeps
+        A = dev(wl.dense_svd(m, n, sg, 4200 + i))
+        keep.append(A)
+        ops.append(rr.api.dense_operator(A))
+        sigs.append(sg)
+    p = rr.api.make_params(4, 8, 2, 36, 1e-10, basis="bf16", refine=True, phase1_sweeps=1)
+    outs, st, infos = rr.rr_batch_svd(ops, p, 9)
+    assert all(x == 0 for x in st), (st, infos)
+    for (s, U, V), sg, A in zip(outs, sigs, keep):
+        assert np.max(np.abs(host(s) - sg[:4]) / sg[:4]) <= 1e-10
+        Ah = host(A)
+        Amul, Atmul = O.dense_apply(Ah)
+        assert O.residual_svd(Amul, Atmul, host(U), host(V), host(s)).max() <= 1.5e-10
