@@ -203,7 +203,7 @@ def stage_roofline(info, peaks, src, refine_sweeps, phase1_sweeps):
         ach = prod_bytes / t / 1e9
         # DRAM bytes per launch from ncu (one A V launch of each kind, read +
         # write; the A^T W launches are taken to move the same bytes)
-        traffic = n_plain * 138.27e6 + n_split * 273.98e6
+        traffic = n_plain * 138.73e6 + n_split * 273.70e6
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                 "traffic": traffic, "traffic_scope": "DRAM bytes per solve, ncu per-launch counts x launches",
                 "kernel": "k_gemm_bf16_tc", "stage": "lowp_product",
