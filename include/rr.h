@@ -12,12 +12,18 @@
  *   - Algorithm 8 (Hessenberg process for a block, the inner-product-free
  *     basis step; equal to row-pivoted LU, Sec. 4.2.2),
  *   - the mixed-precision map of Sec. 4.2 (Fig. 4): low-precision basis and
- *     products, higher-precision projection, FP64 small solve.
+ *     products (BF16, or FP8-E4M3 with power-of-two scales), higher-precision
+ *     projection, FP64 small solve.
+ * Beyond the paper: a refinement phase to FP64-level residuals, batched
+ * solves with tuned launch parameters, and the kernels of a learned start
+ * block (its network's convolutions, loss gradient and optimiser).
  *
  * Conventions for every entry point:
  *   - All matrices are column-major ("Fortran", Sec. 5.1) with an explicit
- *     leading dimension; all matrix pointers are DEVICE pointers unless the
- *     comment says "host".
+ *     leading dimension unless the entry's comment gives another layout (the
+ *     row-major blocks of rr_chebyshev_step_rows and rr_quantize_e4m3, the
+ *     NCHW images of the convolution kernels); all matrix pointers are DEVICE
+ *     pointers unless the comment says "host".
  *   - The caller owns every buffer.  The library allocates no device memory:
  *     scratch space is the caller's workspace (see rr_workspace_size).
  *   - Calls are asynchronous on `stream` (a cudaStream_t passed as void*;
