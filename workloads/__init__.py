@@ -193,3 +193,13 @@ def conv_params(layers, seed: int):
         out.append((r.uniform(-lim, lim, size=(cout, cin, 3, 3)).astype(np.float32),
                     np.zeros(cout, dtype=np.float32)))
     return out
+
+
+def gaussian_kernel(n: int, f: float, l: float, s: float, seed: int, d: int = 2) -> np.ndarray:
+    """Gaussian kernel matrix A_ij = f (exp(-|x_i - x_j|^2 / (2 l^2)) + s delta_ij) over n points
+    drawn uniformly from the square (d = 2) of side sqrt(n), the paper's kernel-matrix family
+    (1000 points, f = 1 or 0.2, l = 1 ... 100, s = 0.01 or 0).  FP64, column-major."""
+    x = _rng(seed).uniform(0.0, math.sqrt(n), size=(n, d))
+    d2 = np.sum((x[:, None, :] - x[None, :, :]) ** 2, axis=-1)
+    return np.asfortranarray(f * (np.exp(-d2 / (2.0 * l * l)) + s * np.eye(n)))
+
