@@ -297,3 +297,36 @@ def test_e4m3_scale_exponent():
     assert O.e4m3_scale_exp(0.0) == 0 and O.e4m3_scale_exp(1e-300) == 126 and O.e4m3_scale_exp(1e300) == -126
     Xv, inv = O.quantize_e4m3(np.array([[1.0, 0.0], [-3.0, 0.0]]), by_rows=False)
     assert np.array_equal(inv, [2.0 ** -7, 1.0]) and np.array_equal(Xv[:, 0], [128.0, -384.0])
+
+
+def test_csr_gershgorin_closed_form_and_containment():
+    """-Lap_5pt + c on an N x N grid: interior rows give [c, c + 8] exactly; the
+    bounds contain the whole spectrum of a random-potential operator."""
+    N, c = 12, 0.5
+    rp, ci, va = wl.grid_potential_csr(N, np.full(N * N, c))
+    lo, up = O.csr_gershgorin(rp, ci, va)
+    assert lo == c and up == c + 8.0
+    rp, ci, va, v = wl.grid_schrodinger_csr(10, 10.0, 5)
+    lo, up = O.csr_gershgorin(rp, ci, va)
+    lam = np.linalg.eigvalsh(O.csr_apply(rp, ci, va)(np.eye(100)))
+    assert lo <= lam.min() and lam.max() <= up
+
+
+def test_residual_svd_exact_and_perturbed_triplets():
+    """Zero (to rounding) for exact singular triplets, invariant to positive scales
+    of u and v and to flipping both signs, and equal to the closed forms for a
+    one-sided sign flip and for a known perturbation of sigma."""
+    m, n = 40, 12
+    sig = np.linspace(3.0, 1.0, n)
+    A = wl.dense_svd(m, n, sig, 7)
+    Uf, s, Vt = np.linalg.svd(A, full_matrices=False)
+    Amul, Atmul = O.dense_apply(A)
+    r = O.residual_svd(Amul, Atmul, 5.0 * Uf[:, :4], 2.0 * Vt[:4].T, s[:4])
+    assert r.max() < 1e-14
+    assert O.residual_svd(Amul, Atmul, -Uf[:, :4], -Vt[:4].T, s[:4]).max() < 1e-14
+    # one sign flipped: A(-v) - s u = -2 s u -> sqrt(4 + 4) s / s
+    assert np.allclose(O.residual_svd(Amul, Atmul, Uf[:, :4], -Vt[:4].T, s[:4]), 2.0 * np.sqrt(2.0))
+    # sigma off by d: A v - (s + d) u = -d u and A^T u - (s + d) v = -d v -> sqrt(2) |d| / (s + d)
+    d = 1e-3
+    r = O.residual_svd(Amul, Atmul, Uf[:, :4], Vt[:4].T, s[:4] + d)
+    assert np.allclose(r, np.sqrt(2.0) * d / (s[:4] + d), rtol=1e-9)
