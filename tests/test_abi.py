@@ -63,3 +63,26 @@ def test_shipped_tuning_table():
     from paper_2505_00281_gb300 import autotune as AT
     t = AT.load()
     assert t and all(set(v) >= {"branches", "max_splits", "order"} for v in t.values())
+
+
+def test_autotune_batch_grouping_and_order(monkeypatch):
+    """batch_svd splits a batch by size class, runs each class with its tuned
+    parameters (defaults for classes the table lacks) and returns the results in
+    the caller's order (host logic, the batch call faked)."""
+    from types import SimpleNamespace
+
+    from paper_2505_00281_gb300 import autotune as AT
+    calls = []
+
+    def fake(ops, params, seed, tuning=None, **kw):
+        calls.append(([o.m for o in ops], dict(tuning), seed))
+        return [("out", o.m) for o in ops], [0] * len(ops), [{"m": o.m} for o in ops]
+    monkeypatch.setattr(AT.api, "rr_batch_svd", fake)
+    ops = [SimpleNamespace(m=m, n=m // 4) for m in (300, 1100, 310, 2100, 1200)]
+    table = {AT.size_class(300, 75): {"branches": 8, "max_splits": 1, "order": 1, "ms": 1.0, "default_ms": 2.0}}
+    outs, st, infos = AT.batch_svd(ops, None, 100, table)
+    assert [o[1] for o in outs] == [300, 1100, 310, 2100, 1200] and [i["m"] for i in infos] == [300, 1100, 310, 2100, 1200]
+    by_sizes = {tuple(c[0]): c[1] for c in calls}
+    assert by_sizes[(300, 310)] == {"branches": 8, "max_splits": 1, "order": 1}
+    assert by_sizes[(1100, 1200)] == AT.DEFAULT and by_sizes[(2100,)] == AT.DEFAULT
+    assert all(x == 0 for x in st)
