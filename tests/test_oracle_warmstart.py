@@ -76,3 +76,22 @@ def test_gaussian_potential_recipe():
     v = wl.gaussian_potential(64, 5)
     assert v.shape == (64, 64) and v.min() >= 0.0 and v.max() <= 8 * 20.0
     assert not np.array_equal(v, wl.gaussian_potential(64, 6))
+
+
+def test_free_modes_are_laplacian_eigenvectors():
+    """The network's input modes (package host logic): at scale 1/N orthonormal,
+    and eigenvectors of the 5-point Dirichlet Laplacian with eigenvalues
+    4 - 2 cos(p pi/(N+1)) - 2 cos(q pi/(N+1)), the k lowest in order."""
+    from paper_2505_00281_gb300.warmstart import free_modes, layer_shapes
+    from oracle import ofrr as O
+    N, k = 20, 12
+    V = free_modes(N, k).reshape(k, N * N).T.astype(np.float64) / N
+    assert np.abs(V.T @ V - np.eye(k)).max() < 1e-6
+    rp, ci, va = wl.grid_potential_csr(N, np.zeros(N * N))
+    AV = O.csr_apply(rp, ci, va)(V)
+    lam = np.sum(V * AV, axis=0)
+    assert np.abs(AV - V * lam).max() < 1e-5
+    t = np.arange(1, 2 * k) * np.pi / (N + 1)
+    allv = np.sort((4 - 2 * np.cos(t)[:, None] - 2 * np.cos(t)[None, :]).ravel())
+    assert np.allclose(lam, allv[:k], atol=1e-5)
+    assert layer_shapes(16, 24, 3) == [(17, 24), (24, 24), (24, 16)]
