@@ -330,3 +330,31 @@ def test_residual_svd_exact_and_perturbed_triplets():
     d = 1e-3
     r = O.residual_svd(Amul, Atmul, Uf[:, :4], Vt[:4].T, s[:4] + d)
     assert np.allclose(r, np.sqrt(2.0) * d / (s[:4] + d), rtol=1e-9)
+
+
+def test_colscale_inf_pins():
+    """Column inf-norm scaling (Sec. 2): every nonzero output column has
+    max |entry| = 1 by the abs-max definition, signs are kept (a column whose
+    largest-magnitude entry is negative keeps it at -1), a zero column stays
+    exactly zero, and nothing is NaN.  Values chosen so the divisions are exact."""
+    X = np.array([[-4.0, 0.0, 1.0, 0.5],
+                  [2.0, 0.0, -3.0, 0.25],
+                  [1.0, 0.0, 2.0, -0.125]])
+    Y = O.colscale_inf(X)
+    expect = np.array([[-1.0, 0.0, 1.0 / 3.0, 1.0],
+                       [0.5, 0.0, -1.0, 0.5],
+                       [0.25, 0.0, 2.0 / 3.0, -0.25]])
+    assert np.array_equal(Y[:, [0, 1, 3]], expect[:, [0, 1, 3]])
+    assert np.allclose(Y[:, 2], expect[:, 2], rtol=0, atol=1e-16)
+    assert not np.isnan(Y).any()
+    assert np.array_equal(np.max(np.abs(Y), axis=0), [1.0, 0.0, 1.0, 1.0])
+    # invariant under positive column scaling; a negative scale flips signs only
+    rng = np.random.default_rng(5)
+    Z = rng.standard_normal((50, 6))
+    D = np.array([2.0 ** 10, 0.5, 3.0, 7.0, 2.0 ** -20, -4.0])
+    W = O.colscale_inf(Z * D)
+    ref = O.colscale_inf(Z) * np.sign(D)
+    assert np.allclose(W, ref, rtol=1e-15, atol=1e-16)
+    # empty row count: shape kept, no NaN
+    E = O.colscale_inf(np.zeros((0, 3)))
+    assert E.shape == (0, 3)

@@ -72,6 +72,44 @@ def test_adam_first_step_is_a_signed_lr_step():
     assert np.allclose(p1, p - 0.01 * np.sign(g), atol=1e-7)   # bias-corrected m/sqrt(v) = sign(g)
 
 
+def test_adam_steps_two_and_three_hand_expanded():
+    """Adam past the first step, against moments expanded by hand.
+    Gradients g1 = 1, g2 = 3, g3 = -2 on one parameter, b1 = 0.9, b2 = 0.999:
+      m1 = 0.1,  v1 = 0.001
+      m2 = 0.9 m1 + 0.1 * 3 = 0.39,      v2 = 0.999 v1 + 0.001 * 9 = 0.009999
+      m3 = 0.9 m2 + 0.1 * (-2) = 0.151,  v3 = 0.999 v2 + 0.001 * 4 = 0.013989001
+    bias corrections 1 - 0.9^2 = 0.19, 1 - 0.999^2 = 0.001999,
+                     1 - 0.9^3 = 0.271, 1 - 0.999^3 = 0.002997001."""
+    lr, eps = 0.01, 1e-8
+    p, m, v = np.array([1.0]), np.zeros(1), np.zeros(1)
+    p, m, v = W.adam_step(p, np.array([1.0]), m, v, 1, lr=lr)
+    assert np.allclose([m[0], v[0]], [0.1, 0.001], rtol=1e-14)
+    p1 = p.copy()
+    p, m, v = W.adam_step(p, np.array([3.0]), m, v, 2, lr=lr)
+    assert np.allclose([m[0], v[0]], [0.39, 0.009999], rtol=1e-14)
+    step2 = lr * (0.39 / 0.19) / (np.sqrt(0.009999 / 0.001999) + eps)
+    assert np.allclose(p, p1 - step2, rtol=1e-14)
+    p2 = p.copy()
+    p, m, v = W.adam_step(p, np.array([-2.0]), m, v, 3, lr=lr)
+    assert np.allclose([m[0], v[0]], [0.151, 0.013989001], rtol=1e-14)
+    step3 = lr * (0.151 / 0.271) / (np.sqrt(0.013989001 / 0.002997001) + eps)
+    assert np.allclose(p, p2 - step3, rtol=1e-14)
+
+
+def test_adam_constant_gradient_steps_are_signed_lr():
+    """With the same gradient g at every step, m_t = g (1 - b1^t) and
+    v_t = g^2 (1 - b2^t), so the bias-corrected step is lr sign(g) at every t
+    (a wrong power in either correction breaks this at t >= 2)."""
+    g = np.array([0.5, -0.1, 4.0])
+    p, m, v = np.zeros(3), np.zeros(3), np.zeros(3)
+    for t in range(1, 6):
+        pn, m, v = W.adam_step(p, g, m, v, t, lr=0.01)
+        assert np.allclose(m, g * (1 - 0.9 ** t), rtol=1e-13)
+        assert np.allclose(v, g * g * (1 - 0.999 ** t), rtol=1e-13)
+        assert np.allclose(pn - p, -0.01 * np.sign(g), rtol=1e-6)
+        p = pn
+
+
 def test_gaussian_potential_recipe():
     v = wl.gaussian_potential(64, 5)
     assert v.shape == (64, 64) and v.min() >= 0.0 and v.max() <= 8 * 20.0
