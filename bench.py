@@ -45,6 +45,13 @@ WORKLOAD = ("dense SVD A=U diag(exp(-i/60)) V^T 16384x4096 FP64 (Haar U, V), top
             "block 128, 4 power sweeps per projection, BF16 basis + FP32 accumulation, FP64 "
             "projection, refined to rel. residual <= 1e-10")
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def bench_config(world: int = 1) -> dict:
+    """The workload's config dict, identical in both arms of the bench."""
+    return {"workload": WORKLOAD, "m": M, "n": N, "block": B, "k": K, "power_sweeps": Q, "tol": TOL,
+            "l2": "inputs larger than L2 (A: 512 MiB FP64 + 256 MiB BF16 copies)",
+            "parallelism": f"replicas x{world}"}
 # nominal FP64 rate of a GB300 (no measured FP64 figure exists): 1.25 TFLOP/s
 
 
@@ -144,14 +151,15 @@ def run_reference(args):
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": t_sweep * S * 1e3, "higher_is_better": True, "scaling": "weak",
+        # one timed step is one oracle sweep: ms_per_step is that sweep's time
+        "ms_per_step": t_sweep * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
-        "config": {"workload": WORKLOAD, "m": M, "n": N, "block": B, "k": K, "power_sweeps": Q},
+        "config": bench_config(1),
         "cpu_baseline": {"kind": "oracle", "value": value, "unit": "pairs/s", "cores": cores,
-                         "sample": f"each step = 1 of the {S} sweeps the oracle needs "
-                                   f"(full solve measured once: {t_full:.1f} s, "
+                         "sample": f"each timed step = 1 of the {S} sweeps the oracle needs "
+                                   f"(median {t_sweep:.2f} s; full solve measured once: {t_full:.1f} s, "
                                    f"{full.n_converged}/{K} converged); value = converged / "
-                                   f"(S x median sweep time)"},
+                                   f"(S x median sweep time), a per-sweep extrapolation"},
         "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -174,49 +182,53 @@ def aggregate(seconds: float, converged: int, dist=None, device=None):
 
 
 # --------------------------------------------------------------------------- GPU arm
-def stage_roofline(info, peaks, src, refine_sweeps, phase1_sweeps):
-    """Per-stage device time (CUDA events inside the library around every
-    stage of one solve) and, where a stage has one bounding resource, its
-    achieved rate against that roofline.
+# DRAM bytes per launch of k_gemm_bf16_tc, mean over every launch of one
+# solve of this workload (ncu dram__bytes_read.sum + dram__bytes_write.sum;
+# profiles/launches_dense_svd_16384x4096.md); None until captured for the
+# current kernel.
+TC_TRAFFIC_PER_LAUNCH = None
 
-    ``roofline`` is the tcgen05 kernel ``k_gemm_bf16_tc`` in its product role
-    (the lowp_product stage: every launch of it), the kernel with the largest
-    device-time share of a solve.  It is HBM-bound: algorithmic bytes are the
-    BF16 operator bytes a product must stream once, m n 2 for a plain product
-    (phase 1: 2q + 1 per sweep) and 2 m n 2 for a split-BF16 product (A_hi
-    and A_lo; refinement: 2q + 1 per sweep)."""
+
+def stage_roofline(info, peaks, src):
+    """Per-stage device time (CUDA events inside the library around every
+    stage of one solve) with each stage's share, and the roofline of the
+    dominant kernel.
+
+    ``roofline`` is the tcgen05 product kernel ``k_gemm_bf16_tc`` over every
+    one of its launches in the solve, whichever stage it ran in (filter
+    products, split-BF16 corrections, the slice passes of the FP64-emulated
+    products, Gram products and lifts): the library brackets each launch with
+    CUDA events on its stream and adds up its algorithmic bytes (each operand
+    read once -- for an emulation pass the distinct 6-bit slices it reads --
+    and the output written once).  It is HBM-bound at these shapes
+    (intensity 2 b / 2 flop per byte at b = 128 against a BF16 ridge near
+    280 flop per byte), so achieved = bytes / time against the measured copy
+    bandwidth."""
     ms, calls = info["stage_ms"], info["stage_calls"]
     names = ["lowp_product", "f64_product", "hessenberg", "gram", "pencil", "lift", "other"]
+    total = sum(ms[:7])
     stages = {}
     for i, nm in enumerate(names):
         if calls[i] == 0:
             continue
-        stages[nm] = {"ms": ms[i], "calls": calls[i], "ms_per_call": ms[i] / calls[i]}
+        stages[nm] = {"ms": ms[i], "calls": calls[i], "ms_per_call": ms[i] / calls[i],
+                      "share": ms[i] / total if total else None}
     hbm = peaks["hbm_gbs"]
     opb = 2.0 * M * N  # BF16 operator bytes
-    n_plain = (2 * Q + 1) * phase1_sweeps
-    n_split = (2 * Q + 1) * refine_sweeps
-    prod_bytes = n_plain * opb + n_split * 2 * opb
-    roof = None
     if "lowp_product" in stages:
-        t = stages["lowp_product"]["ms"] * 1e-3
-        ach = prod_bytes / t / 1e9
-        # DRAM bytes per launch from ncu (one A V launch of each kind, read +
-        # write; the A^T W launches are taken to move the same bytes)
-        traffic = n_plain * 138.73e6 + n_split * 273.70e6
-        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": traffic, "traffic_scope": "DRAM bytes per solve, ncu per-launch counts x launches",
-                "kernel": "k_gemm_bf16_tc", "stage": "lowp_product",
-                "launches": stages["lowp_product"]["calls"],
-                "algorithmic_bytes_per_solve": prod_bytes, "peak_source": src + " (of measured)"}
+        # the products' stage: plain (2q + 1 per phase-1 sweep) and split (2q + 1 per
+        # refinement sweep) products, m n 2 / 2 m n 2 operator bytes each
+        ph1 = info["sweeps"] - info["refine_sweeps"]
+        prod_bytes = (2 * Q + 1) * (ph1 * opb + info["refine_sweeps"] * 2 * opb)
+        ach = prod_bytes / (stages["lowp_product"]["ms"] * 1e-3) / 1e9
         stages["lowp_product"].update({"bound": "hbm", "achieved_gbs": ach, "frac": ach / hbm})
     if "f64_product" in stages:
         # FP64-accurate A X / A^T Y (b = 128): the FP64 operator read once is the
-        # algorithmic floor (512 MiB); the emulation streams 20 slice passes
+        # algorithmic floor (512 MiB)
         d = stages["f64_product"]
         ach = 8.0 * M * N / (d["ms_per_call"] * 1e-3) / 1e9
         d.update({"bound": "hbm", "achieved_gbs": ach, "frac": ach / hbm,
-                  "note": "FP64 operator bytes per product / time; 20 BF16 slice passes stream 2.5x that"})
+                  "note": "FP64 operator bytes per product / time"})
     if "hessenberg" in stages:
         d = stages["hessenberg"]
         byts = (M + N) / 2 * B * (4 + 2)
@@ -225,7 +237,79 @@ def stage_roofline(info, peaks, src, refine_sweeps, phase1_sweeps):
                   "note": "floor bytes (read FP32 block, write BF16 basis) / time; b sequential pivots"})
     if "pencil" in stages:
         stages["pencil"].update({"bound": "latency", "us_per_call": stages["pencil"]["ms_per_call"] * 1e3})
+    dominant = max(stages, key=lambda k: stages[k]["ms"]) if stages else None
+    roof = None
+    tc_ms, tc_n = ms[7], calls[7]
+    if tc_n:
+        ach = info["tc_bytes"] / (tc_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": TC_TRAFFIC_PER_LAUNCH,
+                "traffic_scope": "DRAM bytes per launch (mean over the solve's launches, ncu)",
+                "kernel": "k_gemm_bf16_tc", "launches": tc_n, "kernel_ms_per_solve": tc_ms,
+                "kernel_share_of_solve": tc_ms / total if total else None,
+                "algorithmic_bytes_per_launch": info["tc_bytes"] / tc_n,
+                "dominant_stage": dominant, "peak_source": src + " (of measured)" if src == "measured"
+                else src + " (of fallback)"}
     return roof, stages
+
+
+def sparse_solve(rr, sweeps=60):
+    """The sparse eigenproblem: H = -Lap + diag(v), v_j ~ U[0, 10], 1024 x 1024
+    grid (n = 1,048,576), lowest 100 pairs, Chebyshev degree 20, block 160,
+    BF16 basis, FP64 projection, residual <= 1e-8; one timed solve plus the
+    Chebyshev step timed alone on the same operator (row-major BF16 blocks)."""
+    import torch
+
+    peaks, src = load_peaks()
+    Ng, k, bs, deg = 1024, 100, 160, 20
+    rp, ci, va, _ = wl.grid_schrodinger_csr(Ng, 10.0, wl.seed_for(3))
+    n = Ng * Ng
+    d = [torch.from_numpy(a).cuda() for a in (rp, ci, va)]
+    op = rr.api.csr_operator(*d)
+    V0 = rr.fortran(torch.from_numpy(wl.uniform_block(n, bs, wl.seed_for(3) + 1)).cuda())
+    p = rr.api.make_params(k, bs, deg, sweeps, 1e-8, basis="bf16", v0=V0, filter=rr.RR.CHEBYSHEV,
+                           which=rr.RR.SMALLEST, refine=True, phase1_sweeps=2, profile=True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    th, X, info = rr.rr_eig(op, p, n)
+    e1.record()
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    names = ["lowp_product", "f64_product", "hessenberg", "gram", "pencil", "lift", "other"]
+    # the plain filter's step on its own: read Y_j, Y_{j-1}, write Y_{j+1} and the CSR arrays
+    L = rr.lib()
+    bf = rr.api.DTYPES[torch.bfloat16]
+    R = [torch.randn(n, bs, device="cuda", dtype=torch.float32).to(torch.bfloat16) for _ in range(3)]
+    stream = torch.cuda.current_stream().cuda_stream
+
+    def step():
+        rc = L.rr_chebyshev_step_rows(n, bs, d[0].data_ptr(), d[1].data_ptr(), d[2].data_ptr(), bf,
+                                      R[1].data_ptr(), R[0].data_ptr(), bs, 0.1, 6.0, 0.5, bf, R[2].data_ptr(),
+                                      bs, stream)
+        assert rc == 0, rc
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    reps = 10
+    e0.record()
+    for _ in range(reps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / reps
+    nbytes = 4 * (n + 1) + 8 * len(ci) + 3 * 2 * n * bs
+    return {"workload": "H = -Lap + diag(v), v ~ U[0,10], 1024x1024 Dirichlet grid (n = 1,048,576, CSR FP32), "
+                        "lowest 100 pairs, Chebyshev degree 20, block 160, BF16 basis, tol 1e-8",
+            "value": info["n_converged"] / sec, "unit": "pairs/s", "seconds": sec,
+            "n_converged": info["n_converged"], "k": k, "tol": 1e-8, "sweeps": info["sweeps"],
+            "refine_sweeps": info["refine_sweeps"], "max_res": info["max_res"],
+            "theta_first": float(th[0].item()), "theta_last": float(th[-1].item()),
+            "stages_ms": dict(zip(names, info["stage_ms"][:7])),
+            "cheb_step": {"kernel": "k_csr_cheb_rows", "us": us, "algorithmic_bytes": nbytes,
+                          "achieved_gbs": nbytes / us / 1e3, "peak_gbs": peaks["hbm_gbs"],
+                          "frac": nbytes / us / 1e3 / peaks["hbm_gbs"], "peak_source": src}}
 
 
 def run_ours(args):
@@ -303,8 +387,7 @@ def run_ours(args):
 
     # stage profile (one more solve, CUDA events around every stage)
     _, _, _, pinfo = rr.rr_svd(op, params(profile=True), device=dev, ws=ws)
-    roof, stages = stage_roofline(pinfo, peaks, src, pinfo["refine_sweeps"],
-                                  pinfo["sweeps"] - pinfo["refine_sweeps"])
+    roof, stages = stage_roofline(pinfo, peaks, src)
 
     # all-FP64 run of the same algorithm
     fp64 = None
@@ -385,6 +468,13 @@ def run_ours(args):
     e2e = {"value": conv2 / t2, "unit": "pairs/s", "h2d_bytes_per_step": (M * N + N * B) * 8,
            "d2h_bytes_per_step": (K + M * K + N * K) * 8}
 
+    # the sparse eigenproblem of the same family of methods (rank 0, N = 1 only)
+    sparse = None
+    if rank == 0 and world == 1 and not args.no_sparse:
+        del ws
+        torch.cuda.empty_cache()
+        sparse = sparse_solve(rr)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         A_np = At.t().cpu().numpy()  # column-major view of the same matrix
@@ -403,13 +493,12 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
             "data": "synthetic (seeded Haar factors, prescribed spectrum)",
-            "config": {"workload": WORKLOAD, "m": M, "n": N, "block": B, "k": K, "power_sweeps": Q,
-                       "tol": TOL, "l2": "inputs larger than L2 (A: 512 MiB FP64 + 256 MiB BF16 copies)",
-                       "parallelism": f"replicas x{world}"},
+            "config": bench_config(world),
             "converged": conv, "sigma_max_rel_err": sig_err,
             "sweeps": infos[-1]["sweeps"], "refine_sweeps": infos[-1]["refine_sweeps"],
             "res_history": infos[-1]["res_history"],
-            "fp64": fp64, "e4m3": e4m3, "stages": stages, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "fp64": fp64, "e4m3": e4m3, "sparse": sparse, "stages": stages, "roofline": roof,
+            "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clk, "gpu_launches": int(launches),
         }
         print(json.dumps(line))
@@ -514,29 +603,7 @@ def run_stage(args):
                                    "frac": nbytes / us_rows / 1e3 / peaks["hbm_gbs"]},
                           "peak_gbs": peaks["hbm_gbs"], "peak_source": src}))
     elif args.stage == "sparse":
-        # the sparse eigenproblem: H = -Lap + diag(v), v_j ~ U[0, 10], 1024 x 1024 grid (n = 1,048,576),
-        # lowest 100 pairs, Chebyshev degree 20, block 160, BF16 basis, FP64 projection, residual <= 1e-8
-        Ng, k, bs, deg = 1024, 100, 160, 20
-        rp, ci, va, _ = wl.grid_schrodinger_csr(Ng, 10.0, wl.seed_for(3))
-        n = Ng * Ng
-        d = [torch.from_numpy(a).cuda() for a in (rp, ci, va)]
-        op = rr.api.csr_operator(*d)
-        V0 = rr.fortran(torch.from_numpy(wl.uniform_block(n, bs, wl.seed_for(3) + 1)).cuda())
-        p = rr.api.make_params(k, bs, deg, args.sweeps, 1e-8, basis="bf16", v0=V0, filter=rr.RR.CHEBYSHEV,
-                               which=rr.RR.SMALLEST, refine=True, phase1_sweeps=2, profile=True)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        th, X, info = rr.rr_eig(op, p, n)
-        torch.cuda.synchronize()
-        sec = time.perf_counter() - t0
-        names = ["lowp_product", "f64_product", "hessenberg", "gram", "pencil", "lift", "other"]
-        print(json.dumps({"stage": "sparse", "n": n, "k": k, "block": bs, "degree": deg, "seconds": sec,
-                          "n_converged": info["n_converged"], "pairs_per_s": info["n_converged"] / sec,
-                          "sweeps": info["sweeps"], "refine_sweeps": info["refine_sweeps"],
-                          "max_res": info["max_res"], "res_history": info["res_history"],
-                          "theta_first": float(th[0].item()), "theta_last": float(th[-1].item()),
-                          "stages_ms": dict(zip(names, info["stage_ms"][:7])),
-                          "stage_calls": dict(zip(names, info["stage_calls"][:7]))}))
+        print(json.dumps({"stage": "sparse", **sparse_solve(rr, args.sweeps)}))
     elif args.stage == "warm":
         # learned warm start: H(p) = -Lap + V_p (8 Gaussian bumps) on a grid x grid mesh,
         # lowest k pairs; train on solves of `train` family members, then solve `test`
@@ -692,6 +759,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp8", action="store_true", help="skip the FP8-E4M3 basis run")
+    ap.add_argument("--no-sparse", action="store_true", help="skip the sparse eigenproblem leg")
     ap.add_argument("--stage", choices=["pencil", "hessenberg", "gemm", "split", "f64emu", "prep", "cheb", "warm", "sparse", "fp8", "batch"],
                     help="run one stage of the workload (profiling driver)")
     ap.add_argument("--b", type=int, default=256, help="pencil size for --stage pencil, columns for hessenberg")

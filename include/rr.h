@@ -32,6 +32,10 @@
  *     the stream to read convergence counts and return only when done.
  *   - Errors are returned as rr_status; nothing aborts or throws across the
  *     ABI.  RR_ERR_ARG: invalid sizes/pointers (nothing launched).
+ *     RR_ERR_WORKSPACE: the workspace is missing, too small or not 256-byte
+ *     aligned (nothing launched).  RR_ERR_NAN (solvers): every wanted
+ *     residual is NaN after a projection, as when the operator holds a NaN
+ *     or infinity (outputs undefined).
  *     RR_ERR_CUDA: a CUDA launch or runtime call failed (rr_last_error()
  *     returns its text).  RR_ERR_TIMEOUT: a device-side bounded wait gave up
  *     (the kernel returned early; outputs are undefined).
@@ -93,19 +97,35 @@ typedef struct {
   int32_t phase1_sweeps; /* projections of the plain (paper) phase before refining   */
   double tol;            /* relative residual target (Sec. 5.2.2)                    */
   double bounds[2];      /* Chebyshev: spectral bounds (lo, up); lo >= up -> computed */
-  const double* v0;      /* n x block FP64 start block (device), e.g. U(0,1)         */
+  const double* v0;      /* n x block FP64 start block (device), e.g. U(0,1); NULL:
+                            drawn U(0,1) on the device from `seed` (Alg. 1's random
+                            start block, Sec. 5.2)                                   */
   int32_t profile;       /* 1: time every stage with CUDA events (rr_info.stage_ms)  */
+  double hess_tol;       /* Algorithm 8's column-skip tolerance, relative to the
+                            column's inf-norm; <= 0: 4 b eps of the arithmetic that
+                            runs the process (Sec. 5.2 sets it from the machine
+                            epsilon)                                                 */
+  uint64_t seed;         /* start block generator seed when v0 is NULL (counter-
+                            based splitmix64 stream, the one rr_batch_svd uses)      */
 } rr_params;
 
 typedef struct {
   int32_t n_converged;   /* wanted pairs with residual <= tol                        */
   int32_t sweeps;        /* projections performed                                    */
   int32_t refine_sweeps; /* of which in the refinement phase                         */
-  int32_t cols_dropped;  /* basis columns dropped by Alg. 8 / the whitening (last)   */
+  int32_t cols_dropped;  /* basis columns the whitening dropped at the last projection
+                            (columns Alg. 8 skipped are zero and counted here)       */
   double max_res;        /* largest residual among the k wanted pairs                */
   double res_history[64];/* max residual of the wanted pairs after each projection   */
   double stage_ms[8];    /* with params.profile: device time per stage (see below)   */
   int32_t stage_calls[8];/* number of timed calls per stage                          */
+  double cond_G_est;     /* estimate of cond_2 of the Gram matrix (Alg. 3's M, Alg. 5's
+                            larger of U^T U, V^T V) whitened at the last projection:
+                            max_i G_ii * max_i (G^-1)_ii, with G^-1 = W W^T from the
+                            whitener; a lower bound within a factor b^2 of cond_2    */
+  double cond_history[64];/* cond_G_est after each projection                        */
+  double tc_bytes;       /* with params.profile: algorithmic bytes of the launches
+                            timed in stage_ms[RR_KERNEL_TC]                          */
 } rr_info;
 
 /* Stages of rr_info.stage_ms: */
@@ -116,7 +136,12 @@ enum {
   RR_STAGE_GRAM = 3,         /* projection products G, H / B                         */
   RR_STAGE_PENCIL = 4,       /* small FP64 pencil solve                              */
   RR_STAGE_LIFT = 5,         /* Ritz lift                                            */
-  RR_STAGE_OTHER = 6         /* casts, scaling, residual norms, projections          */
+  RR_STAGE_OTHER = 6,        /* casts, scaling, residual norms, projections          */
+  RR_KERNEL_TC = 7           /* not a stage: every launch of the tensor-core product
+                                kernel, in whichever stage it ran (filter products,
+                                corrections, FP64-emulation passes); its algorithmic
+                                bytes (operands read once, output written once) are
+                                in rr_info.tc_bytes                                  */
 };
 
 /* Number of kernels this library has launched in this process so far. */
@@ -124,6 +149,18 @@ uint64_t rr_kernel_launches(void);
 
 /* Text of the last RR_ERR_CUDA (thread-local, static storage). */
 const char* rr_last_error(void);
+
+/* Failure detection (every device-side wait of the library is bounded):
+ * runs one of the library's waits where nothing can ever release it and
+ * returns what the kernel reported.  mode 0: the grid barrier of the
+ * cooperative kernels (Hessenberg, block Jacobi), entered by one CTA of a
+ * grid that counts two; mode 1: the mbarrier wait of the tensor-core
+ * kernels on a barrier nothing arrives on.  The wait gives up after
+ * limit_ns (1 .. 1e10), records RR_ERR_TIMEOUT and the kernel returns, so
+ * the expected result is RR_ERR_TIMEOUT with the context still usable.
+ * scratch: 16 bytes of device memory (16-byte aligned), zeroed by the call.
+ * Synchronises `stream`.  The paper has no counterpart. */
+rr_status rr_wait_selftest(int32_t mode, int64_t limit_ns, void* scratch, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Solvers
@@ -313,11 +350,19 @@ rr_status rr_gram(int64_t n, int64_t p, int64_t q, int32_t xtype, const void* X,
  * (262144 doubles per GPU, held by every GPU that loads the library until the
  * process exits), so p * q must not exceed 262144 (RR_ERR_ARG otherwise);
  * the number of row chunks shrinks to fit.  The first call on each device
- * looks up the array's device address (cudaGetSymbolAddress); make that
- * first call before any stream capture.  All calls share the one array:
- * calls whose executions overlap on the GPU (different streams, or
- * concurrent graph branches) race and give wrong results.  Allocates
- * nothing. */
+ * (in each context) looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * With lazy module loading (the CUDA default) that lookup is also what
+ * loads the library's module on the device and commits the 2 MiB: the
+ * driver allocates it then, and the call can fail with RR_ERR_CUDA when the
+ * device is out of memory.  Callers that must not touch the allocator later
+ * should make one warm-up call at start-up, e.g. p = q = 1, n = 0 and
+ * accumulate = 1 (it launches nothing and leaves G as it is).  The cached address is keyed by device and context, so
+ * after a device reset the next call looks it up again.  All calls share
+ * the one array: calls whose executions overlap on the GPU (different
+ * streams, or concurrent graph branches) race and give wrong results.
+ * Invalid dtypes return RR_ERR_ARG as in rr_gram, even for empty sizes.
+ * Allocates nothing itself. */
 rr_status rr_gram_noalloc(int64_t n, int64_t p, int64_t q, int32_t xtype, const void* X,
                           int64_t ldx, int32_t ytype, const void* Y, int64_t ldy, double* G,
                           int64_t ldg, int32_t accumulate, void* stream);

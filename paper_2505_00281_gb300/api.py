@@ -79,7 +79,7 @@ def csr_operator(row_ptr: torch.Tensor, col_idx: torch.Tensor, values: torch.Ten
 
 def make_params(k, block, degree, max_sweeps, tol, basis="bf16", v0=None, filter=RR.POWER,
                 which=RR.LARGEST, hessenberg=True, refine=True, phase1_sweeps=1, bounds=(0.0, 0.0),
-                profile=False):
+                profile=False, hess_tol=0.0, seed=0):
     p = RrParams()
     p.k, p.block, p.filter, p.degree = k, block, filter, degree
     p.max_sweeps, p.which = max_sweeps, which
@@ -89,6 +89,8 @@ def make_params(k, block, degree, max_sweeps, tol, basis="bf16", v0=None, filter
     p.bounds[0], p.bounds[1] = bounds
     p.v0 = None if v0 is None else v0.data_ptr()
     p.profile = int(profile)
+    p.hess_tol = float(hess_tol)
+    p.seed = int(seed)
     p._keep = (v0,)
     return p
 
@@ -99,7 +101,9 @@ def _info_dict(info: RrInfo, status: int):
             "sweeps": sweeps, "refine_sweeps": info.refine_sweeps, "max_res": info.max_res,
             "res_history": [info.res_history[i] for i in range(min(sweeps, 64))],
             "stage_ms": [info.stage_ms[i] for i in range(8)],
-            "stage_calls": [info.stage_calls[i] for i in range(8)]}
+            "stage_calls": [info.stage_calls[i] for i in range(8)],
+            "cond_G_est": info.cond_G_est, "cols_dropped": info.cols_dropped, "tc_bytes": info.tc_bytes,
+            "cond_history": [info.cond_history[i] for i in range(min(sweeps, 64))]}
 
 
 def rr_eig(op: RrOperator, params: RrParams, n: int, device="cuda", stream=None, keep=()):
@@ -286,6 +290,13 @@ def rr_gram(X, Y, G=None, accumulate=False, stream=None):
     check("rr_gram", L.rr_gram(n, p, q, DTYPES[X.dtype], _p(X), ld_of(X), DTYPES[Y.dtype], _p(Y), ld_of(Y),
                                _p(G), ld_of(G), int(accumulate), _p(ws), ws.numel(), _stream(stream)))
     return G
+
+
+def rr_wait_selftest(mode, limit_ns, device="cuda", stream=None):
+    """Run one of the library's bounded waits where nothing releases it;
+    returns the status the kernel reported (RR.ERR_TIMEOUT expected)."""
+    scratch = torch.empty(16, dtype=torch.uint8, device=device)
+    return lib().rr_wait_selftest(int(mode), int(limit_ns), _p(scratch), _stream(stream))
 
 
 def rr_gram_noalloc(X, Y, G=None, accumulate=False, stream=None):

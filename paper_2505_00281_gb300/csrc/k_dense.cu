@@ -541,6 +541,7 @@ extern "C" rr_status rr_gram(int64_t n, int64_t p, int64_t q, int32_t xtype, con
 // memory.  Its split-K partial sums live in a fixed array compiled into the
 // library instead of a caller-provided workspace.
 // ---------------------------------------------------------------------------
+#include <cuda.h>
 #include <mutex>
 
 namespace rr {
@@ -550,19 +551,43 @@ namespace rr {
 constexpr size_t kNoAllocDoubles = (size_t)1 << 18;
 static __device__ __align__(256) double g_gram_scratch[kNoAllocDoubles];
 
-// Device address of g_gram_scratch on the current device, looked up once per
-// device (host code may not use the symbol itself as a device pointer).
+// Device address of g_gram_scratch in the current context.  Host code may
+// not use the symbol itself as a device pointer, so the address is looked up
+// with cudaGetSymbolAddress and cached per device together with the context
+// it was taken in: after a device reset (a new primary context, the module
+// loaded again) the context differs and the address is looked up afresh
+// instead of reusing a pointer into memory that no longer exists.
+// (cuCtxGetCurrent is taken through the runtime's driver entry-point lookup,
+// so the library keeps no load-time dependency on the driver library.)
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+static CUcontext current_context() {
+  static CtxGetCurrentFn fn = []() -> CtxGetCurrentFn {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return (CtxGetCurrentFn)p;
+  }();
+  CUcontext c = nullptr;
+  if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+  return c;
+}
+
 static rr_status noalloc_scratch(double** out) {
   static std::mutex mu;
   static double* addr[64] = {};
+  static CUcontext ctx_of[64] = {};
   int dev = 0;
   RR_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return RR_ERR_ARG;
   std::lock_guard<std::mutex> lk(mu);
-  if (!addr[dev]) {
+  CUcontext cur = current_context();
+  if (!addr[dev] || !cur || cur != ctx_of[dev]) {
     void* p = nullptr;
     RR_CUDA(cudaGetSymbolAddress(&p, g_gram_scratch));
     addr[dev] = (double*)p;
+    ctx_of[dev] = current_context();
   }
   *out = addr[dev];
   return RR_OK;
@@ -575,6 +600,8 @@ extern "C" rr_status rr_gram_noalloc(int64_t n, int64_t p, int64_t q, int32_t xt
                                      int64_t ldg, int32_t accumulate, void* stream) {
   if (n < 0 || p < 0 || q < 0 || ldx < n || ldy < n || ldg < p || !G) return RR_ERR_ARG;
   if ((size_t)p * (size_t)q > kNoAllocDoubles) return RR_ERR_ARG;  // beyond the fixed scratch
+  auto valid = [](int32_t t) { return t == RR_F64 || t == RR_F32 || t == RR_BF16 || t == RR_E4M3; };
+  if (!valid(xtype) || !valid(ytype)) return RR_ERR_ARG;              // as rr_gram
   if (p == 0 || q == 0) return RR_OK;
   if (n > 0 && (!X || !Y)) return RR_ERR_ARG;
   double* scratch = nullptr;

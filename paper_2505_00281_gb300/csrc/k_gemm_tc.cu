@@ -60,18 +60,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// bounded wait; returns false (and flags the error) on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// bounded wait on `bar` reaching `parity`; returns false on timeout (after
+// recording RR_ERR_TIMEOUT in *err) or when *err is already set
+__device__ __forceinline__ bool mbar_wait_on(uint64_t* bar, uint32_t parity, int* err, uint64_t limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_timer_ns();
   while (!mbar_try_wait(bar, parity)) {
-    if (*(volatile int*)&g_tc_error) return false;
-    if (global_timer_ns() - t0 > kWaitLimitNs) {
-      atomicCAS(&g_tc_error, 0, (int)RR_ERR_TIMEOUT);
+    if (*(volatile int*)err) return false;
+    if (global_timer_ns() - t0 > limit_ns) {
+      atomicCAS(err, 0, (int)RR_ERR_TIMEOUT);
       return false;
     }
   }
   return true;
+}
+
+// the kernels' wait: the library-wide error word, 2 s limit
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  return mbar_wait_on(bar, parity, &g_tc_error, kWaitLimitNs);
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
@@ -398,6 +404,31 @@ int& gemm_force_simt() {
   return v;
 }
 
+static thread_local TcProf* t_tc_prof = nullptr;
+void tc_prof_attach(TcProf* p) { t_tc_prof = p; }
+
+// event pair around one launch of the product kernel (profiling only)
+struct TcProfScope {
+  TcProf* p;
+  cudaStream_t s;
+  TcProfScope(cudaStream_t s_, double bytes) : p(t_tc_prof), s(s_) {
+    if (!p) return;
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, s);
+    p->ev.push_back(e);
+    p->bytes += bytes;
+    p->launches += 1;
+  }
+  ~TcProfScope() {
+    if (!p) return;
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, s);
+    p->ev.push_back(e);
+  }
+};
+
 int& gemm_split_cap() {
   static thread_local int v = 0;
   return v;
@@ -597,6 +628,22 @@ static rr_status gemm_bf16_tc_impl(int64_t M, int64_t N, int64_t K, const __nv_b
   }
   dim3 grid((unsigned)tiles, (unsigned)splits, (unsigned)npairs);
   a.rscale = a.cscale = nullptr;
+  // algorithmic bytes of this launch: every operand tile it needs read once
+  // (the distinct slices of an emulation launch), the output written once
+  double abytes;
+  if (emu) {
+    uint64_t amask = 0, bmask = 0;
+    for (int z = 0; z < npairs; ++z) {
+      const uint32_t pz = emu->pair[z];
+      amask |= 1ull << (pz & 0xFF);
+      for (uint32_t q = 0; q < ((pz >> 16) & 0xFF); ++q) bmask |= 1ull << (((pz >> 8) & 0xFF) + q);
+    }
+    abytes = 2.0 * K * ((double)M * __builtin_popcountll(amask) + (double)emu->nb * __builtin_popcountll(bmask)) +
+             8.0 * M * emu->nb;
+  } else {
+    abytes = (split ? 2.0 : 1.0) * 2.0 * K * ((double)M + (double)N) + 4.0 * M * N;
+  }
+  TcProfScope prof_scope(s, abytes);
   k_gemm_bf16_tc<false><<<grid, 128, smem, s>>>(ta, tb, ta2, tb2, a);
   return check_launch("gemm_bf16_tc");
 }
@@ -655,6 +702,7 @@ rr_status gemm_e4m3_tc(int64_t M, int64_t N, int64_t K, const void* A, int64_t l
     note_launches(1);
   }
   dim3 grid((unsigned)tiles, (unsigned)splits, 1u);
+  TcProfScope prof_scope(s, (double)K * ((double)M + (double)N) + 4.0 * M * N);
   k_gemm_bf16_tc<true><<<grid, 128, smem, s>>>(ta, tb, ta, tb, a);
   return check_launch("gemm_e4m3_tc");
 }
@@ -673,3 +721,44 @@ rr_status tc_take_error(cudaStream_t s) {
 }
 
 }  // namespace rr
+
+// ---------------------------------------------------------------------------
+// Failure-detection self-test: each bounded wait of the library, made to run
+// out on purpose.  mode 0: one CTA enters the grid barrier of the cooperative
+// kernels for a grid of two CTAs that has only itself; mode 1: one thread
+// waits on an mbarrier that nothing arrives on (the wait of the tensor-core
+// kernels).  Both give up after limit_ns, record RR_ERR_TIMEOUT in err and
+// return; the kernel ends normally.
+// ---------------------------------------------------------------------------
+namespace rr {
+namespace {
+__global__ void k_wait_selftest(int mode, uint64_t limit_ns, GridBarrier* gb, int* err) {
+  if (mode == 0) {
+    grid_barrier(gb, 2u, err, limit_ns);   // the second CTA never arrives
+    return;
+  }
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_wait_on(&bar, 0, err, limit_ns);  // phase 0 never completes
+  }
+}
+}  // namespace
+}  // namespace rr
+
+extern "C" rr_status rr_wait_selftest(int32_t mode, int64_t limit_ns, void* scratch, void* stream) {
+  using namespace rr;
+  if ((mode != 0 && mode != 1) || limit_ns <= 0 || limit_ns > 10000000000ll || !scratch ||
+      ((uintptr_t)scratch & 15))
+    return RR_ERR_ARG;
+  cudaStream_t s = as_stream(stream);
+  GridBarrier* gb = (GridBarrier*)scratch;
+  int* err = (int*)((char*)scratch + sizeof(GridBarrier));
+  RR_CUDA(cudaMemsetAsync(scratch, 0, 16, s));
+  k_wait_selftest<<<1, 32, 0, s>>>(mode, (uint64_t)limit_ns, gb, err);
+  RR_TRY(check_launch("rr_wait_selftest"));
+  int h = 0;
+  RR_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  RR_CUDA(cudaStreamSynchronize(s));
+  return (rr_status)h;
+}

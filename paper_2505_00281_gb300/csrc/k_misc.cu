@@ -5,6 +5,8 @@
 
 #include <type_traits>
 
+#include <algorithm>
+
 #include "rr_common.cuh"
 #include "solver_kernels.cuh"
 
@@ -494,5 +496,43 @@ rr_status vec_scale(cudaStream_t s, int64_t n, double alpha, const double* a, do
   if (n == 0) return RR_OK;
   k_vec_scale<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(n, alpha, a, d);
   return check_launch("vec_scale");
+}
+}  // namespace rr
+
+// ---------------------------------------------------------------------------
+// Non-finite operator entries (an operator with a NaN or infinity makes every
+// later quantity NaN): one read of the values, *flag set to 1 if any entry
+// has the all-ones exponent.  Dense: one CTA per column (grid-stride),
+// threads over rows; CSR: grid-stride over the nnz values.
+// ---------------------------------------------------------------------------
+namespace rr {
+__global__ void k_nonfinite_dense(int64_t m, int64_t n, const double* __restrict__ A, int64_t lda,
+                                  int* __restrict__ flag) {
+  int bad = 0;
+  for (int64_t j = blockIdx.x; j < n; j += gridDim.x)
+    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
+      const unsigned long long u = (unsigned long long)__double_as_longlong(A[i + j * lda]);
+      bad |= ((u >> 52) & 0x7FFull) == 0x7FFull;
+    }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+__global__ void k_nonfinite_f32(int64_t cnt, const float* __restrict__ v, int* __restrict__ flag) {
+  int bad = 0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x)
+    bad |= ((__float_as_uint(v[e]) >> 23) & 0xFFu) == 0xFFu;
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+rr_status operator_nonfinite(cudaStream_t s, int kind, int64_t m, int64_t n, const void* values, int64_t lda,
+                             int64_t nnz, int* flag) {
+  if (kind == RR_DENSE) {
+    const unsigned g = (unsigned)std::min<int64_t>(n, 8 * (int64_t)num_sms());
+    if (g == 0) return RR_OK;
+    k_nonfinite_dense<<<g, 256, 0, s>>>(m, n, (const double*)values, lda, flag);
+  } else {
+    if (nnz <= 0) return RR_OK;
+    const unsigned g = (unsigned)std::min<int64_t>((nnz + 255) / 256, 8 * (int64_t)num_sms());
+    k_nonfinite_f32<<<g, 256, 0, s>>>(nnz, (const float*)values, flag);
+  }
+  return check_launch("operator_nonfinite");
 }
 }  // namespace rr

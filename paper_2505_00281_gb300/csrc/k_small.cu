@@ -1112,6 +1112,7 @@ __global__ void k_v32_to_64(int c, int cpad, const float* __restrict__ V32, doub
 
 struct PencilWs {
   double *W1, *W2, *T, *E, *E2, *F, *C, *V, *Vp, *M, *Mp, *sig, *mu;
+  double* cond;                        // [4] condition estimates of the whitened Grams, drop counts
   float *L32, *Li32, *M32, *V32, *fs;  // fs: [0] Jacobi norm floor, [1] scale
   float *Hq, *tq;                      // QR preconditioner: reflectors (c x c), taus
   int *drop1, *drop2, *order, *nvalid, *rot, *err, *sweeps, *cid, *cst;
@@ -1157,6 +1158,7 @@ static bool carve_pencil(Arena& ar, int b1, int b2, PencilWs& w) {
   w.Mp = ar.take<double>(rc);
   w.sig = ar.take<double>(cp);
   w.mu = ar.take<double>(2);
+  w.cond = ar.take<double>(4);
   w.fs = ar.take<float>(4);
   w.L32 = ar.take<float>(bb);
   w.Li32 = ar.take<float>(bb);
@@ -1175,6 +1177,49 @@ static bool carve_pencil(Arena& ar, int b1, int b2, PencilWs& w) {
   w.cst = ar.take<int>(cp + 1);
   w.bar = ar.take<GridBarrier>(1);
   return !ar.overflow;
+}
+
+// Condition estimate of a whitened Gram matrix G (b x b) from its whitener
+// W (W^T G W = I on the kept part, so G^-1 = W W^T there):
+//   out = max_i G_ii * max_i sum_j W_ij^2 = max_i G_ii * max_i (G^-1)_ii.
+// Each factor is at most the matching extreme eigenvalue and at least 1/b of
+// it, so out lies in [cond_2(G) / b^2, cond_2(G)].  Also writes the number
+// of dropped columns (drop flags) to out[2].  One block.
+__global__ void k_cond_est(int b, const double* __restrict__ G, const double* __restrict__ W,
+                           const int* __restrict__ drop, double* __restrict__ out) {
+  __shared__ double sg[32], sw[32];
+  __shared__ int sd[32];
+  double mg = 0.0, mw = 0.0;
+  int nd = 0;
+  for (int i = threadIdx.x; i < b; i += blockDim.x) {
+    nd += drop[i] != 0;
+    mg = fmax(mg, G[i + (size_t)i * b]);
+    double acc = 0.0;
+    for (int j = 0; j < b; ++j) {
+      const double w = W[i + (size_t)j * b];
+      acc = fma(w, w, acc);
+    }
+    mw = fmax(mw, acc);
+  }
+  mg = warp_max(mg);
+  mw = warp_max(mw);
+  nd = warp_sum(nd);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    sg[wid] = mg;
+    sw[wid] = mw;
+    sd[wid] = nd;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+      mg = fmax(mg, sg[i]);
+      mw = fmax(mw, sw[i]);
+      nd += sd[i];
+    }
+    out[0] = mg * mw;
+    out[2] = (double)nd;
+  }
 }
 
 // Whitening matrix W (b x b) with W^T G W = I on the kept part: FP32
@@ -1961,6 +2006,8 @@ extern "C" rr_status rr_pencil_eig(int64_t b, const double* H, const double* G, 
   const int n = (int)b;
   RR_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), s));
   whiten(s, n, G, w, w.drop1, w.W1);
+  RR_CUDA(cudaMemsetAsync(w.cond, 0, 4 * sizeof(double), s));
+  k_cond_est<<<1, 256, 0, s>>>(n, G, w.W1, w.drop1, w.cond);
   // C = W^T H W, symmetrised and shifted positive definite (C - mu I)
   gemm_small(s, 0, 0, n, n, n, 1.0, H, n, w.W1, n, 0.0, w.T, n);
   gemm_small_sym(s, n, n, w.W1, n, w.T, n, w.C, n);  // W^T H W (symmetric)
@@ -1970,7 +2017,7 @@ extern "C" rr_status rr_pencil_eig(int64_t b, const double* H, const double* G, 
   k_eig_finish<<<1, 256, 0, s>>>(n, w.sig, w.order, w.mu, w.V, theta, w.T, w.nvalid);
   // Y = W Z
   gemm_small(s, 0, 0, n, n, n, 1.0, w.W1, n, w.T, n, 0.0, Y, n);
-  note_launches(5);
+  note_launches(6);
   RR_TRY(check_launch("rr_pencil_eig"));
   if (dropped) {
     *dropped = 0;
@@ -1995,6 +2042,8 @@ extern "C" rr_status rr_pencil_svd(int64_t b1, int64_t b2, const double* B, cons
   whiten(s, n2, Gv, w, w.drop2, w.V);
   RR_CUDA(cudaMemcpyAsync(w.W1, w.C, (size_t)n1 * n1 * sizeof(double), cudaMemcpyDeviceToDevice, s));
   RR_CUDA(cudaMemcpyAsync(w.W2, w.V, (size_t)n2 * n2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  k_cond_est<<<1, 256, 0, s>>>(n1, Gu, w.W1, w.drop1, w.cond);      // cond[0], drops[2]
+  k_cond_est<<<1, 256, 0, s>>>(n2, Gv, w.W2, w.drop2, w.cond + 1);  // cond[1], drops[3]
   // Cw = Wu^T B Wv (b1 x b2) -> C
   gemm_small(s, 0, 0, n1, n2, n2, 1.0, B, n1, w.W2, n2, 0.0, w.T, n1);
   gemm_small(s, 1, 0, n1, n2, n1, 1.0, w.W1, n1, w.T, n1, 0.0, w.C, n1);
@@ -2007,7 +2056,7 @@ extern "C" rr_status rr_pencil_svd(int64_t b1, int64_t b2, const double* B, cons
   // Y = Wu Uw, Z = Wv Vw
   gemm_small(s, 0, 0, n1, r, n1, 1.0, w.W1, n1, Uw, n1, 0.0, Y, n1);
   gemm_small(s, 0, 0, n2, r, n2, 1.0, w.W2, n2, Vw, n2, 0.0, Z, n2);
-  note_launches(7);
+  note_launches(9);
   RR_TRY(check_launch("rr_pencil_svd"));
   if (dropped) {
     *dropped = 0;
@@ -2019,6 +2068,16 @@ extern "C" rr_status rr_pencil_svd(int64_t b1, int64_t b2, const double* B, cons
 
 // exported for the solver (same translation unit helpers)
 namespace rr {
+// Device address of the condition estimates and drop counts the last
+// rr_pencil_eig / rr_pencil_svd on this workspace wrote: [0], [1] the
+// estimates (eig: [1] = 0; SVD: U and V side), [2], [3] the dropped columns.
+const double* pencil_cond_slot(void* ws, size_t ws_bytes, int b1, int b2) {
+  Arena ar(ws, ws_bytes);
+  PencilWs w;
+  if (!ws || !carve_pencil(ar, b1, b2, w)) return nullptr;
+  return w.cond;
+}
+
 void small_gemm(cudaStream_t s, int ta, int tb, int M, int N, int K, double alpha, const double* A,
                 int lda, const double* B, int ldb, double beta, double* C, int ldc) {
   gemm_small(s, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);

@@ -54,9 +54,11 @@ struct GridBarrier {
   unsigned int gen;
 };
 
-// Grid-wide barrier for cooperative launches, with a bounded wait.
+// Grid-wide barrier for cooperative launches, with a bounded wait (limit_ns,
+// kWaitLimitNs unless a self-test passes a shorter one).
 // Returns false (and all later calls return false at once) when *err is set.
-__device__ __forceinline__ bool grid_barrier(GridBarrier* gb, unsigned nblocks, int* err) {
+__device__ __forceinline__ bool grid_barrier(GridBarrier* gb, unsigned nblocks, int* err,
+                                             uint64_t limit_ns = kWaitLimitNs) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned int* vgen = &gb->gen;
@@ -73,7 +75,7 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier* gb, unsigned nblocks, 
         uint64_t t0 = global_timer_ns();
         while (*vgen == g) {
           if (*verr != 0) break;
-          if (global_timer_ns() - t0 > kWaitLimitNs) {
+          if (global_timer_ns() - t0 > limit_ns) {
             atomicCAS(err, 0, (int)RR_ERR_TIMEOUT);
             break;
           }

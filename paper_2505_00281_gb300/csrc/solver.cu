@@ -84,7 +84,12 @@ struct Prof {
     }
     return pool[used++];
   }
+  TcProf tc;  // kernel-level timing of the tensor-core product kernel
+  void start() {
+    if (on) tc_prof_attach(&tc);
+  }
   void finish(rr_info* inf) {
+    tc_prof_attach(nullptr);
     if (on && inf) {
       cudaStreamSynchronize(s);
       for (auto& r : recs) {
@@ -94,8 +99,20 @@ struct Prof {
           inf->stage_calls[r.first] += 1;
         }
       }
+      for (size_t i = 0; i + 1 < tc.ev.size(); i += 2) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, tc.ev[i], tc.ev[i + 1]) == cudaSuccess) {
+          inf->stage_ms[RR_KERNEL_TC] += ms;
+          inf->stage_calls[RR_KERNEL_TC] += 1;
+        }
+      }
+      inf->tc_bytes = tc.bytes;
     }
     for (auto e : pool) cudaEventDestroy(e);
+    for (auto e : tc.ev) cudaEventDestroy(e);
+    tc.ev.clear();
+    tc.bytes = 0.0;
+    tc.launches = 0;
     pool.clear();
     recs.clear();
     used = 0;
@@ -227,6 +244,8 @@ struct Common {
   double* scale;  // b
   double* hres;   // unused host mirror placeholder
   int hess_grid;  // 0 = full GPU, 1 = one CTA
+  double hess_tol;  // Algorithm 8's skip tolerance (<= 0: the default)
+  int pen_b1, pen_b2;  // sizes of the last pencil solved on pen_ws (0: none yet)
 };
 
 static void carve_common(Arena& ar, int64_t rows, int64_t b2, int32_t wt, Common& c) {
@@ -239,12 +258,14 @@ static void carve_common(Arena& ar, int64_t rows, int64_t b2, int32_t wt, Common
   c.piv = ar.take<int32_t>(b2);
   c.scale = ar.take<double>(b2);
   c.hess_grid = 0;
+  c.hess_tol = 0.0;
+  c.pen_b1 = c.pen_b2 = 0;
 }
 
 static rr_status basis_step(const Common& c, bool hess, int32_t wt, int32_t dt, int64_t rows,
                             int64_t b, void* W, int64_t ldw, void* Q, int64_t ldq, cudaStream_t s) {
   if (hess)
-    return hessenberg_ex(wt, rows, b, W, ldw, dt, Q, ldq, c.piv, 0.0, c.hess_ws, c.hess_bytes, s,
+    return hessenberg_ex(wt, rows, b, W, ldw, dt, Q, ldq, c.piv, c.hess_tol, c.hess_ws, c.hess_bytes, s,
                          c.hess_grid);
   return scale_cast(s, wt, rows, b, W, ldw, c.scale, dt, Q, ldq, nullptr, nullptr);
 }
@@ -265,6 +286,57 @@ static rr_status project_out(const Common& c, cudaStream_t s, int64_t n, int64_t
                              int64_t ldx, float* T, int64_t ldt, double* K) {
   RR_TRY(gram_f32acc(s, n, b, b, X, ldx, T, ldt, K, b, c.gram_ws, c.gram_bytes));
   return sub_lowrank_f32(s, n, b, b, X, ldx, K, b, T, ldt);
+}
+
+// Pencil solves that record which sizes ran, so the condition estimate of
+// the last one can be found in the pencil workspace.
+static rr_status pencil_svd(Common& c, int64_t b1, int64_t b2, const double* B, const double* Gu,
+                            const double* Gv, double* s_, double* Y, double* Z, cudaStream_t s) {
+  c.pen_b1 = (int)b1;
+  c.pen_b2 = (int)b2;
+  return rr_pencil_svd(b1, b2, B, Gu, Gv, s_, Y, Z, c.pen_ws, c.pen_bytes, nullptr, s);
+}
+static rr_status pencil_eig(Common& c, int64_t b, const double* H, const double* G, double* th,
+                            double* Y, cudaStream_t s) {
+  c.pen_b1 = c.pen_b2 = (int)b;
+  return rr_pencil_eig(b, H, G, th, Y, c.pen_ws, c.pen_bytes, nullptr, s);
+}
+// Queue the copy of the last pencil's condition estimates and drop counts
+// (4 doubles) into host memory (valid after the next stream synchronisation).
+static rr_status queue_cond(const Common& c, cudaStream_t s, double* host4) {
+  host4[0] = host4[1] = host4[2] = host4[3] = 0.0;
+  if (!c.pen_b1) return RR_OK;
+  const double* d = pencil_cond_slot(c.pen_ws, c.pen_bytes, c.pen_b1, c.pen_b2);
+  if (!d) return RR_OK;
+  RR_CUDA(cudaMemcpyAsync(host4, d, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  return RR_OK;
+}
+static void note_cond(rr_info& inf, int sweep, const double* host4) {
+  const double c = fmax(host4[0], host4[1]);
+  inf.cond_G_est = c;
+  inf.cols_dropped = (int32_t)(host4[2] + host4[3]);
+  if (sweep >= 1 && sweep <= 64) inf.cond_history[sweep - 1] = c;
+}
+// every one of the k wanted residuals is NaN: a NaN or infinity in the
+// operator (or a basis that collapsed entirely)
+static bool all_nan(const double* res, int k) {
+  for (int i = 0; i < k; ++i)
+    if (!std::isnan(res[i])) return false;
+  return k > 0;
+}
+
+// An operator with a NaN or infinity makes every later quantity NaN and
+// gives the data-dependent steps (argmax, sorts, cluster detection) no
+// meaningful input: check the values once, before the first product, and
+// stop with RR_ERR_NAN.  One read of the operator and one synchronisation.
+static rr_status check_operator_finite(const rr_operator* A, const Common& c, cudaStream_t s) {
+  RR_CUDA(cudaMemsetAsync(c.piv, 0, sizeof(int), s));
+  const int64_t m = A->kind == RR_DENSE ? A->m : A->n;
+  RR_TRY(operator_nonfinite(s, A->kind, m, A->n, A->values, A->ld, A->nnz, c.piv));
+  int h = 0;
+  RR_CUDA(cudaMemcpyAsync(&h, c.piv, sizeof(int), cudaMemcpyDeviceToHost, s));
+  RR_CUDA(cudaStreamSynchronize(s));
+  return h ? RR_ERR_NAN : RR_OK;
 }
 
 static int count_converged(const double* res, int k, double tol, double* maxres) {
@@ -480,14 +552,17 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
   carve_op(ar, op, false, refine, b);
   SvdBufs w;
   carve_svd(ar, op, b, refine, w);
-  double* v0buf = batch_mode ? ar.take<double>(n * b) : nullptr;
+  double* v0buf = (batch_mode || !p->v0) ? ar.take<double>(n * b) : nullptr;
   if (ar.overflow) return RR_ERR_WORKSPACE;
   Prof prof;
   prof.on = p->profile != 0 && !batch_mode;
   prof.s = s;
+  prof.start();
   w.c.hess_grid = hess_grid;
+  w.c.hess_tol = p->hess_tol;
   RR_CUDA(cudaMemsetAsync(w.c.hess_ws, 0, 512, s));
   RR_CUDA(cudaMemsetAsync(w.frozen, 0, sizeof(int), s));
+  if (!batch_mode) STAGE(RR_STAGE_OTHER, check_operator_finite(Aop, w.c, s));
   const size_t ds = dsz(dt);
   (void)ds;
 
@@ -497,8 +572,8 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
 
   // a1: start block
   const double* v0 = p->v0;
-  if (batch_mode) {
-    STAGE(RR_STAGE_OTHER, uniform_block(s, n, b, seed, v0buf, n));
+  if (batch_mode || !v0) {
+    STAGE(RR_STAGE_OTHER, uniform_block(s, n, b, batch_mode ? seed : p->seed, v0buf, n));
     v0 = v0buf;
   }
   STAGE(RR_STAGE_OTHER, rr_colscale_cast(n, b, v0, n, dt1, w.Vlo, n, w.c.scale, s));
@@ -506,8 +581,9 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
   rr_info inf;
   memset(&inf, 0, sizeof(inf));
   std::vector<double> hres(b);
+  double hcond[4] = {0.0, 0.0, 0.0, 0.0};
   int sweep = 0;
-  bool converged = false;
+  bool converged = false, nan_seen = false;
 
   // ---------------- phase 1: the paper's method ----------------
   for (int ps = 0; ps < ph1 && sweep < p->max_sweeps; ++ps) {
@@ -523,8 +599,7 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
     STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, dt1, w.Ulo, m, dt1, w.Ulo, m, w.Gu, b, s));
     STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, dt1, w.Vlo, n, dt1, w.Vlo, n, w.Gv, b, s));
     STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, dt1, w.Ulo, m, op.wt, w.Pw, m, w.Bm, b, s));
-    STAGE(RR_STAGE_PENCIL, rr_pencil_svd(b, b, w.Bm, w.Gu, w.Gv, w.sig2, w.Ys, w.Zs, w.c.pen_ws, w.c.pen_bytes,
-                         nullptr, s));
+    STAGE(RR_STAGE_PENCIL, pencil_svd(w.c, b, b, w.Bm, w.Gu, w.Gv, w.sig2, w.Ys, w.Zs, s));
     STAGE(RR_STAGE_LIFT, lift2(op, s, m, b, dt1, w.Ulo, m, b, 0, nullptr, 0, 0, w.Ys, b, w.Ut, m));
     STAGE(RR_STAGE_LIFT, lift2(op, s, n, b, dt1, w.Vlo, n, b, 0, nullptr, 0, 0, w.Zs, b, w.Vt, n));
     RR_CUDA(cudaMemcpyAsync(w.sig, w.sig2, b * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -533,12 +608,18 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
       // plain method: FP64 residual check of the wanted triplets every sweep
       STAGE(RR_STAGE_F64_PRODUCT, svd_residual(op, w, k, w.Rv ? w.Rv : w.P, w.Ru ? w.Ru : w.Qm, s));
       RR_CUDA(cudaMemcpyAsync(hres.data(), w.res, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+      RR_TRY(queue_cond(w.c, s, hcond));
       RR_CUDA(cudaStreamSynchronize(s));
       RR_TRY(read_err(w.c, s));
       double mx;
       inf.n_converged = count_converged(hres.data(), (int)k, p->tol, &mx);
       inf.max_res = mx;
       if (sweep <= 64) inf.res_history[sweep - 1] = mx;
+      note_cond(inf, sweep, hcond);
+      if (all_nan(hres.data(), (int)k)) {
+        nan_seen = true;
+        break;
+      }
       if (inf.n_converged == k) {
         converged = true;
         break;
@@ -547,7 +628,7 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
   }
 
   // ---------------- phase 2: refinement ----------------
-  if (refine) {
+  if (refine && !nan_seen) {
     const int64_t b2 = 2 * b;
     for (;;) {
       // residual of all b Ritz triplets, FP64-accurate
@@ -559,12 +640,18 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
       if (batch_mode) STAGE(RR_STAGE_OTHER, freeze_update(s, k, w.res, p->tol, w.frozen));
       if (!batch_mode) {
         RR_CUDA(cudaMemcpyAsync(hres.data(), w.res, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+        RR_TRY(queue_cond(w.c, s, hcond));
         RR_CUDA(cudaStreamSynchronize(s));
         RR_TRY(read_err(w.c, s));
         double mx;
         inf.n_converged = count_converged(hres.data(), (int)k, p->tol, &mx);
         inf.max_res = mx;
         if (sweep >= 1 && sweep <= 64) inf.res_history[sweep - 1] = mx;
+        note_cond(inf, sweep, hcond);
+        if (all_nan(hres.data(), (int)k)) {
+          nan_seen = true;
+          break;
+        }
         if (inf.n_converged == k) {
           converged = true;
           break;
@@ -622,8 +709,7 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
       STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, RR_F64, w.Vt, n, et, Fg, n, w.Gv + b * b2, b2, s));
       STAGE(RR_STAGE_OTHER, transpose(s, b, b, w.Gv + b * b2, b2, w.Gv + b, b2));
       STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, et, Fg, n, et, Fg, n, w.Gv + b + b * b2, b2, s));
-      STAGE(RR_STAGE_PENCIL, rr_pencil_svd(b2, b2, B, w.Gu, w.Gv, w.sig2, w.Ys, w.Zs, w.c.pen_ws, w.c.pen_bytes,
-                           nullptr, s));
+      STAGE(RR_STAGE_PENCIL, pencil_svd(w.c, b2, b2, B, w.Gu, w.Gv, w.sig2, w.Ys, w.Zs, s));
       // lift the leading b triplets
       STAGE(RR_STAGE_LIFT, lift2(op, s, m, b, RR_F64, w.Ut, m, b, et, Eg, m, b, w.Ys, b2, w.Ut2, m));
       STAGE(RR_STAGE_LIFT, lift2(op, s, n, b, RR_F64, w.Vt, n, b, et, Fg, n, b, w.Zs, b2, w.Vt2, n));
@@ -657,6 +743,7 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
   if (info) *info = inf;
   RR_CUDA(cudaStreamSynchronize(s));
   RR_TRY(read_err(w.c, s));
+  if (nan_seen) return RR_ERR_NAN;
   return converged ? RR_OK : RR_ERR_NO_CONV;
 }
 
@@ -668,7 +755,7 @@ static size_t svd_ws(const rr_operator* A, const rr_params* p, bool batch) {
   carve_op(ar, op, false, refine, p->block);
   SvdBufs w;
   carve_svd(ar, op, p->block, refine, w);
-  if (batch) ar.take<double>(op.n * p->block);
+  if (batch || !p->v0) ar.take<double>(op.n * p->block);
   return ar.off + 4096;
 }
 
@@ -776,11 +863,15 @@ static rr_status eig_run(const rr_operator* Aop, const rr_params* p, double* the
   carve_op(ar, op, true, refine, b);
   EigBufs w;
   carve_eig(ar, op, b, refine, w);
+  double* v0buf = p->v0 ? nullptr : ar.take<double>(n * b);
   if (ar.overflow) return RR_ERR_WORKSPACE;
   Prof prof;
   prof.on = p->profile != 0;
   prof.s = s;
+  prof.start();
+  w.c.hess_tol = p->hess_tol;
   RR_CUDA(cudaMemsetAsync(w.c.hess_ws, 0, 512, s));
+  STAGE(RR_STAGE_OTHER, check_operator_finite(Aop, w.c, s));
   STAGE(RR_STAGE_OTHER, prepare_op(op, op, true, s));
 
   double lo = p->bounds[0], up = p->bounds[1];
@@ -794,12 +885,18 @@ static rr_status eig_run(const rr_operator* Aop, const rr_params* p, double* the
   }
   double ca = lo + 0.1 * (up - lo), ca0 = lo;  // Chebyshev cut and scaling point
 
-  STAGE(RR_STAGE_OTHER, rr_colscale_cast(n, b, p->v0, n, dt, w.Vlo, n, w.c.scale, s));
+  const double* v0 = p->v0;
+  if (!v0) {
+    STAGE(RR_STAGE_OTHER, uniform_block(s, n, b, p->seed, v0buf, n));
+    v0 = v0buf;
+  }
+  STAGE(RR_STAGE_OTHER, rr_colscale_cast(n, b, v0, n, dt, w.Vlo, n, w.c.scale, s));
   rr_info inf;
   memset(&inf, 0, sizeof(inf));
   std::vector<double> hres(b), hth(b);
+  double hcond[4] = {0.0, 0.0, 0.0, 0.0};
   int sweep = 0;
-  bool converged = false;
+  bool converged = false, nan_seen = false;
 
   auto update_bounds = [&]() -> rr_status {
     if (!cheb) return RR_OK;
@@ -834,7 +931,7 @@ static rr_status eig_run(const rr_operator* Aop, const rr_params* p, double* the
     STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp(op, b, w.Vlo, n, w.Pw, n, nullptr, 0, nullptr, s));
     STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, dt, w.Vlo, n, dt, w.Vlo, n, w.G, b, s));
     STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, dt, w.Vlo, n, op.wt, w.Pw, n, w.H, b, s));
-    STAGE(RR_STAGE_PENCIL, rr_pencil_eig(b, w.H, w.G, w.th2, w.Y, w.c.pen_ws, w.c.pen_bytes, nullptr, s));
+    STAGE(RR_STAGE_PENCIL, pencil_eig(w.c, b, w.H, w.G, w.th2, w.Y, s));
     STAGE(RR_STAGE_PENCIL, select_eig(s, b, b, p->which, w.th2, w.Y, b, w.theta, w.Ysel, b));
     STAGE(RR_STAGE_LIFT, lift2(op, s, n, b, dt, w.Vlo, n, b, 0, nullptr, 0, 0, w.Ysel, b, w.X, n));
     ++sweep;
@@ -846,12 +943,18 @@ static rr_status eig_run(const rr_operator* Aop, const rr_params* p, double* the
       STAGE(RR_STAGE_OTHER, residual_block(s, n, k, w.P, n, w.X, n, w.theta, w.R, n, w.ss, 0));
       STAGE(RR_STAGE_OTHER, res_finish(s, k, w.ss, w.theta, w.res));
       RR_CUDA(cudaMemcpyAsync(hres.data(), w.res, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+      RR_TRY(queue_cond(w.c, s, hcond));
       RR_CUDA(cudaStreamSynchronize(s));
       RR_TRY(read_err(w.c, s));
       double mx;
       inf.n_converged = count_converged(hres.data(), (int)k, p->tol, &mx);
       inf.max_res = mx;
       if (sweep <= 64) inf.res_history[sweep - 1] = mx;
+      note_cond(inf, sweep, hcond);
+      if (all_nan(hres.data(), (int)k)) {
+        nan_seen = true;
+        break;
+      }
       if (inf.n_converged == k) {
         converged = true;
         break;
@@ -860,19 +963,25 @@ static rr_status eig_run(const rr_operator* Aop, const rr_params* p, double* the
   }
 
   // ---------------- phase 2 ----------------
-  if (refine) {
+  if (refine && !nan_seen) {
     const int64_t b2 = 2 * b;
     for (;;) {
       STAGE(RR_STAGE_F64_PRODUCT, apply_f64(op, b, w.X, n, w.P, n, s));  // P = A X, FP64-accurate
       STAGE(RR_STAGE_OTHER, residual_block(s, n, b, w.P, n, w.X, n, w.theta, w.R, n, w.ss, 0));
       STAGE(RR_STAGE_OTHER, res_finish(s, b, w.ss, w.theta, w.res));
       RR_CUDA(cudaMemcpyAsync(hres.data(), w.res, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+      RR_TRY(queue_cond(w.c, s, hcond));
       RR_CUDA(cudaStreamSynchronize(s));
       RR_TRY(read_err(w.c, s));
       double mx;
       inf.n_converged = count_converged(hres.data(), (int)k, p->tol, &mx);
       inf.max_res = mx;
       if (sweep >= 1 && sweep <= 64) inf.res_history[sweep - 1] = mx;
+      note_cond(inf, sweep, hcond);
+      if (all_nan(hres.data(), (int)k)) {
+        nan_seen = true;
+        break;
+      }
       if (inf.n_converged == k) {
         converged = true;
         break;
@@ -940,7 +1049,7 @@ static rr_status eig_run(const rr_operator* Aop, const rr_params* p, double* the
       STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, RR_F64, w.P, n, dt, w.Dlo, n, w.H + b * b2, b2, s));
       STAGE(RR_STAGE_OTHER, transpose(s, b, b, w.H + b * b2, b2, w.H + b, b2));
       STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, dt, w.Dlo, n, op.wt, w.AD, n, w.H + b + b * b2, b2, s));
-      STAGE(RR_STAGE_PENCIL, rr_pencil_eig(b2, w.H, w.G, w.th2, w.Y, w.c.pen_ws, w.c.pen_bytes, nullptr, s));
+      STAGE(RR_STAGE_PENCIL, pencil_eig(w.c, b2, w.H, w.G, w.th2, w.Y, s));
       STAGE(RR_STAGE_PENCIL, select_eig(s, b2, b, p->which, w.th2, w.Y, b2, w.theta, w.Ysel, b2));
       STAGE(RR_STAGE_LIFT, lift2(op, s, n, b, RR_F64, w.X, n, b, dt, w.Dlo, n, b, w.Ysel, b2, w.X2, n));
       std::swap(w.X, w.X2);
@@ -959,6 +1068,7 @@ static rr_status eig_run(const rr_operator* Aop, const rr_params* p, double* the
   inf.sweeps = sweep;
   prof.finish(&inf);
   if (info) *info = inf;
+  if (nan_seen) return RR_ERR_NAN;
   return converged ? RR_OK : RR_ERR_NO_CONV;
 }
 
@@ -970,6 +1080,7 @@ static size_t eig_ws(const rr_operator* A, const rr_params* p) {
   carve_op(ar, op, true, refine, p->block);
   EigBufs w;
   carve_eig(ar, op, p->block, refine, w);
+  if (!p->v0) ar.take<double>(op.n * p->block);
   return ar.off + 4096;
 }
 
@@ -1003,7 +1114,7 @@ extern "C" rr_status rr_eig(const rr_operator* A, const rr_params* p, double* th
   RR_TRY(check_op(A, false));
   RR_TRY(check_params(p, A->n));
   if (p->basis == RR_E4M3) return RR_ERR_ARG;
-  if (!theta || !X || !p->v0) return RR_ERR_ARG;
+  if (!theta || !X) return RR_ERR_ARG;
   if (!ws || ws_bytes < eig_ws(A, p) || ((uintptr_t)ws & 255)) return RR_ERR_WORKSPACE;
   return eig_run(A, p, theta, X, ws, ws_bytes, info, as_stream(stream));
 }
@@ -1012,7 +1123,7 @@ extern "C" rr_status rr_svd(const rr_operator* A, const rr_params* p, double* si
                             double* V, void* ws, size_t ws_bytes, rr_info* info, void* stream) {
   RR_TRY(check_op(A, true));
   RR_TRY(check_params(p, A->n));
-  if (!sigma || !U || !V || !p->v0) return RR_ERR_ARG;
+  if (!sigma || !U || !V) return RR_ERR_ARG;
   if (!ws || ws_bytes < svd_ws(A, p, false) || ((uintptr_t)ws & 255)) return RR_ERR_WORKSPACE;
   return svd_run(A, p, sigma, U, V, ws, ws_bytes, info, as_stream(stream), false, 0, 0);
 }

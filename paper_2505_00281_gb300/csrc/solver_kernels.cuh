@@ -1,5 +1,6 @@
 // Internal launchers shared between the kernel files and the host solver.
 #pragma once
+#include <vector>
 #include "rr_common.cuh"
 
 namespace rr {
@@ -27,16 +28,30 @@ rr_status fill(cudaStream_t s, int64_t n, double v, double* d);
 rr_status freeze_update(cudaStream_t s, int64_t k, const double* res, double tol, int* frozen);
 rr_status keep_frozen(cudaStream_t s, const int* frozen, int64_t m, int64_t n, int64_t b, const double* U, double* U2,
                       const double* V, double* V2, const double* sig, double* sig2);
+rr_status operator_nonfinite(cudaStream_t s, int kind, int64_t m, int64_t n, const void* values, int64_t lda,
+                             int64_t nnz, int* flag);
 rr_status uniform_block(cudaStream_t s, int64_t n, int64_t b, uint64_t seed, double* V, int64_t ldv);
 rr_status cheb_coef_update(cudaStream_t s, int64_t b, const double* theta, const double* mu,
                            double alpha_next, double cshift, double beta_next, double* kappa,
                            double* kappa_prev, double* rho);
+const double* pencil_cond_slot(void* ws, size_t ws_bytes, int b1, int b2);
 void small_gemm(cudaStream_t s, int ta, int tb, int M, int N, int K, double alpha, const double* A,
                 int lda, const double* B, int ldb, double beta, double* C, int ldc);
 rr_status fill_f32(cudaStream_t s, int64_t n, float v, float* d);
 // Upper bound on the K splits of the plain / split tensor-core products
 // (0: none) while an instance is alive on this thread; the batched solver
 // sets it around its graph capture.
+// Kernel-level timing of the tensor-core product kernel (k_gemm_bf16_tc in
+// every role: filter products, split corrections, FP64 emulation passes,
+// E4M3 products): while a TcProf is attached to the calling thread, each
+// launch is bracketed by CUDA events on its stream and its algorithmic bytes
+// (each operand read once, the output written once) are added up.
+struct TcProf {
+  std::vector<cudaEvent_t> ev;  // start / end per launch
+  double bytes = 0.0;
+  int launches = 0;
+};
+void tc_prof_attach(TcProf* p);  // nullptr detaches
 int& gemm_split_cap();
 struct GemmSplitCap {
   int prev;

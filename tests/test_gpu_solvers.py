@@ -225,3 +225,58 @@ def test_batch_problems_keep_converged_triplets(rr):
         Ah = host(A)
         Amul, Atmul = O.dense_apply(Ah)
         assert O.residual_svd(Amul, Atmul, host(U), host(V), host(s)).max() <= 1.5e-10
+
+
+def test_svd_seeded_start_block_and_info(rr):
+    """v0 = NULL draws the start block on the device from params.seed (Alg. 1's
+    U(0,1) block): the same seed reproduces the solve bit for bit, another seed
+    reaches the same triplets by another path.  rr_info's Gram condition
+    estimate is at least 1 (G_ii (G^-1)_ii >= 1 for any SPD G) and finite."""
+    m, n, b, k = 2048, 512, 32, 16
+    sig = wl.config2_sigma(n)
+    Ad = dev(wl.dense_svd(m, n, sig, 2000))
+    outs = []
+    for seed in (7, 7, 8):
+        p = rr.api.make_params(k, b, 4, 30, 1e-10, basis="bf16", v0=None, refine=True, phase1_sweeps=1,
+                               seed=seed)
+        s, U, V, info = rr.rr_svd(rr.api.dense_operator(Ad), p)
+        assert info["n_converged"] == k, info
+        assert np.max(np.abs(host(s) - sig[:k]) / sig[:k]) <= 1e-10
+        assert len(info["cond_history"]) == info["sweeps"]
+        assert all(1.0 <= c < 1e16 for c in info["cond_history"]), info["cond_history"]
+        assert info["cond_G_est"] == info["cond_history"][-1]
+        outs.append((host(s), info["res_history"]))
+    assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1] == outs[1][1]
+    assert outs[0][1] != outs[2][1]
+
+
+def test_svd_nan_operator_reports_nan(rr):
+    """A NaN in the operator makes every residual NaN: the solver stops with
+    RR_ERR_NAN instead of running to max_sweeps."""
+    from paper_2505_00281_gb300._lib import RR, RrError
+    m, n, b, k = 512, 128, 16, 4
+    A = wl.dense_svd(m, n, wl.config2_sigma(n), 2200)
+    A[17, 3] = np.nan
+    for basis, refine in (("bf16", True), ("f64", False)):
+        p = rr.api.make_params(k, b, 2, 10, 1e-10, basis=basis, v0=dev(wl.uniform_block(n, b, 2201)),
+                               refine=refine)
+        with pytest.raises(RrError) as e:
+            rr.rr_svd(rr.api.dense_operator(dev(A)), p)
+        assert e.value.status == RR.ERR_NAN
+
+
+def test_eig_hess_tol_is_used(rr):
+    """params.hess_tol reaches Algorithm 8: the default value given explicitly
+    changes nothing bit for bit; a skip tolerance of 0.9 (a column is skipped
+    unless elimination left its pivot within 10 % of its entry inf-norm)
+    changes the iteration."""
+    n, k, b = 600, 8, 16
+    A, lam = wl.config1(n)
+    Ad, V0 = dev(A), dev(wl.uniform_block(n, b, 1001))
+    runs = []
+    for tol in (0.0, 4 * b * 2.0 ** -23, 0.9):
+        p = rr.api.make_params(k, b, 2, 8, 1e-30, basis="f32", v0=V0, refine=False, hess_tol=tol)
+        th, X, info = rr.rr_eig(rr.api.dense_operator(Ad), p, n)
+        runs.append((host(th), info["res_history"], info["cols_dropped"]))
+    assert np.array_equal(runs[0][0], runs[1][0]) and runs[0][1] == runs[1][1]
+    assert runs[2][1] != runs[0][1]

@@ -230,8 +230,13 @@ def test_gemm_lowp_split_two_term_accuracy(rr, M, N, K):
 
 
 # ---------------------------------------------------------------- a4 (Algorithm 8)
-@pytest.mark.parametrize("n,k", [(1000, 48), (20000, 32), (77, 77), (5, 3)])
+@pytest.mark.parametrize("n,k", [(1000, 48), (20000, 32), (77, 77), (5, 3),
+                                 (16384, 128), (4096, 128), (65536, 160)])
 def test_hessenberg_bitexact_fp32(rr, n, k):
+    """Pivots and basis bit for bit against the oracle's FP32 process, up to
+    the shapes the solvers run: 16384 x 128 (the dense SVD's A V blocks, a
+    cooperative grid), 4096 x 128 (its A^T U blocks, one thread-block cluster)
+    and 65536 x 160 (a tall block of the sparse workload's width)."""
     W = np.random.default_rng(n + k).standard_normal((n, k)).astype(np.float32)
     Qo, pivo, keepo, Qfo = O.hessenberg(W, arith="f32")
     Wd = dev(W.astype(np.float64), torch.float32)
@@ -357,6 +362,65 @@ def test_pencil_svd_matches_block_pencil(rr, b1, b2):
     r = min(b1, b2)
     assert np.abs(Ut.T @ Ut - np.eye(r)).max() < 1e-8
     assert np.abs(Vt.T @ Vt - np.eye(r)).max() < 1e-8
+
+
+@pytest.mark.parametrize("rows", [(600, 500)])
+def test_pencil_svd_2b256_random(rr, rows):
+    """The dense SVD's refinement pencil size, 2b = 256 on both sides (the
+    8-CTA cluster Jacobi and the QR preconditioner on 8 CTAs), against the
+    oracle's literal 2x2 block pencil of Algorithm 5 on a random
+    non-orthogonal basis."""
+    rng = np.random.default_rng(256)
+    m, n = rows
+    A = rng.standard_normal((m, n))
+    U = rng.uniform(0, 1, (m, 256))
+    V = rng.uniform(0, 1, (n, 256))
+    B, Gu, Gv = U.T @ A @ V, U.T @ U, V.T @ V
+    s, Y, Z, dropped = rr.rr_pencil_svd(dev(B), dev(Gu), dev(Gv))
+    so, Yo, Zo = O.pencil_svd(B, Gu, Gv)
+    s, Yh, Zh = host(s), host(Y), host(Z)
+    assert dropped == 0
+    assert np.allclose(s, so, rtol=1e-9, atol=1e-12 * so[0])
+    assert np.abs(Yh.T @ Gu @ Yh - np.eye(256)).max() < 1e-8
+    assert np.abs(Zh.T @ Gv @ Zh - np.eye(256)).max() < 1e-8
+    assert np.abs(Yh.T @ B @ Zh - np.diag(s)).max() < 1e-8 * s[0]
+
+
+def test_pencil_svd_2b256_refinement_pencil(rr):
+    """The pencil the dense SVD's refinement solves (2b = 256): S_u = [U~, E],
+    S_v = [V~, F] with U~, V~ orthonormal near-singular vectors of A
+    (perturbed by 1e-6) and E, F correction blocks at the noise level, so half
+    of the 2b singular values sit at the noise floor.  The leading b values
+    against the oracle's literal block pencil to 1e-12 of sigma_1 and the
+    pencil's defining identities (Y^T Gu Y = I, Z^T Gv Z = I,
+    Y^T B Z = diag(s)) to 1e-11."""
+    rng = np.random.default_rng(2256)
+    m, n, b = 1024, 512, 128
+    sig = wl.config2_sigma(n)
+    Uh, Vh = wl.haar(m, n, 1), wl.haar(n, n, 2)
+    A = (Uh * sig) @ Vh.T
+    Ut, _ = np.linalg.qr(Uh[:, :b] + 1e-6 * rng.standard_normal((m, b)))
+    Vt, _ = np.linalg.qr(Vh[:, :b] + 1e-6 * rng.standard_normal((n, b)))
+    R_v = A @ Vt - Ut * np.sum(Ut * (A @ Vt), axis=0)
+    E = R_v + 1e-3 * np.abs(R_v).max() * rng.standard_normal((m, b))
+    F = A.T @ E
+    F = F - Vt @ (Vt.T @ F)
+    E = E / np.abs(E).max(axis=0)
+    F = F / np.abs(F).max(axis=0)
+    Su, Sv = np.hstack([Ut, E]), np.hstack([Vt, F])
+    B, Gu, Gv = Su.T @ A @ Sv, Su.T @ Su, Sv.T @ Sv
+    s, Y, Z, dropped = rr.rr_pencil_svd(dev(B), dev(Gu), dev(Gv))
+    so, Yo, Zo = O.pencil_svd(B, Gu, Gv)
+    s, Yh, Zh = host(s), host(Y), host(Z)
+    kept = 2 * b - dropped
+    assert kept >= b
+    assert np.abs(s[:b] - so[:b]).max() <= 1e-12 * so[0]
+    assert np.abs(s[:b] - sig[:b]).max() <= 1e-9 * sig[0]
+    eu = np.abs(Yh[:, :b].T @ Gu @ Yh[:, :b] - np.eye(b)).max()
+    ev = np.abs(Zh[:, :b].T @ Gv @ Zh[:, :b] - np.eye(b)).max()
+    eb = np.abs(Yh[:, :b].T @ B @ Zh[:, :b] - np.diag(s[:b])).max() / s[0]
+    print("refinement pencil 2b = 256: orthonormality", eu, ev, "Galerkin", eb)
+    assert max(eu, ev, eb) < 1e-11
 
 
 def _clustered_spectrum(rng, b):

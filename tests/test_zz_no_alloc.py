@@ -48,6 +48,32 @@ def test_gram_noalloc_matches_gram_twice(rr):
         assert np.all(np.abs(b - X.T @ Y) <= 2 * bound), call
 
 
+def test_gram_noalloc_largest_size_and_accumulate(rr):
+    """The largest accepted product (p q = 262144: the whole array holds one
+    chunk, so the partial kernel covers all n rows at once) and the
+    accumulating form (G += X^T Y on a nonzero G), both against rr_gram."""
+    rng = np.random.default_rng(3)
+    n, p, q = 3000, 512, 512
+    X, Y = rng.standard_normal((n, p)), rng.standard_normal((n, q))
+    Xd, Yd = _dev(rr, X), _dev(rr, Y)
+    G_ws = rr.rr_gram(Xd, Yd)
+    G_na = rr.rr_gram_noalloc(Xd, Yd)
+    torch.cuda.synchronize()
+    bound = 2 * n * U53 * (np.abs(X).T @ np.abs(Y))
+    assert np.all(np.abs(G_ws.cpu().numpy() - G_na.cpu().numpy()) <= 2 * bound)
+    n, p, q = 5000, 40, 24
+    X, Y = rng.standard_normal((n, p)), rng.standard_normal((n, q))
+    G0 = rng.standard_normal((p, q))
+    Xd, Yd = _dev(rr, X), _dev(rr, Y)
+    Ga, Gb = _dev(rr, G0), _dev(rr, G0)
+    rr.rr_gram(Xd, Yd, G=Ga, accumulate=True)
+    rr.rr_gram_noalloc(Xd, Yd, G=Gb, accumulate=True)
+    torch.cuda.synchronize()
+    bound = 2 * n * U53 * (np.abs(X).T @ np.abs(Y)) + 2 * U53 * np.abs(G0)
+    assert np.all(np.abs(Ga.cpu().numpy() - Gb.cpu().numpy()) <= 2 * bound)
+    assert np.all(np.abs(Gb.cpu().numpy() - (G0 + X.T @ Y)) <= 2 * bound)
+
+
 def test_gram_noalloc_rejects_sizes_beyond_its_scratch(rr):
     from paper_2505_00281_gb300._lib import RR, RrError
 
