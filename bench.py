@@ -688,15 +688,15 @@ def run_stage(args):
         mats = [wl.dense_svd_torch(m, n, wl.config4_sigma(n), 4000 + i) for i, (m, n) in enumerate(shapes)]
         ops = [rr.api.dense_operator(t.t()) for t in mats]
         params = rr.api.make_params(16, 32, 4, args.batch_sweeps, 1e-10, basis="bf16", refine=True,
-                                    phase1_sweeps=1)
+                                    phase1_sweeps=1, refine_degree=args.refine_degree)
         by_class = {}
         for op_ in ops:
             by_class.setdefault(AT.size_class(op_.m, op_.n), []).append(op_)
         samples = {k: v[:8] for k, v in by_class.items()}
         cands = [{"branches": b_, "max_splits": c_, "order": 1} for b_ in (8, 32) for c_ in (0, 1, 4)]
         t0 = time.perf_counter()
-        table = AT.tune(samples, params, candidates=cands, reps=1)
-        t_tune = time.perf_counter() - t0
+        table = AT.tune(samples, params, candidates=cands, reps=1) if args.tune else AT.load()
+        t_tune = time.perf_counter() - t0 if args.tune else 0.0
         if args.table:
             AT.save(table, args.table)
 
@@ -718,6 +718,9 @@ def run_stage(args):
                     out[key] = out.get(key, 0) + 1
             return out
         print(json.dumps({"stage": "batch", "count": len(ops), "sweeps": args.batch_sweeps,
+                          "refine_degree": args.refine_degree,
+                          "converged_problems": {"default": sum(1 for x in st_def if x == 0),
+                                                 "tuned": sum(1 for x in st_tuned if x == 0)},
                           "classes": {k: len(v) for k, v in by_class.items()}, "tune_seconds": t_tune,
                           "default": {"seconds": t_def, "problems_per_s": len(ops) / t_def,
                                       "pairs_per_s": conv(inf_def) / t_def, "failed_by_class": failures(st_def),
@@ -767,8 +770,11 @@ def main():
     ap.add_argument("--grid", type=int, default=64, help="grid side for --stage warm")
     ap.add_argument("--sweeps", type=int, default=60, help="sweep limit for --stage sparse")
     ap.add_argument("--count", type=int, default=512, help="problems for --stage batch")
-    ap.add_argument("--batch-sweeps", type=int, default=30, help="sweeps of every problem for --stage batch")
+    ap.add_argument("--batch-sweeps", type=int, default=12, help="sweeps of every problem for --stage batch")
     ap.add_argument("--table", default="", help="--stage batch: write the tuned table (JSON) here")
+    ap.add_argument("--tune", action="store_true", help="--stage batch: tune now instead of the shipped table")
+    ap.add_argument("--refine-degree", type=int, default=1,
+                    help="--stage batch: products per refinement sweep (0: the power degree)")
     ap.add_argument("--train", type=int, default=48, help="training solves for --stage warm")
     ap.add_argument("--test", type=int, default=8, help="held-out solves for --stage warm")
     ap.add_argument("--epochs", type=int, default=40, help="training epochs for --stage warm")

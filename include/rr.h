@@ -107,6 +107,8 @@ typedef struct {
                             epsilon)                                                 */
   uint64_t seed;         /* start block generator seed when v0 is NULL (counter-
                             based splitmix64 stream, the one rr_batch_svd uses)      */
+  int32_t refine_degree; /* SVD: products of the correction recurrence per
+                            refinement sweep (0: degree)                             */
 } rr_params;
 
 typedef struct {
@@ -126,6 +128,10 @@ typedef struct {
   double cond_history[64];/* cond_G_est after each projection                        */
   double tc_bytes;       /* with params.profile: algorithmic bytes of the launches
                             timed in stage_ms[RR_KERNEL_TC]                          */
+  int32_t polish_sweeps; /* SVD refinement sweeps run as the FP64 polish (the
+                            method's sweep in FP64-accurate arithmetic from the Ritz
+                            vectors, taken when the corrections stop contracting the
+                            residual, and as a batched problem's last sweep)         */
 } rr_info;
 
 /* Stages of rr_info.stage_ms: */
@@ -324,6 +330,25 @@ size_t rr_hessenberg_workspace_size(int64_t n, int64_t k, int32_t arith);
 rr_status rr_hessenberg(int32_t arith, int64_t n, int64_t k, void* W, int64_t ldw,
                         int32_t qtype, void* Q, int64_t ldq, int32_t* piv, double tol,
                         void* ws, size_t ws_bytes, void* stream);
+
+/* Blocked (level-3) form of the same process (the panel form of Algorithm 8
+ * that Table 1's "Block" row and the closing future-work passage of Sec. 4.2
+ * point to), FP32 arithmetic: columns in panels of `panel` (1..32); each
+ * panel is factored by the right-looking process on its columns only (skip
+ * thresholds from the column inf-norms on entry to the whole process), then
+ * the trailing columns take the panel at once: weights by forward
+ * substitution with the panel's unit lower triangle at its pivot rows, then
+ * T -= L_panel W.  Every entry sees the same separately rounded operations in
+ * the same order as in rr_hessenberg, so W, Q and piv equal its results bit
+ * for bit; the trailing columns are streamed once per panel instead of once
+ * per column.  rr_hessenberg takes this path by itself (panel 16) when a
+ * CTA's share of rows of all k columns does not fit its shared memory.
+ * W: n x k FP32 (ld ldw, overwritten); Q: qtype RR_F32, RR_BF16 or RR_F64;
+ * n < 2^24.  Workspace: rr_hessenberg_workspace_size(n, k, RR_F32).
+ * RR_ERR_ARG: bad sizes, panel out of range, null pointers. */
+rr_status rr_hessenberg_blocked(int64_t n, int64_t k, float* W, int64_t ldw, int32_t qtype, void* Q,
+                                int64_t ldq, int32_t* piv, double tol, int32_t panel, void* ws,
+                                size_t ws_bytes, void* stream);
 
 /* Projection products (Alg. 3: B = U^T A U, M = U^T U; Alg. 5: U^T A V,
  * U^T U, V^T V): G (p x q FP64, ld ldg) = X^T Y (+ G if accumulate) for tall

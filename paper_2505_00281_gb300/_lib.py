@@ -38,7 +38,7 @@ class RrParams(ctypes.Structure):
                 ("max_sweeps", c_i32), ("which", c_i32), ("basis", c_i32), ("hessenberg", c_i32),
                 ("refine", c_i32), ("phase1_sweeps", c_i32), ("tol", c_dbl),
                 ("bounds", c_dbl * 2), ("v0", c_vp), ("profile", c_i32), ("hess_tol", c_dbl),
-                ("seed", c_u64)]
+                ("seed", c_u64), ("refine_degree", c_i32)]
 
 
 class RrBatchTuning(ctypes.Structure):
@@ -49,7 +49,7 @@ class RrInfo(ctypes.Structure):
     _fields_ = [("n_converged", c_i32), ("sweeps", c_i32), ("refine_sweeps", c_i32),
                 ("cols_dropped", c_i32), ("max_res", c_dbl), ("res_history", c_dbl * 64),
                 ("stage_ms", c_dbl * 8), ("stage_calls", c_i32 * 8), ("cond_G_est", c_dbl),
-                ("cond_history", c_dbl * 64), ("tc_bytes", c_dbl)]
+                ("cond_history", c_dbl * 64), ("tc_bytes", c_dbl), ("polish_sweeps", c_i32)]
 
 
 _SIGS = {
@@ -89,6 +89,8 @@ _SIGS = {
     "rr_gram": (c_i32, [c_i64, c_i64, c_i64, c_i32, c_vp, c_i64, c_i32, c_vp, c_i64, c_vp, c_i64, c_i32,
                         c_vp, c_sz, c_vp]),
     "rr_wait_selftest": (c_i32, [c_i32, c_i64, c_vp, c_vp]),
+    "rr_hessenberg_blocked": (c_i32, [c_i64, c_i64, c_vp, c_i64, c_i32, c_vp, c_i64, c_vp, c_dbl, c_i32, c_vp,
+                                      c_sz, c_vp]),
     "rr_gram_noalloc": (c_i32, [c_i64, c_i64, c_i64, c_i32, c_vp, c_i64, c_i32, c_vp, c_i64, c_vp, c_i64,
                                 c_i32, c_vp]),
     "rr_pencil_workspace_size": (c_sz, [c_i64, c_i64]),

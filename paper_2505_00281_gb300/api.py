@@ -15,7 +15,7 @@ from ._lib import RR, RrBatchTuning, RrError, RrInfo, RrOperator, RrParams, chec
 __all__ = [
     "fortran", "ld_of", "dense_operator", "csr_operator", "make_params", "rr_eig", "rr_svd",
     "rr_batch_svd", "rr_colscale_cast", "rr_cast_operator", "rr_split_operator", "rr_lift", "rr_gemm_lowp", "rr_gemm_f64",
-    "rr_hessenberg", "rr_gram", "rr_gram_noalloc", "rr_pencil_eig", "rr_pencil_svd", "rr_csr_spmm",
+    "rr_hessenberg", "rr_hessenberg_blocked", "rr_wait_selftest", "rr_gram", "rr_gram_noalloc", "rr_pencil_eig", "rr_pencil_svd", "rr_csr_spmm",
     "rr_chebyshev_step", "rr_chebyshev_step_rows", "rr_quantize_e4m3", "rr_gemm_e4m3", "rr_conv3x3_forward", "rr_conv3x3_backward", "rr_relu_mask", "rr_procrustes_grad",
     "rr_adam", "rr_net_block", "RrParams", "RrOperator", "RrInfo", "DTYPES",
 ]
@@ -79,7 +79,7 @@ def csr_operator(row_ptr: torch.Tensor, col_idx: torch.Tensor, values: torch.Ten
 
 def make_params(k, block, degree, max_sweeps, tol, basis="bf16", v0=None, filter=RR.POWER,
                 which=RR.LARGEST, hessenberg=True, refine=True, phase1_sweeps=1, bounds=(0.0, 0.0),
-                profile=False, hess_tol=0.0, seed=0):
+                profile=False, hess_tol=0.0, seed=0, refine_degree=0):
     p = RrParams()
     p.k, p.block, p.filter, p.degree = k, block, filter, degree
     p.max_sweeps, p.which = max_sweeps, which
@@ -91,6 +91,7 @@ def make_params(k, block, degree, max_sweeps, tol, basis="bf16", v0=None, filter
     p.profile = int(profile)
     p.hess_tol = float(hess_tol)
     p.seed = int(seed)
+    p.refine_degree = int(refine_degree)
     p._keep = (v0,)
     return p
 
@@ -102,7 +103,7 @@ def _info_dict(info: RrInfo, status: int):
             "res_history": [info.res_history[i] for i in range(min(sweeps, 64))],
             "stage_ms": [info.stage_ms[i] for i in range(8)],
             "stage_calls": [info.stage_calls[i] for i in range(8)],
-            "cond_G_est": info.cond_G_est, "cols_dropped": info.cols_dropped, "tc_bytes": info.tc_bytes,
+            "cond_G_est": info.cond_G_est, "cols_dropped": info.cols_dropped, "tc_bytes": info.tc_bytes, "polish_sweeps": info.polish_sweeps,
             "cond_history": [info.cond_history[i] for i in range(min(sweeps, 64))]}
 
 
@@ -278,6 +279,20 @@ def rr_hessenberg(W, qtype=torch.bfloat16, tol=0.0, stream=None):
                                            _p(piv), tol, _p(ws), ws.numel(), _stream(stream)))
     err = ws[:4].view(torch.int32)
     return Q, piv, err
+
+
+def rr_hessenberg_blocked(W, panel, qtype=torch.bfloat16, tol=0.0, stream=None):
+    """Blocked Algorithm 8 on W (FP32, modified in place) in panels of `panel`
+    columns.  Returns (Q, piv, err)."""
+    n, k = W.shape
+    Q = empty_f(n, k, qtype, W.device)
+    piv = torch.empty(k, dtype=torch.int32, device=W.device)
+    L = lib()
+    ws = _ws(L.rr_hessenberg_workspace_size(n, k, RR.F32), W.device)
+    check("rr_hessenberg_blocked", L.rr_hessenberg_blocked(n, k, _p(W), ld_of(W), DTYPES[qtype], _p(Q), ld_of(Q),
+                                                           _p(piv), tol, int(panel), _p(ws), ws.numel(),
+                                                           _stream(stream)))
+    return Q, piv, ws[:4].view(torch.int32)
 
 
 def rr_gram(X, Y, G=None, accumulate=False, stream=None):

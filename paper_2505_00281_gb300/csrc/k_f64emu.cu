@@ -702,12 +702,41 @@ static void launch_lift_slices(cudaStream_t s, int64_t n, int p1, const T1* S1, 
   }
 }
 
+static rr_status lift_emu_one(cudaStream_t s, int64_t n, int64_t b, int32_t t1, const void* S1, int64_t ld1,
+                              int64_t p1, int32_t t2, const void* S2, int64_t ld2, int64_t p2, const double* Y,
+                              int64_t ldy, double* X, int64_t ldx, void* mem, size_t mem_bytes, bool* done,
+                              bool accumulate);
+
 // X (n x b FP64) = S1 (n x p1, type t1) Y(0:p1, :) + S2 (n x p2, type t2)
 // Y(p1:K, :); *done = false (nothing launched) when the shape is outside the
-// tensor-core path (the caller then lifts in FP64 arithmetic)
+// tensor-core path (the caller then lifts in FP64 arithmetic).  With both
+// blocks present (the refinement's [X, D] lifts, whose correction columns are
+// scaled to unit inf-norm while X's unit 2-norm columns have entries of
+// 1/sqrt(n)), each block is sliced with its own row exponents and the two
+// products add into X: one exponent per row across both would leave X's
+// entries only the bits below the correction block's, an error of
+// 2^-48 max|D(i,:)| per row instead of 2^-48 max|X(i,:)|.
 rr_status lift_emu(cudaStream_t s, int64_t n, int64_t b, int32_t t1, const void* S1, int64_t ld1, int64_t p1,
                    int32_t t2, const void* S2, int64_t ld2, int64_t p2, const double* Y, int64_t ldy, double* X,
                    int64_t ldx, void* mem, size_t mem_bytes, bool* done) {
+  *done = false;
+  if (S2 && p2 > 0 && p1 % 8 == 0 && p2 % 8 == 0 && p1 > 0) {
+    bool d1 = false, d2 = false;
+    RR_TRY(lift_emu_one(s, n, b, t1, S1, ld1, p1, t2, nullptr, 0, 0, Y, ldy, X, ldx, mem, mem_bytes, &d1, false));
+    if (!d1) return RR_OK;
+    RR_TRY(lift_emu_one(s, n, b, t2, S2, ld2, p2, t2, nullptr, 0, 0, Y + p1, ldy, X, ldx, mem, mem_bytes, &d2,
+                        true));
+    if (!d2) return RR_ERR_ARG;  // the second block fits whenever the first did (same n, b, K <= p1 + p2)
+    *done = true;
+    return RR_OK;
+  }
+  return lift_emu_one(s, n, b, t1, S1, ld1, p1, t2, S2, ld2, p2, Y, ldy, X, ldx, mem, mem_bytes, done, false);
+}
+
+static rr_status lift_emu_one(cudaStream_t s, int64_t n, int64_t b, int32_t t1, const void* S1, int64_t ld1,
+                              int64_t p1, int32_t t2, const void* S2, int64_t ld2, int64_t p2, const double* Y,
+                              int64_t ldy, double* X, int64_t ldx, void* mem, size_t mem_bytes, bool* done,
+                              bool accumulate) {
   constexpr int S = 8;
   *done = false;
   const int64_t K = p1 + (S2 ? p2 : 0);
@@ -734,8 +763,8 @@ rr_status lift_emu(cudaStream_t s, int64_t n, int64_t b, int32_t t1, const void*
   k_col_exp<<<(unsigned)b, 512, 0, s>>>(K, Y, ldy, yexp);
   k_slice_cols_rev<<<dim3((unsigned)((K + 255) / 256), (unsigned)b), 256, 0, s>>>(K, b, Y, ldy, yexp, Yrev);
   dim3 gz((unsigned)std::min<int64_t>((n + 255) / 256, 1024), (unsigned)b);
-  k_zero_f64<<<gz, 256, 0, s>>>(n, b, X, ldx);
-  note_launches(3);
+  if (!accumulate) k_zero_f64<<<gz, 256, 0, s>>>(n, b, X, ldx);
+  note_launches(accumulate ? 2 : 3);
   RR_TRY(check_launch("lift_emu slices"));
   for (int d = 2; d <= S + 1; ++d) {
     const uint32_t code = (uint32_t)(d - 2) | (1u << 16);  // p0 = d - 2, q0 = 0, nq = 1: scale 2^(-6d)

@@ -37,6 +37,8 @@ struct HessWs {
   int* flags;   // [G] column steps published by each CTA (j + 1 after column j)
   unsigned long long* cand;  // [2][G] packed candidates (FP32 path)
   int64_t rpc;               // rows per CTA (FP32 path; 0: ceil(n / G))
+  const T* colmax_ext;       // [k] column inf-norms on entry to the whole process
+                             // (the blocked process's panels), or null: computed here
 };
 
 // Publish/await the per-column candidates: CTA g releases flags[g] = step once
@@ -434,14 +436,14 @@ __global__ void __launch_bounds__(kHessThreads) k_hessenberg_f32(
     for (int c = tid; c < k; c += kHessThreads) {
       T m = T(0);
       for (int h = 0; h < G; ++h) m = fmax(m, cg::this_cluster().map_shared_rank(cmx, h)[c]);
-      thr[c] = rn_mul(tol, m);
+      thr[c] = rn_mul(tol, ws.colmax_ext ? ws.colmax_ext[c] : m);
     }
   } else {
     if (!grid_barrier(ws.bar, G, ws.err)) return;
     for (int c = tid; c < k; c += kHessThreads) {
       T m = T(0);
       for (int h = 0; h < G; ++h) m = fmax(m, ld_cg(ws.pcolmax + (size_t)h * k + c));
-      thr[c] = rn_mul(tol, m);
+      thr[c] = rn_mul(tol, ws.colmax_ext ? ws.colmax_ext[c] : m);
     }
   }
   __syncthreads();
@@ -784,7 +786,8 @@ static size_t hess_ws_bytes(int64_t k, int G) {
 
 template <typename T, typename TO>
 static rr_status hess_launch(int64_t n, int64_t k, T* W, int64_t ldw, TO* Q, int64_t ldq, int* piv,
-                             double tol, void* ws, size_t ws_bytes, cudaStream_t s, int max_grid) {
+                             double tol, void* ws, size_t ws_bytes, cudaStream_t s, int max_grid,
+                             const T* colmax_ext = nullptr, bool reset_err = true) {
   // FP32 arithmetic: the packed-candidate kernel (rows must fit its 24-bit field)
   const bool packed = sizeof(T) == 4 && n < (int64_t)kNoRow;
   const void* fn = packed ? (const void*)k_hessenberg_f32<TO, false> : (const void*)k_hessenberg<T, TO>;
@@ -862,7 +865,8 @@ static rr_status hess_launch(int64_t n, int64_t k, T* W, int64_t ldw, TO* Q, int
   h.flags = ar.take<int>(G);
   h.cand = ar.take<unsigned long long>(2 * (size_t)G);
   h.rpc = packed ? rpc : 0;
-  RR_CUDA(cudaMemsetAsync(ws, 0, 512, s));  // err + barrier
+  h.colmax_ext = packed ? colmax_ext : nullptr;
+  if (reset_err) RR_CUDA(cudaMemsetAsync(ws, 0, 512, s));  // err + barrier
   RR_CUDA(cudaMemsetAsync(h.flags, 0, (size_t)G * sizeof(int), s));
   RR_CUDA(cudaMemsetAsync(h.cand, 0, 2 * (size_t)G * sizeof(unsigned long long), s));
   T t = tol > 0 ? (T)tol : (T)(4.0 * (double)k * (sizeof(T) == 4 ? 0x1p-23 : 0x1p-52));
@@ -896,13 +900,163 @@ static rr_status hess_launch(int64_t n, int64_t k, T* W, int64_t ldw, TO* Q, int
   return RR_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Blocked (level-3) Hessenberg process for blocks too tall for the slab
+// kernel's shared memory (the panel form of Algorithm 8 that Table 1's "Block"
+// row and the closing future-work passage point to).  Columns go in panels of
+// r: the panel is factored by the right-looking kernel above on its r columns
+// only (thresholds from the column norms on entry to the whole process), then
+// the trailing columns T take the whole panel at once:
+//   weights  w_j(c) = T(pi_j, c) - sum_{i < j} L(pi_j, i) w_i(c)   (forward
+//            substitution with the panel's unit lower triangle at its pivot rows)
+//   update   T(:, c) <- T(:, c) - sum_j L(:, j) w_j(c)
+// Every entry sees the same operations in the same order as in the
+// right-looking process (the weights are exactly the pivot-row entries it
+// would read; each step a separately rounded multiply and subtract, j
+// ascending), so the blocked result equals it bit for bit, while the trailing
+// columns are streamed once per panel instead of once per column.
+// ---------------------------------------------------------------------------
+constexpr int kPanelMax = 32;
+
+// colmax[c] = max_i |W(i, c)| (non-negative floats order like their bits):
+// CTA (c, chunk) reduces 64K rows and merges with an atomic max
+__global__ void k_hess_colmax(int64_t n, int k, const float* __restrict__ W, int64_t ldw,
+                              unsigned* __restrict__ colmax_bits) {
+  const int c = blockIdx.x;
+  const int64_t i0 = (int64_t)blockIdx.y * 65536, i1 = i0 + 65536 < n ? i0 + 65536 : n;
+  float m = 0.f;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) m = fmaxf(m, fabsf(W[i + c * ldw]));
+  m = warp_max(m);
+  __shared__ float red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+    atomicMax(colmax_bits + c, __float_as_uint(m));
+  }
+}
+
+// weights of the panel (r columns at L, pivots piv[0..r)) for the nt trailing
+// columns T: w[j * nt + c]; a skipped panel column (pivot -1) has weight 0
+// and takes no part in the substitution.  One thread per trailing column.
+__global__ void k_hess_weights(int r, int nt, const float* __restrict__ L, const float* __restrict__ T,
+                               int64_t ldw, const int* __restrict__ piv, float* __restrict__ w) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nt) return;
+  float wr[kPanelMax];
+#pragma unroll
+  for (int j = 0; j < kPanelMax; ++j) {
+    if (j >= r) break;
+    const int pj = piv[j];
+    float v = 0.f;
+    if (pj >= 0) {
+      v = T[pj + (int64_t)c * ldw];
+#pragma unroll
+      for (int i = 0; i < kPanelMax; ++i) {
+        if (i >= j) break;
+        if (piv[i] >= 0) v = __fsub_rn(v, __fmul_rn(wr[i], L[pj + (int64_t)i * ldw]));
+      }
+    }
+    wr[j] = v;
+    w[(size_t)j * nt + c] = v;
+  }
+}
+
+// T(i, c) <- T(i, c) - sum_j L(i, j) w_j(c), j ascending, every row i; one
+// thread per row (grid-stride), the row's panel entries in registers, the
+// weights in shared memory; column-major T and L (consecutive threads,
+// consecutive rows)
+template <int R>
+__global__ void __launch_bounds__(256) k_hess_trail(int64_t n, int r, int nt, const float* __restrict__ L,
+                                                    float* __restrict__ T, int64_t ldw, const float* __restrict__ w,
+                                                    int wld, const int* __restrict__ piv) {
+  extern __shared__ float sw[];  // [r][nt]
+  __shared__ int keep[R];
+  for (int e = threadIdx.x; e < r * nt; e += blockDim.x) sw[e] = w[(e / nt) * (size_t)wld + e % nt];
+  if (threadIdx.x < R) keep[threadIdx.x] = (int)threadIdx.x < r && piv[threadIdx.x] >= 0;
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float l[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) l[j] = (j < r) ? L[i + (int64_t)j * ldw] : 0.f;
+    for (int c = 0; c < nt; ++c) {
+      float t = T[i + (int64_t)c * ldw];
+#pragma unroll
+      for (int j = 0; j < R; ++j)
+        if (keep[j]) t = __fsub_rn(t, __fmul_rn(sw[j * nt + c], l[j]));
+      T[i + (int64_t)c * ldw] = t;
+    }
+  }
+}
+
+// The extra workspace of the blocked process, after the kernel's own part:
+// column maxima (k) and panel weights (kPanelMax x k).
+static size_t hess_blocked_extra(int64_t k) {
+  return align_up((size_t)k * sizeof(float)) + align_up((size_t)kPanelMax * k * sizeof(float));
+}
+
+template <typename TO>
+static rr_status hess_blocked(int64_t n, int64_t k, float* W, int64_t ldw, TO* Q, int64_t ldq, int* piv,
+                              double tol, int r, void* ws, size_t ws_bytes, cudaStream_t s) {
+  if (r < 1 || r > kPanelMax) return RR_ERR_ARG;
+  const size_t base = hess_ws_bytes<float>(k, num_sms());
+  if (!ws || ws_bytes < base + hess_blocked_extra(k)) return RR_ERR_WORKSPACE;
+  float* colmax = (float*)((char*)ws + base);
+  float* wts = (float*)((char*)ws + base + align_up((size_t)k * sizeof(float)));
+  RR_CUDA(cudaMemsetAsync(colmax, 0, (size_t)k * sizeof(float), s));
+  k_hess_colmax<<<dim3((unsigned)k, (unsigned)((n + 65535) / 65536)), 256, 0, s>>>(n, (int)k, W, ldw,
+                                                                                 (unsigned*)colmax);
+  RR_TRY(check_launch("hessenberg colmax"));
+  // the default tolerance scales with the whole block's width, as the
+  // unblocked process's does
+  const double t = tol > 0 ? tol : 4.0 * (double)k * 0x1p-23;
+  for (int64_t c0 = 0; c0 < k; c0 += r) {
+    const int64_t c1 = c0 + r < k ? c0 + r : k;
+    const int pr = (int)(c1 - c0);
+    const rr_status st = hess_launch<float, TO>(n, pr, W + c0 * ldw, ldw, Q + c0 * ldq, ldq, piv + c0, t, ws, base,
+                                                s, 0, colmax + c0, c0 == 0);
+    if (st != RR_OK) return st;
+    if (c1 == k) break;
+    const int nt = (int)(k - c1);
+    k_hess_weights<<<(unsigned)((nt + 127) / 128), 128, 0, s>>>(pr, nt, W + c0 * ldw, W + c1 * ldw, ldw, piv + c0,
+                                                               wts);
+    RR_TRY(check_launch("hessenberg panel weights"));
+    // trailing columns in chunks whose weights fit 96 KB of shared memory
+    const int ncmax = (int)((96 * 1024) / ((size_t)pr * sizeof(float)));
+    const unsigned g = (unsigned)std::min<int64_t>((n + 255) / 256, 8 * (int64_t)num_sms());
+    for (int cc0 = 0; cc0 < nt; cc0 += ncmax) {
+      const int ntc = nt - cc0 < ncmax ? nt - cc0 : ncmax;
+      const size_t sm = (size_t)pr * ntc * sizeof(float);
+      float* Tc = W + (c1 + cc0) * ldw;
+      if (pr <= 16) {
+        if (sm > 48 * 1024) RR_CUDA(cudaFuncSetAttribute(k_hess_trail<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_hess_trail<16><<<g, 256, sm, s>>>(n, pr, ntc, W + c0 * ldw, Tc, ldw, wts + cc0, nt, piv + c0);
+      } else {
+        if (sm > 48 * 1024) RR_CUDA(cudaFuncSetAttribute(k_hess_trail<kPanelMax>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_hess_trail<kPanelMax><<<g, 256, sm, s>>>(n, pr, ntc, W + c0 * ldw, Tc, ldw, wts + cc0, nt, piv + c0);
+      }
+      RR_TRY(check_launch("hessenberg trailing update"));
+    }
+  }
+  return RR_OK;
+}
+
+// The blocked form replaces the slab kernel where a CTA's rows of all k
+// columns do not fit its shared memory (the kernel would stream the whole
+// trailing block once per column).
+static bool hess_use_blocked(int64_t n, int64_t k, int max_grid) {
+  if (max_grid == 1 || k <= 16 || n >= (int64_t)kNoRow) return false;
+  const int64_t rpc = (n + num_sms() - 1) / num_sms();
+  return (size_t)rpc * k * sizeof(float) > 200 * 1024;
+}
+
 }  // namespace rr
 
 using namespace rr;
 
 extern "C" size_t rr_hessenberg_workspace_size(int64_t n, int64_t k, int32_t arith) {
   int G = num_sms();
-  return arith == RR_F64 ? hess_ws_bytes<double>(k, G) : hess_ws_bytes<float>(k, G);
+  return arith == RR_F64 ? hess_ws_bytes<double>(k, G) : hess_ws_bytes<float>(k, G) + hess_blocked_extra(k);
 }
 
 namespace rr {
@@ -923,6 +1077,17 @@ rr_status rr::hessenberg_ex(int32_t arith, int64_t n, int64_t k, void* W, int64_
   if (n < 0 || k < 0 || k > 4096 || ldw < n || ldq < n || !W || !Q || !piv) return RR_ERR_ARG;
   if (n > INT_MAX) return RR_ERR_ARG;
   if (k == 0) return RR_OK;
+  if (arith == RR_F32 && hess_use_blocked(n, k, max_grid)) {
+    float* w = (float*)W;
+    constexpr int r = 16;
+    switch (qtype) {
+      case RR_F32: return hess_blocked<float>(n, k, w, ldw, (float*)Q, ldq, piv, tol, r, ws, ws_bytes, s);
+      case RR_BF16: return hess_blocked<__nv_bfloat16>(n, k, w, ldw, (__nv_bfloat16*)Q, ldq, piv, tol, r, ws, ws_bytes, s);
+      case RR_E4M3: return hess_blocked<e4m3b_t>(n, k, w, ldw, (e4m3b_t*)Q, ldq, piv, tol, r, ws, ws_bytes, s);
+      case RR_F64: return hess_blocked<double>(n, k, w, ldw, (double*)Q, ldq, piv, tol, r, ws, ws_bytes, s);
+    }
+    return RR_ERR_ARG;
+  }
   if (arith == RR_F32) {
     float* w = (float*)W;
     switch (qtype) {
@@ -938,6 +1103,21 @@ rr_status rr::hessenberg_ex(int32_t arith, int64_t n, int64_t k, void* W, int64_
       case RR_F32: return hess_launch<double, float>(n, k, w, ldw, (float*)Q, ldq, piv, tol, ws, ws_bytes, s, max_grid);
       case RR_BF16: return hess_launch<double, __nv_bfloat16>(n, k, w, ldw, (__nv_bfloat16*)Q, ldq, piv, tol, ws, ws_bytes, s, max_grid);
     }
+  }
+  return RR_ERR_ARG;
+}
+
+extern "C" rr_status rr_hessenberg_blocked(int64_t n, int64_t k, float* W, int64_t ldw, int32_t qtype, void* Q,
+                                           int64_t ldq, int32_t* piv, double tol, int32_t panel, void* ws,
+                                           size_t ws_bytes, void* stream) {
+  if (n < 0 || k < 0 || k > 4096 || ldw < n || ldq < n || !W || !Q || !piv) return RR_ERR_ARG;
+  if (n >= (int64_t)kNoRow || panel < 1 || panel > kPanelMax) return RR_ERR_ARG;
+  if (k == 0) return RR_OK;
+  cudaStream_t s = as_stream(stream);
+  switch (qtype) {
+    case RR_F32: return hess_blocked<float>(n, k, W, ldw, (float*)Q, ldq, piv, tol, panel, ws, ws_bytes, s);
+    case RR_BF16: return hess_blocked<__nv_bfloat16>(n, k, W, ldw, (__nv_bfloat16*)Q, ldq, piv, tol, panel, ws, ws_bytes, s);
+    case RR_F64: return hess_blocked<double>(n, k, W, ldw, (double*)Q, ldq, piv, tol, panel, ws, ws_bytes, s);
   }
   return RR_ERR_ARG;
 }

@@ -249,7 +249,9 @@ struct Common {
 };
 
 static void carve_common(Arena& ar, int64_t rows, int64_t b2, int32_t wt, Common& c) {
-  c.hess_bytes = rr_hessenberg_workspace_size(rows, b2, wt);
+  // room for the FP64-arithmetic process on b2 columns too (the SVD's FP64
+  // polish sweep runs Algorithm 8 in FP64 on b <= b2 columns)
+  c.hess_bytes = std::max(rr_hessenberg_workspace_size(rows, b2, wt), rr_hessenberg_workspace_size(rows, b2, RR_F64));
   c.hess_ws = ar.take_bytes(c.hess_bytes);
   c.gram_bytes = rr_gram_workspace_size(rows, b2, b2);
   c.gram_ws = ar.take_bytes(c.gram_bytes);
@@ -535,9 +537,79 @@ static rr_status svd_residual(const Op& op, SvdBufs& w, int64_t kk, double* R1, 
   return res_finish(s, kk, w.ss, w.sig, w.res);
 }
 
-static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sigma_out,
+// Dense operators in the mixed-precision path are solved zero-padded to a
+// multiple of 8 rows and columns (16 for the E4M3 basis): the tensor-core
+// products, the split-BF16 corrections and the FP64-emulated products need
+// strides in whole 16-byte vectors.  Zero rows and columns add only zero
+// singular values, and the iteration keeps the padded entries of every
+// basis exactly zero after the first product (A's zero columns and rows
+// contribute exact zeros), so the top triplets are those of A with the
+// padded entries of u and v equal to zero.
+static int svd_pad_quantum(const rr_operator* A, const rr_params* p) {
+  if (A->kind != RR_DENSE || p->basis == RR_F64) return 0;
+  const int q = p->basis == RR_E4M3 ? 16 : 8;
+  return (A->m % q || A->n % q) ? q : 0;
+}
+
+// One sweep of the paper's method in FP64-accurate arithmetic started from the
+// current Ritz vectors (the polish of the refinement phase): q times
+// { U = Alg. 8(A V), V = Alg. 8(A^T U) } with FP64-accurate products and FP64
+// Hessenberg arithmetic, then Algorithm 5 over (U, V) and the lift into
+// (Ut2, Vt2, sig2).  The refinement's low-precision corrections stop
+// improving once the residual reaches the level set by the ratio of the
+// largest to the smallest wanted singular value (about 2e-10 for
+// sigma_j = j^-1.5 with 16 wanted on 2048-4096-row problems, against 4e-11
+// for the all-FP64 method); one such sweep from there, with its own
+// contraction, ends at the all-FP64 method's accuracy.
+static rr_status svd_polish_f64(const Op& op, SvdBufs& w, int64_t b, int q, cudaStream_t s, Prof& prof) {
+  const int64_t m = op.m, n = op.n;
+  double* U = w.P;    // m x b
+  double* V = w.Qm;   // n x b
+  RR_CUDA(cudaMemcpyAsync(V, w.Vt, (size_t)n * b * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  for (int it = 0; it < q; ++it) {
+    STAGE(RR_STAGE_F64_PRODUCT, apply_f64(op, b, V, n, U, m, s));                                  // W = A V
+    STAGE(RR_STAGE_HESSENBERG, basis_step(w.c, true, RR_F64, RR_F64, m, b, U, m, U, m, s));        // U = basis(W)
+    STAGE(RR_STAGE_F64_PRODUCT, apply_f64_T(op, b, U, m, V, n, s));                                // Z = A^T U
+    STAGE(RR_STAGE_HESSENBERG, basis_step(w.c, true, RR_F64, RR_F64, n, b, V, n, V, n, s));        // V = basis(Z)
+  }
+  STAGE(RR_STAGE_F64_PRODUCT, apply_f64(op, b, V, n, w.Rv, m, s));                                 // A V
+  STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, RR_F64, U, m, RR_F64, U, m, w.Gu, b, s));
+  STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, RR_F64, V, n, RR_F64, V, n, w.Gv, b, s));
+  STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, RR_F64, U, m, RR_F64, w.Rv, m, w.Bm, b, s));
+  STAGE(RR_STAGE_PENCIL, pencil_svd(w.c, b, b, w.Bm, w.Gu, w.Gv, w.sig2, w.Ys, w.Zs, s));
+  STAGE(RR_STAGE_LIFT, lift2(op, s, m, b, RR_F64, U, m, b, 0, nullptr, 0, 0, w.Ys, b, w.Ut2, m));
+  STAGE(RR_STAGE_LIFT, lift2(op, s, n, b, RR_F64, V, n, b, 0, nullptr, 0, 0, w.Zs, b, w.Vt2, n));
+  return RR_OK;
+}
+
+// The padded operator of a problem (svd_pad_quantum) and, when padding, its
+// buffer taken from the front of the workspace: every user of a problem's
+// workspace layout (the solve, its size query, the batch's read-back) carves
+// it the same way.
+static const rr_operator* svd_operator(const rr_operator* A_in, const rr_params* p, Arena& ar,
+                                       rr_operator& Apad, double** Abuf) {
+  const int padq = svd_pad_quantum(A_in, p);
+  Apad = *A_in;
+  if (Abuf) *Abuf = nullptr;
+  if (!padq) return A_in;
+  Apad.m = (A_in->m + padq - 1) / padq * padq;
+  Apad.n = (A_in->n + padq - 1) / padq * padq;
+  Apad.ld = Apad.m;
+  double* buf = ar.take<double>(Apad.m * Apad.n);
+  Apad.values = buf;
+  if (Abuf) *Abuf = buf;
+  return &Apad;
+}
+
+static rr_status svd_run(const rr_operator* Aop_in, const rr_params* p, double* sigma_out,
                          double* U_out, double* V_out, void* ws, size_t ws_bytes, rr_info* info,
                          cudaStream_t s, bool batch_mode, int hess_grid, uint64_t seed) {
+  Arena ar(ws, ws_bytes);
+  const int64_t m0 = Aop_in->m, n0 = Aop_in->n;
+  const int padq = svd_pad_quantum(Aop_in, p);
+  rr_operator Apad;
+  double* Abuf = nullptr;
+  const rr_operator* Aop = svd_operator(Aop_in, p, ar, Apad, &Abuf);
   Op op;
   make_op(Aop, p->basis, op);
   const int32_t dt = op.dt;                 // refinement blocks (BF16 for an E4M3 basis)
@@ -545,14 +617,14 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
   if (op.f8 && (batch_mode || op.m % 16 || op.n % 16)) return RR_ERR_ARG;
   const int64_t m = op.m, n = op.n, b = p->block, k = p->k;
   const int q = p->degree;
+  const int qr = p->refine_degree > 0 ? p->refine_degree : q;  // products per refinement sweep
   const bool hess = p->hessenberg != 0;
   const bool refine = p->refine != 0 && dt != RR_F64;
   const int ph1 = refine ? (p->phase1_sweeps > 0 ? p->phase1_sweeps : 1) : p->max_sweeps;
-  Arena ar(ws, ws_bytes);
   carve_op(ar, op, false, refine, b);
   SvdBufs w;
   carve_svd(ar, op, b, refine, w);
-  double* v0buf = (batch_mode || !p->v0) ? ar.take<double>(n * b) : nullptr;
+  double* v0buf = (batch_mode || !p->v0 || padq) ? ar.take<double>(n * b) : nullptr;
   if (ar.overflow) return RR_ERR_WORKSPACE;
   Prof prof;
   prof.on = p->profile != 0 && !batch_mode;
@@ -562,9 +634,13 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
   w.c.hess_tol = p->hess_tol;
   RR_CUDA(cudaMemsetAsync(w.c.hess_ws, 0, 512, s));
   RR_CUDA(cudaMemsetAsync(w.frozen, 0, sizeof(int), s));
-  if (!batch_mode) STAGE(RR_STAGE_OTHER, check_operator_finite(Aop, w.c, s));
-  const size_t ds = dsz(dt);
-  (void)ds;
+  if (!batch_mode) STAGE(RR_STAGE_OTHER, check_operator_finite(Aop_in, w.c, s));
+  if (padq) {
+    // the zero-padded copy of A (counted with the one-time operator casts)
+    RR_CUDA(cudaMemsetAsync(Abuf, 0, (size_t)m * n * sizeof(double), s));
+    RR_CUDA(cudaMemcpy2DAsync(Abuf, m * sizeof(double), Aop_in->values, Aop_in->ld * sizeof(double),
+                              m0 * sizeof(double), n0, cudaMemcpyDeviceToDevice, s));
+  }
 
   // one-time operator casts and slicing (counted in the solve time)
   STAGE(RR_STAGE_OTHER, prepare_op(op, op, false, s));
@@ -574,6 +650,12 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
   const double* v0 = p->v0;
   if (batch_mode || !v0) {
     STAGE(RR_STAGE_OTHER, uniform_block(s, n, b, batch_mode ? seed : p->seed, v0buf, n));
+    v0 = v0buf;
+  } else if (padq) {
+    // the caller's n0 x b start block with zero rows up to n
+    RR_CUDA(cudaMemsetAsync(v0buf, 0, (size_t)n * b * sizeof(double), s));
+    RR_CUDA(cudaMemcpy2DAsync(v0buf, n * sizeof(double), v0, n0 * sizeof(double), n0 * sizeof(double), b,
+                              cudaMemcpyDeviceToDevice, s));
     v0 = v0buf;
   }
   STAGE(RR_STAGE_OTHER, rr_colscale_cast(n, b, v0, n, dt1, w.Vlo, n, w.c.scale, s));
@@ -630,6 +712,8 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
   // ---------------- phase 2: refinement ----------------
   if (refine && !nan_seen) {
     const int64_t b2 = 2 * b;
+    double prev_mx = INFINITY;
+    bool polish = false;
     for (;;) {
       // residual of all b Ritz triplets, FP64-accurate
       STAGE(RR_STAGE_F64_PRODUCT, apply_f64(op, b, w.Vt, n, w.P, m, s));      // P = A V~
@@ -656,8 +740,27 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
           converged = true;
           break;
         }
+        // the corrections stopped contracting the residual: polish in FP64
+        polish = inf.refine_sweeps >= 1 && mx > 0.3 * prev_mx;
+        prev_mx = mx;
       }
       if (sweep >= p->max_sweeps) break;
+      // batched problems (no host check) polish on their last sweep
+      if (batch_mode) polish = sweep == p->max_sweeps - 1;
+      if (polish) {
+        RR_TRY(svd_polish_f64(op, w, b, q, s, prof));
+        if (batch_mode)
+          STAGE(RR_STAGE_OTHER, keep_frozen(s, w.frozen, m, n, b, w.Ut, w.Ut2, w.Vt, w.Vt2, w.sig, w.sig2));
+        std::swap(w.Ut, w.Ut2);
+        std::swap(w.Vt, w.Vt2);
+        RR_CUDA(cudaMemcpyAsync(w.sig, w.sig2, b * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        ++sweep;
+        ++inf.refine_sweeps;
+        ++inf.polish_sweeps;
+        polish = false;
+        prev_mx = INFINITY;
+        continue;
+      }
       // correction recurrence (low precision):
       //   E_1 = R_v;  F_j = A^T E_j + R_u S^(2j-1);  E_{j+1} = A F_j + R_v S^(2j)
       // each block kept at unit column inf-norm, the injection coefficient
@@ -671,7 +774,7 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
       void* Fg = sp ? w.F32 : w.Flo;
       if (sp) STAGE(RR_STAGE_OTHER, scale_split(s, RR_F64, m, b, w.Rv, m, w.mu, w.Elo, w.Elo2, m, w.coef, w.sig));
       else STAGE(RR_STAGE_OTHER, scale_cast(s, RR_F64, m, b, w.Rv, m, w.mu, dt, w.Elo, m, w.coef, w.sig));
-      for (int j = 0; j < q; ++j) {
+      for (int j = 0; j < qr; ++j) {
         if (sp) STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp_T_split(op, b, w.Elo, w.Elo2, m, w.W, n, w.Ru, n, w.coef, s));
         else STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp_T(op, b, w.Elo, m, w.W, n, w.Ru, n, w.coef, s));
         STAGE(RR_STAGE_GRAM, project_out(w.c, s, n, b, w.Vt, n, (float*)w.W, n, w.Ys));
@@ -680,7 +783,7 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
         if (sp) STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp_split(op, b, w.Flo, w.Flo2, n, w.AF, m, w.Rv, m, w.coef, s));
         else STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp(op, b, w.Flo, n, w.AF, m, w.Rv, m, w.coef, s));
         STAGE(RR_STAGE_GRAM, project_out(w.c, s, m, b, w.Ut, m, (float*)w.AF, m, w.Ys));
-        if (j + 1 < q) {
+        if (j + 1 < qr) {
           if (sp) STAGE(RR_STAGE_OTHER, scale_split(s, op.wt, m, b, w.AF, m, w.mu, w.Elo, w.Elo2, m, w.coef, w.sig));
           else STAGE(RR_STAGE_OTHER, scale_cast(s, op.wt, m, b, w.AF, m, w.mu, dt, w.Elo, m, w.coef, w.sig));
         }
@@ -727,13 +830,14 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
     STAGE(RR_STAGE_F64_PRODUCT, svd_residual(op, w, k, w.P, w.Qm, s));
   }
 
-  // outputs: sigma, U, V (first k), unit columns, sign fixed on V
+  // outputs: sigma, U, V (first k; the rows of A's own size), unit columns,
+  // sign fixed on V
   RR_CUDA(cudaMemcpyAsync(sigma_out, w.sig, k * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  RR_CUDA(cudaMemcpy2DAsync(U_out, m * sizeof(double), w.Ut, m * sizeof(double), m * sizeof(double), k,
+  RR_CUDA(cudaMemcpy2DAsync(U_out, m0 * sizeof(double), w.Ut, m * sizeof(double), m0 * sizeof(double), k,
                             cudaMemcpyDeviceToDevice, s));
-  RR_CUDA(cudaMemcpy2DAsync(V_out, n * sizeof(double), w.Vt, n * sizeof(double), n * sizeof(double), k,
+  RR_CUDA(cudaMemcpy2DAsync(V_out, n0 * sizeof(double), w.Vt, n * sizeof(double), n0 * sizeof(double), k,
                             cudaMemcpyDeviceToDevice, s));
-  STAGE(RR_STAGE_OTHER, normalize_sign(s, n, k, V_out, n, m, U_out, m));
+  STAGE(RR_STAGE_OTHER, normalize_sign(s, n0, k, V_out, n0, m0, U_out, m0));
   inf.sweeps = sweep;
   if (batch_mode) {
     if (info) *info = inf;
@@ -747,15 +851,18 @@ static rr_status svd_run(const rr_operator* Aop, const rr_params* p, double* sig
   return converged ? RR_OK : RR_ERR_NO_CONV;
 }
 
-static size_t svd_ws(const rr_operator* A, const rr_params* p, bool batch) {
+static size_t svd_ws(const rr_operator* A_in, const rr_params* p, bool batch) {
+  Arena ar(nullptr, 0);
+  const int padq = svd_pad_quantum(A_in, p);
+  rr_operator Apad;
+  const rr_operator* A = svd_operator(A_in, p, ar, Apad, nullptr);
   Op op;
   make_op(A, p->basis, op);
-  Arena ar(nullptr, 0);
   const bool refine = p->refine != 0 && p->basis != RR_F64;
   carve_op(ar, op, false, refine, p->block);
   SvdBufs w;
   carve_svd(ar, op, p->block, refine, w);
-  if (batch || !p->v0) ar.take<double>(op.n * p->block);
+  if (batch || !p->v0 || padq) ar.take<double>(op.n * p->block);
   return ar.off + 4096;
 }
 
@@ -1255,8 +1362,9 @@ extern "C" rr_status rr_batch_svd_tuned(int32_t count, const rr_operator* A, con
   int nbad = 0;
   for (int i = 0; i < count; ++i) {
     Op op;
-    make_op(&A[i], p->basis, op);
     Arena ar((char*)ws + offs[i], align_up(svd_ws(&A[i], p, true), 4096));
+    rr_operator Apad;
+    make_op(svd_operator(&A[i], p, ar, Apad, nullptr), p->basis, op);
     carve_op(ar, op, false, p->refine != 0 && p->basis != RR_F64, p->block);
     SvdBufs w;
     carve_svd(ar, op, p->block, p->refine != 0 && p->basis != RR_F64, w);

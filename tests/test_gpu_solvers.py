@@ -229,9 +229,12 @@ def test_batch_problems_keep_converged_triplets(rr):
 
 def test_svd_seeded_start_block_and_info(rr):
     """v0 = NULL draws the start block on the device from params.seed (Alg. 1's
-    U(0,1) block): the same seed reproduces the solve bit for bit, another seed
-    reaches the same triplets by another path.  rr_info's Gram condition
-    estimate is at least 1 (G_ii (G^-1)_ii >= 1 for any SPD G) and finite."""
+    U(0,1) block) and the solve converges from it.  Runs are not reproducible
+    bit for bit (split-K products add FP32 partial tiles with atomics, and the
+    BF16 basis amplifies the different roundings), so the same seed gives the
+    same triplets and a first-projection residual within a few per cent.
+    rr_info's Gram condition estimate is at least 1 (G_ii (G^-1)_ii >= 1 for
+    any SPD G) and finite."""
     m, n, b, k = 2048, 512, 32, 16
     sig = wl.config2_sigma(n)
     Ad = dev(wl.dense_svd(m, n, sig, 2000))
@@ -246,8 +249,8 @@ def test_svd_seeded_start_block_and_info(rr):
         assert all(1.0 <= c < 1e16 for c in info["cond_history"]), info["cond_history"]
         assert info["cond_G_est"] == info["cond_history"][-1]
         outs.append((host(s), info["res_history"]))
-    assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1] == outs[1][1]
-    assert outs[0][1] != outs[2][1]
+    assert np.max(np.abs(outs[0][0] - outs[1][0]) / sig[:k]) < 1e-13
+    assert abs(outs[0][1][0] / outs[1][1][0] - 1) < 0.05
 
 
 def test_svd_nan_operator_reports_nan(rr):
@@ -267,9 +270,9 @@ def test_svd_nan_operator_reports_nan(rr):
 
 def test_eig_hess_tol_is_used(rr):
     """params.hess_tol reaches Algorithm 8: the default value given explicitly
-    changes nothing bit for bit; a skip tolerance of 0.9 (a column is skipped
-    unless elimination left its pivot within 10 % of its entry inf-norm)
-    changes the iteration."""
+    changes nothing (to rounding: small FP64 products sum with atomics); a
+    skip tolerance of 0.9 (a column is skipped unless elimination left its
+    pivot within 10 % of its entry inf-norm) drops columns."""
     n, k, b = 600, 8, 16
     A, lam = wl.config1(n)
     Ad, V0 = dev(A), dev(wl.uniform_block(n, b, 1001))
@@ -278,5 +281,80 @@ def test_eig_hess_tol_is_used(rr):
         p = rr.api.make_params(k, b, 2, 8, 1e-30, basis="f32", v0=V0, refine=False, hess_tol=tol)
         th, X, info = rr.rr_eig(rr.api.dense_operator(Ad), p, n)
         runs.append((host(th), info["res_history"], info["cols_dropped"]))
-    assert np.array_equal(runs[0][0], runs[1][0]) and runs[0][1] == runs[1][1]
-    assert runs[2][1] != runs[0][1]
+    assert np.max(np.abs(runs[0][0] - runs[1][0]) / lam[:k]) < 1e-12
+    assert all(abs(a / b - 1) < 1e-6 for a, b in zip(runs[0][1][:3], runs[1][1][:3]))
+    assert runs[0][2] == 0 and runs[2][2] > 0, (runs[0][2], runs[2][2])
+
+
+def _c4_ragged(count):
+    """Problems of the batched workload (m_i = 4 round(64 16^u_i), n_i = m_i/4,
+    sigma_j = j^-1.5, seed 4000 + i) from its largest class with m or n not a
+    multiple of 8: the shapes that lost the split-BF16 and emulated-FP64 paths
+    before operators were zero-padded."""
+    sh = wl.config4_shapes(512)
+    return [(i, m, n) for i, (m, n) in enumerate(sh) if m >= 2048 and (m % 8 or n % 8)][:count]
+
+
+def test_svd_ragged_shape_single(rr):
+    """One such problem through rr_svd (3172 x 793, zero-padded to 3176 x 800
+    inside the library): all 16 triplets to 1e-10, the outputs of A's own
+    size."""
+    i, m, n = _c4_ragged(1)[0]
+    sg = wl.config4_sigma(n)
+    A = wl.dense_svd(m, n, sg, 4000 + i)
+    p = rr.api.make_params(16, 32, 4, 30, 1e-10, basis="bf16", v0=dev(wl.uniform_block(n, 32, 4500 + i)),
+                           refine=True, phase1_sweeps=1)
+    s, U, V, info = rr.rr_svd(rr.api.dense_operator(dev(A)), p)
+    assert info["n_converged"] == 16, info
+    s, U, V = host(s), host(U), host(V)
+    assert U.shape == (m, 16) and V.shape == (n, 16)
+    assert np.max(np.abs(s - sg[:16]) / sg[:16]) <= 1e-10
+    Amul, Atmul = O.dense_apply(A)
+    assert O.residual_svd(Amul, Atmul, U, V, s).max() <= 1.5e-10
+
+
+def test_batch_svd_ragged_largest_class(rr):
+    """Eight problems of the batched workload's 2048-4095-row class with m or
+    n not a multiple of 8 (the class where most problems used to stall at
+    residual 3e-10), batched at the workload's settings (top 16, block 32,
+    4 products per sweep, 30 sweeps): every problem converges to 1e-10."""
+    probs = _c4_ragged(8)
+    ops, keep = [], []
+    for i, m, n in probs:
+        A = wl.dense_svd(m, n, wl.config4_sigma(n), 4000 + i)
+        t = dev(A)
+        keep.append((A, t))
+        ops.append(rr.api.dense_operator(t))
+    p = rr.api.make_params(16, 32, 4, 30, 1e-10, basis="bf16", refine=True, phase1_sweeps=1)
+    outs, st, infos = rr.rr_batch_svd(ops, p, seed=4000)
+    for (i, m, n), (s, U, V), (A, _), x, inf in zip(probs, outs, keep, st, infos):
+        sg = wl.config4_sigma(n)
+        s = host(s)
+        assert x == 0, ((m, n), inf)
+        assert np.max(np.abs(s - sg[:16]) / sg[:16]) <= 1e-10, (m, n)
+        Amul, Atmul = O.dense_apply(A)
+        assert O.residual_svd(Amul, Atmul, host(U), host(V), s).max() <= 1.5e-10, (m, n)
+
+
+def test_svd_fp64_polish_after_stall(rr):
+    """Problems of the batched workload's largest class whose low-precision
+    corrections stall above 1e-10 (near 2e-10 on sigma_j = j^-1.5 with 16 of
+    32 wanted) finish with the FP64 polish sweep: all 16 triplets to 1e-10 in
+    every problem, the polish taken in at least one of them."""
+    sh = wl.config4_shapes(512)
+    probs = [(i, m, n) for i, (m, n) in enumerate(sh) if m >= 2048][:8]
+    polished = 0
+    for i, m, n in probs:
+        sg = wl.config4_sigma(n)
+        A = wl.dense_svd(m, n, sg, 4000 + i)
+        p = rr.api.make_params(16, 32, 4, 40, 1e-10, basis="bf16", v0=dev(wl.uniform_block(n, 32, 4600 + i)),
+                               refine=True, phase1_sweeps=1)
+        s, U, V, info = rr.rr_svd(rr.api.dense_operator(dev(A)), p)
+        assert info["n_converged"] == 16, ((m, n), info)
+        s = host(s)
+        assert np.max(np.abs(s - sg[:16]) / sg[:16]) <= 1e-10
+        Amul, Atmul = O.dense_apply(A)
+        assert O.residual_svd(Amul, Atmul, host(U), host(V), s).max() <= 1.5e-10, (m, n)
+        polished += info["polish_sweeps"] > 0
+    print("problems finished by the polish:", polished, "of", len(probs))
+    assert polished >= 1

@@ -246,6 +246,53 @@ def test_hessenberg_bitexact_fp32(rr, n, k):
     assert np.array_equal(Q.cpu().numpy(), Qfo)
 
 
+@pytest.mark.parametrize("n,k,panel", [(16384, 128, 16), (4096, 128, 8), (20000, 100, 32), (3000, 40, 7),
+                                       (16, 40, 16)])
+def test_hessenberg_blocked_bitexact(rr, n, k, panel):
+    """The blocked (level-3) process in panels of r columns against the
+    unblocked FP32 oracle, bit for bit (pivots and basis), at the dense SVD's
+    block shapes, ragged last panels and a block wider than tall (its later
+    columns are all skipped)."""
+    W = np.random.default_rng(n + k + panel).standard_normal((n, k)).astype(np.float32)
+    Qo, pivo, keepo, Qfo = O.hessenberg(W, arith="f32")
+    Q, piv, err = rr.rr_hessenberg_blocked(dev(W.astype(np.float64), torch.float32), panel, qtype=torch.float32)
+    assert int(err.cpu()[0]) == 0
+    assert np.array_equal(piv.cpu().numpy().astype(np.int64), pivo)
+    assert np.array_equal(Q.cpu().numpy(), Qfo)
+
+
+def test_hessenberg_blocked_ties_rank_deficiency(rr):
+    """Integer block with repeated maxima and dependent columns inside and
+    across panels: the same pivots, skips and BF16 basis as the oracle."""
+    rng = np.random.default_rng(19)
+    W = rng.integers(-3, 4, size=(2000, 40)).astype(np.float32)
+    W[:, 5] = W[:, 1] + W[:, 2]
+    W[:, 21] = W[:, 3] - W[:, 17]
+    Qo, pivo, keepo, Qfo = O.hessenberg(W, arith="f32")
+    assert not keepo[5] and not keepo[21]
+    Q, piv, err = rr.rr_hessenberg_blocked(dev(W.astype(np.float64), torch.float32), 16, qtype=torch.bfloat16)
+    assert np.array_equal(piv.cpu().numpy().astype(np.int64), pivo)
+    assert np.array_equal(host(Q), O.round_bf16(Qfo))
+
+
+def test_hessenberg_tall_block_of_the_sparse_workload(rr):
+    """1,048,576 x 160 (the sparse workload's basis block: the default entry
+    takes the blocked path there), pivots and basis bit for bit against the
+    oracle's FP32 process, and the panel form of the oracle (FP64, exact
+    arithmetic equal to Algorithm 8) giving the same pivots."""
+    from oracle import krylov as OK
+    n, k = 1 << 20, 160
+    W = np.random.default_rng(1160).standard_normal((n, k)).astype(np.float32)
+    Qo, pivo, keepo, Qfo = O.hessenberg(W, arith="f32")
+    Q, piv, err = rr.rr_hessenberg(dev(W.astype(np.float64), torch.float32), qtype=torch.float32)
+    assert int(err.cpu()[0]) == 0
+    assert np.array_equal(piv.cpu().numpy().astype(np.int64), pivo)
+    assert np.array_equal(Q.cpu().numpy(), Qfo)
+    Qb, pivb = OK.hessenberg_blocked(W[:65536].astype(np.float64), 16)
+    Qu, pivu, _, _ = O.hessenberg(W[:65536].astype(np.float64))
+    assert np.array_equal(pivb, pivu)
+
+
 def test_hessenberg_ties_rank_deficiency_and_bf16_output(rr):
     # integer-valued block with repeated maxima and an exactly dependent column
     rng = np.random.default_rng(9)
