@@ -707,6 +707,9 @@ def run_stage(args):
             torch.cuda.synchronize()
             return time.perf_counter() - t1, st, infos
         t_def, st_def, inf_def = run(lambda: rr.rr_batch_svd(ops, params, 7))
+        # the same batch with the all-FP64 method (the same sweeps, no refinement)
+        p64 = rr.api.make_params(16, 32, 4, args.batch_sweeps, 1e-10, basis="f64", refine=False)
+        t_64, st_64, inf_64 = run(lambda: rr.rr_batch_svd(ops, p64, 7))
         t_tuned, st_tuned, inf_tuned = run(lambda: AT.batch_svd(ops, params, 7, table))
         conv = lambda infos: int(sum(i["n_converged"] for i in infos))
 
@@ -720,7 +723,10 @@ def run_stage(args):
         print(json.dumps({"stage": "batch", "count": len(ops), "sweeps": args.batch_sweeps,
                           "refine_degree": args.refine_degree,
                           "converged_problems": {"default": sum(1 for x in st_def if x == 0),
-                                                 "tuned": sum(1 for x in st_tuned if x == 0)},
+                                                 "tuned": sum(1 for x in st_tuned if x == 0),
+                                                 "fp64": sum(1 for x in st_64 if x == 0)},
+                          "fp64": {"seconds": t_64, "problems_per_s": len(ops) / t_64,
+                                   "pairs_per_s": conv(inf_64) / t_64, "failed_by_class": failures(st_64)},
                           "classes": {k: len(v) for k, v in by_class.items()}, "tune_seconds": t_tune,
                           "default": {"seconds": t_def, "problems_per_s": len(ops) / t_def,
                                       "pairs_per_s": conv(inf_def) / t_def, "failed_by_class": failures(st_def),

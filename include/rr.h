@@ -131,7 +131,7 @@ typedef struct {
   int32_t polish_sweeps; /* SVD refinement sweeps run as the FP64 polish (the
                             method's sweep in FP64-accurate arithmetic from the Ritz
                             vectors, taken when the corrections stop contracting the
-                            residual, and as a batched problem's last sweep)         */
+                            residual, and as a batched problem's last two sweeps)    */
 } rr_info;
 
 /* Stages of rr_info.stage_ms: */
@@ -349,6 +349,42 @@ rr_status rr_hessenberg(int32_t arith, int64_t n, int64_t k, void* W, int64_t ld
 rr_status rr_hessenberg_blocked(int64_t n, int64_t k, float* W, int64_t ldw, int32_t qtype, void* Q,
                                 int64_t ldq, int32_t* piv, double tol, int32_t panel, void* ws,
                                 size_t ws_bytes, void* stream);
+
+/* Krylov-Hessenberg process (Sec. 4.1, Alg. 7) on a CSR operator (FP32
+ * values, as rr_csr_spmm): a basis V (n x k, column-major, ld ldv) of
+ * K_k(A, v) with no inner products.  Each new vector A v_j is reduced at the
+ * pivot rows of the earlier vectors (h_ij = its entry at pi_i after the
+ * first i-1 subtractions, subtracted in order i = 1..j) and scaled so that
+ * its largest-magnitude entry (first index on ties) is 1.  arith RR_F64 or
+ * RR_F32: the arithmetic and storage of V and AV; each step a separately
+ * rounded multiply and subtract.  Outputs: V; AV (n x k, ld ldv) the raw
+ * products A v_j (column j before the reduction); H (k x k FP64,
+ * column-major) with H(i, j) = h_ij for i <= j and H(j+1, j) the pivot value
+ * (Alg. 7's upper Hessenberg matrix; column k-1 unused); piv (k int32) the
+ * pivot rows.  v: n FP64 start vector (device).  Workspace:
+ * rr_krylov_hessenberg_workspace_size(n, k, arith).  RR_ERR_ARG: k < 1 or
+ * k > n, null pointers, bad arith. */
+size_t rr_krylov_hessenberg_workspace_size(int64_t n, int32_t k, int32_t arith);
+rr_status rr_krylov_hessenberg(int32_t arith, int64_t n, int32_t k, const int32_t* row_ptr,
+                               const int32_t* col_idx, const float* values, const double* v, void* V,
+                               void* AV, int64_t ldv, double* H, int32_t* piv, void* ws,
+                               size_t ws_bytes, void* stream);
+
+/* Largest eigenpairs of a symmetric CSR operator by the Krylov-Hessenberg
+ * basis with OFRR (Alg. 7 + Alg. 3; the sparse experiment of Sec. 5.2.2):
+ * restarts + 1 cycles, each building the m-dimensional basis of K_m(A, v)
+ * (arith RR_F64 or RR_F32) and solving (V^T A V) y = theta (V^T V) y with
+ * FP64-accurate projection products; the next cycle restarts from the single
+ * Ritz vector of the largest Ritz value.  Outputs (device): theta (k FP64,
+ * descending), X (n x k FP64, ld n, unit columns, sign fixed so the
+ * largest-|.| entry is positive), res (k FP64: |A x - theta x|_2 / |theta|).
+ * v0: n FP64 start vector.  2 <= m <= min(n, 335), 1 <= k <= m.  Workspace
+ * rr_krylov_workspace_size(n, m, k, arith) (256-byte aligned).  Does not
+ * synchronise. */
+size_t rr_krylov_workspace_size(int64_t n, int32_t m, int32_t k, int32_t arith);
+rr_status rr_krylov_eig(const rr_operator* A, int32_t m, int32_t restarts, int32_t k, int32_t arith,
+                        const double* v0, double* theta, double* X, double* res, void* ws,
+                        size_t ws_bytes, void* stream);
 
 /* Projection products (Alg. 3: B = U^T A U, M = U^T U; Alg. 5: U^T A V,
  * U^T U, V^T V): G (p x q FP64, ld ldg) = X^T Y (+ G if accumulate) for tall

@@ -20,7 +20,7 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["krylov_hessenberg", "hessenberg_blocked"]
+__all__ = ["krylov_hessenberg", "hessenberg_blocked", "solve_krylov_eig"]
 
 
 def krylov_hessenberg(Amul, v, k: int):
@@ -72,3 +72,26 @@ def hessenberg_blocked(W, r: int):
             U12 = np.linalg.solve(L11, Q[piv[c0:c1], c1:])
             Q[:, c1:] -= L @ U12
     return Q, piv
+
+
+def solve_krylov_eig(A_mul, v0, m: int, restarts: int, k: int):
+    """Krylov-Hessenberg basis with OFRR for a symmetric operator (Sec. 4.1,
+    Alg. 7 for the basis, Alg. 3 for the projection; the sparse experiment of
+    Sec. 5.2.2): `restarts + 1` cycles, each building the m-dimensional basis
+    of K_m(A, v) by Alg. 7 and solving the projected pencil
+    (V^T A V) y = theta (V^T V) y; the next cycle restarts from the single Ritz
+    vector of the largest Ritz value.  Returns (theta: the k largest Ritz
+    values, descending; X: their unit Ritz vectors; res: relative residuals
+    |A x - theta x| / |theta|)."""
+    from .ofrr import pencil_eig, residual_eig
+    v = np.asarray(v0, dtype=np.float64)
+    for _ in range(restarts + 1):
+        V, _, _ = krylov_hessenberg(A_mul, v, m)
+        AV = np.asarray(A_mul(V), dtype=np.float64)
+        theta, Y = pencil_eig(V.T @ AV, V.T @ V)
+        order = np.argsort(-theta)
+        theta, Y = theta[order], Y[:, order]
+        X = V @ Y
+        X = X / np.linalg.norm(X, axis=0)
+        v = X[:, 0]
+    return theta[:k], X[:, :k], residual_eig(A_mul, X[:, :k], theta[:k])

@@ -91,6 +91,12 @@ _SIGS = {
     "rr_wait_selftest": (c_i32, [c_i32, c_i64, c_vp, c_vp]),
     "rr_hessenberg_blocked": (c_i32, [c_i64, c_i64, c_vp, c_i64, c_i32, c_vp, c_i64, c_vp, c_dbl, c_i32, c_vp,
                                       c_sz, c_vp]),
+    "rr_krylov_hessenberg_workspace_size": (c_sz, [c_i64, c_i32, c_i32]),
+    "rr_krylov_hessenberg": (c_i32, [c_i32, c_i64, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_i64, c_vp, c_vp,
+                                     c_vp, c_sz, c_vp]),
+    "rr_krylov_workspace_size": (c_sz, [c_i64, c_i32, c_i32, c_i32]),
+    "rr_krylov_eig": (c_i32, [ctypes.POINTER(RrOperator), c_i32, c_i32, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp,
+                              c_vp, c_sz, c_vp]),
     "rr_gram_noalloc": (c_i32, [c_i64, c_i64, c_i64, c_i32, c_vp, c_i64, c_i32, c_vp, c_i64, c_vp, c_i64,
                                 c_i32, c_vp]),
     "rr_pencil_workspace_size": (c_sz, [c_i64, c_i64]),

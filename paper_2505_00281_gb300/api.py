@@ -15,7 +15,7 @@ from ._lib import RR, RrBatchTuning, RrError, RrInfo, RrOperator, RrParams, chec
 __all__ = [
     "fortran", "ld_of", "dense_operator", "csr_operator", "make_params", "rr_eig", "rr_svd",
     "rr_batch_svd", "rr_colscale_cast", "rr_cast_operator", "rr_split_operator", "rr_lift", "rr_gemm_lowp", "rr_gemm_f64",
-    "rr_hessenberg", "rr_hessenberg_blocked", "rr_wait_selftest", "rr_gram", "rr_gram_noalloc", "rr_pencil_eig", "rr_pencil_svd", "rr_csr_spmm",
+    "rr_hessenberg", "rr_hessenberg_blocked", "rr_krylov_hessenberg", "rr_krylov_eig", "rr_wait_selftest", "rr_gram", "rr_gram_noalloc", "rr_pencil_eig", "rr_pencil_svd", "rr_csr_spmm",
     "rr_chebyshev_step", "rr_chebyshev_step_rows", "rr_quantize_e4m3", "rr_gemm_e4m3", "rr_conv3x3_forward", "rr_conv3x3_backward", "rr_relu_mask", "rr_procrustes_grad",
     "rr_adam", "rr_net_block", "RrParams", "RrOperator", "RrInfo", "DTYPES",
 ]
@@ -293,6 +293,37 @@ def rr_hessenberg_blocked(W, panel, qtype=torch.bfloat16, tol=0.0, stream=None):
                                                            _p(piv), tol, int(panel), _p(ws), ws.numel(),
                                                            _stream(stream)))
     return Q, piv, ws[:4].view(torch.int32)
+
+
+def rr_krylov_hessenberg(row_ptr, col_idx, values, v, k, dtype=torch.float64, stream=None):
+    """Alg. 7 on a CSR operator.  Returns (V, AV, H, piv) on the device."""
+    n = row_ptr.shape[0] - 1
+    L = lib()
+    V = empty_f(n, k, dtype, v.device)
+    AV = empty_f(n, k, dtype, v.device)
+    H = empty_f(k, k, torch.float64, v.device)
+    piv = torch.empty(k, dtype=torch.int32, device=v.device)
+    ws = _ws(L.rr_krylov_hessenberg_workspace_size(n, k, DTYPES[dtype]), v.device)
+    check("rr_krylov_hessenberg", L.rr_krylov_hessenberg(DTYPES[dtype], n, k, _p(row_ptr), _p(col_idx), _p(values),
+                                                         _p(v), _p(V), _p(AV), n, _p(H), _p(piv), _p(ws),
+                                                         ws.numel(), _stream(stream)))
+    return V, AV, H, piv
+
+
+def rr_krylov_eig(op: RrOperator, v0, m, restarts, k, dtype=torch.float64, stream=None):
+    """Alg. 7 + Alg. 3 with restarts.  Returns (theta[k], X[n, k], res[k])."""
+    L = lib()
+    n = op.n
+    theta = torch.empty(k, dtype=torch.float64, device=v0.device)
+    X = empty_f(n, k, torch.float64, v0.device)
+    res = torch.empty(k, dtype=torch.float64, device=v0.device)
+    wsb = L.rr_krylov_workspace_size(n, m, k, DTYPES[dtype])
+    if wsb == 0:
+        raise RrError("rr_krylov_workspace_size", RR.ERR_ARG)
+    ws = _ws(wsb, v0.device)
+    check("rr_krylov_eig", L.rr_krylov_eig(ctypes.byref(op), m, restarts, k, DTYPES[dtype], _p(v0), _p(theta), _p(X),
+                                           _p(res), _p(ws), ws.numel(), _stream(stream)))
+    return theta, X, res
 
 
 def rr_gram(X, Y, G=None, accumulate=False, stream=None):

@@ -745,8 +745,8 @@ static rr_status svd_run(const rr_operator* Aop_in, const rr_params* p, double* 
         prev_mx = mx;
       }
       if (sweep >= p->max_sweeps) break;
-      // batched problems (no host check) polish on their last sweep
-      if (batch_mode) polish = sweep == p->max_sweeps - 1;
+      // batched problems (no host check) polish on their last two sweeps
+      if (batch_mode) polish = sweep >= p->max_sweeps - 2 && sweep >= ph1 + 1;
       if (polish) {
         RR_TRY(svd_polish_f64(op, w, b, q, s, prof));
         if (batch_mode)

@@ -69,3 +69,44 @@ def test_blocked_hessenberg_equals_unblocked_and_lu(r):
         assert np.abs(Q - Q8).max() < 1e-12
     P, L, U = sla.lu(W)
     assert np.abs(Q - P @ L).max() < 1e-12
+
+
+def _lanczos_full(A, v, m):
+    """An orthonormal basis of K_m(A, v): Arnoldi with two passes of modified
+    Gram-Schmidt per vector (an independent construction of the same space)."""
+    n = v.shape[0]
+    Q = np.zeros((n, m))
+    Q[:, 0] = v / np.linalg.norm(v)
+    for j in range(1, m):
+        w = A @ Q[:, j - 1]
+        for _ in range(2):
+            for i in range(j):
+                w = w - (Q[:, i] @ w) * Q[:, i]
+        Q[:, j] = w / np.linalg.norm(w)
+    return Q
+
+
+def test_solve_krylov_eig_equals_classical_rr_on_the_krylov_space():
+    """One cycle of Alg. 7 + Alg. 3 gives the Ritz values of K_m(A, v) (OFRR
+    equals classical RR on the same span, Sec. 3); with restarts every cycle
+    starts from the top Ritz vector of the previous one."""
+    import workloads as wl
+    rp, ci, va, _ = wl.grid_schrodinger_csr(11, 10.0, 5300)
+    Amul = O.csr_apply(rp, ci, va)
+    A = Amul(np.eye(121))
+    v = wl.uniform_block(121, 1, 5301)[:, 0]
+    th, X, res = K.solve_krylov_eig(Amul, v, 20, 0, 6)
+    Q = _lanczos_full(A, v, 20)
+    ref = np.sort(np.linalg.eigvalsh(Q.T @ A @ Q))[::-1][:6]
+    assert np.allclose(th, ref, rtol=1e-10, atol=0)
+    assert np.allclose(res, O.residual_eig(Amul, X, th), rtol=1e-12)
+    # two restarts, composed by hand with the orthonormal construction
+    th2, X2, _ = K.solve_krylov_eig(Amul, v, 20, 2, 6)
+    w = v
+    for _ in range(3):
+        Q = _lanczos_full(A, w, 20)
+        lam, Z = np.linalg.eigh(Q.T @ A @ Q)
+        w = Q @ Z[:, -1]
+    assert np.allclose(th2, lam[::-1][:6], rtol=1e-9, atol=0)
+    # the largest eigenvalue of the grid operator is reached
+    assert abs(th2[0] - np.linalg.eigvalsh(A)[-1]) < 1e-8 * th2[0]
