@@ -736,6 +736,101 @@ def run_stage(args):
                           "tuned": {"seconds": t_tuned, "problems_per_s": len(ops) / t_tuned,
                                     "pairs_per_s": conv(inf_tuned) / t_tuned, "failed_by_class": failures(st_tuned)},
                           "table": table}))
+    elif args.stage == "kernel":
+        # the Gaussian kernel-matrix family at scale: n points uniform in the square of side sqrt(n)
+        # (one per unit area, as the paper's 1000-point sets), f = 0.2, l = 10, s = 0.01; the 20
+        # largest eigenpairs, block 32, 3 products per sweep, BF16 basis refined to 1e-10, through the
+        # matrix-free operator; and the operator product alone (FP32 and FP64 evaluation)
+        n, f, l, sh, k, bs = args.points, 0.2, 10.0, 0.01, 20, 32
+        x = torch.from_numpy(wl.kernel_points(n, 6500)).cuda()
+        op = rr.api.kernel_operator(x, f, l, sh)
+        V = rr.fortran(torch.rand(n, bs, device="cuda", dtype=torch.float64))
+        out = {}
+        for name, Xd, odt in (("fp32", V.to(torch.float32), torch.float32), ("fp64", V, torch.float64)):
+            for _ in range(2):
+                rr.api.rr_kernel_apply(op, rr.fortran(Xd), out_dtype=odt)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            reps = 3
+            for _ in range(reps):
+                rr.api.rr_kernel_apply(op, rr.fortran(Xd), out_dtype=odt)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            flops = 2.0 * n * n * bs
+            out[name] = {"ms": ms, "tflops": flops / ms / 1e9, "entries_per_s": n * n / ms * 1e3}
+        # FP32 FMA peak from the unit counts: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
+        fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        out["fp32"]["frac_of_fp32_fma_peak"] = out["fp32"]["tflops"] / fp32_peak
+        p = rr.api.make_params(k, bs, 3, 40, 1e-10, basis="bf16", v0=None, seed=6501, refine=True, phase1_sweeps=2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        th, X, info = rr.rr_eig(op, p, n)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        print(json.dumps({"stage": "kernel", "n": n, "f": f, "l": l, "s": sh, "k": k, "block": bs,
+                          "products": out, "fp32_fma_peak_tflops": fp32_peak, "bound": "alu",
+                          "solve": {"seconds": sec, "n_converged": info["n_converged"], "sweeps": info["sweeps"],
+                                    "max_res": info["max_res"], "pairs_per_s": info["n_converged"] / sec,
+                                    "theta_first": float(th[0].item()), "theta_last": float(th[-1].item())}}))
+    elif args.stage == "krylov":
+        # Krylov-Hessenberg + OFRR on the sparse workload's operator (1024 x 1024 grid, n = 1,048,576):
+        # Krylov dimension 100, 4 restarts from the top Ritz vector, the 20 largest pairs reported
+        Ng, m, restarts, k = 1024, 100, 4, 20
+        rp, ci, va, _ = wl.grid_schrodinger_csr(Ng, 10.0, wl.seed_for(3))
+        d = [torch.from_numpy(a).cuda() for a in (rp, ci, va)]
+        op = rr.api.csr_operator(*d)
+        v = torch.from_numpy(wl.uniform_block(Ng * Ng, 1, 6601)[:, 0]).cuda()
+        out = {}
+        for name, dt in (("fp64", torch.float64), ("fp32", torch.float32)):
+            rr.rr_krylov_eig(op, v, m, 0, k, dtype=dt)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            th, X, res = rr.rr_krylov_eig(op, v, m, restarts, k, dtype=dt)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            r = res.cpu().numpy()
+            # bytes of one cycle's basis process: every step reads the earlier vectors once
+            es = 8 if dt == torch.float64 else 4
+            byts = (restarts + 1) * (es * Ng * Ng * m * (m + 1) / 2 + m * (len(ci) * 8 + (Ng * Ng + 1) * 4))
+            out[name] = {"ms": ms, "theta_first": float(th[0].item()), "res_first": float(r[0]),
+                         "res_median": float(np.median(r)), "converged_1e-8": int((r < 1e-8).sum()),
+                         "process_bytes": byts, "process_gbs_over_solve": byts / ms / 1e6}
+        print(json.dumps({"stage": "krylov", "n": Ng * Ng, "m": m, "restarts": restarts, "k": k, **out}))
+    elif args.stage == "builders":
+        # Table 3's comparison on this GPU: MGS-L, MGS-R, CGS, CGS-2, Hess-L, Hess-R on U(0,1)
+        # blocks of 25000 x 200, 50000 x 200 and 50000 x 400 in FP64, FP32 and FP16 storage (FP16
+        # computes in FP32); CUDA events, median of 3 after one warm-up.  The paper's numbers
+        # (RTX 3070 Ti) are context only.
+        shapes = [(25000, 200), (50000, 200), (50000, 400)]
+        methods = ["mgs_l", "mgs_r", "cgs", "cgs2", "hess_l", "hess_r"]
+        out = {}
+        for dt, name in ((torch.float64, "fp64"), (torch.float32, "fp32"), (torch.float16, "fp16")):
+            for (n, k) in shapes:
+                W0 = rr.fortran(torch.rand(k, n, device="cuda", dtype=torch.float64).t()).to(dt)
+                W0 = rr.fortran(W0)
+                for mth in methods:
+                    if args.quick and mth == "mgs_l" and k > 200:
+                        continue
+                    ts = []
+                    for rep in range(4):
+                        W = rr.fortran(W0.clone())
+                        torch.cuda.synchronize()
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record()
+                        rr.api.rr_basis_builder(W, mth, want_r=False)
+                        e1.record()
+                        torch.cuda.synchronize()
+                        if rep:
+                            ts.append(e0.elapsed_time(e1))
+                    out.setdefault(name, {}).setdefault(f"{n}x{k}", {})[mth] = float(np.median(ts))
+        print(json.dumps({"stage": "builders", "ms": out}))
     elif args.stage == "prep":
         A = torch.randn(N, M, device="cuda", dtype=torch.float64).t()   # M x N column-major
         X = rr.fortran(torch.randn(N, B, device="cuda", dtype=torch.float64))
@@ -769,11 +864,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp8", action="store_true", help="skip the FP8-E4M3 basis run")
     ap.add_argument("--no-sparse", action="store_true", help="skip the sparse eigenproblem leg")
-    ap.add_argument("--stage", choices=["pencil", "hessenberg", "gemm", "split", "f64emu", "prep", "cheb", "warm", "sparse", "fp8", "batch"],
+    ap.add_argument("--stage", choices=["pencil", "hessenberg", "gemm", "split", "f64emu", "prep", "cheb", "warm", "sparse",
+                                        "fp8", "batch", "kernel", "krylov", "builders"],
                     help="run one stage of the workload (profiling driver)")
     ap.add_argument("--b", type=int, default=256, help="pencil size for --stage pencil, columns for hessenberg")
     ap.add_argument("--rows", type=int, default=M, help="rows of the block for --stage hessenberg")
     ap.add_argument("--grid", type=int, default=64, help="grid side for --stage warm")
+    ap.add_argument("--points", type=int, default=65536, help="points of the kernel operator for --stage kernel")
+    ap.add_argument("--quick", action="store_true", help="--stage builders: skip MGS-L at k = 400")
     ap.add_argument("--sweeps", type=int, default=60, help="sweep limit for --stage sparse")
     ap.add_argument("--count", type=int, default=512, help="problems for --stage batch")
     ap.add_argument("--batch-sweeps", type=int, default=12, help="sweeps of every problem for --stage batch")

@@ -50,7 +50,8 @@
 extern "C" {
 #endif
 
-typedef enum { RR_F64 = 0, RR_F32 = 1, RR_BF16 = 2, RR_E4M3 = 3 } rr_dtype;
+typedef enum { RR_F64 = 0, RR_F32 = 1, RR_BF16 = 2, RR_E4M3 = 3, RR_F16 = 4 } rr_dtype;
+/* (RR_F16: storage of the comparator basis builders only, rr_basis_builder.) */
 
 typedef enum {
   RR_OK = 0,
@@ -63,14 +64,23 @@ typedef enum {
   RR_ERR_NAN = 7
 } rr_status;
 
-enum { RR_DENSE = 0, RR_CSR = 1 };
+enum { RR_DENSE = 0, RR_CSR = 1, RR_KERNEL = 2 };
 enum { RR_LARGEST = 0, RR_SMALLEST = 1 };
 enum { RR_POWER = 0, RR_CHEBYSHEV = 1 };
+enum { RR_MGS_L = 0, RR_MGS_R = 1, RR_CGS = 2, RR_CGS2 = 3, RR_HESS_L = 4, RR_HESS_R = 5 };
 
 /* The operator A.
- *   RR_DENSE: m x n FP64, column-major, leading dimension ld >= m.
- *   RR_CSR:   square n x n (m == n), FP32 values, int32 row_ptr[n+1] and
- *             col_idx[nnz] (sorted within rows), symmetric (used by rr_eig).
+ *   RR_DENSE:  m x n FP64, column-major, leading dimension ld >= m.
+ *   RR_CSR:    square n x n (m == n), FP32 values, int32 row_ptr[n+1] and
+ *              col_idx[nnz] (sorted within rows), symmetric (used by rr_eig).
+ *   RR_KERNEL: the Gaussian kernel matrix of Sec. 2 / Sec. 5's kernel-matrix
+ *              experiments, never stored (matrix-free):
+ *              A(i, j) = f (exp(-|x_i - y_j|^2 / (2 l^2)) + s [i == j]),
+ *              with (f, l, s) = kparams; values = the m points x_i (m x d
+ *              FP64, column-major, ld >= m), points_y = the n points y_j
+ *              (n x d, ld n) or NULL for the square symmetric operator over
+ *              the x_i alone (the shift s applies only then); nnz = d
+ *              (1 .. 8); dtype RR_F64.
  * All pointers are device pointers.  The library never writes to them. */
 typedef struct {
   int32_t kind;
@@ -79,6 +89,8 @@ typedef struct {
   const void* values;
   const int32_t* row_ptr;
   const int32_t* col_idx;
+  const double* points_y;  /* RR_KERNEL only */
+  double kparams[3];       /* RR_KERNEL only: f, l, s */
 } rr_operator;
 
 /* Solver parameters (Algorithm 1 inputs A, k, m, iter; Sec. 4.2 precisions). */
@@ -386,6 +398,23 @@ rr_status rr_krylov_eig(const rr_operator* A, int32_t m, int32_t restarts, int32
                         const double* v0, double* theta, double* X, double* res, void* ws,
                         size_t ws_bytes, void* stream);
 
+/* The basis builders the paper compares (Sec. 4, Table 1; timed in Table 3)
+ * on an n x k block W (column-major, ld ldw), overwritten with the basis Q:
+ *   RR_MGS_L  modified Gram-Schmidt, left-looking, no re-orthogonalisation;
+ *   RR_MGS_R  modified Gram-Schmidt, right-looking;
+ *   RR_CGS    classical Gram-Schmidt; RR_CGS2 with one re-orthogonalisation;
+ *   RR_HESS_L Hessenberg process, left-looking (no column skip);
+ *   RR_HESS_R Hessenberg process, right-looking (Algorithm 8, rr_hessenberg).
+ * storage RR_F64 (FP64 arithmetic), RR_F32 or RR_F16 (FP32 arithmetic).
+ * R (k x k FP64, column-major, may be NULL): the Gram-Schmidt methods'
+ * triangular factor (W = Q R).  piv (k int32, the Hessenberg methods,
+ * required there): pivot rows.  Workspace: rr_basis_builder_workspace_size.
+ * RR_ERR_ARG: bad method, storage or sizes (k <= n, k <= 4096; Hess-L
+ * k <= 335). */
+size_t rr_basis_builder_workspace_size(int32_t method, int32_t storage, int64_t n, int64_t k);
+rr_status rr_basis_builder(int32_t method, int32_t storage, int64_t n, int64_t k, void* W, int64_t ldw,
+                           double* R, int32_t* piv, void* ws, size_t ws_bytes, void* stream);
+
 /* Projection products (Alg. 3: B = U^T A U, M = U^T U; Alg. 5: U^T A V,
  * U^T U, V^T V): G (p x q FP64, ld ldg) = X^T Y (+ G if accumulate) for tall
  * X (n x p) and Y (n x q) of types xtype/ytype (RR_F64, RR_F32, RR_BF16).
@@ -450,6 +479,19 @@ rr_status rr_pencil_eig(int64_t b, const double* H, const double* G, double* the
 rr_status rr_pencil_svd(int64_t b1, int64_t b2, const double* B, const double* Gu,
                         const double* Gv, double* s, double* Y, double* Z, void* ws,
                         size_t ws_bytes, int32_t* dropped, void* stream);
+
+/* Matrix-free product with a kernel operator (RR_KERNEL):
+ *   Y (rows x b) = op(A) X (+ coef_j R(:, j)),  op(A) = A (trans = 0, rows = m)
+ *   or A^T (trans = 1, rows = n); X (cols x b, xtype RR_BF16 / RR_F32 /
+ *   RR_F64, ld ldx), Y of otype RR_F32 or RR_F64 (ld ldy), R FP64 and coef
+ *   (b FP64) may be NULL.  Every entry of A is evaluated where it is used
+ *   (one exponential, d differences) and never stored; FP32 evaluation and
+ *   accumulation when xtype and otype are 32-bit or narrower, FP64 when
+ *   either is RR_F64.  RR_ERR_ARG: not a valid RR_KERNEL operator, bad sizes
+ *   or types. */
+rr_status rr_kernel_apply(int32_t trans, const rr_operator* A, int64_t b, int32_t xtype, const void* X,
+                          int64_t ldx, int32_t otype, void* Y, int64_t ldy, const double* R, int64_t ldr,
+                          const double* coef, void* stream);
 
 /* Sparse block product (a CSR operator applied to a block; Sec. 5.1 CSR):
  * Y (n x b, FP32 out, ld ldy) = A X with A CSR FP32, X (n x b, dtype xtype

@@ -13,9 +13,10 @@ c_i32p = ctypes.POINTER(ctypes.c_int32)
 
 
 class RR:
-    F64, F32, BF16, E4M3 = 0, 1, 2, 3
+    F64, F32, BF16, E4M3, F16 = 0, 1, 2, 3, 4
+    MGS_L, MGS_R, CGS, CGS2, HESS_L, HESS_R = range(6)
     OK, ERR_ARG, ERR_CUDA, ERR_NOT_SPD, ERR_NO_CONV, ERR_TIMEOUT, ERR_WORKSPACE, ERR_NAN = range(8)
-    DENSE, CSR = 0, 1
+    DENSE, CSR, KERNEL = 0, 1, 2
     LARGEST, SMALLEST = 0, 1
     POWER, CHEBYSHEV = 0, 1
     NAMES = {0: "RR_OK", 1: "RR_ERR_ARG", 2: "RR_ERR_CUDA", 3: "RR_ERR_NOT_SPD",
@@ -30,7 +31,8 @@ class RrError(RuntimeError):
 
 class RrOperator(ctypes.Structure):
     _fields_ = [("kind", c_i32), ("dtype", c_i32), ("m", c_i64), ("n", c_i64), ("ld", c_i64),
-                ("nnz", c_i64), ("values", c_vp), ("row_ptr", c_vp), ("col_idx", c_vp)]
+                ("nnz", c_i64), ("values", c_vp), ("row_ptr", c_vp), ("col_idx", c_vp), ("points_y", c_vp),
+                ("kparams", c_dbl * 3)]
 
 
 class RrParams(ctypes.Structure):
@@ -97,6 +99,10 @@ _SIGS = {
     "rr_krylov_workspace_size": (c_sz, [c_i64, c_i32, c_i32, c_i32]),
     "rr_krylov_eig": (c_i32, [ctypes.POINTER(RrOperator), c_i32, c_i32, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp,
                               c_vp, c_sz, c_vp]),
+    "rr_kernel_apply": (c_i32, [c_i32, ctypes.POINTER(RrOperator), c_i64, c_i32, c_vp, c_i64, c_i32, c_vp, c_i64,
+                                c_vp, c_i64, c_vp, c_vp]),
+    "rr_basis_builder_workspace_size": (c_sz, [c_i32, c_i32, c_i64, c_i64]),
+    "rr_basis_builder": (c_i32, [c_i32, c_i32, c_i64, c_i64, c_vp, c_i64, c_vp, c_vp, c_vp, c_sz, c_vp]),
     "rr_gram_noalloc": (c_i32, [c_i64, c_i64, c_i64, c_i32, c_vp, c_i64, c_i32, c_vp, c_i64, c_vp, c_i64,
                                 c_i32, c_vp]),
     "rr_pencil_workspace_size": (c_sz, [c_i64, c_i64]),

@@ -13,9 +13,9 @@ import torch
 from ._lib import RR, RrBatchTuning, RrError, RrInfo, RrOperator, RrParams, check, lib
 
 __all__ = [
-    "fortran", "ld_of", "dense_operator", "csr_operator", "make_params", "rr_eig", "rr_svd",
+    "fortran", "ld_of", "dense_operator", "csr_operator", "kernel_operator", "rr_kernel_apply", "make_params", "rr_eig", "rr_svd",
     "rr_batch_svd", "rr_colscale_cast", "rr_cast_operator", "rr_split_operator", "rr_lift", "rr_gemm_lowp", "rr_gemm_f64",
-    "rr_hessenberg", "rr_hessenberg_blocked", "rr_krylov_hessenberg", "rr_krylov_eig", "rr_wait_selftest", "rr_gram", "rr_gram_noalloc", "rr_pencil_eig", "rr_pencil_svd", "rr_csr_spmm",
+    "rr_hessenberg", "rr_hessenberg_blocked", "rr_basis_builder", "rr_krylov_hessenberg", "rr_krylov_eig", "rr_wait_selftest", "rr_gram", "rr_gram_noalloc", "rr_pencil_eig", "rr_pencil_svd", "rr_csr_spmm",
     "rr_chebyshev_step", "rr_chebyshev_step_rows", "rr_quantize_e4m3", "rr_gemm_e4m3", "rr_conv3x3_forward", "rr_conv3x3_backward", "rr_relu_mask", "rr_procrustes_grad",
     "rr_adam", "rr_net_block", "RrParams", "RrOperator", "RrInfo", "DTYPES",
 ]
@@ -75,6 +75,32 @@ def csr_operator(row_ptr: torch.Tensor, col_idx: torch.Tensor, values: torch.Ten
                     col_idx.data_ptr())
     op._keep = (row_ptr, col_idx, values)
     return op
+
+
+def kernel_operator(X: torch.Tensor, f: float, l: float, s: float = 0.0, Y: torch.Tensor = None) -> RrOperator:
+    """The matrix-free Gaussian kernel operator A(i, j) = f (exp(-|x_i - y_j|^2 /
+    (2 l^2)) + s [i == j]) over the rows of X (m x d FP64; Y n x d, or None for
+    the square symmetric operator over X)."""
+    if X.dtype != torch.float64 or (Y is not None and Y.dtype != torch.float64):
+        raise ValueError("kernel points must be FP64")
+    Xf = fortran(X)
+    Yf = fortran(Y) if Y is not None else None
+    n = Y.shape[0] if Y is not None else X.shape[0]
+    op = RrOperator(RR.KERNEL, RR.F64, X.shape[0], n, ld_of(Xf), X.shape[1], Xf.data_ptr(), None, None,
+                    Yf.data_ptr() if Yf is not None else None)
+    op.kparams[0], op.kparams[1], op.kparams[2] = f, l, s
+    op._keep = (Xf, Yf)
+    return op
+
+
+def rr_kernel_apply(op: RrOperator, X, trans=False, out_dtype=torch.float32, stream=None):
+    """Y = op(A) X for a kernel operator (matrix-free)."""
+    rows = op.n if trans else op.m
+    Y = empty_f(rows, X.shape[1], out_dtype, X.device)
+    check("rr_kernel_apply", lib().rr_kernel_apply(int(trans), ctypes.byref(op), X.shape[1], DTYPES[X.dtype], _p(X),
+                                                   ld_of(X), DTYPES[out_dtype], _p(Y), ld_of(Y), None, 0, None,
+                                                   _stream(stream)))
+    return Y
 
 
 def make_params(k, block, degree, max_sweeps, tol, basis="bf16", v0=None, filter=RR.POWER,
@@ -324,6 +350,26 @@ def rr_krylov_eig(op: RrOperator, v0, m, restarts, k, dtype=torch.float64, strea
     check("rr_krylov_eig", L.rr_krylov_eig(ctypes.byref(op), m, restarts, k, DTYPES[dtype], _p(v0), _p(theta), _p(X),
                                            _p(res), _p(ws), ws.numel(), _stream(stream)))
     return theta, X, res
+
+
+BUILDERS = {"mgs_l": RR.MGS_L, "mgs_r": RR.MGS_R, "cgs": RR.CGS, "cgs2": RR.CGS2, "hess_l": RR.HESS_L,
+            "hess_r": RR.HESS_R}
+
+
+def rr_basis_builder(W, method, want_r=True, stream=None):
+    """One of the comparator basis builders on W (FP64 / FP32 / FP16, modified
+    in place into the basis Q).  Returns (Q, R or None, piv or None)."""
+    n, k = W.shape
+    m = BUILDERS[method] if isinstance(method, str) else method
+    storage = {torch.float64: RR.F64, torch.float32: RR.F32, torch.float16: RR.F16}[W.dtype]
+    L = lib()
+    ws = _ws(L.rr_basis_builder_workspace_size(m, storage, n, k), W.device)
+    hess = m in (RR.HESS_L, RR.HESS_R)
+    R = fortran(torch.zeros(k, k, dtype=torch.float64, device=W.device)) if (want_r and not hess) else None
+    piv = torch.empty(k, dtype=torch.int32, device=W.device) if hess else None
+    check("rr_basis_builder", L.rr_basis_builder(m, storage, n, k, _p(W), ld_of(W), _p(R), _p(piv), _p(ws),
+                                                 ws.numel(), _stream(stream)))
+    return W, R, piv
 
 
 def rr_gram(X, Y, G=None, accumulate=False, stream=None):

@@ -47,19 +47,42 @@ __global__ void k_kh_load(int64_t n, const double* __restrict__ v, T* __restrict
     w[i] = (T)v[i];
 }
 
-// h_ij = w^(i-1)(pi_i) for i < j1 by forward substitution (one thread),
-// written to c[i] and to column `hcol` of H (FP64)
+// h_ij = w^(i-1)(pi_i) for i < j1 by forward substitution, written to c[i]
+// and to column `hcol` of H (FP64).  The pivot rows' entries Pr[i][l] =
+// v_l(pi_i), l < i, kept compactly (k x k, row i at Pr + i k), and w at the
+// pivot rows are staged in shared memory by the block; one thread then runs
+// the sequential substitution.
 template <typename T>
-__global__ void k_kh_coeffs(int j1, const T* __restrict__ V, int64_t ldv, const int* __restrict__ piv,
+__global__ void k_kh_coeffs(int j1, int k, const T* __restrict__ Pr, const int* __restrict__ piv,
                             const T* __restrict__ w, T* __restrict__ c, double* __restrict__ Hcol) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  extern __shared__ unsigned char kh_smem[];
+  T* sP = reinterpret_cast<T*>(kh_smem);      // [j1][j1]
+  T* sw = sP + (size_t)j1 * j1;               // [j1]
+  for (int e = threadIdx.x; e < j1 * j1; e += blockDim.x) {
+    const int i = e / j1, l = e % j1;
+    sP[e] = l < i ? Pr[(size_t)i * k + l] : T(0);
+  }
+  for (int i = threadIdx.x; i < j1; i += blockDim.x) sw[i] = w[piv[i]];
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  T* sc = sw;  // c_i overwrites w(pi_i) once it is known
   for (int i = 0; i < j1; ++i) {
-    const int p = piv[i];
-    T ci = w[p];
-    for (int l = 0; l < i; ++l) ci = ksub<T>(ci, kmul<T>(c[l], V[p + (int64_t)l * ldv]));
+    T ci = sw[i];
+    const T* row = sP + (size_t)i * j1;
+    for (int l = 0; l < i; ++l) ci = ksub<T>(ci, kmul<T>(sc[l], row[l]));
+    sc[i] = ci;
     c[i] = ci;
     Hcol[i] = (double)ci;
   }
+}
+
+// after pivot pi_j of the new vector v_j is known: Pr[j][l] = v_l(pi_j),
+// l < j (the new pivot row's entries in the earlier vectors)
+template <typename T>
+__global__ void k_kh_pivot_row(int j, int k, const T* __restrict__ V, int64_t ldv, const int* __restrict__ piv,
+                               T* __restrict__ Pr) {
+  const int p = piv[j];
+  for (int l = threadIdx.x; l < j; l += blockDim.x) Pr[(size_t)j * k + l] = V[p + (int64_t)l * ldv];
 }
 
 // w(r) <- w(r) - sum_{i < j1} c_i v_i(r) (in order), and the per-CTA argmax
@@ -74,7 +97,16 @@ __global__ void __launch_bounds__(kKhThreads) k_kh_update(int64_t n, int j1, con
   int64_t bi = INT64_MAX;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     T t = w[i];
-    for (int l = 0; l < j1; ++l) t = ksub<T>(t, kmul<T>(c[l], V[i + (int64_t)l * ldv]));
+    // the loads of 8 columns go out before their ordered subtractions
+    int l = 0;
+    for (; l + 8 <= j1; l += 8) {
+      T v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = V[i + (int64_t)(l + u) * ldv];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) t = ksub<T>(t, kmul<T>(c[l + u], v[u]));
+    }
+    for (; l < j1; ++l) t = ksub<T>(t, kmul<T>(c[l], V[i + (int64_t)l * ldv]));
     w[i] = t;
     const T a = fabs(t);
     if (a > bv) {
@@ -110,17 +142,39 @@ __global__ void __launch_bounds__(kKhThreads) k_kh_update(int64_t n, int j1, con
 
 // pivot of the new vector from the per-CTA partials (first index on ties);
 // piv[j] = row, H(j, j-1) = w(row) (skipped when j == 0), *pw = w(row)
+// (one CTA of 256 threads: strided partials, then warp and block merges)
 template <typename T>
-__global__ void k_kh_pivot(int nparts, const T* __restrict__ pv, const int64_t* __restrict__ pi,
-                           const T* __restrict__ w, int j, int* __restrict__ piv, double* __restrict__ Hsub,
-                           T* __restrict__ pw) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__global__ void __launch_bounds__(256) k_kh_pivot(int nparts, const T* __restrict__ pv, const int64_t* __restrict__ pi,
+                                                  const T* __restrict__ w, int j, int* __restrict__ piv,
+                                                  double* __restrict__ Hsub, T* __restrict__ pw) {
+  __shared__ T rv[8];
+  __shared__ int64_t ri[8];
   T bv = T(-1);
   int64_t bi = INT64_MAX;
-  for (int q = 0; q < nparts; ++q)
+  for (int q = threadIdx.x; q < nparts; q += blockDim.x)
     if (pv[q] > bv || (pv[q] == bv && pi[q] < bi)) {
       bv = pv[q];
       bi = pi[q];
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+    const int64_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ov > bv || (ov == bv && oi < bi)) {
+      bv = ov;
+      bi = oi;
+    }
+  }
+  if ((threadIdx.x & 31) == 0) {
+    rv[threadIdx.x >> 5] = bv;
+    ri[threadIdx.x >> 5] = bi;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int q = 1; q < (int)(blockDim.x >> 5); ++q)
+    if (rv[q] > bv || (rv[q] == bv && ri[q] < bi)) {
+      bv = rv[q];
+      bi = ri[q];
     }
   const int r = bi == INT64_MAX ? 0 : (int)bi;
   piv[j] = r;
@@ -140,7 +194,7 @@ template <typename T>
 size_t kh_ws_bytes(int64_t n, int k) {
   const int nparts = 8 * 160;
   return align_up((size_t)n * sizeof(T)) + align_up((size_t)k * sizeof(T)) + align_up(nparts * sizeof(T)) +
-         align_up(nparts * sizeof(int64_t)) + align_up(sizeof(T)) + 256;
+         align_up(nparts * sizeof(int64_t)) + align_up(sizeof(T)) + align_up((size_t)k * k * sizeof(T)) + 256;
 }
 
 template <typename T>
@@ -154,14 +208,19 @@ rr_status kh_run(cudaStream_t s, int64_t n, int k, const int32_t* rp, const int3
   T* pv = ar.take<T>(8 * 160);
   int64_t* pi = ar.take<int64_t>(8 * 160);
   T* pw = ar.take<T>(1);
+  T* Pr = ar.take<T>((size_t)k * k);
   if (nparts > 8 * 160) return RR_ERR_ARG;
+  const size_t csm = ((size_t)k * k + k) * sizeof(T);
+  if (csm > 227 * 1024) return RR_ERR_ARG;
+  if (csm > 48 * 1024)
+    RR_CUDA(cudaFuncSetAttribute(k_kh_coeffs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
   const int32_t dt = sizeof(T) == 8 ? RR_F64 : RR_F32;
   const unsigned g = (unsigned)nparts;
   RR_CUDA(cudaMemsetAsync(H, 0, (size_t)k * k * sizeof(double), s));
   // v_1 = v / v(pivot)
   k_kh_load<T><<<g, kKhThreads, 0, s>>>(n, v, w);
   k_kh_update<T><<<g, kKhThreads, 0, s>>>(n, 0, V, ldv, c, w, pv, pi);  // no subtraction: argmax only
-  k_kh_pivot<T><<<1, 32, 0, s>>>(nparts, pv, pi, w, 0, piv, nullptr, pw);
+  k_kh_pivot<T><<<1, 256, 0, s>>>(nparts, pv, pi, w, 0, piv, nullptr, pw);
   k_kh_scale<T><<<g, kKhThreads, 0, s>>>(n, w, pw, V);
   note_launches(4);
   for (int j = 0; j < k; ++j) {
@@ -169,13 +228,51 @@ rr_status kh_run(cudaStream_t s, int64_t n, int k, const int32_t* rp, const int3
     RR_TRY(rr_csr_spmm(n, 1, rp, ci, va, dt, V + (int64_t)j * ldv, ldv, dt, AV + (int64_t)j * ldv, ldv, s));
     if (j + 1 == k) break;
     RR_CUDA(cudaMemcpyAsync(w, AV + (int64_t)j * ldv, (size_t)n * sizeof(T), cudaMemcpyDeviceToDevice, s));
-    k_kh_coeffs<T><<<1, 32, 0, s>>>(j + 1, V, ldv, piv, w, c, H + (int64_t)j * k);
-    k_kh_update<T><<<g, kKhThreads, 0, s>>>(n, j + 1, V, ldv, c, w, pv, pi);
-    k_kh_pivot<T><<<1, 32, 0, s>>>(nparts, pv, pi, w, j + 1, piv, H + (int64_t)j * k + j + 1, pw);
-    k_kh_scale<T><<<g, kKhThreads, 0, s>>>(n, w, pw, V + (int64_t)(j + 1) * ldv);
-    note_launches(4);
+    const int j1 = j + 1;
+    k_kh_coeffs<T><<<1, 256, ((size_t)j1 * j1 + j1) * sizeof(T), s>>>(j1, k, Pr, piv, w, c, H + (int64_t)j * k);
+    k_kh_update<T><<<g, kKhThreads, 0, s>>>(n, j1, V, ldv, c, w, pv, pi);
+    k_kh_pivot<T><<<1, 256, 0, s>>>(nparts, pv, pi, w, j1, piv, H + (int64_t)j * k + j1, pw);
+    k_kh_scale<T><<<g, kKhThreads, 0, s>>>(n, w, pw, V + (int64_t)j1 * ldv);
+    k_kh_pivot_row<T><<<1, 128, 0, s>>>(j1, k, V, ldv, piv, Pr);
+    note_launches(5);
   }
   return check_launch("krylov_hessenberg");
+}
+
+// Left-looking Hessenberg process on a block (the Hess-L comparator of
+// Table 3): column j takes all earlier columns' eliminations at once when it
+// is reached (coefficients by forward substitution at the earlier pivot rows,
+// then the ordered subtraction), then its argmax and scaling -- the Krylov
+// process's step with the next column of W in place of A v_j.  In place: W
+// becomes Q.  No column skip (the comparator is timed on full-rank blocks).
+template <typename T>
+rr_status hess_left_t(cudaStream_t s, int64_t n, int k, T* W, int64_t ldw, int* piv, void* ws, size_t ws_bytes) {
+  if (ws_bytes < kh_ws_bytes<T>(n, k) + align_up((size_t)k * k * sizeof(double)) || !ws) return RR_ERR_WORKSPACE;
+  Arena ar(ws, ws_bytes);
+  ar.take<T>(n);
+  T* c = ar.take<T>(k);
+  const int nparts = (int)std::min<int64_t>((n + kKhThreads - 1) / kKhThreads, 8 * (int64_t)num_sms());
+  T* pv = ar.take<T>(8 * 160);
+  int64_t* pi = ar.take<int64_t>(8 * 160);
+  T* pw = ar.take<T>(1);
+  T* Pr = ar.take<T>((size_t)k * k);
+  double* H = ar.take<double>((size_t)k * k);
+  const size_t csm = ((size_t)k * k + k) * sizeof(T);
+  if (csm > 227 * 1024) return RR_ERR_ARG;
+  if (csm > 48 * 1024)
+    RR_CUDA(cudaFuncSetAttribute(k_kh_coeffs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
+  const unsigned g = (unsigned)nparts;
+  for (int j = 0; j < k; ++j) {
+    T* wj = W + (int64_t)j * ldw;
+    if (j > 0)
+      k_kh_coeffs<T><<<1, 256, ((size_t)j * j + j) * sizeof(T), s>>>(j, k, Pr, piv, wj, c, H + (int64_t)j * k);
+    k_kh_update<T><<<g, kKhThreads, 0, s>>>(n, j, W, ldw, c, wj, pv, pi);
+    k_kh_pivot<T><<<1, 256, 0, s>>>(nparts, pv, pi, wj, j, piv, nullptr, pw);
+    k_kh_scale<T><<<g, kKhThreads, 0, s>>>(n, wj, pw, wj);
+    k_kh_pivot_row<T><<<1, 128, 0, s>>>(j, k, W, ldw, piv, Pr);
+    note_launches(5);
+  }
+  return check_launch("hess_left");
 }
 
 // H (b x b) <- (H + H^T) / 2 in place (one thread per entry pair)
@@ -246,6 +343,20 @@ static bool carve_krylov(Arena& ar, int64_t n, int m, int k, int32_t arith, Kryl
 }
 
 }  // namespace
+}  // namespace rr
+
+namespace rr {
+size_t hess_left_ws_bytes(int64_t n, int64_t k, int32_t arith) {
+  return (arith == RR_F64 ? kh_ws_bytes<double>(n, (int)k) : kh_ws_bytes<float>(n, (int)k)) +
+         align_up((size_t)k * k * sizeof(double)) + 256;
+}
+rr_status hess_left_run(cudaStream_t s, int32_t arith, int64_t n, int64_t k, void* W, int64_t ldw, int* piv,
+                        void* ws, size_t ws_bytes) {
+  if (k > 335) return RR_ERR_ARG;  // the pivot-row triangle in shared memory
+  if (arith == RR_F64) return hess_left_t<double>(s, n, (int)k, (double*)W, ldw, piv, ws, ws_bytes);
+  if (arith == RR_F32) return hess_left_t<float>(s, n, (int)k, (float*)W, ldw, piv, ws, ws_bytes);
+  return RR_ERR_ARG;
+}
 }  // namespace rr
 
 using namespace rr;

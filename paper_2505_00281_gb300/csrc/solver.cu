@@ -27,6 +27,7 @@ namespace rr {
 
 struct Op {
   int kind;
+  const rr_operator* kop;  // RR_KERNEL: the caller's operator (points, parameters)
   int64_t m, n;
   const double* A;
   int64_t lda;
@@ -151,6 +152,7 @@ struct StageScope {
 static rr_status apply_lowp(const Op& op, int64_t b, const void* X, int64_t ldx, void* out,
                             int64_t ldo, const double* R, int64_t ldr, const double* coef,
                             cudaStream_t s) {
+  if (op.kind == RR_KERNEL) return kernel_apply(s, op.kop, 0, b, op.dt, X, ldx, op.wt, out, ldo, R, ldr, coef);
   if (op.kind == RR_DENSE) {
     if (op.dt == RR_F64) {
       RR_TRY(rr_gemm_f64(0, op.m, b, op.n, op.A, op.lda, (const double*)X, ldx, (double*)out, ldo, 0, s));
@@ -180,6 +182,7 @@ static rr_status apply_ph1(const Op& op, int64_t b, const void* X, int64_t ldx, 
 static rr_status apply_lowp_T(const Op& op, int64_t b, const void* X, int64_t ldx, void* out,
                               int64_t ldo, const double* R, int64_t ldr, const double* coef,
                               cudaStream_t s) {
+  if (op.kind == RR_KERNEL) return kernel_apply(s, op.kop, 1, b, op.dt, X, ldx, op.wt, out, ldo, R, ldr, coef);
   if (op.kind != RR_DENSE) return RR_ERR_ARG;
   if (op.dt == RR_F64) {
     if (R) return RR_ERR_ARG;
@@ -217,6 +220,8 @@ static rr_status apply_lowp_T_split(const Op& op, int64_t b, const void* Xh, con
 // refinement), otherwise FP64 arithmetic (the all-FP64 mode, CSR operators).
 static rr_status apply_f64(const Op& op, int64_t b, const double* X, int64_t ldx, double* out,
                            int64_t ldo, cudaStream_t s) {
+  if (op.kind == RR_KERNEL)
+    return kernel_apply(s, op.kop, 0, b, RR_F64, X, ldx, RR_F64, out, ldo, nullptr, 0, nullptr);
   if (op.kind == RR_DENSE) {
     if (op.has_emu && b <= 256) return emu_gemm(s, op.emu, 0, b, X, ldx, out, ldo, op.emu_blk);
     return rr_gemm_f64(0, op.m, b, op.n, op.A, op.lda, X, ldx, out, ldo, 0, s);
@@ -225,6 +230,8 @@ static rr_status apply_f64(const Op& op, int64_t b, const double* X, int64_t ldx
 }
 static rr_status apply_f64_T(const Op& op, int64_t b, const double* X, int64_t ldx, double* out,
                              int64_t ldo, cudaStream_t s) {
+  if (op.kind == RR_KERNEL)
+    return kernel_apply(s, op.kop, 1, b, RR_F64, X, ldx, RR_F64, out, ldo, nullptr, 0, nullptr);
   if (op.kind != RR_DENSE) return RR_ERR_ARG;
   if (op.has_emu && op.emu.cols && b <= 256) return emu_gemm(s, op.emu, 1, b, X, ldx, out, ldo, op.emu_blk);
   return rr_gemm_f64(1, op.n, b, op.m, op.A, op.lda, X, ldx, out, ldo, 0, s);
@@ -333,8 +340,14 @@ static bool all_nan(const double* res, int k) {
 // stop with RR_ERR_NAN.  One read of the operator and one synchronisation.
 static rr_status check_operator_finite(const rr_operator* A, const Common& c, cudaStream_t s) {
   RR_CUDA(cudaMemsetAsync(c.piv, 0, sizeof(int), s));
-  const int64_t m = A->kind == RR_DENSE ? A->m : A->n;
-  RR_TRY(operator_nonfinite(s, A->kind, m, A->n, A->values, A->ld, A->nnz, c.piv));
+  if (A->kind == RR_KERNEL) {
+    // the points of both sides (m x d, n x d)
+    RR_TRY(operator_nonfinite(s, RR_DENSE, A->m, A->nnz, A->values, A->ld, 0, c.piv));
+    if (A->points_y) RR_TRY(operator_nonfinite(s, RR_DENSE, A->n, A->nnz, A->points_y, A->n, 0, c.piv));
+  } else {
+    const int64_t m = A->kind == RR_DENSE ? A->m : A->n;
+    RR_TRY(operator_nonfinite(s, A->kind, m, A->n, A->values, A->ld, A->nnz, c.piv));
+  }
   int h = 0;
   RR_CUDA(cudaMemcpyAsync(&h, c.piv, sizeof(int), cudaMemcpyDeviceToHost, s));
   RR_CUDA(cudaStreamSynchronize(s));
@@ -436,7 +449,8 @@ static void make_op(const rr_operator* A, int32_t basis, Op& op) {
   op.f8_rs = op.f8_cs = op.f8_bs = nullptr;
   op.f8_ldr = op.f8_ldc = 0;
   op.kind = A->kind;
-  op.m = A->kind == RR_DENSE ? A->m : A->n;
+  op.kop = A;
+  op.m = A->kind == RR_CSR ? A->n : A->m;
   op.n = A->n;
   op.A = (const double*)A->values;
   op.lda = A->ld;
@@ -1197,6 +1211,12 @@ static rr_status check_op(const rr_operator* A, bool svd) {
     if (A->dtype != RR_F64 || A->m <= 0 || A->n <= 0 || A->ld < A->m) return RR_ERR_ARG;
     if (svd && A->m < A->n) return RR_ERR_ARG;
     if (!svd && A->m != A->n) return RR_ERR_ARG;
+    return RR_OK;
+  }
+  if (A->kind == RR_KERNEL) {
+    RR_TRY(check_kernel_operator(A));
+    if (svd && A->m < A->n) return RR_ERR_ARG;
+    if (!svd && A->points_y) return RR_ERR_ARG;  // the eigensolver takes the symmetric operator
     return RR_OK;
   }
   if (A->kind == RR_CSR) {

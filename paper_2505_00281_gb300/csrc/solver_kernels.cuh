@@ -30,6 +30,15 @@ rr_status keep_frozen(cudaStream_t s, const int* frozen, int64_t m, int64_t n, i
                       const double* V, double* V2, const double* sig, double* sig2);
 rr_status operator_nonfinite(cudaStream_t s, int kind, int64_t m, int64_t n, const void* values, int64_t lda,
                              int64_t nnz, int* flag);
+// left-looking Hessenberg process on a block (k_krylov.cu)
+size_t hess_left_ws_bytes(int64_t n, int64_t k, int32_t arith);
+rr_status hess_left_run(cudaStream_t s, int32_t arith, int64_t n, int64_t k, void* W, int64_t ldw, int* piv,
+                        void* ws, size_t ws_bytes);
+// matrix-free Gaussian kernel operator (k_kernel.cu)
+rr_status kernel_apply(cudaStream_t s, const rr_operator* A, int trans, int64_t b, int32_t xtype, const void* X,
+                       int64_t ldx, int32_t otype, void* Y, int64_t ldy, const double* R, int64_t ldr,
+                       const double* coef);
+rr_status check_kernel_operator(const rr_operator* A);
 rr_status uniform_block(cudaStream_t s, int64_t n, int64_t b, uint64_t seed, double* V, int64_t ldv);
 rr_status cheb_coef_update(cudaStream_t s, int64_t b, const double* theta, const double* mu,
                            double alpha_next, double cshift, double beta_next, double* kappa,

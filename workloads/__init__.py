@@ -195,11 +195,30 @@ def conv_params(layers, seed: int):
     return out
 
 
+def kernel_points(n: int, seed: int, d: int = 2) -> np.ndarray:
+    """n points drawn uniformly from the cube of side sqrt(n) in d dimensions
+    (the square for d = 2: one point per unit area at every n), n x d FP64."""
+    return np.asfortranarray(_rng(seed).uniform(0.0, math.sqrt(n), size=(n, d)))
+
+
+def kernel_subset(n: int, m: int, seed: int) -> np.ndarray:
+    """m distinct indices of n points, drawn without replacement (the second
+    point set of the paper's kernel SVD: a random subset of the first)."""
+    return np.sort(_rng(seed).choice(n, size=m, replace=False))
+
+
 def gaussian_kernel(n: int, f: float, l: float, s: float, seed: int, d: int = 2) -> np.ndarray:
     """Gaussian kernel matrix A_ij = f (exp(-|x_i - x_j|^2 / (2 l^2)) + s delta_ij) over n points
     drawn uniformly from the square (d = 2) of side sqrt(n), the paper's kernel-matrix family
     (1000 points, f = 1 or 0.2, l = 1 ... 100, s = 0.01 or 0).  FP64, column-major."""
-    x = _rng(seed).uniform(0.0, math.sqrt(n), size=(n, d))
+    x = kernel_points(n, seed, d)
     d2 = np.sum((x[:, None, :] - x[None, :, :]) ** 2, axis=-1)
     return np.asfortranarray(f * (np.exp(-d2 / (2.0 * l * l)) + s * np.eye(n)))
+
+
+def gaussian_kernel_rect(x: np.ndarray, y: np.ndarray, f: float, l: float) -> np.ndarray:
+    """A_ij = f exp(-|x_i - y_j|^2 / (2 l^2)) between two point sets (the
+    kernel SVD setting), FP64 column-major."""
+    d2 = np.sum((x[:, None, :] - y[None, :, :]) ** 2, axis=-1)
+    return np.asfortranarray(f * np.exp(-d2 / (2.0 * l * l)))
 
