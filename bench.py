@@ -764,6 +764,11 @@ def run_stage(args):
         # FP32 FMA peak from the unit counts: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
         fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
         out["fp32"]["frac_of_fp32_fma_peak"] = out["fp32"]["tflops"] / fp32_peak
+        if args.products_only:
+            print(json.dumps({"stage": "kernel", "n": n, "block": bs, "products": out, "fp32_fma_peak_tflops": fp32_peak}))
+            torch.cuda.synchronize()
+            print("stage", args.stage, "done")
+            return 0
         p = rr.api.make_params(k, bs, 3, 40, 1e-10, basis="bf16", v0=None, seed=6501, refine=True, phase1_sweeps=2)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -872,6 +877,7 @@ def main():
     ap.add_argument("--grid", type=int, default=64, help="grid side for --stage warm")
     ap.add_argument("--points", type=int, default=65536, help="points of the kernel operator for --stage kernel")
     ap.add_argument("--quick", action="store_true", help="--stage builders: skip MGS-L at k = 400")
+    ap.add_argument("--products-only", action="store_true", help="--stage kernel: time the operator products only")
     ap.add_argument("--sweeps", type=int, default=60, help="sweep limit for --stage sparse")
     ap.add_argument("--count", type=int, default=512, help="problems for --stage batch")
     ap.add_argument("--batch-sweeps", type=int, default=12, help="sweeps of every problem for --stage batch")

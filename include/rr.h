@@ -409,8 +409,7 @@ rr_status rr_krylov_eig(const rr_operator* A, int32_t m, int32_t restarts, int32
  * R (k x k FP64, column-major, may be NULL): the Gram-Schmidt methods'
  * triangular factor (W = Q R).  piv (k int32, the Hessenberg methods,
  * required there): pivot rows.  Workspace: rr_basis_builder_workspace_size.
- * RR_ERR_ARG: bad method, storage or sizes (k <= n, k <= 4096; Hess-L
- * k <= 335). */
+ * RR_ERR_ARG: bad method, storage or sizes (k <= n, k <= 4096). */
 size_t rr_basis_builder_workspace_size(int32_t method, int32_t storage, int64_t n, int64_t k);
 rr_status rr_basis_builder(int32_t method, int32_t storage, int64_t n, int64_t k, void* W, int64_t ldw,
                            double* R, int32_t* piv, void* ws, size_t ws_bytes, void* stream);

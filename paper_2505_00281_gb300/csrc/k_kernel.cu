@@ -5,10 +5,12 @@
 // on a square operator whose two point sets are the same.  The product
 //   Y = op(A) X (+ coef_j R(:, j)),  op(A) = A or A^T
 // evaluates each entry where it is used and never stores A: a CTA takes 128
-// output rows, walks the columns in tiles of 32 points, computes the 128 x 32
-// tile of A in shared memory (each entry once: d subtractions and squares, one
-// exponential) and accumulates the tile times the matching 32 rows of X,
-// 2 rows x 16 output columns per thread (16-byte shared-memory loads of X).  Work per entry: one exponential and 2 b
+// or 256 output rows (64 or 32 output columns per pass), walks the
+// columns in tiles of 32 points (16 in FP64), computes that tile of A in
+// shared memory (each entry once: d subtractions and squares, one
+// exponential) and accumulates the tile times the matching rows of X, 2 rows
+// x 16 output columns per thread (16-byte shared-memory loads of X).  Small
+// grids split the points over CTAs and add their partial sums atomically.  Work per entry: one exponential and 2 b
 // multiply-adds, against 8 bytes per point row read once per tile: bound by
 // the exponential unit and the FMA pipe, not by memory.  FP32 evaluation for
 // the low-precision products, FP64 for the FP64-accurate ones.
@@ -22,10 +24,11 @@
 namespace rr {
 namespace {
 
-constexpr int kKR = 128;  // output rows per CTA (2 per thread)
+// output rows per CTA: 2 per thread, 256 / CG threads per column group
 // columns (points) per tile: 32 in FP32, 16 in FP64 (static shared memory)
 template <typename TC> constexpr int kcols() { return sizeof(TC) == 8 ? 16 : 32; }
-constexpr int kKB = 64;   // output columns per pass (16 per thread)
+// output columns per pass: 16 per thread, CG column groups (CG = 1, 2 or 4:
+// b up to 16, 32 or 64 per pass)
 constexpr int kKD = 8;    // largest point dimension
 
 template <typename T> __device__ __forceinline__ T kexp(T x);
@@ -67,13 +70,16 @@ __device__ __forceinline__ void ld16(const double* p, double (&v)[16]) {
   }
 }
 
-template <typename TC, typename TX, typename TO, int kKC = kcols<TC>()>
+template <typename TC, typename TX, typename TO, int CG, int kKC = kcols<TC>()>
 __global__ void __launch_bounds__(256) k_kernel_mv(int64_t rows, int64_t cols, int d, const double* __restrict__ P,
                                                    int64_t ldp, const double* __restrict__ Q, int64_t ldq, TC f,
                                                    TC inv2l2, TC shift, int square, int b, const TX* __restrict__ X,
                                                    int64_t ldx, TO* __restrict__ Y, int64_t ldy,
                                                    const double* __restrict__ R, int64_t ldr,
-                                                   const double* __restrict__ coef) {
+                                                   const double* __restrict__ coef, int64_t jspan) {
+  constexpr int TR = 256 / CG;      // threads per column group (rows / 2)
+  constexpr int kKR = 2 * TR;       // output rows per CTA
+  constexpr int kKB = 16 * CG;      // output columns per pass
   __shared__ TC sq[kKC][kKD];                       // the column tile's points
   __shared__ TC sa[kKC][kKR + 1];                   // A tile, transposed (column j, row r)
   __shared__ __align__(16) TC sx[kKC][kKB];         // X rows of the tile, this pass's columns
@@ -81,11 +87,13 @@ __global__ void __launch_bounds__(256) k_kernel_mv(int64_t rows, int64_t cols, i
   const int64_t r0 = (int64_t)blockIdx.x * kKR;
   const int c0 = blockIdx.y * kKB;
   const int nb = min(kKB, b - c0);
-  // this thread: rows r0 + lr and r0 + lr + 64, columns c0 + 16 cg .. + 15;
-  // it evaluates the A-tile entries of its two rows in tile columns cg + 4 t
-  const int lr = tid & 63, cg = tid >> 6;
+  // the points of this CTA's share of the columns (blockIdx.z of the split)
+  const int64_t jb = (int64_t)blockIdx.z * jspan, je = jb + jspan < cols ? jb + jspan : cols;
+  // this thread: rows r0 + lr and r0 + lr + TR, columns c0 + 16 cg .. + 15;
+  // it evaluates the A-tile entries of its two rows in tile columns cg + CG t
+  const int lr = tid % TR, cg = tid / TR;
   TC pr[2][kKD];
-  int64_t gr[2] = {r0 + lr, r0 + lr + 64};
+  int64_t gr[2] = {r0 + lr, r0 + lr + TR};
 #pragma unroll
   for (int h = 0; h < 2; ++h)
 #pragma unroll
@@ -95,8 +103,8 @@ __global__ void __launch_bounds__(256) k_kernel_mv(int64_t rows, int64_t cols, i
   for (int h = 0; h < 2; ++h)
 #pragma unroll
     for (int c = 0; c < 16; ++c) acc[h][c] = TC(0);
-  for (int64_t j0 = 0; j0 < cols; j0 += kKC) {
-    const int nc = cols - j0 < kKC ? (int)(cols - j0) : kKC;
+  for (int64_t j0 = jb; j0 < je; j0 += kKC) {
+    const int nc = je - j0 < kKC ? (int)(je - j0) : kKC;
     __syncthreads();
     for (int e = tid; e < kKC * d; e += 256) {
       const int j = e / d, t = e % d;
@@ -108,8 +116,8 @@ __global__ void __launch_bounds__(256) k_kernel_mv(int64_t rows, int64_t cols, i
     }
     __syncthreads();
 #pragma unroll
-    for (int t8 = 0; t8 < kKC / 4; ++t8) {
-      const int j = cg + 4 * t8;
+    for (int t8 = 0; t8 < kKC / CG; ++t8) {
+      const int j = cg + CG * t8;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         TC dist = TC(0);
@@ -122,14 +130,14 @@ __global__ void __launch_bounds__(256) k_kernel_mv(int64_t rows, int64_t cols, i
         }
         TC a = kexp<TC>(-dist * inv2l2);
         if (square && gr[h] == j0 + j) a += shift;
-        sa[j][lr + 64 * h] = (j < nc && gr[h] < rows) ? f * a : TC(0);
+        sa[j][lr + TR * h] = (j < nc && gr[h] < rows) ? f * a : TC(0);
       }
     }
     __syncthreads();
     for (int j = 0; j < nc; ++j) {
       TC xv[16];
       ld16(&sx[j][cg * 16], xv);
-      const TC a0 = sa[j][lr], a1 = sa[j][lr + 64];
+      const TC a0 = sa[j][lr], a1 = sa[j][lr + TR];
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
         acc[0][c] += a0 * xv[c];
@@ -145,21 +153,61 @@ __global__ void __launch_bounds__(256) k_kernel_mv(int64_t rows, int64_t cols, i
       const int col = c0 + cg * 16 + c;
       if (col >= b) break;
       TC v = acc[h][c];
+      if (gridDim.z > 1) {
+        // split over the points: partial sums added into Y, which the
+        // launcher initialised with the added term (or zero)
+        atomicAdd(Y + gr[h] + (int64_t)col * ldy, (TO)v);
+        continue;
+      }
       if (R && coef) v += (TC)(coef[col] * R[gr[h] + (int64_t)col * ldr]);
       Y[gr[h] + (int64_t)col * ldy] = (TO)v;
     }
   }
 }
 
+// Y(:, j) = coef_j R(:, j) or 0: the starting value of a split product
+template <typename TO>
+__global__ void k_kmv_init(int64_t rows, int64_t b, TO* __restrict__ Y, int64_t ldy, const double* __restrict__ R,
+                           int64_t ldr, const double* __restrict__ coef) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < rows * b; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % rows, j = e / rows;
+    Y[i + j * ldy] = (R && coef) ? (TO)(coef[j] * R[i + j * ldr]) : TO(0);
+  }
+}
+
+template <typename TC, typename TX, typename TO, int CG>
+rr_status launch_cg(cudaStream_t s, int64_t rows, int64_t cols, int d, const double* P, int64_t ldp, const double* Q,
+                    int64_t ldq, double f, double l, double shift, int square, int64_t b, const TX* X, int64_t ldx, TO* Y,
+                    int64_t ldy, const double* R, int64_t ldr, const double* coef) {
+  constexpr int kKR = 2 * (256 / CG), kKB = 16 * CG, KC = kcols<TC>();
+  const int64_t gx = (rows + kKR - 1) / kKR, gy = (b + kKB - 1) / kKB;
+  // split the points over CTAs until the grid covers the GPU twice
+  int64_t split = 1;
+  const int64_t want = 2 * (int64_t)num_sms();
+  while (gx * gy * split < want && split < 64 && cols / (split * 2) >= 4 * KC) split *= 2;
+  const int64_t jspan = ((cols + split - 1) / split + KC - 1) / KC * KC;
+  split = (cols + jspan - 1) / jspan;
+  if (split > 1) {
+    k_kmv_init<TO><<<(unsigned)std::min<int64_t>((rows * b + 255) / 256, 4096), 256, 0, s>>>(rows, b, Y, ldy, R, ldr,
+                                                                                          coef);
+    note_launches(1);
+  }
+  dim3 g((unsigned)gx, (unsigned)gy, (unsigned)split);
+  k_kernel_mv<TC, TX, TO, CG><<<g, 256, 0, s>>>(rows, cols, d, P, ldp, Q, ldq, (TC)f, (TC)(1.0 / (2.0 * l * l)),
+                                                (TC)shift, square, (int)b, X, ldx, Y, ldy, R, ldr, coef, jspan);
+  return check_launch("kernel operator product");
+}
+
+// column groups per pass from b: 32 columns (b <= 32), else 64 (static
+// shared memory keeps a CTA at 512 threads' worth of rows at most)
 template <typename TC, typename TX, typename TO>
 rr_status launch_kernel_mv(cudaStream_t s, int64_t rows, int64_t cols, int d, const double* P, int64_t ldp,
                            const double* Q, int64_t ldq, double f, double l, double shift, int square, int64_t b,
                            const TX* X, int64_t ldx, TO* Y, int64_t ldy, const double* R, int64_t ldr,
                            const double* coef) {
-  dim3 g((unsigned)((rows + kKR - 1) / kKR), (unsigned)((b + kKB - 1) / kKB));
-  k_kernel_mv<TC, TX, TO><<<g, 256, 0, s>>>(rows, cols, d, P, ldp, Q, ldq, (TC)f, (TC)(1.0 / (2.0 * l * l)),
-                                            (TC)shift, square, (int)b, X, ldx, Y, ldy, R, ldr, coef);
-  return check_launch("kernel operator product");
+  if (b <= 32)
+    return launch_cg<TC, TX, TO, 2>(s, rows, cols, d, P, ldp, Q, ldq, f, l, shift, square, b, X, ldx, Y, ldy, R, ldr, coef);
+  return launch_cg<TC, TX, TO, 4>(s, rows, cols, d, P, ldp, Q, ldq, f, l, shift, square, b, X, ldx, Y, ldy, R, ldr, coef);
 }
 
 template <typename TC, typename TX>

@@ -48,41 +48,38 @@ __global__ void k_kh_load(int64_t n, const double* __restrict__ v, T* __restrict
 }
 
 // h_ij = w^(i-1)(pi_i) for i < j1 by forward substitution, written to c[i]
-// and to column `hcol` of H (FP64).  The pivot rows' entries Pr[i][l] =
-// v_l(pi_i), l < i, kept compactly (k x k, row i at Pr + i k), and w at the
-// pivot rows are staged in shared memory by the block; one thread then runs
-// the sequential substitution.
+// and to column `hcol` of H (FP64).  Pr holds the pivot rows' entries
+// column-major, Pr[l k + i] = v_l(pi_i) for l < i.  The substitution runs by
+// columns of the triangle: once c_l is final, every later row i subtracts
+// c_l v_l(pi_i) (threads over i, one barrier per l), so each c_i sees
+// exactly the subtractions of the sequential loop in its order, with the
+// triangle's columns read coalesced from global memory.
 template <typename T>
 __global__ void k_kh_coeffs(int j1, int k, const T* __restrict__ Pr, const int* __restrict__ piv,
                             const T* __restrict__ w, T* __restrict__ c, double* __restrict__ Hcol) {
   extern __shared__ unsigned char kh_smem[];
-  T* sP = reinterpret_cast<T*>(kh_smem);      // [j1][j1]
-  T* sw = sP + (size_t)j1 * j1;               // [j1]
-  for (int e = threadIdx.x; e < j1 * j1; e += blockDim.x) {
-    const int i = e / j1, l = e % j1;
-    sP[e] = l < i ? Pr[(size_t)i * k + l] : T(0);
-  }
+  T* sw = reinterpret_cast<T*>(kh_smem);  // [j1]: w(pi_i), then c_i
   for (int i = threadIdx.x; i < j1; i += blockDim.x) sw[i] = w[piv[i]];
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  T* sc = sw;  // c_i overwrites w(pi_i) once it is known
-  for (int i = 0; i < j1; ++i) {
-    T ci = sw[i];
-    const T* row = sP + (size_t)i * j1;
-    for (int l = 0; l < i; ++l) ci = ksub<T>(ci, kmul<T>(sc[l], row[l]));
-    sc[i] = ci;
-    c[i] = ci;
-    Hcol[i] = (double)ci;
+  for (int l = 0; l + 1 < j1; ++l) {
+    const T cl = sw[l];
+    const T* col = Pr + (size_t)l * k;
+    for (int i = l + 1 + threadIdx.x; i < j1; i += blockDim.x) sw[i] = ksub<T>(sw[i], kmul<T>(cl, col[i]));
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < j1; i += blockDim.x) {
+    c[i] = sw[i];
+    Hcol[i] = (double)sw[i];
   }
 }
 
-// after pivot pi_j of the new vector v_j is known: Pr[j][l] = v_l(pi_j),
+// after pivot pi_j of the new vector v_j is known: Pr[l k + j] = v_l(pi_j),
 // l < j (the new pivot row's entries in the earlier vectors)
 template <typename T>
 __global__ void k_kh_pivot_row(int j, int k, const T* __restrict__ V, int64_t ldv, const int* __restrict__ piv,
                                T* __restrict__ Pr) {
   const int p = piv[j];
-  for (int l = threadIdx.x; l < j; l += blockDim.x) Pr[(size_t)j * k + l] = V[p + (int64_t)l * ldv];
+  for (int l = threadIdx.x; l < j; l += blockDim.x) Pr[(size_t)l * k + j] = V[p + (int64_t)l * ldv];
 }
 
 // w(r) <- w(r) - sum_{i < j1} c_i v_i(r) (in order), and the per-CTA argmax
@@ -210,10 +207,6 @@ rr_status kh_run(cudaStream_t s, int64_t n, int k, const int32_t* rp, const int3
   T* pw = ar.take<T>(1);
   T* Pr = ar.take<T>((size_t)k * k);
   if (nparts > 8 * 160) return RR_ERR_ARG;
-  const size_t csm = ((size_t)k * k + k) * sizeof(T);
-  if (csm > 227 * 1024) return RR_ERR_ARG;
-  if (csm > 48 * 1024)
-    RR_CUDA(cudaFuncSetAttribute(k_kh_coeffs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
   const int32_t dt = sizeof(T) == 8 ? RR_F64 : RR_F32;
   const unsigned g = (unsigned)nparts;
   RR_CUDA(cudaMemsetAsync(H, 0, (size_t)k * k * sizeof(double), s));
@@ -229,7 +222,7 @@ rr_status kh_run(cudaStream_t s, int64_t n, int k, const int32_t* rp, const int3
     if (j + 1 == k) break;
     RR_CUDA(cudaMemcpyAsync(w, AV + (int64_t)j * ldv, (size_t)n * sizeof(T), cudaMemcpyDeviceToDevice, s));
     const int j1 = j + 1;
-    k_kh_coeffs<T><<<1, 256, ((size_t)j1 * j1 + j1) * sizeof(T), s>>>(j1, k, Pr, piv, w, c, H + (int64_t)j * k);
+    k_kh_coeffs<T><<<1, 256, (size_t)j1 * sizeof(T), s>>>(j1, k, Pr, piv, w, c, H + (int64_t)j * k);
     k_kh_update<T><<<g, kKhThreads, 0, s>>>(n, j1, V, ldv, c, w, pv, pi);
     k_kh_pivot<T><<<1, 256, 0, s>>>(nparts, pv, pi, w, j1, piv, H + (int64_t)j * k + j1, pw);
     k_kh_scale<T><<<g, kKhThreads, 0, s>>>(n, w, pw, V + (int64_t)j1 * ldv);
@@ -257,15 +250,11 @@ rr_status hess_left_t(cudaStream_t s, int64_t n, int k, T* W, int64_t ldw, int* 
   T* pw = ar.take<T>(1);
   T* Pr = ar.take<T>((size_t)k * k);
   double* H = ar.take<double>((size_t)k * k);
-  const size_t csm = ((size_t)k * k + k) * sizeof(T);
-  if (csm > 227 * 1024) return RR_ERR_ARG;
-  if (csm > 48 * 1024)
-    RR_CUDA(cudaFuncSetAttribute(k_kh_coeffs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
   const unsigned g = (unsigned)nparts;
   for (int j = 0; j < k; ++j) {
     T* wj = W + (int64_t)j * ldw;
     if (j > 0)
-      k_kh_coeffs<T><<<1, 256, ((size_t)j * j + j) * sizeof(T), s>>>(j, k, Pr, piv, wj, c, H + (int64_t)j * k);
+      k_kh_coeffs<T><<<1, 256, (size_t)j * sizeof(T), s>>>(j, k, Pr, piv, wj, c, H + (int64_t)j * k);
     k_kh_update<T><<<g, kKhThreads, 0, s>>>(n, j, W, ldw, c, wj, pv, pi);
     k_kh_pivot<T><<<1, 256, 0, s>>>(nparts, pv, pi, wj, j, piv, nullptr, pw);
     k_kh_scale<T><<<g, kKhThreads, 0, s>>>(n, wj, pw, wj);
@@ -287,29 +276,53 @@ __global__ void k_symmetrize(int b, double* __restrict__ H) {
   }
 }
 
-// X(:, j) /= |X(:, j)|_2 (one CTA per column)
-__global__ void k_normalize_cols(int64_t n, double* __restrict__ X, int64_t ldx) {
-  double* x = X + (int64_t)blockIdx.x * ldx;
+// X(:, j) /= |X(:, j)|_2: CTA (j, chunk) writes the chunk's sum of squares,
+// then every CTA of the scaling pass sums its column's chunks (fixed order)
+constexpr int kNrmChunks = 64;
+__global__ void k_colnorm_parts(int64_t n, const double* __restrict__ X, int64_t ldx, double* __restrict__ parts) {
+  const double* x = X + (int64_t)blockIdx.x * ldx;
+  const int64_t per = (n + kNrmChunks - 1) / kNrmChunks;
+  const int64_t i0 = (int64_t)blockIdx.y * per, i1 = i0 + per < n ? i0 + per : n;
   double acc = 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) acc = fma(x[i], x[i], acc);
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) acc = fma(x[i], x[i], acc);
   __shared__ double red[32];
   acc = warp_sum(acc);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
-  if (threadIdx.x < 32) {
-    acc = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-    acc = warp_sum(acc);
-    if (threadIdx.x == 0) red[0] = acc > 0 ? 1.0 / sqrt(acc) : 0.0;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    parts[(size_t)blockIdx.x * kNrmChunks + blockIdx.y] = t;
+  }
+}
+__global__ void k_normalize_cols(int64_t n, double* __restrict__ X, int64_t ldx, const double* __restrict__ parts) {
+  __shared__ double sc;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int c = 0; c < kNrmChunks; ++c) t += parts[(size_t)blockIdx.x * kNrmChunks + c];
+    sc = t > 0 ? 1.0 / sqrt(t) : 0.0;
   }
   __syncthreads();
-  const double sc = red[0];
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) x[i] *= sc;
+  double* x = X + (int64_t)blockIdx.x * ldx;
+  for (int64_t i = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.y * blockDim.x)
+    x[i] *= sc;
+}
+
+// Ysel rows 0..m-1 (ld m) into a zero-padded (mp x k) copy (the lift's K must
+// be a multiple of 8 for the tensor-core path; the basis has zero columns
+// m..mp-1)
+__global__ void k_pad_rows(int m, int mp, int k, const double* __restrict__ Y, double* __restrict__ Yp) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= mp * k) return;
+  const int i = e % mp, j = e / mp;
+  Yp[e] = i < m ? Y[i + (size_t)j * m] : 0.0;
 }
 
 struct KrylovWs {
   void *V, *AV, *kh;
   size_t kh_bytes;
-  double *H, *P, *G, *Y, *th, *tsel, *Ysel, *X, *AX, *R, *ss;
+  int mp;  // m rounded up to 8 (columns of V: the extra ones stay zero)
+  double *H, *P, *G, *Y, *th, *tsel, *Ysel, *Ypad, *nparts, *X, *AX, *R, *ss;
   int* piv;
   void *gram_ws, *pen_ws, *lift_ws;
   size_t gram_bytes, pen_bytes, lift_bytes;
@@ -317,7 +330,8 @@ struct KrylovWs {
 
 static bool carve_krylov(Arena& ar, int64_t n, int m, int k, int32_t arith, KrylovWs& w) {
   const size_t es = arith == RR_F64 ? 8 : 4;
-  w.V = ar.take_bytes((size_t)n * m * es);
+  w.mp = (m + 7) / 8 * 8;
+  w.V = ar.take_bytes((size_t)n * w.mp * es);
   w.AV = ar.take_bytes((size_t)n * m * es);
   w.kh_bytes = arith == RR_F64 ? kh_ws_bytes<double>(n, m) : kh_ws_bytes<float>(n, m);
   w.kh = ar.take_bytes(w.kh_bytes);
@@ -328,6 +342,8 @@ static bool carve_krylov(Arena& ar, int64_t n, int m, int k, int32_t arith, Kryl
   w.th = ar.take<double>(m);
   w.tsel = ar.take<double>(m);
   w.Ysel = ar.take<double>((size_t)m * m);
+  w.Ypad = ar.take<double>((size_t)w.mp * k);
+  w.nparts = ar.take<double>((size_t)k * kNrmChunks);
   w.X = ar.take<double>((size_t)n * k);
   w.AX = ar.take<double>((size_t)n * k);
   w.R = ar.take<double>((size_t)n * k);
@@ -337,7 +353,7 @@ static bool carve_krylov(Arena& ar, int64_t n, int m, int k, int32_t arith, Kryl
   w.gram_ws = ar.take_bytes(w.gram_bytes);
   w.pen_bytes = rr_pencil_workspace_size(m, m);
   w.pen_ws = ar.take_bytes(w.pen_bytes);
-  w.lift_bytes = rr_lift_workspace_size(n, k, m);
+  w.lift_bytes = rr_lift_workspace_size(n, k, w.mp);
   w.lift_ws = ar.take_bytes(w.lift_bytes);
   return !ar.overflow;
 }
@@ -352,7 +368,6 @@ size_t hess_left_ws_bytes(int64_t n, int64_t k, int32_t arith) {
 }
 rr_status hess_left_run(cudaStream_t s, int32_t arith, int64_t n, int64_t k, void* W, int64_t ldw, int* piv,
                         void* ws, size_t ws_bytes) {
-  if (k > 335) return RR_ERR_ARG;  // the pivot-row triangle in shared memory
   if (arith == RR_F64) return hess_left_t<double>(s, n, (int)k, (double*)W, ldw, piv, ws, ws_bytes);
   if (arith == RR_F32) return hess_left_t<float>(s, n, (int)k, (float*)W, ldw, piv, ws, ws_bytes);
   return RR_ERR_ARG;
@@ -401,6 +416,9 @@ extern "C" rr_status rr_krylov_eig(const rr_operator* A, int32_t m, int32_t rest
   cudaStream_t s = as_stream(stream);
   const float* va = (const float*)A->values;
   const double* v = v0;
+  const size_t es = arith == RR_F64 ? 8 : 4;
+  if (w.mp > m)
+    RR_CUDA(cudaMemset2DAsync((char*)w.V + (size_t)m * n * es, n * es, 0, n * es, w.mp - m, s));
   for (int cyc = 0; cyc <= restarts; ++cyc) {
     // Alg. 7: the basis of K_m(A, v) and the raw products A V
     RR_TRY(rr_krylov_hessenberg(arith, n, m, A->row_ptr, A->col_idx, va, v, w.V, w.AV, n, w.H, w.piv, w.kh,
@@ -414,8 +432,13 @@ extern "C" rr_status rr_krylov_eig(const rr_operator* A, int32_t m, int32_t rest
     RR_TRY(select_eig(s, m, m, RR_LARGEST, w.th, w.Y, m, w.tsel, w.Ysel, m));
     // Ritz vectors of the k largest values (unit columns); the next cycle
     // restarts from the first
-    RR_TRY(rr_lift(n, k, arith, w.V, n, m, 0, nullptr, n, 0, w.Ysel, m, w.X, n, w.lift_ws, w.lift_bytes, stream));
-    k_normalize_cols<<<(unsigned)k, 256, 0, s>>>(n, w.X, n);
+    k_pad_rows<<<(unsigned)((w.mp * k + 255) / 256), 256, 0, s>>>(m, w.mp, k, w.Ysel, w.Ypad);
+    RR_TRY(check_launch("krylov pad"));
+    RR_TRY(rr_lift(n, k, arith, w.V, n, w.mp, 0, nullptr, n, 0, w.Ypad, w.mp, w.X, n, w.lift_ws, w.lift_bytes,
+                   stream));
+    k_colnorm_parts<<<dim3((unsigned)k, kNrmChunks), 256, 0, s>>>(n, w.X, n, w.nparts);
+    k_normalize_cols<<<dim3((unsigned)k, 64), 256, 0, s>>>(n, w.X, n, w.nparts);
+    note_launches(1);
     RR_TRY(check_launch("krylov normalize"));
     v = w.X;
   }
