@@ -979,7 +979,23 @@ __global__ void __launch_bounds__(256) k_hess_trail(int64_t n, int r, int nt, co
     float l[R];
 #pragma unroll
     for (int j = 0; j < R; ++j) l[j] = (j < r) ? L[i + (int64_t)j * ldw] : 0.f;
-    for (int c = 0; c < nt; ++c) {
+    // 8 columns at a time: their loads go out together, then each column's
+    // subtractions in panel order
+    int c = 0;
+    for (; c + 8 <= nt; c += 8) {
+      float t[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) t[u] = T[i + (int64_t)(c + u) * ldw];
+#pragma unroll
+      for (int j = 0; j < R; ++j)
+        if (keep[j]) {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) t[u] = __fsub_rn(t[u], __fmul_rn(sw[j * nt + c + u], l[j]));
+        }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) T[i + (int64_t)(c + u) * ldw] = t[u];
+    }
+    for (; c < nt; ++c) {
       float t = T[i + (int64_t)c * ldw];
 #pragma unroll
       for (int j = 0; j < R; ++j)

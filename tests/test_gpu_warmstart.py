@@ -157,11 +157,12 @@ def _problems(N, k, block, seeds):
 def test_trained_start_vs_random(rr):
     """Train on Ritz vectors of one family (H = -Lap + V_p, 64 x 64 grid, 16
     lowest pairs), then solve held-out members from the random start and from
-    the trained start.  The trained start must lower the Rayleigh-Ritz
-    residuals of the first projection (geometric mean over the held-out set)
-    and converge everywhere within one sweep of the random start on average.
-    Measured on a GB300: first-projection residual 0.57 (random) vs 0.41
-    (trained); sweeps to 1e-10 unchanged (15.1 vs 15.5)."""
+    the trained start.  Asserted: both converge everywhere, and the trained
+    start lowers the Rayleigh-Ritz residuals of the first projection
+    (geometric mean over the held-out set) -- the gain this network gives.
+    Reported, not asserted: sweeps and wall time to 1e-10, where the trained
+    start shows no gain (measured on a GB300: first-projection residual 0.57
+    random vs 0.41 trained; sweeps 15.25 vs 15.1)."""
     from paper_2505_00281_gb300 import warmstart as WS
     N, k, block, degree = 64, 16, 24, 10
     data = WS.eigen_targets(_problems(N, k, block, range(70000, 70048)), k, block, degree)
@@ -176,7 +177,7 @@ def test_trained_start_vs_random(rr):
         return float(np.exp(np.mean(np.log(v))))
     res1 = {a: gm([r[a]["res"][0] for r in rows]) for a in ("random", "learned")}
     sweeps = {a: float(np.mean([r[a]["sweeps"] for r in rows])) for a in ("random", "learned")}
-    print("first-projection residual", res1, "sweeps", sweeps)
+    ms = {a: float(np.mean([r[a]["ms"] for r in rows])) for a in ("random", "learned")}
+    print("first-projection residual", res1, "sweeps to 1e-10", sweeps, "ms per solve", ms)
     assert all(r[a]["n_converged"] == k for r in rows for a in ("random", "learned"))
-    assert res1["learned"] < res1["random"], (res1, sweeps)
-    assert sweeps["learned"] <= sweeps["random"] + 1.0, (res1, sweeps)
+    assert res1["learned"] < 0.9 * res1["random"], (res1, sweeps)
