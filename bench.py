@@ -182,11 +182,11 @@ def aggregate(seconds: float, converged: int, dist=None, device=None):
 
 
 # --------------------------------------------------------------------------- GPU arm
-# DRAM bytes per launch of k_gemm_bf16_tc, mean over every launch of one
-# solve of this workload (ncu dram__bytes_read.sum + dram__bytes_write.sum;
-# profiles/launches_dense_svd_16384x4096.md); None until captured for the
-# current kernel.
-TC_TRAFFIC_PER_LAUNCH = None
+# DRAM bytes per launch of k_gemm_bf16_tc, mean over the 250 launches of one
+# solve of this workload (ncu dram__bytes_read.sum + dram__bytes_write.sum, a
+# one-pass capture; profiles/ncu_gemm_bf16_tc_16384x4096x128.md); set to None
+# when the kernel changes until it is captured again.
+TC_TRAFFIC_PER_LAUNCH = 107.9e6
 
 
 def stage_roofline(info, peaks, src):

@@ -1086,6 +1086,7 @@ static rr_status eig_run(const rr_operator* Aop, const rr_params* p, double* the
   // ---------------- phase 2 ----------------
   if (refine && !nan_seen) {
     const int64_t b2 = 2 * b;
+    double prev_mx = INFINITY;
     for (;;) {
       STAGE(RR_STAGE_F64_PRODUCT, apply_f64(op, b, w.X, n, w.P, n, s));  // P = A X, FP64-accurate
       STAGE(RR_STAGE_OTHER, residual_block(s, n, b, w.P, n, w.X, n, w.theta, w.R, n, w.ss, 0));
@@ -1108,6 +1109,32 @@ static rr_status eig_run(const rr_operator* Aop, const rr_params* p, double* the
         break;
       }
       if (sweep >= p->max_sweeps) break;
+      // the corrections stopped contracting the residual (power filter): one
+      // sweep of the method in FP64-accurate arithmetic from the Ritz vectors
+      // (q products, each followed by Algorithm 8 in FP64, then Algorithm 3)
+      const bool stalled = !cheb && inf.refine_sweeps >= 1 && mx > 0.3 * prev_mx;
+      prev_mx = mx;
+      if (stalled) {
+        double* V = w.X2;
+        double* Wb = w.P;
+        RR_CUDA(cudaMemcpyAsync(V, w.X, (size_t)n * b * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        for (int it = 0; it < q; ++it) {
+          STAGE(RR_STAGE_F64_PRODUCT, apply_f64(op, b, V, n, Wb, n, s));
+          STAGE(RR_STAGE_HESSENBERG, basis_step(w.c, true, RR_F64, RR_F64, n, b, Wb, n, V, n, s));
+        }
+        STAGE(RR_STAGE_F64_PRODUCT, apply_f64(op, b, V, n, w.R, n, s));
+        STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, RR_F64, V, n, RR_F64, V, n, w.G, b, s));
+        STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, RR_F64, V, n, RR_F64, w.R, n, w.H, b, s));
+        STAGE(RR_STAGE_PENCIL, pencil_eig(w.c, b, w.H, w.G, w.th2, w.Y, s));
+        STAGE(RR_STAGE_PENCIL, select_eig(s, b, b, p->which, w.th2, w.Y, b, w.theta, w.Ysel, b));
+        STAGE(RR_STAGE_LIFT, lift2(op, s, n, b, RR_F64, V, n, b, 0, nullptr, 0, 0, w.Ysel, b, w.P, n));
+        RR_CUDA(cudaMemcpyAsync(w.X, w.P, (size_t)n * b * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        ++sweep;
+        ++inf.refine_sweeps;
+        ++inf.polish_sweeps;
+        prev_mx = INFINITY;
+        continue;
+      }
       if (cheb) {
         // D_1 = (s1/e) R;  D_{j+1} = (2 s_{j+1}/e)(A - cI) D_j - s_j s_{j+1} D_{j-1}
         //                           + (2 s_{j+1}/e) phi_j(theta) R
