@@ -469,18 +469,153 @@ static rr_status gram_dispatch_y(int32_t ytype, dim3 g, cudaStream_t s, int64_t 
 }  // namespace rr
 
 namespace rr {
+// FP32 Gram partials for tall blocks (the refinement's projection of the
+// Ritz vectors out of a correction block): a CTA takes a 64 x 64 tile of
+// X^T Y over one chunk of rows, 4 x 4 outputs per thread; the chunk's 32 rows
+// of both tiles are staged in shared memory row by row (a row's 64 values
+// contiguous), so a thread reads its 4 X and 4 Y values as two 16-byte loads
+// per 16 FMAs.  part[chunk][i + j p] (FP64, summed by k_gram_reduce).
+constexpr int kG32 = 64, kG32R = 32;
+__global__ void __launch_bounds__(256) k_gram32(int64_t n, int64_t p, int64_t q, const double* __restrict__ X,
+                                                int64_t ldx, const float* __restrict__ Y, int64_t ldy, int64_t rpc,
+                                                double* __restrict__ part) {
+  // rows padded by 4 floats: the column-wise staging stores meet 4-way
+  // instead of 32-way bank conflicts, the 16-byte row loads stay aligned
+  __shared__ __align__(16) float Xs[kG32R][kG32 + 4];
+  __shared__ __align__(16) float Ys[kG32R][kG32 + 4];
+  const int64_t p0 = (int64_t)blockIdx.x * kG32, q0 = (int64_t)blockIdx.y * kG32;
+  const int64_t r0 = (int64_t)blockIdx.z * rpc, r1 = r0 + rpc < n ? r0 + rpc : n;
+  const int tid = threadIdx.x, ti = tid & 15, tj = tid >> 4;  // outputs 4 ti.., 4 tj..
+  float acc[4][4] = {};
+  for (int64_t rs = r0; rs < r1; rs += kG32R) {
+    // stage: thread e loads row (e % 32) of column (e / 32) of both tiles (rows contiguous in HBM)
+    for (int e = tid; e < kG32R * kG32; e += 256) {
+      const int rr_ = e % kG32R, c = e / kG32R;
+      const int64_t row = rs + rr_;
+      Xs[rr_][c] = (row < r1 && p0 + c < p) ? (float)X[row + (p0 + c) * ldx] : 0.f;
+      Ys[rr_][c] = (row < r1 && q0 + c < q) ? Y[row + (q0 + c) * ldy] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int rr_ = 0; rr_ < kG32R; ++rr_) {
+      const float4 xv = reinterpret_cast<const float4*>(&Xs[rr_][0])[ti];
+      const float4 yv = reinterpret_cast<const float4*>(&Ys[rr_][0])[tj];
+      const float xa[4] = {xv.x, xv.y, xv.z, xv.w}, ya[4] = {yv.x, yv.y, yv.z, yv.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = fmaf(xa[a], ya[c], acc[a][c]);
+    }
+    __syncthreads();
+  }
+  double* out = part + (size_t)blockIdx.z * p * q;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int64_t i = p0 + 4 * ti + a, j = q0 + 4 * tj + c;
+      if (i < p && j < q) out[i + j * p] = (double)acc[a][c];
+    }
+}
+
+// The same partials with the whole p x q result in one CTA (p, q <= TP =
+// 16 PT): every row of X and Y is read once.  A thread owns PT x PT outputs
+// (rows ti + 16 a of G, columns PT tj ..); each staged row gives it PT X
+// values (conflict-free scalar shared loads) and PT Y values (broadcast
+// 8-byte loads) per PT^2 FMAs, and the next rows' global loads are issued
+// before the current rows are used.
+template <int PT>
+__global__ void __launch_bounds__(256, 1) k_gram32_full(int64_t n, int p, int q, const double* __restrict__ X,
+                                                        int64_t ldx, const float* __restrict__ Y, int64_t ldy,
+                                                        int64_t rpc, double* __restrict__ part) {
+  constexpr int TP = 16 * PT, R = 16;
+  __shared__ __align__(16) float Xs[R][TP + 2];
+  __shared__ __align__(16) float Ys[R][TP + 2];
+  const int64_t r0 = (int64_t)blockIdx.x * rpc, r1 = r0 + rpc < n ? r0 + rpc : n;
+  const int tid = threadIdx.x, ti = tid & 15, tj = tid >> 4;
+  float acc[PT][PT] = {};
+  // staging: R rows x TP columns of each operand, thread e -> (row e % R, column e / R)
+  constexpr int PER = R * TP / 256;
+  float xr[PER], yr[PER];
+  auto fetch = [&](int64_t rs) {
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = tid + 256 * u, rr_ = e % R, c = e / R;
+      const int64_t row = rs + rr_;
+      xr[u] = (row < r1 && c < p) ? (float)X[row + c * ldx] : 0.f;
+      yr[u] = (row < r1 && c < q) ? Y[row + c * ldy] : 0.f;
+    }
+  };
+  fetch(r0);
+  for (int64_t rs = r0; rs < r1; rs += R) {
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = tid + 256 * u, rr_ = e % R, c = e / R;
+      Xs[rr_][c] = xr[u];
+      Ys[rr_][c] = yr[u];
+    }
+    __syncthreads();
+    if (rs + R < r1) fetch(rs + R);  // in flight while the tile is used
+#pragma unroll 2
+    for (int rr_ = 0; rr_ < R; ++rr_) {
+      float xa[PT], ya[PT];
+#pragma unroll
+      for (int a = 0; a < PT; ++a) xa[a] = Xs[rr_][ti + 16 * a];
+#pragma unroll
+      for (int a = 0; a < PT; a += 2) {
+        const float2 yv = *reinterpret_cast<const float2*>(&Ys[rr_][PT * tj + a]);
+        ya[a] = yv.x;
+        ya[a + 1] = yv.y;
+      }
+#pragma unroll
+      for (int a = 0; a < PT; ++a)
+#pragma unroll
+        for (int c = 0; c < PT; ++c) acc[a][c] = fmaf(xa[a], ya[c], acc[a][c]);
+    }
+  }
+  double* out = part + (size_t)blockIdx.x * p * q;
+#pragma unroll
+  for (int a = 0; a < PT; ++a)
+#pragma unroll
+    for (int c = 0; c < PT; ++c) {
+      const int i = ti + 16 * a, j = PT * tj + c;
+      if (i < p && j < q) out[i + (int64_t)j * p] = (double)acc[a][c];
+    }
+}
+
 // G = X^T Y with FP32 products and FP32 accumulation per row chunk (chunk
 // sums added in FP64): for X FP64 (read as FP32) and Y FP32, where FP32
 // accuracy is all the caller needs.
 rr_status gram_f32acc(cudaStream_t s, int64_t n, int64_t p, int64_t q, const double* X, int64_t ldx,
                       const float* Y, int64_t ldy, double* G, int64_t ldg, void* ws, size_t ws_bytes) {
   if (p == 0 || q == 0) return RR_OK;
-  int64_t chunks = gram_chunks(n, p, q);
-  if (ws_bytes < (size_t)chunks * p * q * sizeof(double) || !ws) return RR_ERR_WORKSPACE;
+  if (!ws) return RR_ERR_WORKSPACE;
+  const int64_t fitc = (int64_t)(ws_bytes / ((size_t)p * q * sizeof(double)));
+  if (p <= 160 && q <= 160 && n >= 64 * 1024 && fitc >= num_sms()) {
+    // tall blocks: one CTA per row chunk holds the whole product
+    const int64_t chunks = num_sms();
+    const int64_t rpc = ((n + chunks - 1) / chunks + 15) / 16 * 16;
+    const int64_t used = (n + rpc - 1) / rpc;
+    if (p <= 128 && q <= 128)
+      k_gram32_full<8><<<(unsigned)used, 256, 0, s>>>(n, (int)p, (int)q, X, ldx, Y, ldy, rpc, (double*)ws);
+    else
+      k_gram32_full<10><<<(unsigned)used, 256, 0, s>>>(n, (int)p, (int)q, X, ldx, Y, ldy, rpc, (double*)ws);
+    RR_TRY(check_launch("gram_f32acc partial"));
+    k_gram_reduce<<<(unsigned)((p * q + 255) / 256), 256, 0, s>>>(p, q, used, (const double*)ws, G, ldg, 0);
+    return check_launch("gram_f32acc reduce");
+  }
+  const int64_t tiles = ((p + kG32 - 1) / kG32) * ((q + kG32 - 1) / kG32);
+  int64_t chunks = (2 * (int64_t)num_sms() + tiles - 1) / tiles;
+  const int64_t fit = (int64_t)(ws_bytes / ((size_t)p * q * sizeof(double)));
+  if (chunks > fit) chunks = fit;
+  if (chunks > (n + kG32R - 1) / kG32R) chunks = (n + kG32R - 1) / kG32R;
+  if (chunks < 1) return RR_ERR_WORKSPACE;
   int64_t rpc = (n + chunks - 1) / chunks;
+  rpc = (rpc + kG32R - 1) / kG32R * kG32R;
   chunks = (n + rpc - 1) / rpc;
-  dim3 g((unsigned)((p + GT - 1) / GT), (unsigned)((q + GT - 1) / GT), (unsigned)chunks);
-  k_gram_partial<double, float, float><<<g, 256, 0, s>>>(n, p, q, X, ldx, Y, ldy, rpc, (double*)ws);
+  dim3 g((unsigned)((p + kG32 - 1) / kG32), (unsigned)((q + kG32 - 1) / kG32), (unsigned)chunks);
+  k_gram32<<<g, 256, 0, s>>>(n, p, q, X, ldx, Y, ldy, rpc, (double*)ws);
   RR_TRY(check_launch("gram_f32acc partial"));
   k_gram_reduce<<<(unsigned)((p * q + 255) / 256), 256, 0, s>>>(p, q, chunks, (const double*)ws, G, ldg, 0);
   return check_launch("gram_f32acc reduce");

@@ -71,12 +71,152 @@ __global__ void __launch_bounds__(256) k_lift(int64_t n, int64_t b, int64_t p, c
   }
 }
 
-// T (n x b, FP32) -= X (n x p, FP64) * K (p x b), in FP32 arithmetic
+// T (n x b, FP32) -= X (n x p, FP64 read as FP32) K (p x b, FP64 read as
+// FP32), FP32 accumulation: a CTA takes 128 rows x 64 columns of T, 8 x 4
+// outputs per thread, the p dimension in steps of 32 staged in shared memory
+// (X rows contiguous per column, K columns contiguous per row) so a thread's
+// operands are three 16-byte loads per 32 FMAs.
+constexpr int kSL_M = 128, kSL_N = 64, kSL_K = 32;
+__global__ void __launch_bounds__(256) k_sub_lowrank32(int64_t n, int64_t b, int64_t p, const double* __restrict__ X,
+                                                       int64_t ldx, const double* __restrict__ K, int64_t ldk,
+                                                       float* __restrict__ T, int64_t ldt) {
+  __shared__ __align__(16) float Xs[kSL_K][kSL_M];
+  __shared__ __align__(16) float Ks[kSL_K][kSL_N + 4];  // padded: see k_gram32
+  const int64_t m0 = (int64_t)blockIdx.x * kSL_M, n0 = (int64_t)blockIdx.y * kSL_N;
+  const int tid = threadIdx.x, ti = tid & 15, tj = tid >> 4;  // rows 8 ti.., columns 4 tj..
+  float acc[8][4] = {};
+  for (int64_t k0 = 0; k0 < p; k0 += kSL_K) {
+    for (int e = tid; e < kSL_K * kSL_M; e += 256) {
+      const int r = e % kSL_M, kk = e / kSL_M;
+      Xs[kk][r] = (m0 + r < n && k0 + kk < p) ? (float)X[(m0 + r) + (k0 + kk) * ldx] : 0.f;
+    }
+    for (int e = tid; e < kSL_K * kSL_N; e += 256) {
+      const int kk = e % kSL_K, c = e / kSL_K;
+      Ks[kk][c] = (k0 + kk < p && n0 + c < b) ? (float)K[(k0 + kk) + (n0 + c) * ldk] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < kSL_K; ++kk) {
+      const float4 x0 = reinterpret_cast<const float4*>(&Xs[kk][0])[2 * ti];
+      const float4 x1 = reinterpret_cast<const float4*>(&Xs[kk][0])[2 * ti + 1];
+      const float4 kv = reinterpret_cast<const float4*>(&Ks[kk][0])[tj];
+      const float xa[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+      const float ka[4] = {kv.x, kv.y, kv.z, kv.w};
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = fmaf(xa[a], ka[c], acc[a][c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int64_t j = n0 + 4 * tj + c;
+    if (j >= b) continue;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int64_t i = m0 + 8 * ti + a;
+      if (i < n) T[i + j * ldt] -= acc[a][c];
+    }
+  }
+}
+
+// The same update for narrow T (b <= 16 CT): K (p x b) stays in shared memory
+// (FP32, row stride 16 CT + 1), and a persistent CTA walks tiles of 128 rows
+// holding all b columns, so X is read once.  Thread (ti, tj) owns rows
+// ti + 16 a (a < 8) and columns CT tj .. CT tj + CT - 1: the shared X loads are
+// conflict-free and each T store of a warp covers 16 consecutive rows.  The p
+// dimension goes in steps of 32, the next step's X loads issued before the
+// current step is used.
+constexpr int kSLF_M = 128, kSLF_K = 32;
+template <int CT>
+__global__ void __launch_bounds__(256, 1) k_sub_lowrank32_full(int64_t n, int b, int p, const double* __restrict__ X,
+                                                               int64_t ldx, const double* __restrict__ K, int64_t ldk,
+                                                               float* __restrict__ T, int64_t ldt) {
+  constexpr int TB = 16 * CT, KS = TB + 1;
+  extern __shared__ __align__(16) float sm_slf[];
+  float* Ks = sm_slf;                              // [p][KS]
+  float* Xs = sm_slf + (((size_t)p * KS + 3) & ~(size_t)3);  // [kSLF_K][kSLF_M]
+  const int tid = threadIdx.x, ti = tid & 15, tj = tid >> 4;
+  for (int e = tid; e < p * TB; e += 256) {
+    const int kk = e % p, c = e / p;
+    Ks[kk * KS + c] = c < b ? (float)K[kk + (int64_t)c * ldk] : 0.f;
+  }
+  const int64_t tiles = (n + kSLF_M - 1) / kSLF_M;
+  const int ksteps = (p + kSLF_K - 1) / kSLF_K;
+  constexpr int PER = kSLF_K * kSLF_M / 256;
+  float xr[PER];
+  auto fetch = [&](int64_t tile, int step) {
+    const int64_t m0 = tile * kSLF_M;
+    const int k0 = step * kSLF_K;
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = tid + 256 * u, r = e % kSLF_M, kk = e / kSLF_M;
+      xr[u] = (m0 + r < n && k0 + kk < p) ? (float)X[(m0 + r) + (int64_t)(k0 + kk) * ldx] : 0.f;
+    }
+  };
+  int64_t tile = blockIdx.x;
+  if (tile < tiles) fetch(tile, 0);
+  for (; tile < tiles; tile += gridDim.x) {
+    const int64_t m0 = tile * kSLF_M;
+    float acc[8][CT] = {};
+    for (int step = 0; step < ksteps; ++step) {
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < PER; ++u) Xs[tid + 256 * u] = xr[u];  // e = kk * M + r
+      __syncthreads();
+      if (step + 1 < ksteps)
+        fetch(tile, step + 1);
+      else if (tile + gridDim.x < tiles)
+        fetch(tile + gridDim.x, 0);
+      const int k0 = step * kSLF_K, kn = p - k0 < kSLF_K ? p - k0 : kSLF_K;
+#pragma unroll 2
+      for (int kk = 0; kk < kn; ++kk) {
+        float xa[8], ka[CT];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) xa[a] = Xs[kk * kSLF_M + ti + 16 * a];
+        const float* kr = Ks + (size_t)(k0 + kk) * KS + CT * tj;
+#pragma unroll
+        for (int c = 0; c < CT; ++c) ka[c] = kr[c];
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+          for (int c = 0; c < CT; ++c) acc[a][c] = fmaf(xa[a], ka[c], acc[a][c]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < CT; ++c) {
+      const int j = CT * tj + c;
+      if (j >= b) continue;
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const int64_t i = m0 + ti + 16 * a;
+        if (i < n) T[i + j * ldt] -= acc[a][c];
+      }
+    }
+  }
+}
+
+template <int CT>
+static rr_status launch_sub_lowrank32_full(cudaStream_t s, int64_t n, int64_t b, int64_t p, const double* X,
+                                           int64_t ldx, const double* K, int64_t ldk, float* T, int64_t ldt) {
+  const size_t smem = ((((size_t)p * (16 * CT + 1) + 3) & ~(size_t)3) + (size_t)kSLF_K * kSLF_M) * sizeof(float);
+  RR_CUDA(cudaFuncSetAttribute(k_sub_lowrank32_full<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int64_t tiles = (n + kSLF_M - 1) / kSLF_M;
+  const int64_t grid = tiles < num_sms() ? tiles : num_sms();
+  k_sub_lowrank32_full<CT><<<(unsigned)grid, 256, smem, s>>>(n, (int)b, (int)p, X, ldx, K, ldk, T, ldt);
+  return check_launch("sub_lowrank_f32 full");
+}
+
 rr_status sub_lowrank_f32(cudaStream_t s, int64_t n, int64_t b, int64_t p, const double* X, int64_t ldx,
                           const double* K, int64_t ldk, float* T, int64_t ldt) {
   if (n == 0 || b == 0 || p == 0) return RR_OK;
-  dim3 g((unsigned)((n + LBM - 1) / LBM), (unsigned)((b + LBN - 1) / LBN));
-  k_lift<double, float, float><<<g, 256, 0, s>>>(n, b, p, X, ldx, K, ldk, T, ldt, 1, -1.0);
+  if (b <= 160 && p <= 160 && n >= 64 * 1024) {
+    if (b <= 128) return launch_sub_lowrank32_full<8>(s, n, b, p, X, ldx, K, ldk, T, ldt);
+    return launch_sub_lowrank32_full<10>(s, n, b, p, X, ldx, K, ldk, T, ldt);
+  }
+  dim3 g((unsigned)((n + kSL_M - 1) / kSL_M), (unsigned)((b + kSL_N - 1) / kSL_N));
+  k_sub_lowrank32<<<g, 256, 0, s>>>(n, b, p, X, ldx, K, ldk, T, ldt);
   return check_launch("sub_lowrank_f32");
 }
 

@@ -203,12 +203,14 @@ static void gemm_mixed(cudaStream_t s, int ta, int tb, int M, int N, int K, doub
   k_gemm_small<float, 256><<<g, 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, 0, 1, K);
 }
 
-// Symmetrise C, shift it to positive definite by a Gershgorin bound
-// (C - mu I, mu < lambda_min), and decouple dropped indices (zero row and
-// column; their singular value is then exactly 0).
+// Symmetrise C and decouple dropped indices (zero row and column; their
+// singular value is then exactly 0), and bracket lambda_min of the kept part
+// for the shift that makes it positive definite: sh[0] = the Gershgorin lower
+// bound (a valid shift), sh[1] = min_i C_ii (an upper bound on lambda_min),
+// sh[2] = max_i sum_j |C_ij|, sh[3] = the span of the Gershgorin interval.
 __global__ void __launch_bounds__(kSmallThreads) k_eig_prep(int b, double* __restrict__ C,
                                                             const int* __restrict__ dropped,
-                                                            double* __restrict__ mu_out) {
+                                                            double* __restrict__ sh) {
   const int tid = threadIdx.x;
   for (int e = tid; e < b * b; e += kSmallThreads) {
     int i = e % b, j = e / b;
@@ -220,43 +222,147 @@ __global__ void __launch_bounds__(kSmallThreads) k_eig_prep(int b, double* __res
     }
   }
   __syncthreads();
-  __shared__ double red_lo[32], red_hi[32];
-  double lo = DBL_MAX, hi = -DBL_MAX;
+  __shared__ double red[4][32];
+  double lo = DBL_MAX, hi = -DBL_MAX, dmin = DBL_MAX, rmax = 0.0;
   for (int i = tid; i < b; i += kSmallThreads) {
     if (dropped[i]) continue;
     double r = 0.0;
     for (int j = 0; j < b; ++j)
       if (j != i) r += fabs(C[i + j * b]);
-    lo = fmin(lo, C[i + i * b] - r);
-    hi = fmax(hi, C[i + i * b] + r);
+    const double d = C[i + i * b];
+    lo = fmin(lo, d - r);
+    hi = fmax(hi, d + r);
+    dmin = fmin(dmin, d);
+    rmax = fmax(rmax, fabs(d) + r);
   }
   for (int o = 16; o > 0; o >>= 1) {
     lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
     hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    dmin = fmin(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
+    rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
   }
   if ((tid & 31) == 0) {
-    red_lo[tid >> 5] = lo;
-    red_hi[tid >> 5] = hi;
+    red[0][tid >> 5] = lo;
+    red[1][tid >> 5] = hi;
+    red[2][tid >> 5] = dmin;
+    red[3][tid >> 5] = rmax;
   }
   __syncthreads();
-  __shared__ double s_mu;
   if (tid == 0) {
-    double l = DBL_MAX, h = -DBL_MAX;
+    double l = DBL_MAX, h = -DBL_MAX, u = DBL_MAX, rm = 0.0;
     for (int w = 0; w < kSmallThreads / 32; ++w) {
-      l = fmin(l, red_lo[w]);
-      h = fmax(h, red_hi[w]);
+      l = fmin(l, red[0][w]);
+      h = fmax(h, red[1][w]);
+      u = fmin(u, red[2][w]);
+      rm = fmax(rm, red[3][w]);
     }
     if (l > h) {  // everything dropped
       l = 0.0;
       h = 1.0;
+      u = 0.0;
     }
     double span = fmax(h - l, fmax(fabs(l), fabs(h)));
     if (span == 0.0) span = 1.0;
-    s_mu = l - 1e-3 * span;
-    *mu_out = s_mu;
+    sh[0] = l;
+    sh[1] = u;
+    sh[2] = rm;
+    sh[3] = span;
   }
+}
+
+// A tighter shift than the Gershgorin bound.  The one-sided Jacobi works on
+// C - mu I, whose singular values lambda - mu all lie near |mu| when mu is far
+// below the spectrum; FP32 Jacobi then resolves close eigenvalues only to
+// u32 (lambda - mu)^2 / gap, which the FP64 refinement cannot recover from
+// once the resulting angles are large.  The shift is found by bisection with
+// definiteness tests: CTA p of a round factors C - sigma_p I by FP32 LDL^T
+// (no pivoting; the Schur-complement pivots are all positive iff the FP32
+// matrix is positive definite, up to rounding), sigma_p spread uniformly over
+// the bracket [sh[0], sh[1]].  Dropped indices take a unit diagonal.  The
+// packed lower triangle lives in shared memory (b (b + 1) / 2 floats).
+constexpr int kShiftTrials = 32, kShiftThreads = 256;
+__global__ void __launch_bounds__(kShiftThreads) k_shift_trials(int b, const double* __restrict__ C,
+                                                                const int* __restrict__ dropped,
+                                                                const double* __restrict__ sh,
+                                                                int* __restrict__ ok) {
+  extern __shared__ float sh_pk[];  // column j at off(j) = j (2b - j + 1) / 2, rows j..b-1
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double l = sh[0], u = sh[1];
+  const double sigma = l + (u - l) * (double)(blockIdx.x + 1) / (double)(kShiftTrials + 1);
+  for (int j = warp; j < b; j += kShiftThreads / 32) {
+    const size_t off = (size_t)j * (2 * b - j + 1) / 2;
+    for (int i = j + lane; i < b; i += 32) {
+      double v;
+      if (dropped[i] || dropped[j]) v = i == j ? 1.0 : 0.0;
+      else v = C[i + (size_t)j * b] - (i == j ? sigma : 0.0);
+      sh_pk[off + (i - j)] = (float)v;
+    }
+  }
+  int good = 1;
+  for (int j = 0; j < b; ++j) {
+    __syncthreads();
+    const size_t oj = (size_t)j * (2 * b - j + 1) / 2;
+    const float d = sh_pk[oj];
+    if (!(d > 0.f)) {  // every thread reads the same pivot: a uniform exit
+      good = 0;
+      break;
+    }
+    const float rd = 1.f / d;
+    for (int k = j + 1 + warp; k < b; k += kShiftThreads / 32) {
+      const float lk = sh_pk[oj + (k - j)] * rd;
+      const size_t ok_ = (size_t)k * (2 * b - k + 1) / 2;
+      for (int i = k + lane; i < b; i += 32) sh_pk[ok_ + (i - k)] = fmaf(-sh_pk[oj + (i - j)], lk, sh_pk[ok_ + (i - k)]);
+    }
+  }
+  if (tid == 0) ok[blockIdx.x] = good;
+}
+
+// Narrow the bracket to the trials that passed: the largest passing sigma is
+// the new lower end, the next trial the new upper end.  After the last round
+// the shift is that lower end less the FP32 backward error of the test,
+// (b + 1) b u32 |C - sigma I|, and 1e-3 of the span (which keeps the smallest
+// singular value clear of the Jacobi's norm floor); mu goes to mu_out and the
+// diagonal of C is shifted.
+__global__ void k_shift_pick(int b, double* __restrict__ C, const int* __restrict__ dropped, double* __restrict__ sh,
+                             const int* __restrict__ ok, int last, double* __restrict__ mu_out) {
+  __shared__ double s_mu;
+  if (threadIdx.x == 0) {
+    const double l = sh[0], u = sh[1];
+    int best = -1;
+    for (int p = 0; p < kShiftTrials; ++p)
+      if (ok[p]) best = p;
+    auto sig = [&](int p) { return l + (u - l) * (double)(p + 1) / (double)(kShiftTrials + 1); };
+    const double nl = best >= 0 ? sig(best) : l;
+    const double nu = best + 1 < kShiftTrials ? sig(best + 1) : u;
+    sh[0] = nl;
+    sh[1] = nu;
+    if (last) {
+      const double tol = 1.1 * (double)(b + 1) * (double)b * 0x1p-24 * (sh[2] + fabs(nl));
+      // a passing trial is only trusted to its backward error; the Gershgorin
+      // bound needs no margin, but the same one is harmless
+      s_mu = nl - tol - 1e-3 * sh[3];
+      *mu_out = s_mu;
+    }
+  }
+  if (!last) return;
   __syncthreads();
-  for (int i = tid; i < b; i += kSmallThreads) C[i + i * b] = dropped[i] ? 0.0 : C[i + i * b] - s_mu;
+  for (int i = threadIdx.x; i < b; i += blockDim.x) C[i + (size_t)i * b] = dropped[i] ? 0.0 : C[i + (size_t)i * b] - s_mu;
+}
+
+static size_t shift_trial_smem(int b) { return (size_t)b * (b + 1) / 2 * sizeof(float); }
+
+// Symmetrise, bracket, two rounds of trials, shift.
+static rr_status eig_shift(cudaStream_t s, int b, double* C, const int* dropped, double* sh, int* ok, double* mu) {
+  k_eig_prep<<<1, kSmallThreads, 0, s>>>(b, C, dropped, sh);
+  const size_t sm = shift_trial_smem(b);
+  if (sm > 48 * 1024)
+    RR_CUDA(cudaFuncSetAttribute(k_shift_trials, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  for (int round = 0; round < 2; ++round) {
+    k_shift_trials<<<kShiftTrials, kShiftThreads, sm, s>>>(b, C, dropped, sh, ok);
+    k_shift_pick<<<1, 256, 0, s>>>(b, C, dropped, sh, ok, round == 1, mu);
+  }
+  note_launches(4);  // with check_launch's one: prep, two trial rounds, two picks
+  return check_launch("eigen shift");
 }
 
 // Zero the rows (drop_r) and columns (drop_c) of a rectangular b1 x b2 matrix.
@@ -1112,6 +1218,8 @@ __global__ void k_v32_to_64(int c, int cpad, const float* __restrict__ V32, doub
 
 struct PencilWs {
   double *W1, *W2, *T, *E, *E2, *F, *C, *V, *Vp, *M, *Mp, *sig, *mu;
+  double* sh;                          // [4] bracket and scales of the eigen shift
+  int* shok;                           // [kShiftTrials] definiteness trials
   double* cond;                        // [4] condition estimates of the whitened Grams, drop counts
   float *L32, *Li32, *M32, *V32, *fs;  // fs: [0] Jacobi norm floor, [1] scale
   float *Hq, *tq;                      // QR preconditioner: reflectors (c x c), taus
@@ -1158,6 +1266,8 @@ static bool carve_pencil(Arena& ar, int b1, int b2, PencilWs& w) {
   w.Mp = ar.take<double>(rc);
   w.sig = ar.take<double>(cp);
   w.mu = ar.take<double>(2);
+  w.sh = ar.take<double>(4);
+  w.shok = ar.take<int>(kShiftTrials);
   w.cond = ar.take<double>(4);
   w.fs = ar.take<float>(4);
   w.L32 = ar.take<float>(bb);
@@ -2011,13 +2121,13 @@ extern "C" rr_status rr_pencil_eig(int64_t b, const double* H, const double* G, 
   // C = W^T H W, symmetrised and shifted positive definite (C - mu I)
   gemm_small(s, 0, 0, n, n, n, 1.0, H, n, w.W1, n, 0.0, w.T, n);
   gemm_small_sym(s, n, n, w.W1, n, w.T, n, w.C, n);  // W^T H W (symmetric)
-  k_eig_prep<<<1, kSmallThreads, 0, s>>>(n, w.C, w.drop1, w.mu);
+  RR_TRY(eig_shift(s, n, w.C, w.drop1, w.sh, w.shok, w.mu));
   RR_TRY(jacobi_svd(s, n, n, w.C, w, w.M, w.V));
   k_colnorm_sort<<<1, kSmallThreads, n * sizeof(double), s>>>(n, n, w.M, n, w.sig, w.order);
   k_eig_finish<<<1, 256, 0, s>>>(n, w.sig, w.order, w.mu, w.V, theta, w.T, w.nvalid);
   // Y = W Z
   gemm_small(s, 0, 0, n, n, n, 1.0, w.W1, n, w.T, n, 0.0, Y, n);
-  note_launches(6);
+  note_launches(5);
   RR_TRY(check_launch("rr_pencil_eig"));
   if (dropped) {
     *dropped = 0;
