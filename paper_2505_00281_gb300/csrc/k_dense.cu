@@ -476,7 +476,7 @@ namespace rr {
 // contiguous), so a thread reads its 4 X and 4 Y values as two 16-byte loads
 // per 16 FMAs.  part[chunk][i + j p] (FP64, summed by k_gram_reduce).
 constexpr int kG32 = 64, kG32R = 32;
-__global__ void __launch_bounds__(256) k_gram32(int64_t n, int64_t p, int64_t q, const double* __restrict__ X,
+__global__ void __launch_bounds__(256) k_gram32(int64_t n, int64_t p, int64_t q, const float* __restrict__ X,
                                                 int64_t ldx, const float* __restrict__ Y, int64_t ldy, int64_t rpc,
                                                 double* __restrict__ part) {
   // rows padded by 4 floats: the column-wise staging stores meet 4-way
@@ -492,7 +492,7 @@ __global__ void __launch_bounds__(256) k_gram32(int64_t n, int64_t p, int64_t q,
     for (int e = tid; e < kG32R * kG32; e += 256) {
       const int rr_ = e % kG32R, c = e / kG32R;
       const int64_t row = rs + rr_;
-      Xs[rr_][c] = (row < r1 && p0 + c < p) ? (float)X[row + (p0 + c) * ldx] : 0.f;
+      Xs[rr_][c] = (row < r1 && p0 + c < p) ? X[row + (p0 + c) * ldx] : 0.f;
       Ys[rr_][c] = (row < r1 && q0 + c < q) ? Y[row + (q0 + c) * ldy] : 0.f;
     }
     __syncthreads();
@@ -520,12 +520,13 @@ __global__ void __launch_bounds__(256) k_gram32(int64_t n, int64_t p, int64_t q,
 
 // The same partials with the whole p x q result in one CTA (p, q <= TP =
 // 16 PT): every row of X and Y is read once.  A thread owns PT x PT outputs
-// (rows ti + 16 a of G, columns PT tj ..); each staged row gives it PT X
-// values (conflict-free scalar shared loads) and PT Y values (broadcast
-// 8-byte loads) per PT^2 FMAs, and the next rows' global loads are issued
-// before the current rows are used.
+// (rows 2 ti + 32 a' + {0, 1} of G, a' < PT / 2, and columns PT tj ..); each
+// staged row gives it PT X values (8-byte shared loads, 16 distinct per
+// warp: one wavefront) and PT Y values (broadcast 8-byte loads) per PT^2
+// FMAs, and the next rows' global loads are issued before the current rows
+// are used.
 template <int PT>
-__global__ void __launch_bounds__(256, 1) k_gram32_full(int64_t n, int p, int q, const double* __restrict__ X,
+__global__ void __launch_bounds__(256, 1) k_gram32_full(int64_t n, int p, int q, const float* __restrict__ X,
                                                         int64_t ldx, const float* __restrict__ Y, int64_t ldy,
                                                         int64_t rpc, double* __restrict__ part) {
   constexpr int TP = 16 * PT, R = 16;
@@ -542,7 +543,7 @@ __global__ void __launch_bounds__(256, 1) k_gram32_full(int64_t n, int p, int q,
     for (int u = 0; u < PER; ++u) {
       const int e = tid + 256 * u, rr_ = e % R, c = e / R;
       const int64_t row = rs + rr_;
-      xr[u] = (row < r1 && c < p) ? (float)X[row + c * ldx] : 0.f;
+      xr[u] = (row < r1 && c < p) ? X[row + c * ldx] : 0.f;
       yr[u] = (row < r1 && c < q) ? Y[row + c * ldy] : 0.f;
     }
   };
@@ -561,7 +562,11 @@ __global__ void __launch_bounds__(256, 1) k_gram32_full(int64_t n, int p, int q,
     for (int rr_ = 0; rr_ < R; ++rr_) {
       float xa[PT], ya[PT];
 #pragma unroll
-      for (int a = 0; a < PT; ++a) xa[a] = Xs[rr_][ti + 16 * a];
+      for (int a = 0; a < PT; a += 2) {
+        const float2 xv = *reinterpret_cast<const float2*>(&Xs[rr_][2 * ti + 16 * a]);
+        xa[a] = xv.x;
+        xa[a + 1] = xv.y;
+      }
 #pragma unroll
       for (int a = 0; a < PT; a += 2) {
         const float2 yv = *reinterpret_cast<const float2*>(&Ys[rr_][PT * tj + a]);
@@ -579,15 +584,15 @@ __global__ void __launch_bounds__(256, 1) k_gram32_full(int64_t n, int p, int q,
   for (int a = 0; a < PT; ++a)
 #pragma unroll
     for (int c = 0; c < PT; ++c) {
-      const int i = ti + 16 * a, j = PT * tj + c;
+      const int i = 2 * ti + 16 * (a & ~1) + (a & 1), j = PT * tj + c;
       if (i < p && j < q) out[i + (int64_t)j * p] = (double)acc[a][c];
     }
 }
 
 // G = X^T Y with FP32 products and FP32 accumulation per row chunk (chunk
-// sums added in FP64): for X FP64 (read as FP32) and Y FP32, where FP32
-// accuracy is all the caller needs.
-rr_status gram_f32acc(cudaStream_t s, int64_t n, int64_t p, int64_t q, const double* X, int64_t ldx,
+// sums added in FP64), X and Y FP32, where FP32 accuracy is all the caller
+// needs.
+rr_status gram_f32acc(cudaStream_t s, int64_t n, int64_t p, int64_t q, const float* X, int64_t ldx,
                       const float* Y, int64_t ldy, double* G, int64_t ldg, void* ws, size_t ws_bytes) {
   if (p == 0 || q == 0) return RR_OK;
   if (!ws) return RR_ERR_WORKSPACE;

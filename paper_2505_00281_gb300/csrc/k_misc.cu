@@ -71,13 +71,13 @@ __global__ void __launch_bounds__(256) k_lift(int64_t n, int64_t b, int64_t p, c
   }
 }
 
-// T (n x b, FP32) -= X (n x p, FP64 read as FP32) K (p x b, FP64 read as
-// FP32), FP32 accumulation: a CTA takes 128 rows x 64 columns of T, 8 x 4
+// T (n x b, FP32) -= X (n x p, FP32) K (p x b, FP64 read as FP32), FP32
+// accumulation: a CTA takes 128 rows x 64 columns of T, 8 x 4
 // outputs per thread, the p dimension in steps of 32 staged in shared memory
 // (X rows contiguous per column, K columns contiguous per row) so a thread's
 // operands are three 16-byte loads per 32 FMAs.
 constexpr int kSL_M = 128, kSL_N = 64, kSL_K = 32;
-__global__ void __launch_bounds__(256) k_sub_lowrank32(int64_t n, int64_t b, int64_t p, const double* __restrict__ X,
+__global__ void __launch_bounds__(256) k_sub_lowrank32(int64_t n, int64_t b, int64_t p, const float* __restrict__ X,
                                                        int64_t ldx, const double* __restrict__ K, int64_t ldk,
                                                        float* __restrict__ T, int64_t ldt) {
   __shared__ __align__(16) float Xs[kSL_K][kSL_M];
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(256) k_sub_lowrank32(int64_t n, int64_t b, int
   for (int64_t k0 = 0; k0 < p; k0 += kSL_K) {
     for (int e = tid; e < kSL_K * kSL_M; e += 256) {
       const int r = e % kSL_M, kk = e / kSL_M;
-      Xs[kk][r] = (m0 + r < n && k0 + kk < p) ? (float)X[(m0 + r) + (k0 + kk) * ldx] : 0.f;
+      Xs[kk][r] = (m0 + r < n && k0 + kk < p) ? X[(m0 + r) + (k0 + kk) * ldx] : 0.f;
     }
     for (int e = tid; e < kSL_K * kSL_N; e += 256) {
       const int kk = e % kSL_K, c = e / kSL_K;
@@ -122,21 +122,31 @@ __global__ void __launch_bounds__(256) k_sub_lowrank32(int64_t n, int64_t b, int
 }
 
 // The same update for narrow T (b <= 16 CT): K (p x b) stays in shared memory
-// (FP32, row stride 16 CT + 1), and a persistent CTA walks tiles of 128 rows
+// (FP32, row stride 16 CT + 2), and a persistent CTA walks tiles of 128 rows
 // holding all b columns, so X is read once.  Thread (ti, tj) owns rows
 // ti + 16 a (a < 8) and columns CT tj .. CT tj + CT - 1: the shared X loads are
 // conflict-free and each T store of a warp covers 16 consecutive rows.  The p
 // dimension goes in steps of 32, the next step's X loads issued before the
-// current step is used.
+// current step is used; the tile of T itself is copied to shared memory by
+// asynchronous 4-byte copies issued with the tile's first step, so the
+// epilogue's read of T does not wait on HBM.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = valid ? 4 : 0;  // 0: fill with zeros, nothing read
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 constexpr int kSLF_M = 128, kSLF_K = 32;
 template <int CT>
-__global__ void __launch_bounds__(256, 1) k_sub_lowrank32_full(int64_t n, int b, int p, const double* __restrict__ X,
+__global__ void __launch_bounds__(256, 1) k_sub_lowrank32_full(int64_t n, int b, int p, const float* __restrict__ X,
                                                                int64_t ldx, const double* __restrict__ K, int64_t ldk,
                                                                float* __restrict__ T, int64_t ldt) {
-  constexpr int TB = 16 * CT, KS = TB + 1;
+  constexpr int TB = 16 * CT, KS = TB + 2;
   extern __shared__ __align__(16) float sm_slf[];
-  float* Ks = sm_slf;                              // [p][KS]
-  float* Xs = sm_slf + (((size_t)p * KS + 3) & ~(size_t)3);  // [kSLF_K][kSLF_M]
+  float* Ks = sm_slf;                                        // [p][KS]
+  float* Xs = Ks + (((size_t)p * KS + 3) & ~(size_t)3);      // [kSLF_K][kSLF_M]
+  float* Ts = Xs + kSLF_K * kSLF_M;                          // [b][kSLF_M]
   const int tid = threadIdx.x, ti = tid & 15, tj = tid >> 4;
   for (int e = tid; e < p * TB; e += 256) {
     const int kk = e % p, c = e / p;
@@ -152,7 +162,7 @@ __global__ void __launch_bounds__(256, 1) k_sub_lowrank32_full(int64_t n, int b,
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
       const int e = tid + 256 * u, r = e % kSLF_M, kk = e / kSLF_M;
-      xr[u] = (m0 + r < n && k0 + kk < p) ? (float)X[(m0 + r) + (int64_t)(k0 + kk) * ldx] : 0.f;
+      xr[u] = (m0 + r < n && k0 + kk < p) ? X[(m0 + r) + (int64_t)(k0 + kk) * ldx] : 0.f;
     }
   };
   int64_t tile = blockIdx.x;
@@ -164,6 +174,15 @@ __global__ void __launch_bounds__(256, 1) k_sub_lowrank32_full(int64_t n, int b,
       __syncthreads();
 #pragma unroll
       for (int u = 0; u < PER; ++u) Xs[tid + 256 * u] = xr[u];  // e = kk * M + r
+      if (step == 0) {
+        // every thread is past the previous tile's epilogue: refill Ts
+        for (int e = tid; e < b * kSLF_M; e += 256) {
+          const int r = e % kSLF_M, c = e / kSLF_M;
+          const bool in = m0 + r < n;
+          cp_async4(Ts + e, in ? T + (m0 + r) + (int64_t)c * ldt : T, in);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+      }
       __syncthreads();
       if (step + 1 < ksteps)
         fetch(tile, step + 1);
@@ -177,13 +196,19 @@ __global__ void __launch_bounds__(256, 1) k_sub_lowrank32_full(int64_t n, int b,
         for (int a = 0; a < 8; ++a) xa[a] = Xs[kk * kSLF_M + ti + 16 * a];
         const float* kr = Ks + (size_t)(k0 + kk) * KS + CT * tj;
 #pragma unroll
-        for (int c = 0; c < CT; ++c) ka[c] = kr[c];
+        for (int c = 0; c < CT; c += 2) {
+          const float2 kv = *reinterpret_cast<const float2*>(kr + c);
+          ka[c] = kv.x;
+          ka[c + 1] = kv.y;
+        }
 #pragma unroll
         for (int a = 0; a < 8; ++a)
 #pragma unroll
           for (int c = 0; c < CT; ++c) acc[a][c] = fmaf(xa[a], ka[c], acc[a][c]);
       }
     }
+    cp_async_wait_all();
+    __syncthreads();
 #pragma unroll
     for (int c = 0; c < CT; ++c) {
       const int j = CT * tj + c;
@@ -191,16 +216,17 @@ __global__ void __launch_bounds__(256, 1) k_sub_lowrank32_full(int64_t n, int b,
 #pragma unroll
       for (int a = 0; a < 8; ++a) {
         const int64_t i = m0 + ti + 16 * a;
-        if (i < n) T[i + j * ldt] -= acc[a][c];
+        if (i < n) T[i + j * ldt] = Ts[j * kSLF_M + ti + 16 * a] - acc[a][c];
       }
     }
   }
 }
 
 template <int CT>
-static rr_status launch_sub_lowrank32_full(cudaStream_t s, int64_t n, int64_t b, int64_t p, const double* X,
+static rr_status launch_sub_lowrank32_full(cudaStream_t s, int64_t n, int64_t b, int64_t p, const float* X,
                                            int64_t ldx, const double* K, int64_t ldk, float* T, int64_t ldt) {
-  const size_t smem = ((((size_t)p * (16 * CT + 1) + 3) & ~(size_t)3) + (size_t)kSLF_K * kSLF_M) * sizeof(float);
+  const size_t smem =
+      ((((size_t)p * (16 * CT + 2) + 3) & ~(size_t)3) + (size_t)kSLF_K * kSLF_M + (size_t)b * kSLF_M) * sizeof(float);
   RR_CUDA(cudaFuncSetAttribute(k_sub_lowrank32_full<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int64_t tiles = (n + kSLF_M - 1) / kSLF_M;
   const int64_t grid = tiles < num_sms() ? tiles : num_sms();
@@ -208,7 +234,7 @@ static rr_status launch_sub_lowrank32_full(cudaStream_t s, int64_t n, int64_t b,
   return check_launch("sub_lowrank_f32 full");
 }
 
-rr_status sub_lowrank_f32(cudaStream_t s, int64_t n, int64_t b, int64_t p, const double* X, int64_t ldx,
+rr_status sub_lowrank_f32(cudaStream_t s, int64_t n, int64_t b, int64_t p, const float* X, int64_t ldx,
                           const double* K, int64_t ldk, float* T, int64_t ldt) {
   if (n == 0 || b == 0 || p == 0) return RR_OK;
   if (b <= 160 && p <= 160 && n >= 64 * 1024) {
@@ -218,6 +244,23 @@ rr_status sub_lowrank_f32(cudaStream_t s, int64_t n, int64_t b, int64_t p, const
   dim3 g((unsigned)((n + kSL_M - 1) / kSL_M), (unsigned)((b + kSL_N - 1) / kSL_N));
   k_sub_lowrank32<<<g, 256, 0, s>>>(n, b, p, X, ldx, K, ldk, T, ldt);
   return check_launch("sub_lowrank_f32");
+}
+
+// Y (n x b, FP32) = X (n x b, FP64) rounded to nearest.
+__global__ void k_cast_f32(int64_t n, int64_t b, const double* __restrict__ X, int64_t ldx, float* __restrict__ Y,
+                           int64_t ldy) {
+  const int64_t tot = n * b;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % n, j = e / n;
+    Y[i + j * ldy] = (float)X[i + j * ldx];
+  }
+}
+
+rr_status cast_f32(cudaStream_t s, int64_t n, int64_t b, const double* X, int64_t ldx, float* Y, int64_t ldy) {
+  if (n == 0 || b == 0) return RR_OK;
+  const int64_t want = (n * b + 255) / 256, cap = 8 * (int64_t)num_sms();
+  k_cast_f32<<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(n, b, X, ldx, Y, ldy);
+  return check_launch("cast_f32");
 }
 
 rr_status lift(cudaStream_t s, int32_t stype, int64_t n, int64_t b, int64_t p, const void* S,

@@ -285,13 +285,13 @@ static rr_status gram(const Common& c, int64_t n, int64_t p, int64_t q, int32_t 
   return rr_gram(n, p, q, xt, X, ldx, yt, Y, ldy, G, ldg, 0, c.gram_ws, c.gram_bytes, s);
 }
 
-// Remove the span of the orthonormal FP64 Ritz vectors X (n x b) from the FP32
-// block T (n x b): T <- T - X (X^T T), in FP32 arithmetic (the block is
+// Remove the span of the orthonormal Ritz vectors X (n x b, their FP32 copy)
+// from the FP32 block T (n x b): T <- T - X (X^T T), in FP32 arithmetic (the block is
 // stored in BF16 next; FP32 leaves components along X of ~1e-7 relative).
 // Keeps the correction blocks of the refinement phase away from the
 // converged directions, which the power / Chebyshev steps would otherwise
 // amplify until [X, D] is numerically dependent.  K is b x b FP64 scratch.
-static rr_status project_out(const Common& c, cudaStream_t s, int64_t n, int64_t b, const double* X,
+static rr_status project_out(const Common& c, cudaStream_t s, int64_t n, int64_t b, const float* X,
                              int64_t ldx, float* T, int64_t ldt, double* K) {
   RR_TRY(gram_f32acc(s, n, b, b, X, ldx, T, ldt, K, b, c.gram_ws, c.gram_bytes));
   return sub_lowrank_f32(s, n, b, b, X, ldx, K, b, T, ldt);
@@ -394,6 +394,7 @@ struct SvdBufs {
   double *Ut, *Vt, *Ut2, *Vt2, *sig, *P, *Qm, *Rv, *Ru, *ss, *res, *mu, *coef;
   // split mode: lo halves of the correction blocks, FP32 final blocks
   void *Elo2, *Flo2, *E32, *F32;
+  float *Ut32, *Vt32;  // FP32 copies of the singular vectors for the refinement's projections
   int* frozen;  // batch mode: the problem reached tol (later lifts are undone)
 };
 
@@ -429,9 +430,12 @@ static void carve_svd(Arena& ar, const Op& op, int64_t b, bool refine, SvdBufs& 
     w.AF = ar.take_bytes(m * b * ws_);
     w.mu = ar.take<double>(b);
     w.coef = ar.take<double>(b);
+    w.Ut32 = ar.take<float>(m * b);
+    w.Vt32 = ar.take<float>(n * b);
   } else {
     w.Ut2 = w.Vt2 = w.Rv = w.Ru = w.mu = w.coef = nullptr;
     w.Elo = w.Flo = w.AF = nullptr;
+    w.Ut32 = w.Vt32 = nullptr;
   }
   w.Elo2 = w.Flo2 = w.E32 = w.F32 = nullptr;
   if (refine && op.split) {
@@ -780,6 +784,9 @@ static rr_status svd_run(const rr_operator* Aop_in, const rr_params* p, double* 
       // each block kept at unit column inf-norm, the injection coefficient
       // tracked per column (coef <- coef * sigma / mu after each scaling).
       STAGE(RR_STAGE_OTHER, fill(s, b, 1.0, w.coef));
+      // FP32 copies of the singular vectors for the projections of this sweep
+      STAGE(RR_STAGE_OTHER, cast_f32(s, n, b, w.Vt, n, w.Vt32, n));
+      STAGE(RR_STAGE_OTHER, cast_f32(s, m, b, w.Ut, m, w.Ut32, m));
       // split mode: blocks and operator carried as BF16 pairs (hi + lo), the
       // final correction blocks kept in FP32 for the projection and the lift
       const bool sp = op.split;
@@ -791,12 +798,12 @@ static rr_status svd_run(const rr_operator* Aop_in, const rr_params* p, double* 
       for (int j = 0; j < qr; ++j) {
         if (sp) STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp_T_split(op, b, w.Elo, w.Elo2, m, w.W, n, w.Ru, n, w.coef, s));
         else STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp_T(op, b, w.Elo, m, w.W, n, w.Ru, n, w.coef, s));
-        STAGE(RR_STAGE_GRAM, project_out(w.c, s, n, b, w.Vt, n, (float*)w.W, n, w.Ys));
+        STAGE(RR_STAGE_GRAM, project_out(w.c, s, n, b, w.Vt32, n, (float*)w.W, n, w.Ys));
         if (sp) STAGE(RR_STAGE_OTHER, scale_split(s, op.wt, n, b, w.W, n, w.mu, w.Flo, w.Flo2, n, w.coef, w.sig));
         else STAGE(RR_STAGE_OTHER, scale_cast(s, op.wt, n, b, w.W, n, w.mu, dt, w.Flo, n, w.coef, w.sig));
         if (sp) STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp_split(op, b, w.Flo, w.Flo2, n, w.AF, m, w.Rv, m, w.coef, s));
         else STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp(op, b, w.Flo, n, w.AF, m, w.Rv, m, w.coef, s));
-        STAGE(RR_STAGE_GRAM, project_out(w.c, s, m, b, w.Ut, m, (float*)w.AF, m, w.Ys));
+        STAGE(RR_STAGE_GRAM, project_out(w.c, s, m, b, w.Ut32, m, (float*)w.AF, m, w.Ys));
         if (j + 1 < qr) {
           if (sp) STAGE(RR_STAGE_OTHER, scale_split(s, op.wt, m, b, w.AF, m, w.mu, w.Elo, w.Elo2, m, w.coef, w.sig));
           else STAGE(RR_STAGE_OTHER, scale_cast(s, op.wt, m, b, w.AF, m, w.mu, dt, w.Elo, m, w.coef, w.sig));
@@ -889,6 +896,7 @@ struct EigBufs {
   void *Vlo, *W, *Pw, *Dlo, *Dprev, *AD;
   double *G, *H, *Y, *Ysel, *th2;
   double *X, *X2, *theta, *P, *R, *ss, *res, *mu, *coef, *kap, *kap_prev, *rho, *gam, *gersh;
+  float* X32;  // FP32 copy of the Ritz vectors for the refinement's projections
 };
 
 // Row stride of the filter's row-major blocks: b rounded up to 8 columns
@@ -926,9 +934,11 @@ static void carve_eig(Arena& ar, const Op& op, int64_t b, bool refine, EigBufs& 
     w.X2 = ar.take<double>(n * b);
     w.Dlo = ar.take_bytes(n * b * ds);
     w.AD = ar.take_bytes(n * b * ws_);
+    w.X32 = ar.take<float>(n * b);
   } else {
     w.X2 = nullptr;
     w.Dlo = w.AD = nullptr;
+    w.X32 = nullptr;
   }
 }
 
@@ -1135,6 +1145,8 @@ static rr_status eig_run(const rr_operator* Aop, const rr_params* p, double* the
         prev_mx = INFINITY;
         continue;
       }
+      // FP32 copy of the Ritz vectors for the projections of this sweep
+      STAGE(RR_STAGE_OTHER, cast_f32(s, n, b, w.X, n, w.X32, n));
       if (cheb) {
         // D_1 = (s1/e) R;  D_{j+1} = (2 s_{j+1}/e)(A - cI) D_j - s_j s_{j+1} D_{j-1}
         //                           + (2 s_{j+1}/e) phi_j(theta) R
@@ -1160,7 +1172,7 @@ static rr_status eig_run(const rr_operator* Aop, const rr_params* p, double* the
           STAGE(RR_STAGE_OTHER, vec_scale(s, b, an, w.kap, w.gam));
           STAGE(RR_STAGE_LOWP_PRODUCT, rr_chebyshev_step(n, b, op.rp, op.ci, op.va, dt, d0, dm1, n, an, c, bn, w.rho, w.R, n,
                                    w.gam, op.wt, w.W, n, s));
-          STAGE(RR_STAGE_GRAM, project_out(w.c, s, n, b, w.X, n, (float*)w.W, n, w.Y));
+          STAGE(RR_STAGE_GRAM, project_out(w.c, s, n, b, w.X32, n, (float*)w.W, n, w.Y));
           if (j + 1 < q) {
             // Dhat_{j+1} = T / mu into the buffer of Dhat_{j-1}
             void* dst = dm1 ? dm1 : d1;
@@ -1181,7 +1193,7 @@ static rr_status eig_run(const rr_operator* Aop, const rr_params* p, double* the
           STAGE(RR_STAGE_OTHER, scale_cast(s, RR_F64, n, b, w.R, n, w.mu, dt, w.Vlo, n, w.coef, w.theta));
           for (int j = 1; j < q; ++j) {
             STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp(op, b, w.Vlo, n, w.W, n, w.R, n, w.coef, s));
-            STAGE(RR_STAGE_GRAM, project_out(w.c, s, n, b, w.X, n, (float*)w.W, n, w.Y));
+            STAGE(RR_STAGE_GRAM, project_out(w.c, s, n, b, w.X32, n, (float*)w.W, n, w.Y));
             if (j + 1 < q) STAGE(RR_STAGE_OTHER, scale_cast(s, op.wt, n, b, w.W, n, w.mu, dt, w.Vlo, n, w.coef, w.theta));
           }
         }

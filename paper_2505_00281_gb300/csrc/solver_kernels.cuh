@@ -89,10 +89,11 @@ namespace rr {
 rr_status hessenberg_ex(int32_t arith, int64_t n, int64_t k, void* W, int64_t ldw, int32_t qtype,
                         void* Q, int64_t ldq, int32_t* piv, double tol, void* ws, size_t ws_bytes,
                         cudaStream_t s, int max_grid);
-rr_status gram_f32acc(cudaStream_t s, int64_t n, int64_t p, int64_t q, const double* X, int64_t ldx,
+rr_status gram_f32acc(cudaStream_t s, int64_t n, int64_t p, int64_t q, const float* X, int64_t ldx,
                       const float* Y, int64_t ldy, double* G, int64_t ldg, void* ws, size_t ws_bytes);
-rr_status sub_lowrank_f32(cudaStream_t s, int64_t n, int64_t b, int64_t p, const double* X, int64_t ldx,
+rr_status sub_lowrank_f32(cudaStream_t s, int64_t n, int64_t b, int64_t p, const float* X, int64_t ldx,
                           const double* K, int64_t ldk, float* T, int64_t ldt);
+rr_status cast_f32(cudaStream_t s, int64_t n, int64_t b, const double* X, int64_t ldx, float* Y, int64_t ldy);
 rr_status tc_take_error(cudaStream_t s);
 rr_status tc_prepare_attributes();
 

@@ -379,6 +379,35 @@ def test_pencil_eig_matches_generalized_eigensolver(rr, b):
     assert np.abs(H @ Yh - G @ Yh * th).max() < 1e-8 * scale
 
 
+@pytest.mark.parametrize("b", [144, 160, 320])
+def test_pencil_eig_positive_spectrum_dense_whitened(rr, b):
+    """A pencil whose whitened matrix C = L^-1 H L^-T is dense with a positive
+    spectrum in [0.16, 0.86] (a BF16 power-filtered basis gives such pencils):
+    the Gershgorin interval of C reaches far below the spectrum, and the shift
+    must still keep the Jacobi's singular values apart.  G has condition
+    ~5e5.  Exact values by construction; the oracle's generalized eigensolver
+    as the second reference."""
+    import scipy.linalg as sla
+    rng = np.random.default_rng(7300 + b)
+    Q, _ = np.linalg.qr(rng.standard_normal((b, b)))
+    theta = np.sort(rng.uniform(0.16, 0.86, b))
+    C = (Q * theta) @ Q.T
+    Bq, _ = np.linalg.qr(rng.standard_normal((b, b)))
+    G = (Bq * np.logspace(0, np.log10(5e5), b)) @ Bq.T
+    G = 0.5 * (G + G.T)
+    L = np.linalg.cholesky(G)
+    H = L @ C @ L.T
+    H = 0.5 * (H + H.T)
+    th, Y, dropped = rr.rr_pencil_eig(dev(H), dev(G))
+    th, Yh = host(th), host(Y)
+    ref = sla.eigh(H, G, eigvals_only=True)
+    assert dropped == 0
+    assert np.abs(th - ref).max() <= 1e-10
+    assert np.abs(th - theta).max() <= 1e-9
+    assert np.abs(Yh.T @ G @ Yh - np.eye(b)).max() < 1e-8
+    assert np.abs(H @ Yh - G @ Yh * th).max() < 1e-8 * np.abs(H).max()
+
+
 def test_pencil_eig_rank_deficient_drops(rr):
     rng = np.random.default_rng(5)
     U = rng.standard_normal((80, 10))
