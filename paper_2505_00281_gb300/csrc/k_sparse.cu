@@ -252,10 +252,10 @@ __device__ __forceinline__ void st_vec(TO* p, const A (&v)[V]) {
 // CTA's CSR entries are staged in shared memory (coalesced loads by all
 // threads), so a thread's gathers depend on no global load; Y_prev is
 // requested before the barrier.  A CTA whose rows hold more than kRowsStage
-// entries reads them from global memory.
+// entries leaves them to a second kernel that stages them in windows.
 constexpr int kRowsStage = 1024;
 
-template <typename TY, typename A, int V, bool kStaged>
+template <typename TY, typename A, int V>
 __device__ __forceinline__ void rows_gather(int e0, int e1, const int* __restrict__ sci, const float* __restrict__ sva,
                                             const TY* __restrict__ Yc, int64_t ldr, int64_t j0, A (&acc)[V]) {
   for (int e = e0; e < e1; e += kRowChunk) {
@@ -264,8 +264,8 @@ __device__ __forceinline__ void rows_gather(int e0, int e1, const int* __restric
 #pragma unroll
     for (int t = 0; t < kRowChunk; ++t) {
       const bool ok = e + t < e1;
-      v[t] = ok ? (A)(kStaged ? sva[e + t] : __ldg(sva + e + t)) : A(0);
-      const int c = ok ? (kStaged ? sci[e + t] : __ldg(sci + e + t)) : 0;
+      v[t] = ok ? (A)sva[e + t] : A(0);
+      const int c = ok ? sci[e + t] : 0;
       y[t] = ok ? __ldg(reinterpret_cast<const uint4*>(Yc + (int64_t)c * ldr + j0)) : make_uint4(0, 0, 0, 0);
     }
 #pragma unroll
@@ -278,8 +278,101 @@ __device__ __forceinline__ void rows_gather(int e0, int e1, const int* __restric
   }
 }
 
+// Resident CTAs per SM the row kernel is compiled for (BF16 blocks have a
+// kernel of their own below).
+template <typename T> struct kRowsMinBlocks { static constexpr int value = 5; };
+template <> struct kRowsMinBlocks<double> { static constexpr int value = 3; };
+
+// A row group (the R rows of one CTA of the step kernels) whose rows hold
+// more entries than one stage: windows of kRowsStage entries, one gather at a
+// time, by every thread of the CTA (the barriers are the CTA's).
 template <typename TY, typename TO>
-__global__ void __launch_bounds__(256, std::is_same<TY, double>::value ? 3 : 5) k_csr_cheb_rows(
+__device__ __forceinline__ void cheb_rows_windows(int g, int n, const int32_t* __restrict__ rp,
+                                                  const int32_t* __restrict__ ci, const float* __restrict__ va,
+                                                  const TY* __restrict__ Yc, const TY* __restrict__ Yp, int64_t ldr,
+                                                  typename AccT<TY>::type alpha, typename AccT<TY>::type cshift,
+                                                  typename AccT<TY>::type beta, TO* __restrict__ Yn, int64_t ldn,
+                                                  int* s_ci, float* s_va) {
+  using A = typename AccT<TY>::type;
+  constexpr int V = VecW<TY>::V;
+  const int R = blockDim.y;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
+  const int r0 = g * R, rows = n - r0 < R ? n - r0 : R;
+  const int base = __ldg(rp + r0), E = __ldg(rp + r0 + rows) - base;
+  const int row = r0 + threadIdx.y;
+  const bool mine = (int)threadIdx.y < rows;
+  const int64_t j0 = (int64_t)threadIdx.x * V;
+  const int e0 = mine ? __ldg(rp + row) - base : 0, e1 = mine ? __ldg(rp + row + 1) - base : 0;
+  A acc[V];
+#pragma unroll
+  for (int k = 0; k < V; ++k) acc[k] = A(0);
+  for (int ws = 0; ws < E; ws += kRowsStage) {
+    const int we = E - ws < kRowsStage ? E : ws + kRowsStage;
+    __syncthreads();  // the previous window (or group) is read
+    for (int t = tid; t < we - ws; t += nth) {
+      s_ci[t] = __ldg(ci + base + ws + t);
+      s_va[t] = __ldg(va + base + ws + t);
+    }
+    __syncthreads();
+    const int lo = e0 > ws ? e0 : ws, hi = e1 < we ? e1 : we;
+    for (int e = lo - ws; e < hi - ws; ++e) {
+      A f[V];
+      unpack_vec<TY>(__ldg(reinterpret_cast<const uint4*>(Yc + (int64_t)s_ci[e] * ldr + j0)), f);
+      const A v = (A)s_va[e];
+#pragma unroll
+      for (int k = 0; k < V; ++k) acc[k] = fma(v, f[k], acc[k]);
+    }
+  }
+  if (!mine) return;
+  A f[V];
+  unpack_vec<TY>(__ldg(reinterpret_cast<const uint4*>(Yc + row * ldr + j0)), f);
+#pragma unroll
+  for (int k = 0; k < V; ++k) acc[k] = fma(-cshift, f[k], acc[k]);
+  unpack_vec<TY>(__ldg(reinterpret_cast<const uint4*>(Yp + row * ldr + j0)), f);
+  A out[V];
+#pragma unroll
+  for (int k = 0; k < V; ++k) out[k] = fma(-beta, f[k], alpha * acc[k]);
+  st_vec<TO, A, V>(Yn + row * ldn + j0, out);
+}
+
+// The groups the step kernels skip (more than kRowsStage entries): each
+// thread tests one group, the CTA lists the long ones and processes them in
+// turn.  Same CTA shape as the step kernel; launched after it on the same
+// stream, it costs one pass over the group boundaries when there are none.
+template <typename TY, typename TO>
+__global__ void __launch_bounds__(256) k_csr_cheb_rows_long(int n, const int32_t* __restrict__ rp,
+                                                            const int32_t* __restrict__ ci,
+                                                            const float* __restrict__ va, const TY* __restrict__ Yc,
+                                                            const TY* __restrict__ Yp, int64_t ldr,
+                                                            typename AccT<TY>::type alpha,
+                                                            typename AccT<TY>::type cshift,
+                                                            typename AccT<TY>::type beta, TO* __restrict__ Yn,
+                                                            int64_t ldn) {
+  __shared__ int s_ci[kRowsStage];
+  __shared__ float s_va[kRowsStage];
+  __shared__ int s_list[256];
+  __shared__ int s_cnt;
+  const int R = blockDim.y;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
+  const int groups = (n + R - 1) / R;
+  for (int g0 = blockIdx.x * nth; g0 < groups; g0 += gridDim.x * nth) {
+    if (tid == 0) s_cnt = 0;
+    __syncthreads();
+    const int g = g0 + tid;
+    if (g < groups) {
+      const int r0 = g * R, rows = n - r0 < R ? n - r0 : R;
+      if (__ldg(rp + r0 + rows) - __ldg(rp + r0) > kRowsStage) s_list[atomicAdd(&s_cnt, 1)] = g;
+    }
+    __syncthreads();
+    const int cnt = s_cnt;
+    for (int k = 0; k < cnt; ++k)
+      cheb_rows_windows<TY, TO>(s_list[k], n, rp, ci, va, Yc, Yp, ldr, alpha, cshift, beta, Yn, ldn, s_ci, s_va);
+    __syncthreads();  // s_cnt and s_list are reused
+  }
+}
+
+template <typename TY, typename TO>
+__global__ void __launch_bounds__(256, kRowsMinBlocks<TY>::value) k_csr_cheb_rows(
     int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
     const float* __restrict__ va, const TY* __restrict__ Yc, const TY* __restrict__ Yp, int64_t ldr,
     typename AccT<TY>::type alpha, typename AccT<TY>::type cshift, typename AccT<TY>::type beta,
@@ -289,10 +382,11 @@ __global__ void __launch_bounds__(256, std::is_same<TY, double>::value ? 3 : 5) 
   __shared__ int s_ci[kRowsStage];
   __shared__ float s_va[kRowsStage];
   const int R = blockDim.y;
-  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
   const int r0 = blockIdx.x * R;
   const int rows = n - r0 < R ? n - r0 : R;
   const int base = __ldg(rp + r0), E = __ldg(rp + r0 + rows) - base;
+  if (E > kRowsStage) return;  // the same for the whole CTA: k_csr_cheb_rows_long takes it
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
   const bool mine = (int)threadIdx.y < rows;
   const int row = r0 + threadIdx.y;
   const int64_t j0 = (int64_t)threadIdx.x * V;
@@ -301,21 +395,18 @@ __global__ void __launch_bounds__(256, std::is_same<TY, double>::value ? 3 : 5) 
   if (mine) {  // independent of the stage: in flight across the barrier
     e0 = __ldg(rp + row);
     e1 = __ldg(rp + row + 1);
-    if (Yp) praw = __ldg(reinterpret_cast<const uint4*>(Yp + row * ldr + j0));
+    praw = __ldg(reinterpret_cast<const uint4*>(Yp + row * ldr + j0));  // never null here
   }
-  const bool staged = E <= kRowsStage;  // the same for the whole CTA
-  if (staged)
-    for (int t = tid; t < E; t += nth) {
-      s_ci[t] = __ldg(ci + base + t);
-      s_va[t] = __ldg(va + base + t);
-    }
+  for (int t = tid; t < E; t += nth) {
+    s_ci[t] = __ldg(ci + base + t);
+    s_va[t] = __ldg(va + base + t);
+  }
   __syncthreads();
   if (!mine) return;
   A acc[V];
 #pragma unroll
   for (int k = 0; k < V; ++k) acc[k] = A(0);
-  if (staged) rows_gather<TY, A, V, true>(e0 - base, e1 - base, s_ci, s_va, Yc, ldr, j0, acc);
-  else rows_gather<TY, A, V, false>(e0, e1, ci, va, Yc, ldr, j0, acc);
+  rows_gather<TY, A, V>(e0 - base, e1 - base, s_ci, s_va, Yc, ldr, j0, acc);
   // the shift: the row's own vector, usually just gathered as the diagonal entry (an L1 hit)
   A f[V];
   unpack_vec<TY>(__ldg(reinterpret_cast<const uint4*>(Yc + row * ldr + j0)), f);
@@ -326,6 +417,81 @@ __global__ void __launch_bounds__(256, std::is_same<TY, double>::value ? 3 : 5) 
 #pragma unroll
   for (int k = 0; k < V; ++k) out[k] = fma(-beta, f[k], alpha * acc[k]);
   st_vec<TO, A, V>(Yn + row * ldn + j0, out);
+}
+
+// BF16 blocks: the same step written for the register budget of eight
+// resident CTAs per SM (32 registers, no spills), which is what hides the
+// latency of the staged entries and the gathers: FP32 accumulators in pairs
+// (a BF16 pair unpacks into one), the output packed pair by pair.
+__device__ __forceinline__ float2 bf16x2_unpack(unsigned w) {
+  return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xFFFF0000u));
+}
+
+template <typename TO>
+__global__ void __launch_bounds__(256, 8) k_csr_cheb_rows_bf16(int n, const int32_t* __restrict__ rp,
+                                                               const int32_t* __restrict__ ci,
+                                                               const float* __restrict__ va,
+                                                               const __nv_bfloat16* __restrict__ Yc,
+                                                               const __nv_bfloat16* __restrict__ Yp, int64_t ldr,
+                                                               float alpha, float cshift, float beta,
+                                                               TO* __restrict__ Yn, int64_t ldn) {
+  __shared__ int s_ci[kRowsStage];
+  __shared__ float s_va[kRowsStage];
+  const int R = blockDim.y;
+  const int r0 = blockIdx.x * R;
+  const int rows = n - r0 < R ? n - r0 : R;
+  const int base = __ldg(rp + r0), E = __ldg(rp + r0 + rows) - base;
+  if (E > kRowsStage) return;  // the same for the whole CTA: k_csr_cheb_rows_long takes it
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
+  const bool mine = (int)threadIdx.y < rows;
+  const int row = r0 + threadIdx.y;
+  const int64_t j0 = (int64_t)threadIdx.x * 8;
+  int e0 = 0, e1 = 0;
+  uint4 praw = make_uint4(0, 0, 0, 0);
+  if (mine) {  // independent of the stage: in flight across the barrier
+    e0 = __ldg(rp + row) - base;
+    e1 = __ldg(rp + row + 1) - base;
+    praw = __ldg(reinterpret_cast<const uint4*>(Yp + row * ldr + j0));
+  }
+  for (int t = tid; t < E; t += nth) {
+    s_ci[t] = __ldg(ci + base + t);
+    s_va[t] = __ldg(va + base + t);
+  }
+  __syncthreads();
+  if (!mine) return;
+  float2 acc[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  for (int e = e0; e < e1; e += kRowChunk) {
+    uint4 y[kRowChunk];
+    float v[kRowChunk];
+#pragma unroll
+    for (int t = 0; t < kRowChunk; ++t) {
+      const bool ok = e + t < e1;
+      const int c = ok ? s_ci[e + t] : 0;
+      v[t] = ok ? s_va[e + t] : 0.f;
+      y[t] = ok ? __ldg(reinterpret_cast<const uint4*>(Yc + (int64_t)c * ldr + j0)) : make_uint4(0, 0, 0, 0);
+    }
+#pragma unroll
+    for (int t = 0; t < kRowChunk; ++t) {
+      const unsigned w[4] = {y[t].x, y[t].y, y[t].z, y[t].w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float2 f = bf16x2_unpack(w[q]);
+        acc[q].x = fmaf(v[t], f.x, acc[q].x);
+        acc[q].y = fmaf(v[t], f.y, acc[q].y);
+      }
+    }
+  }
+  // the shift: the row's own vector, usually just gathered as the diagonal entry (an L1 hit)
+  const uint4 u = __ldg(reinterpret_cast<const uint4*>(Yc + row * ldr + j0));
+  const unsigned wu[4] = {u.x, u.y, u.z, u.w}, wp[4] = {praw.x, praw.y, praw.z, praw.w};
+  float o[8];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float2 f = bf16x2_unpack(wu[q]), pp = bf16x2_unpack(wp[q]);
+    o[2 * q] = fmaf(-beta, pp.x, alpha * fmaf(-cshift, f.x, acc[q].x));
+    o[2 * q + 1] = fmaf(-beta, pp.y, alpha * fmaf(-cshift, f.y, acc[q].y));
+  }
+  st_vec<TO, float, 8>(Yn + row * ldn + j0, o);
 }
 
 // column-major (ld) <-> row-major (row stride ldr, pad columns b .. bp - 1
@@ -400,11 +566,24 @@ static rr_status cheb_rows_launch(cudaStream_t s, int64_t n, int64_t b, const in
   constexpr int V = VecW<TY>::V;
   const int64_t units = (b + V - 1) / V;
   if (units > kRowsMaxUnits || n > INT32_MAX) return RR_ERR_ARG;
+  if (n == 0 || units == 0) return RR_OK;
   const int64_t R = std::max<int64_t>(1, 256 / units);
   dim3 th((unsigned)units, (unsigned)R);
-  k_csr_cheb_rows<TY, TO><<<(unsigned)((n + R - 1) / R), th, 0, s>>>(
-      (int)n, rp, ci, va, (const TY*)Yc, (const TY*)Yp, ldr, (A)alpha, (A)c, (A)(Yp ? beta : 0.0), (TO*)Yn, ldn);
-  return check_launch("rr_chebyshev_step_rows");
+  // without Y_prev the kernels read Y_cur in its place, times beta = 0
+  const TY* yp = (const TY*)(Yp ? Yp : Yc);
+  const A bt = (A)(Yp ? beta : 0.0);
+  const int64_t groups = (n + R - 1) / R;
+  if constexpr (std::is_same<TY, __nv_bfloat16>::value && !std::is_same<TO, double>::value)
+    k_csr_cheb_rows_bf16<TO><<<(unsigned)groups, th, 0, s>>>((int)n, rp, ci, va, (const TY*)Yc, yp, ldr, (A)alpha,
+                                                           (A)c, bt, (TO*)Yn, ldn);
+  else
+    k_csr_cheb_rows<TY, TO><<<(unsigned)groups, th, 0, s>>>((int)n, rp, ci, va, (const TY*)Yc, yp, ldr, (A)alpha,
+                                                            (A)c, bt, (TO*)Yn, ldn);
+  RR_TRY(check_launch("rr_chebyshev_step_rows"));
+  const int64_t per = (int64_t)th.x * th.y, lg = (groups + per - 1) / per;
+  k_csr_cheb_rows_long<TY, TO><<<(unsigned)(lg < 4 * num_sms() ? lg : 4 * num_sms()), th, 0, s>>>(
+      (int)n, rp, ci, va, (const TY*)Yc, yp, ldr, (A)alpha, (A)c, bt, (TO*)Yn, ldn);
+  return check_launch("rr_chebyshev_step_rows long rows");
 }
 
 // row-major step: (ytype, out_type) in {(BF16, BF16), (BF16, F32), (F32, F32), (F64, F64)}

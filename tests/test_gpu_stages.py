@@ -554,6 +554,43 @@ def test_pencil_svd_clustered_spectrum(rr):
 
 
 # ---------------------------------------------------------------- a3
+@pytest.mark.parametrize("b", [20, 160])
+def test_chebyshev_step_rows_long_rows(rr, b):
+    """Rows with more CSR entries than a CTA stages in shared memory (dense
+    rows among sparse ones): those CTAs read their entries from global
+    memory.  BF16 blocks against the oracle's CSR product."""
+    rng = np.random.default_rng(7400 + b)
+    n = 3000
+    rows = []
+    for i in range(n):
+        if i % 500 == 7:
+            cols = np.arange(n)                       # a dense row
+        else:
+            cols = np.unique(np.concatenate([[i], rng.integers(0, n, 4)]))
+        rows.append(cols)
+    rp = np.concatenate([[0], np.cumsum([len(c) for c in rows])]).astype(np.int32)
+    ci = np.concatenate(rows).astype(np.int32)
+    va = rng.uniform(-1, 1, len(ci)).astype(np.float32)
+    X = O.round_bf16(rng.standard_normal((n, b)))
+    Xp = O.round_bf16(rng.standard_normal((n, b)))
+    bp = -(-b // 8) * 8
+
+    def rows_(a):
+        t = torch.zeros(n, bp, dtype=torch.float64)
+        t[:, :b] = torch.from_numpy(a)
+        return t.to(torch.bfloat16).to(DEV)
+    d_rp, d_ci, d_va = (torch.from_numpy(a).to(DEV) for a in (rp, ci, va))
+    alpha, c, beta = 0.7, 3.0, 0.4
+    Yn = rr.rr_chebyshev_step_rows(d_rp, d_ci, d_va, rows_(X), rows_(Xp), b, alpha, c, beta, out_dtype=torch.float32)
+    Amul = O.csr_apply(rp, ci, va)
+    ref = alpha * (Amul(X) - c * X) - beta * Xp
+    absb = alpha * (O.csr_apply(rp, ci, np.abs(va))(np.abs(X)) + c * np.abs(X)) + beta * np.abs(Xp)
+    got = host(Yn)[:, :b]
+    # FP32 sums of a row's terms: the error bound grows with the row's length
+    lens = np.diff(rp).astype(np.float64)[:, None]
+    assert np.all(np.abs(got - ref) <= (lens + 8) * U24 * absb + 1e-30)
+
+
 @pytest.mark.parametrize("ytype,otype,b", [("bf16", "bf16", 20), ("bf16", "f32", 160), ("f32", "f32", 13),
                                            ("f64", "f64", 7)])
 def test_chebyshev_step_rows(rr, ytype, otype, b):
