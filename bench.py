@@ -604,6 +604,24 @@ def run_stage(args):
                           "peak_gbs": peaks["hbm_gbs"], "peak_source": src}))
     elif args.stage == "sparse":
         print(json.dumps({"stage": "sparse", **sparse_solve(rr, args.sweeps)}))
+    elif args.stage == "project":
+        # a tall refined eigensolve whose correction blocks are projected against
+        # the Ritz vectors by the whole-block FP32 Gram and low-rank update:
+        # block-diagonal CSR (4 x 4 blocks), n rows, 64 largest pairs, block 160,
+        # BF16 basis, 3 products per correction, 6 sweeps
+        import torch
+        n, k, bs = args.rows if args.rows != M else 131072, 64, 160
+        rp, ci, va, lam = wl.block_diag_csr(n, k, 7100 + bs)
+        d = [torch.from_numpy(a).cuda() for a in (rp, ci, va)]
+        V0 = rr.fortran(torch.from_numpy(wl.uniform_block(n, bs, 7200 + bs)).cuda())
+        p = rr.api.make_params(k, bs, 2, 6, 1e-10, basis="bf16", v0=V0, refine=True, phase1_sweeps=2,
+                               refine_degree=3, profile=True)
+        th, X, info = rr.rr_eig(rr.api.csr_operator(*d), p, n)
+        torch.cuda.synchronize()
+        names = ["lowp_product", "f64_product", "hessenberg", "gram", "pencil", "lift", "other"]
+        print(json.dumps({"stage": "project", "n": n, "k": k, "b": bs, "sweeps": info["sweeps"],
+                          "res_history": info["res_history"][:info["sweeps"]],
+                          "stages_ms": dict(zip(names, info["stage_ms"][:7]))}))
     elif args.stage == "warm":
         # learned warm start: H(p) = -Lap + V_p (8 Gaussian bumps) on a grid x grid mesh,
         # lowest k pairs; train on solves of `train` family members, then solve `test`
@@ -870,10 +888,11 @@ def main():
     ap.add_argument("--no-fp8", action="store_true", help="skip the FP8-E4M3 basis run")
     ap.add_argument("--no-sparse", action="store_true", help="skip the sparse eigenproblem leg")
     ap.add_argument("--stage", choices=["pencil", "hessenberg", "gemm", "split", "f64emu", "prep", "cheb", "warm", "sparse",
-                                        "fp8", "batch", "kernel", "krylov", "builders"],
+                                        "fp8", "batch", "kernel", "krylov", "builders", "project"],
                     help="run one stage of the workload (profiling driver)")
     ap.add_argument("--b", type=int, default=256, help="pencil size for --stage pencil, columns for hessenberg")
-    ap.add_argument("--rows", type=int, default=M, help="rows of the block for --stage hessenberg")
+    ap.add_argument("--rows", type=int, default=M,
+                    help="rows of the block for --stage hessenberg (of the operator for --stage project)")
     ap.add_argument("--grid", type=int, default=64, help="grid side for --stage warm")
     ap.add_argument("--points", type=int, default=65536, help="points of the kernel operator for --stage kernel")
     ap.add_argument("--quick", action="store_true", help="--stage builders: skip MGS-L at k = 400")

@@ -274,13 +274,13 @@ __global__ void __launch_bounds__(kSmallThreads) k_eig_prep(int b, double* __res
 // C - mu I, whose singular values lambda - mu all lie near |mu| when mu is far
 // below the spectrum; FP32 Jacobi then resolves close eigenvalues only to
 // u32 (lambda - mu)^2 / gap, which the FP64 refinement cannot recover from
-// once the resulting angles are large.  The shift is found by bisection with
-// definiteness tests: CTA p of a round factors C - sigma_p I by FP32 LDL^T
+// once the resulting angles are large.  The shift is found by a parallel search
+// with definiteness tests: CTA p factors C - sigma_p I by FP32 LDL^T
 // (no pivoting; the Schur-complement pivots are all positive iff the FP32
 // matrix is positive definite, up to rounding), sigma_p spread uniformly over
 // the bracket [sh[0], sh[1]].  Dropped indices take a unit diagonal.  The
 // packed lower triangle lives in shared memory (b (b + 1) / 2 floats).
-constexpr int kShiftTrials = 32, kShiftThreads = 256;
+constexpr int kShiftTrials = 64, kShiftThreads = 256;
 __global__ void __launch_bounds__(kShiftThreads) k_shift_trials(int b, const double* __restrict__ C,
                                                                 const int* __restrict__ dropped,
                                                                 const double* __restrict__ sh,
@@ -318,8 +318,10 @@ __global__ void __launch_bounds__(kShiftThreads) k_shift_trials(int b, const dou
 }
 
 // Narrow the bracket to the trials that passed: the largest passing sigma is
-// the new lower end, the next trial the new upper end.  After the last round
-// the shift is that lower end less the FP32 backward error of the test,
+// the new lower end, the next trial the new upper end (64 trials place the
+// shift within 1/65 of the bracket below lambda_min, which keeps the relative
+// gaps of the singular values those of the spectrum).  On the last round the
+// shift is that lower end less the FP32 backward error of the test,
 // (b + 1) b u32 |C - sigma I|, and 1e-3 of the span (which keeps the smallest
 // singular value clear of the Jacobi's norm floor); mu goes to mu_out and the
 // diagonal of C is shifted.
@@ -351,17 +353,15 @@ __global__ void k_shift_pick(int b, double* __restrict__ C, const int* __restric
 
 static size_t shift_trial_smem(int b) { return (size_t)b * (b + 1) / 2 * sizeof(float); }
 
-// Symmetrise, bracket, two rounds of trials, shift.
+// Symmetrise, bracket, one round of trials, shift.
 static rr_status eig_shift(cudaStream_t s, int b, double* C, const int* dropped, double* sh, int* ok, double* mu) {
   k_eig_prep<<<1, kSmallThreads, 0, s>>>(b, C, dropped, sh);
   const size_t sm = shift_trial_smem(b);
   if (sm > 48 * 1024)
     RR_CUDA(cudaFuncSetAttribute(k_shift_trials, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  for (int round = 0; round < 2; ++round) {
-    k_shift_trials<<<kShiftTrials, kShiftThreads, sm, s>>>(b, C, dropped, sh, ok);
-    k_shift_pick<<<1, 256, 0, s>>>(b, C, dropped, sh, ok, round == 1, mu);
-  }
-  note_launches(4);  // with check_launch's one: prep, two trial rounds, two picks
+  k_shift_trials<<<kShiftTrials, kShiftThreads, sm, s>>>(b, C, dropped, sh, ok);
+  k_shift_pick<<<1, 256, 0, s>>>(b, C, dropped, sh, ok, 1, mu);
+  note_launches(2);  // with check_launch's one: prep, the trials, the pick
   return check_launch("eigen shift");
 }
 

@@ -360,32 +360,13 @@ def test_svd_fp64_polish_after_stall(rr):
     assert polished >= 1
 
 
-def _block_diag_csr(n, k, seed):
-    """Symmetric CSR made of 4 x 4 diagonal blocks Q diag(e) Q^T (Q random
-    orthogonal): the k + 8 largest eigenvalues spread over [0.6, 1], the rest
-    in [0, 0.2].  Values are stored in FP32; the exact spectrum is that of the
-    stored blocks (brute force per block, FP64)."""
-    rng = np.random.default_rng(seed)
-    e = rng.uniform(0.0, 0.2, n)
-    e[rng.permutation(n)[:k + 8]] = np.linspace(1.0, 0.6, k + 8)
-    nb = n // 4
-    Q, _ = np.linalg.qr(rng.standard_normal((nb, 4, 4)))
-    B = (Q * e.reshape(nb, 1, 4)) @ np.swapaxes(Q, 1, 2)
-    B = 0.5 * (B + np.swapaxes(B, 1, 2))
-    B32 = B.astype(np.float32)
-    lam = np.sort(np.linalg.eigvalsh(B32.astype(np.float64)).ravel())[::-1]
-    rp = np.arange(0, 4 * n + 1, 4, dtype=np.int32)
-    ci = (4 * np.repeat(np.arange(nb), 16) + np.tile(np.tile(np.arange(4), 4), nb)).astype(np.int32)
-    return rp, ci, B32.reshape(-1), lam
-
-
 @pytest.mark.parametrize("k,b", [(40, 96), (64, 160)])
 def test_eig_csr_tall_block_refined(rr, k, b):
     """A tall operator (n = 131072) refined with 3 products per correction:
     the correction blocks are projected against the Ritz vectors by the
     whole-block FP32 Gram and low-rank update kernels of tall blocks."""
     n = 131072
-    rp, ci, va, lam = _block_diag_csr(n, k, 7100 + b)
+    rp, ci, va, lam = wl.block_diag_csr(n, k, 7100 + b)
     d = [torch.from_numpy(a).to(DEV) for a in (rp, ci, va)]
     V0 = wl.uniform_block(n, b, 7200 + b)
     p = rr.api.make_params(k, b, 2, 40, 1e-10, basis="bf16", v0=dev(V0), refine=True, phase1_sweeps=2,

@@ -222,3 +222,21 @@ def gaussian_kernel_rect(x: np.ndarray, y: np.ndarray, f: float, l: float) -> np
     d2 = np.sum((x[:, None, :] - y[None, :, :]) ** 2, axis=-1)
     return np.asfortranarray(f * np.exp(-d2 / (2.0 * l * l)))
 
+
+def block_diag_csr(n: int, k: int, seed: int):
+    """Symmetric CSR made of 4 x 4 diagonal blocks Q diag(e) Q^T (Q random
+    orthogonal): the k + 8 largest eigenvalues spread over [0.6, 1], the rest
+    in [0, 0.2].  Values are stored in FP32; the exact spectrum is that of the
+    stored blocks (brute force per block, FP64)."""
+    rng = _rng(seed)
+    e = rng.uniform(0.0, 0.2, n)
+    e[rng.permutation(n)[:k + 8]] = np.linspace(1.0, 0.6, k + 8)
+    nb = n // 4
+    Q, _ = np.linalg.qr(rng.standard_normal((nb, 4, 4)))
+    B = (Q * e.reshape(nb, 1, 4)) @ np.swapaxes(Q, 1, 2)
+    B = 0.5 * (B + np.swapaxes(B, 1, 2))
+    B32 = B.astype(np.float32)
+    lam = np.sort(np.linalg.eigvalsh(B32.astype(np.float64)).ravel())[::-1]
+    rp = np.arange(0, 4 * n + 1, 4, dtype=np.int32)
+    ci = (4 * np.repeat(np.arange(nb), 16) + np.tile(np.tile(np.arange(4), 4), nb)).astype(np.int32)
+    return rp, ci, B32.reshape(-1), lam
