@@ -182,11 +182,12 @@ def aggregate(seconds: float, converged: int, dist=None, device=None):
 
 
 # --------------------------------------------------------------------------- GPU arm
-# DRAM bytes per launch of k_gemm_bf16_tc, mean over the 250 launches of one
-# solve of this workload (ncu dram__bytes_read.sum + dram__bytes_write.sum, a
-# one-pass capture; profiles/ncu_gemm_bf16_tc_16384x4096x128.md); set to None
-# when the kernel changes until it is captured again.
-TC_TRAFFIC_PER_LAUNCH = 107.9e6
+# DRAM bytes per launch of k_gemm_bf16_tc by role (the low-precision products,
+# the FP64-emulation passes), mean over one solve of this workload (ncu
+# dram__bytes_read.sum + dram__bytes_write.sum, a one-pass capture of every
+# launch of the kernel in one solve; profiles/ncu_gemm_bf16_tc_16384x4096x128.md).
+# Emptied when the kernel changes, until it is captured again.
+TC_TRAFFIC_PER_LAUNCH = {"lowp_product": 234.0e6, "f64_emulation": 96.8e6}
 
 
 def stage_roofline(info, peaks, src):
@@ -194,16 +195,21 @@ def stage_roofline(info, peaks, src):
     stage of one solve) with each stage's share, and the roofline of the
     dominant kernel.
 
-    ``roofline`` is the tcgen05 product kernel ``k_gemm_bf16_tc`` over every
-    one of its launches in the solve, whichever stage it ran in (filter
-    products, split-BF16 corrections, the slice passes of the FP64-emulated
-    products, Gram products and lifts): the library brackets each launch with
-    CUDA events on its stream and adds up its algorithmic bytes (each operand
-    read once -- for an emulation pass the distinct 6-bit slices it reads --
-    and the output written once).  It is HBM-bound at these shapes
-    (intensity 2 b / 2 flop per byte at b = 128 against a BF16 ridge near
-    280 flop per byte), so achieved = bytes / time against the measured copy
-    bandwidth."""
+    ``roofline`` is the tcgen05 product kernel ``k_gemm_bf16_tc``, the
+    dominant kernel, whose launches play two roles: the low-precision
+    products (filter products, split-BF16 corrections; HBM-bound at b = 128,
+    128 flop per byte of operator against a BF16 ridge near 260) and the
+    FP64-emulation passes (all slice pairs of an FP64-accurate product, Gram
+    or lift in one launch: 36 pair products per operator slice set, above the
+    ridge, so tensor-bound).  The library brackets every launch with CUDA
+    events on its stream and adds up, per role, its algorithmic bytes (each
+    operand read once -- for an emulation pass the distinct 6-bit slices --
+    and the output written once) and flops (2 M N K per product formed).  The
+    line carries the role that holds most of the kernel's time against its
+    own bound; ``roles`` gives both, and ``kernel_roofline_time_frac`` the
+    roofline time of every launch (max of bytes / measured bandwidth and
+    flops / measured BF16 rate, per role) over the kernel's measured time.
+    """
     ms, calls = info["stage_ms"], info["stage_calls"]
     names = ["lowp_product", "f64_product", "hessenberg", "gram", "pencil", "lift", "other"]
     total = sum(ms[:7])
@@ -241,15 +247,41 @@ def stage_roofline(info, peaks, src):
     roof = None
     tc_ms, tc_n = ms[7], calls[7]
     if tc_n:
-        ach = info["tc_bytes"] / (tc_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": TC_TRAFFIC_PER_LAUNCH,
-                "traffic_scope": "DRAM bytes per launch (mean over the solve's launches, ncu)",
-                "kernel": "k_gemm_bf16_tc", "launches": tc_n, "kernel_ms_per_solve": tc_ms,
-                "kernel_share_of_solve": tc_ms / total if total else None,
-                "algorithmic_bytes_per_launch": info["tc_bytes"] / tc_n,
-                "dominant_stage": dominant, "peak_source": src + " (of measured)" if src == "measured"
-                else src + " (of fallback)"}
+        tens = peaks["bf16_tflops_sustained"] if "bf16_tflops_sustained" in peaks else peaks["bf16_tflops"]
+        rms, rby, rfl = info["tc_role_ms"], info["tc_role_bytes"], info["tc_role_flops"]
+        roles = {}
+        t_roof = 0.0
+        for r, nm in enumerate(["lowp_product", "f64_emulation"]):
+            if rms[r] <= 0:
+                continue
+            t_b = rby[r] / (hbm * 1e9) * 1e3   # ms at the measured copy bandwidth
+            t_f = rfl[r] / (tens * 1e12) * 1e3  # ms at the measured BF16 rate
+            t_roof += max(t_b, t_f)
+            roles[nm] = {"ms": rms[r], "bound": "hbm" if t_b >= t_f else "tensor",
+                         "achieved_gbs": rby[r] / (rms[r] * 1e-3) / 1e9,
+                         "achieved_tflops": rfl[r] / (rms[r] * 1e-3) / 1e12,
+                         "frac": max(t_b, t_f) / rms[r]}
+        # the role that holds most of the kernel's time carries the line; the
+        # other role and the kernel-wide fraction (roofline time of every
+        # launch / its measured time) are reported beside it
+        main = max(roles, key=lambda k: roles[k]["ms"])
+        d = roles[main]
+        if d["bound"] == "tensor":
+            roof = {"bound": "tensor", "achieved": d["achieved_tflops"], "peak": tens, "unit": "TFLOP/s",
+                    "frac": d["achieved_tflops"] / tens}
+        else:
+            roof = {"bound": "hbm", "achieved": d["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+                    "frac": d["achieved_gbs"] / hbm}
+        roof.update({"traffic": TC_TRAFFIC_PER_LAUNCH.get(main),
+                     "traffic_scope": "DRAM bytes per launch of this role (mean over one solve, ncu)",
+                     "kernel": "k_gemm_bf16_tc", "role": main, "launches": tc_n,
+                     "kernel_ms_per_solve": tc_ms, "kernel_share_of_solve": tc_ms / total if total else None,
+                     "role_share_of_kernel": d["ms"] / tc_ms, "roles": roles,
+                     "kernel_roofline_time_frac": t_roof / tc_ms,
+                     "algorithmic_bytes_per_launch": info["tc_bytes"] / tc_n,
+                     "dominant_stage": dominant,
+                     "peak_source": src + " (of measured; BF16 sustained for the tensor bound)" if src == "measured"
+                     else src + " (of fallback)"})
     return roof, stages
 
 

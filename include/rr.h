@@ -144,6 +144,13 @@ typedef struct {
                             method's sweep in FP64-accurate arithmetic from the Ritz
                             vectors, taken when the corrections stop contracting the
                             residual, and as a batched problem's last two sweeps)    */
+  double tc_role_ms[2];   /* with params.profile: stage_ms[RR_KERNEL_TC] split by the
+                            launch's role: [0] low-precision products (filter,
+                            split corrections, E4M3), [1] FP64-emulation passes
+                            (FP64-accurate products, Grams, lifts)                  */
+  double tc_role_bytes[2];/* algorithmic bytes of those launches (as tc_bytes)        */
+  double tc_role_flops[2];/* algorithmic flops: 2 M N K per product formed (per slice
+                            pair of an emulation pass)                              */
 } rr_info;
 
 /* Stages of rr_info.stage_ms: */

@@ -51,7 +51,8 @@ class RrInfo(ctypes.Structure):
     _fields_ = [("n_converged", c_i32), ("sweeps", c_i32), ("refine_sweeps", c_i32),
                 ("cols_dropped", c_i32), ("max_res", c_dbl), ("res_history", c_dbl * 64),
                 ("stage_ms", c_dbl * 8), ("stage_calls", c_i32 * 8), ("cond_G_est", c_dbl),
-                ("cond_history", c_dbl * 64), ("tc_bytes", c_dbl), ("polish_sweeps", c_i32)]
+                ("cond_history", c_dbl * 64), ("tc_bytes", c_dbl), ("polish_sweeps", c_i32),
+                ("tc_role_ms", c_dbl * 2), ("tc_role_bytes", c_dbl * 2), ("tc_role_flops", c_dbl * 2)]
 
 
 _SIGS = {

@@ -130,6 +130,8 @@ def _info_dict(info: RrInfo, status: int):
             "stage_ms": [info.stage_ms[i] for i in range(8)],
             "stage_calls": [info.stage_calls[i] for i in range(8)],
             "cond_G_est": info.cond_G_est, "cols_dropped": info.cols_dropped, "tc_bytes": info.tc_bytes, "polish_sweeps": info.polish_sweeps,
+            "tc_role_ms": list(info.tc_role_ms), "tc_role_bytes": list(info.tc_role_bytes),
+            "tc_role_flops": list(info.tc_role_flops),
             "cond_history": [info.cond_history[i] for i in range(min(sweeps, 64))]}
 
 

@@ -589,14 +589,15 @@ rr_status emu_gemm(cudaStream_t s, const EmuOperator& op, int trans, int64_t N, 
   RR_TRY(check_launch("emu_gemm slices"));
   const int64_t lda = trans ? op.m : op.n;  // K-contiguous leading dimension of the A slices
   uint32_t pairs[64];
-  const int np = emu_pairs(S, 2 * N <= 256, pairs);
-  // one launch per pair: consecutive launches add into C in stream order
-  for (int z = 0; z < np; ++z) {
-    const int nq = (int)(pairs[z] >> 16);
-    TcEmu e{C, ldc, nullptr, rexp, xe, (int)N, S, S, (int)M, (int)N, 1, pairs + z, 4096};
-    RR_TRY(gemm_bf16_tc_emu(M, N * nq, K, As, lda, T, K, e, s));
-  }
-  return RR_OK;
+  const bool two = 2 * N <= 256;
+  const int np = emu_pairs(S, two, pairs);
+  // one launch for every pair (grid z = pair): the tiles of all pairs share
+  // the GPU, no SM idles between passes, and each CTA adds its exactly scaled
+  // products into C with FP64 atomics (C starts at zero).  A one-slice pair
+  // of a two-slice launch also reads the next X slice (present: nq = 1 only
+  // where q0 + 1 < S) and ignores it.
+  TcEmu e{C, ldc, nullptr, rexp, xe, (int)N, S, S, (int)M, (int)N, np, pairs, 4096};
+  return gemm_bf16_tc_emu(M, two ? 2 * N : N, K, As, lda, T, K, e, s);
 }
 
 // ---------------------------------------------------------------------------

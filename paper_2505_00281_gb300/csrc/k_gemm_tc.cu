@@ -184,6 +184,7 @@ struct TcArgs {
   int nb;
   int a_slice_rows, b_slice_rows;
   int npairs;
+  int pair_major;  // grid (pair, split, tile) instead of (tile, split, pair)
   uint32_t pair[48];
 };
 
@@ -196,7 +197,7 @@ __device__ __forceinline__ double mul_pow2(double d, int e) {
   return d == 0.0 ? d : ldexp(d, e);
 }
 
-template <bool kF8>
+template <bool kF8, bool kEmu>
 __global__ void __launch_bounds__(128, 1) k_gemm_bf16_tc(const __grid_constant__ CUtensorMap tmA,
                                                           const __grid_constant__ CUtensorMap tmB,
                                                           const __grid_constant__ CUtensorMap tmA2,
@@ -216,14 +217,19 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16_tc(const __grid_constant__
   __shared__ uint32_t s_tmem;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t m0 = (int64_t)blockIdx.x * kBM;
+  // pair-major grids (x = slice pair, z = row tile) put the CTAs of one row
+  // tile's slice pairs side by side, so a tile of an operator slice read by
+  // several pairs comes from HBM once and from L2 for the others
+  const int tile = a.pair_major ? (int)blockIdx.z : (int)blockIdx.x;
+  const int zi = a.pair_major ? (int)blockIdx.x : (int)blockIdx.z;
+  const int64_t m0 = (int64_t)tile * kBM;
   const int split = blockIdx.y;
   const int ks0 = split * a.ksteps_per_split;
   int ks1 = ks0 + a.ksteps_per_split;
   if (ks1 > a.nk) ks1 = a.nk;
   const int nks = ks1 > ks0 ? ks1 - ks0 : 0;
   // slice pair of this launch row (FP64 emulation; 0 otherwise)
-  const uint32_t pz = a.npairs > 0 ? a.pair[blockIdx.z] : 0u;
+  const uint32_t pz = a.npairs > 0 ? a.pair[zi] : 0u;
   const int p0 = (int)(pz & 0xFF), q0 = (int)((pz >> 8) & 0xFF), nq = (int)((pz >> 16) & 0xFF);
   const int a_off = p0 * a.a_slice_rows, b_off = q0 * a.b_slice_rows;
 
@@ -313,43 +319,45 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16_tc(const __grid_constant__
     __syncwarp();
     ready = __all_sync(0xffffffffu, ready) && *(volatile int*)&g_tc_error == 0;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ready && a.cexp) {
-      // FP64-emulation epilogue; the 32 C loads of a chunk are issued before
-      // any store (read-modify-write mode)
-      const int64_t row = m0 + warp * 32 + lane;
-      const bool rv = row < a.M;
-      const int er = rv ? __ldg(a.rexp + row) - 6 * (p0 + 1) - 6 * (q0 + nq) : 0;
-      double* __restrict__ Cr = a.C64 ? a.C64 + row
-                                      : a.part + ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * a.M * a.nb + row;
-      const int64_t ldo = a.C64 ? a.ldc64 : a.M;
-      const bool rmw = a.C64 && !a.atomic;
-      for (int c0 = 0; c0 < a.nb; c0 += 32) {
-        uint32_t r0[32], r1[32];
-        tmem_ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r0);
-        if (nq > 1) tmem_ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a.nb + c0), r1);
-        if (rv) {
-          const int cnt = a.nb - c0 < 32 ? a.nb - c0 : 32;
-          double cv[32];
-          if (rmw) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (j < cnt) cv[j] = Cr[(int64_t)(c0 + j) * ldo];
-          }
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            if (j < cnt) {
-              int iv = __float2int_rn(__uint_as_float(r0[j]));
-              if (nq > 1) iv = iv * 64 + __float2int_rn(__uint_as_float(r1[j]));
-              const double t = mul_pow2(__int2double_rn(iv), er + __ldg(a.cexp + c0 + j));
-              if (rmw) cv[j] += t;
-              else if (a.C64) atomicAdd(Cr + (int64_t)(c0 + j) * ldo, t);
-              else Cr[(int64_t)(c0 + j) * ldo] = t;
+    if (kEmu) {
+      if (ready) {
+        // FP64-emulation epilogue; the 32 C loads of a chunk are issued before
+        // any store (read-modify-write mode)
+        const int64_t row = m0 + warp * 32 + lane;
+        const bool rv = row < a.M;
+        const int er = rv ? __ldg(a.rexp + row) - 6 * (p0 + 1) - 6 * (q0 + nq) : 0;
+        double* __restrict__ Cr = a.C64 ? a.C64 + row
+                                        : a.part + ((size_t)zi * gridDim.y + blockIdx.y) * a.M * a.nb + row;
+        const int64_t ldo = a.C64 ? a.ldc64 : a.M;
+        const bool rmw = a.C64 && !a.atomic;
+        for (int c0 = 0; c0 < a.nb; c0 += 32) {
+          uint32_t r0[32], r1[32];
+          tmem_ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r0);
+          if (nq > 1) tmem_ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a.nb + c0), r1);
+          if (rv) {
+            const int cnt = a.nb - c0 < 32 ? a.nb - c0 : 32;
+            double cv[32];
+            if (rmw) {
+  #pragma unroll
+              for (int j = 0; j < 32; ++j)
+                if (j < cnt) cv[j] = Cr[(int64_t)(c0 + j) * ldo];
             }
-          }
-          if (rmw) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (j < cnt) Cr[(int64_t)(c0 + j) * ldo] = cv[j];
+  #pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              if (j < cnt) {
+                int iv = __float2int_rn(__uint_as_float(r0[j]));
+                if (nq > 1) iv = iv * 64 + __float2int_rn(__uint_as_float(r1[j]));
+                const double t = mul_pow2(__int2double_rn(iv), er + __ldg(a.cexp + c0 + j));
+                if (rmw) cv[j] += t;
+                else if (a.C64) atomicAdd(Cr + (int64_t)(c0 + j) * ldo, t);
+                else Cr[(int64_t)(c0 + j) * ldo] = t;
+              }
+            }
+            if (rmw) {
+  #pragma unroll
+              for (int j = 0; j < 32; ++j)
+                if (j < cnt) Cr[(int64_t)(c0 + j) * ldo] = cv[j];
+            }
           }
         }
       }
@@ -411,13 +419,16 @@ void tc_prof_attach(TcProf* p) { t_tc_prof = p; }
 struct TcProfScope {
   TcProf* p;
   cudaStream_t s;
-  TcProfScope(cudaStream_t s_, double bytes) : p(t_tc_prof), s(s_) {
+  TcProfScope(cudaStream_t s_, double bytes, double flops, int role) : p(t_tc_prof), s(s_) {
     if (!p) return;
     cudaEvent_t e;
     cudaEventCreate(&e);
     cudaEventRecord(e, s);
     p->ev.push_back(e);
+    p->role.push_back(role);
     p->bytes += bytes;
+    p->role_bytes[role] += bytes;
+    p->role_flops[role] += flops;
     p->launches += 1;
   }
   ~TcProfScope() {
@@ -439,8 +450,9 @@ int& gemm_split_cap() {
 rr_status tc_prepare_attributes() {
   static bool done = false;
   if (!done) {
-    RR_CUDA(cudaFuncSetAttribute(k_gemm_bf16_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-    RR_CUDA(cudaFuncSetAttribute(k_gemm_bf16_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    RR_CUDA(cudaFuncSetAttribute(k_gemm_bf16_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    RR_CUDA(cudaFuncSetAttribute(k_gemm_bf16_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    RR_CUDA(cudaFuncSetAttribute(k_gemm_bf16_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
     done = true;
   }
   return RR_OK;
@@ -594,7 +606,7 @@ static rr_status gemm_bf16_tc_impl(int64_t M, int64_t N, int64_t K, const __nv_b
   if (stages < 2) return RR_ERR_ARG;
   const size_t smem = 1024 + (size_t)stages * stage_bytes + (2 * stages + 1) * sizeof(uint64_t);
   RR_TRY(tc_prepare_attributes());
-  TcArgs a;
+  TcArgs a{};
   a.M = M;
   a.N = N;
   a.K = K;
@@ -626,25 +638,34 @@ static rr_status gemm_bf16_tc_impl(int64_t M, int64_t N, int64_t K, const __nv_b
     k_tc_init_c<<<gi, 256, 0, s>>>(M, N, C, ldc, R, ldr, coef);
     note_launches(1);
   }
-  dim3 grid((unsigned)tiles, (unsigned)splits, (unsigned)npairs);
+  a.pair_major = emu && emu->C64 && npairs > 1 && tiles <= 65535;
+  dim3 grid = a.pair_major ? dim3((unsigned)npairs, (unsigned)splits, (unsigned)tiles)
+                           : dim3((unsigned)tiles, (unsigned)splits, (unsigned)npairs);
   a.rscale = a.cscale = nullptr;
   // algorithmic bytes of this launch: every operand tile it needs read once
-  // (the distinct slices of an emulation launch), the output written once
-  double abytes;
+  // (the distinct slices of an emulation launch), the output written once;
+  // algorithmic flops: 2 M N K per product it forms (per slice pair of an
+  // emulation launch, with that pair's own slice count)
+  double abytes, aflops = 0.0;
   if (emu) {
     uint64_t amask = 0, bmask = 0;
     for (int z = 0; z < npairs; ++z) {
       const uint32_t pz = emu->pair[z];
       amask |= 1ull << (pz & 0xFF);
       for (uint32_t q = 0; q < ((pz >> 16) & 0xFF); ++q) bmask |= 1ull << (((pz >> 8) & 0xFF) + q);
+      aflops += 2.0 * (double)M * (double)emu->nb * (double)((pz >> 16) & 0xFF) * (double)K;
     }
     abytes = 2.0 * K * ((double)M * __builtin_popcountll(amask) + (double)emu->nb * __builtin_popcountll(bmask)) +
              8.0 * M * emu->nb;
   } else {
     abytes = (split ? 2.0 : 1.0) * 2.0 * K * ((double)M + (double)N) + 4.0 * M * N;
+    aflops = (split ? 3.0 : 1.0) * 2.0 * (double)M * (double)N * (double)K;
   }
-  TcProfScope prof_scope(s, abytes);
-  k_gemm_bf16_tc<false><<<grid, 128, smem, s>>>(ta, tb, ta2, tb2, a);
+  TcProfScope prof_scope(s, abytes, aflops, emu ? 1 : 0);
+  if (emu)  // the FP64-emulation passes: an instantiation of their own (epilogue, profiles)
+    k_gemm_bf16_tc<false, true><<<grid, 128, smem, s>>>(ta, tb, ta2, tb2, a);
+  else
+    k_gemm_bf16_tc<false, false><<<grid, 128, smem, s>>>(ta, tb, ta2, tb2, a);
   return check_launch("gemm_bf16_tc");
 }
 
@@ -702,8 +723,8 @@ rr_status gemm_e4m3_tc(int64_t M, int64_t N, int64_t K, const void* A, int64_t l
     note_launches(1);
   }
   dim3 grid((unsigned)tiles, (unsigned)splits, 1u);
-  TcProfScope prof_scope(s, (double)K * ((double)M + (double)N) + 4.0 * M * N);
-  k_gemm_bf16_tc<true><<<grid, 128, smem, s>>>(ta, tb, ta, tb, a);
+  TcProfScope prof_scope(s, (double)K * ((double)M + (double)N) + 4.0 * M * N, 2.0 * (double)M * N * K, 0);
+  k_gemm_bf16_tc<true, false><<<grid, 128, smem, s>>>(ta, tb, ta, tb, a);
   return check_launch("gemm_e4m3_tc");
 }
 

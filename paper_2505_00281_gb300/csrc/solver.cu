@@ -105,14 +105,21 @@ struct Prof {
         if (cudaEventElapsedTime(&ms, tc.ev[i], tc.ev[i + 1]) == cudaSuccess) {
           inf->stage_ms[RR_KERNEL_TC] += ms;
           inf->stage_calls[RR_KERNEL_TC] += 1;
+          inf->tc_role_ms[tc.role[i / 2]] += ms;
         }
       }
       inf->tc_bytes = tc.bytes;
+      for (int r = 0; r < 2; ++r) {
+        inf->tc_role_bytes[r] = tc.role_bytes[r];
+        inf->tc_role_flops[r] = tc.role_flops[r];
+      }
     }
     for (auto e : pool) cudaEventDestroy(e);
     for (auto e : tc.ev) cudaEventDestroy(e);
     tc.ev.clear();
+    tc.role.clear();
     tc.bytes = 0.0;
+    tc.role_bytes[0] = tc.role_bytes[1] = tc.role_flops[0] = tc.role_flops[1] = 0.0;
     tc.launches = 0;
     pool.clear();
     recs.clear();

@@ -57,7 +57,10 @@ rr_status fill_f32(cudaStream_t s, int64_t n, float v, float* d);
 // (each operand read once, the output written once) are added up.
 struct TcProf {
   std::vector<cudaEvent_t> ev;  // start / end per launch
+  std::vector<int> role;        // per launch: 0 low-precision product, 1 FP64-emulation pass
   double bytes = 0.0;
+  double role_bytes[2] = {0.0, 0.0};
+  double role_flops[2] = {0.0, 0.0};
   int launches = 0;
 };
 void tc_prof_attach(TcProf* p);  // nullptr detaches
