@@ -187,7 +187,7 @@ def aggregate(seconds: float, converged: int, dist=None, device=None):
 # dram__bytes_read.sum + dram__bytes_write.sum, a one-pass capture of every
 # launch of the kernel in one solve; profiles/ncu_gemm_bf16_tc_16384x4096x128.md).
 # Emptied when the kernel changes, until it is captured again.
-TC_TRAFFIC_PER_LAUNCH = {"lowp_product": 234.0e6, "f64_emulation": 96.8e6}
+TC_TRAFFIC_PER_LAUNCH = {"lowp_product": 221.6e6, "f64_emulation": 231.7e6}
 
 
 def stage_roofline(info, peaks, src):

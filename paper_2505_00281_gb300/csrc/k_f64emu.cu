@@ -767,10 +767,19 @@ static rr_status lift_emu_one(cudaStream_t s, int64_t n, int64_t b, int32_t t1, 
   if (!accumulate) k_zero_f64<<<gz, 256, 0, s>>>(n, b, X, ldx);
   note_launches(accumulate ? 2 : 3);
   RR_TRY(check_launch("lift_emu slices"));
-  for (int d = 2; d <= S + 1; ++d) {
-    const uint32_t code = (uint32_t)(d - 2) | (1u << 16);  // p0 = d - 2, q0 = 0, nq = 1: scale 2^(-6d)
-    TcEmu e{X, ldx, nullptr, rexp, yexp, (int)b, 1, 1, 0, 0, 1, &code, 4096};
-    RR_TRY(gemm_bf16_tc_emu(n, b, (d - 1) * K, Acat, S * K, Yrev + (size_t)(S - d + 1) * K, S * K, e, s));
+  uint32_t codes[S];
+  for (int d = 2; d <= S + 1; ++d)
+    codes[d - 2] = (uint32_t)(d - 2) | (1u << 16);  // p0 = d - 2, q0 = 0, nq = 1: scale 2^(-6d)
+  if (K % 64 == 0) {
+    // every diagonal in one launch (pair-major: the diagonals of a row tile
+    // share its A_cat tiles in L2), adding into X with FP64 atomics
+    TcEmu e{X, ldx, nullptr, rexp, yexp, (int)b, 1, 1, 0, 0, S, codes, 4096, (int)K, S};
+    RR_TRY(gemm_bf16_tc_emu(n, b, S * K, Acat, S * K, Yrev, S * K, e, s));
+  } else {
+    for (int d = 2; d <= S + 1; ++d) {
+      TcEmu e{X, ldx, nullptr, rexp, yexp, (int)b, 1, 1, 0, 0, 1, codes + (d - 2), 4096};
+      RR_TRY(gemm_bf16_tc_emu(n, b, (d - 1) * K, Acat, S * K, Yrev + (size_t)(S - d + 1) * K, S * K, e, s));
+    }
   }
   *done = true;
   return RR_OK;

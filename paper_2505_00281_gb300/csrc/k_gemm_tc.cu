@@ -185,6 +185,7 @@ struct TcArgs {
   int a_slice_rows, b_slice_rows;
   int npairs;
   int pair_major;  // grid (pair, split, tile) instead of (tile, split, pair)
+  int lift_ksteps, lift_s;  // > 0: a lift's anti-diagonals, pair z = diagonal p0 + 2
   uint32_t pair[48];
 };
 
@@ -224,14 +225,19 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16_tc(const __grid_constant__
   const int zi = a.pair_major ? (int)blockIdx.x : (int)blockIdx.z;
   const int64_t m0 = (int64_t)tile * kBM;
   const int split = blockIdx.y;
-  const int ks0 = split * a.ksteps_per_split;
-  int ks1 = ks0 + a.ksteps_per_split;
-  if (ks1 > a.nk) ks1 = a.nk;
-  const int nks = ks1 > ks0 ? ks1 - ks0 : 0;
   // slice pair of this launch row (FP64 emulation; 0 otherwise)
   const uint32_t pz = a.npairs > 0 ? a.pair[zi] : 0u;
   const int p0 = (int)(pz & 0xFF), q0 = (int)((pz >> 8) & 0xFF), nq = (int)((pz >> 16) & 0xFF);
   const int a_off = p0 * a.a_slice_rows, b_off = q0 * a.b_slice_rows;
+  // K steps of this pair: all of K, or for a lift's anti-diagonal d = p0 + 2
+  // the first (p0 + 1) lift_ksteps of A and as many of B from its step
+  // (lift_s - 1 - p0) lift_ksteps
+  const int nkz = a.lift_ksteps ? (p0 + 1) * a.lift_ksteps : a.nk;
+  const int bk0 = a.lift_ksteps ? (a.lift_s - 1 - p0) * a.lift_ksteps : 0;
+  const int ks0 = split * a.ksteps_per_split;
+  int ks1 = ks0 + a.ksteps_per_split;
+  if (ks1 > nkz) ks1 = nkz;
+  const int nks = ks1 > ks0 ? ks1 - ks0 : 0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < a.stages; ++s) {
@@ -264,7 +270,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16_tc(const __grid_constant__
         mbar_expect_tx(&full[s], stage_bytes);
         const int kx = (ks0 + i) * (kF8 ? 2 * kBK : kBK);  // elements per 128-byte row
         tma_load_2d(sa, &tmA, &full[s], kx, (int)m0 + a_off);
-        tma_load_2d(sb, &tmB, &full[s], kx, b_off);
+        tma_load_2d(sb, &tmB, &full[s], kx + bk0 * kBK, b_off);
         if (spl) {
           tma_load_2d(sb + b_bytes, &tmA2, &full[s], kx, (int)m0 + a_off);
           tma_load_2d(sb + b_bytes + a_bytes, &tmB2, &full[s], kx, b_off);
@@ -589,7 +595,7 @@ static rr_status gemm_bf16_tc_impl(int64_t M, int64_t N, int64_t K, const __nv_b
   if (emu && emu->part) {
     splits = tc_emu_partial_splits(M, K, npairs, emu->max_kchunk);
     if (splits < 1) return RR_ERR_ARG;
-  } else if (tiles * npairs < sms) {
+  } else if (tiles * npairs < sms && !(emu && emu->lift_k0 > 0)) {  // a lift's diagonals: whole K ranges
     splits = (int)(sms / (tiles * npairs));
     if (splits > nk) splits = nk;
     if (gemm_split_cap() > 0 && splits > gemm_split_cap()) splits = gemm_split_cap();
@@ -638,6 +644,10 @@ static rr_status gemm_bf16_tc_impl(int64_t M, int64_t N, int64_t K, const __nv_b
     k_tc_init_c<<<gi, 256, 0, s>>>(M, N, C, ldc, R, ldr, coef);
     note_launches(1);
   }
+  a.lift_ksteps = emu && emu->lift_k0 > 0 ? emu->lift_k0 / kBK : 0;
+  a.lift_s = emu ? emu->lift_s : 0;
+  if (a.lift_ksteps && (emu->lift_k0 % kBK || (int64_t)emu->lift_s * emu->lift_k0 != K || splits != 1))
+    return RR_ERR_ARG;
   a.pair_major = emu && emu->C64 && npairs > 1 && tiles <= 65535;
   dim3 grid = a.pair_major ? dim3((unsigned)npairs, (unsigned)splits, (unsigned)tiles)
                            : dim3((unsigned)tiles, (unsigned)splits, (unsigned)npairs);
@@ -653,7 +663,8 @@ static rr_status gemm_bf16_tc_impl(int64_t M, int64_t N, int64_t K, const __nv_b
       const uint32_t pz = emu->pair[z];
       amask |= 1ull << (pz & 0xFF);
       for (uint32_t q = 0; q < ((pz >> 16) & 0xFF); ++q) bmask |= 1ull << (((pz >> 8) & 0xFF) + q);
-      aflops += 2.0 * (double)M * (double)emu->nb * (double)((pz >> 16) & 0xFF) * (double)K;
+      const double kz = emu->lift_k0 > 0 ? (double)(((pz & 0xFF) + 1) * emu->lift_k0) : (double)K;
+      aflops += 2.0 * (double)M * (double)emu->nb * (double)((pz >> 16) & 0xFF) * kz;
     }
     abytes = 2.0 * K * ((double)M * __builtin_popcountll(amask) + (double)emu->nb * __builtin_popcountll(bmask)) +
              8.0 * M * emu->nb;

@@ -117,6 +117,10 @@ struct TcEmu {
   int npairs;                      // <= 48
   const uint32_t* pair;            // host array
   int max_kchunk;                  // K elements per exact FP32 accumulation
+  // > 0: a lift's anti-diagonal products in one launch (pair z codes diagonal
+  // d = p0 + 2 of lift_s): A's K range [0, (p0 + 1) lift_k0), B's
+  // [(lift_s - 1 - p0) lift_k0, lift_s lift_k0); K = lift_s lift_k0
+  int lift_k0, lift_s;
 };
 rr_status gemm_bf16_tc_emu(int64_t M, int64_t N, int64_t K, const __nv_bfloat16* A, int64_t lda,
                            const __nv_bfloat16* B, int64_t ldb, const TcEmu& e, cudaStream_t s);
