@@ -11,6 +11,9 @@
 // are small FP64 GEMMs spread over the GPU.
 #include <cfloat>
 #include <climits>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include <cooperative_groups.h>
 
@@ -1216,8 +1219,14 @@ __global__ void k_v32_to_64(int c, int cpad, const float* __restrict__ V32, doub
 }
 
 
+// scratch of one whitening (whiten())
+struct WhitenScratch {
+  double *W1, *W2, *T, *E, *E2, *F;
+};
+
 struct PencilWs {
   double *W1, *W2, *T, *E, *E2, *F, *C, *V, *Vp, *M, *Mp, *sig, *mu;
+  WhitenScratch wb;                    // the SVD pencil's second whitening (beside the first)
   double* sh;                          // [4] bracket and scales of the eigen shift
   int* shok;                           // [kShiftTrials] definiteness trials
   double* cond;                        // [4] condition estimates of the whitened Grams, drop counts
@@ -1261,6 +1270,12 @@ static bool carve_pencil(Arena& ar, int b1, int b2, PencilWs& w) {
   w.F = ar.take<double>(bb);
   w.C = ar.take<double>(bb);
   w.V = ar.take<double>(bb);
+  w.wb.W1 = ar.take<double>(bb);
+  w.wb.W2 = ar.take<double>(bb);
+  w.wb.T = ar.take<double>(bb);
+  w.wb.E = ar.take<double>(bb);
+  w.wb.E2 = ar.take<double>(bb);
+  w.wb.F = ar.take<double>(bb);
   w.Vp = ar.take<double>(cc);
   w.M = ar.take<double>(rc);
   w.Mp = ar.take<double>(rc);
@@ -1338,7 +1353,7 @@ __global__ void k_cond_est(int b, const double* __restrict__ G, const double* __
 // E is formed in FP64; the correction W (E/2 - 3/8 E^2) only needs FP32
 // relative accuracy (its rounding, u32 |E|, is what the next step removes),
 // so E^2 and W F are FP32 products.
-static void whiten(cudaStream_t s, int b, const double* G, PencilWs& w, int* dropped, double* Wout) {
+static void whiten(cudaStream_t s, int b, const double* G, const WhitenScratch& w, int* dropped, double* Wout) {
   const int g1 = (b * b + 255) / 256;
   if (b <= kCT * kCTMax) {
     const size_t sm = chol_blocked_smem(b);
@@ -1369,6 +1384,55 @@ static void whiten(cudaStream_t s, int b, const double* G, PencilWs& w, int* dro
   }
   if (Wc != Wout) cudaMemcpyAsync(Wout, Wc, (size_t)b * b * sizeof(double), cudaMemcpyDeviceToDevice, s);
   note_launches(16);
+}
+
+// A second stream per caller stream (and device) for independent small steps
+// (the SVD pencil's two whitenings), created on first use and kept for the
+// life of the process; work forks to it and joins back through events, which
+// stream capture records as two parallel branches.
+struct SideStream {
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+
+static std::mutex g_side_mu;
+static std::map<std::pair<int, cudaStream_t>, SideStream> g_side_pool;
+
+static rr_status side_stream(cudaStream_t s, SideStream* out) {
+  auto& mu = g_side_mu;
+  auto& pool = g_side_pool;
+  int dev = 0;
+  RR_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = pool.find({dev, s});
+  if (it == pool.end()) {
+    SideStream ss;
+    RR_CUDA(cudaStreamCreateWithFlags(&ss.s2, cudaStreamNonBlocking));
+    RR_CUDA(cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming));
+    RR_CUDA(cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming));
+    it = pool.emplace(std::make_pair(dev, s), ss).first;
+  }
+  *out = it->second;
+  return RR_OK;
+}
+
+rr_status pencil_side_prepare(cudaStream_t s) {
+  SideStream ss;
+  return side_stream(s, &ss);
+}
+
+// Destroy the side stream of s (before s itself is destroyed; its work must be
+// complete).
+void pencil_side_release(cudaStream_t s) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  std::lock_guard<std::mutex> lock(g_side_mu);
+  auto it = g_side_pool.find({dev, s});
+  if (it == g_side_pool.end()) return;
+  cudaStreamDestroy(it->second.s2);
+  cudaEventDestroy(it->second.fork);
+  cudaEventDestroy(it->second.join);
+  g_side_pool.erase(it);
 }
 
 // floor[0] = scale * max_j |M(:, j)|^2 (one block)
@@ -2115,7 +2179,7 @@ extern "C" rr_status rr_pencil_eig(int64_t b, const double* H, const double* G, 
   cudaStream_t s = as_stream(stream);
   const int n = (int)b;
   RR_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), s));
-  whiten(s, n, G, w, w.drop1, w.W1);
+  whiten(s, n, G, WhitenScratch{w.W1, w.W2, w.T, w.E, w.E2, w.F}, w.drop1, w.W1);
   RR_CUDA(cudaMemsetAsync(w.cond, 0, 4 * sizeof(double), s));
   k_cond_est<<<1, 256, 0, s>>>(n, G, w.W1, w.drop1, w.cond);
   // C = W^T H W, symmetrised and shifted positive definite (C - mu I)
@@ -2147,13 +2211,21 @@ extern "C" rr_status rr_pencil_svd(int64_t b1, int64_t b2, const double* B, cons
   cudaStream_t s = as_stream(stream);
   const int n1 = (int)b1, n2 = (int)b2, r = n1 < n2 ? n1 : n2;
   RR_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), s));
-  // whitening of both sides: Wu -> C, Wv -> V (whiten() uses W1/W2/T/E/E2/F as scratch)
-  whiten(s, n1, Gu, w, w.drop1, w.C);
-  whiten(s, n2, Gv, w, w.drop2, w.V);
+  // whitening of both sides, at the same time on two streams (each is a
+  // chain of latency-bound small kernels): Wu -> C on s, Wv -> V on the side
+  // stream, each with its own scratch
+  SideStream ss;
+  RR_TRY(side_stream(s, &ss));
+  RR_CUDA(cudaEventRecord(ss.fork, s));
+  RR_CUDA(cudaStreamWaitEvent(ss.s2, ss.fork, 0));
+  whiten(s, n1, Gu, WhitenScratch{w.W1, w.W2, w.T, w.E, w.E2, w.F}, w.drop1, w.C);
+  whiten(ss.s2, n2, Gv, w.wb, w.drop2, w.V);
+  k_cond_est<<<1, 256, 0, ss.s2>>>(n2, Gv, w.V, w.drop2, w.cond + 1);  // cond[1], drops[3]
+  RR_CUDA(cudaEventRecord(ss.join, ss.s2));
+  RR_CUDA(cudaStreamWaitEvent(s, ss.join, 0));
   RR_CUDA(cudaMemcpyAsync(w.W1, w.C, (size_t)n1 * n1 * sizeof(double), cudaMemcpyDeviceToDevice, s));
   RR_CUDA(cudaMemcpyAsync(w.W2, w.V, (size_t)n2 * n2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
   k_cond_est<<<1, 256, 0, s>>>(n1, Gu, w.W1, w.drop1, w.cond);      // cond[0], drops[2]
-  k_cond_est<<<1, 256, 0, s>>>(n2, Gv, w.W2, w.drop2, w.cond + 1);  // cond[1], drops[3]
   // Cw = Wu^T B Wv (b1 x b2) -> C
   gemm_small(s, 0, 0, n1, n2, n2, 1.0, B, n1, w.W2, n2, 0.0, w.T, n1);
   gemm_small(s, 1, 0, n1, n2, n1, 1.0, w.W1, n1, w.T, n1, 0.0, w.C, n1);

@@ -1373,6 +1373,7 @@ extern "C" rr_status rr_batch_svd_tuned(int32_t count, const rr_operator* A, con
   for (int i = 0; i < NS && st == RR_OK; ++i) {
     cu(cudaStreamCreateWithFlags(&br[i], cudaStreamNonBlocking), "rr_batch_svd stream");
     cu(cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming), "rr_batch_svd event");
+    if (st == RR_OK && pencil_side_prepare(br[i]) != RR_OK) st = RR_ERR_CUDA;  // before the capture
   }
   cu(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming), "rr_batch_svd event");
   // the graph must see the caller's prior work on `s`: order cap after s
@@ -1419,6 +1420,7 @@ extern "C" rr_status rr_batch_svd_tuned(int32_t count, const rr_operator* A, con
   if (pre) cudaEventDestroy(pre);
   if (cap) cudaStreamDestroy(cap);
   for (int i = 0; i < NS; ++i) {
+    if (br[i]) pencil_side_release(br[i]);
     if (br[i]) cudaStreamDestroy(br[i]);
     if (join[i]) cudaEventDestroy(join[i]);
   }

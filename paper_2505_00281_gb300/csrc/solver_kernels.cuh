@@ -64,6 +64,10 @@ struct TcProf {
   int launches = 0;
 };
 void tc_prof_attach(TcProf* p);  // nullptr detaches
+// the small pencils' side stream for the caller stream s (created here if new;
+// call before capturing work on s)
+rr_status pencil_side_prepare(cudaStream_t s);
+void pencil_side_release(cudaStream_t s);  // before s is destroyed, its work complete
 int& gemm_split_cap();
 struct GemmSplitCap {
   int prev;
