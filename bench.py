@@ -21,6 +21,7 @@ instance (seed + rank), no collective on the data path ("scaling": "weak").
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import math
 import os
@@ -66,7 +67,9 @@ def load_peaks():
 
 # --------------------------------------------------------------------------- clocks
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples every 100 ms; stop(t0, t1) keeps the samples taken
+    between the host wall-clock times t0 and t1 (the timed region)."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -78,12 +81,12 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
 
-    def stop(self):
+    def stop(self, t0=None, t1=None):
         if not self.proc:
             return None
         self.proc.terminate()
@@ -92,24 +95,30 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
             out = ""
-        sm, mx, reasons = [], [], set()
+        rows = []
         for line in out.splitlines():
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[2]), float(parts[3]), parts[6:10]))
             except ValueError:
                 continue
-            for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
-                                  "sw_power_cap"), parts[5:9]):
+        inside = [r for r in rows if t0 is None or (t0 - 0.05 <= r[0] <= t1 + 0.05)]
+        if not inside and rows and t0 is not None:
+            # a region shorter than the sampling interval: the sample nearest its middle
+            mid = 0.5 * (t0 + t1)
+            inside = [min(rows, key=lambda r: abs(r[0] - mid))]
+        if not inside:
+            return None
+        reasons = set()
+        for r in inside:
+            for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), r[3]):
                 if val.lower().startswith("active"):
                     reasons.add(name)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
-                "reasons": sorted(reasons)}
+        return {"sm_mhz": statistics.median([r[1] for r in inside]), "sm_max_mhz": max(r[2] for r in inside),
+                "samples": len(inside), "reasons": sorted(reasons)}
 
 
 # --------------------------------------------------------------------------- oracle legs
@@ -396,8 +405,10 @@ def run_ours(args):
     launches0 = L.rr_kernel_launches()
     barrier()
     clocks.start()
+    time.sleep(0.3)  # nvidia-smi's first samples come after its start-up
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    wt0 = time.time()
     ev0.record(stream)
     conv = 0
     infos = []
@@ -407,7 +418,8 @@ def run_ours(args):
         infos.append(info)
     ev1.record(stream)
     barrier()
-    clk = clocks.stop()
+    wt1 = time.time()
+    clk = clocks.stop(wt0, wt1)
     launches = L.rr_kernel_launches() - launches0
     t = ev0.elapsed_time(ev1) / 1e3
     t, conv = aggregate(t, conv, dist, dev)
@@ -912,7 +924,7 @@ def run_stage(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true")
