@@ -790,6 +790,8 @@ def run_stage(args):
                           "fp64": {"seconds": t_64, "problems_per_s": len(ops) / t_64,
                                    "pairs_per_s": conv(inf_64) / t_64, "failed_by_class": failures(st_64)},
                           "classes": {k: len(v) for k, v in by_class.items()}, "tune_seconds": t_tune,
+                          "sweeps_mean": {"default": float(np.mean([i["sweeps"] for i in inf_def])),
+                                          "fp64": float(np.mean([i["sweeps"] for i in inf_64]))},
                           "default": {"seconds": t_def, "problems_per_s": len(ops) / t_def,
                                       "pairs_per_s": conv(inf_def) / t_def, "failed_by_class": failures(st_def),
                                       "max_res_by_class": {k: max(i["max_res"] for op_, i in zip(ops, inf_def)
@@ -946,7 +948,7 @@ def main():
     ap.add_argument("--batch-sweeps", type=int, default=12, help="sweeps of every problem for --stage batch")
     ap.add_argument("--table", default="", help="--stage batch: write the tuned table (JSON) here")
     ap.add_argument("--tune", action="store_true", help="--stage batch: tune now instead of the shipped table")
-    ap.add_argument("--refine-degree", type=int, default=1,
+    ap.add_argument("--refine-degree", type=int, default=0,
                     help="--stage batch: products per refinement sweep (0: the power degree)")
     ap.add_argument("--train", type=int, default=48, help="training solves for --stage warm")
     ap.add_argument("--test", type=int, default=8, help="held-out solves for --stage warm")

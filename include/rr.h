@@ -214,11 +214,14 @@ rr_status rr_svd(const rr_operator* A, const rr_params* p, double* sigma, double
  * package's autotuner): branches = concurrent graph branches (1..64, default
  * 16), max_splits = upper bound on the K splits of each tensor-core product
  * (0 = as many as fill the GPU, the single-problem choice), order = 0 (as
- * given) or 1 (largest m n first). */
+ * given) or 1 (largest m n first), fixed_sweeps = 0 (default: each problem
+ * stops at tol under device-side loop control) or 1 (every problem runs
+ * max_sweeps sweeps, keeping the triplets it reached tol with). */
 typedef struct {
   int32_t branches;
   int32_t max_splits;
   int32_t order;
+  int32_t fixed_sweeps;
 } rr_batch_tuning;
 
 /* Bytes of device workspace rr_batch_svd needs for `count` operators. */
@@ -230,9 +233,16 @@ size_t rr_batch_workspace_size(int32_t count, const rr_operator* A, const rr_par
  * `seed` + problem index).  per_problem (host, count entries) and info (host,
  * count entries) receive each problem's status and counts.  The batch runs
  * as captured CUDA graphs launched on `stream` (one graph for up to 4096
- * problem-sweeps, i.e. 4096 / max_sweeps problems), every problem for exactly
- * max_sweeps sweeps; a problem whose k wanted residuals reached tol keeps
- * those Ritz triplets through its remaining sweeps.  Synchronises. */
+ * captured problem-sweeps).  A problem's first sweep is captured as plain
+ * graph nodes and its later sweeps run inside WHILE graph nodes: after each
+ * sweep a kernel checks the k wanted residuals against tol and the sweep
+ * count against max_sweeps and sets the node's condition, so every problem
+ * stops on the GPU as soon as it converges (info[i].sweeps = the sweeps it
+ * ran).  With the mixed-precision refinement, a problem whose correction
+ * sweeps stop contracting its residual (largest wanted residual above 0.3
+ * times the previous sweep's), or that reaches the last two of max_sweeps,
+ * continues with FP64 polish sweeps (the correction sweep in FP64-accurate
+ * arithmetic).  Synchronises. */
 rr_status rr_batch_svd(int32_t count, const rr_operator* A, const rr_params* p, uint64_t seed,
                        double* const* sigma, double* const* U, double* const* V,
                        void* ws, size_t ws_bytes, rr_status* per_problem, rr_info* info,

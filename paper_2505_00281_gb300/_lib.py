@@ -44,7 +44,7 @@ class RrParams(ctypes.Structure):
 
 
 class RrBatchTuning(ctypes.Structure):
-    _fields_ = [("branches", c_i32), ("max_splits", c_i32), ("order", c_i32)]
+    _fields_ = [("branches", c_i32), ("max_splits", c_i32), ("order", c_i32), ("fixed_sweeps", c_i32)]
 
 
 class RrInfo(ctypes.Structure):

@@ -175,7 +175,9 @@ def rr_svd(op: RrOperator, params: RrParams, device="cuda", stream=None, ws=None
 
 def rr_batch_svd(ops, params: RrParams, seed: int, device="cuda", stream=None, tuning=None):
     """Batched SVDs in one graph launch.  Returns (list of (sigma, U, V), statuses, infos).
-    tuning: None (library defaults) or a dict with branches, max_splits, order."""
+    tuning: None (library defaults) or a dict with branches, max_splits, order and
+    optionally fixed_sweeps (1: every problem runs max_sweeps sweeps; default 0:
+    each problem stops at tol under device-side loop control)."""
     L = lib()
     cnt = len(ops)
     arr = (RrOperator * cnt)(*ops)
@@ -196,7 +198,8 @@ def rr_batch_svd(ops, params: RrParams, seed: int, device="cuda", stream=None, t
         st = L.rr_batch_svd(cnt, arr, ctypes.byref(params), seed, S, U, V, _p(ws), ws.numel(), per, infos,
                             _stream(stream))
     else:
-        t = RrBatchTuning(int(tuning["branches"]), int(tuning["max_splits"]), int(tuning["order"]))
+        t = RrBatchTuning(int(tuning["branches"]), int(tuning["max_splits"]), int(tuning["order"]),
+                          int(tuning.get("fixed_sweeps", 0)))
         st = L.rr_batch_svd_tuned(cnt, arr, ctypes.byref(params), seed, S, U, V, _p(ws), ws.numel(),
                                   ctypes.byref(t), per, infos, _stream(stream))
     if st not in (RR.OK, RR.ERR_NO_CONV):

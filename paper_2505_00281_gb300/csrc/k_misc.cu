@@ -601,6 +601,38 @@ rr_status vec_mul(cudaStream_t s, int64_t n, const double* a, const double* b, d
   return check_launch("vec_mul");
 }
 
+// Y(:, j) += c_j^pw X(:, j) (n x b, FP64; pw = 1 or 2): the residual blocks'
+// injection terms of the FP64 correction sweep
+__global__ void k_add_cols_scaled(int64_t n, int64_t b, const double* __restrict__ X, int64_t ldx,
+                                  const double* __restrict__ c, int pw, double* __restrict__ Y, int64_t ldy) {
+  const int64_t j = blockIdx.y;
+  const double cj = pw == 2 ? c[j] * c[j] : c[j];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    Y[i + j * ldy] += cj * X[i + j * ldx];
+}
+
+rr_status add_cols_scaled(cudaStream_t s, int64_t n, int64_t b, const double* X, int64_t ldx, const double* c, int pw,
+                          double* Y, int64_t ldy) {
+  if (n <= 0 || b <= 0) return RR_OK;
+  k_add_cols_scaled<<<dim3((unsigned)std::min<int64_t>((n + 255) / 256, 256), (unsigned)b), 256, 0, s>>>(
+      n, b, X, ldx, c, pw, Y, ldy);
+  return check_launch("add_cols_scaled");
+}
+
+// Y (2b x b, ld ldy) = [I; -K]: the coefficients that take [T, X] to
+// T - X K (the projection of a block against an orthonormal X by the lift)
+__global__ void k_eye_neg(int64_t b, const double* __restrict__ K, int64_t ldk, double* __restrict__ Y, int64_t ldy) {
+  const int64_t j = blockIdx.y;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 2 * b; i += (int64_t)gridDim.x * blockDim.x)
+    Y[i + j * ldy] = i < b ? (i == j ? 1.0 : 0.0) : -K[(i - b) + j * ldk];
+}
+
+rr_status eye_neg(cudaStream_t s, int64_t b, const double* K, int64_t ldk, double* Y, int64_t ldy) {
+  if (b <= 0) return RR_OK;
+  k_eye_neg<<<dim3((unsigned)((2 * b + 127) / 128), (unsigned)b), 128, 0, s>>>(b, K, ldk, Y, ldy);
+  return check_launch("eye_neg");
+}
+
 __global__ void k_fill(int64_t n, double v, double* __restrict__ d) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j < n) d[j] = v;
@@ -642,6 +674,42 @@ rr_status keep_frozen(cudaStream_t s, const int* frozen, int64_t m, int64_t n, i
   k_keep_frozen<<<(unsigned)std::min<int64_t>((tot + 255) / 256, 1024), 256, 0, s>>>(frozen, m, n, b, U, U2, V, V2,
                                                                                    sig, sig2);
   return check_launch("keep_frozen");
+}
+
+// Device-side loop control of the batched solver: each problem's sweeps run
+// as the body of a WHILE node of the captured graph, and this one-thread
+// kernel, at the end of every body (and once before the node), sets the
+// node's condition.  ctl[0] = the frozen flag (k_freeze), ctl[1] = sweeps
+// done, ctl[2] = FP64 polish sweeps done, ctl[4..5] = the previous sweep's
+// largest wanted residual (a double); (inc, inc_polish) are added to the
+// counts first.  Another sweep runs while the problem is not frozen, fewer
+// than max_sweeps sweeps are done and, when stop_at >= 0, fewer than
+// stop_at.  With stall != 0 the loop also ends when the largest of the k
+// residuals res[0..k) is above 0.3 times the previous one (the correction
+// sweeps stopped contracting; the FP64 polish takes over); res == nullptr
+// (before the first sweep of a loop) only records the residual.
+__global__ void k_loop_ctl(cudaGraphConditionalHandle h, int* __restrict__ ctl, int inc, int inc_polish,
+                           int max_sweeps, int stop_at, const double* __restrict__ res, int k, int stall) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  const int sw = ctl[1] + inc;
+  ctl[1] = sw;
+  ctl[2] += inc_polish;
+  double* prev = reinterpret_cast<double*>(ctl + 4);
+  bool stalled = false;
+  if (res) {
+    double mx = 0.0;
+    for (int i = 0; i < k; ++i) mx = fmax(mx, res[i]);  // a NaN residual is skipped by fmax
+    stalled = stall != 0 && mx > 0.3 * *prev;
+    *prev = mx;
+  }
+  const bool go = ctl[0] == 0 && sw < max_sweeps && (stop_at < 0 || sw < stop_at) && !stalled;
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+rr_status loop_ctl(cudaStream_t s, cudaGraphConditionalHandle h, int* ctl, int inc, int inc_polish, int max_sweeps,
+                   int stop_at, const double* res, int k, int stall) {
+  k_loop_ctl<<<1, 32, 0, s>>>(h, ctl, inc, inc_polish, max_sweeps, stop_at, res, k, stall);
+  return check_launch("loop_ctl");
 }
 
 rr_status fill(cudaStream_t s, int64_t n, double v, double* d) {

@@ -1881,6 +1881,15 @@ constexpr double kBigAngle = 0.003;
 // direction information: such pairs are neither rotated nor linked (for
 // (near-)equal lam their exact angle would be an arbitrary large rotation)
 constexpr double kCoupleNoise = 1e-13;
+// ... but a pair whose values are well apart (relative gap above kSepGap)
+// is always rotated: its angle c_ij / (lam_j - lam_i) is small and fixed by
+// c_ij even at the rounding level, and an angle left behind between a large
+// and a small singular value returns in the small one's residual multiplied
+// by (sigma_large / sigma_small)^2 (u = C v / sigma takes the v error into u
+// amplified by sigma_large / sigma_small, and A^T u again): a skipped 1e-13
+// coupling between sigma_1 and sigma_16 = sigma_1 / 64 alone leaves that
+// pair at residual 4e-10.
+constexpr double kSepGap = 1e-3;
 constexpr int kClMax = 32;          // largest cluster resolved as one block
 constexpr int kClWarps = 8;         // clusters resolved at once
 
@@ -1907,7 +1916,8 @@ __global__ void k_oa_update(int c, const double* __restrict__ K, const double* _
     const double li = K[i + (size_t)i * c] / T[i + (size_t)i * c];
     const double lj = K[j + (size_t)j * c] / T[j + (size_t)j * c];
     const double cij = oa_coupling(K, T, c, i, j, li, lj);
-    if (fabs(cij) > kCoupleNoise * fmax(fabs(li), fabs(lj))) wij = 0.5 * atan(2.0 * cij / (lj - li));
+    const double big = fmax(fabs(li), fabs(lj));
+    if (fabs(lj - li) > kSepGap * big || fabs(cij) > kCoupleNoise * big) wij = 0.5 * atan(2.0 * cij / (lj - li));
   }
   F1[e] = f + wij;
   Wout[e] = wij;

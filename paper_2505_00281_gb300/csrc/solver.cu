@@ -402,7 +402,10 @@ struct SvdBufs {
   // split mode: lo halves of the correction blocks, FP32 final blocks
   void *Elo2, *Flo2, *E32, *F32;
   float *Ut32, *Vt32;  // FP32 copies of the singular vectors for the refinement's projections
-  int* frozen;  // batch mode: the problem reached tol (later lifts are undone)
+  // batch mode: [0] the problem reached tol (frozen), [1] sweeps done, [2]
+  // FP64 polish sweeps done, [4..5] the previous sweep's largest residual
+  // (a double; device-side loop control)
+  int* frozen;
 };
 
 static void carve_svd(Arena& ar, const Op& op, int64_t b, bool refine, SvdBufs& w) {
@@ -421,7 +424,7 @@ static void carve_svd(Arena& ar, const Op& op, int64_t b, bool refine, SvdBufs& 
   w.sig2 = ar.take<double>(b2);
   w.Ut = ar.take<double>(m * b);
   w.Vt = ar.take<double>(n * b);
-  w.frozen = ar.take<int>(1);
+  w.frozen = ar.take<int>(8);
   w.sig = ar.take<double>(b);
   w.P = ar.take<double>(m * b);
   w.Qm = ar.take<double>(n * b);
@@ -576,35 +579,120 @@ static int svd_pad_quantum(const rr_operator* A, const rr_params* p) {
   return (A->m % q || A->n % q) ? q : 0;
 }
 
-// One sweep of the paper's method in FP64-accurate arithmetic started from the
-// current Ritz vectors (the polish of the refinement phase): q times
-// { U = Alg. 8(A V), V = Alg. 8(A^T U) } with FP64-accurate products and FP64
-// Hessenberg arithmetic, then Algorithm 5 over (U, V) and the lift into
-// (Ut2, Vt2, sig2).  The refinement's low-precision corrections stop
-// improving once the residual reaches the level set by the ratio of the
-// largest to the smallest wanted singular value (about 2e-10 for
-// sigma_j = j^-1.5 with 16 wanted on 2048-4096-row problems, against 4e-11
-// for the all-FP64 method); one such sweep from there, with its own
-// contraction, ends at the all-FP64 method's accuracy.
-static rr_status svd_polish_f64(const Op& op, SvdBufs& w, int64_t b, int q, cudaStream_t s, Prof& prof) {
-  const int64_t m = op.m, n = op.n;
-  double* U = w.P;    // m x b
-  double* V = w.Qm;   // n x b
-  RR_CUDA(cudaMemcpyAsync(V, w.Vt, (size_t)n * b * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  for (int it = 0; it < q; ++it) {
-    STAGE(RR_STAGE_F64_PRODUCT, apply_f64(op, b, V, n, U, m, s));                                  // W = A V
-    STAGE(RR_STAGE_HESSENBERG, basis_step(w.c, true, RR_F64, RR_F64, m, b, U, m, U, m, s));        // U = basis(W)
-    STAGE(RR_STAGE_F64_PRODUCT, apply_f64_T(op, b, U, m, V, n, s));                                // Z = A^T U
-    STAGE(RR_STAGE_HESSENBERG, basis_step(w.c, true, RR_F64, RR_F64, n, b, V, n, V, n, s));        // V = basis(Z)
-  }
-  STAGE(RR_STAGE_F64_PRODUCT, apply_f64(op, b, V, n, w.Rv, m, s));                                 // A V
-  STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, RR_F64, U, m, RR_F64, U, m, w.Gu, b, s));
-  STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, RR_F64, V, n, RR_F64, V, n, w.Gv, b, s));
-  STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, RR_F64, U, m, RR_F64, w.Rv, m, w.Bm, b, s));
-  STAGE(RR_STAGE_PENCIL, pencil_svd(w.c, b, b, w.Bm, w.Gu, w.Gv, w.sig2, w.Ys, w.Zs, s));
-  STAGE(RR_STAGE_LIFT, lift2(op, s, m, b, RR_F64, U, m, b, 0, nullptr, 0, 0, w.Ys, b, w.Ut2, m));
-  STAGE(RR_STAGE_LIFT, lift2(op, s, n, b, RR_F64, V, n, b, 0, nullptr, 0, 0, w.Zs, b, w.Vt2, n));
+// The FP64 polish of the refinement phase: one correction sweep carried in
+// FP64-accurate arithmetic (FP64 blocks, FP64-accurate products, Algorithm 8
+// in FP64 arithmetic) from the residual blocks of the current triplets:
+//   F = A^T R_v + R_u Sigma    (= A^T A V~ - V~ Sigma^2),
+//   E = A F + R_v Sigma^2      (= A A^T A V~ - U~ Sigma^3),
+// each scaled to unit column inf-norm and projected against the orthonormal
+// V~ / U~ (F <- F - V~ (V~^T F), FP64-accurate: exactly, R_v and R_u are
+// orthogonal to U~ and V~, but their rounding noise is not, and relative to a
+// residual of 1e-11 it would leave S_u = [U~, E] with a Gram condition of
+// 1e11 and more), then Algorithm 8, Algorithm 5 over S_u = [U~, E],
+// S_v = [V~, F] and the lift into (Ut2, Vt2, sig2).  The low-precision
+// corrections stop improving at a level set by their precision and the
+// ratio of the largest to the smallest wanted singular value (near 2e-10 for
+// sigma_j = j^-1.5 with 16 wanted); this sweep contracts to the FP64
+// rounding level (about 1e-14 there, against 1e-11 to 1e-10 for the paper's
+// method run in FP64).  Needs P = A V~, Q = A^T U~, R_v, R_u from the
+// residual check before it; overwrites R_v, R_u, P, Q and the pencil blocks.
+static rr_status svd_polish_f64(const Op& op, SvdBufs& w, int64_t b, cudaStream_t s, Prof& prof) {
+  const int64_t m = op.m, n = op.n, b2 = 2 * b;
+  double* F0 = w.Vt2;  // n x b
+  double* E0 = w.Ut2;  // m x b
+  STAGE(RR_STAGE_F64_PRODUCT, apply_f64_T(op, b, w.Rv, m, F0, n, s));         // A^T R_v
+  STAGE(RR_STAGE_OTHER, add_cols_scaled(s, n, b, w.Ru, n, w.sig, 1, F0, n));   // + R_u Sigma
+  STAGE(RR_STAGE_F64_PRODUCT, apply_f64(op, b, F0, n, E0, m, s));               // A F
+  STAGE(RR_STAGE_OTHER, add_cols_scaled(s, m, b, w.Rv, m, w.sig, 2, E0, m));   // + R_v Sigma^2
+  // unit inf-norm columns (R_v and R_u are free now), then the projections:
+  // [T, X] [I; -X^T T] = T - X (X^T T) by the FP64-accurate lift
+  double* Fs = w.Ru;
+  double* Es = w.Rv;
+  STAGE(RR_STAGE_OTHER, scale_cast(s, RR_F64, n, b, F0, n, w.mu, RR_F64, Fs, n, nullptr, nullptr));
+  STAGE(RR_STAGE_OTHER, scale_cast(s, RR_F64, m, b, E0, m, w.mu, RR_F64, Es, m, nullptr, nullptr));
+  STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, RR_F64, w.Vt, n, RR_F64, Fs, n, w.Ys, b, s));
+  STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, RR_F64, w.Ut, m, RR_F64, Es, m, w.Zs, b, s));
+  STAGE(RR_STAGE_OTHER, eye_neg(s, b, w.Ys, b, w.Gv, b2));
+  STAGE(RR_STAGE_OTHER, eye_neg(s, b, w.Zs, b, w.Gu, b2));
+  double* F = w.Vt2;
+  double* E = w.Ut2;
+  STAGE(RR_STAGE_LIFT, lift2(op, s, n, b, RR_F64, Fs, n, b, RR_F64, w.Vt, n, b, w.Gv, b2, F, n));
+  STAGE(RR_STAGE_LIFT, lift2(op, s, m, b, RR_F64, Es, m, b, RR_F64, w.Ut, m, b, w.Gu, b2, E, m));
+  STAGE(RR_STAGE_HESSENBERG, basis_step(w.c, true, RR_F64, RR_F64, m, b, E, m, E, m, s));
+  STAGE(RR_STAGE_HESSENBERG, basis_step(w.c, true, RR_F64, RR_F64, n, b, F, n, F, n, s));
+  double* AF = w.Rv;
+  STAGE(RR_STAGE_F64_PRODUCT, apply_f64(op, b, F, n, AF, m, s));                // A F of the basis
+  // projected blocks over S_u = [U~, E], S_v = [V~, F]  (ld 2b)
+  double* B = w.Bm;
+  STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, RR_F64, w.Ut, m, RR_F64, w.P, m, B, b2, s));             // U~^T A V~
+  STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, RR_F64, w.Qm, n, RR_F64, F, n, B + b * b2, b2, s));      // U~^T A F
+  STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, RR_F64, E, m, RR_F64, w.P, m, B + b, b2, s));            // E^T A V~
+  STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, RR_F64, E, m, RR_F64, AF, m, B + b + b * b2, b2, s));    // E^T A F
+  STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, RR_F64, w.Ut, m, RR_F64, w.Ut, m, w.Gu, b2, s));
+  STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, RR_F64, w.Ut, m, RR_F64, E, m, w.Gu + b * b2, b2, s));
+  STAGE(RR_STAGE_OTHER, transpose(s, b, b, w.Gu + b * b2, b2, w.Gu + b, b2));
+  STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, RR_F64, E, m, RR_F64, E, m, w.Gu + b + b * b2, b2, s));
+  STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, RR_F64, w.Vt, n, RR_F64, w.Vt, n, w.Gv, b2, s));
+  STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, RR_F64, w.Vt, n, RR_F64, F, n, w.Gv + b * b2, b2, s));
+  STAGE(RR_STAGE_OTHER, transpose(s, b, b, w.Gv + b * b2, b2, w.Gv + b, b2));
+  STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, RR_F64, F, n, RR_F64, F, n, w.Gv + b + b * b2, b2, s));
+  STAGE(RR_STAGE_PENCIL, pencil_svd(w.c, b2, b2, B, w.Gu, w.Gv, w.sig2, w.Ys, w.Zs, s));
+  // lift the leading b triplets (into P and Q, which the blocks above no
+  // longer need), then into the sweep's outputs
+  STAGE(RR_STAGE_LIFT, lift2(op, s, m, b, RR_F64, w.Ut, m, b, RR_F64, E, m, b, w.Ys, b2, w.P, m));
+  STAGE(RR_STAGE_LIFT, lift2(op, s, n, b, RR_F64, w.Vt, n, b, RR_F64, F, n, b, w.Zs, b2, w.Qm, n));
+  RR_CUDA(cudaMemcpyAsync(w.Ut2, w.P, (size_t)m * b * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  RR_CUDA(cudaMemcpyAsync(w.Vt2, w.Qm, (size_t)n * b * sizeof(double), cudaMemcpyDeviceToDevice, s));
   return RR_OK;
+}
+
+// Device-side loop of the batched solver.  At this point of the capture on
+// `outer` a WHILE node is added whose body, captured on `body_s` (a stream
+// that is not capturing), is `body(body_s)` followed by the loop-control
+// kernel: sweeps repeat on the GPU while the problem is not frozen and its
+// sweep count is below max_sweeps (and below stop_at when stop_at >= 0) and,
+// with stall != 0, while the largest of the k residuals res keeps falling
+// below 0.3 times the previous sweep's.  ctl = [frozen, sweeps, polish
+// sweeps, -, previous largest residual (double)]; before the node, inc_first
+// sweeps are added to the count and the condition is set for the first
+// iteration; each iteration adds one sweep (and one polish sweep when
+// polish != 0).
+template <class F>
+static rr_status device_loop(cudaStream_t outer, cudaStream_t body_s, int* ctl, int max_sweeps, int stop_at,
+                             int inc_first, int polish, const double* res, int k, int stall, F&& body) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* ed = nullptr;
+  size_t nd = 0;
+  RR_CUDA(cudaStreamGetCaptureInfo(outer, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+  if (cs != cudaStreamCaptureStatusActive || !g) return RR_ERR_ARG;
+  cudaGraphConditionalHandle h;
+  RR_CUDA(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+  RR_TRY(loop_ctl(outer, h, ctl, inc_first, 0, max_sweeps, stop_at, res, k, 0));
+  RR_CUDA(cudaStreamGetCaptureInfo(outer, &cs, nullptr, &g, &deps, &ed, &nd));
+  // (a union with members that have no default constructor: zeroed storage)
+  alignas(cudaGraphNodeParams) unsigned char npbuf[sizeof(cudaGraphNodeParams)];
+  memset(npbuf, 0, sizeof(npbuf));
+  cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(npbuf);
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  RR_CUDA(cudaGraphAddNode(&node, g, deps, ed, nd, &np));
+  RR_CUDA(cudaStreamUpdateCaptureDependencies(outer, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  RR_CUDA(cudaStreamBeginCaptureToGraph(body_s, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeThreadLocal));
+  rr_status st = body(body_s);
+  if (st == RR_OK) st = loop_ctl(body_s, h, ctl, 1, polish, max_sweeps, stop_at, res, k, stall);
+  cudaGraph_t bg = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(body_s, &bg);  // the body graph stays owned by the node
+  if (st == RR_OK && e != cudaSuccess) {
+    set_last_error("device_loop end capture", e);
+    st = RR_ERR_CUDA;
+  }
+  return st;
 }
 
 // The padded operator of a problem (svd_pad_quantum) and, when padding, its
@@ -628,7 +716,8 @@ static const rr_operator* svd_operator(const rr_operator* A_in, const rr_params*
 
 static rr_status svd_run(const rr_operator* Aop_in, const rr_params* p, double* sigma_out,
                          double* U_out, double* V_out, void* ws, size_t ws_bytes, rr_info* info,
-                         cudaStream_t s, bool batch_mode, int hess_grid, uint64_t seed) {
+                         cudaStream_t s, bool batch_mode, int hess_grid, uint64_t seed,
+                         cudaStream_t body_s) {
   Arena ar(ws, ws_bytes);
   const int64_t m0 = Aop_in->m, n0 = Aop_in->n;
   const int padq = svd_pad_quantum(Aop_in, p);
@@ -658,7 +747,7 @@ static rr_status svd_run(const rr_operator* Aop_in, const rr_params* p, double* 
   w.c.hess_grid = hess_grid;
   w.c.hess_tol = p->hess_tol;
   RR_CUDA(cudaMemsetAsync(w.c.hess_ws, 0, 512, s));
-  RR_CUDA(cudaMemsetAsync(w.frozen, 0, sizeof(int), s));
+  RR_CUDA(cudaMemsetAsync(w.frozen, 0, 8 * sizeof(int), s));
   if (!batch_mode) STAGE(RR_STAGE_OTHER, check_operator_finite(Aop_in, w.c, s));
   if (padq) {
     // the zero-padded copy of A (counted with the one-time operator casts)
@@ -693,8 +782,11 @@ static rr_status svd_run(const rr_operator* Aop_in, const rr_params* p, double* 
   bool converged = false, nan_seen = false;
 
   // ---------------- phase 1: the paper's method ----------------
-  for (int ps = 0; ps < ph1 && sweep < p->max_sweeps; ++ps) {
-    if (ps > 0) STAGE(RR_STAGE_OTHER, rr_colscale_cast(n, b, w.Vt, n, dt1, w.Vlo, n, w.c.scale, s));
+  // One sweep: q times { U = Alg. 8(A V), V = Alg. 8(A^T U) }, then
+  // Algorithm 5 over (U, V) and the lift into (Ut, Vt, sig); `recast` starts
+  // from the previous sweep's Ritz vectors.
+  auto ph1_sweep = [&](cudaStream_t s, bool recast) -> rr_status {
+    if (recast) STAGE(RR_STAGE_OTHER, rr_colscale_cast(n, b, w.Vt, n, dt1, w.Vlo, n, w.c.scale, s));
     for (int it = 0; it < q; ++it) {
       STAGE(RR_STAGE_LOWP_PRODUCT, apply_ph1(op, b, w.Vlo, n, (float*)w.W, m, s));                      // W = A V
       STAGE(RR_STAGE_HESSENBERG, basis_step(w.c, hess, op.wt, dt1, m, b, w.W, m, w.Ulo, m, s));         // U = basis(W)
@@ -710,43 +802,159 @@ static rr_status svd_run(const rr_operator* Aop_in, const rr_params* p, double* 
     STAGE(RR_STAGE_LIFT, lift2(op, s, m, b, dt1, w.Ulo, m, b, 0, nullptr, 0, 0, w.Ys, b, w.Ut, m));
     STAGE(RR_STAGE_LIFT, lift2(op, s, n, b, dt1, w.Vlo, n, b, 0, nullptr, 0, 0, w.Zs, b, w.Vt, n));
     RR_CUDA(cudaMemcpyAsync(w.sig, w.sig2, b * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return RR_OK;
+  };
+  // batched problems: sweeps after the first run in WHILE nodes of the graph
+  // (device-side loop control), each problem stopping at tol
+  const bool dloop = batch_mode && body_s != nullptr;
+
+  if (dloop && !refine) {
+    // the plain method in a batch: the residual check after every sweep
+    RR_TRY(ph1_sweep(s, false));
     ++sweep;
-    if (!refine && !batch_mode) {
-      // plain method: FP64 residual check of the wanted triplets every sweep
-      STAGE(RR_STAGE_F64_PRODUCT, svd_residual(op, w, k, w.Rv ? w.Rv : w.P, w.Ru ? w.Ru : w.Qm, s));
-      RR_CUDA(cudaMemcpyAsync(hres.data(), w.res, k * sizeof(double), cudaMemcpyDeviceToHost, s));
-      RR_TRY(queue_cond(w.c, s, hcond));
-      RR_CUDA(cudaStreamSynchronize(s));
-      RR_TRY(read_err(w.c, s));
-      double mx;
-      inf.n_converged = count_converged(hres.data(), (int)k, p->tol, &mx);
-      inf.max_res = mx;
-      if (sweep <= 64) inf.res_history[sweep - 1] = mx;
-      note_cond(inf, sweep, hcond);
-      if (all_nan(hres.data(), (int)k)) {
-        nan_seen = true;
-        break;
-      }
-      if (inf.n_converged == k) {
-        converged = true;
-        break;
+    STAGE(RR_STAGE_F64_PRODUCT, svd_residual(op, w, k, w.P, w.Qm, s));
+    STAGE(RR_STAGE_OTHER, freeze_update(s, k, w.res, p->tol, w.frozen));
+    RR_TRY(device_loop(s, body_s, w.frozen, p->max_sweeps, -1, sweep, 0, w.res, (int)k, 0,
+                       [&](cudaStream_t bs) -> rr_status {
+      RR_TRY(ph1_sweep(bs, true));
+      RR_TRY(svd_residual(op, w, k, w.P, w.Qm, bs));
+      return freeze_update(bs, k, w.res, p->tol, w.frozen);
+    }));
+  } else {
+    for (int ps = 0; ps < ph1 && sweep < p->max_sweeps; ++ps) {
+      RR_TRY(ph1_sweep(s, ps > 0));
+      ++sweep;
+      if (!refine && !batch_mode) {
+        // plain method: FP64 residual check of the wanted triplets every sweep
+        STAGE(RR_STAGE_F64_PRODUCT, svd_residual(op, w, k, w.Rv ? w.Rv : w.P, w.Ru ? w.Ru : w.Qm, s));
+        RR_CUDA(cudaMemcpyAsync(hres.data(), w.res, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+        RR_TRY(queue_cond(w.c, s, hcond));
+        RR_CUDA(cudaStreamSynchronize(s));
+        RR_TRY(read_err(w.c, s));
+        double mx;
+        inf.n_converged = count_converged(hres.data(), (int)k, p->tol, &mx);
+        inf.max_res = mx;
+        if (sweep <= 64) inf.res_history[sweep - 1] = mx;
+        note_cond(inf, sweep, hcond);
+        if (all_nan(hres.data(), (int)k)) {
+          nan_seen = true;
+          break;
+        }
+        if (inf.n_converged == k) {
+          converged = true;
+          break;
+        }
       }
     }
   }
 
   // ---------------- phase 2: refinement ----------------
-  if (refine && !nan_seen) {
+  // residual of all b Ritz triplets, FP64-accurate (P, Q, R_v, R_u, res)
+  auto residual_all = [&](cudaStream_t s) -> rr_status {
+    STAGE(RR_STAGE_F64_PRODUCT, apply_f64(op, b, w.Vt, n, w.P, m, s));      // P = A V~
+    STAGE(RR_STAGE_F64_PRODUCT, apply_f64_T(op, b, w.Ut, m, w.Qm, n, s));   // Q = A^T U~
+    STAGE(RR_STAGE_OTHER, residual_block(s, m, b, w.P, m, w.Ut, m, w.sig, w.Rv, m, w.ss, 0));
+    STAGE(RR_STAGE_OTHER, residual_block(s, n, b, w.Qm, n, w.Vt, n, w.sig, w.Ru, n, w.ss, 1));
+    STAGE(RR_STAGE_OTHER, res_finish(s, b, w.ss, w.sig, w.res));
+    if (batch_mode) STAGE(RR_STAGE_OTHER, freeze_update(s, k, w.res, p->tol, w.frozen));
+    return RR_OK;
+  };
+  // One refinement sweep from the residual blocks into (Ut2, Vt2, sig2).
+  auto corr_sweep = [&](cudaStream_t s) -> rr_status {
     const int64_t b2 = 2 * b;
+    // correction recurrence (low precision):
+    //   E_1 = R_v;  F_j = A^T E_j + R_u S^(2j-1);  E_{j+1} = A F_j + R_v S^(2j)
+    // each block kept at unit column inf-norm, the injection coefficient
+    // tracked per column (coef <- coef * sigma / mu after each scaling).
+    STAGE(RR_STAGE_OTHER, fill(s, b, 1.0, w.coef));
+    // FP32 copies of the singular vectors for the projections of this sweep
+    STAGE(RR_STAGE_OTHER, cast_f32(s, n, b, w.Vt, n, w.Vt32, n));
+    STAGE(RR_STAGE_OTHER, cast_f32(s, m, b, w.Ut, m, w.Ut32, m));
+    // split mode: blocks and operator carried as BF16 pairs (hi + lo), the
+    // final correction blocks kept in FP32 for the projection and the lift
+    const bool sp = op.split;
+    const int32_t et = sp ? RR_F32 : dt;
+    void* Eg = sp ? w.E32 : w.Elo;
+    void* Fg = sp ? w.F32 : w.Flo;
+    if (sp) STAGE(RR_STAGE_OTHER, scale_split(s, RR_F64, m, b, w.Rv, m, w.mu, w.Elo, w.Elo2, m, w.coef, w.sig));
+    else STAGE(RR_STAGE_OTHER, scale_cast(s, RR_F64, m, b, w.Rv, m, w.mu, dt, w.Elo, m, w.coef, w.sig));
+    for (int j = 0; j < qr; ++j) {
+      if (sp) STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp_T_split(op, b, w.Elo, w.Elo2, m, w.W, n, w.Ru, n, w.coef, s));
+      else STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp_T(op, b, w.Elo, m, w.W, n, w.Ru, n, w.coef, s));
+      STAGE(RR_STAGE_GRAM, project_out(w.c, s, n, b, w.Vt32, n, (float*)w.W, n, w.Ys));
+      if (sp) STAGE(RR_STAGE_OTHER, scale_split(s, op.wt, n, b, w.W, n, w.mu, w.Flo, w.Flo2, n, w.coef, w.sig));
+      else STAGE(RR_STAGE_OTHER, scale_cast(s, op.wt, n, b, w.W, n, w.mu, dt, w.Flo, n, w.coef, w.sig));
+      if (sp) STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp_split(op, b, w.Flo, w.Flo2, n, w.AF, m, w.Rv, m, w.coef, s));
+      else STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp(op, b, w.Flo, n, w.AF, m, w.Rv, m, w.coef, s));
+      STAGE(RR_STAGE_GRAM, project_out(w.c, s, m, b, w.Ut32, m, (float*)w.AF, m, w.Ys));
+      if (j + 1 < qr) {
+        if (sp) STAGE(RR_STAGE_OTHER, scale_split(s, op.wt, m, b, w.AF, m, w.mu, w.Elo, w.Elo2, m, w.coef, w.sig));
+        else STAGE(RR_STAGE_OTHER, scale_cast(s, op.wt, m, b, w.AF, m, w.mu, dt, w.Elo, m, w.coef, w.sig));
+      }
+    }
+    // conditioning of the correction blocks (Algorithm 8), then A F for the
+    // low-precision block of the projected matrix
+    STAGE(RR_STAGE_HESSENBERG, basis_step(w.c, hess, op.wt, et, m, b, w.AF, m, Eg, m, s));
+    STAGE(RR_STAGE_HESSENBERG, basis_step(w.c, hess, op.wt, et, n, b, w.W, n, Fg, n, s));
+    if (sp) {
+      STAGE(RR_STAGE_OTHER, scale_split(s, RR_F32, n, b, w.F32, n, nullptr, w.Flo, w.Flo2, n, nullptr, nullptr));
+      STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp_split(op, b, w.Flo, w.Flo2, n, w.AF, m, nullptr, 0, nullptr, s));
+    } else {
+      STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp(op, b, w.Flo, n, w.AF, m, nullptr, 0, nullptr, s));
+    }
+    // projected blocks over S_u = [U~, E], S_v = [V~, F]  (ld 2b)
+    double* B = w.Bm;
+    STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, RR_F64, w.Ut, m, RR_F64, w.P, m, B, b2, s));                   // U~^T A V~
+    STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, RR_F64, w.Qm, n, et, Fg, n, B + b * b2, b2, s));             // U~^T A F
+    STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, et, Eg, m, RR_F64, w.P, m, B + b, b2, s));                   // E^T A V~
+    STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, et, Eg, m, op.wt, w.AF, m, B + b + b * b2, b2, s));          // E^T A F
+    STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, RR_F64, w.Ut, m, RR_F64, w.Ut, m, w.Gu, b2, s));
+    STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, RR_F64, w.Ut, m, et, Eg, m, w.Gu + b * b2, b2, s));
+    STAGE(RR_STAGE_OTHER, transpose(s, b, b, w.Gu + b * b2, b2, w.Gu + b, b2));
+    STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, et, Eg, m, et, Eg, m, w.Gu + b + b * b2, b2, s));
+    STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, RR_F64, w.Vt, n, RR_F64, w.Vt, n, w.Gv, b2, s));
+    STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, RR_F64, w.Vt, n, et, Fg, n, w.Gv + b * b2, b2, s));
+    STAGE(RR_STAGE_OTHER, transpose(s, b, b, w.Gv + b * b2, b2, w.Gv + b, b2));
+    STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, et, Fg, n, et, Fg, n, w.Gv + b + b * b2, b2, s));
+    STAGE(RR_STAGE_PENCIL, pencil_svd(w.c, b2, b2, B, w.Gu, w.Gv, w.sig2, w.Ys, w.Zs, s));
+    // lift the leading b triplets
+    STAGE(RR_STAGE_LIFT, lift2(op, s, m, b, RR_F64, w.Ut, m, b, et, Eg, m, b, w.Ys, b2, w.Ut2, m));
+    STAGE(RR_STAGE_LIFT, lift2(op, s, n, b, RR_F64, w.Vt, n, b, et, Fg, n, b, w.Zs, b2, w.Vt2, n));
+    return RR_OK;
+  };
+  // the device loops' fixed buffers: the sweep's output becomes the current
+  // Ritz triplets (the host loop swaps the pointers instead)
+  auto adopt = [&](cudaStream_t s) -> rr_status {
+    RR_CUDA(cudaMemcpyAsync(w.Ut, w.Ut2, (size_t)m * b * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    RR_CUDA(cudaMemcpyAsync(w.Vt, w.Vt2, (size_t)n * b * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    RR_CUDA(cudaMemcpyAsync(w.sig, w.sig2, (size_t)b * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return RR_OK;
+  };
+
+  if (refine && !nan_seen && dloop) {
+    // correction sweeps while the problem is not frozen and they contract
+    // the residual (the single solve's stall rule), at most up to the sweep
+    // where the fixed schedule polishes (its last two sweeps), then FP64
+    // polish sweeps while the problem is still not frozen
+    RR_TRY(residual_all(s));
+    const int polish_from = std::max(p->max_sweeps - 2, ph1 + 1);
+    RR_TRY(device_loop(s, body_s, w.frozen, p->max_sweeps, polish_from, sweep, 0, w.res, (int)k, 1,
+                       [&](cudaStream_t bs) -> rr_status {
+      RR_TRY(corr_sweep(bs));
+      RR_TRY(adopt(bs));
+      return residual_all(bs);
+    }));
+    RR_TRY(device_loop(s, body_s, w.frozen, p->max_sweeps, -1, 0, 1, w.res, (int)k, 0,
+                       [&](cudaStream_t bs) -> rr_status {
+      RR_TRY(svd_polish_f64(op, w, b, bs, prof));
+      RR_TRY(adopt(bs));
+      return residual_all(bs);
+    }));
+  } else if (refine && !nan_seen) {
     double prev_mx = INFINITY;
     bool polish = false;
     for (;;) {
-      // residual of all b Ritz triplets, FP64-accurate
-      STAGE(RR_STAGE_F64_PRODUCT, apply_f64(op, b, w.Vt, n, w.P, m, s));      // P = A V~
-      STAGE(RR_STAGE_F64_PRODUCT, apply_f64_T(op, b, w.Ut, m, w.Qm, n, s));   // Q = A^T U~
-      STAGE(RR_STAGE_OTHER, residual_block(s, m, b, w.P, m, w.Ut, m, w.sig, w.Rv, m, w.ss, 0));
-      STAGE(RR_STAGE_OTHER, residual_block(s, n, b, w.Qm, n, w.Vt, n, w.sig, w.Ru, n, w.ss, 1));
-      STAGE(RR_STAGE_OTHER, res_finish(s, b, w.ss, w.sig, w.res));
-      if (batch_mode) STAGE(RR_STAGE_OTHER, freeze_update(s, k, w.res, p->tol, w.frozen));
+      RR_TRY(residual_all(s));
       if (!batch_mode) {
         RR_CUDA(cudaMemcpyAsync(hres.data(), w.res, k * sizeof(double), cudaMemcpyDeviceToHost, s));
         RR_TRY(queue_cond(w.c, s, hcond));
@@ -773,77 +981,13 @@ static rr_status svd_run(const rr_operator* Aop_in, const rr_params* p, double* 
       // batched problems (no host check) polish on their last two sweeps
       if (batch_mode) polish = sweep >= p->max_sweeps - 2 && sweep >= ph1 + 1;
       if (polish) {
-        RR_TRY(svd_polish_f64(op, w, b, q, s, prof));
-        if (batch_mode)
-          STAGE(RR_STAGE_OTHER, keep_frozen(s, w.frozen, m, n, b, w.Ut, w.Ut2, w.Vt, w.Vt2, w.sig, w.sig2));
-        std::swap(w.Ut, w.Ut2);
-        std::swap(w.Vt, w.Vt2);
-        RR_CUDA(cudaMemcpyAsync(w.sig, w.sig2, b * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        ++sweep;
-        ++inf.refine_sweeps;
+        RR_TRY(svd_polish_f64(op, w, b, s, prof));
         ++inf.polish_sweeps;
         polish = false;
         prev_mx = INFINITY;
-        continue;
-      }
-      // correction recurrence (low precision):
-      //   E_1 = R_v;  F_j = A^T E_j + R_u S^(2j-1);  E_{j+1} = A F_j + R_v S^(2j)
-      // each block kept at unit column inf-norm, the injection coefficient
-      // tracked per column (coef <- coef * sigma / mu after each scaling).
-      STAGE(RR_STAGE_OTHER, fill(s, b, 1.0, w.coef));
-      // FP32 copies of the singular vectors for the projections of this sweep
-      STAGE(RR_STAGE_OTHER, cast_f32(s, n, b, w.Vt, n, w.Vt32, n));
-      STAGE(RR_STAGE_OTHER, cast_f32(s, m, b, w.Ut, m, w.Ut32, m));
-      // split mode: blocks and operator carried as BF16 pairs (hi + lo), the
-      // final correction blocks kept in FP32 for the projection and the lift
-      const bool sp = op.split;
-      const int32_t et = sp ? RR_F32 : dt;
-      void* Eg = sp ? w.E32 : w.Elo;
-      void* Fg = sp ? w.F32 : w.Flo;
-      if (sp) STAGE(RR_STAGE_OTHER, scale_split(s, RR_F64, m, b, w.Rv, m, w.mu, w.Elo, w.Elo2, m, w.coef, w.sig));
-      else STAGE(RR_STAGE_OTHER, scale_cast(s, RR_F64, m, b, w.Rv, m, w.mu, dt, w.Elo, m, w.coef, w.sig));
-      for (int j = 0; j < qr; ++j) {
-        if (sp) STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp_T_split(op, b, w.Elo, w.Elo2, m, w.W, n, w.Ru, n, w.coef, s));
-        else STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp_T(op, b, w.Elo, m, w.W, n, w.Ru, n, w.coef, s));
-        STAGE(RR_STAGE_GRAM, project_out(w.c, s, n, b, w.Vt32, n, (float*)w.W, n, w.Ys));
-        if (sp) STAGE(RR_STAGE_OTHER, scale_split(s, op.wt, n, b, w.W, n, w.mu, w.Flo, w.Flo2, n, w.coef, w.sig));
-        else STAGE(RR_STAGE_OTHER, scale_cast(s, op.wt, n, b, w.W, n, w.mu, dt, w.Flo, n, w.coef, w.sig));
-        if (sp) STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp_split(op, b, w.Flo, w.Flo2, n, w.AF, m, w.Rv, m, w.coef, s));
-        else STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp(op, b, w.Flo, n, w.AF, m, w.Rv, m, w.coef, s));
-        STAGE(RR_STAGE_GRAM, project_out(w.c, s, m, b, w.Ut32, m, (float*)w.AF, m, w.Ys));
-        if (j + 1 < qr) {
-          if (sp) STAGE(RR_STAGE_OTHER, scale_split(s, op.wt, m, b, w.AF, m, w.mu, w.Elo, w.Elo2, m, w.coef, w.sig));
-          else STAGE(RR_STAGE_OTHER, scale_cast(s, op.wt, m, b, w.AF, m, w.mu, dt, w.Elo, m, w.coef, w.sig));
-        }
-      }
-      // conditioning of the correction blocks (Algorithm 8), then A F for the
-      // low-precision block of the projected matrix
-      STAGE(RR_STAGE_HESSENBERG, basis_step(w.c, hess, op.wt, et, m, b, w.AF, m, Eg, m, s));
-      STAGE(RR_STAGE_HESSENBERG, basis_step(w.c, hess, op.wt, et, n, b, w.W, n, Fg, n, s));
-      if (sp) {
-        STAGE(RR_STAGE_OTHER, scale_split(s, RR_F32, n, b, w.F32, n, nullptr, w.Flo, w.Flo2, n, nullptr, nullptr));
-        STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp_split(op, b, w.Flo, w.Flo2, n, w.AF, m, nullptr, 0, nullptr, s));
       } else {
-        STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp(op, b, w.Flo, n, w.AF, m, nullptr, 0, nullptr, s));
+        RR_TRY(corr_sweep(s));
       }
-      // projected blocks over S_u = [U~, E], S_v = [V~, F]  (ld 2b)
-      double* B = w.Bm;
-      STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, RR_F64, w.Ut, m, RR_F64, w.P, m, B, b2, s));                   // U~^T A V~
-      STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, RR_F64, w.Qm, n, et, Fg, n, B + b * b2, b2, s));             // U~^T A F
-      STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, et, Eg, m, RR_F64, w.P, m, B + b, b2, s));                   // E^T A V~
-      STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, et, Eg, m, op.wt, w.AF, m, B + b + b * b2, b2, s));          // E^T A F
-      STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, RR_F64, w.Ut, m, RR_F64, w.Ut, m, w.Gu, b2, s));
-      STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, RR_F64, w.Ut, m, et, Eg, m, w.Gu + b * b2, b2, s));
-      STAGE(RR_STAGE_OTHER, transpose(s, b, b, w.Gu + b * b2, b2, w.Gu + b, b2));
-      STAGE(RR_STAGE_GRAM, gram(w.c, m, b, b, et, Eg, m, et, Eg, m, w.Gu + b + b * b2, b2, s));
-      STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, RR_F64, w.Vt, n, RR_F64, w.Vt, n, w.Gv, b2, s));
-      STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, RR_F64, w.Vt, n, et, Fg, n, w.Gv + b * b2, b2, s));
-      STAGE(RR_STAGE_OTHER, transpose(s, b, b, w.Gv + b * b2, b2, w.Gv + b, b2));
-      STAGE(RR_STAGE_GRAM, gram(w.c, n, b, b, et, Fg, n, et, Fg, n, w.Gv + b + b * b2, b2, s));
-      STAGE(RR_STAGE_PENCIL, pencil_svd(w.c, b2, b2, B, w.Gu, w.Gv, w.sig2, w.Ys, w.Zs, s));
-      // lift the leading b triplets
-      STAGE(RR_STAGE_LIFT, lift2(op, s, m, b, RR_F64, w.Ut, m, b, et, Eg, m, b, w.Ys, b2, w.Ut2, m));
-      STAGE(RR_STAGE_LIFT, lift2(op, s, n, b, RR_F64, w.Vt, n, b, et, Fg, n, b, w.Zs, b2, w.Vt2, n));
       if (batch_mode)
         STAGE(RR_STAGE_OTHER, keep_frozen(s, w.frozen, m, n, b, w.Ut, w.Ut2, w.Vt, w.Vt2, w.sig, w.sig2));
       std::swap(w.Ut, w.Ut2);
@@ -853,11 +997,10 @@ static rr_status svd_run(const rr_operator* Aop_in, const rr_params* p, double* 
       ++inf.refine_sweeps;
     }
   }
-  if (batch_mode && !refine) {
+  if (batch_mode && !refine && !dloop) {
     // final residual for the caller's convergence count (read after the graph)
     STAGE(RR_STAGE_F64_PRODUCT, svd_residual(op, w, k, w.P, w.Qm, s));
   }
-
   // outputs: sigma, U, V (first k; the rows of A's own size), unit columns,
   // sign fixed on V
   RR_CUDA(cudaMemcpyAsync(sigma_out, w.sig, k * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -1298,7 +1441,7 @@ extern "C" rr_status rr_svd(const rr_operator* A, const rr_params* p, double* si
   RR_TRY(check_params(p, A->n));
   if (!sigma || !U || !V) return RR_ERR_ARG;
   if (!ws || ws_bytes < svd_ws(A, p, false) || ((uintptr_t)ws & 255)) return RR_ERR_WORKSPACE;
-  return svd_run(A, p, sigma, U, V, ws, ws_bytes, info, as_stream(stream), false, 0, 0);
+  return svd_run(A, p, sigma, U, V, ws, ws_bytes, info, as_stream(stream), false, 0, 0, nullptr);
 }
 
 extern "C" size_t rr_batch_workspace_size(int32_t count, const rr_operator* A, const rr_params* p) {
@@ -1312,10 +1455,14 @@ extern "C" size_t rr_batch_workspace_size(int32_t count, const rr_operator* A, c
 }
 
 // All problems are captured into one CUDA graph: NS streams fork from the
-// caller's stream, problems are dealt round-robin to them, every problem runs
-// a fixed number of sweeps (phase 1 + refinement) with no host
-// synchronisation, its Hessenberg steps on one CTA (plain launches), and the
-// branches join back before the single graph launch completes.
+// caller's stream, problems are dealt round-robin to them, each problem runs
+// with no host synchronisation, its Hessenberg steps on one CTA (plain
+// launches), and the branches join back before the single graph launch
+// completes.  A problem's first sweep is captured as plain nodes; its later
+// sweeps run in WHILE nodes whose condition a kernel sets on the GPU after
+// each sweep's residual check, so a problem stops at tol (device-side loop
+// control).  With tuning->fixed_sweeps every sweep is captured instead and
+// every problem runs max_sweeps sweeps, keeping the triplets it froze at.
 extern "C" rr_status rr_batch_svd(int32_t count, const rr_operator* A, const rr_params* p,
                                   uint64_t seed, double* const* sigma, double* const* U,
                                   double* const* V, void* ws, size_t ws_bytes,
@@ -1328,10 +1475,11 @@ extern "C" rr_status rr_batch_svd_tuned(int32_t count, const rr_operator* A, con
                                         size_t ws_bytes, const rr_batch_tuning* tuning, rr_status* per_problem,
                                         rr_info* info, void* stream) {
   if (count <= 0 || !A || !p || !sigma || !U || !V || !ws || p->basis == RR_E4M3) return RR_ERR_ARG;
-  const rr_batch_tuning tune = tuning ? *tuning : rr_batch_tuning{16, 0, 0};
+  const rr_batch_tuning tune = tuning ? *tuning : rr_batch_tuning{16, 0, 0, 0};
   if (tune.branches < 1 || tune.branches > kBatchMaxBranches || tune.max_splits < 0 ||
-      (tune.order != 0 && tune.order != 1))
+      (tune.order != 0 && tune.order != 1) || (tune.fixed_sweeps != 0 && tune.fixed_sweeps != 1))
     return RR_ERR_ARG;
+  const bool dloop = tune.fixed_sweeps == 0;
   for (int i = 0; i < count; ++i) {
     RR_TRY(check_op(&A[i], true));
     RR_TRY(check_params(p, A[i].n));
@@ -1348,7 +1496,7 @@ extern "C" rr_status rr_batch_svd_tuned(int32_t count, const rr_operator* A, con
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return A[a].m * A[a].n > A[b].m * A[b].n; });
   // Capture on a private stream (the legacy default stream cannot be
   // captured); the instantiated graph is launched on the caller's stream.
-  cudaStream_t cap = nullptr;
+  cudaStream_t cap = nullptr, body = nullptr;
   cudaStream_t br[kBatchMaxBranches] = {};
   cudaEvent_t fork = nullptr, join[kBatchMaxBranches] = {};
   rr_params pp = *p;
@@ -1376,12 +1524,21 @@ extern "C" rr_status rr_batch_svd_tuned(int32_t count, const rr_operator* A, con
     if (st == RR_OK && pencil_side_prepare(br[i]) != RR_OK) st = RR_ERR_CUDA;  // before the capture
   }
   cu(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming), "rr_batch_svd event");
+  // the stream the loop bodies are captured on (one body at a time)
+  if (dloop && st == RR_OK) {
+    cu(cudaStreamCreateWithFlags(&body, cudaStreamNonBlocking), "rr_batch_svd stream");
+    if (st == RR_OK && pencil_side_prepare(body) != RR_OK) st = RR_ERR_CUDA;
+  }
   // the graph must see the caller's prior work on `s`: order cap after s
   cudaEvent_t pre = nullptr;
   cu(cudaEventCreateWithFlags(&pre, cudaEventDisableTiming), "rr_batch_svd event");
-  // one graph per chunk of problems, at most kBatchSweepBudget problem-sweeps
-  // each (graphs of a few hundred thousand nodes), launched in order on `s`
-  const int per_graph = std::max(1, kBatchSweepBudget / std::max(1, (int)p->max_sweeps));
+  // one graph per chunk of problems, at most kBatchSweepBudget captured
+  // problem-sweeps each (graphs of a few hundred thousand nodes), launched in
+  // order on `s`; with device loops a problem captures its phase-1 sweeps,
+  // one correction sweep, one polish sweep and three residual checks
+  const int ph1c = p->refine != 0 && p->basis != RR_F64 ? std::max(1, (int)p->phase1_sweeps) : 1;
+  const int captured = dloop ? std::min((int)p->max_sweeps, ph1c + 3) : (int)p->max_sweeps;
+  const int per_graph = std::max(1, kBatchSweepBudget / std::max(1, captured));
   for (int r0 = 0; r0 < count && st == RR_OK; r0 += per_graph) {
     const int r1 = std::min(count, r0 + per_graph);
     cu(cudaEventRecord(pre, s), "rr_batch_svd record");
@@ -1399,7 +1556,7 @@ extern "C" rr_status rr_batch_svd_tuned(int32_t count, const rr_operator* A, con
         const int i = order[r];
         size_t need = align_up(svd_ws(&A[i], p, true), 4096);
         st = svd_run(&A[i], &pp, sigma[i], U[i], V[i], (char*)ws + offs[i], need, &infos[i], br[(r - r0) % NS],
-                     true, 1, seed + (uint64_t)i);
+                     true, 1, seed + (uint64_t)i, dloop ? body : nullptr);
       }
       for (int i = 0; i < NS; ++i) {
         cudaEventRecord(join[i], br[i]);
@@ -1419,6 +1576,10 @@ extern "C" rr_status rr_batch_svd_tuned(int32_t count, const rr_operator* A, con
   for (cudaGraphExec_t e : execs) cudaGraphExecDestroy(e);
   if (pre) cudaEventDestroy(pre);
   if (cap) cudaStreamDestroy(cap);
+  if (body) {
+    pencil_side_release(body);
+    cudaStreamDestroy(body);
+  }
   for (int i = 0; i < NS; ++i) {
     if (br[i]) pencil_side_release(br[i]);
     if (br[i]) cudaStreamDestroy(br[i]);
@@ -1440,6 +1601,14 @@ extern "C" rr_status rr_batch_svd_tuned(int32_t count, const rr_operator* A, con
     RR_CUDA(cudaMemcpy(hres.data(), w.res, p->k * sizeof(double), cudaMemcpyDeviceToHost));
     int e = 0;
     RR_CUDA(cudaMemcpy(&e, w.c.hess_ws, sizeof(int), cudaMemcpyDeviceToHost));
+    if (dloop) {
+      // sweeps the problem ran (device-side loop control)
+      int ctl[3] = {0, 0, 0};
+      RR_CUDA(cudaMemcpy(ctl, w.frozen, sizeof(ctl), cudaMemcpyDeviceToHost));
+      infos[i].sweeps = ctl[1];
+      infos[i].polish_sweeps = ctl[2];
+      infos[i].refine_sweeps = p->refine != 0 && p->basis != RR_F64 ? std::max(0, ctl[1] - ph1c) : 0;
+    }
     double mx;
     infos[i].n_converged = count_converged(hres.data(), p->k, p->tol, &mx);
     infos[i].max_res = mx;

@@ -25,7 +25,12 @@ rr_status normalize_sign(cudaStream_t s, int64_t n, int64_t k, double* X, int64_
                          double* U, int64_t ldu);
 rr_status vec_mul(cudaStream_t s, int64_t n, const double* a, const double* b, double* d);
 rr_status fill(cudaStream_t s, int64_t n, double v, double* d);
+rr_status eye_neg(cudaStream_t s, int64_t b, const double* K, int64_t ldk, double* Y, int64_t ldy);
+rr_status add_cols_scaled(cudaStream_t s, int64_t n, int64_t b, const double* X, int64_t ldx, const double* c, int pw,
+                          double* Y, int64_t ldy);
 rr_status freeze_update(cudaStream_t s, int64_t k, const double* res, double tol, int* frozen);
+rr_status loop_ctl(cudaStream_t s, cudaGraphConditionalHandle h, int* ctl, int inc, int inc_polish, int max_sweeps,
+                   int stop_at, const double* res, int k, int stall);
 rr_status keep_frozen(cudaStream_t s, const int* frozen, int64_t m, int64_t n, int64_t b, const double* U, double* U2,
                       const double* V, double* V2, const double* sig, double* sig2);
 rr_status operator_nonfinite(cudaStream_t s, int kind, int64_t m, int64_t n, const void* values, int64_t lda,

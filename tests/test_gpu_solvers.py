@@ -227,6 +227,40 @@ def test_batch_problems_keep_converged_triplets(rr):
         assert O.residual_svd(Amul, Atmul, host(U), host(V), host(s)).max() <= 1.5e-10
 
 
+@pytest.mark.parametrize("basis,refine", [("bf16", True), ("f64", False)])
+def test_batch_device_loop_stops_at_tol(rr, basis, refine):
+    """Device-side loop control of the batched solver: a problem's sweeps after
+    the first run inside WHILE graph nodes whose condition a kernel sets after
+    each residual check, so each problem stops on the GPU once its k wanted
+    residuals reach tol.  Easy problems (wide gaps) stop after a few of the 36
+    allowed sweeps and a harder one (sigma_j = j^-1.5) in the same batch runs
+    longer; the triplets match the closed form, as do those of the schedule
+    that runs every problem for all 36 sweeps (fixed_sweeps)."""
+    shapes = [(256, 64), (264, 66), (320, 80), (1024, 256)]
+    ops, sigs, keep = [], [], []
+    for i, (m, n) in enumerate(shapes):
+        sg = np.exp(-np.arange(1, n + 1) / 4.0) if i < 3 else wl.config4_sigma(n)
+        A = wl.dense_svd(m, n, sg, 4300 + i)
+        keep.append((A, dev(A)))
+        ops.append(rr.api.dense_operator(keep[-1][1]))
+        sigs.append(sg)
+    p = rr.api.make_params(4, 8, 2, 36, 1e-10, basis=basis, refine=refine, phase1_sweeps=1)
+    outs, st, infos = rr.rr_batch_svd(ops, p, 9)
+    fixed = {"branches": 16, "max_splits": 0, "order": 0, "fixed_sweeps": 1}
+    outs_f, st_f, infos_f = rr.rr_batch_svd(ops, p, 9, tuning=fixed)
+    assert all(x == 0 for x in st) and all(x == 0 for x in st_f), (st, st_f, infos)
+    sweeps = [inf["sweeps"] for inf in infos]
+    assert all(inf["sweeps"] == 36 for inf in infos_f)
+    assert max(sweeps[:3]) <= 12 and min(sweeps) >= 1, sweeps
+    assert sweeps[3] >= min(sweeps[:3]), sweeps
+    for o in (outs, outs_f):
+        for (s, U, V), sg, (A, _) in zip(o, sigs, keep):
+            s = host(s)
+            assert np.max(np.abs(s - sg[:4]) / sg[:4]) <= 1e-10
+            Amul, Atmul = O.dense_apply(A)
+            assert O.residual_svd(Amul, Atmul, host(U), host(V), s).max() <= 1.5e-10
+
+
 def test_svd_seeded_start_block_and_info(rr):
     """v0 = NULL draws the start block on the device from params.seed (Alg. 1's
     U(0,1) block) and the solve converges from it.  Runs are not reproducible
@@ -337,27 +371,36 @@ def test_batch_svd_ragged_largest_class(rr):
 
 
 def test_svd_fp64_polish_after_stall(rr):
-    """Problems of the batched workload's largest class whose low-precision
-    corrections stall above 1e-10 (near 2e-10 on sigma_j = j^-1.5 with 16 of
-    32 wanted) finish with the FP64 polish sweep: all 16 triplets to 1e-10 in
-    every problem, the polish taken in at least one of them."""
+    """Asked for a tolerance below what the low-precision corrections reach
+    (1e-14; on sigma_j = j^-1.5 with 16 of 32 wanted they stop near 1e-13),
+    the solver switches to FP64 polish sweeps once the residual stops
+    contracting (largest wanted residual above 0.3 times the previous one).
+    The polish sweeps (the correction sweep in FP64-accurate arithmetic) keep
+    every triplet at the FP64 level: residual below 1e-12 by the oracle,
+    sigma to 1e-13.  Single solves (host stall rule) and the batched solver
+    (device-side stall rule inside its WHILE graph nodes) alike."""
     sh = wl.config4_shapes(512)
-    probs = [(i, m, n) for i, (m, n) in enumerate(sh) if m >= 2048][:8]
-    polished = 0
-    for i, m, n in probs:
-        sg = wl.config4_sigma(n)
-        A = wl.dense_svd(m, n, sg, 4000 + i)
-        p = rr.api.make_params(16, 32, 4, 40, 1e-10, basis="bf16", v0=dev(wl.uniform_block(n, 32, 4600 + i)),
+    probs = [(i, m, n) for i, (m, n) in enumerate(sh) if m >= 2048][:4]
+    mats = [(m, n, wl.config4_sigma(n), wl.dense_svd(m, n, wl.config4_sigma(n), 4000 + i)) for i, m, n in probs]
+
+    def check(s, U, V, sg, A):
+        s = host(s)
+        assert np.max(np.abs(s - sg[:16]) / sg[:16]) <= 1e-13
+        Amul, Atmul = O.dense_apply(A)
+        assert O.residual_svd(Amul, Atmul, host(U), host(V), s).max() <= 1e-12
+
+    for (i, _, _), (m, n, sg, A) in zip(probs, mats):
+        p = rr.api.make_params(16, 32, 4, 10, 1e-14, basis="bf16", v0=dev(wl.uniform_block(n, 32, 4600 + i)),
                                refine=True, phase1_sweeps=1)
         s, U, V, info = rr.rr_svd(rr.api.dense_operator(dev(A)), p)
-        assert info["n_converged"] == 16, ((m, n), info)
-        s = host(s)
-        assert np.max(np.abs(s - sg[:16]) / sg[:16]) <= 1e-10
-        Amul, Atmul = O.dense_apply(A)
-        assert O.residual_svd(Amul, Atmul, host(U), host(V), s).max() <= 1.5e-10, (m, n)
-        polished += info["polish_sweeps"] > 0
-    print("problems finished by the polish:", polished, "of", len(probs))
-    assert polished >= 1
+        assert info["polish_sweeps"] >= 1 and info["sweeps"] == 10, ((m, n), info["res_history"])
+        check(s, U, V, sg, A)
+    keep = [dev(A) for _, _, _, A in mats]
+    p = rr.api.make_params(16, 32, 4, 10, 1e-14, basis="bf16", refine=True, phase1_sweeps=1)
+    outs, st, infos = rr.rr_batch_svd([rr.api.dense_operator(t) for t in keep], p, seed=4000)
+    for (s, U, V), (m, n, sg, A), inf in zip(outs, mats, infos):
+        assert inf["polish_sweeps"] >= 1 and inf["sweeps"] == 10, ((m, n), inf)
+        check(s, U, V, sg, A)
 
 
 @pytest.mark.parametrize("k,b", [(40, 96), (64, 160)])

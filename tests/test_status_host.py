@@ -84,12 +84,13 @@ def test_gram_noalloc_rejects_bad_dtype_even_when_empty(L):
 
 @pytest.mark.skipif(shutil.which("gcc") is None, reason="needs gcc")
 def test_struct_layout_matches_header(tmp_path):
-    """sizeof and field offsets of rr_operator, rr_params and rr_info as the C
-    compiler lays them out from include/rr.h, against the ctypes structures."""
+    """sizeof and field offsets of rr_operator, rr_params, rr_info and
+    rr_batch_tuning as the C compiler lays them out from include/rr.h, against
+    the ctypes structures."""
     from paper_2505_00281_gb300 import _lib
-    fields = {"rr_params": [f for f, _ in _lib.RrParams._fields_],
-              "rr_info": [f for f, _ in _lib.RrInfo._fields_],
-              "rr_operator": [f for f, _ in _lib.RrOperator._fields_]}
+    classes = (("rr_params", _lib.RrParams), ("rr_info", _lib.RrInfo), ("rr_operator", _lib.RrOperator),
+               ("rr_batch_tuning", _lib.RrBatchTuning))
+    fields = {t: [f for f, _ in cls._fields_] for t, cls in classes}
     src = ['#include <stdio.h>', '#include <stddef.h>', '#include "rr.h"', 'int main(void) {']
     for t, fs in fields.items():
         src.append(f'printf("{t} %zu\\n", sizeof({t}));')
@@ -102,7 +103,7 @@ def test_struct_layout_matches_header(tmp_path):
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)], check=True)
     got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
                                                         check=True).stdout.splitlines())
-    for t, cls in (("rr_params", _lib.RrParams), ("rr_info", _lib.RrInfo), ("rr_operator", _lib.RrOperator)):
+    for t, cls in classes:
         assert int(got[t]) == ctypes.sizeof(cls), t
         for f in fields[t]:
             assert int(got[f"{t}.{f}"]) == getattr(cls, f).offset, (t, f)
