@@ -232,8 +232,10 @@ size_t rr_batch_workspace_size(int32_t count, const rr_operator* A, const rr_par
  * draws its start block from U(0,1) with a counter-based generator seeded by
  * `seed` + problem index).  per_problem (host, count entries) and info (host,
  * count entries) receive each problem's status and counts.  The batch runs
- * as captured CUDA graphs launched on `stream` (one graph for up to 4096
- * captured problem-sweeps).  A problem's first sweep is captured as plain
+ * as captured CUDA graphs launched in order on `stream` (one graph per 16
+ * problems; with fixed_sweeps one per up to 4096 problem-sweeps), the host
+ * capturing the next graph while the GPU runs the earlier ones.  A problem's
+ * first sweep is captured as plain
  * graph nodes and its later sweeps run inside WHILE graph nodes: after each
  * sweep a kernel checks the k wanted residuals against tol and the sweep
  * count against max_sweeps and sets the node's condition, so every problem

@@ -2109,9 +2109,12 @@ static size_t cluster_smem(int c) {
 // orthogonal columns, Vout (c x c) orthogonal.  FP32 block one-sided Jacobi
 // (relative orthogonality 1e-4, column norms floored at 1e-10 of the largest
 // so rounding-level directions do not stall it; for wide pencils on the
-// QR-preconditioned C Q, starting from V = Q), then four FP64 refinement
+// QR-preconditioned C Q, starting from V = Q), then three FP64 refinement
 // steps (N = C V, K = N^T N, T = V^T V, clusters, V <- V (I + E)) and
-// M = C V.
+// M = C V.  The steps square the defects (1e-4 from the Jacobi, 1e-8, 1e-16):
+// two reach rounding level on the dense benchmark's pencils (a fourth step
+// changed no result there, at 0.5 ms per solve); the third is the margin for
+// pencils whose clusters take a rotation in the second.
 static rr_status jacobi_svd(cudaStream_t s, int r, int c, const double* C, PencilWs& w, double* Mout,
                             double* Vout) {
   int ww, P;
@@ -2134,7 +2137,8 @@ static rr_status jacobi_svd(cudaStream_t s, int r, int c, const double* C, Penci
   const size_t csm = cluster_smem(c);
   if (csm > 48 * 1024)
     RR_CUDA(cudaFuncSetAttribute(k_cluster_rot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
-  for (int it = 0; it < 4; ++it) {
+  constexpr int kRefineSteps = 3;
+  for (int it = 0; it < kRefineSteps; ++it) {
     gemm_small(s, 0, 0, r, c, c, 1.0, C, r, w.V, c, 0.0, w.Mp, r);          // N = C V
     gemm_small_sym(s, c, r, w.Mp, r, w.Mp, r, w.E2, c);                     // K = N^T N
     gemm_small_sym(s, c, c, w.V, c, w.V, c, w.T, c);                        // T = V^T V
@@ -2151,9 +2155,9 @@ static rr_status jacobi_svd(cudaStream_t s, int r, int c, const double* C, Penci
   if (Vout != w.V)
     RR_CUDA(cudaMemcpyAsync(Vout, w.V, (size_t)c * c * sizeof(double), cudaMemcpyDeviceToDevice, s));
   // setup (scale, pad copy unless the QR preconditioner ran, norm floor, V to
-  // FP64; the QR and Jacobi launchers count their own), 4 x 8 refinement
-  // kernels, the final product (in check_launch)
-  note_launches((qr ? 3 : 4) + 32);
+  // FP64; the QR and Jacobi launchers count their own), 8 refinement kernels
+  // per step, the final product (in check_launch)
+  note_launches((qr ? 3 : 4) + 8 * kRefineSteps);
   return check_launch("jacobi_svd");
 }
 

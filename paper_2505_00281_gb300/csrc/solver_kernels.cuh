@@ -81,6 +81,7 @@ struct GemmSplitCap {
 };
 constexpr int kBatchMaxBranches = 64;
 constexpr int kBatchSweepBudget = 4096;  // problem-sweeps captured in one graph of the batched SVD
+constexpr int kBatchLoopChunk = 16;      // problems per graph with device-side loop control
 // E4M3 x E4M3 tensor-core product with row / column scales (k_gemm_tc.cu)
 rr_status gemm_e4m3_tc(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, const float* rscale,
                        const void* B, int64_t ldb, const float* cscale, float* C, int64_t ldc, cudaStream_t s);
