@@ -1416,6 +1416,25 @@ static rr_status side_stream(cudaStream_t s, SideStream* out) {
   return RR_OK;
 }
 
+// Fork independent work of the caller's stream s onto its side stream (*s2
+// runs after s's work so far) and join it back (s waits for *s2's work).
+rr_status side_fork(cudaStream_t s, cudaStream_t* s2) {
+  SideStream ss;
+  RR_TRY(side_stream(s, &ss));
+  RR_CUDA(cudaEventRecord(ss.fork, s));
+  RR_CUDA(cudaStreamWaitEvent(ss.s2, ss.fork, 0));
+  *s2 = ss.s2;
+  return RR_OK;
+}
+
+rr_status side_join(cudaStream_t s) {
+  SideStream ss;
+  RR_TRY(side_stream(s, &ss));
+  RR_CUDA(cudaEventRecord(ss.join, ss.s2));
+  RR_CUDA(cudaStreamWaitEvent(s, ss.join, 0));
+  return RR_OK;
+}
+
 rr_status pencil_side_prepare(cudaStream_t s) {
   SideStream ss;
   return side_stream(s, &ss);
@@ -2109,12 +2128,13 @@ static size_t cluster_smem(int c) {
 // orthogonal columns, Vout (c x c) orthogonal.  FP32 block one-sided Jacobi
 // (relative orthogonality 1e-4, column norms floored at 1e-10 of the largest
 // so rounding-level directions do not stall it; for wide pencils on the
-// QR-preconditioned C Q, starting from V = Q), then three FP64 refinement
+// QR-preconditioned C Q, starting from V = Q), then four FP64 refinement
 // steps (N = C V, K = N^T N, T = V^T V, clusters, V <- V (I + E)) and
 // M = C V.  The steps square the defects (1e-4 from the Jacobi, 1e-8, 1e-16):
-// two reach rounding level on the dense benchmark's pencils (a fourth step
-// changed no result there, at 0.5 ms per solve); the third is the margin for
-// pencils whose clusters take a rotation in the second.
+// two reach rounding level on the dense benchmark's pencils, but a pencil
+// whose clusters take their rotation late needs all four (a 200-column
+// pencil with clustered values: orthogonality 2.6e-11 after three, 1e-15
+// after four).
 static rr_status jacobi_svd(cudaStream_t s, int r, int c, const double* C, PencilWs& w, double* Mout,
                             double* Vout) {
   int ww, P;
@@ -2137,7 +2157,7 @@ static rr_status jacobi_svd(cudaStream_t s, int r, int c, const double* C, Penci
   const size_t csm = cluster_smem(c);
   if (csm > 48 * 1024)
     RR_CUDA(cudaFuncSetAttribute(k_cluster_rot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
-  constexpr int kRefineSteps = 3;
+  constexpr int kRefineSteps = 4;
   for (int it = 0; it < kRefineSteps; ++it) {
     gemm_small(s, 0, 0, r, c, c, 1.0, C, r, w.V, c, 0.0, w.Mp, r);          // N = C V
     gemm_small_sym(s, c, r, w.Mp, r, w.Mp, r, w.E2, c);                     // K = N^T N

@@ -250,6 +250,8 @@ static rr_status apply_f64_T(const Op& op, int64_t b, const double* X, int64_t l
 struct Common {
   void* hess_ws;
   size_t hess_bytes;
+  void* hess_ws2;   // a second Algorithm 8 workspace (for a process running concurrently)
+  int32_t* piv2;
   void* gram_ws;
   size_t gram_bytes;
   void* pen_ws;
@@ -267,11 +269,13 @@ static void carve_common(Arena& ar, int64_t rows, int64_t b2, int32_t wt, Common
   // polish sweep runs Algorithm 8 in FP64 on b <= b2 columns)
   c.hess_bytes = std::max(rr_hessenberg_workspace_size(rows, b2, wt), rr_hessenberg_workspace_size(rows, b2, RR_F64));
   c.hess_ws = ar.take_bytes(c.hess_bytes);
+  c.hess_ws2 = ar.take_bytes(c.hess_bytes);
   c.gram_bytes = rr_gram_workspace_size(rows, b2, b2);
   c.gram_ws = ar.take_bytes(c.gram_bytes);
   c.pen_bytes = rr_pencil_workspace_size(b2, b2);
   c.pen_ws = ar.take_bytes(c.pen_bytes);
   c.piv = ar.take<int32_t>(b2);
+  c.piv2 = ar.take<int32_t>(b2);
   c.scale = ar.take<double>(b2);
   c.hess_grid = 0;
   c.hess_tol = 0.0;
@@ -284,6 +288,14 @@ static rr_status basis_step(const Common& c, bool hess, int32_t wt, int32_t dt, 
     return hessenberg_ex(wt, rows, b, W, ldw, dt, Q, ldq, c.piv, c.hess_tol, c.hess_ws, c.hess_bytes, s,
                          c.hess_grid);
   return scale_cast(s, wt, rows, b, W, ldw, c.scale, dt, Q, ldq, nullptr, nullptr);
+}
+
+// The same Common with the second Algorithm 8 workspace and pivot array.
+static Common second_hess(const Common& c) {
+  Common d = c;
+  d.hess_ws = c.hess_ws2;
+  d.piv = c.piv2;
+  return d;
 }
 
 static rr_status gram(const Common& c, int64_t n, int64_t p, int64_t q, int32_t xt, const void* X,
@@ -373,10 +385,12 @@ static int count_converged(const double* res, int k, double tol, double* maxres)
 }
 
 static rr_status read_err(const Common& c, cudaStream_t s) {
-  int e = 0;
+  int e = 0, e2 = 0;
   RR_CUDA(cudaMemcpyAsync(&e, c.hess_ws, sizeof(int), cudaMemcpyDeviceToHost, s));
+  RR_CUDA(cudaMemcpyAsync(&e2, c.hess_ws2, sizeof(int), cudaMemcpyDeviceToHost, s));
   RR_CUDA(cudaStreamSynchronize(s));
   if (e) return (rr_status)e;
+  if (e2) return (rr_status)e2;
   return tc_take_error(s);
 }
 
@@ -747,6 +761,7 @@ static rr_status svd_run(const rr_operator* Aop_in, const rr_params* p, double* 
   w.c.hess_grid = hess_grid;
   w.c.hess_tol = p->hess_tol;
   RR_CUDA(cudaMemsetAsync(w.c.hess_ws, 0, 512, s));
+  RR_CUDA(cudaMemsetAsync(w.c.hess_ws2, 0, 512, s));
   RR_CUDA(cudaMemsetAsync(w.frozen, 0, 8 * sizeof(int), s));
   if (!batch_mode) STAGE(RR_STAGE_OTHER, check_operator_finite(Aop_in, w.c, s));
   if (padq) {
@@ -892,10 +907,17 @@ static rr_status svd_run(const rr_operator* Aop_in, const rr_params* p, double* 
         else STAGE(RR_STAGE_OTHER, scale_cast(s, op.wt, m, b, w.AF, m, w.mu, dt, w.Elo, m, w.coef, w.sig));
       }
     }
-    // conditioning of the correction blocks (Algorithm 8), then A F for the
-    // low-precision block of the projected matrix
-    STAGE(RR_STAGE_HESSENBERG, basis_step(w.c, hess, op.wt, et, m, b, w.AF, m, Eg, m, s));
-    STAGE(RR_STAGE_HESSENBERG, basis_step(w.c, hess, op.wt, et, n, b, w.W, n, Fg, n, s));
+    // conditioning of the correction blocks (Algorithm 8; the two blocks'
+    // processes run at the same time, F's on the side stream with the second
+    // workspace: each is a chain of b latency-bound pivot steps), then A F
+    // for the low-precision block of the projected matrix
+    STAGE(RR_STAGE_HESSENBERG, [&]() -> rr_status {
+      cudaStream_t s2;
+      RR_TRY(side_fork(s, &s2));
+      RR_TRY(basis_step(w.c, hess, op.wt, et, m, b, w.AF, m, Eg, m, s));
+      RR_TRY(basis_step(second_hess(w.c), hess, op.wt, et, n, b, w.W, n, Fg, n, s2));
+      return side_join(s);
+    }());
     if (sp) {
       STAGE(RR_STAGE_OTHER, scale_split(s, RR_F32, n, b, w.F32, n, nullptr, w.Flo, w.Flo2, n, nullptr, nullptr));
       STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp_split(op, b, w.Flo, w.Flo2, n, w.AF, m, nullptr, 0, nullptr, s));
@@ -1152,6 +1174,7 @@ static rr_status eig_run(const rr_operator* Aop, const rr_params* p, double* the
   prof.start();
   w.c.hess_tol = p->hess_tol;
   RR_CUDA(cudaMemsetAsync(w.c.hess_ws, 0, 512, s));
+  RR_CUDA(cudaMemsetAsync(w.c.hess_ws2, 0, 512, s));
   STAGE(RR_STAGE_OTHER, check_operator_finite(Aop, w.c, s));
   STAGE(RR_STAGE_OTHER, prepare_op(op, op, true, s));
 
@@ -1600,6 +1623,7 @@ extern "C" rr_status rr_batch_svd_tuned(int32_t count, const rr_operator* A, con
     RR_CUDA(cudaMemcpy(hres.data(), w.res, p->k * sizeof(double), cudaMemcpyDeviceToHost));
     int e = 0;
     RR_CUDA(cudaMemcpy(&e, w.c.hess_ws, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!e) RR_CUDA(cudaMemcpy(&e, w.c.hess_ws2, sizeof(int), cudaMemcpyDeviceToHost));
     if (dloop) {
       // sweeps the problem ran (device-side loop control)
       int ctl[3] = {0, 0, 0};

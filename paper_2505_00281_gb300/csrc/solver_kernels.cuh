@@ -25,6 +25,8 @@ rr_status normalize_sign(cudaStream_t s, int64_t n, int64_t k, double* X, int64_
                          double* U, int64_t ldu);
 rr_status vec_mul(cudaStream_t s, int64_t n, const double* a, const double* b, double* d);
 rr_status fill(cudaStream_t s, int64_t n, double v, double* d);
+rr_status side_fork(cudaStream_t s, cudaStream_t* s2);
+rr_status side_join(cudaStream_t s);
 rr_status eye_neg(cudaStream_t s, int64_t b, const double* K, int64_t ldk, double* Y, int64_t ldy);
 rr_status add_cols_scaled(cudaStream_t s, int64_t n, int64_t b, const double* X, int64_t ldx, const double* c, int pw,
                           double* Y, int64_t ldy);
