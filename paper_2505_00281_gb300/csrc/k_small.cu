@@ -1985,15 +1985,33 @@ __global__ void __launch_bounds__(1024) k_cluster_rot(int c, const double* __res
   }
   __syncthreads();
   const float tb = (float)tan(2.0 * kBigAngle);
-  for (int e = tid; e < c * c; e += blockDim.x) {
-    const int i = e % c, j = e / c;
-    if (i >= j) continue;
-    const float cij = (float)K[e] - 0.5f * (lamf[i] + lamf[j]) * (float)T[e];
-    if (fabsf(2.f * cij) > tb * fabsf(lamf[j] - lamf[i]) &&
-        fabsf(cij) > (float)kCoupleNoise * fmaxf(fabsf(lamf[i]), fabsf(lamf[j]))) {
-      const int a = min(pos[i], pos[j]), b = max(pos[i], pos[j]);
-      atomicAdd(&link[a], 1);
-      atomicAdd(&link[b], -1);
+  // every pair (i < j) once; four entries of K and T per thread in flight at
+  // a time (one load after another made this pass most of the kernel's time)
+  const int cc = c * c;
+  for (int e0 = tid; e0 < cc; e0 += 4 * (int)blockDim.x) {
+    float kv[4], tv[4];
+    int ii[4], jj[4];
+    bool ok[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = e0 + u * (int)blockDim.x;
+      ii[u] = e % c;
+      jj[u] = e / c;
+      ok[u] = e < cc && ii[u] < jj[u];
+      kv[u] = ok[u] ? (float)K[e] : 0.f;
+      tv[u] = ok[u] ? (float)T[e] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (!ok[u]) continue;
+      const int i = ii[u], j = jj[u];
+      const float cij = kv[u] - 0.5f * (lamf[i] + lamf[j]) * tv[u];
+      if (fabsf(2.f * cij) > tb * fabsf(lamf[j] - lamf[i]) &&
+          fabsf(cij) > (float)kCoupleNoise * fmaxf(fabsf(lamf[i]), fabsf(lamf[j]))) {
+        const int a = min(pos[i], pos[j]), b = max(pos[i], pos[j]);
+        atomicAdd(&link[a], 1);
+        atomicAdd(&link[b], -1);
+      }
     }
   }
   __syncthreads();

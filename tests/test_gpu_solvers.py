@@ -261,6 +261,30 @@ def test_batch_device_loop_stops_at_tol(rr, basis, refine):
             assert O.residual_svd(Amul, Atmul, host(U), host(V), s).max() <= 1.5e-10
 
 
+def test_batch_svd_several_graphs(rr):
+    """A batch larger than one captured graph (graphs of 16 problems, launched
+    in order while the host captures the next): 40 problems of the batched
+    workload's smallest class in three graphs, every one converged to the
+    closed form, its sweep count within max_sweeps."""
+    sh = [(m, n) for m, n in wl.config4_shapes(512) if m < 512][:40]
+    ops, keep, sigs = [], [], []
+    for i, (m, n) in enumerate(sh):
+        sg = wl.config4_sigma(n)
+        A = wl.dense_svd(m, n, sg, 4400 + i)
+        keep.append((A, dev(A)))
+        ops.append(rr.api.dense_operator(keep[-1][1]))
+        sigs.append(sg)
+    p = rr.api.make_params(16, 32, 4, 12, 1e-10, basis="bf16", refine=True, phase1_sweeps=1)
+    outs, st, infos = rr.rr_batch_svd(ops, p, seed=4400)
+    assert all(x == 0 for x in st), [(i, inf) for i, (x, inf) in enumerate(zip(st, infos)) if x]
+    assert all(1 <= inf["sweeps"] <= 12 for inf in infos)
+    for (s, U, V), sg, (A, _) in zip(outs, sigs, keep):
+        s = host(s)
+        assert np.max(np.abs(s - sg[:16]) / sg[:16]) <= 1e-10
+        Amul, Atmul = O.dense_apply(A)
+        assert O.residual_svd(Amul, Atmul, host(U), host(V), s).max() <= 1.5e-10
+
+
 def test_svd_seeded_start_block_and_info(rr):
     """v0 = NULL draws the start block on the device from params.seed (Alg. 1's
     U(0,1) block) and the solve converges from it.  Runs are not reproducible
