@@ -523,8 +523,9 @@ __global__ void __launch_bounds__(256) k_gram32(int64_t n, int64_t p, int64_t q,
 // (rows 2 ti + 32 a' + {0, 1} of G, a' < PT / 2, and columns PT tj ..); each
 // staged row gives it PT X values (8-byte shared loads, 16 distinct per
 // warp: one wavefront) and PT Y values (broadcast 8-byte loads) per PT^2
-// FMAs, and the next rows' global loads are issued before the current rows
-// are used.
+// FMAs, issued as packed FP32 pairs (each component rounded as one fmaf),
+// and the next rows' global loads are issued before the current rows are
+// used.
 template <int PT>
 __global__ void __launch_bounds__(256, 1) k_gram32_full(int64_t n, int p, int q, const float* __restrict__ X,
                                                         int64_t ldx, const float* __restrict__ Y, int64_t ldy,
@@ -534,7 +535,12 @@ __global__ void __launch_bounds__(256, 1) k_gram32_full(int64_t n, int p, int q,
   __shared__ __align__(16) float Ys[R][TP + 2];
   const int64_t r0 = (int64_t)blockIdx.x * rpc, r1 = r0 + rpc < n ? r0 + rpc : n;
   const int tid = threadIdx.x, ti = tid & 15, tj = tid >> 4;
-  float acc[PT][PT] = {};
+  static_assert(PT % 2 == 0, "column pairs");
+  float2 acc[PT][PT / 2];
+#pragma unroll
+  for (int a = 0; a < PT; ++a)
+#pragma unroll
+    for (int c = 0; c < PT / 2; ++c) acc[a][c] = make_float2(0.f, 0.f);
   // staging: R rows x TP columns of each operand, thread e -> (row e % R, column e / R)
   constexpr int PER = R * TP / 256;
   float xr[PER], yr[PER];
@@ -560,7 +566,8 @@ __global__ void __launch_bounds__(256, 1) k_gram32_full(int64_t n, int p, int q,
     if (rs + R < r1) fetch(rs + R);  // in flight while the tile is used
 #pragma unroll 2
     for (int rr_ = 0; rr_ < R; ++rr_) {
-      float xa[PT], ya[PT];
+      float xa[PT];
+      float2 ya[PT / 2];
 #pragma unroll
       for (int a = 0; a < PT; a += 2) {
         const float2 xv = *reinterpret_cast<const float2*>(&Xs[rr_][2 * ti + 16 * a]);
@@ -568,15 +575,13 @@ __global__ void __launch_bounds__(256, 1) k_gram32_full(int64_t n, int p, int q,
         xa[a + 1] = xv.y;
       }
 #pragma unroll
-      for (int a = 0; a < PT; a += 2) {
-        const float2 yv = *reinterpret_cast<const float2*>(&Ys[rr_][PT * tj + a]);
-        ya[a] = yv.x;
-        ya[a + 1] = yv.y;
+      for (int c = 0; c < PT / 2; ++c) ya[c] = *reinterpret_cast<const float2*>(&Ys[rr_][PT * tj + 2 * c]);
+#pragma unroll
+      for (int a = 0; a < PT; ++a) {
+        const float2 xx = make_float2(xa[a], xa[a]);
+#pragma unroll
+        for (int c = 0; c < PT / 2; ++c) acc[a][c] = __ffma2_rn(xx, ya[c], acc[a][c]);
       }
-#pragma unroll
-      for (int a = 0; a < PT; ++a)
-#pragma unroll
-        for (int c = 0; c < PT; ++c) acc[a][c] = fmaf(xa[a], ya[c], acc[a][c]);
     }
   }
   double* out = part + (size_t)blockIdx.x * p * q;
@@ -585,7 +590,7 @@ __global__ void __launch_bounds__(256, 1) k_gram32_full(int64_t n, int p, int q,
 #pragma unroll
     for (int c = 0; c < PT; ++c) {
       const int i = 2 * ti + 16 * (a & ~1) + (a & 1), j = PT * tj + c;
-      if (i < p && j < q) out[i + (int64_t)j * p] = (double)acc[a][c];
+      if (i < p && j < q) out[i + (int64_t)j * p] = (double)((c & 1) ? acc[a][c >> 1].y : acc[a][c >> 1].x);
     }
 }
 

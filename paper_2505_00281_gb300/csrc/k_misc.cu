@@ -129,7 +129,8 @@ __global__ void __launch_bounds__(256) k_sub_lowrank32(int64_t n, int64_t b, int
 // dimension goes in steps of 32, the next step's X loads issued before the
 // current step is used; the tile of T itself is copied to shared memory by
 // asynchronous 4-byte copies issued with the tile's first step, so the
-// epilogue's read of T does not wait on HBM.
+// epilogue's read of T does not wait on HBM.  The FMAs are issued as packed
+// FP32 pairs over the columns (each component rounded as one fmaf).
 __device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   const int n = valid ? 4 : 0;  // 0: fill with zeros, nothing read
@@ -169,7 +170,12 @@ __global__ void __launch_bounds__(256, 1) k_sub_lowrank32_full(int64_t n, int b,
   if (tile < tiles) fetch(tile, 0);
   for (; tile < tiles; tile += gridDim.x) {
     const int64_t m0 = tile * kSLF_M;
-    float acc[8][CT] = {};
+    static_assert(CT % 2 == 0, "column pairs");
+    float2 acc[8][CT / 2];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int c = 0; c < CT / 2; ++c) acc[a][c] = make_float2(0.f, 0.f);
     for (int step = 0; step < ksteps; ++step) {
       __syncthreads();
 #pragma unroll
@@ -191,20 +197,19 @@ __global__ void __launch_bounds__(256, 1) k_sub_lowrank32_full(int64_t n, int b,
       const int k0 = step * kSLF_K, kn = p - k0 < kSLF_K ? p - k0 : kSLF_K;
 #pragma unroll 2
       for (int kk = 0; kk < kn; ++kk) {
-        float xa[8], ka[CT];
+        float xa[8];
+        float2 ka[CT / 2];
 #pragma unroll
         for (int a = 0; a < 8; ++a) xa[a] = Xs[kk * kSLF_M + ti + 16 * a];
         const float* kr = Ks + (size_t)(k0 + kk) * KS + CT * tj;
 #pragma unroll
-        for (int c = 0; c < CT; c += 2) {
-          const float2 kv = *reinterpret_cast<const float2*>(kr + c);
-          ka[c] = kv.x;
-          ka[c + 1] = kv.y;
+        for (int c = 0; c < CT / 2; ++c) ka[c] = *reinterpret_cast<const float2*>(kr + 2 * c);
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+          const float2 xx = make_float2(xa[a], xa[a]);
+#pragma unroll
+          for (int c = 0; c < CT / 2; ++c) acc[a][c] = __ffma2_rn(xx, ka[c], acc[a][c]);
         }
-#pragma unroll
-        for (int a = 0; a < 8; ++a)
-#pragma unroll
-          for (int c = 0; c < CT; ++c) acc[a][c] = fmaf(xa[a], ka[c], acc[a][c]);
       }
     }
     cp_async_wait_all();
@@ -216,7 +221,7 @@ __global__ void __launch_bounds__(256, 1) k_sub_lowrank32_full(int64_t n, int b,
 #pragma unroll
       for (int a = 0; a < 8; ++a) {
         const int64_t i = m0 + ti + 16 * a;
-        if (i < n) T[i + j * ldt] = Ts[j * kSLF_M + ti + 16 * a] - acc[a][c];
+        if (i < n) T[i + j * ldt] = Ts[j * kSLF_M + ti + 16 * a] - ((c & 1) ? acc[a][c >> 1].y : acc[a][c >> 1].x);
       }
     }
   }
