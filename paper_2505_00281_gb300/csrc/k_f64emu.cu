@@ -177,81 +177,86 @@ __global__ void k_exp_init(int64_t count, int* __restrict__ e) {
 // lo split in column-major and row-major copies, and the exponents of the
 // largest entry of every row and column (atomic max into rexp / cexp, which
 // start at kExpNone).  Every output may be null.  A block takes a 32-row x
-// 256-column tile, a warp 32 x 32 (lane = row): column loads are coalesced,
-// a lane writes its row's 32 entries of the row-major copies as four 16-byte
-// stores.
-__global__ void __launch_bounds__(256) k_op_pass1(int64_t m, int64_t n, const double* __restrict__ A, int64_t lda,
+// 256-column tile, a warp 32 x 32 (lane = row) in two halves of 16 columns
+// (62 registers instead of 120: four blocks per SM, twice the resident
+// warps; the pass is bound by the loads in flight): column
+// loads are coalesced, a lane writes its row's 16 entries of a half to the
+// row-major copies as two 16-byte stores.
+__global__ void __launch_bounds__(256, 4) k_op_pass1(int64_t m, int64_t n, const double* __restrict__ A, int64_t lda,
                                                   __nv_bfloat16* __restrict__ hi_col, __nv_bfloat16* __restrict__ hi_row,
                                                   __nv_bfloat16* __restrict__ lo_col, __nv_bfloat16* __restrict__ lo_row,
                                                   int* __restrict__ rexp, int* __restrict__ cexp) {
   __shared__ int rmax[8][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t i = (int64_t)blockIdx.x * 32 + lane;
-  const int64_t jw = (int64_t)blockIdx.y * 256 + warp * 32;
   const bool rv = i < m;
   const bool need_lo = lo_col || lo_row;
   int emx = kExpNone;
-  unsigned hp[16], lp[16];
-  double av[32];
+#pragma unroll 1
+  for (int half = 0; half < 2; ++half) {
+    const int64_t jw = (int64_t)blockIdx.y * 256 + warp * 32 + 16 * half;
+    unsigned hp[8], lp[8];
+    double av[16];
 #pragma unroll
-  for (int c = 0; c < 32; ++c) {
-    const int64_t j = jw + c;
-    av[c] = (rv && j < n) ? A[i + j * lda] : 0.0;
-  }
+    for (int c = 0; c < 16; ++c) {
+      const int64_t j = jw + c;
+      av[c] = (rv && j < n) ? A[i + j * lda] : 0.0;
+    }
 #pragma unroll
-  for (int c = 0; c < 32; ++c) {
-    const int64_t j = jw + c;
-    const double a = av[c];
-    const unsigned long long u = (unsigned long long)__double_as_longlong(a);
-    const int E = (int)((u >> 52) & 0x7FF);
-    const int e = E == 0 ? kExpNone : E - 1022;
-    emx = max(emx, e);
-    if (cexp) {
-      int ce = e;
+    for (int c = 0; c < 16; ++c) {
+      const int64_t j = jw + c;
+      const double a = av[c];
+      const unsigned long long u = (unsigned long long)__double_as_longlong(a);
+      const int E = (int)((u >> 52) & 0x7FF);
+      const int e = E == 0 ? kExpNone : E - 1022;
+      emx = max(emx, e);
+      if (cexp) {
+        int ce = e;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) ce = max(ce, __shfl_xor_sync(0xffffffffu, ce, o));
-      if (lane == 0 && j < n) atomicMax(cexp + j, ce);
-    }
-    unsigned h = 0, l = 0;
-    if (need_lo) {
-      bf16_split_bits(a, h, l);
-    } else {
-      h = bf16_bits_of(a);
-    }
-    if (c & 1) {
-      hp[c >> 1] |= h << 16;
-      lp[c >> 1] |= l << 16;
-    } else {
-      hp[c >> 1] = h;
-      lp[c >> 1] = l;
-    }
-    if (rv && j < n) {
-      if (hi_col) hi_col[i + j * m] = __ushort_as_bfloat16((unsigned short)h);
-      if (lo_col) lo_col[i + j * m] = __ushort_as_bfloat16((unsigned short)l);
-    }
-  }
-  if (rv) {
-    const bool vec = (jw + 32 <= n) && (n % 8 == 0);
-    if (hi_row) {
-      if (vec) {
-        uint4* dst = reinterpret_cast<uint4*>(hi_row + i * n + jw);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) dst[k] = make_uint4(hp[4 * k], hp[4 * k + 1], hp[4 * k + 2], hp[4 * k + 3]);
+        for (int o = 16; o > 0; o >>= 1) ce = max(ce, __shfl_xor_sync(0xffffffffu, ce, o));
+        if (lane == 0 && j < n) atomicMax(cexp + j, ce);
+      }
+      unsigned h = 0, l = 0;
+      if (need_lo) {
+        bf16_split_bits(a, h, l);
       } else {
-#pragma unroll
-        for (int c = 0; c < 32; ++c)
-          if (jw + c < n) hi_row[i * n + jw + c] = __ushort_as_bfloat16((unsigned short)(hp[c >> 1] >> (16 * (c & 1))));
+        h = bf16_bits_of(a);
+      }
+      if (c & 1) {
+        hp[c >> 1] |= h << 16;
+        lp[c >> 1] |= l << 16;
+      } else {
+        hp[c >> 1] = h;
+        lp[c >> 1] = l;
+      }
+      if (rv && j < n) {
+        if (hi_col) hi_col[i + j * m] = __ushort_as_bfloat16((unsigned short)h);
+        if (lo_col) lo_col[i + j * m] = __ushort_as_bfloat16((unsigned short)l);
       }
     }
-    if (lo_row) {
-      if (vec) {
-        uint4* dst = reinterpret_cast<uint4*>(lo_row + i * n + jw);
+    if (rv) {
+      const bool vec = (jw + 16 <= n) && (n % 8 == 0);
+      if (hi_row) {
+        if (vec) {
+          uint4* dst = reinterpret_cast<uint4*>(hi_row + i * n + jw);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) dst[k] = make_uint4(lp[4 * k], lp[4 * k + 1], lp[4 * k + 2], lp[4 * k + 3]);
-      } else {
+          for (int k = 0; k < 2; ++k) dst[k] = make_uint4(hp[4 * k], hp[4 * k + 1], hp[4 * k + 2], hp[4 * k + 3]);
+        } else {
 #pragma unroll
-        for (int c = 0; c < 32; ++c)
-          if (jw + c < n) lo_row[i * n + jw + c] = __ushort_as_bfloat16((unsigned short)(lp[c >> 1] >> (16 * (c & 1))));
+          for (int c = 0; c < 16; ++c)
+            if (jw + c < n) hi_row[i * n + jw + c] = __ushort_as_bfloat16((unsigned short)(hp[c >> 1] >> (16 * (c & 1))));
+        }
+      }
+      if (lo_row) {
+        if (vec) {
+          uint4* dst = reinterpret_cast<uint4*>(lo_row + i * n + jw);
+#pragma unroll
+          for (int k = 0; k < 2; ++k) dst[k] = make_uint4(lp[4 * k], lp[4 * k + 1], lp[4 * k + 2], lp[4 * k + 3]);
+        } else {
+#pragma unroll
+          for (int c = 0; c < 16; ++c)
+            if (jw + c < n) lo_row[i * n + jw + c] = __ushort_as_bfloat16((unsigned short)(lp[c >> 1] >> (16 * (c & 1))));
+        }
       }
     }
   }
