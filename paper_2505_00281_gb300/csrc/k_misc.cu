@@ -261,6 +261,19 @@ __global__ void k_cast_f32(int64_t n, int64_t b, const double* __restrict__ X, i
   }
 }
 
+__global__ void k_widen_f32(int64_t n, const float* __restrict__ x, double* __restrict__ y) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    y[e] = (double)x[e];
+}
+
+// y (n, FP64) = x (n, FP32), contiguous
+rr_status widen_f32(cudaStream_t s, int64_t n, const float* x, double* y) {
+  if (n <= 0) return RR_OK;
+  const int64_t want = (n + 255) / 256, cap = 4 * (int64_t)num_sms();
+  k_widen_f32<<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(n, x, y);
+  return check_launch("widen_f32");
+}
+
 rr_status cast_f32(cudaStream_t s, int64_t n, int64_t b, const double* X, int64_t ldx, float* Y, int64_t ldy) {
   if (n == 0 || b == 0) return RR_OK;
   const int64_t want = (n * b + 255) / 256, cap = 8 * (int64_t)num_sms();

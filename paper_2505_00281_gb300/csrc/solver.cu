@@ -316,6 +316,31 @@ static rr_status project_out(const Common& c, cudaStream_t s, int64_t n, int64_t
   return sub_lowrank_f32(s, n, b, b, X, ldx, K, b, T, ldt);
 }
 
+// Scratch of the tensor-core form of project_out for tall blocks: the Ritz
+// vectors as split BF16 pairs (taken once per sweep), the block T as split
+// BF16 pairs, the FP32 Gram.
+struct ProjTc {
+  __nv_bfloat16 *Xh = nullptr, *Xl = nullptr, *Th = nullptr, *Tl = nullptr;
+  float* K32 = nullptr;
+};
+
+// Tall blocks (n >= 65536, n a multiple of 8, b <= 256) of a BF16 basis: the Gram K = X^T T
+// on the tensor cores from split BF16 operands (X = X_hi + X_lo, T = T_hi +
+// T_lo, the lo.lo product dropped: about 2^-16 relative, against FP32's
+// 2^-24 with the FP32-pipe kernel at three times the time), the update
+// T -= X K as before.  The block is stored in BF16 right after the
+// projection, so components along X at 1e-5 of the block are far below its
+// own rounding.
+static bool proj_tc_applies(int64_t n, int64_t b) { return n >= 65536 && n % 8 == 0 && b <= 256; }
+
+static rr_status project_out_tc(const ProjTc& pt, cudaStream_t s, int64_t n, int64_t b, const float* X, int64_t ldx,
+                                float* T, int64_t ldt, double* K) {
+  RR_TRY(scale_split(s, RR_F32, n, b, T, ldt, nullptr, pt.Th, pt.Tl, n, nullptr, nullptr));
+  RR_TRY(gemm_bf16_tc_split(b, b, n, pt.Xh, pt.Xl, n, pt.Th, pt.Tl, n, pt.K32, b, nullptr, 0, nullptr, s));
+  RR_TRY(widen_f32(s, b * b, pt.K32, K));
+  return sub_lowrank_f32(s, n, b, b, X, ldx, K, b, T, ldt);
+}
+
 // Pencil solves that record which sizes ran, so the condition estimate of
 // the last one can be found in the pencil workspace.
 static rr_status pencil_svd(Common& c, int64_t b1, int64_t b2, const double* B, const double* Gu,
@@ -1069,6 +1094,7 @@ struct EigBufs {
   double *G, *H, *Y, *Ysel, *th2;
   double *X, *X2, *theta, *P, *R, *ss, *res, *mu, *coef, *kap, *kap_prev, *rho, *gam, *gersh;
   float* X32;  // FP32 copy of the Ritz vectors for the refinement's projections
+  ProjTc ptc;  // tensor-core projections of tall blocks (null when they do not apply)
 };
 
 // Row stride of the filter's row-major blocks: b rounded up to 8 columns
@@ -1107,6 +1133,13 @@ static void carve_eig(Arena& ar, const Op& op, int64_t b, bool refine, EigBufs& 
     w.Dlo = ar.take_bytes(n * b * ds);
     w.AD = ar.take_bytes(n * b * ws_);
     w.X32 = ar.take<float>(n * b);
+    if (op.dt == RR_BF16 && proj_tc_applies(n, b)) {
+      w.ptc.Xh = (__nv_bfloat16*)ar.take_bytes(n * b * 2);
+      w.ptc.Xl = (__nv_bfloat16*)ar.take_bytes(n * b * 2);
+      w.ptc.Th = (__nv_bfloat16*)ar.take_bytes(n * b * 2);
+      w.ptc.Tl = (__nv_bfloat16*)ar.take_bytes(n * b * 2);
+      w.ptc.K32 = ar.take<float>(b * b);
+    }
   } else {
     w.X2 = nullptr;
     w.Dlo = w.AD = nullptr;
@@ -1318,8 +1351,15 @@ static rr_status eig_run(const rr_operator* Aop, const rr_params* p, double* the
         prev_mx = INFINITY;
         continue;
       }
-      // FP32 copy of the Ritz vectors for the projections of this sweep
+      // FP32 copy (and, for tall blocks, split BF16 pairs) of the Ritz vectors
+      // for the projections of this sweep
       STAGE(RR_STAGE_OTHER, cast_f32(s, n, b, w.X, n, w.X32, n));
+      if (w.ptc.Xh)
+        STAGE(RR_STAGE_OTHER, scale_split(s, RR_F64, n, b, w.X, n, nullptr, w.ptc.Xh, w.ptc.Xl, n, nullptr, nullptr));
+      auto proj = [&](float* T) -> rr_status {
+        return w.ptc.Xh ? project_out_tc(w.ptc, s, n, b, w.X32, n, T, n, w.Y)
+                        : project_out(w.c, s, n, b, w.X32, n, T, n, w.Y);
+      };
       if (cheb) {
         // D_1 = (s1/e) R;  D_{j+1} = (2 s_{j+1}/e)(A - cI) D_j - s_j s_{j+1} D_{j-1}
         //                           + (2 s_{j+1}/e) phi_j(theta) R
@@ -1345,7 +1385,7 @@ static rr_status eig_run(const rr_operator* Aop, const rr_params* p, double* the
           STAGE(RR_STAGE_OTHER, vec_scale(s, b, an, w.kap, w.gam));
           STAGE(RR_STAGE_LOWP_PRODUCT, rr_chebyshev_step(n, b, op.rp, op.ci, op.va, dt, d0, dm1, n, an, c, bn, w.rho, w.R, n,
                                    w.gam, op.wt, w.W, n, s));
-          STAGE(RR_STAGE_GRAM, project_out(w.c, s, n, b, w.X32, n, (float*)w.W, n, w.Y));
+          STAGE(RR_STAGE_GRAM, proj((float*)w.W));
           if (j + 1 < q) {
             // Dhat_{j+1} = T / mu into the buffer of Dhat_{j-1}
             void* dst = dm1 ? dm1 : d1;
@@ -1366,7 +1406,7 @@ static rr_status eig_run(const rr_operator* Aop, const rr_params* p, double* the
           STAGE(RR_STAGE_OTHER, scale_cast(s, RR_F64, n, b, w.R, n, w.mu, dt, w.Vlo, n, w.coef, w.theta));
           for (int j = 1; j < q; ++j) {
             STAGE(RR_STAGE_LOWP_PRODUCT, apply_lowp(op, b, w.Vlo, n, w.W, n, w.R, n, w.coef, s));
-            STAGE(RR_STAGE_GRAM, project_out(w.c, s, n, b, w.X32, n, (float*)w.W, n, w.Y));
+            STAGE(RR_STAGE_GRAM, proj((float*)w.W));
             if (j + 1 < q) STAGE(RR_STAGE_OTHER, scale_cast(s, op.wt, n, b, w.W, n, w.mu, dt, w.Vlo, n, w.coef, w.theta));
           }
         }
