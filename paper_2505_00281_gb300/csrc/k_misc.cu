@@ -261,17 +261,21 @@ __global__ void k_cast_f32(int64_t n, int64_t b, const double* __restrict__ X, i
   }
 }
 
-__global__ void k_widen_f32(int64_t n, const float* __restrict__ x, double* __restrict__ y) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-    y[e] = (double)x[e];
+// T (n x b, FP32, ld ldt) -= P (n x b, FP32, ld ldp)
+__global__ void k_sub_block_f32(int64_t n, int64_t b, const float* __restrict__ P, int64_t ldp, float* __restrict__ T,
+                                int64_t ldt) {
+  const int64_t tot = n * b;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % n, j = e / n;
+    T[i + j * ldt] -= P[i + j * ldp];
+  }
 }
 
-// y (n, FP64) = x (n, FP32), contiguous
-rr_status widen_f32(cudaStream_t s, int64_t n, const float* x, double* y) {
-  if (n <= 0) return RR_OK;
-  const int64_t want = (n + 255) / 256, cap = 4 * (int64_t)num_sms();
-  k_widen_f32<<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(n, x, y);
-  return check_launch("widen_f32");
+rr_status sub_block_f32(cudaStream_t s, int64_t n, int64_t b, const float* P, int64_t ldp, float* T, int64_t ldt) {
+  if (n <= 0 || b <= 0) return RR_OK;
+  const int64_t want = (n * b + 255) / 256, cap = 8 * (int64_t)num_sms();
+  k_sub_block_f32<<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(n, b, P, ldp, T, ldt);
+  return check_launch("sub_block_f32");
 }
 
 rr_status cast_f32(cudaStream_t s, int64_t n, int64_t b, const double* X, int64_t ldx, float* Y, int64_t ldy) {

@@ -317,28 +317,38 @@ static rr_status project_out(const Common& c, cudaStream_t s, int64_t n, int64_t
 }
 
 // Scratch of the tensor-core form of project_out for tall blocks: the Ritz
-// vectors as split BF16 pairs (taken once per sweep), the block T as split
-// BF16 pairs, the FP32 Gram.
+// vectors as split BF16 pairs, column-major and row-major (taken once per
+// sweep), the block T as split BF16 pairs, the FP32 Gram and its split
+// pair, the product X K.
 struct ProjTc {
-  __nv_bfloat16 *Xh = nullptr, *Xl = nullptr, *Th = nullptr, *Tl = nullptr;
-  float* K32 = nullptr;
+  __nv_bfloat16 *Xh = nullptr, *Xl = nullptr, *Xrh = nullptr, *Xrl = nullptr, *Th = nullptr, *Tl = nullptr;
+  __nv_bfloat16 *Kh = nullptr, *Kl = nullptr;
+  float *K32 = nullptr, *P = nullptr;
 };
 
-// Tall blocks (n >= 65536, n a multiple of 8, b <= 256) of a BF16 basis: the Gram K = X^T T
-// on the tensor cores from split BF16 operands (X = X_hi + X_lo, T = T_hi +
-// T_lo, the lo.lo product dropped: about 2^-16 relative, against FP32's
-// 2^-24 with the FP32-pipe kernel at three times the time), the update
-// T -= X K as before.  The block is stored in BF16 right after the
-// projection, so components along X at 1e-5 of the block are far below its
-// own rounding.
+// Tall blocks (n >= 65536, n a multiple of 8, b <= 256) of a BF16 basis: both
+// products of the projection on the tensor cores from split BF16 operands
+// (X = X_hi + X_lo, T = T_hi + T_lo, K likewise; the lo.lo products dropped:
+// about 2^-16 relative, against FP32's 2^-24 with the FP32-pipe kernels at
+// more than twice the time): K = X^T T, then P = X K and T -= P.  The block
+// is stored in BF16 right after the projection, so components along X at
+// 1e-5 of the block are far below its own rounding.
 static bool proj_tc_applies(int64_t n, int64_t b) { return n >= 65536 && n % 8 == 0 && b <= 256; }
 
-static rr_status project_out_tc(const ProjTc& pt, cudaStream_t s, int64_t n, int64_t b, const float* X, int64_t ldx,
-                                float* T, int64_t ldt, double* K) {
+// The split pairs of the Ritz vectors X (n x b, FP64) in both layouts.
+static rr_status proj_tc_prepare(const ProjTc& pt, cudaStream_t s, int64_t n, int64_t b, const double* X,
+                                 int64_t ldx) {
+  RR_TRY(scale_split(s, RR_F64, n, b, X, ldx, nullptr, pt.Xh, pt.Xl, n, nullptr, nullptr));
+  RR_TRY(block_to_rows(s, RR_BF16, n, b, b, pt.Xh, n, pt.Xrh, b));
+  return block_to_rows(s, RR_BF16, n, b, b, pt.Xl, n, pt.Xrl, b);
+}
+
+static rr_status project_out_tc(const ProjTc& pt, cudaStream_t s, int64_t n, int64_t b, float* T, int64_t ldt) {
   RR_TRY(scale_split(s, RR_F32, n, b, T, ldt, nullptr, pt.Th, pt.Tl, n, nullptr, nullptr));
   RR_TRY(gemm_bf16_tc_split(b, b, n, pt.Xh, pt.Xl, n, pt.Th, pt.Tl, n, pt.K32, b, nullptr, 0, nullptr, s));
-  RR_TRY(widen_f32(s, b * b, pt.K32, K));
-  return sub_lowrank_f32(s, n, b, b, X, ldx, K, b, T, ldt);
+  RR_TRY(scale_split(s, RR_F32, b, b, pt.K32, b, nullptr, pt.Kh, pt.Kl, b, nullptr, nullptr));
+  RR_TRY(gemm_bf16_tc_split(n, b, b, pt.Xrh, pt.Xrl, b, pt.Kh, pt.Kl, b, pt.P, n, nullptr, 0, nullptr, s));
+  return sub_block_f32(s, n, b, pt.P, n, T, ldt);
 }
 
 // Pencil solves that record which sizes ran, so the condition estimate of
@@ -1136,9 +1146,14 @@ static void carve_eig(Arena& ar, const Op& op, int64_t b, bool refine, EigBufs& 
     if (op.dt == RR_BF16 && proj_tc_applies(n, b)) {
       w.ptc.Xh = (__nv_bfloat16*)ar.take_bytes(n * b * 2);
       w.ptc.Xl = (__nv_bfloat16*)ar.take_bytes(n * b * 2);
+      w.ptc.Xrh = (__nv_bfloat16*)ar.take_bytes(n * b * 2);
+      w.ptc.Xrl = (__nv_bfloat16*)ar.take_bytes(n * b * 2);
       w.ptc.Th = (__nv_bfloat16*)ar.take_bytes(n * b * 2);
       w.ptc.Tl = (__nv_bfloat16*)ar.take_bytes(n * b * 2);
+      w.ptc.Kh = (__nv_bfloat16*)ar.take_bytes(b * b * 2);
+      w.ptc.Kl = (__nv_bfloat16*)ar.take_bytes(b * b * 2);
       w.ptc.K32 = ar.take<float>(b * b);
+      w.ptc.P = ar.take<float>(n * b);
     }
   } else {
     w.X2 = nullptr;
@@ -1351,14 +1366,12 @@ static rr_status eig_run(const rr_operator* Aop, const rr_params* p, double* the
         prev_mx = INFINITY;
         continue;
       }
-      // FP32 copy (and, for tall blocks, split BF16 pairs) of the Ritz vectors
-      // for the projections of this sweep
-      STAGE(RR_STAGE_OTHER, cast_f32(s, n, b, w.X, n, w.X32, n));
-      if (w.ptc.Xh)
-        STAGE(RR_STAGE_OTHER, scale_split(s, RR_F64, n, b, w.X, n, nullptr, w.ptc.Xh, w.ptc.Xl, n, nullptr, nullptr));
+      // FP32 copy (for tall BF16-basis blocks split BF16 pairs) of the Ritz
+      // vectors for the projections of this sweep
+      if (w.ptc.Xh) STAGE(RR_STAGE_OTHER, proj_tc_prepare(w.ptc, s, n, b, w.X, n));
+      else STAGE(RR_STAGE_OTHER, cast_f32(s, n, b, w.X, n, w.X32, n));
       auto proj = [&](float* T) -> rr_status {
-        return w.ptc.Xh ? project_out_tc(w.ptc, s, n, b, w.X32, n, T, n, w.Y)
-                        : project_out(w.c, s, n, b, w.X32, n, T, n, w.Y);
+        return w.ptc.Xh ? project_out_tc(w.ptc, s, n, b, T, n) : project_out(w.c, s, n, b, w.X32, n, T, n, w.Y);
       };
       if (cheb) {
         // D_1 = (s1/e) R;  D_{j+1} = (2 s_{j+1}/e)(A - cI) D_j - s_j s_{j+1} D_{j-1}

@@ -109,7 +109,7 @@ rr_status gram_f32acc(cudaStream_t s, int64_t n, int64_t p, int64_t q, const flo
 rr_status sub_lowrank_f32(cudaStream_t s, int64_t n, int64_t b, int64_t p, const float* X, int64_t ldx,
                           const double* K, int64_t ldk, float* T, int64_t ldt);
 rr_status cast_f32(cudaStream_t s, int64_t n, int64_t b, const double* X, int64_t ldx, float* Y, int64_t ldy);
-rr_status widen_f32(cudaStream_t s, int64_t n, const float* x, double* y);
+rr_status sub_block_f32(cudaStream_t s, int64_t n, int64_t b, const float* P, int64_t ldp, float* T, int64_t ldt);
 rr_status tc_take_error(cudaStream_t s);
 rr_status tc_prepare_attributes();
 
