@@ -107,3 +107,20 @@ def test_struct_layout_matches_header(tmp_path):
         assert int(got[t]) == ctypes.sizeof(cls), t
         for f in fields[t]:
             assert int(got[f"{t}.{f}"]) == getattr(cls, f).offset, (t, f)
+
+
+def test_batch_tuning_argument_errors(L):
+    """rr_batch_svd_tuned rejects launch parameters out of range (branches
+    outside 1..64, order or fixed_sweeps other than 0 / 1) before anything
+    reaches the device."""
+    from paper_2505_00281_gb300._lib import RR, RrBatchTuning, RrInfo
+    op = (type(_op(256, 64)) * 1)(_op(256, 64))
+    p = _params(k=8, block=16)
+    ptrs = (ctypes.c_void_p * 1)(FAKE)
+    per = (ctypes.c_int32 * 1)()
+    infos = (RrInfo * 1)()
+    for t in (RrBatchTuning(0, 0, 0, 0), RrBatchTuning(65, 0, 0, 0), RrBatchTuning(16, -1, 0, 0),
+              RrBatchTuning(16, 0, 2, 0), RrBatchTuning(16, 0, 0, 2)):
+        assert L.rr_batch_svd_tuned(1, op, ctypes.byref(p), 7, ptrs, ptrs, ptrs, FAKE, 1 << 40, ctypes.byref(t),
+                                    per, infos, None) == RR.ERR_ARG, (t.branches, t.max_splits, t.order,
+                                                                      t.fixed_sweeps)
