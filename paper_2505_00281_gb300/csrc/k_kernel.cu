@@ -38,7 +38,6 @@ template <> __device__ __forceinline__ double kexp<double>(double x) { return ex
 template <typename TX> __device__ __forceinline__ float ldx_f(const TX* p);
 template <> __device__ __forceinline__ float ldx_f<float>(const float* p) { return *p; }
 template <> __device__ __forceinline__ float ldx_f<__nv_bfloat16>(const __nv_bfloat16* p) { return __bfloat162float(*p); }
-template <> __device__ __forceinline__ float ldx_f<double>(const double* p) { return (float)*p; }
 
 template <typename TC, typename TX>
 __device__ __forceinline__ TC load_x(const TX* p) {
