@@ -673,6 +673,8 @@ def run_stage(args):
         from paper_2505_00281_gb300 import warmstart as WS
         Ng = args.grid
         k, bs, deg, hidden, depth = (16, 24, 10, 24, 3) if Ng <= 64 else (32, 48, 20, 32, 4)
+        hidden = args.hidden or hidden
+        depth = args.depth or depth
 
         def problems(seeds):
             for sd in seeds:
@@ -953,6 +955,8 @@ def main():
     ap.add_argument("--train", type=int, default=48, help="training solves for --stage warm")
     ap.add_argument("--test", type=int, default=8, help="held-out solves for --stage warm")
     ap.add_argument("--epochs", type=int, default=40, help="training epochs for --stage warm")
+    ap.add_argument("--hidden", type=int, default=0, help="--stage warm: hidden channels (0: by grid)")
+    ap.add_argument("--depth", type=int, default=0, help="--stage warm: convolution layers (0: by grid)")
     args = ap.parse_args()
     if args.stage:
         return run_stage(args)
