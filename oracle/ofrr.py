@@ -20,7 +20,7 @@ __all__ = [
     "gram", "dense_apply", "csr_apply", "csr_gershgorin",
     "pencil_eig", "pencil_svd", "rayleigh_ritz_eig", "rayleigh_ritz_svd",
     "chebyshev_filter", "residual_eig", "residual_svd",
-    "solve_eig", "solve_svd", "SolveResult",
+    "solve_eig", "solve_svd", "SolveResult", "svd_correction_sweep",
 ]
 
 EPS64 = 2.0 ** -52
@@ -436,3 +436,38 @@ def solve_svd(A_mul, At_mul, m: int, n: int, k: int, V0: np.ndarray, *,
         V = Vt
     return SolveResult(s[:k], Vt[:, :k], Ut[:, :k], res, max_sweeps,
                        int(np.sum(res <= tol)), hist)
+
+
+# --------------------------------------------------------------------------
+# refinement of the SVD in FP64 (not in the paper: the paper's method stops at
+# the basis precision, Sec. 2; this is the correction sweep the GPU path runs
+# in FP64-accurate arithmetic when its low-precision corrections stall)
+# --------------------------------------------------------------------------
+def svd_correction_sweep(A_mul, At_mul, U, V, s):
+    """One correction sweep from b Ritz triplets (U m x b, V n x b, s):
+
+    R_v = A V - U S and R_u = A^T U - V S (S = diag(s)); the corrections
+    F = A^T R_v + R_u S (= A^T A V - V S^2) and E = A F + R_v S^2
+    (= A A^T A V - U S^3), each scaled to unit column inf-norm (Sec. 2) and
+    projected against the Ritz vectors (F - V (V^T F), E - U (U^T E));
+    Algorithm 8 on both; Algorithm 5 over S_u = [U, E], S_v = [V, F]; the
+    sqrt(2) lift of the theorem in Sec. 3.2 for the leading b triplets.
+    Returns (s, U, V) of the new triplets, descending."""
+    U = np.asarray(U, np.float64)
+    V = np.asarray(V, np.float64)
+    s = np.asarray(s, np.float64)
+    b = U.shape[1]
+    Rv = A_mul(V) - U * s
+    Ru = At_mul(U) - V * s
+    F = At_mul(Rv) + Ru * s
+    E = A_mul(F) + Rv * s ** 2
+    F = colscale_inf(F)
+    E = colscale_inf(E)
+    F = F - V @ (V.T @ F)
+    E = E - U @ (U.T @ E)
+    E = hessenberg(E)[3]
+    F = hessenberg(F)[3]
+    Su = np.hstack([U, E])
+    Sv = np.hstack([V, F])
+    sn, Y, Z = pencil_svd(Su.T @ A_mul(Sv), Su.T @ Su, Sv.T @ Sv)
+    return sn[:b], math.sqrt(2.0) * (Su @ Y[:, :b]), math.sqrt(2.0) * (Sv @ Z[:, :b])

@@ -358,3 +358,36 @@ def test_colscale_inf_pins():
     # empty row count: shape kept, no NaN
     E = O.colscale_inf(np.zeros((0, 3)))
     assert E.shape == (0, 3)
+
+
+def test_svd_correction_sweep_fixed_point_and_contraction():
+    """The FP64 correction sweep of the SVD refinement (the GPU's polish):
+    exact singular triplets (LAPACK) are its fixed point; from the paper's
+    method after two sweeps (residual ~6e-4 on sigma_j = j^-1.5 with 8 of 16
+    wanted) each of the first three sweeps contracts the residual by more
+    than 30x (1.6e-8, 4.6e-11, 5.3e-13), the fifth ends at the FP64 floor
+    (4.8e-15; without the projection of the corrections against the Ritz
+    vectors the Gram of [U, E] reaches cond 1e7 and the residual stalls near
+    1e-13), sigma is at the FP64 level after the first and the lifted
+    vectors have unit 2-norm (the sqrt(2) of the theorem)."""
+    m, n, b, k = 300, 75, 16, 8
+    sg = wl.config4_sigma(n)
+    A = wl.dense_svd(m, n, sg, 4321)
+    Am, Atm = O.dense_apply(A)
+    Uf, sf, Vft = np.linalg.svd(A, full_matrices=False)
+    s1, U1, V1 = O.svd_correction_sweep(Am, Atm, Uf[:, :b], Vft[:b].T, sf[:b])
+    assert np.max(np.abs(s1[:k] - sg[:k]) / sg[:k]) <= 1e-13
+    assert O.residual_svd(Am, Atm, U1[:, :k], V1[:, :k], s1[:k]).max() <= 1e-12
+    r = O.solve_svd(Am, Atm, m, n, b, wl.uniform_block(n, b, 4322), degree=2, max_sweeps=2, tol=1e-16)
+    res0 = O.residual_svd(Am, Atm, r.U[:, :k], r.X[:, :k], r.values[:k]).max()
+    assert res0 > 1e-9, res0
+    U, V, sv, hist = r.U, r.X, r.values, [res0]
+    for it in range(5):
+        sv, U, V = O.svd_correction_sweep(Am, Atm, U, V, sv)
+        hist.append(O.residual_svd(Am, Atm, U[:, :k], V[:, :k], sv[:k]).max())
+        if it < 3:
+            assert hist[-1] <= hist[-2] / 30, hist
+        assert np.max(np.abs(sv[:k] - sg[:k]) / sg[:k]) <= 1e-14
+        assert np.abs(np.linalg.norm(U, axis=0) - 1).max() <= 1e-12
+        assert np.abs(np.linalg.norm(V, axis=0) - 1).max() <= 1e-12
+    assert hist[-1] <= 2e-14, hist
